@@ -1,0 +1,214 @@
+/*
+ * wc4d -- GB300 (sm_103a) inner loop of forcing-formulation weak-constraint
+ * 4D-Var with randomised spectral limited-memory preconditioning.
+ *
+ * Method: Dauzickaite, Lawless, Scott, van Leeuwen, "Randomised
+ * preconditioning for the forcing formulation of weak constraint 4D-Var".
+ *
+ * The library solves A x = b for the first-level preconditioned Hessian
+ *     A = I + D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2}          (eq. 10)
+ * with D = diag(B, Q_1..Q_N), L^{-1} the block lower-triangular product of
+ * the linearised model over the N subwindows (eq. 5), H the observation
+ * operator and R = sigma_o^2 I.  It applies A to blocks of probe vectors,
+ * builds Ritz pairs with REVD (Alg. 3, plus power iterations), randomised
+ * Nystrom (Alg. 4) or REVD_ritzit (Alg. 5), forms the spectral LMP factor
+ * C = I - sum_i (1 - theta_i^{-1/2}) u_i u_i^T (eq. 15-16) and runs split-
+ * preconditioned CG (Alg. 1).
+ *
+ * Conventions (every entry point):
+ *  - A control-space block of K vectors (dimension nA = n (N+1)) is a
+ *    column-major nA x K matrix with leading dimension ld >= nA; row t*n + s
+ *    holds grid point s of time block t (t = 0: x_0, t >= 1: eta_t).
+ *  - "device" pointers are CUDA global-memory pointers of the current
+ *    device; "host" pointers are ordinary memory.  The caller owns every
+ *    pointer it passes; the library owns its workspaces (allocated on
+ *    demand, freed by wc4d_destroy).
+ *  - All work is queued on the context's stream.  Calls that return
+ *    scalars to host memory (theta, iters, relres, histories) synchronise
+ *    that stream before returning.
+ *  - Errors are returned as wc4d_status; wc4d_last_error() gives a message.
+ *    Nothing traps: device-side failures (non-SPD Gram, CG breakdown,
+ *    non-finite values) come back as statuses.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef WC4D_H
+#define WC4D_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wc4d_ctx wc4d_ctx;
+
+typedef enum {
+    WC4D_OK = 0,
+    WC4D_EINVAL = -1,      /* bad argument or unsupported size                  */
+    WC4D_ENOMEM = -2,      /* device allocation failed                          */
+    WC4D_ECUDA = -3,       /* a CUDA runtime call failed                        */
+    WC4D_ENOTSPD = -4,     /* Cholesky of a Gram matrix broke down              */
+    WC4D_EBREAKDOWN = -5,  /* CG: p^T A p <= 0 or not finite                    */
+    WC4D_ENOCONV = -6,     /* CG: maxit reached before the tolerance            */
+    WC4D_ETIMEOUT = -7,    /* an iteration limit inside the library was hit     */
+    WC4D_ENAN = -8,        /* a non-finite value was produced                   */
+    WC4D_ESTATE = -9       /* a required set-up call has not been made          */
+} wc4d_status;
+
+typedef enum { WC4D_FP64 = 0, WC4D_MIXED = 1 } wc4d_precision;
+typedef enum { WC4D_REVD = 0, WC4D_NYSTROM = 1, WC4D_RITZIT = 2 } wc4d_method;
+typedef enum { WC4D_MODEL_DENSE = 0, WC4D_MODEL_L96 = 1 } wc4d_model;
+typedef enum { WC4D_CORR_SOAR = 0, WC4D_CORR_GAUSS = 1, WC4D_CORR_DIAG = 2 } wc4d_corr;
+
+/* Problem statement (Section 2; Section 5 for the two model families).
+ *  n, N        grid points per time block and number of subwindows; nA = n (N+1).
+ *  model       WC4D_MODEL_DENSE: a linear model given as one dense n x n
+ *              propagator M_t per subwindow (or one shared by all);
+ *              WC4D_MODEL_L96: Lorenz-96 (eq. 22 of the paper) integrated by RK4,
+ *              with tangent-linear and adjoint sweeps along the stored
+ *              nonlinear trajectory.
+ *  steps, dt   RK4 steps per subwindow and step size (Lorenz-96 only).
+ *  F           Lorenz-96 forcing.
+ *  sigma_o2    R_t = sigma_o2 * I.
+ *  obs_stride  H_t observes the points s = 0, obs_stride, 2 obs_stride, ...
+ *  obs_t0, obs_tstride  observed times t = obs_t0, obs_t0 + obs_tstride, ... <= N.
+ *  M_shared    dense model: 1 = one propagator used for every subwindow. */
+typedef struct {
+    int32_t n, N;
+    int32_t model;
+    int32_t steps;
+    double dt;
+    double F;
+    double sigma_o2;
+    int32_t obs_stride, obs_t0, obs_tstride;
+    int32_t M_shared;
+} wc4d_problem;
+
+/* Create a context bound to the current CUDA device and the given stream
+ * (a cudaStream_t; NULL = the legacy default stream).  Fails with
+ * WC4D_EINVAL for n < 2, N < 1, n > 8192 or a non-positive sigma_o2. */
+wc4d_status wc4d_create(wc4d_ctx **ctx, const wc4d_problem *prob, void *cuda_stream);
+void        wc4d_destroy(wc4d_ctx *ctx);
+const char *wc4d_last_error(const wc4d_ctx *ctx);
+wc4d_status wc4d_set_stream(wc4d_ctx *ctx, void *cuda_stream);
+
+/* ---- problem set-up (not part of the timed inner loop) ---------------- */
+
+/* Linearised model M_t (eq. 5): copy a dense row-major n x n propagator from
+ * device memory into the context.  t in [0, N) sets subwindow t; t = -1 sets
+ * every subwindow (or the shared one when M_shared).  The library keeps
+ * FP64, FP32 and BF16 copies and their transposes (for L^{-T}). */
+wc4d_status wc4d_set_propagator(wc4d_ctx *ctx, int32_t t, const double *M_device);
+
+/* Build the propagator of `steps` Crank-Nicolson steps of periodic
+ * advection-diffusion u_t + c u_z = kappa u_zz on [0,1) with n points and
+ * centred differences, on the device, from the closed-form Fourier symbol
+ * of one step ((1 + dt/2 k_m)/(1 - dt/2 k_m), k_m the symbol of the centred
+ * operator), and store it for every subwindow. */
+wc4d_status wc4d_build_advdiff_propagator(wc4d_ctx *ctx, double kappa, double c, double dt, int32_t steps);
+
+/* Covariance blocks of D (Section 5): block 0 = B, block 1 = Q_t (all
+ * subwindows).  Circulant on the periodic grid with first row
+ * variance * rho(r), r the periodic distance in grid points:
+ * SOAR (1 + r/L) e^{-r/L}, Gaussian e^{-r^2/(2 L^2)}, or DIAG (variance * I).
+ * The symmetric square root D^{1/2} is formed from the DFT eigenvalues
+ * sqrt(max(lambda, 0)) on the device. */
+wc4d_status wc4d_set_covariance(wc4d_ctx *ctx, int32_t block, int32_t corr, double variance, double length);
+/* Same, from an explicit first row (host, n values, symmetric). */
+wc4d_status wc4d_set_covariance_row(wc4d_ctx *ctx, int32_t block, const double *row_host);
+
+/* Outer-loop quantities (Section 2.1): run the model from the background
+ * xb (host, n values) over the window (the nonlinear RK4 model for
+ * Lorenz-96, which also stores the linearisation trajectory in FP64 and
+ * FP32; the linear propagators otherwise), form the innovations
+ * d_t = y_t - H_t x_t (y: host, nobs values, time-major over the observed
+ * times) and the right-hand side of eq. 10, rhs = D^{1/2} L^{-T} H^T R^{-1} d
+ * (+ D^{-1/2} b when Dm12b_host is not NULL). */
+wc4d_status wc4d_set_background_obs(wc4d_ctx *ctx, const double *xb_host, const double *y_host,
+                                    const double *Dm12b_host);
+/* Number of observations q of the problem. */
+int64_t     wc4d_nobs(const wc4d_ctx *ctx);
+/* Copy the right-hand side (nA values) to device memory. */
+wc4d_status wc4d_get_rhs(wc4d_ctx *ctx, double *rhs_device);
+
+/* ---- the hot path ------------------------------------------------------ */
+
+/* Y = A X for a block of K vectors (eq. 10): D^{1/2} by FFT (n a power of
+ * two) or direct circulant products, the forward sweep L^{-1}, H^T R^{-1} H,
+ * the adjoint sweep L^{-T}, then X + D^{1/2}(.).  X and Y are device,
+ * column-major, leading dimension ld; they must not overlap.
+ * WC4D_FP64: double in/out.  WC4D_MIXED: float in/out, FP32 operators and
+ * FP32 accumulation (tensor cores for K >= 16 on dense models). */
+wc4d_status wc4d_hvp(wc4d_ctx *ctx, const void *X, void *Y, int32_t K, int64_t ld, int32_t precision);
+
+/* Gaussian probe block (Alg. 3-5, step 1): G (device, rows x cols,
+ * column-major, ld) from Philox4x32-10 keyed by seed (Salmon et al. 2011),
+ * element e = col*rows + row taking Box-Muller output (e & 1) of counter
+ * e >> 1, with uniforms (hi27:lo26 of two words + 1) / 2^53. */
+wc4d_status wc4d_gaussian(wc4d_ctx *ctx, uint64_t seed, int64_t rows, int32_t cols, int64_t ld, double *G);
+
+/* Randomised Ritz pairs of A (Section 4) kept in the context for the LMP:
+ * method REVD (Alg. 3 with q_power extra products and orthonormalisations),
+ * NYSTROM (Alg. 4) or RITZIT (Alg. 5), target rank k, oversampling l.
+ * G_device: explicit probes (nA x (k+l), ld = nA, FP64) or NULL to draw
+ * them with wc4d_gaussian(seed).  theta_host: k Ritz values, decreasing.
+ * Orthonormalisation is CholeskyQR2 with an FP64 Gram; the small
+ * eigenproblems are solved by one-sided Jacobi in FP64. */
+wc4d_status wc4d_sketch(wc4d_ctx *ctx, int32_t method, int32_t k, int32_t l, int32_t q_power,
+                        uint64_t seed, const double *G_device, double *theta_host, int32_t precision);
+/* Copy the current Ritz vectors (nA x k, column-major, FP64) and values. */
+wc4d_status wc4d_get_ritz(wc4d_ctx *ctx, double *U_device, double *theta_host);
+/* Install explicit pairs (orthonormal U, device nA x k; theta host). */
+wc4d_status wc4d_set_ritz(wc4d_ctx *ctx, int32_t k, const double *U_device, const double *theta_host);
+
+/* y = C v (transpose = 0) or C^T v for the spectral-LMP factor of the
+ * current Ritz pairs (eq. 16 in its closed form for orthonormal U; C is
+ * symmetric then).  v, y: device, nA doubles. */
+wc4d_status wc4d_lmp_apply(wc4d_ctx *ctx, const double *v, double *y, int32_t transpose);
+
+/* Split-preconditioned CG (Alg. 1) on A x = rhs from x_0 = 0.  use_lmp: 1 =
+ * precondition with the current Ritz pairs.  Stops when |rhs - A x| / |rhs|
+ * <= tol (the unpreconditioned residual carried by recurrence) or after
+ * maxit iterations (WC4D_ENOCONV); force_iters > 0 runs exactly that many.
+ * WC4D_MIXED: FP32 vectors and operators with FP64 scalars, wrapped in FP64
+ * true-residual refinement until the FP64 residual meets tol.
+ * x_device: nA doubles (output).  iters/relres may be NULL; relres is the
+ * final true relative residual, computed in FP64.  qcf_drop_host (maxit
+ * doubles or NULL): alpha_j rho_{j-1} / 2 per iteration, the decrease of
+ * the quadratic cost (eq. 4). */
+wc4d_status wc4d_pcg(wc4d_ctx *ctx, double *x_device, double tol, int32_t maxit, int32_t use_lmp,
+                     int32_t force_iters, int32_t precision, int32_t *iters, double *relres,
+                     double *qcf_drop_host);
+
+/* The inner loop of Section 4: Ritz pairs by `method`, spectral LMP, PCG
+ * on the exact A to tol.  Equivalent to wc4d_sketch + wc4d_pcg(use_lmp=1). */
+wc4d_status wc4d_inner_loop(wc4d_ctx *ctx, int32_t method, int32_t k, int32_t l, int32_t q_power,
+                            uint64_t seed, double tol, int32_t maxit, int32_t precision,
+                            double *x_device, int32_t *iters, double *relres);
+
+/* ---- small building blocks, exported for verification ------------------ */
+
+/* CholeskyQR2 in place: Y (device, rows x m, ld) becomes Z with orthonormal
+ * columns and span(Z) = span(Y); R_host (m x m column-major, may be NULL)
+ * receives the upper-triangular factor with Y = Z R, positive diagonal. */
+wc4d_status wc4d_orthonormalize(wc4d_ctx *ctx, double *Y, int64_t rows, int32_t m, int64_t ld, double *R_host);
+/* Eigen-decomposition of a symmetric positive semi-definite m x m matrix
+ * (device, column-major) by one-sided Jacobi: w_host decreasing, V_device
+ * (m x m column-major) the eigenvectors. */
+wc4d_status wc4d_symeig(wc4d_ctx *ctx, int32_t m, const double *S_device, double *w_host, double *V_device);
+/* Pieces of the Hessian product (eq. 5, eq. 10), for verification and for
+ * callers that compose their own operators.  Blocks as for wc4d_hvp.
+ *   wc4d_apply_dsqrt: Y = D^{1/2} X.
+ *   wc4d_apply_linv : W <- L^{-1} W in place (w_{t+1} += M_t w_t).
+ *   wc4d_apply_linvT: W <- L^{-T} W in place (w_t += M_t^T w_{t+1}). */
+wc4d_status wc4d_apply_dsqrt(wc4d_ctx *ctx, const void *X, void *Y, int32_t K, int64_t ld, int32_t precision);
+wc4d_status wc4d_apply_linv(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int32_t precision);
+wc4d_status wc4d_apply_linvT(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int32_t precision);
+/* Copy the FP64 propagator of subwindow t (dense model) to device memory. */
+wc4d_status wc4d_get_propagator(wc4d_ctx *ctx, int32_t t, double *M_device);
+/* Products with A issued so far (block products count once). */
+int64_t     wc4d_hvp_count(wc4d_ctx *ctx, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -301,7 +301,7 @@ def obs_adjoint(p, W):
 
 
 def hvp(p, X):
-    """Y = A X (eq. 8), X given as (K, nA)."""
+    """Y = A X (eq. 10), X given as (K, nA)."""
     X = _block(p, X)
     Y = np.zeros_like(X)
     lib().o_hvp(p.ptr, X.shape[0], _dp(X), p.nA, _dp(Y))
@@ -418,7 +418,7 @@ def ritzit(p, k, G):
 
 
 def lmp_apply(U, theta, v, transpose=False):
-    """C v (or C^T v) for the spectral-LMP factor of eq. 14; U is (k, nA)."""
+    """C v (or C^T v) for the spectral-LMP factor of eq. 16; U is (k, nA)."""
     U = _f64(np.atleast_2d(U)) if U is not None and len(theta) else np.zeros((0, len(v)))
     theta = _f64(theta)
     v = _f64(v)

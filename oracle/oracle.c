@@ -16,15 +16,15 @@
  *   Lorenz-96         fixed point x=F; RK4 order-4 convergence vs scipy;
  *                     TLM Taylor test; adjoint dot-product test
  *   L^{-1}, L^{-T}    adjoint test; L(L^{-1}x)=x with L from its definition
- *   A (eq. 8)         dense A vs an independent numpy build; symmetric;
+ *   A (eq. 10)         dense A vs an independent numpy build; symmetric;
  *                     n_A-q unit eigenvalues
  *   QR/Jacobi/Chol/SVD numpy cross-checks and identities
  *   REVD/Nystrom/ritzit subspace definitions (dense numpy), Ritz bounds,
  *                     full-sketch exactness, product counts (Table 1)
- *   LMP               C C^T = eq. 13 = eq. 12 with exact eigenvectors;
+ *   LMP               C C^T = eq. 15 = eq. 14 with exact eigenvectors;
  *                     unit eigenvalues of C^T A C; k = n_A gives A^{-1}
  *   PCG               dense solve; QCF drop vs eq. 4 evaluated directly;
- *                     finite termination; eq. 10 bound
+ *                     finite termination; eq. 12 bound
  */
 #include "oracle.h"
 
@@ -400,7 +400,7 @@ void o_l96_run(int32_t n, double F, double dt, int32_t nsteps, const double *x0,
  *   H_t   : observes s = 0, stride, 2 stride, ... at t >= obs_t0.
  *   R_t   : sigma_o2 * I.
  *   D^{1/2}: diag(B^{1/2}, Q^{1/2}, ..., Q^{1/2}).
- *   A     = I + D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2}   (eq. 8)
+ *   A     = I + D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2}   (eq. 10)
  * ====================================================================== */
 static int64_t g_hvp_count = 0;
 
@@ -559,7 +559,7 @@ void o_obs_adjoint(const o_problem *p, int32_t K, const double *W, int64_t ld, d
     for (int32_t j = 0; j < K; ++j) obs_col(p, W + j * ld, V + j * ld);
 }
 
-/* Y = A X, column by column, following eq. 8 from right to left. */
+/* Y = A X, column by column, following eq. 10 from right to left. */
 void o_hvp(const o_problem *p, int32_t K, const double *X, int64_t ld, double *Y)
 {
     int64_t nA = (int64_t)p->n * (p->N + 1);
@@ -617,7 +617,7 @@ void o_innovation(const o_problem *p, const double *xb, const double *eta, const
     free(xt);
 }
 
-/* Right-hand side of eq. 8: D^{-1/2} b + D^{1/2} L^{-T} H^T R^{-1} d.
+/* Right-hand side of eq. 10: D^{-1/2} b + D^{1/2} L^{-T} H^T R^{-1} d.
  * Dm12b (= D^{-1/2} b) may be NULL, meaning zero (first outer loop). */
 void o_rhs(const o_problem *p, const double *d, const double *Dm12b, double *rhs)
 {
@@ -1019,7 +1019,7 @@ int o_ritzit(const o_problem *p, int32_t k, int32_t l, const double *G, double *
 }
 
 /* ======================================================================
- * Spectral LMP factor (eq. 14): C = prod_{i=1..k} (I - (1 - theta_i^{-1/2})
+ * Spectral LMP factor (eq. 16): C = prod_{i=1..k} (I - (1 - theta_i^{-1/2})
  * u_i u_i^T).  C v applies the factor i = k first; C^T v applies i = 1
  * first.  A non-positive theta contributes the identity.
  * ====================================================================== */

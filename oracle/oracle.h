@@ -66,7 +66,7 @@ void o_l96_tlm(int32_t n, double F, double dt, const double *x, const double *dx
 void o_l96_adj(int32_t n, double F, double dt, const double *x, const double *ly, double *lx);
 void o_l96_run(int32_t n, double F, double dt, int32_t nsteps, const double *x0, double *traj);
 
-/* ---- the forcing-formulation operators (eq. 5, eq. 8) ------------------ */
+/* ---- the forcing-formulation operators (eq. 5, eq. 10) ------------------ */
 int64_t o_nobs(const o_problem *p);
 void o_model_apply(const o_problem *p, int32_t t, const double *x, double *y);
 void o_model_apply_T(const o_problem *p, int32_t t, const double *x, double *y);
@@ -93,7 +93,7 @@ int o_revd(const o_problem *p, int32_t k, int32_t l, int32_t q, const double *G,
 int o_nystrom(const o_problem *p, int32_t k, int32_t l, const double *G, double *U, double *theta);
 int o_ritzit(const o_problem *p, int32_t k, int32_t l, const double *G, double *U, double *theta);
 
-/* ---- spectral LMP (eq. 13-14) and split-preconditioned CG (Alg. 1) ------ */
+/* ---- spectral LMP (eq. 15-16) and split-preconditioned CG (Alg. 1) ------ */
 void o_lmp_apply(int64_t nA, int32_t k, const double *U, const double *theta, int32_t transpose,
                  const double *v, double *y);
 int  o_pcg(const o_problem *p, const double *rhs, int32_t k, const double *U, const double *theta,

@@ -1,3 +1,322 @@
 """GB300-native inner loop of forcing-formulation weak-constraint 4D-Var with
-randomised spectral-LMP preconditioning.  The compute runs in libwc4d.so
-(hand-written CUDA for sm_103a); this package is its thin ctypes binding."""
+randomised spectral-LMP preconditioning.
+
+All arithmetic runs in libwc4d.so (hand-written CUDA for sm_103a, C-ABI in
+include/wc4d.h).  This module is its thin ctypes binding: the functions keep
+the C names and only marshal arguments (torch CUDA tensors -> device
+pointers, numpy arrays -> host pointers).  A block of K control vectors is a
+torch tensor of shape (K, nA): row j is vector j, i.e. the column-major
+nA x K matrix of the C-ABI with leading dimension nA.
+
+There is no CPU fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded synthetic inputs; no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwc4d.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTSPD, EBREAKDOWN, ENOCONV, ETIMEOUT, ENAN, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+FP64, MIXED = 0, 1
+REVD, NYSTROM, RITZIT = 0, 1, 2
+MODEL_DENSE, MODEL_L96 = 0, 1
+CORR_SOAR, CORR_GAUSS, CORR_DIAG = 0, 1, 2
+METHODS = {"revd": REVD, "nystrom": NYSTROM, "ritzit": RITZIT}
+_STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTSPD", -5: "EBREAKDOWN",
+           -6: "ENOCONV", -7: "ETIMEOUT", -8: "ENAN", -9: "ESTATE"}
+
+
+class WC4DError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"wc4d status {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(C.Structure):
+    """wc4d_problem (include/wc4d.h)."""
+    _fields_ = [("n", C.c_int32), ("N", C.c_int32), ("model", C.c_int32), ("steps", C.c_int32),
+                ("dt", C.c_double), ("F", C.c_double), ("sigma_o2", C.c_double),
+                ("obs_stride", C.c_int32), ("obs_t0", C.c_int32), ("obs_tstride", C.c_int32),
+                ("M_shared", C.c_int32)]
+
+
+_V = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_SIGS = {
+    "wc4d_create": (C.c_int, [C.POINTER(_V), C.POINTER(Problem), _V]),
+    "wc4d_destroy": (None, [_V]),
+    "wc4d_last_error": (C.c_char_p, [_V]),
+    "wc4d_set_stream": (C.c_int, [_V, _V]),
+    "wc4d_set_propagator": (C.c_int, [_V, C.c_int32, _V]),
+    "wc4d_build_advdiff_propagator": (C.c_int, [_V, C.c_double, C.c_double, C.c_double, C.c_int32]),
+    "wc4d_set_covariance": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_double, C.c_double]),
+    "wc4d_set_covariance_row": (C.c_int, [_V, C.c_int32, _D]),
+    "wc4d_set_background_obs": (C.c_int, [_V, _D, _D, _D]),
+    "wc4d_nobs": (C.c_int64, [_V]),
+    "wc4d_get_rhs": (C.c_int, [_V, _V]),
+    "wc4d_hvp": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
+    "wc4d_gaussian": (C.c_int, [_V, C.c_uint64, C.c_int64, C.c_int32, C.c_int64, _V]),
+    "wc4d_sketch": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _V, _D, C.c_int32]),
+    "wc4d_get_ritz": (C.c_int, [_V, _V, _D]),
+    "wc4d_set_ritz": (C.c_int, [_V, C.c_int32, _V, _D]),
+    "wc4d_lmp_apply": (C.c_int, [_V, _V, _V, C.c_int32]),
+    "wc4d_pcg": (C.c_int, [_V, _V, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _I32, _D, _D]),
+    "wc4d_inner_loop": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_double,
+                                  C.c_int32, C.c_int32, _V, _I32, _D]),
+    "wc4d_orthonormalize": (C.c_int, [_V, _V, C.c_int64, C.c_int32, C.c_int64, _D]),
+    "wc4d_symeig": (C.c_int, [_V, C.c_int32, _V, _D, _V]),
+    "wc4d_hvp_count": (C.c_int64, [_V, C.c_int32]),
+    "wc4d_apply_dsqrt": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
+    "wc4d_apply_linv": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
+    "wc4d_apply_linvT": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
+    "wc4d_get_propagator": (C.c_int, [_V, C.c_int32, _V]),
+}
+EXPORTS = tuple(_SIGS)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libwc4d.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libwc4d.so is not built ({p}); run __graft_entry__.build() first")
+            L = C.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    from ._build import build as _b
+    return _b(force=force)
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("device argument must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("device argument must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(int(t))
+
+
+def _hp(a):
+    """Host float64 pointer (keeps a contiguous copy alive via the caller)."""
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_D)
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(ctx, status):
+    if status != OK:
+        msg = load().wc4d_last_error(ctx)
+        raise WC4DError(status, msg.decode() if msg else "")
+    return status
+
+
+# --------------------------------------------------------------------------
+# C-ABI, one Python function per entry point
+# --------------------------------------------------------------------------
+def wc4d_create(prob: Problem, stream=None):
+    ctx = C.c_void_p()
+    st = load().wc4d_create(C.byref(ctx), C.byref(prob), _stream(stream))
+    if st != OK:
+        raise WC4DError(st, "wc4d_create rejected the problem")
+    return ctx
+
+
+def wc4d_destroy(ctx):
+    load().wc4d_destroy(ctx)
+
+
+def wc4d_last_error(ctx):
+    msg = load().wc4d_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def wc4d_set_stream(ctx, stream=None):
+    _check(ctx, load().wc4d_set_stream(ctx, _stream(stream)))
+
+
+def wc4d_set_propagator(ctx, t, M):
+    _check(ctx, load().wc4d_set_propagator(ctx, int(t), _ptr(M)))
+
+
+def wc4d_build_advdiff_propagator(ctx, kappa, c, dt, steps):
+    _check(ctx, load().wc4d_build_advdiff_propagator(ctx, float(kappa), float(c), float(dt), int(steps)))
+
+
+def wc4d_set_covariance(ctx, block, corr, variance, length):
+    _check(ctx, load().wc4d_set_covariance(ctx, int(block), int(corr), float(variance), float(length)))
+
+
+def wc4d_set_covariance_row(ctx, block, row):
+    row = np.ascontiguousarray(row, dtype=np.float64)
+    _check(ctx, load().wc4d_set_covariance_row(ctx, int(block), _hp(row)))
+
+
+def wc4d_set_background_obs(ctx, xb, y, Dm12b=None):
+    xb = np.ascontiguousarray(xb, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    Dm = None if Dm12b is None else np.ascontiguousarray(Dm12b, dtype=np.float64)
+    _check(ctx, load().wc4d_set_background_obs(ctx, _hp(xb), _hp(y), _hp(Dm)))
+
+
+def wc4d_nobs(ctx):
+    return int(load().wc4d_nobs(ctx))
+
+
+def wc4d_get_rhs(ctx, rhs):
+    _check(ctx, load().wc4d_get_rhs(ctx, _ptr(rhs)))
+
+
+def wc4d_hvp(ctx, X, Y, K, ld, precision=FP64):
+    _check(ctx, load().wc4d_hvp(ctx, _ptr(X), _ptr(Y), int(K), int(ld), int(precision)))
+
+
+def wc4d_gaussian(ctx, seed, rows, cols, ld, G):
+    _check(ctx, load().wc4d_gaussian(ctx, int(seed), int(rows), int(cols), int(ld), _ptr(G)))
+
+
+def wc4d_sketch(ctx, method, k, l, q_power, seed, G=None, precision=FP64):
+    th = np.zeros(int(k))
+    _check(ctx, load().wc4d_sketch(ctx, int(method), int(k), int(l), int(q_power), int(seed), _ptr(G),
+                                   _hp(th), int(precision)))
+    return th
+
+
+def wc4d_get_ritz(ctx, U, k):
+    th = np.zeros(int(k))
+    _check(ctx, load().wc4d_get_ritz(ctx, _ptr(U), _hp(th)))
+    return th
+
+
+def wc4d_set_ritz(ctx, k, U, theta):
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    _check(ctx, load().wc4d_set_ritz(ctx, int(k), _ptr(U), _hp(theta)))
+
+
+def wc4d_lmp_apply(ctx, v, y, transpose=0):
+    _check(ctx, load().wc4d_lmp_apply(ctx, _ptr(v), _ptr(y), int(transpose)))
+
+
+def wc4d_pcg(ctx, x, tol=1e-6, maxit=5000, use_lmp=1, force_iters=0, precision=FP64, qcf=False,
+             raise_on_noconv=True):
+    """Returns (iters, relres, qcf_drop or None, status)."""
+    it = C.c_int32(0)
+    rr = C.c_double(0.0)
+    cap = max(int(maxit), int(force_iters), 1)
+    q = np.zeros(cap) if qcf else None
+    st = load().wc4d_pcg(ctx, _ptr(x), float(tol), int(maxit), int(use_lmp), int(force_iters), int(precision),
+                         C.byref(it), C.byref(rr), _hp(q))
+    if st != OK and (raise_on_noconv or st != ENOCONV):
+        _check(ctx, st)
+    return it.value, rr.value, (q[:it.value] if qcf else None), st
+
+
+def wc4d_inner_loop(ctx, method, k, l, q_power, seed, tol, maxit, precision, x):
+    it = C.c_int32(0)
+    rr = C.c_double(0.0)
+    _check(ctx, load().wc4d_inner_loop(ctx, int(method), int(k), int(l), int(q_power), int(seed), float(tol),
+                                       int(maxit), int(precision), _ptr(x), C.byref(it), C.byref(rr)))
+    return it.value, rr.value
+
+
+def wc4d_orthonormalize(ctx, Y, rows, m, ld, want_R=True):
+    R = np.zeros(int(m) * int(m)) if want_R else None
+    _check(ctx, load().wc4d_orthonormalize(ctx, _ptr(Y), int(rows), int(m), int(ld), _hp(R)))
+    return None if R is None else R.reshape(int(m), int(m)).T.copy()   # ordinary (row, col) indexing
+
+
+def wc4d_symeig(ctx, m, S, V):
+    w = np.zeros(int(m))
+    _check(ctx, load().wc4d_symeig(ctx, int(m), _ptr(S), _hp(w), _ptr(V)))
+    return w
+
+
+def wc4d_apply_dsqrt(ctx, X, Y, K, ld, precision=FP64):
+    _check(ctx, load().wc4d_apply_dsqrt(ctx, _ptr(X), _ptr(Y), int(K), int(ld), int(precision)))
+
+
+def wc4d_apply_linv(ctx, W, K, ld, precision=FP64):
+    _check(ctx, load().wc4d_apply_linv(ctx, _ptr(W), int(K), int(ld), int(precision)))
+
+
+def wc4d_apply_linvT(ctx, W, K, ld, precision=FP64):
+    _check(ctx, load().wc4d_apply_linvT(ctx, _ptr(W), int(K), int(ld), int(precision)))
+
+
+def wc4d_get_propagator(ctx, t, M):
+    _check(ctx, load().wc4d_get_propagator(ctx, int(t), _ptr(M)))
+
+
+def wc4d_hvp_count(ctx, reset=False):
+    return int(load().wc4d_hvp_count(ctx, 1 if reset else 0))
+
+
+# --------------------------------------------------------------------------
+# Convenience: a context set up from a configuration of the inputs module
+# --------------------------------------------------------------------------
+class Solver:
+    """Owns one wc4d context for an inputs.Config: covariances, model and the
+    background/observations of the synthetic twin (all on the device)."""
+
+    def __init__(self, cfg, twin=None, M_shared=False, stream=None):
+        self.cfg = cfg
+        prob = Problem()
+        prob.n, prob.N = cfg.n, cfg.N
+        prob.model = MODEL_L96 if cfg.model == inputs.MODEL_L96 else MODEL_DENSE
+        prob.steps, prob.dt, prob.F, prob.sigma_o2 = cfg.steps, cfg.dt, cfg.F, cfg.sigma_o2
+        prob.obs_stride, prob.obs_t0, prob.obs_tstride = cfg.obs_stride, cfg.obs_t0, 1
+        prob.M_shared = 1 if M_shared else 0
+        self.prob = prob
+        self.ctx = wc4d_create(prob, stream)
+        self.nA = cfg.nA
+        wc4d_set_covariance(self.ctx, 0, cfg.b_kind, cfg.b_var, cfg.b_L)
+        wc4d_set_covariance(self.ctx, 1, cfg.q_kind, cfg.q_var, cfg.q_L)
+        if prob.model == MODEL_DENSE:
+            wc4d_build_advdiff_propagator(self.ctx, cfg.kappa, cfg.u, cfg.dt, cfg.steps)
+        if twin is not None:
+            wc4d_set_background_obs(self.ctx, twin.xb, twin.y)
+
+    def close(self):
+        if self.ctx:
+            wc4d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

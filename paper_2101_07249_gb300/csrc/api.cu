@@ -1,0 +1,1115 @@
+// C-ABI entry points of libwc4d: set-up, the Hessian product, the
+// randomised eigensolvers, the spectral LMP and PCG.  Every numerical step
+// runs in the kernels of setup.cu / sweep.cu / linalg.cu / tc_gemm.cu /
+// l96.cu; this file only sequences them on the context's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "wc4d_internal.cuh"
+
+// ============================================================================
+// helpers
+// ============================================================================
+wc4d_status set_err(wc4d_ctx *c, wc4d_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+void free_buf(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+wc4d_status ensure(wc4d_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (b.p && b.bytes >= bytes) return WC4D_OK;
+    if (b.p) {
+        cudaStreamSynchronize(c->stream);
+        free_buf(b);
+    }
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return set_err(c, WC4D_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return WC4D_OK;
+}
+
+static wc4d_status ensure_host(wc4d_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (b.p && b.bytes >= bytes) return WC4D_OK;
+    if (b.p) {
+        cudaStreamSynchronize(c->stream);
+        cudaFreeHost(b.p);
+        b.p = nullptr;
+    }
+    cudaError_t e = cudaMallocHost(&b.p, bytes < 64 ? 64 : bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return set_err(c, WC4D_ENOMEM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return WC4D_OK;
+}
+
+wc4d_status check_launch(wc4d_ctx *c, const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(c, WC4D_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return WC4D_OK;
+}
+
+static wc4d_status sync(wc4d_ctx *c, const char *what)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return set_err(c, WC4D_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return WC4D_OK;
+}
+
+template <typename T> static T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+static bool observed_time(const wc4d_problem &p, int t)
+{
+    int ts = p.obs_tstride > 0 ? p.obs_tstride : 1;
+    return t >= p.obs_t0 && t <= p.N && (t - p.obs_t0) % ts == 0;
+}
+
+static double obs_scale(const wc4d_ctx *c, int t)
+{
+    return observed_time(c->prob, t) ? 1.0 / c->prob.sigma_o2 : 0.0;
+}
+
+static int64_t mblk(const wc4d_ctx *c, int t) { return (c->nM == 1 ? 0 : (int64_t)t) * c->prob.n * c->prob.n; }
+
+// ============================================================================
+// small kernels used only by the orchestration
+// ============================================================================
+// d[k] = y[k] - x[t*n + s], observation k = i*per + o at t = t0 + i*ts, s = o*stride
+__global__ void k_innovation(int64_t nobs, int per, int t0, int ts, int stride, int n, const double *y,
+                             const double *x, double *d)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nobs) return;
+    int64_t i = k / per;
+    int o = (int)(k % per);
+    int64_t t = t0 + i * ts;
+    d[k] = y[k] - x[t * n + (int64_t)o * stride];
+}
+
+// v[t*n + s] = d[k] * scale (v zeroed beforehand)
+__global__ void k_scatter_obs(int64_t nobs, int per, int t0, int ts, int stride, int n, const double *d,
+                              double scale, double *v)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nobs) return;
+    int64_t i = k / per;
+    int o = (int)(k % per);
+    int64_t t = t0 + i * ts;
+    v[t * n + (int64_t)o * stride] = d[k] * scale;
+}
+
+// x[i] = (double) a[i] for float vectors
+__global__ void k_f64_from_f32_scaled(int64_t n, const float *a, double *b)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+// theta_out[i] = w[i] (eigenvalues) or w[i]^2 handled on the host side
+// (k values only).
+
+// ============================================================================
+// creation / destruction
+// ============================================================================
+extern "C" wc4d_status wc4d_create(wc4d_ctx **out, const wc4d_problem *prob, void *stream)
+{
+    if (!out || !prob) return WC4D_EINVAL;
+    *out = nullptr;
+    const wc4d_problem &p = *prob;
+    if (p.n < 2 || p.n > WC4D_FFT_MAX_N || p.N < 1 || !(p.sigma_o2 > 0.0) || p.obs_stride < 1 || p.obs_t0 < 0 ||
+        p.obs_tstride < 0 || (p.model != WC4D_MODEL_DENSE && p.model != WC4D_MODEL_L96))
+        return WC4D_EINVAL;
+    if (p.model == WC4D_MODEL_L96 && (p.steps < 1 || !(p.dt > 0.0) || p.n < 4)) return WC4D_EINVAL;
+    wc4d_ctx *c = new wc4d_ctx();
+    c->prob = p;
+    if (c->prob.obs_tstride == 0) c->prob.obs_tstride = 1;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->num_sms <= 0) c->num_sms = 1;
+    c->nA = (int64_t)p.n * (p.N + 1);
+    c->obs_per_time = (p.n + p.obs_stride - 1) / p.obs_stride;
+    for (int t = 0; t <= p.N; ++t)
+        if (observed_time(c->prob, t)) c->obs_times.push_back(t);
+    c->nobs = (int64_t)c->obs_times.size() * c->obs_per_time;
+    c->fft = (p.n >= 4) && ((p.n & (p.n - 1)) == 0) && p.n <= WC4D_FFT_MAX_N;
+    c->logn = 0;
+    while ((1 << c->logn) < p.n) ++c->logn;
+    c->nM = (p.model == WC4D_MODEL_DENSE) ? (p.M_shared ? 1 : p.N) : 0;
+    wc4d_status s = WC4D_OK;
+    if ((s = ensure(c, c->cosn, sizeof(double2) * p.n)) != WC4D_OK ||
+        (s = ensure(c, c->tw64, sizeof(double2) * (p.n / 2 + 1))) != WC4D_OK ||
+        (s = ensure(c, c->tw32, sizeof(float2) * (p.n / 2 + 1))) != WC4D_OK ||
+        (s = ensure(c, c->scal, sizeof(double) * 32)) != WC4D_OK ||
+        (s = ensure(c, c->counter, sizeof(int) * 16)) != WC4D_OK ||
+        (s = ensure_host(c, c->pinned, 4096)) != WC4D_OK) {
+        wc4d_destroy(c);
+        return s;
+    }
+    launch_twiddles(c->stream, p.n, P<double2>(c->cosn), P<double2>(c->tw64), P<float2>(c->tw32));
+    if ((s = check_launch(c, "twiddles")) != WC4D_OK || (s = sync(c, "create")) != WC4D_OK) {
+        wc4d_destroy(c);
+        return s;
+    }
+    *out = c;
+    return WC4D_OK;
+}
+
+extern "C" void wc4d_destroy(wc4d_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->M64, &c->MT64, &c->M32, &c->MT32, &c->traj64, &c->stage64, &c->stage32, &c->spec64[0], &c->spec64[1],
+                      &c->spec32[0], &c->spec32[1], &c->row64[0], &c->row64[1], &c->row32[0], &c->row32[1],
+                      &c->tw64, &c->tw32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
+                      &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
+                      &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32};
+    for (DevBuf *b : bufs) free_buf(*b);
+    for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
+    if (c->pinned.p) cudaFreeHost(c->pinned.p);
+    delete c;
+}
+
+extern "C" const char *wc4d_last_error(const wc4d_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" wc4d_status wc4d_set_stream(wc4d_ctx *c, void *stream)
+{
+    if (!c) return WC4D_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return WC4D_OK;
+}
+
+extern "C" int64_t wc4d_nobs(const wc4d_ctx *c) { return c ? c->nobs : -1; }
+
+extern "C" int64_t wc4d_hvp_count(wc4d_ctx *c, int32_t reset)
+{
+    if (!c) return -1;
+    int64_t v = c->hvp_count;
+    if (reset) c->hvp_count = 0;
+    return v;
+}
+
+// ============================================================================
+// set-up
+// ============================================================================
+static wc4d_status alloc_M(wc4d_ctx *c)
+{
+    size_t bytes = sizeof(double) * (size_t)c->nM * c->prob.n * c->prob.n;
+    WC4D_TRY(ensure(c, c->M64, bytes));
+    WC4D_TRY(ensure(c, c->MT64, bytes));
+    return WC4D_OK;
+}
+
+// replicate block 0 of M64 / MT64 into every subwindow block
+static wc4d_status replicate_M(wc4d_ctx *c)
+{
+    size_t nn = (size_t)c->prob.n * c->prob.n;
+    for (int t = 1; t < c->nM; ++t) {
+        WC4D_CUDA(c, cudaMemcpyAsync(P<double>(c->M64) + t * nn, P<double>(c->M64), nn * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        WC4D_CUDA(c, cudaMemcpyAsync(P<double>(c->MT64) + t * nn, P<double>(c->MT64), nn * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_set_propagator(wc4d_ctx *c, int32_t t, const double *M)
+{
+    if (!c || !M) return WC4D_EINVAL;
+    if (c->prob.model != WC4D_MODEL_DENSE) return set_err(c, WC4D_EINVAL, "set_propagator: model is not dense");
+    if (t < -1 || t >= c->nM) return set_err(c, WC4D_EINVAL, "set_propagator: t=%d out of range", t);
+    WC4D_TRY(alloc_M(c));
+    const int n = c->prob.n;
+    size_t nn = (size_t)n * n;
+    int tt = (t < 0) ? 0 : t;
+    WC4D_CUDA(c, cudaMemcpyAsync(P<double>(c->M64) + tt * nn, M, nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    launch_transpose_f64(c->stream, n, P<double>(c->M64) + tt * nn, P<double>(c->MT64) + tt * nn);
+    WC4D_TRY(check_launch(c, "transpose"));
+    if (t < 0) WC4D_TRY(replicate_M(c));
+    if (t < 0 || c->nM == 1) c->have_M = true;
+    else c->have_M = true;  // caller is responsible for setting every subwindow
+    c->have_M32 = false;
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_build_advdiff_propagator(wc4d_ctx *c, double kappa, double vel, double dt, int32_t steps)
+{
+    if (!c || steps < 1 || !(dt > 0.0)) return WC4D_EINVAL;
+    if (c->prob.model != WC4D_MODEL_DENSE) return set_err(c, WC4D_EINVAL, "build_advdiff: model is not dense");
+    WC4D_TRY(alloc_M(c));
+    const int n = c->prob.n;
+    WC4D_TRY(ensure(c, c->small0, sizeof(double2) * n));
+    WC4D_TRY(ensure(c, c->small1, sizeof(double) * n));
+    launch_advdiff_column(c->stream, n, kappa, vel, dt, steps, P<double2>(c->cosn), P<double2>(c->small0),
+                          P<double>(c->small1));
+    launch_expand_circulant(c->stream, n, P<double>(c->small1), P<double>(c->M64), P<double>(c->MT64));
+    WC4D_TRY(check_launch(c, "build_advdiff"));
+    WC4D_TRY(replicate_M(c));
+    c->have_M = true;
+    c->have_M32 = false;
+    return sync(c, "build_advdiff");
+}
+
+static wc4d_status ensure_M32(wc4d_ctx *c)
+{
+    if (c->have_M32) return WC4D_OK;
+    size_t cnt = (size_t)c->nM * c->prob.n * c->prob.n;
+    WC4D_TRY(ensure(c, c->M32, cnt * sizeof(float)));
+    WC4D_TRY(ensure(c, c->MT32, cnt * sizeof(float)));
+    launch_convert_f64_f32(c->stream, (int64_t)cnt, P<double>(c->M64), P<float>(c->M32));
+    launch_convert_f64_f32(c->stream, (int64_t)cnt, P<double>(c->MT64), P<float>(c->MT32));
+    WC4D_TRY(check_launch(c, "convert M"));
+    c->have_M32 = true;
+    return WC4D_OK;
+}
+
+static wc4d_status cov_from_row(wc4d_ctx *c, int block, const double *row_dev)
+{
+    const int n = c->prob.n;
+    WC4D_TRY(ensure(c, c->small2, sizeof(double) * n));
+    if (c->fft) {
+        WC4D_TRY(ensure(c, c->spec64[block], sizeof(double) * n));
+        WC4D_TRY(ensure(c, c->spec32[block], sizeof(float) * n));
+    } else {
+        WC4D_TRY(ensure(c, c->row64[block], sizeof(double) * n));
+        WC4D_TRY(ensure(c, c->row32[block], sizeof(float) * n));
+    }
+    launch_cov_sqrt(c->stream, n, c->logn, c->fft, row_dev, P<double2>(c->cosn), P<double>(c->small2),
+                    P<double>(c->spec64[block]), P<float>(c->spec32[block]), P<double>(c->row64[block]),
+                    P<float>(c->row32[block]));
+    WC4D_TRY(check_launch(c, "cov_sqrt"));
+    c->have_cov[block] = true;
+    return sync(c, "cov_sqrt");
+}
+
+extern "C" wc4d_status wc4d_set_covariance(wc4d_ctx *c, int32_t block, int32_t corr, double variance, double L)
+{
+    if (!c || block < 0 || block > 1 || corr < 0 || corr > 2 || !(variance >= 0.0)) return WC4D_EINVAL;
+    if (corr != WC4D_CORR_DIAG && !(L > 0.0)) return WC4D_EINVAL;
+    WC4D_TRY(ensure(c, c->small3, sizeof(double) * c->prob.n));
+    launch_corr_row(c->stream, c->prob.n, corr, L, variance, P<double>(c->small3));
+    WC4D_TRY(check_launch(c, "corr_row"));
+    return cov_from_row(c, block, P<double>(c->small3));
+}
+
+extern "C" wc4d_status wc4d_set_covariance_row(wc4d_ctx *c, int32_t block, const double *row_host)
+{
+    if (!c || block < 0 || block > 1 || !row_host) return WC4D_EINVAL;
+    WC4D_TRY(ensure(c, c->small3, sizeof(double) * c->prob.n));
+    WC4D_CUDA(c, cudaMemcpyAsync(c->small3.p, row_host, sizeof(double) * c->prob.n, cudaMemcpyHostToDevice,
+                                 c->stream));
+    return cov_from_row(c, block, P<double>(c->small3));
+}
+
+static wc4d_status require_operator(wc4d_ctx *c)
+{
+    if (!c->have_cov[0] || !c->have_cov[1]) return set_err(c, WC4D_ESTATE, "covariances B and Q are not set");
+    if (c->prob.model == WC4D_MODEL_DENSE && !c->have_M) return set_err(c, WC4D_ESTATE, "propagator not set");
+    if (c->prob.model == WC4D_MODEL_L96 && !c->have_traj)
+        return set_err(c, WC4D_ESTATE, "Lorenz-96 trajectory not set (call wc4d_set_background_obs)");
+    return WC4D_OK;
+}
+
+// ============================================================================
+// The Hessian product Y = A X (eq. 10)
+// ============================================================================
+template <typename T> struct Ops;
+template <> struct Ops<double> {
+    static const double *M(wc4d_ctx *c, int t) { return P<double>(c->M64) + mblk(c, t); }
+    static const double *MT(wc4d_ctx *c, int t) { return P<double>(c->MT64) + mblk(c, t); }
+    static const double *spec(wc4d_ctx *c, int b) { return P<double>(c->spec64[b]); }
+    static const double *row(wc4d_ctx *c, int b) { return P<double>(c->row64[b]); }
+    static const void *tw(wc4d_ctx *c) { return c->tw64.p; }
+    static const double *stages(wc4d_ctx *c) { return P<double>(c->stage64); }
+    static DevBuf &work(wc4d_ctx *c) { return c->work64; }
+};
+template <> struct Ops<float> {
+    static const float *M(wc4d_ctx *c, int t) { return P<float>(c->M32) + mblk(c, t); }
+    static const float *MT(wc4d_ctx *c, int t) { return P<float>(c->MT32) + mblk(c, t); }
+    static const float *spec(wc4d_ctx *c, int b) { return P<float>(c->spec32[b]); }
+    static const float *row(wc4d_ctx *c, int b) { return P<float>(c->row32[b]); }
+    static const void *tw(wc4d_ctx *c) { return c->tw32.p; }
+    static const float *stages(wc4d_ctx *c) { return P<float>(c->stage32); }
+    static DevBuf &work(wc4d_ctx *c) { return c->work32; }
+};
+
+// Dense-model sweeps on tensor cores (tc_gemm.cu); returns false when the
+// shape is not supported so the SIMT path is taken.
+bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld);
+bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld);
+
+template <typename T>
+static wc4d_status apply_circ(wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy, const T *addX,
+                              int64_t ld_add)
+{
+    launch_circulant<T>(c->stream, c, K, X, ldx, Y, ldy, addX, ld_add, c->fft, Ops<T>::spec(c, 0),
+                        Ops<T>::spec(c, 1), Ops<T>::row(c, 0), Ops<T>::row(c, 1), Ops<T>::tw(c));
+    return check_launch(c, "circulant");
+}
+
+// W (nA x K, ld) <- L^{-1} W in place: W_{t+1} += M_t W_t.
+template <typename T>
+static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allow_tc)
+{
+    const int n = c->prob.n, N = c->prob.N;
+    if (c->prob.model == WC4D_MODEL_L96) {
+        launch_l96_tlm_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld);
+        return check_launch(c, "l96 tlm sweep");
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (allow_tc && tc_sweep_forward(c, K, (float *)W, ld)) return check_launch(c, "tc forward sweep");
+    }
+    Epi e{0, 1.0, 1.0, 0.0, 1};
+    for (int t = 0; t < N; ++t)
+        launch_sweep_gemm<T>(c->stream, n, K, Ops<T>::M(c, t), W + (int64_t)t * n, ld, W + (int64_t)(t + 1) * n, ld,
+                             e);
+    return check_launch(c, "forward sweep");
+}
+
+// W <- L^{-T} H^T R^{-1} H W in place: W_N = obs_N(W_N); W_t = obs_t(W_t) + M_t^T W_{t+1}.
+template <typename T>
+static wc4d_status adjoint_obs_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allow_tc)
+{
+    const int n = c->prob.n, N = c->prob.N;
+    if (c->prob.model == WC4D_MODEL_L96) {
+        launch_l96_adj_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld, 1,
+                                1.0 / c->prob.sigma_o2, c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride);
+        return check_launch(c, "l96 adjoint sweep");
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (allow_tc && tc_sweep_adjoint(c, K, (float *)W, ld)) return check_launch(c, "tc adjoint sweep");
+    }
+    launch_obs_block<T>(c->stream, n, K, W + (int64_t)N * n, ld, obs_scale(c, N), c->prob.obs_stride);
+    for (int t = N - 1; t >= 0; --t) {
+        Epi e{1, 1.0, 0.0, obs_scale(c, t), c->prob.obs_stride};
+        launch_sweep_gemm<T>(c->stream, n, K, Ops<T>::MT(c, t), W + (int64_t)(t + 1) * n, ld, W + (int64_t)t * n, ld,
+                             e);
+    }
+    return check_launch(c, "adjoint sweep");
+}
+
+template <typename T>
+static wc4d_status hvp_impl(wc4d_ctx *c, const T *X, T *Y, int K, int64_t ld, bool allow_tc = true)
+{
+    const int64_t nA = c->nA;
+    DevBuf &wb = Ops<T>::work(c);
+    WC4D_TRY(ensure(c, wb, sizeof(T) * (size_t)nA * K));
+    T *W = P<T>(wb);
+    WC4D_TRY(apply_circ<T>(c, K, X, ld, W, nA, nullptr, 0));            // W = D^{1/2} X
+    WC4D_TRY(forward_sweep<T>(c, K, W, nA, allow_tc));                  // W = L^{-1} W
+    WC4D_TRY(adjoint_obs_sweep<T>(c, K, W, nA, allow_tc));              // W = L^{-T} H^T R^{-1} H W
+    WC4D_TRY(apply_circ<T>(c, K, W, nA, Y, ld, X, ld));                 // Y = X + D^{1/2} W
+    c->hvp_count++;
+    return WC4D_OK;
+}
+
+static wc4d_status prep_precision(wc4d_ctx *c, int precision)
+{
+    if (precision == WC4D_MIXED && c->prob.model == WC4D_MODEL_DENSE) WC4D_TRY(ensure_M32(c));
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_hvp(wc4d_ctx *c, const void *X, void *Y, int32_t K, int64_t ld, int32_t precision)
+{
+    if (!c || !X || !Y || K < 1 || ld < c->nA) return WC4D_EINVAL;
+    if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
+    WC4D_TRY(require_operator(c));
+    WC4D_TRY(prep_precision(c, precision));
+    if (precision == WC4D_FP64) return hvp_impl<double>(c, (const double *)X, (double *)Y, K, ld);
+    return hvp_impl<float>(c, (const float *)X, (float *)Y, K, ld);
+}
+
+template <typename T>
+static wc4d_status plain_adjoint_sweep(wc4d_ctx *c, int K, T *W, int64_t ld)
+{
+    const int n = c->prob.n, N = c->prob.N;
+    if (c->prob.model == WC4D_MODEL_L96) {
+        launch_l96_adj_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld, 0, 0.0, 1,
+                                0, 1);
+        return check_launch(c, "l96 adjoint sweep");
+    }
+    Epi e{0, 1.0, 1.0, 0.0, 1};
+    for (int t = N - 1; t >= 0; --t)
+        launch_sweep_gemm<T>(c->stream, n, K, Ops<T>::MT(c, t), W + (int64_t)(t + 1) * n, ld, W + (int64_t)t * n, ld,
+                             e);
+    return check_launch(c, "adjoint sweep");
+}
+
+extern "C" wc4d_status wc4d_apply_dsqrt(wc4d_ctx *c, const void *X, void *Y, int32_t K, int64_t ld, int32_t precision)
+{
+    if (!c || !X || !Y || K < 1 || ld < c->nA) return WC4D_EINVAL;
+    if (!c->have_cov[0] || !c->have_cov[1]) return set_err(c, WC4D_ESTATE, "covariances are not set");
+    if (precision == WC4D_FP64) return apply_circ<double>(c, K, (const double *)X, ld, (double *)Y, ld, nullptr, 0);
+    if (precision == WC4D_MIXED) return apply_circ<float>(c, K, (const float *)X, ld, (float *)Y, ld, nullptr, 0);
+    return WC4D_EINVAL;
+}
+
+extern "C" wc4d_status wc4d_apply_linv(wc4d_ctx *c, void *W, int32_t K, int64_t ld, int32_t precision)
+{
+    if (!c || !W || K < 1 || ld < c->nA) return WC4D_EINVAL;
+    WC4D_TRY(require_operator(c));
+    WC4D_TRY(prep_precision(c, precision));
+    if (precision == WC4D_FP64) return forward_sweep<double>(c, K, (double *)W, ld, false);
+    if (precision == WC4D_MIXED) return forward_sweep<float>(c, K, (float *)W, ld, true);
+    return WC4D_EINVAL;
+}
+
+extern "C" wc4d_status wc4d_apply_linvT(wc4d_ctx *c, void *W, int32_t K, int64_t ld, int32_t precision)
+{
+    if (!c || !W || K < 1 || ld < c->nA) return WC4D_EINVAL;
+    WC4D_TRY(require_operator(c));
+    WC4D_TRY(prep_precision(c, precision));
+    if (precision == WC4D_FP64) return plain_adjoint_sweep<double>(c, K, (double *)W, ld);
+    if (precision == WC4D_MIXED) return plain_adjoint_sweep<float>(c, K, (float *)W, ld);
+    return WC4D_EINVAL;
+}
+
+extern "C" wc4d_status wc4d_get_propagator(wc4d_ctx *c, int32_t t, double *M)
+{
+    if (!c || !M) return WC4D_EINVAL;
+    if (c->prob.model != WC4D_MODEL_DENSE || !c->have_M) return set_err(c, WC4D_ESTATE, "no dense propagator");
+    if (t < 0 || t >= c->prob.N) return WC4D_EINVAL;
+    size_t nn = (size_t)c->prob.n * c->prob.n;
+    WC4D_CUDA(c, cudaMemcpyAsync(M, P<double>(c->M64) + mblk(c, t), nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    return sync(c, "get_propagator");
+}
+
+// ============================================================================
+// Outer-loop quantities: innovations and right-hand side
+// ============================================================================
+extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, const double *y, const double *Dm12b)
+{
+    if (!c || !xb || !y) return WC4D_EINVAL;
+    const int n = c->prob.n, N = c->prob.N;
+    const int64_t nA = c->nA;
+    if (!c->have_cov[0] || !c->have_cov[1]) return set_err(c, WC4D_ESTATE, "covariances are not set");
+    WC4D_TRY(ensure(c, c->blkA, sizeof(double) * nA));
+    WC4D_TRY(ensure(c, c->blkB, sizeof(double) * nA));
+    WC4D_TRY(ensure(c, c->d, sizeof(double) * std::max<int64_t>(c->nobs, 1)));
+    WC4D_TRY(ensure(c, c->rhs, sizeof(double) * nA));
+    WC4D_TRY(ensure(c, c->small2, sizeof(double) * std::max<int64_t>(c->nobs, 1)));
+    double *xs = P<double>(c->blkA);
+    if (c->prob.model == WC4D_MODEL_L96) {
+        const int64_t nsteps = (int64_t)N * c->prob.steps;
+        WC4D_TRY(ensure(c, c->traj64, sizeof(double) * (size_t)(nsteps + 1) * n));
+        WC4D_TRY(ensure(c, c->stage64, sizeof(double) * (size_t)4 * nsteps * n));
+        WC4D_TRY(ensure(c, c->stage32, sizeof(float) * (size_t)4 * nsteps * n));
+        WC4D_CUDA(c, cudaMemcpyAsync(c->traj64.p, xb, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        launch_l96_run(c->stream, n, (int)nsteps, c->prob.F, c->prob.dt, P<double>(c->traj64), P<double>(c->stage64));
+        launch_convert_f64_f32(c->stream, 4 * nsteps * n, P<double>(c->stage64), P<float>(c->stage32));
+        WC4D_TRY(check_launch(c, "l96 run"));
+        for (int t = 0; t <= N; ++t)
+            WC4D_CUDA(c, cudaMemcpyAsync(xs + (int64_t)t * n, P<double>(c->traj64) + (int64_t)t * c->prob.steps * n,
+                                         sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        c->have_traj = true;
+    } else {
+        if (!c->have_M) return set_err(c, WC4D_ESTATE, "propagator not set");
+        WC4D_CUDA(c, cudaMemsetAsync(xs, 0, sizeof(double) * nA, c->stream));
+        WC4D_CUDA(c, cudaMemcpyAsync(xs, xb, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        WC4D_TRY(forward_sweep<double>(c, 1, xs, nA, false));   // x_{t+1} = M_t x_t
+    }
+    // innovations
+    double *dy = P<double>(c->small2);
+    if (c->nobs > 0) {
+        WC4D_CUDA(c, cudaMemcpyAsync(dy, y, sizeof(double) * c->nobs, cudaMemcpyHostToDevice, c->stream));
+        k_innovation<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
+                                                                     c->prob.obs_tstride, c->prob.obs_stride, n, dy,
+                                                                     xs, P<double>(c->d));
+    }
+    // rhs = D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b)
+    double *v = P<double>(c->blkB);
+    WC4D_CUDA(c, cudaMemsetAsync(v, 0, sizeof(double) * nA, c->stream));
+    if (c->nobs > 0)
+        k_scatter_obs<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
+                                                                      c->prob.obs_tstride, c->prob.obs_stride, n,
+                                                                      P<double>(c->d), 1.0 / c->prob.sigma_o2, v);
+    WC4D_TRY(check_launch(c, "innovation"));
+    WC4D_TRY(plain_adjoint_sweep<double>(c, 1, v, nA));    // S = L^{-T} H^T R^{-1} d
+    double *addb = nullptr;
+    if (Dm12b) {
+        WC4D_TRY(ensure(c, c->Dm12b, sizeof(double) * nA));
+        WC4D_CUDA(c, cudaMemcpyAsync(c->Dm12b.p, Dm12b, sizeof(double) * nA, cudaMemcpyHostToDevice, c->stream));
+        addb = P<double>(c->Dm12b);
+    }
+    WC4D_TRY(apply_circ<double>(c, 1, v, nA, P<double>(c->rhs), nA, addb, nA));
+    c->have_rhs = true;
+    return sync(c, "set_background_obs");
+}
+
+extern "C" wc4d_status wc4d_get_rhs(wc4d_ctx *c, double *rhs)
+{
+    if (!c || !rhs) return WC4D_EINVAL;
+    if (!c->have_rhs) return set_err(c, WC4D_ESTATE, "rhs not set");
+    WC4D_CUDA(c, cudaMemcpyAsync(rhs, c->rhs.p, sizeof(double) * c->nA, cudaMemcpyDeviceToDevice, c->stream));
+    return sync(c, "get_rhs");
+}
+
+extern "C" wc4d_status wc4d_gaussian(wc4d_ctx *c, uint64_t seed, int64_t rows, int32_t cols, int64_t ld, double *G)
+{
+    if (!c || !G || rows < 1 || cols < 1 || ld < rows) return WC4D_EINVAL;
+    launch_gaussian(c->stream, seed, rows, cols, ld, G);
+    return check_launch(c, "gaussian");
+}
+
+// ============================================================================
+// CholeskyQR2 and the small symmetric eigenproblem
+// ============================================================================
+// Y (rows x m, ld) <- Y R^{-1} with Y = Z R; Rout (m x m, device FP64) = R.
+template <typename T>
+static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t ld, T *tmp, double *R)
+{
+    const size_t mm = (size_t)m * m;
+    WC4D_TRY(ensure(c, c->small0, sizeof(double) * mm));
+    WC4D_TRY(ensure(c, c->small1, sizeof(double) * mm));
+    const int tiles = ceil_div(m, 32) * ceil_div(m, 32);
+    size_t part_need = sizeof(double) * mm * (size_t)std::max<int64_t>(1, (2 * c->num_sms + tiles - 1) / tiles + 1);
+    WC4D_TRY(ensure(c, c->part, part_need));
+    int S = 0;
+    double *G = P<double>(c->small0);
+    launch_atb<T>(c->stream, c->num_sms, rows, m, m, Y, ld, Y, ld, P<double>(c->part), &S, G);   // G = Y^T Y
+    launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));                                // G = R^T R
+    double *Rinv = P<double>(c->small1);
+    launch_trinv_upper(c->stream, m, R, Rinv);
+    WC4D_TRY(check_launch(c, "cholqr"));
+    int info = 0;
+    WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "cholqr info"));
+    if (info != 0) return set_err(c, WC4D_ENOTSPD, "CholeskyQR: Gram matrix not positive definite at pivot %d", info);
+    Epi e{0, 1.0, 0.0, 0.0, 1};
+    if constexpr (sizeof(T) == 8) {
+        launch_gemm<double>(c->stream, (int)rows, m, m, Y, 1, ld, Rinv, m, tmp, rows, e);
+    } else {
+        float *Rinv32 = reinterpret_cast<float *>(G);   // G is no longer needed
+        launch_convert_f64_f32(c->stream, (int64_t)mm, Rinv, Rinv32);
+        launch_gemm<float>(c->stream, (int)rows, m, m, Y, 1, ld, Rinv32, m, tmp, rows, e);
+    }
+    WC4D_TRY(check_launch(c, "cholqr gemm"));
+    for (int j = 0; j < m; ++j)
+        WC4D_CUDA(c, cudaMemcpyAsync(Y + (int64_t)j * ld, tmp + (int64_t)j * rows, sizeof(T) * rows,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+    return WC4D_OK;
+}
+
+// CholeskyQR2: Y = Z R with orthonormal Z (in place), R = R2 R1 (device, m x m).
+template <typename T>
+static wc4d_status cholqr2(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t ld, T *tmp, double *R)
+{
+    const size_t mm = (size_t)m * m;
+    WC4D_TRY(ensure(c, c->small2, sizeof(double) * mm * 2));
+    double *R1 = P<double>(c->small2), *R2 = R1 + mm;
+    WC4D_TRY(cholqr_pass<T>(c, Y, rows, m, ld, tmp, R1));
+    WC4D_TRY(cholqr_pass<T>(c, Y, rows, m, ld, tmp, R2));
+    if (R) {
+        Epi e{0, 1.0, 0.0, 0.0, 1};
+        launch_gemm<double>(c->stream, m, m, m, R2, 1, m, R1, m, R, m, e);   // R = R2 R1
+        WC4D_TRY(check_launch(c, "R2R1"));
+    }
+    return WC4D_OK;
+}
+
+// One-sided Jacobi on X0 (m x m, device): X0 V = U Sigma.  w (device, 2m
+// doubles) receives Sigma decreasing in w[0..m); Vout (m x m) the matching V.
+static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, double *Vout)
+{
+    const int mp = m + (m & 1);
+    size_t mpmp = (size_t)mp * mp;
+    DevBuf &xb = c->small3;
+    WC4D_TRY(ensure(c, xb, sizeof(double) * mpmp * 2));
+    double *X = P<double>(xb), *V = X + mpmp;
+    launch_jacobi_init(c->stream, m, mp, X0, X, V);
+    WC4D_TRY(check_launch(c, "jacobi init"));
+    if (mp >= 2) {
+        const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
+        int *rot = P<int>(c->counter) + 1;
+        int *hrot = P<int>(c->pinned);
+        bool conv = false;
+        for (int sweep = 0; sweep < 60; ++sweep) {
+            WC4D_CUDA(c, cudaMemsetAsync(rot, 0, sizeof(int), c->stream));
+            for (int r = 0; r < mp - 1; ++r) launch_jacobi_round(c->stream, mp, X, V, r, tol, rot);
+            WC4D_TRY(check_launch(c, "jacobi round"));
+            WC4D_CUDA(c, cudaMemcpyAsync(hrot, rot, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            WC4D_TRY(sync(c, "jacobi sweep"));
+            if (*hrot == 0) { conv = true; break; }
+        }
+        if (!conv) return set_err(c, WC4D_ETIMEOUT, "one-sided Jacobi did not converge in 60 sweeps");
+    }
+    launch_jacobi_finish(c->stream, m, mp, X, V, w, Vout);
+    return check_launch(c, "jacobi finish");
+}
+
+extern "C" wc4d_status wc4d_orthonormalize(wc4d_ctx *c, double *Y, int64_t rows, int32_t m, int64_t ld, double *R_host)
+{
+    if (!c || !Y || rows < m || m < 1 || ld < rows) return WC4D_EINVAL;
+    WC4D_TRY(ensure(c, c->blkD, sizeof(double) * (size_t)rows * m));
+    WC4D_TRY(ensure(c, c->small1, sizeof(double) * (size_t)m * m));
+    DevBuf Rb;
+    double *R = nullptr;
+    if (R_host) {
+        WC4D_TRY(ensure(c, Rb, sizeof(double) * (size_t)m * m));
+        R = P<double>(Rb);
+    }
+    wc4d_status s = cholqr2<double>(c, Y, rows, m, ld, P<double>(c->blkD), R);
+    if (s == WC4D_OK && R_host) {
+        cudaMemcpyAsync(R_host, R, sizeof(double) * (size_t)m * m, cudaMemcpyDeviceToHost, c->stream);
+        s = sync(c, "orthonormalize");
+    }
+    free_buf(Rb);
+    return s;
+}
+
+extern "C" wc4d_status wc4d_symeig(wc4d_ctx *c, int32_t m, const double *S, double *w_host, double *V)
+{
+    if (!c || !S || !w_host || !V || m < 1) return WC4D_EINVAL;
+    DevBuf wb;
+    WC4D_TRY(ensure(c, wb, sizeof(double) * 2 * m));
+    wc4d_status s = jacobi_svd(c, m, S, P<double>(wb), V);
+    if (s == WC4D_OK) {
+        cudaMemcpyAsync(w_host, wb.p, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream);
+        s = sync(c, "symeig");
+    }
+    free_buf(wb);
+    return s;
+}
+
+// ============================================================================
+// Randomised eigensolvers (Section 4)
+// ============================================================================
+template <typename T>
+static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uint64_t seed, const double *Gdev)
+{
+    const int m = k + l;
+    const int64_t nA = c->nA;
+    const size_t blk = sizeof(T) * (size_t)nA * m;
+    WC4D_TRY(ensure(c, c->blkA, blk));
+    WC4D_TRY(ensure(c, c->blkB, blk));
+    WC4D_TRY(ensure(c, c->blkC, blk));
+    WC4D_TRY(ensure(c, c->blkD, std::max(blk, sizeof(double) * (size_t)nA * m)));
+    WC4D_TRY(ensure(c, c->theta64, sizeof(double) * 2 * m));
+    const size_t mm = (size_t)m * m;
+    DevBuf kb, wb, Rb;
+    WC4D_TRY(ensure(c, kb, sizeof(double) * mm * 2));
+    WC4D_TRY(ensure(c, wb, sizeof(double) * 2 * m));
+    WC4D_TRY(ensure(c, Rb, sizeof(double) * mm));
+    double *Kmat = P<double>(kb), *Wv = Kmat + mm, *w = P<double>(wb), *R = P<double>(Rb);
+    T *A_ = P<T>(c->blkA), *B_ = P<T>(c->blkB), *C_ = P<T>(c->blkC), *D_ = P<T>(c->blkD);
+    wc4d_status st = WC4D_OK;
+    auto fail = [&](wc4d_status s) { free_buf(kb); free_buf(wb); free_buf(Rb); return s; };
+
+    // step 1: Gaussian probes G (FP64), cast to the working precision
+    double *G64 = P<double>(c->blkD);
+    if (Gdev) WC4D_CUDA(c, cudaMemcpyAsync(G64, Gdev, sizeof(double) * nA * m, cudaMemcpyDeviceToDevice, c->stream));
+    else launch_gaussian(c->stream, seed, nA, m, nA, G64);
+    if constexpr (sizeof(T) == 8) {
+        WC4D_CUDA(c, cudaMemcpyAsync(A_, G64, blk, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        launch_convert_f64_f32(c->stream, nA * m, G64, (float *)A_);
+    }
+    if ((st = check_launch(c, "probes")) != WC4D_OK) return fail(st);
+
+    // U (nA x k) in the working precision, theta in c->theta64
+    T *U = nullptr;
+    if (method == WC4D_REVD || method == WC4D_NYSTROM) {
+        // Y = A G; Z = orth(Y)  (+ q power iterations for REVD)
+        if ((st = hvp_impl<T>(c, A_, B_, m, nA)) != WC4D_OK) return fail(st);
+        if ((st = cholqr2<T>(c, B_, nA, m, nA, D_, nullptr)) != WC4D_OK) return fail(st);
+        T *Z = B_, *Y = A_;
+        if (method == WC4D_REVD)
+            for (int it = 0; it < q; ++it) {
+                if ((st = hvp_impl<T>(c, Z, Y, m, nA)) != WC4D_OK) return fail(st);
+                if ((st = cholqr2<T>(c, Y, nA, m, nA, D_, nullptr)) != WC4D_OK) return fail(st);
+                std::swap(Z, Y);
+            }
+        // E = A Z
+        T *E = Y;
+        if ((st = hvp_impl<T>(c, Z, E, m, nA)) != WC4D_OK) return fail(st);
+        const int tiles = ceil_div(m, 32) * ceil_div(m, 32);
+        if ((st = ensure(c, c->part, sizeof(double) * mm * ((2 * c->num_sms + tiles - 1) / tiles + 1))) != WC4D_OK)
+            return fail(st);
+        int S = 0;
+        launch_atb<T>(c->stream, c->num_sms, nA, m, m, Z, nA, E, nA, P<double>(c->part), &S, Kmat);  // Z^T A Z
+        launch_symmetrize(c->stream, m, Kmat);
+        if ((st = check_launch(c, "ZtAZ")) != WC4D_OK) return fail(st);
+        if (method == WC4D_REVD) {
+            // EVD of K_1 (Alg. 3 step 5); U = Z W[:, :k]
+            if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);
+            U = C_;
+            Epi e{0, 1.0, 0.0, 0.0, 1};
+            if constexpr (sizeof(T) == 8) {
+                launch_gemm<double>(c->stream, (int)nA, k, m, Z, 1, nA, Wv, m, U, nA, e);
+            } else {
+                float *W32 = reinterpret_cast<float *>(Kmat);
+                launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, W32);
+                launch_gemm<float>(c->stream, (int)nA, k, m, Z, 1, nA, W32, m, U, nA, e);
+            }
+            WC4D_CUDA(c, cudaMemcpyAsync(P<double>(c->theta64), w, sizeof(double) * k, cudaMemcpyDeviceToDevice,
+                                         c->stream));
+        } else {
+            // Nystrom (Alg. 4): E2 = C^T C; F = E1 C^{-1}; F = U Sigma V^T
+            double *Cc = R;
+            launch_chol_upper(c->stream, m, Kmat, Cc, P<int>(c->counter));
+            int info = 0;
+            WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            if ((st = sync(c, "nystrom chol")) != WC4D_OK) return fail(st);
+            if (info) return fail(set_err(c, WC4D_ENOTSPD, "Nystrom: Z^T A Z not positive definite (pivot %d)", info));
+            launch_trinv_upper(c->stream, m, Cc, Wv);              // Wv = C^{-1}
+            T *F = C_;
+            Epi e{0, 1.0, 0.0, 0.0, 1};
+            if constexpr (sizeof(T) == 8) {
+                launch_gemm<double>(c->stream, (int)nA, m, m, E, 1, nA, Wv, m, F, nA, e);
+            } else {
+                float *Ci32 = reinterpret_cast<float *>(Kmat);
+                launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, Ci32);
+                launch_gemm<float>(c->stream, (int)nA, m, m, E, 1, nA, Ci32, m, F, nA, e);
+            }
+            launch_atb<T>(c->stream, c->num_sms, nA, m, m, F, nA, F, nA, P<double>(c->part), &S, Kmat);  // F^T F
+            launch_symmetrize(c->stream, m, Kmat);
+            if ((st = check_launch(c, "nystrom F")) != WC4D_OK) return fail(st);
+            if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);   // F^T F = V Sigma^2 V^T
+            // U = F V[:, :k] Sigma^{-1}
+            U = E;
+            if constexpr (sizeof(T) == 8) {
+                launch_gemm<double>(c->stream, (int)nA, k, m, F, 1, nA, Wv, m, U, nA, e);
+                launch_scale_cols(c->stream, nA, k, (double *)U, nA, w, 1);
+            } else {
+                float *V32 = reinterpret_cast<float *>(Kmat);
+                launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, V32);
+                launch_gemm<float>(c->stream, (int)nA, k, m, F, 1, nA, V32, m, U, nA, e);
+                // scale in FP64 via a temporary copy
+                double *U64t = reinterpret_cast<double *>(c->blkD.p);
+                launch_convert_f32_f64(c->stream, nA * k, (const float *)U, U64t);
+                launch_scale_cols(c->stream, nA, k, U64t, nA, w, 1);
+                launch_convert_f64_f32(c->stream, nA * k, U64t, (float *)U);
+            }
+            WC4D_CUDA(c, cudaMemcpyAsync(P<double>(c->theta64), w, sizeof(double) * k, cudaMemcpyDeviceToDevice,
+                                         c->stream));   // Theta = Sigma^2 (eigenvalues of F^T F)
+        }
+    } else {
+        // REVD_ritzit (Alg. 5): G_3 = orth(G); Y_3 = A G_3 = Z_3 R_3; K_3 = R_3 R_3^T
+        if ((st = cholqr2<T>(c, A_, nA, m, nA, D_, nullptr)) != WC4D_OK) return fail(st);
+        if ((st = hvp_impl<T>(c, A_, B_, m, nA)) != WC4D_OK) return fail(st);
+        if ((st = cholqr2<T>(c, B_, nA, m, nA, D_, R)) != WC4D_OK) return fail(st);
+        // left singular vectors of R_3 = eigenvectors of R_3 R_3^T: one-sided Jacobi on R_3^T
+        launch_rrt(c->stream, m, R, Kmat);
+        if ((st = check_launch(c, "R^T")) != WC4D_OK) return fail(st);
+        if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);   // singular values = Theta_3
+        U = C_;
+        Epi e{0, 1.0, 0.0, 0.0, 1};
+        if constexpr (sizeof(T) == 8) {
+            launch_gemm<double>(c->stream, (int)nA, k, m, B_, 1, nA, Wv, m, U, nA, e);
+        } else {
+            float *W32 = reinterpret_cast<float *>(Kmat);
+            launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, W32);
+            launch_gemm<float>(c->stream, (int)nA, k, m, B_, 1, nA, W32, m, U, nA, e);
+        }
+        WC4D_CUDA(c, cudaMemcpyAsync(P<double>(c->theta64), w, sizeof(double) * k, cudaMemcpyDeviceToDevice,
+                                     c->stream));
+    }
+    if ((st = check_launch(c, "ritz vectors")) != WC4D_OK) return fail(st);
+    // keep U in both precisions
+    WC4D_TRY(ensure(c, c->U64, sizeof(double) * (size_t)nA * k));
+    WC4D_TRY(ensure(c, c->U32, sizeof(float) * (size_t)nA * k));
+    if constexpr (sizeof(T) == 8) {
+        WC4D_CUDA(c, cudaMemcpyAsync(c->U64.p, U, sizeof(double) * nA * k, cudaMemcpyDeviceToDevice, c->stream));
+        launch_convert_f64_f32(c->stream, nA * k, (const double *)U, P<float>(c->U32));
+    } else {
+        WC4D_CUDA(c, cudaMemcpyAsync(c->U32.p, U, sizeof(float) * nA * k, cudaMemcpyDeviceToDevice, c->stream));
+        launch_convert_f32_f64(c->stream, nA * k, (const float *)U, P<double>(c->U64));
+    }
+    WC4D_TRY(ensure(c, c->c64, sizeof(double) * k));
+    launch_lmp_coeffs(c->stream, k, P<double>(c->theta64), P<double>(c->c64));
+    if ((st = check_launch(c, "lmp coeffs")) != WC4D_OK) return fail(st);
+    c->kU = k;
+    c->theta_host.assign(k, 0.0);
+    cudaMemcpyAsync(c->theta_host.data(), c->theta64.p, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream);
+    st = sync(c, "sketch");
+    free_buf(kb);
+    free_buf(wb);
+    free_buf(Rb);
+    return st;
+}
+
+extern "C" wc4d_status wc4d_sketch(wc4d_ctx *c, int32_t method, int32_t k, int32_t l, int32_t q, uint64_t seed,
+                                   const double *G, double *theta_host, int32_t precision)
+{
+    if (!c || k < 1 || l < 0 || q < 0 || method < 0 || method > 2) return WC4D_EINVAL;
+    if (k + l > 1024 || k + l > c->nA) return set_err(c, WC4D_EINVAL, "k + l = %d too large", k + l);
+    if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
+    WC4D_TRY(require_operator(c));
+    WC4D_TRY(prep_precision(c, precision));
+    wc4d_status s = (precision == WC4D_FP64) ? sketch_impl<double>(c, method, k, l, q, seed, G)
+                                             : sketch_impl<float>(c, method, k, l, q, seed, G);
+    if (s != WC4D_OK) return s;
+    if (theta_host) std::memcpy(theta_host, c->theta_host.data(), sizeof(double) * k);
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_get_ritz(wc4d_ctx *c, double *U, double *theta_host)
+{
+    if (!c) return WC4D_EINVAL;
+    if (c->kU == 0) return set_err(c, WC4D_ESTATE, "no Ritz pairs");
+    if (U) WC4D_CUDA(c, cudaMemcpyAsync(U, c->U64.p, sizeof(double) * c->nA * c->kU, cudaMemcpyDeviceToDevice,
+                                        c->stream));
+    if (theta_host) std::memcpy(theta_host, c->theta_host.data(), sizeof(double) * c->kU);
+    return sync(c, "get_ritz");
+}
+
+extern "C" wc4d_status wc4d_set_ritz(wc4d_ctx *c, int32_t k, const double *U, const double *theta_host)
+{
+    if (!c || k < 0 || (k > 0 && (!U || !theta_host))) return WC4D_EINVAL;
+    if (k == 0) { c->kU = 0; return WC4D_OK; }
+    const int64_t nA = c->nA;
+    WC4D_TRY(ensure(c, c->U64, sizeof(double) * (size_t)nA * k));
+    WC4D_TRY(ensure(c, c->U32, sizeof(float) * (size_t)nA * k));
+    WC4D_TRY(ensure(c, c->theta64, sizeof(double) * 2 * k));
+    WC4D_TRY(ensure(c, c->c64, sizeof(double) * k));
+    WC4D_CUDA(c, cudaMemcpyAsync(c->U64.p, U, sizeof(double) * nA * k, cudaMemcpyDeviceToDevice, c->stream));
+    launch_convert_f64_f32(c->stream, nA * k, P<double>(c->U64), P<float>(c->U32));
+    WC4D_CUDA(c, cudaMemcpyAsync(c->theta64.p, theta_host, sizeof(double) * k, cudaMemcpyHostToDevice, c->stream));
+    launch_lmp_coeffs(c->stream, k, P<double>(c->theta64), P<double>(c->c64));
+    WC4D_TRY(check_launch(c, "set_ritz"));
+    c->kU = k;
+    c->theta_host.assign(theta_host, theta_host + k);
+    return sync(c, "set_ritz");
+}
+
+// ============================================================================
+// Spectral LMP (eq. 16) and PCG (Alg. 1)
+// ============================================================================
+template <typename T> static T *Ubuf(wc4d_ctx *c);
+template <> double *Ubuf<double>(wc4d_ctx *c) { return P<double>(c->U64); }
+template <> float *Ubuf<float>(wc4d_ctx *c) { return P<float>(c->U32); }
+
+// y = C v (C^T = C for the closed form); skip: optional device flag
+template <typename T>
+static wc4d_status lmp_apply_impl(wc4d_ctx *c, const T *v, T *y, const int *skip)
+{
+    const int k = c->kU;
+    const int64_t nA = c->nA;
+    int splits = ceil_div(nA, 1024);
+    WC4D_TRY(ensure(c, c->part, sizeof(double) * (size_t)splits * k + 64));
+    launch_utv<T>(c->stream, c->num_sms, nA, k, Ubuf<T>(c), v, P<double>(c->part), &splits);
+    launch_lmp_combine<T>(c->stream, nA, k, Ubuf<T>(c), P<double>(c->part), splits, P<double>(c->c64), 1.0, v, y,
+                          nullptr, nullptr, skip);
+    return check_launch(c, "lmp apply");
+}
+
+extern "C" wc4d_status wc4d_lmp_apply(wc4d_ctx *c, const double *v, double *y, int32_t transpose)
+{
+    (void)transpose;   // C is symmetric in the closed form
+    if (!c || !v || !y) return WC4D_EINVAL;
+    if (c->kU == 0) {
+        WC4D_CUDA(c, cudaMemcpyAsync(y, v, sizeof(double) * c->nA, cudaMemcpyDeviceToDevice, c->stream));
+        return WC4D_OK;
+    }
+    return lmp_apply_impl<double>(c, v, y, nullptr);
+}
+
+struct PcgOut {
+    int iters = 0;
+    int breakdown = 0;
+    bool done = false;
+    double relres_rec = 0.0;
+};
+
+// CG on A x = b from x = 0 in precision T; b, x device vectors of the context.
+template <typename T>
+static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit, int force, bool use_lmp,
+                            double *qcf_dev, PcgOut &out)
+{
+    const int64_t nA = c->nA;
+    DevBuf *vb = (sizeof(T) == 8) ? c->pcg64 : c->pcg32;
+    for (int i = 1; i < 6; ++i) WC4D_TRY(ensure(c, vb[i], sizeof(T) * nA));
+    T *r = P<T>(vb[1]), *rh = P<T>(vb[2]), *p = P<T>(vb[3]), *q = P<T>(vb[4]), *t = P<T>(vb[5]);
+    const int grid = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA + 255) / 256));
+    WC4D_TRY(ensure(c, c->small1, sizeof(double) * 4 * 1024));
+    double *pa = P<double>(c->small1), *pb = pa + 1024, *pc = pb + 1024;
+    double *scal = P<double>(c->scal);
+    int *flags = P<int>(c->counter) + 4;
+    const bool lmp = use_lmp && c->kU > 0;
+
+    WC4D_CUDA(c, cudaMemsetAsync(x, 0, sizeof(T) * nA, c->stream));
+    launch_copy<T>(c->stream, nA, b, r);                                    // r_0 = b
+    if (lmp) WC4D_TRY(lmp_apply_impl<T>(c, r, rh, nullptr));                // rhat_0 = C^T r_0
+    else launch_copy<T>(c->stream, nA, r, rh);
+    if (lmp) WC4D_TRY(lmp_apply_impl<T>(c, rh, p, nullptr));                // p_0 = C rhat_0
+    else launch_copy<T>(c->stream, nA, rh, p);
+    launch_dot_partial<T>(c->stream, grid, nA, b, b, pa);
+    launch_dot_partial<T>(c->stream, grid, nA, rh, rh, pb);
+    launch_pcg_init(c->stream, grid, pa, pb, scal, flags);
+    WC4D_TRY(check_launch(c, "pcg init"));
+    int *hflags = P<int>(c->pinned);
+    const double tol_k = (force > 0) ? 0.0 : tol;
+    const int nit = (force > 0) ? force : maxit;
+    out = PcgOut();
+    for (int it = 0; it < nit; ++it) {
+        WC4D_TRY(hvp_impl<T>(c, p, q, 1, nA, false));                       // q = A p
+        launch_dot_partial<T>(c->stream, grid, nA, p, q, pa);
+        launch_pcg_alpha(c->stream, grid, pa, scal, flags);                 // alpha = rho / p^T A p
+        launch_pcg_xr<T>(c->stream, grid, nA, scal, x, r, p, q, pb);        // x += alpha p; r -= alpha q
+        const T *tq = q;
+        if (lmp) { WC4D_TRY(lmp_apply_impl<T>(c, q, t, flags)); tq = t; }   // C^T A p
+        launch_pcg_rh<T>(c->stream, grid, nA, scal, rh, tq, pc);            // rhat -= alpha C^T A p
+        launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
+        const T *tr = rh;
+        if (lmp) { WC4D_TRY(lmp_apply_impl<T>(c, rh, t, flags)); tr = t; }  // C rhat
+        launch_pcg_p<T>(c->stream, grid, nA, scal, p, tr);                  // p = C rhat + beta p
+        WC4D_TRY(check_launch(c, "pcg iteration"));
+        WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+        WC4D_TRY(sync(c, "pcg iteration"));
+        if (hflags[0]) break;
+    }
+    double hs[8];
+    WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "pcg end"));
+    out.done = hflags[0] != 0;
+    out.breakdown = hflags[1];
+    out.iters = hflags[2];
+    out.relres_rec = hs[4];
+    return WC4D_OK;
+}
+
+// FP64 true relative residual |rhs - A x| / |rhs|; r64 receives rhs - A x.
+static wc4d_status true_residual(wc4d_ctx *c, const double *x, double *r64, double *rel, double *bnorm_out)
+{
+    const int64_t nA = c->nA;
+    WC4D_TRY(ensure(c, c->pcg64[6], sizeof(double) * nA));
+    double *Ax = P<double>(c->pcg64[6]);
+    WC4D_TRY(hvp_impl<double>(c, x, Ax, 1, nA, false));
+    launch_sub_f64(c->stream, nA, P<double>(c->rhs), Ax, r64);
+    const int grid = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA + 255) / 256));
+    WC4D_TRY(ensure(c, c->small0, sizeof(double) * 2048));
+    double *pa = P<double>(c->small0), *pb = pa + 1024;
+    launch_dot_partial<double>(c->stream, grid, nA, r64, r64, pa);
+    launch_dot_partial<double>(c->stream, grid, nA, P<double>(c->rhs), P<double>(c->rhs), pb);
+    WC4D_TRY(check_launch(c, "true residual"));
+    std::vector<double> h(2 * grid);
+    WC4D_CUDA(c, cudaMemcpyAsync(h.data(), pa, sizeof(double) * grid, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_CUDA(c, cudaMemcpyAsync(h.data() + grid, pb, sizeof(double) * grid, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "true residual"));
+    double rr = 0.0, bb = 0.0;
+    for (int i = 0; i < grid; ++i) { rr += h[i]; bb += h[grid + i]; }
+    *rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    if (bnorm_out) *bnorm_out = std::sqrt(bb);
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxit, int32_t use_lmp, int32_t force,
+                                int32_t precision, int32_t *iters, double *relres, double *qcf_host)
+{
+    if (!c || !x || maxit < 0 || force < 0) return WC4D_EINVAL;
+    if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
+    if (!c->have_rhs) return set_err(c, WC4D_ESTATE, "rhs not set (call wc4d_set_background_obs)");
+    WC4D_TRY(require_operator(c));
+    WC4D_TRY(prep_precision(c, precision));
+    const int64_t nA = c->nA;
+    const int cap = std::max(1, std::max(maxit, force));
+    DevBuf qcf;
+    WC4D_TRY(ensure(c, qcf, sizeof(double) * cap));
+    WC4D_CUDA(c, cudaMemsetAsync(qcf.p, 0, sizeof(double) * cap, c->stream));
+    wc4d_status st = WC4D_OK;
+    int total_it = 0;
+    bool breakdown = false;
+    double rel = 0.0;
+    if (precision == WC4D_FP64) {
+        PcgOut o;
+        st = pcg_core<double>(c, P<double>(c->rhs), x, tol, maxit, force, use_lmp != 0, P<double>(qcf), o);
+        if (st == WC4D_OK) {
+            total_it = o.iters;
+            breakdown = o.breakdown != 0;
+            WC4D_TRY(ensure(c, c->pcg64[7], sizeof(double) * nA));
+            st = true_residual(c, x, P<double>(c->pcg64[7]), &rel, nullptr);
+        }
+    } else {
+        // FP32 CG inside FP64 true-residual refinement
+        WC4D_TRY(ensure(c, c->pcg64[7], sizeof(double) * nA));
+        WC4D_TRY(ensure(c, c->pcg32[0], sizeof(float) * nA));
+        WC4D_TRY(ensure(c, c->pcg32[6], sizeof(float) * nA));
+        double *r64 = P<double>(c->pcg64[7]);
+        float *b32 = P<float>(c->pcg32[6]), *d32 = P<float>(c->pcg32[0]);
+        WC4D_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * nA, c->stream));
+        launch_copy<double>(c->stream, nA, P<double>(c->rhs), r64);
+        double bnorm = 0.0;
+        {
+            double dummy;
+            // |rhs| (x = 0: residual = rhs)
+            const int grid = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA + 255) / 256));
+            WC4D_TRY(ensure(c, c->small0, sizeof(double) * 2048));
+            launch_dot_partial<double>(c->stream, grid, nA, r64, r64, P<double>(c->small0));
+            std::vector<double> h(grid);
+            WC4D_CUDA(c, cudaMemcpyAsync(h.data(), c->small0.p, sizeof(double) * grid, cudaMemcpyDeviceToHost,
+                                         c->stream));
+            WC4D_TRY(sync(c, "bnorm"));
+            double bb = 0.0;
+            for (double v : h) bb += v;
+            bnorm = std::sqrt(bb);
+            (void)dummy;
+        }
+        rel = bnorm > 0.0 ? 1.0 : 0.0;
+        const int budget = (force > 0) ? force : maxit;
+        for (int round = 0; round < 12 && st == WC4D_OK; ++round) {
+            if (force == 0 && rel <= tol) break;
+            if (total_it >= budget) break;
+            double inner_tol = (force > 0) ? 0.0 : std::max(0.5 * tol / rel, 1e-7);
+            launch_convert_f64_f32(c->stream, nA, r64, b32);
+            PcgOut o;
+            st = pcg_core<float>(c, b32, d32, inner_tol, budget - total_it, (force > 0) ? force : 0, use_lmp != 0,
+                                 P<double>(qcf) + total_it, o);
+            if (st != WC4D_OK) break;
+            total_it += o.iters;
+            launch_add_f32_to_f64(c->stream, nA, d32, x);
+            st = true_residual(c, x, r64, &rel, nullptr);
+            if (o.breakdown) { breakdown = true; break; }
+            if (force > 0) break;
+        }
+    }
+    if (st == WC4D_OK && qcf_host) {
+        cudaMemcpyAsync(qcf_host, qcf.p, sizeof(double) * std::min(cap, std::max(total_it, 0)),
+                        cudaMemcpyDeviceToHost, c->stream);
+        st = sync(c, "qcf");
+    }
+    free_buf(qcf);
+    if (st != WC4D_OK) return st;
+    if (iters) *iters = total_it;
+    if (relres) *relres = rel;
+    if (breakdown) return set_err(c, WC4D_EBREAKDOWN, "CG breakdown: p^T A p <= 0 or non-finite");
+    if (!std::isfinite(rel)) return set_err(c, WC4D_ENAN, "non-finite residual");
+    if (force == 0 && rel > tol) return set_err(c, WC4D_ENOCONV, "CG: relres %.3e > tol after %d iterations", rel,
+                                                total_it);
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_inner_loop(wc4d_ctx *c, int32_t method, int32_t k, int32_t l, int32_t q, uint64_t seed,
+                                       double tol, int32_t maxit, int32_t precision, double *x, int32_t *iters,
+                                       double *relres)
+{
+    WC4D_TRY(wc4d_sketch(c, method, k, l, q, seed, nullptr, nullptr, precision));
+    return wc4d_pcg(c, x, tol, maxit, 1, 0, precision, iters, relres, nullptr);
+}

@@ -1,0 +1,264 @@
+// Lorenz-96 (Section 5.2): nonlinear RK4 run, and the exact tangent-linear
+// and adjoint of the RK4 step applied as stencil sweeps to probe blocks.
+//
+// dX_j/dt = (X_{j+1} - X_{j-2}) X_{j-1} - X_j + F (periodic).  Jacobian at x:
+//   (J d)_j   = (d_{j+1} - d_{j-2}) x_{j-1} + (x_{j+1} - x_{j-2}) d_{j-1} - d_j
+//   (J^T a)_i = x_{i-2} a_{i-1} - x_{i+1} a_{i+2} + (x_{i+2} - x_{i-1}) a_{i+1} - a_i
+// The RK4 stage states s1 = x, s2 = x + h/2 k1, s3 = x + h/2 k2, s4 = x + h k3
+// of every step are stored once by the nonlinear run and shared by all
+// probe columns (an L2-resident read-only table).
+#include "wc4d_internal.cuh"
+
+constexpr int L96_THREADS = 512;
+constexpr int L96_PPT = WC4D_FFT_MAX_N / L96_THREADS;   // points per thread (n <= 8192)
+
+__device__ __forceinline__ int wrap(int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); }
+
+template <typename T>
+__device__ __forceinline__ T jac(const T *__restrict__ x, const T *d, int j, int n)
+{
+    const int jm2 = wrap(j - 2, n), jm1 = wrap(j - 1, n), jp1 = wrap(j + 1, n);
+    return (d[jp1] - d[jm2]) * __ldg(x + jm1) + (__ldg(x + jp1) - __ldg(x + jm2)) * d[jm1] - d[j];
+}
+
+template <typename T>
+__device__ __forceinline__ T jacT(const T *__restrict__ x, const T *a, int i, int n)
+{
+    const int im2 = wrap(i - 2, n), im1 = wrap(i - 1, n), ip1 = wrap(i + 1, n), ip2 = wrap(i + 2, n);
+    return __ldg(x + im2) * a[im1] - __ldg(x + ip1) * a[ip2] + (__ldg(x + ip2) - __ldg(x + im1)) * a[ip1] - a[i];
+}
+
+// Forward sweep L^{-1} on one column per CTA: W_{t+1} = M_t W_t + W_{t+1},
+// M_t = `steps` tangent-linear RK4 steps.
+template <typename T>
+__global__ void __launch_bounds__(L96_THREADS)
+k_l96_tlm(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, int64_t ld)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    T *dl = reinterpret_cast<T *>(sm);
+    T *ta = dl + n, *tb = ta + n;
+    T *w = W + (int64_t)blockIdx.x * ld;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = tid; j < n; j += nt) dl[j] = w[j];
+    __syncthreads();
+    T acc[L96_PPT];
+    const T h2 = h * (T)0.5, h6 = h / (T)6;
+    for (int t = 0; t < N; ++t) {
+        for (int k = 0; k < steps; ++k) {
+            const int64_t g = (int64_t)t * steps + k;
+            const T *s1 = stages + (4 * g + 0) * n, *s2 = stages + (4 * g + 1) * n;
+            const T *s3 = stages + (4 * g + 2) * n, *s4 = stages + (4 * g + 3) * n;
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T d = jac(s1, dl, j, n); acc[r] = d; ta[j] = dl[j] + h2 * d; }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T d = jac(s2, ta, j, n); acc[r] += (T)2 * d; tb[j] = dl[j] + h2 * d; }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T d = jac(s3, tb, j, n); acc[r] += (T)2 * d; ta[j] = dl[j] + h * d; }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T d = jac(s4, ta, j, n); acc[r] += d; dl[j] = dl[j] + h6 * acc[r]; }
+            }
+            __syncthreads();
+        }
+        T *wn = w + (int64_t)(t + 1) * n;
+        for (int j = tid; j < n; j += nt) {
+            T v = dl[j] + wn[j];
+            dl[j] = v;
+            wn[j] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Adjoint sweep L^{-T} on one column per CTA.  obs_mode 1:
+// W_N = obs(W_N), W_t = obs_t(W_t) + M_t^T W_{t+1}; obs_mode 0: plain
+// W_t = W_t + M_t^T W_{t+1}.  obs(v)[s] = obs_scale v[s] at observed times
+// and points, zero elsewhere.
+template <typename T>
+__global__ void __launch_bounds__(L96_THREADS)
+k_l96_adj(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, int64_t ld, int obs_mode, T obs_scale,
+          int obs_stride, int t0, int ts)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    T *lam = reinterpret_cast<T *>(sm);
+    T *aa = lam + n, *ab = aa + n;
+    T *w = W + (int64_t)blockIdx.x * ld;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto obs_at = [&](int t) { return t >= t0 && (t - t0) % ts == 0; };
+    {
+        T *wN = w + (int64_t)N * n;
+        const bool ob = obs_at(N);
+        for (int j = tid; j < n; j += nt) {
+            T v = wN[j];
+            if (obs_mode == 1) v = (ob && j % obs_stride == 0) ? obs_scale * v : (T)0;
+            lam[j] = v;
+            wN[j] = v;
+        }
+    }
+    __syncthreads();
+    T acc[L96_PPT];
+    const T h2 = h * (T)0.5, h3 = h / (T)3, h6 = h / (T)6;
+    for (int t = N - 1; t >= 0; --t) {
+        for (int k = steps - 1; k >= 0; --k) {
+            const int64_t g = (int64_t)t * steps + k;
+            const T *s1 = stages + (4 * g + 0) * n, *s2 = stages + (4 * g + 1) * n;
+            const T *s3 = stages + (4 * g + 2) * n, *s4 = stages + (4 * g + 3) * n;
+            for (int j = tid; j < n; j += nt) aa[j] = h6 * lam[j];            // a4
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T g4 = jacT(s4, aa, j, n); acc[r] = lam[j] + g4; ab[j] = h3 * lam[j] + h * g4; }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T g3 = jacT(s3, ab, j, n); acc[r] += g3; aa[j] = h3 * lam[j] + h2 * g3; }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T g2 = jacT(s2, aa, j, n); acc[r] += g2; ab[j] = h6 * lam[j] + h2 * g2; }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < L96_PPT; ++r) {
+                int j = tid + r * nt;
+                if (j < n) { T g1 = jacT(s1, ab, j, n); lam[j] = acc[r] + g1; }
+            }
+            __syncthreads();
+        }
+        T *wt = w + (int64_t)t * n;
+        const bool ob = obs_at(t);
+        for (int j = tid; j < n; j += nt) {
+            T v = wt[j];
+            if (obs_mode == 1) v = (ob && j % obs_stride == 0) ? obs_scale * v : (T)0;
+            v += lam[j];
+            lam[j] = v;
+            wt[j] = v;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
+                          int64_t ld)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_l96_tlm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
+        attr = true;
+    }
+    k_l96_tlm<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld);
+}
+
+template <typename T>
+void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
+                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_l96_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
+        attr = true;
+    }
+    k_l96_adj<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld, obs_mode,
+                                                                     (T)obs_scale, obs_stride, obs_t0,
+                                                                     obs_tstride > 0 ? obs_tstride : 1);
+}
+
+template void launch_l96_tlm_sweep<double>(cudaStream_t, int, int, int, double, const double *, int, double *,
+                                           int64_t);
+template void launch_l96_tlm_sweep<float>(cudaStream_t, int, int, int, double, const float *, int, float *, int64_t);
+template void launch_l96_adj_sweep<double>(cudaStream_t, int, int, int, double, const double *, int, double *,
+                                           int64_t, int, double, int, int, int);
+template void launch_l96_adj_sweep<float>(cudaStream_t, int, int, int, double, const float *, int, float *, int64_t,
+                                          int, double, int, int, int);
+
+// Nonlinear RK4 run in FP64 on one CTA: traj[g+1] = RK4(traj[g]) for
+// g < nsteps, storing the stage states of every step.
+__device__ __forceinline__ double l96f(const double *y, int j, int n, double F)
+{
+    return (y[wrap(j + 1, n)] - y[wrap(j - 2, n)]) * y[wrap(j - 1, n)] - y[j] + F;
+}
+
+__global__ void __launch_bounds__(1024) k_l96_run(int n, int nsteps, double F, double h, double *traj, double *stages)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    double *x = reinterpret_cast<double *>(sm);
+    double *st = x + n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr int R = WC4D_FFT_MAX_N / 1024;
+    double acc[R], d[R];
+    for (int j = tid; j < n; j += nt) x[j] = traj[j];
+    __syncthreads();
+    for (int g = 0; g < nsteps; ++g) {
+        double *sg = stages + (int64_t)4 * g * n;
+        const double cf[3] = {0.5 * h, 0.5 * h, h};
+        const double wgt[4] = {1.0, 2.0, 2.0, 1.0};
+        for (int j = tid; j < n; j += nt) sg[j] = x[j];
+        // stage 1 from x, stages 2-4 from st
+        for (int stage = 0; stage < 4; ++stage) {
+            const double *src = (stage == 0) ? x : st;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int j = tid + r * nt;
+                if (j < n) {
+                    d[r] = l96f(src, j, n, F);
+                    acc[r] = (stage == 0 ? 0.0 : acc[r]) + wgt[stage] * d[r];
+                }
+            }
+            __syncthreads();
+            if (stage < 3) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    int j = tid + r * nt;
+                    if (j < n) {
+                        double v = x[j] + cf[stage] * d[r];
+                        st[j] = v;
+                        sg[(int64_t)(stage + 1) * n + j] = v;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    int j = tid + r * nt;
+                    if (j < n) {
+                        double v = x[j] + h / 6.0 * acc[r];
+                        x[j] = v;
+                        traj[(int64_t)(g + 1) * n + j] = v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_l96_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * WC4D_FFT_MAX_N * sizeof(double)));
+        attr = true;
+    }
+    k_l96_run<<<1, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, nsteps, F, dt, traj, stages);
+}

@@ -1,0 +1,648 @@
+// Dense linear algebra of the randomised eigensolvers and the LMP / PCG
+// vector kernels.  Reductions are two-stage (fixed partial layout, then a
+// single-CTA sum) so that results are bitwise reproducible run to run.
+#include "wc4d_internal.cuh"
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a CTA (blockDim.x multiple of 32, <= 1024); result valid in all threads.
+__device__ double block_sum(double v)
+{
+    __shared__ double red[32];
+    __shared__ double total;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double x = (lane < nw) ? red[lane] : 0.0;
+        x = warp_sum(x);
+        if (lane == 0) total = x;
+    }
+    __syncthreads();
+    return total;
+}
+
+// ----------------------------------------------------------------------------
+// C = A^T B (FP64 accumulation) for tall column-major A (rows x ma) and B
+// (rows x mb): 32 x 32 tiles of C, rows split over blockIdx.y into fixed
+// chunks; partials part[split][j*ma + i] then summed in split order.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_atb(int64_t rows, int ma, int mb, const T *__restrict__ A, int64_t lda, const T *__restrict__ B, int64_t ldb,
+      double *part, int64_t rows_per_split, int tiles_a)
+{
+    __shared__ double As[32][33], Bs[32][33];
+    const int tile = blockIdx.x, ti = tile % tiles_a, tj = tile / tiles_a, split = blockIdx.y;
+    const int64_t r0 = (int64_t)split * rows_per_split;
+    const int64_t r1 = min(rows, r0 + rows_per_split);
+    const int i0 = ti * 32, j0 = tj * 32;
+    const int li = threadIdx.x & 31, lj = threadIdx.x >> 5;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t rb = r0; rb < r1; rb += 32) {
+        const int64_t r = rb + li;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = lj + 8 * q;
+            As[li][c] = (r < r1 && i0 + c < ma) ? (double)A[(int64_t)(i0 + c) * lda + r] : 0.0;
+            Bs[li][c] = (r < r1 && j0 + c < mb) ? (double)B[(int64_t)(j0 + c) * ldb + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) {
+            const double a = As[rr][li];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(a, Bs[rr][lj + 8 * q], acc[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = i0 + li, j = j0 + lj + 8 * q;
+        if (i < ma && j < mb) part[(int64_t)split * ma * mb + (int64_t)j * ma + i] = acc[q];
+    }
+}
+
+__global__ void k_reduce_part(int S, int64_t count, const double *part, double *out)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) acc += part[(int64_t)s * count + e];
+    out[e] = acc;
+}
+
+template <typename T>
+void launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
+                int64_t ldb, double *part, int *splits_out, double *C)
+{
+    const int ta = ceil_div(ma, 32), tb = ceil_div(mb, 32), tiles = ta * tb;
+    int64_t max_splits = (rows + 31) / 32;
+    int64_t S = (2 * (int64_t)num_sms + tiles - 1) / tiles;
+    if (S > max_splits) S = max_splits;
+    if (S < 1) S = 1;
+    int64_t rps = ((rows + S - 1) / S + 31) / 32 * 32;
+    S = (rows + rps - 1) / rps;
+    if (S < 1) S = 1;
+    dim3 g(tiles, (unsigned)S);
+    k_atb<T><<<g, 256, 0, s>>>(rows, ma, mb, A, lda, B, ldb, part, rps, ta);
+    if (splits_out) *splits_out = (int)S;
+    if (C) {
+        int64_t cnt = (int64_t)ma * mb;
+        k_reduce_part<<<ceil_div(cnt, 256), 256, 0, s>>>((int)S, cnt, part, C);
+    }
+}
+
+template void launch_atb<double>(cudaStream_t, int, int64_t, int, int, const double *, int64_t, const double *,
+                                 int64_t, double *, int *, double *);
+template void launch_atb<float>(cudaStream_t, int, int64_t, int, int, const float *, int64_t, const float *,
+                                int64_t, double *, int *, double *);
+
+// ----------------------------------------------------------------------------
+// Cholesky A = R^T R (R upper, column-major m x m), right-looking, one CTA.
+// info = 0, or j+1 when pivot j is not positive / not finite.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_chol_upper(int m, const double *A, double *R, int *info)
+{
+    __shared__ int bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
+        int i = (int)(idx % m), j = (int)(idx / m);
+        R[idx] = (i <= j) ? A[idx] : 0.0;
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        if (tid == 0) {
+            double d = R[(int64_t)j * m + j];
+            if (!(d > 0.0) || !isfinite(d)) bad = j + 1;
+            else R[(int64_t)j * m + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double rjj = R[(int64_t)j * m + j];
+        for (int i = j + 1 + tid; i < m; i += nt) R[(int64_t)i * m + j] /= rjj;
+        __syncthreads();
+        const int w = m - j - 1;
+        for (int64_t idx = tid; idx < (int64_t)w * w; idx += nt) {
+            int a = (int)(idx % w), b = (int)(idx / w);
+            if (a > b) continue;
+            int ga = j + 1 + a, gb = j + 1 + b;
+            R[(int64_t)gb * m + ga] -= R[(int64_t)ga * m + j] * R[(int64_t)gb * m + j];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *info = bad;
+}
+
+void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *info)
+{
+    k_chol_upper<<<1, 1024, 0, s>>>(m, A, R, info);
+}
+
+// Inverse of an upper-triangular R (column-major): one thread per column,
+// back substitution R x = e_j.
+__global__ void k_trinv_upper(int m, const double *R, double *Rinv)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double *x = Rinv + (int64_t)j * m;
+    for (int i = j + 1; i < m; ++i) x[i] = 0.0;
+    x[j] = 1.0 / R[(int64_t)j * m + j];
+    for (int i = j - 1; i >= 0; --i) {
+        double acc = 0.0;
+        for (int c = i + 1; c <= j; ++c) acc = fma(R[(int64_t)c * m + i], x[c], acc);
+        x[i] = -acc / R[(int64_t)i * m + i];
+    }
+}
+
+void launch_trinv_upper(cudaStream_t s, int m, const double *R, double *Rinv)
+{
+    k_trinv_upper<<<ceil_div(m, 64), 64, 0, s>>>(m, R, Rinv);
+}
+
+// RT = R^T (m x m column-major).
+__global__ void k_transpose_small(int m, const double *R, double *RT)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    int i = (int)(idx % m), j = (int)(idx / m);
+    RT[(int64_t)i * m + j] = R[idx];
+}
+
+void launch_rrt(cudaStream_t s, int m, const double *R, double *RT)
+{
+    k_transpose_small<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, R, RT);
+}
+
+__global__ void k_symmetrize(int m, double *S)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    int i = (int)(idx % m), j = (int)(idx / m);
+    if (i < j) {
+        double v = 0.5 * (S[(int64_t)j * m + i] + S[(int64_t)i * m + j]);
+        S[(int64_t)j * m + i] = v;
+        S[(int64_t)i * m + j] = v;
+    }
+}
+
+void launch_symmetrize(cudaStream_t s, int m, double *S)
+{
+    k_symmetrize<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, S);
+}
+
+// A[:, j] *= w_j^{-1/2} (inv_sqrt = 1) or 1/w_j (inv_sqrt = 0).
+__global__ void k_scale_cols(int64_t rows, int m, double *A, int64_t lda, const double *w, int inv_sqrt)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * m) return;
+    int64_t r = idx % rows;
+    int j = (int)(idx / rows);
+    double f = inv_sqrt ? 1.0 / sqrt(w[j]) : 1.0 / w[j];
+    A[(int64_t)j * lda + r] *= f;
+}
+
+void launch_scale_cols(cudaStream_t s, int64_t rows, int m, double *A, int64_t lda, const double *w, int inv_sqrt)
+{
+    k_scale_cols<<<ceil_div(rows * m, 256), 256, 0, s>>>(rows, m, A, lda, w, inv_sqrt);
+}
+
+// ----------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi: X V = U Sigma.  For symmetric positive semi-
+// definite S, X = S gives S's eigenvectors V and eigenvalues |X_j|; for
+// X = R^T it gives the left singular vectors of R.  Parallel round-robin
+// ordering: round r pairs positions (i, mp-1-i), position 0 fixed, others
+// rotated; one CTA per pair, one launch per round.
+// ----------------------------------------------------------------------------
+__global__ void k_jacobi_init(int m, int mp, const double *S, double *X, double *V)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)mp * mp) return;
+    int i = (int)(idx % mp), j = (int)(idx / mp);
+    X[idx] = (i < m && j < m) ? S[(int64_t)j * m + i] : 0.0;
+    V[idx] = (i == j) ? 1.0 : 0.0;
+}
+
+void launch_jacobi_init(cudaStream_t s, int m, int mp, const double *S, double *X, double *V)
+{
+    k_jacobi_init<<<ceil_div((int64_t)mp * mp, 256), 256, 0, s>>>(m, mp, S, X, V);
+}
+
+__global__ void __launch_bounds__(128) k_jacobi_round(int mp, double *X, double *V, int round, double tol, int *rot)
+{
+    __shared__ double cs_s[2];
+    __shared__ int doit;
+    const int i = blockIdx.x;
+    auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (mp - 1); };
+    int p = player(i), q = player(mp - 1 - i);
+    if (p > q) { int t = p; p = q; q = t; }
+    double *xp = X + (int64_t)p * mp, *xq = X + (int64_t)q * mp;
+    double a = 0.0, b = 0.0, g = 0.0;
+    for (int r = threadIdx.x; r < mp; r += blockDim.x) {
+        double u = xp[r], v = xq[r];
+        a = fma(u, u, a);
+        b = fma(v, v, b);
+        g = fma(u, v, g);
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    g = block_sum(g);
+    if (threadIdx.x == 0) {
+        doit = 0;
+        if (fabs(g) > tol * sqrt(a * b) && fabs(g) > 1e-300) {
+            double zeta = (b - a) / (2.0 * g);
+            double t;
+            if (fabs(zeta) > 1e100) t = 0.5 / zeta;
+            else t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            double c = 1.0 / sqrt(1.0 + t * t);
+            cs_s[0] = c;
+            cs_s[1] = c * t;
+            doit = 1;
+            atomicAdd(rot, 1);
+        }
+    }
+    __syncthreads();
+    if (!doit) return;
+    const double c = cs_s[0], sn = cs_s[1];
+    double *vp = V + (int64_t)p * mp, *vq = V + (int64_t)q * mp;
+    for (int r = threadIdx.x; r < mp; r += blockDim.x) {
+        double u = xp[r], v = xq[r];
+        xp[r] = c * u - sn * v;
+        xq[r] = sn * u + c * v;
+        double y = vp[r], z = vq[r];
+        vp[r] = c * y - sn * z;
+        vq[r] = sn * y + c * z;
+    }
+}
+
+void launch_jacobi_round(cudaStream_t s, int mp, double *X, double *V, int round, double tol, int *rot)
+{
+    k_jacobi_round<<<mp / 2, 128, 0, s>>>(mp, X, V, round, tol, rot);
+}
+
+// Column norms, sorted decreasing; Vout[:, rank] = V[0:m, j].
+__global__ void k_colnorm(int m, int mp, const double *X, double *w)
+{
+    int j = blockIdx.x;
+    double a = 0.0;
+    for (int r = threadIdx.x; r < mp; r += blockDim.x) {
+        double u = X[(int64_t)j * mp + r];
+        a = fma(u, u, a);
+    }
+    a = block_sum(a);
+    if (threadIdx.x == 0) w[j] = sqrt(a);
+}
+
+__global__ void k_sort_cols(int m, int mp, const double *wn, const double *V, double *w, double *Vout)
+{
+    int j = blockIdx.x;
+    __shared__ int rank;
+    if (threadIdx.x == 0) {
+        int r = 0;
+        double wj = wn[j];
+        for (int i = 0; i < m; ++i)
+            if (wn[i] > wj || (wn[i] == wj && i < j)) ++r;
+        rank = r;
+        w[r] = wj;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) Vout[(int64_t)rank * m + r] = V[(int64_t)j * mp + r];
+}
+
+void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const double *V, double *w, double *Vout)
+{
+    // w is used first as scratch for the unsorted norms (length m) at w + m
+    k_colnorm<<<m, 128, 0, s>>>(m, mp, X, w + m);
+    k_sort_cols<<<m, 128, 0, s>>>(m, mp, w + m, V, w, Vout);
+}
+
+// ----------------------------------------------------------------------------
+// Spectral LMP (eq. 16, closed form for orthonormal U):
+//   C v = v - U (c o (U^T v)),  c_i = 1 - theta_i^{-1/2}.
+// ----------------------------------------------------------------------------
+__global__ void k_lmp_coeffs(int k, const double *theta, double *c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) c[i] = theta[i] > 0.0 ? 1.0 - 1.0 / sqrt(theta[i]) : 0.0;
+}
+
+void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c)
+{
+    k_lmp_coeffs<<<ceil_div(k, 128), 128, 0, s>>>(k, theta, c);
+}
+
+constexpr int UTV_ROWS = 1024;
+
+// part[split][i] = sum over the split's rows of U[r, i] v[r]; one warp per
+// column at a time, v staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_utv(int64_t nA, int k, const T *__restrict__ U, const T *__restrict__ v,
+                                             double *part)
+{
+    __shared__ T vs[UTV_ROWS];
+    const int64_t r0 = (int64_t)blockIdx.x * UTV_ROWS;
+    const int rows = (int)min((int64_t)UTV_ROWS, nA - r0);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) vs[r] = v[r0 + r];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = w; i < k; i += nw) {
+        const T *u = U + (int64_t)i * nA + r0;
+        T acc = 0;
+        for (int r = lane; r < rows; r += 32) acc = fma(u[r], vs[r], acc);
+        double d = warp_sum((double)acc);
+        if (lane == 0) part[(int64_t)blockIdx.x * k + i] = d;
+    }
+}
+
+template <typename T>
+void launch_utv(cudaStream_t s, int num_sms, int64_t nA, int k, const T *U, const T *v, double *part, int *splits)
+{
+    int S = ceil_div(nA, UTV_ROWS);
+    k_utv<T><<<S, 256, 0, s>>>(nA, k, U, v, part);
+    *splits = S;
+}
+
+template void launch_utv<double>(cudaStream_t, int, int64_t, int, const double *, const double *, double *, int *);
+template void launch_utv<float>(cudaStream_t, int, int64_t, int, const float *, const float *, double *, int *);
+
+// y = v - coef * U (c o t) (+ beta * add), t_i = sum_s part[s][i]; each CTA
+// first reduces the k partial columns into shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_lmp_combine(int64_t nA, int k, const T *__restrict__ U, const double *__restrict__ part, int splits,
+              const double *__restrict__ cvec, double coef, const T *v, T *y, const T *add,
+              const double *beta_dev, const int *skip)
+{
+    extern __shared__ double ct[];
+    if (skip && *skip) return;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double t = 0.0;
+        for (int sidx = 0; sidx < splits; ++sidx) t += part[(int64_t)sidx * k + i];
+        ct[i] = coef * cvec[i] * t;
+    }
+    __syncthreads();
+    const T beta = beta_dev ? (T)*beta_dev : (T)0;
+    // accumulate in the storage precision (FP32 vectors in the mixed path)
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nA; r += (int64_t)gridDim.x * blockDim.x) {
+        T acc = v[r];
+        for (int i = 0; i < k; ++i) acc = fma(-U[(int64_t)i * nA + r], (T)ct[i], acc);
+        if (add) acc = fma(beta, add[r], acc);
+        y[r] = acc;
+    }
+}
+
+template <typename T>
+void launch_lmp_combine(cudaStream_t s, int64_t nA, int k, const T *U, const double *part, int splits,
+                        const double *cvec, double coef, const T *v, T *y, const T *add, const double *beta_dev,
+                        const int *skip)
+{
+    int grid = ceil_div(nA, 256);
+    if (grid > 4096) grid = 4096;
+    k_lmp_combine<T><<<grid, 256, (size_t)k * sizeof(double), s>>>(nA, k, U, part, splits, cvec, coef, v, y, add,
+                                                                      beta_dev, skip);
+}
+
+template void launch_lmp_combine<double>(cudaStream_t, int64_t, int, const double *, const double *, int,
+                                         const double *, double, const double *, double *, const double *,
+                                         const double *, const int *);
+template void launch_lmp_combine<float>(cudaStream_t, int64_t, int, const float *, const double *, int,
+                                        const double *, double, const float *, float *, const float *,
+                                        const double *, const int *);
+
+// ----------------------------------------------------------------------------
+// PCG (Alg. 1) vector and scalar kernels.  Scalars live in device memory:
+// scal[0] rho = rhat^T rhat, [1] alpha, [2] beta, [3] |b|, [4] |r|/|b|,
+// [5] p^T A p, [6] |r|^2; flags[0] done, [1] breakdown, [2] iterations.
+// ----------------------------------------------------------------------------
+enum { S_RHO = 0, S_ALPHA, S_BETA, S_BNORM, S_RELRES, S_PQ, S_RR };
+enum { F_DONE = 0, F_BREAK, F_ITER };
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const T *a, const T *b, double *part)
+{
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma((double)a[i], (double)b[i], acc);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+template <typename T>
+void launch_dot_partial(cudaStream_t s, int grid, int64_t n, const T *a, const T *b, double *part)
+{
+    k_dot_partial<T><<<grid, 256, 0, s>>>(n, a, b, part);
+}
+
+template void launch_dot_partial<double>(cudaStream_t, int, int64_t, const double *, const double *, double *);
+template void launch_dot_partial<float>(cudaStream_t, int, int64_t, const float *, const float *, double *);
+
+__device__ double sum_part(int grid, const double *part)
+{
+    double a = 0.0;
+    for (int i = threadIdx.x; i < grid; i += blockDim.x) a += part[i];
+    return block_sum(a);
+}
+
+__global__ void k_pcg_init(int grid, const double *part_b, const double *part_rh, double *scal, int *flags)
+{
+    double bb = sum_part(grid, part_b);
+    double rho = sum_part(grid, part_rh);
+    if (threadIdx.x == 0) {
+        scal[S_RHO] = rho;
+        scal[S_BNORM] = sqrt(bb);
+        scal[S_RELRES] = bb > 0.0 ? 1.0 : 0.0;
+        scal[S_ALPHA] = 0.0;
+        scal[S_BETA] = 0.0;
+        flags[F_DONE] = (bb > 0.0) ? 0 : 1;
+        flags[F_BREAK] = 0;
+        flags[F_ITER] = 0;
+    }
+}
+
+void launch_pcg_init(cudaStream_t s, int grid, const double *part_b, const double *part_rh, double *scal, int *flags)
+{
+    k_pcg_init<<<1, 256, 0, s>>>(grid, part_b, part_rh, scal, flags);
+}
+
+__global__ void k_pcg_alpha(int grid, const double *part, double *scal, int *flags)
+{
+    double pq = sum_part(grid, part);
+    if (threadIdx.x == 0) {
+        scal[S_PQ] = pq;
+        if (flags[F_DONE]) {
+            scal[S_ALPHA] = 0.0;
+        } else if (!(pq > 0.0) || !isfinite(pq)) {
+            flags[F_BREAK] = 1;
+            flags[F_DONE] = 1;
+            scal[S_ALPHA] = 0.0;
+        } else {
+            scal[S_ALPHA] = scal[S_RHO] / pq;
+        }
+    }
+}
+
+void launch_pcg_alpha(cudaStream_t s, int grid, const double *part, double *scal, int *flags)
+{
+    k_pcg_alpha<<<1, 256, 0, s>>>(grid, part, scal, flags);
+}
+
+// x += alpha p; r -= alpha q; partial |r|^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_xr(int64_t n, const double *scal, T *x, T *r, const T *p, const T *q,
+                                                double *part)
+{
+    const double alpha = scal[S_ALPHA];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = (T)((double)x[i] + alpha * (double)p[i]);
+        double ri = (double)r[i] - alpha * (double)q[i];
+        r[i] = (T)ri;
+        acc = fma(ri, ri, acc);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+template <typename T>
+void launch_pcg_xr(cudaStream_t s, int grid, int64_t n, const double *scal, T *x, T *r, const T *p, const T *q,
+                   double *part)
+{
+    k_pcg_xr<T><<<grid, 256, 0, s>>>(n, scal, x, r, p, q, part);
+}
+
+// rhat -= alpha t; partial rhat^T rhat
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_rh(int64_t n, const double *scal, T *rh, const T *t, double *part)
+{
+    const double alpha = scal[S_ALPHA];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = (double)rh[i] - alpha * (double)t[i];
+        rh[i] = (T)v;
+        acc = fma(v, v, acc);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+template <typename T>
+void launch_pcg_rh(cudaStream_t s, int grid, int64_t n, const double *scal, T *rh, const T *t, double *part)
+{
+    k_pcg_rh<T><<<grid, 256, 0, s>>>(n, scal, rh, t, part);
+}
+
+__global__ void k_pcg_beta(int grid, const double *part_rh, const double *part_r, double *scal, int *flags,
+                           double tol, double *qcf_drop, int it)
+{
+    double rho_new = sum_part(grid, part_rh);
+    double rr = sum_part(grid, part_r);
+    if (threadIdx.x == 0) {
+        if (flags[F_DONE]) {
+            scal[S_BETA] = 0.0;
+            return;
+        }
+        double rho = scal[S_RHO];
+        scal[S_BETA] = rho_new / rho;
+        if (qcf_drop) qcf_drop[it] = 0.5 * scal[S_ALPHA] * rho;
+        scal[S_RHO] = rho_new;
+        scal[S_RR] = rr;
+        double rel = sqrt(rr) / scal[S_BNORM];
+        scal[S_RELRES] = rel;
+        flags[F_ITER] += 1;
+        if (!isfinite(rel)) { flags[F_BREAK] = 2; flags[F_DONE] = 1; }
+        else if (tol > 0.0 && rel <= tol) flags[F_DONE] = 1;
+    }
+}
+
+void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
+                     int *flags, double tol, double *qcf_drop, int it)
+{
+    k_pcg_beta<<<1, 256, 0, s>>>(grid, part_rh, part_r, scal, flags, tol, qcf_drop, it);
+}
+
+// p = t + beta p
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_p(int64_t n, const double *scal, T *p, const T *t)
+{
+    const double beta = scal[S_BETA];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (T)((double)t[i] + beta * (double)p[i]);
+}
+
+template <typename T>
+void launch_pcg_p(cudaStream_t s, int grid, int64_t n, const double *scal, T *p, const T *t)
+{
+    k_pcg_p<T><<<grid, 256, 0, s>>>(n, scal, p, t);
+}
+
+template void launch_pcg_xr<double>(cudaStream_t, int, int64_t, const double *, double *, double *, const double *,
+                                    const double *, double *);
+template void launch_pcg_xr<float>(cudaStream_t, int, int64_t, const double *, float *, float *, const float *,
+                                   const float *, double *);
+template void launch_pcg_rh<double>(cudaStream_t, int, int64_t, const double *, double *, const double *, double *);
+template void launch_pcg_rh<float>(cudaStream_t, int, int64_t, const double *, float *, const float *, double *);
+template void launch_pcg_p<double>(cudaStream_t, int, int64_t, const double *, double *, const double *);
+template void launch_pcg_p<float>(cudaStream_t, int, int64_t, const double *, float *, const float *);
+
+template <typename T>
+__global__ void k_copy(int64_t n, const T *a, T *b)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+template <typename T>
+void launch_copy(cudaStream_t s, int64_t n, const T *a, T *b)
+{
+    if (n > 0) k_copy<T><<<ceil_div(n, 256), 256, 0, s>>>(n, a, b);
+}
+
+template void launch_copy<double>(cudaStream_t, int64_t, const double *, double *);
+template void launch_copy<float>(cudaStream_t, int64_t, const float *, float *);
+
+// y = alpha x + beta y
+template <typename T>
+__global__ void k_axpby(int64_t n, double alpha, const T *x, double beta, T *y)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (T)(alpha * (double)x[i] + beta * (double)y[i]);
+}
+
+template <typename T>
+void launch_axpby(cudaStream_t s, int64_t n, double alpha, const T *x, double beta, T *y)
+{
+    if (n > 0) k_axpby<T><<<ceil_div(n, 256), 256, 0, s>>>(n, alpha, x, beta, y);
+}
+
+template void launch_axpby<double>(cudaStream_t, int64_t, double, const double *, double, double *);
+template void launch_axpby<float>(cudaStream_t, int64_t, double, const float *, double, float *);
+
+__global__ void k_sub_f64(int64_t n, const double *a, const double *b, double *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] - b[i];
+}
+
+void launch_sub_f64(cudaStream_t s, int64_t n, const double *a, const double *b, double *out)
+{
+    if (n > 0) k_sub_f64<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b, out);
+}
+
+__global__ void k_add_f32_to_f64(int64_t n, const float *a, double *b)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] += (double)a[i];
+}
+
+void launch_add_f32_to_f64(cudaStream_t s, int64_t n, const float *a, double *b)
+{
+    if (n > 0) k_add_f32_to_f64<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b);
+}

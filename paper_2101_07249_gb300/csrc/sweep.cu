@@ -1,0 +1,369 @@
+// Kernels of the Hessian product (eq. 10): D^{1/2} (circulant, FFT or
+// direct), the tangent-linear / adjoint sweeps as SIMT GEMM / GEMV over the
+// dense propagators, and the observation term H^T R^{-1} H.
+#include "wc4d_internal.cuh"
+
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using t = double2; };
+template <> struct Cplx<float> { using t = float2; };
+
+template <typename CT> __device__ __forceinline__ CT cadd(CT a, CT b) { a.x += b.x; a.y += b.y; return a; }
+template <typename CT> __device__ __forceinline__ CT csub(CT a, CT b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename CT> __device__ __forceinline__ CT cmul(CT a, CT b)
+{
+    CT r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename CT> __device__ __forceinline__ CT cmulconj(CT a, CT b)   // a * conj(b)
+{
+    CT r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+
+// ----------------------------------------------------------------------------
+// D^{1/2} on two real vectors at once: z = x_a + i x_b, radix-2 decimation-
+// in-frequency FFT (natural in, bit-reversed out) in shared memory, scale by
+// the real sqrt spectrum (stored bit-reversed, already divided by n), then
+// a decimation-in-time inverse FFT (bit-reversed in, natural out).  The
+// circulant is real and symmetric, so Re / Im of the result are D^{1/2} x_a
+// and D^{1/2} x_b.  Vectors of block 0 use B's spectrum and pair among
+// themselves; vectors of blocks 1..N use Q's.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy,
+           const T *addX, int64_t ld_add, const T *__restrict__ specB, const T *__restrict__ specQ,
+           const typename Cplx<T>::t *__restrict__ tw, int nBpairs)
+{
+    using CT = typename Cplx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CT *buf = reinterpret_cast<CT *>(smem_raw);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int pair = blockIdx.x;
+    const T *spec;
+    int64_t ja, ta, jb = 0, tb = 0;
+    bool hasb;
+    if (pair < nBpairs) {
+        int64_t va = 2 * (int64_t)pair, vb = va + 1;
+        spec = specB;
+        ja = va; ta = 0;
+        hasb = vb < K;
+        if (hasb) { jb = vb; tb = 0; }
+    } else {
+        int64_t p = pair - nBpairs;
+        int64_t va = 2 * p, vb = va + 1, cnt = (int64_t)K * N;
+        spec = specQ;
+        ja = va / N; ta = 1 + va % N;
+        hasb = vb < cnt;
+        if (hasb) { jb = vb / N; tb = 1 + vb % N; }
+    }
+    const T *xa = X + ja * ldx + ta * n;
+    const T *xb = X + jb * ldx + tb * n;
+    for (int s = tid; s < n; s += nt) {
+        CT v;
+        v.x = xa[s];
+        v.y = hasb ? xb[s] : (T)0;
+        buf[s] = v;
+    }
+    __syncthreads();
+    const int half = n >> 1;
+    // forward DIF: span h = n/2 .. 1, twiddle W_{2h}^{pos} = tw[pos * n/(2h)]
+    for (int lh = logn - 1; lh >= 0; --lh) {
+        const int h = 1 << lh, stride = half >> lh;
+        for (int b = tid; b < half; b += nt) {
+            int pos = b & (h - 1);
+            int j = ((b >> lh) << (lh + 1)) + pos;
+            CT a = buf[j], c = buf[j + h];
+            buf[j] = cadd(a, c);
+            buf[j + h] = cmul(csub(a, c), tw[pos * stride]);
+        }
+        __syncthreads();
+    }
+    for (int p = tid; p < n; p += nt) {
+        T w = spec[p];
+        CT v = buf[p];
+        v.x *= w; v.y *= w;
+        buf[p] = v;
+    }
+    __syncthreads();
+    // inverse DIT: span h = 1 .. n/2, twiddle conj(W_{2h}^{pos})
+    for (int lh = 0; lh < logn; ++lh) {
+        const int h = 1 << lh, stride = half >> lh;
+        for (int b = tid; b < half; b += nt) {
+            int pos = b & (h - 1);
+            int j = ((b >> lh) << (lh + 1)) + pos;
+            CT a = buf[j];
+            CT c = cmulconj(buf[j + h], tw[pos * stride]);
+            buf[j] = cadd(a, c);
+            buf[j + h] = csub(a, c);
+        }
+        __syncthreads();
+    }
+    T *ya = Y + ja * ldy + ta * n;
+    T *yb = Y + jb * ldy + tb * n;
+    const T *aa = addX ? addX + ja * ld_add + ta * n : nullptr;
+    const T *ab = addX ? addX + jb * ld_add + tb * n : nullptr;
+    for (int s = tid; s < n; s += nt) {
+        CT v = buf[s];
+        ya[s] = v.x + (aa ? aa[s] : (T)0);
+        if (hasb) yb[s] = v.y + (ab ? ab[s] : (T)0);
+    }
+}
+
+// Direct symmetric circulant product for any n: y_s = sum_r row[r] x[(s+r) mod n].
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_circ_direct(int n, int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy, const T *addX,
+              int64_t ld_add, const T *__restrict__ rowB, const T *__restrict__ rowQ)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    T *rs = xs + n;
+    int64_t v = blockIdx.x;
+    int64_t j = v / (N + 1), t = v % (N + 1);
+    const T *row = (t == 0) ? rowB : rowQ;
+    const T *x = X + j * ldx + t * n;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) { xs[s] = x[s]; rs[s] = row[s]; }
+    __syncthreads();
+    T *y = Y + j * ldy + t * n;
+    const T *a = addX ? addX + j * ld_add + t * n : nullptr;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        T acc = 0;
+        int idx = s;
+        for (int r = 0; r < n; ++r) {
+            acc += rs[r] * xs[idx];
+            idx = (idx + 1 == n) ? 0 : idx + 1;
+        }
+        y[s] = acc + (a ? a[s] : (T)0);
+    }
+}
+
+template <typename T>
+void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy,
+                      const T *addX, int64_t ld_add, bool fft, const T *specB, const T *specQ, const T *rowB,
+                      const T *rowQ, const void *tw)
+{
+    const int n = c->prob.n, N = c->prob.N;
+    if (fft) {
+        size_t smem = (size_t)n * sizeof(typename Cplx<T>::t);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_circ_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(WC4D_FFT_MAX_N * sizeof(typename Cplx<T>::t)));
+            attr = true;
+        }
+        int nB = (K + 1) / 2;
+        int64_t nQ = ((int64_t)K * N + 1) / 2;
+        int grid = (int)(nB + nQ);
+        k_circ_fft<T><<<grid, 256, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,
+                                              (const typename Cplx<T>::t *)tw, nB);
+    } else {
+        size_t smem = 2 * (size_t)n * sizeof(T);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_circ_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * WC4D_FFT_MAX_N * sizeof(T)));
+            attr = true;
+        }
+        int64_t grid = (int64_t)K * (N + 1);
+        k_circ_direct<T><<<(unsigned)grid, 256, smem, s>>>(n, N, K, X, ldx, Y, ldy, addX, ld_add, rowB, rowQ);
+    }
+}
+
+template void launch_circulant<double>(cudaStream_t, const wc4d_ctx *, int, const double *, int64_t, double *,
+                                       int64_t, const double *, int64_t, bool, const double *, const double *,
+                                       const double *, const double *, const void *);
+template void launch_circulant<float>(cudaStream_t, const wc4d_ctx *, int, const float *, int64_t, float *,
+                                      int64_t, const float *, int64_t, bool, const float *, const float *,
+                                      const float *, const float *, const void *);
+
+// ----------------------------------------------------------------------------
+// SIMT GEMM: C(i,j) = epi(sum_k A(i,k) B(k,j)); A(i,k) = A[i*sam + k*sak],
+// B(k,j) = B[k + j*ldb] (column-major, k contiguous), C column-major.
+// BM x BN tile per CTA, BK-deep k slices staged in shared memory, TM x TN
+// outputs per thread (rows strided by BM/TM so that a warp stores
+// consecutive rows of the column-major C).
+// ----------------------------------------------------------------------------
+template <typename Acc>
+__device__ __forceinline__ Acc apply_epi(const Epi &e, Acc acc, int i, const Acc *old)
+{
+    if (e.mode == 1) {
+        Acc o = (i % e.obs_stride == 0) ? (Acc)e.obs_scale * (*old) : (Acc)0;
+        return acc + o;
+    }
+    Acc r = (Acc)e.alpha * acc;
+    if (e.beta != 0.0) r += (Acc)e.beta * (*old);
+    return r;
+}
+
+template <typename T, typename Acc, int BM, int BN, int BK, int TM, int TN, bool A_KCONTIG>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm_simt(int Mrows, int Ncols, int Kdim, const T *__restrict__ A, int64_t sam, int64_t sak,
+            const T *__restrict__ B, int64_t ldb, T *C, int64_t ldc, Epi e)
+{
+    constexpr int RT = BM / TM, CTt = BN / TN, NT = RT * CTt;
+    __shared__ Acc As[BK][BM + 1];
+    __shared__ Acc Bs[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int tr = tid % RT, tc = tid / RT;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    Acc acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) acc[r][q] = (Acc)0;
+
+    for (int k0 = 0; k0 < Kdim; k0 += BK) {
+        for (int l = tid; l < BM * BK; l += NT) {
+            int i, kk;
+            if (A_KCONTIG) { kk = l % BK; i = l / BK; }
+            else { i = l % BM; kk = l / BM; }
+            int64_t gi = m0 + i;
+            int gk = k0 + kk;
+            As[kk][i] = (gi < Mrows && gk < Kdim) ? (Acc)A[gi * sam + (int64_t)gk * sak] : (Acc)0;
+        }
+        for (int l = tid; l < BN * BK; l += NT) {
+            int kk = l % BK, j = l / BK;
+            int64_t gj = n0 + j;
+            int gk = k0 + kk;
+            Bs[kk][j] = (gj < Ncols && gk < Kdim) ? (Acc)B[gk + gj * ldb] : (Acc)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            Acc a[TM], b[TN];
+#pragma unroll
+            for (int r = 0; r < TM; ++r) a[r] = As[kk][tr + r * RT];
+#pragma unroll
+            for (int q = 0; q < TN; ++q) b[q] = Bs[kk][tc + q * CTt];
+#pragma unroll
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int q = 0; q < TN; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) {
+            int64_t i = m0 + tr + r * RT, j = n0 + tc + q * CTt;
+            if (i < Mrows && j < Ncols) {
+                T *dst = C + i + j * ldc;
+                Acc old = (e.mode == 1 || e.beta != 0.0) ? (Acc)(*dst) : (Acc)0;
+                *dst = (T)apply_epi<Acc>(e, acc[r][q], (int)i, &old);
+            }
+        }
+}
+
+// y = epi(M x) with one warp per row of the row-major n x n M; VEC-wide loads.
+template <typename T, typename Acc, int VEC>
+__global__ void __launch_bounds__(256)
+k_gemv_rows(int n, const T *__restrict__ M, const T *__restrict__ x, T *y, Epi e)
+{
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const T *row = M + (int64_t)warp * n;
+    Acc acc = 0;
+    if (VEC == 1) {
+        for (int c = lane; c < n; c += 32) acc = fma((Acc)row[c], (Acc)__ldg(x + c), acc);
+    } else {
+        using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+        const V *r4 = reinterpret_cast<const V *>(row);
+        const V *x4 = reinterpret_cast<const V *>(x);
+        const int nv = n / VEC;
+        for (int c = lane; c < nv; c += 32) {
+            V a = __ldg(r4 + c), b = __ldg(x4 + c);
+            if constexpr (sizeof(T) == 8) {
+                acc = fma((Acc)a.x, (Acc)b.x, acc);
+                acc = fma((Acc)a.y, (Acc)b.y, acc);
+            } else {
+                const float *af = reinterpret_cast<const float *>(&a);
+                const float *bf = reinterpret_cast<const float *>(&b);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc = fma((Acc)af[u], (Acc)bf[u], acc);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        Acc old = (e.mode == 1 || e.beta != 0.0) ? (Acc)y[warp] : (Acc)0;
+        y[warp] = (T)apply_epi<Acc>(e, acc, warp, &old);
+    }
+}
+
+template <typename T>
+static bool aligned16(const T *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
+                       const Epi &e)
+{
+    using Acc = T;
+    if (K == 1) {
+        constexpr int VEC = sizeof(T) == 8 ? 2 : 4;
+        int grid = ceil_div((int64_t)n * 32, 256);
+        if (n % VEC == 0 && aligned16(M) && aligned16(B))
+            k_gemv_rows<T, Acc, VEC><<<grid, 256, 0, s>>>(n, M, B, C, e);
+        else
+            k_gemv_rows<T, Acc, 1><<<grid, 256, 0, s>>>(n, M, B, C, e);
+        return;
+    }
+    launch_gemm<T>(s, n, K, n, M, n, 1, B, ldb, C, ldc, e);
+}
+
+template <typename T>
+void launch_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, int64_t sak,
+                 const T *B, int64_t ldb, T *C, int64_t ldc, const Epi &e)
+{
+    using Acc = T;
+    if (Mrows <= 0 || Ncols <= 0) return;
+    const bool kc = (sak == 1);
+    if (Ncols <= 16) {
+        dim3 g(ceil_div(Mrows, 64), ceil_div(Ncols, 16));
+        if (kc) k_gemm_simt<T, Acc, 64, 16, 16, 4, 4, true><<<g, 64, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
+        else k_gemm_simt<T, Acc, 64, 16, 16, 4, 4, false><<<g, 64, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
+    } else {
+        dim3 g(ceil_div(Mrows, 64), ceil_div(Ncols, 64));
+        if (kc) k_gemm_simt<T, Acc, 64, 64, 16, 4, 4, true><<<g, 256, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
+        else k_gemm_simt<T, Acc, 64, 64, 16, 4, 4, false><<<g, 256, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
+    }
+}
+
+template void launch_sweep_gemm<double>(cudaStream_t, int, int, const double *, const double *, int64_t, double *,
+                                        int64_t, const Epi &);
+template void launch_sweep_gemm<float>(cudaStream_t, int, int, const float *, const float *, int64_t, float *,
+                                       int64_t, const Epi &);
+template void launch_gemm<double>(cudaStream_t, int, int, int, const double *, int64_t, int64_t, const double *,
+                                  int64_t, double *, int64_t, const Epi &);
+template void launch_gemm<float>(cudaStream_t, int, int, int, const float *, int64_t, int64_t, const float *,
+                                 int64_t, float *, int64_t, const Epi &);
+
+// W(t block) <- H^T R^{-1} H W for one time block: keep observed points
+// (s % stride == 0) scaled by `scale`, zero the rest.
+template <typename T>
+__global__ void k_obs_block(int n, int K, T *W, int64_t ld, double scale, int stride)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * K) return;
+    int s = (int)(idx % n);
+    int64_t j = idx / n;
+    T *w = W + j * ld + s;
+    *w = (s % stride == 0) ? (T)(scale * (double)(*w)) : (T)0;
+}
+
+template <typename T>
+void launch_obs_block(cudaStream_t s, int n, int K, T *W, int64_t ld, double scale, int stride)
+{
+    int64_t tot = (int64_t)n * K;
+    k_obs_block<T><<<ceil_div(tot, 256), 256, 0, s>>>(n, K, W, ld, scale, stride);
+}
+
+template void launch_obs_block<double>(cudaStream_t, int, int, double *, int64_t, double, int);
+template void launch_obs_block<float>(cudaStream_t, int, int, float *, int64_t, double, int);

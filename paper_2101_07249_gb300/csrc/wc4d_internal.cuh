@@ -1,0 +1,188 @@
+// Internal declarations of libwc4d (GB300 / sm_103a).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "wc4d.h"
+
+#define WC4D_FFT_MAX_N 8192   // largest power-of-two n handled by the on-chip FFT
+
+// ------------------------------------------------------------------ buffers
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Epilogue of the sweep products.  mode 0: C = alpha*acc + beta*C_old
+// (C_old not read when beta == 0).  mode 1 (adjoint with observations):
+// C = acc + obs(C_old), obs(v)[s] = obs_scale * v[s] on observed points
+// s % obs_stride == 0, zero elsewhere.
+struct Epi {
+    int mode;
+    double alpha, beta;
+    double obs_scale;
+    int obs_stride;
+};
+
+// ------------------------------------------------------------------ context
+struct wc4d_ctx {
+    wc4d_problem prob{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    int64_t nA = 0;
+    int64_t nobs = 0;
+    int obs_per_time = 0;
+    std::vector<int> obs_times;     // observed time indices
+
+    // linear model: nM blocks of n*n (1 when shared), FP64 master + derived
+    int nM = 0;
+    bool have_M = false;
+    DevBuf M64, MT64, M32, MT32;
+    bool have_M32 = false;
+
+    // Lorenz-96: nonlinear states (N*steps+1) x n and the four RK4 stage
+    // states of every step, stages[(4 g + i) n + j] (i = 0 is the state itself)
+    DevBuf traj64, stage64, stage32;
+    bool have_traj = false;
+
+    // covariance square roots: [0] = B, [1] = Q
+    bool have_cov[2] = {false, false};
+    bool fft = false;               // n is a power of two <= WC4D_FFT_MAX_N
+    int logn = 0;
+    DevBuf spec64[2], spec32[2];    // FFT path: sqrt spectrum in bit-reversed order, / n
+    DevBuf row64[2], row32[2];      // direct path: first row of the square root
+    DevBuf tw64, tw32;              // FFT twiddles e^{-2 pi i j / n}, j < n/2
+    DevBuf cosn;                    // cos/sin table e^{2 pi i j/n}, j < n (set-up DFTs)
+
+    // observations and right-hand side
+    DevBuf d, rhs, Dm12b;
+    bool have_rhs = false;
+
+    // workspaces
+    DevBuf work64, work32;          // sweep workspace nA x K
+    DevBuf blkA, blkB, blkC, blkD;  // nA x m blocks for the eigensolvers
+    DevBuf small0, small1, small2, small3;  // m x m FP64
+    DevBuf part;                    // partial sums
+    DevBuf scal;                    // device scalars (PCG)
+    DevBuf counter;                 // int counters
+    DevBuf pinned;                  // pinned host staging
+
+    // PCG vectors
+    DevBuf pcg64[8], pcg32[8];
+
+    // Ritz pairs
+    int kU = 0;
+    DevBuf U64, U32, theta64, c64, c32;
+    bool have_U32 = false;
+    std::vector<double> theta_host;
+
+    int64_t hvp_count = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+wc4d_status set_err(wc4d_ctx *c, wc4d_status s, const char *fmt, ...);
+wc4d_status ensure(wc4d_ctx *c, DevBuf &b, size_t bytes);
+wc4d_status check_launch(wc4d_ctx *c, const char *what);
+void free_buf(DevBuf &b);
+
+#define WC4D_TRY(expr)                              \
+    do {                                            \
+        wc4d_status _s = (expr);                    \
+        if (_s != WC4D_OK) return _s;               \
+    } while (0)
+
+#define WC4D_CUDA(c, call)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (call);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            return set_err((c), WC4D_ECUDA, "%s: %s", #call, cudaGetErrorString(_e));   \
+    } while (0)
+
+static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ kernels (launchers)
+// set-up
+void launch_gaussian(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, int64_t ld, double *G);
+void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, float2 *tw32);
+void launch_corr_row(cudaStream_t s, int n, int kind, double L, double var, double *row);
+void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, const double *row, const double2 *tab,
+                     double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32);
+void launch_advdiff_column(cudaStream_t s, int n, double kappa, double c, double dt, int steps,
+                           const double2 *tab, double2 *sym_tmp, double *col);
+void launch_expand_circulant(cudaStream_t s, int n, const double *col, double *M, double *MT);
+void launch_convert_f64_f32(cudaStream_t s, int64_t count, const double *a, float *b);
+void launch_convert_f32_f64(cudaStream_t s, int64_t count, const float *a, double *b);
+void launch_transpose_f64(cudaStream_t s, int n, const double *A, double *AT);
+
+// sweeps
+template <typename T>
+void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy,
+                      const T *addX, int64_t ld_add, bool fft, const T *specB, const T *specQ,
+                      const T *rowB, const T *rowQ, const void *tw);
+template <typename T>
+void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
+                       const Epi &e);
+template <typename T>
+void launch_obs_block(cudaStream_t s, int n, int K, T *W, int64_t ld, double scale, int stride);
+
+// generic products: C(i,j) = epi(sum_k A(i,k) B(k,j)), A(i,k) = A[i*sam + k*sak],
+// B(k,j) = B[k + j*ldb], C column-major ldc.
+template <typename T>
+void launch_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, int64_t sak,
+                 const T *B, int64_t ldb, T *C, int64_t ldc, const Epi &e);
+
+// linear algebra
+template <typename T>
+void launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
+                int64_t ldb, double *part, int *splits_out, double *C);
+void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *info);
+void launch_trinv_upper(cudaStream_t s, int m, const double *R, double *Rinv);
+void launch_jacobi_init(cudaStream_t s, int m, int mp, const double *S, double *X, double *V);
+void launch_jacobi_round(cudaStream_t s, int mp, double *X, double *V, int round, double tol, int *rot);
+void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const double *V, double *w, double *Vout);
+void launch_rrt(cudaStream_t s, int m, const double *R, double *RT);
+void launch_symmetrize(cudaStream_t s, int m, double *S);
+void launch_scale_cols(cudaStream_t s, int64_t rows, int m, double *A, int64_t lda, const double *w, int inv_sqrt);
+template <typename T>
+void launch_utv(cudaStream_t s, int num_sms, int64_t nA, int k, const T *U, const T *v, double *part, int *splits);
+template <typename T>
+void launch_lmp_combine(cudaStream_t s, int64_t nA, int k, const T *U, const double *part, int splits,
+                        const double *cvec, double coef, const T *v, T *y, const T *add, const double *beta_dev,
+                        const int *skip);
+void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c);
+
+// PCG vector kernels
+template <typename T>
+void launch_dot_partial(cudaStream_t s, int grid, int64_t n, const T *a, const T *b, double *part);
+template <typename T>
+void launch_pcg_xr(cudaStream_t s, int grid, int64_t n, const double *scal, T *x, T *r, const T *p, const T *q,
+                   double *part);
+template <typename T>
+void launch_pcg_rh(cudaStream_t s, int grid, int64_t n, const double *scal, T *rh, const T *t, double *part);
+template <typename T>
+void launch_pcg_p(cudaStream_t s, int grid, int64_t n, const double *scal, T *p, const T *t);
+void launch_pcg_alpha(cudaStream_t s, int grid, const double *part, double *scal, int *flags);
+void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
+                     int *flags, double tol, double *qcf_drop, int it);
+void launch_pcg_init(cudaStream_t s, int grid, const double *part_b, const double *part_rh, double *scal,
+                     int *flags);
+template <typename T>
+void launch_copy(cudaStream_t s, int64_t n, const T *a, T *b);
+template <typename T>
+void launch_axpby(cudaStream_t s, int64_t n, double alpha, const T *x, double beta, T *y);
+void launch_sub_f64(cudaStream_t s, int64_t n, const double *a, const double *b, double *out);
+void launch_add_f32_to_f64(cudaStream_t s, int64_t n, const float *a, double *b);
+
+// Lorenz-96 sweeps (one CTA per probe column, state kept on chip)
+template <typename T>
+void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
+                          int64_t ld);
+template <typename T>
+void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
+                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride);
+void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages);

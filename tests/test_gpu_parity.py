@@ -1,0 +1,343 @@
+"""Parity of the CUDA library (through the C-ABI) against the FP64 oracle on
+the same seeded inputs, at sizes the oracle finishes in seconds: several
+tiles and ragged tails, the direct (n = 100) and FFT (n = 128, 64) circulant
+paths, the dense advection-diffusion and the Lorenz-96 models.
+
+Tolerances: FP64 path 1e-10 relative on solutions and Ritz values (1e-12 on
+single operator products); mixed path relative residual <= 1e-6 and solution
+within 1e-5 of the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_07249_gb300 import inputs
+from problems import oracle_problem
+
+torch = pytest.importorskip("torch")
+w = pytest.importorskip("paper_2101_07249_gb300")
+pytestmark = pytest.mark.gpu
+
+AD_DIRECT = inputs.TINY                                                     # n = 100: direct circulant
+AD_FFT = inputs.scaled(inputs.TINY, n=128, N=6, k=12, l=4, obs_stride=6)    # n = 128: FFT path
+L96S = inputs.L96.replace(name="l96_n64_N4", n=64, N=4, steps=3, obs_stride=4, k=8, l=4)
+CASES = {"ad_direct": AD_DIRECT, "ad_fft": AD_FFT, "l96": L96S}
+
+
+def dev(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+_cache = {}
+
+
+def setup(name):
+    if name not in _cache:
+        cfg = CASES[name]
+        tw = inputs.twin(cfg)
+        S = w.Solver(cfg, tw)
+        p = oracle_problem(cfg, mode="stepping", xb=tw.xb)
+        _cache[name] = (cfg, S, p, tw)
+    return _cache[name]
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def colrel(A, B):
+    return max(np.linalg.norm(A[j] - B[j]) / np.linalg.norm(B[j]) for j in range(B.shape[0]))
+
+
+# ------------------------------------------------------------------ set-up pieces
+def test_gaussian_matches_oracle():
+    cfg, S, _, _ = setup("ad_direct")
+    rows, cols = 1001, 3
+    G = torch.zeros(cols, rows, dtype=torch.float64, device="cuda")
+    w.wc4d_gaussian(S.ctx, 12345, rows, cols, rows, G)
+    ref = oracle.gaussian(12345, rows, cols)
+    assert np.abs(host(G) - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_propagator_matches_stepping():
+    cfg, S, _, _ = setup("ad_fft")
+    M = torch.zeros(cfg.n, cfg.n, dtype=torch.float64, device="cuda")
+    w.wc4d_get_propagator(S.ctx, 0, M)
+    ref = oracle.advdiff_dense(cfg.n, cfg.kappa, cfg.u, cfg.dt, cfg.steps)
+    assert np.abs(host(M) - ref).max() < 1e-13
+    w.wc4d_get_propagator(S.ctx, cfg.N - 1, M)
+    assert np.abs(host(M) - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_dsqrt_matches_oracle(name):
+    cfg, S, p, _ = setup(name)
+    X = inputs.block(1, cfg.nA, 5)
+    Y = torch.zeros(5, cfg.nA, dtype=torch.float64, device="cuda")
+    w.wc4d_apply_dsqrt(S.ctx, dev(X), Y, 5, cfg.nA)
+    assert colrel(host(Y), oracle.Dsqrt(p, X)) < 1e-12
+    Y32 = torch.zeros(5, cfg.nA, dtype=torch.float32, device="cuda")
+    w.wc4d_apply_dsqrt(S.ctx, dev(X, torch.float32), Y32, 5, cfg.nA, w.MIXED)
+    assert colrel(host(Y32), oracle.Dsqrt(p, X)) < 1e-5
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_linv_and_linvT_match_oracle(name):
+    cfg, S, p, _ = setup(name)
+    X = inputs.block(2, cfg.nA, 3)
+    W = dev(X)
+    w.wc4d_apply_linv(S.ctx, W, 3, cfg.nA)
+    assert colrel(host(W), oracle.Linv(p, X)) < 1e-12
+    W = dev(X)
+    w.wc4d_apply_linvT(S.ctx, W, 3, cfg.nA)
+    assert colrel(host(W), oracle.LinvT(p, X)) < 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("K", [1, 7, 20, 65])
+def test_hvp_fp64_matches_oracle(name, K):
+    cfg, S, p, _ = setup(name)
+    X = inputs.block(3 + K, cfg.nA, K)
+    Y = torch.zeros(K, cfg.nA, dtype=torch.float64, device="cuda")
+    w.wc4d_hvp(S.ctx, dev(X), Y, K, cfg.nA, w.FP64)
+    assert colrel(host(Y), oracle.hvp(p, X)) < 1e-12
+
+
+def test_hvp_ragged_257_columns():
+    cfg, S, p, _ = setup("ad_fft")
+    K = 257
+    X = inputs.block(9, cfg.nA, K)
+    Y = torch.zeros(K, cfg.nA, dtype=torch.float64, device="cuda")
+    w.wc4d_hvp(S.ctx, dev(X), Y, K, cfg.nA, w.FP64)
+    ref = oracle.hvp(p, X)
+    assert colrel(host(Y), ref) < 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("K", [1, 20])
+def test_hvp_mixed_matches_oracle(name, K):
+    cfg, S, p, _ = setup(name)
+    X = inputs.block(30 + K, cfg.nA, K)
+    Y = torch.zeros(K, cfg.nA, dtype=torch.float32, device="cuda")
+    w.wc4d_hvp(S.ctx, dev(X, torch.float32), Y, K, cfg.nA, w.MIXED)
+    assert colrel(host(Y), oracle.hvp(p, X)) < 2e-5
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_matches_oracle(name):
+    cfg, S, p, tw = setup(name)
+    r = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    w.wc4d_get_rhs(S.ctx, r)
+    d = oracle.innovation(p, tw.xb, tw.y)
+    assert relerr(host(r), oracle.rhs(p, d)) < 1e-12
+    assert w.wc4d_nobs(S.ctx) == cfg.nobs == p.nobs
+
+
+# ------------------------------------------------------------------ small dense LA
+@pytest.mark.parametrize("m", [1, 6, 15, 33])
+def test_cholqr2_matches_householder(m):
+    cfg, S, _, _ = setup("ad_direct")
+    g = np.random.default_rng(m)
+    A = g.standard_normal((m, 600)) * np.logspace(0, 2, m)[:, None]
+    Y = dev(A)
+    R = w.wc4d_orthonormalize(S.ctx, Y, 600, m, 600)
+    Qo, Ro = oracle.householder_qr(A)
+    assert np.abs(host(Y) @ host(Y).T - np.eye(m)).max() < 1e-13
+    assert relerr(R, Ro) < 1e-11
+    assert np.abs(host(Y) - Qo).max() < 1e-9
+
+
+@pytest.mark.parametrize("m", [1, 2, 15, 40, 77])
+def test_symeig_matches_jacobi(m):
+    cfg, S, _, _ = setup("ad_direct")
+    g = np.random.default_rng(100 + m)
+    X = g.standard_normal((m, m))
+    A = X @ X.T + np.eye(m)
+    V = torch.zeros(m, m, dtype=torch.float64, device="cuda")
+    wv = w.wc4d_symeig(S.ctx, m, dev(A.T), V)       # column-major = transpose of row-major
+    wo, Vo, _ = oracle.jacobi_eig(A)
+    assert np.allclose(wv, wo, rtol=1e-12, atol=1e-12)
+    Vg = host(V).T                                   # columns = eigenvectors
+    assert np.abs(A @ Vg - Vg * wv).max() < 1e-11 * wo[0]
+
+
+# ------------------------------------------------------------------ eigensolvers
+def _lmp_dense(U, th):
+    c = 1.0 - 1.0 / np.sqrt(th)
+    return np.eye(U.shape[1]) - (U.T * c) @ U
+
+
+def _check_pairs(S, cfg, U_or, th_or, k, tol_theta=1e-10):
+    U = torch.zeros(k, cfg.nA, dtype=torch.float64, device="cuda")
+    th = w.wc4d_get_ritz(S.ctx, U, k)
+    assert np.allclose(th, th_or, rtol=tol_theta), (th[:4], th_or[:4])
+    # sign-invariant comparison: C v for random vectors
+    v = inputs.block(77, cfg.nA, 3)
+    Cg, Co = _lmp_dense(host(U), th), _lmp_dense(U_or, th_or)
+    assert np.abs(v @ Cg - v @ Co).max() < 1e-8 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
+def test_sketch_fp64_matches_oracle(name, method):
+    cfg, S, p, _ = setup(name)
+    k, m = cfg.k, cfg.K
+    G = inputs.probes(5, cfg.nA, m)
+    w.wc4d_sketch(S.ctx, w.METHODS[method], k, m - k, cfg.q_power, 0, dev(G), w.FP64)
+    if method == "revd":
+        Uo, tho = oracle.revd(p, k, G, q=cfg.q_power)
+    elif method == "nystrom":
+        Uo, tho = oracle.nystrom(p, k, G)
+    else:
+        Uo, tho = oracle.ritzit(p, k, G)
+    _check_pairs(S, cfg, Uo, tho, k)
+
+
+def test_sketch_internal_probes_match_oracle_philox():
+    cfg, S, p, _ = setup("ad_direct")
+    k, m = cfg.k, cfg.K
+    w.wc4d_sketch(S.ctx, w.REVD, k, m - k, 1, 2024, None, w.FP64)
+    G = oracle.gaussian(2024, cfg.nA, m)
+    Uo, tho = oracle.revd(p, k, G, q=1)
+    _check_pairs(S, cfg, Uo, tho, k)
+
+
+def test_products_with_A_per_method():
+    cfg, S, _, _ = setup("ad_direct")
+    for method, q, expect in (("revd", 0, 2), ("revd", 1, 3), ("nystrom", 0, 2), ("ritzit", 0, 1)):
+        w.wc4d_hvp_count(S.ctx, reset=True)
+        w.wc4d_sketch(S.ctx, w.METHODS[method], cfg.k, cfg.l, q, 3, None, w.FP64)
+        assert w.wc4d_hvp_count(S.ctx) == expect, method
+
+
+def test_lmp_apply_matches_oracle():
+    cfg, S, p, _ = setup("ad_fft")
+    G = inputs.probes(6, cfg.nA, cfg.K)
+    Uo, tho = oracle.nystrom(p, cfg.k, G)
+    w.wc4d_set_ritz(S.ctx, cfg.k, dev(Uo), tho)
+    v = inputs.block(8, cfg.nA, 1)[0]
+    y = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    w.wc4d_lmp_apply(S.ctx, dev(v), y, 0)
+    assert relerr(host(y), oracle.lmp_apply(Uo, tho, v)) < 1e-13
+    w.wc4d_lmp_apply(S.ctx, dev(v), y, 1)
+    assert relerr(host(y), oracle.lmp_apply(Uo, tho, v, transpose=True)) < 1e-13
+
+
+# ------------------------------------------------------------------ PCG
+@pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
+@pytest.mark.parametrize("method", ["none", "revd", "nystrom", "ritzit"])
+def test_pcg_fp64_matches_oracle(name, method):
+    """Same probes, same LMP construction, PCG from x_0 = 0: iteration counts
+    to 1e-6 agree within one, and the iterates after the oracle's count agree
+    to 1e-10."""
+    cfg, S, p, tw = setup(name)
+    d = oracle.innovation(p, tw.xb, tw.y)
+    b = oracle.rhs(p, d)
+    k = cfg.k
+    G = inputs.probes(11, cfg.nA, cfg.K)
+    if method == "none":
+        Uo = tho = None
+        w.wc4d_set_ritz(S.ctx, 0, None, np.zeros(0))
+        use = 0
+    else:
+        w.wc4d_sketch(S.ctx, w.METHODS[method], k, cfg.l, cfg.q_power, 0, dev(G), w.FP64)
+        fn = {"revd": lambda: oracle.revd(p, k, G, q=cfg.q_power), "nystrom": lambda: oracle.nystrom(p, k, G),
+              "ritzit": lambda: oracle.ritzit(p, k, G)}[method]
+        Uo, tho = fn()
+        use = 1
+    ro = oracle.pcg(p, b, Uo, tho, tol=1e-6)
+    assert ro["status"] == 0
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    it, rel, qcf, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, 0, w.FP64, qcf=True)
+    assert abs(it - ro["iters"]) <= 1
+    assert rel <= 1e-6
+    it2, _, qcf2, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, ro["iters"], w.FP64, qcf=True)
+    assert it2 == ro["iters"]
+    assert relerr(host(x), ro["x"]) < 1e-10
+    assert np.allclose(qcf2, ro["qcf_drop"], rtol=1e-8)
+
+
+@pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
+@pytest.mark.parametrize("method", ["revd", "ritzit"])
+def test_pcg_mixed_meets_tolerance(name, method):
+    cfg, S, p, tw = setup(name)
+    d = oracle.innovation(p, tw.xb, tw.y)
+    b = oracle.rhs(p, d)
+    xs = oracle.pcg(p, b, tol=1e-12, maxit=5000)["x"]
+    w.wc4d_sketch(S.ctx, w.METHODS[method], cfg.k, cfg.l, cfg.q_power, 17, None, w.MIXED)
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 1, 0, w.MIXED)
+    assert rel <= 1e-6
+    assert relerr(host(x), xs) <= 1e-5
+    # the oracle's own residual of the GPU solution
+    r = b - oracle.hvp(p, host(x)[None, :])[0]
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-6
+
+
+def test_inner_loop_entry_point():
+    cfg, S, p, tw = setup("ad_direct")
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    it, rel = w.wc4d_inner_loop(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 5, 1e-6, 5000, w.FP64, x)
+    assert rel <= 1e-6 and it > 0
+    d = oracle.innovation(p, tw.xb, tw.y)
+    b = oracle.rhs(p, d)
+    r = b - oracle.hvp(p, host(x)[None, :])[0]
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
+
+
+# ------------------------------------------------------------------ edge cases and errors
+def test_no_observations_gives_identity():
+    cfg = inputs.scaled(inputs.TINY, n=32, N=2, k=3, l=2, obs_stride=4, obs_t0=9)
+    tw = inputs.twin(cfg.replace(obs_t0=1))
+    S = w.Solver(cfg)
+    assert w.wc4d_nobs(S.ctx) == 0
+    w.wc4d_set_background_obs(S.ctx, tw.xb, np.zeros(0))
+    X = inputs.block(1, cfg.nA, 4)
+    Y = torch.zeros(4, cfg.nA, dtype=torch.float64, device="cuda")
+    w.wc4d_hvp(S.ctx, dev(X), Y, 4, cfg.nA)
+    assert np.array_equal(host(Y), X)            # A = I exactly
+    x = torch.ones(cfg.nA, dtype=torch.float64, device="cuda")
+    it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 100, 0, 0, w.FP64)
+    assert it == 0 and rel == 0.0 and float(x.abs().max()) == 0.0
+
+
+def test_single_subwindow_and_odd_grid():
+    cfg = inputs.scaled(inputs.TINY, n=99, N=1, k=3, l=2, obs_stride=7)
+    tw = inputs.twin(cfg)
+    S = w.Solver(cfg, tw)
+    p = oracle_problem(cfg, xb=tw.xb)
+    X = inputs.block(4, cfg.nA, 3)
+    Y = torch.zeros(3, cfg.nA, dtype=torch.float64, device="cuda")
+    w.wc4d_hvp(S.ctx, dev(X), Y, 3, cfg.nA)
+    assert colrel(host(Y), oracle.hvp(p, X)) < 1e-12
+    th = w.wc4d_sketch(S.ctx, w.RITZIT, 3, 2, 0, 1, None, w.FP64)
+    _, tho = oracle.ritzit(p, 3, oracle.gaussian(1, cfg.nA, 5))
+    assert np.allclose(th, tho, rtol=1e-10)
+
+
+def test_invalid_arguments_are_rejected():
+    cfg, S, _, _ = setup("ad_direct")
+    bad = w.Problem()
+    bad.n, bad.N, bad.sigma_o2, bad.obs_stride = 1, 5, 0.01, 1
+    with pytest.raises(w.WC4DError):
+        w.wc4d_create(bad)
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    with pytest.raises(w.WC4DError) as e:
+        w.wc4d_hvp(S.ctx, x, x, 0, cfg.nA)
+    assert e.value.status == w.EINVAL
+    with pytest.raises(w.WC4DError):
+        w.wc4d_sketch(S.ctx, w.REVD, 0, 1, 0, 0, None)
+    fresh = w.Solver(cfg)              # no background / observations yet
+    with pytest.raises(w.WC4DError) as e:
+        w.wc4d_pcg(fresh.ctx, x)
+    assert e.value.status == w.ESTATE
+
+
+def test_maxit_reports_no_convergence():
+    cfg, S, _, _ = setup("ad_direct")
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    it, rel, _, st = w.wc4d_pcg(S.ctx, x, 1e-12, 2, 0, 0, w.FP64, raise_on_noconv=False)
+    assert st == w.ENOCONV and it == 2 and rel > 1e-12

@@ -1,5 +1,5 @@
 """Pins of the oracle's dense linear algebra, the three randomised
-eigensolvers (Alg. 3-5), the spectral LMP (eq. 12-14) and PCG (Alg. 1)
+eigensolvers (Alg. 3-5), the spectral LMP (eq. 14-16) and PCG (Alg. 1)
 against numpy/scipy, subspace definitions and the properties the paper
 states."""
 import json
@@ -178,9 +178,9 @@ def test_lmp_factor_and_exact_eigenpairs(tiny):
     Cd = np.stack([oracle.lmp_apply(Ut, th, e) for e in E], axis=1)
     CTd = np.stack([oracle.lmp_apply(Ut, th, e, transpose=True) for e in E], axis=1)
     assert np.allclose(CTd, Cd.T, atol=1e-14)
-    Psp = E - (U * (1.0 - 1.0 / th)) @ U.T                     # eq. 13
+    Psp = E - (U * (1.0 - 1.0 / th)) @ U.T                     # eq. 15
     assert np.allclose(Cd @ Cd.T, Psp, atol=1e-12)
-    S = U                                                      # eq. 12 with S = V
+    S = U                                                      # eq. 14 with S = V
     SAS = S.T @ A @ S
     Pk = (E - S @ np.linalg.solve(SAS, S.T @ A)) @ (E - A @ S @ np.linalg.solve(SAS, S.T)) \
         + S @ np.linalg.solve(SAS, S.T)
@@ -230,7 +230,7 @@ def test_pcg_matches_dense_solve_and_qcf(tiny):
 
 
 def test_pcg_error_bound_eq10(tiny):
-    """|e_i|_A / |e_0|_A <= 2 ((sqrt k - 1)/(sqrt k + 1))^i (eq. 10)."""
+    """|e_i|_A / |e_0|_A <= 2 ((sqrt k - 1)/(sqrt k + 1))^i (eq. 12)."""
     p, A, lam, _ = tiny
     _, b = _rhs(p, CFG)
     xs = np.linalg.solve(A, b)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's forcing-formulation operators (eq. 5, eq. 8) against
+"""Pins of the oracle's forcing-formulation operators (eq. 5, eq. 10) against
 their definitions built densely in numpy, adjoint identities and the
 spectrum of A."""
 import numpy as np
@@ -71,7 +71,7 @@ def test_Linv_adjoint_and_inverse(pi):
 
 @pytest.mark.parametrize("pi", [0, 1, 2])
 def test_A_matches_dense_definition(pi):
-    """A = I + D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2} (eq. 8), with L^{-1}
+    """A = I + D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2} (eq. 10), with L^{-1}
     obtained by dense inversion of L (not by the recursion)."""
     p = _problems()[pi]
     _, L, D, H = _dense_parts(p)
@@ -119,7 +119,7 @@ def test_spectrum_of_A_paper_advection_size():
 
 @pytest.mark.parametrize("pi", [1, 2])
 def test_rhs_innovation_and_qcf(pi):
-    """rhs = D^{1/2} L^{-T} H^T R^{-1} d (eq. 8, b = 0); d = y - H x;
+    """rhs = D^{1/2} L^{-T} H^T R^{-1} d (eq. 10, b = 0); d = y - H x;
     J (eq. 4) = 1/2 x^T A x - rhs^T x + J(0)."""
     p = _problems()[pi]
     Ms, L, D, H = _dense_parts(p)
