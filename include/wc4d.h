@@ -205,6 +205,18 @@ wc4d_status wc4d_apply_linv(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int32
 wc4d_status wc4d_apply_linvT(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int32_t precision);
 /* Copy the FP64 propagator of subwindow t (dense model) to device memory. */
 wc4d_status wc4d_get_propagator(wc4d_ctx *ctx, int32_t t, double *M_device);
+/* Kernel launches issued by the library in this process (all contexts). */
+int64_t     wc4d_launch_count(int32_t reset);
+/* Optional CUDA-event timing of kernel classes on the context's stream:
+ * wc4d_profile(ctx, 1) clears the log and starts recording an event pair
+ * around every launch group of the classes below; wc4d_profile_read
+ * synchronises and returns the summed device time (ms) and the number of
+ * timed groups of one class.  Classes: 0 sweep GEMV (one probe column),
+ * 1 sweep SIMT GEMM, 2 sweep tensor-core GEMM, 3 D^{1/2} circulant,
+ * 4 LMP application, 5 Gram products, 6 other dense LA, 7 Lorenz-96
+ * tangent-linear sweep, 8 Lorenz-96 adjoint sweep, 9 PCG vector kernels. */
+wc4d_status wc4d_profile(wc4d_ctx *ctx, int32_t enable);
+wc4d_status wc4d_profile_read(wc4d_ctx *ctx, int32_t cls, double *total_ms, int64_t *launch_groups);
 /* Products with A issued so far (block products count once). */
 int64_t     wc4d_hvp_count(wc4d_ctx *ctx, int32_t reset);
 

@@ -78,7 +78,11 @@ _SIGS = {
     "wc4d_apply_linv": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_apply_linvT": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_get_propagator": (C.c_int, [_V, C.c_int32, _V]),
+    "wc4d_launch_count": (C.c_int64, [C.c_int32]),
+    "wc4d_profile": (C.c_int, [_V, C.c_int32]),
+    "wc4d_profile_read": (C.c_int, [_V, C.c_int32, _D, C.POINTER(C.c_int64)]),
 }
+PROF_CLASSES = ("gemv", "gemm", "tc_gemm", "circulant", "lmp", "gram", "la", "l96_tlm", "l96_adj", "pcg_vec")
 EXPORTS = tuple(_SIGS)
 
 _lock = threading.Lock()
@@ -279,6 +283,22 @@ def wc4d_apply_linvT(ctx, W, K, ld, precision=FP64):
 
 def wc4d_get_propagator(ctx, t, M):
     _check(ctx, load().wc4d_get_propagator(ctx, int(t), _ptr(M)))
+
+
+def wc4d_launch_count(reset=False):
+    return int(load().wc4d_launch_count(1 if reset else 0))
+
+
+def wc4d_profile(ctx, enable=True):
+    _check(ctx, load().wc4d_profile(ctx, 1 if enable else 0))
+
+
+def wc4d_profile_read(ctx, cls):
+    """(total device ms, number of timed launch groups) of one kernel class."""
+    ms = C.c_double(0.0)
+    n = C.c_int64(0)
+    _check(ctx, load().wc4d_profile_read(ctx, int(cls), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 def wc4d_hvp_count(ctx, reset=False):

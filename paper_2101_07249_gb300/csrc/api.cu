@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 
 #include "wc4d_internal.cuh"
 
@@ -72,6 +73,31 @@ wc4d_status check_launch(wc4d_ctx *c, const char *what)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(c, WC4D_ECUDA, "%s: %s", what, cudaGetErrorString(e));
     return WC4D_OK;
+}
+
+static std::atomic<int64_t> g_launches{0};
+void wc4d_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(wc4d_ctx *ctx, int pid) : c(ctx), id(pid), slot(-1)
+{
+    if (!c || !c->prof_on) return;
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+        for (int i = 0; i < 256; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+            c->ev_pool.push_back(e);
+        }
+    }
+    slot = (int)c->prof_log.size();
+    ProfEntry pe{id, c->ev_pool[c->ev_used], c->ev_pool[c->ev_used + 1]};
+    c->ev_used += 2;
+    c->prof_log.push_back(pe);
+    cudaEventRecord(pe.e0, c->stream);
+}
+
+ProfScope::~ProfScope()
+{
+    if (slot >= 0) cudaEventRecord(c->prof_log[slot].e1, c->stream);
 }
 
 static wc4d_status sync(wc4d_ctx *c, const char *what)
@@ -192,6 +218,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -205,6 +232,38 @@ extern "C" wc4d_status wc4d_set_stream(wc4d_ctx *c, void *stream)
 }
 
 extern "C" int64_t wc4d_nobs(const wc4d_ctx *c) { return c ? c->nobs : -1; }
+
+extern "C" int64_t wc4d_launch_count(int32_t reset)
+{
+    return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+extern "C" wc4d_status wc4d_profile(wc4d_ctx *c, int32_t enable)
+{
+    if (!c) return WC4D_EINVAL;
+    WC4D_TRY(sync(c, "profile"));
+    c->prof_log.clear();
+    c->ev_used = 0;
+    c->prof_on = enable != 0;
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_profile_read(wc4d_ctx *c, int32_t cls, double *total_ms, int64_t *launch_groups)
+{
+    if (!c || cls < 0 || cls >= PROF_N) return WC4D_EINVAL;
+    WC4D_TRY(sync(c, "profile_read"));
+    double ms = 0.0;
+    int64_t cnt = 0;
+    for (const ProfEntry &e : c->prof_log) {
+        if (e.id != cls) continue;
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, e.e0, e.e1) == cudaSuccess) { ms += t; ++cnt; }
+        else cudaGetLastError();
+    }
+    if (total_ms) *total_ms = ms;
+    if (launch_groups) *launch_groups = cnt;
+    return WC4D_OK;
+}
 
 extern "C" int64_t wc4d_hvp_count(wc4d_ctx *c, int32_t reset)
 {
@@ -368,6 +427,7 @@ template <typename T>
 static wc4d_status apply_circ(wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy, const T *addX,
                               int64_t ld_add)
 {
+    ProfScope ps(c, PROF_CIRC);
     launch_circulant<T>(c->stream, c, K, X, ldx, Y, ldy, addX, ld_add, c->fft, Ops<T>::spec(c, 0),
                         Ops<T>::spec(c, 1), Ops<T>::row(c, 0), Ops<T>::row(c, 1), Ops<T>::tw(c));
     return check_launch(c, "circulant");
@@ -379,16 +439,20 @@ static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allo
 {
     const int n = c->prob.n, N = c->prob.N;
     if (c->prob.model == WC4D_MODEL_L96) {
+        ProfScope ps(c, PROF_L96_TLM);
         launch_l96_tlm_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld);
         return check_launch(c, "l96 tlm sweep");
     }
     if constexpr (sizeof(T) == 4) {
+        ProfScope ps(c, PROF_TC);
         if (allow_tc && tc_sweep_forward(c, K, (float *)W, ld)) return check_launch(c, "tc forward sweep");
     }
     Epi e{0, 1.0, 1.0, 0.0, 1};
-    for (int t = 0; t < N; ++t)
+    for (int t = 0; t < N; ++t) {
+        ProfScope ps(c, K == 1 ? PROF_GEMV : PROF_GEMM);
         launch_sweep_gemm<T>(c->stream, n, K, Ops<T>::M(c, t), W + (int64_t)t * n, ld, W + (int64_t)(t + 1) * n, ld,
                              e);
+    }
     return check_launch(c, "forward sweep");
 }
 
@@ -398,16 +462,19 @@ static wc4d_status adjoint_obs_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool 
 {
     const int n = c->prob.n, N = c->prob.N;
     if (c->prob.model == WC4D_MODEL_L96) {
+        ProfScope ps(c, PROF_L96_ADJ);
         launch_l96_adj_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld, 1,
                                 1.0 / c->prob.sigma_o2, c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride);
         return check_launch(c, "l96 adjoint sweep");
     }
     if constexpr (sizeof(T) == 4) {
+        ProfScope ps(c, PROF_TC);
         if (allow_tc && tc_sweep_adjoint(c, K, (float *)W, ld)) return check_launch(c, "tc adjoint sweep");
     }
     launch_obs_block<T>(c->stream, n, K, W + (int64_t)N * n, ld, obs_scale(c, N), c->prob.obs_stride);
     for (int t = N - 1; t >= 0; --t) {
         Epi e{1, 1.0, 0.0, obs_scale(c, t), c->prob.obs_stride};
+        ProfScope ps(c, K == 1 ? PROF_GEMV : PROF_GEMM);
         launch_sweep_gemm<T>(c->stream, n, K, Ops<T>::MT(c, t), W + (int64_t)(t + 1) * n, ld, W + (int64_t)t * n, ld,
                              e);
     }
@@ -539,17 +606,17 @@ extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, co
     double *dy = P<double>(c->small2);
     if (c->nobs > 0) {
         WC4D_CUDA(c, cudaMemcpyAsync(dy, y, sizeof(double) * c->nobs, cudaMemcpyHostToDevice, c->stream));
-        k_innovation<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
+        WC4D_LAUNCH(k_innovation<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
                                                                      c->prob.obs_tstride, c->prob.obs_stride, n, dy,
-                                                                     xs, P<double>(c->d));
+                                                                     xs, P<double>(c->d)));
     }
     // rhs = D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b)
     double *v = P<double>(c->blkB);
     WC4D_CUDA(c, cudaMemsetAsync(v, 0, sizeof(double) * nA, c->stream));
     if (c->nobs > 0)
-        k_scatter_obs<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
+        WC4D_LAUNCH(k_scatter_obs<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
                                                                       c->prob.obs_tstride, c->prob.obs_stride, n,
-                                                                      P<double>(c->d), 1.0 / c->prob.sigma_o2, v);
+                                                                      P<double>(c->d), 1.0 / c->prob.sigma_o2, v));
     WC4D_TRY(check_launch(c, "innovation"));
     WC4D_TRY(plain_adjoint_sweep<double>(c, 1, v, nA));    // S = L^{-T} H^T R^{-1} d
     double *addb = nullptr;
@@ -593,6 +660,7 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     WC4D_TRY(ensure(c, c->part, part_need));
     int S = 0;
     double *G = P<double>(c->small0);
+    ProfScope ps(c, PROF_GRAM);
     launch_atb<T>(c->stream, c->num_sms, rows, m, m, Y, ld, Y, ld, P<double>(c->part), &S, G);   // G = Y^T Y
     launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));                                // G = R^T R
     double *Rinv = P<double>(c->small1);
@@ -912,6 +980,7 @@ static wc4d_status lmp_apply_impl(wc4d_ctx *c, const T *v, T *y, const int *skip
 {
     const int k = c->kU;
     const int64_t nA = c->nA;
+    ProfScope ps(c, PROF_LMP);
     int splits = ceil_div(nA, 1024);
     WC4D_TRY(ensure(c, c->part, sizeof(double) * (size_t)splits * k + 64));
     launch_utv<T>(c->stream, c->num_sms, nA, k, Ubuf<T>(c), v, P<double>(c->part), &splits);

@@ -166,7 +166,7 @@ void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
                              (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
         attr = true;
     }
-    k_l96_tlm<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld);
+    WC4D_LAUNCH(k_l96_tlm<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld));
 }
 
 template <typename T>
@@ -179,9 +179,9 @@ void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
                              (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
         attr = true;
     }
-    k_l96_adj<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld, obs_mode,
+    WC4D_LAUNCH(k_l96_adj<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld, obs_mode,
                                                                      (T)obs_scale, obs_stride, obs_t0,
-                                                                     obs_tstride > 0 ? obs_tstride : 1);
+                                                                     obs_tstride > 0 ? obs_tstride : 1));
 }
 
 template void launch_l96_tlm_sweep<double>(cudaStream_t, int, int, int, double, const double *, int, double *,
@@ -260,5 +260,5 @@ void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, doub
                              (int)(2 * WC4D_FFT_MAX_N * sizeof(double)));
         attr = true;
     }
-    k_l96_run<<<1, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, nsteps, F, dt, traj, stages);
+    WC4D_LAUNCH(k_l96_run<<<1, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, nsteps, F, dt, traj, stages));
 }

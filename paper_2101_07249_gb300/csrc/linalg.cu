@@ -92,11 +92,11 @@ void launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const
     S = (rows + rps - 1) / rps;
     if (S < 1) S = 1;
     dim3 g(tiles, (unsigned)S);
-    k_atb<T><<<g, 256, 0, s>>>(rows, ma, mb, A, lda, B, ldb, part, rps, ta);
+    WC4D_LAUNCH(k_atb<T><<<g, 256, 0, s>>>(rows, ma, mb, A, lda, B, ldb, part, rps, ta));
     if (splits_out) *splits_out = (int)S;
     if (C) {
         int64_t cnt = (int64_t)ma * mb;
-        k_reduce_part<<<ceil_div(cnt, 256), 256, 0, s>>>((int)S, cnt, part, C);
+        WC4D_LAUNCH(k_reduce_part<<<ceil_div(cnt, 256), 256, 0, s>>>((int)S, cnt, part, C));
     }
 }
 
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_chol_upper(int m, const double *A, dou
 
 void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *info)
 {
-    k_chol_upper<<<1, 1024, 0, s>>>(m, A, R, info);
+    WC4D_LAUNCH(k_chol_upper<<<1, 1024, 0, s>>>(m, A, R, info));
 }
 
 // Inverse of an upper-triangular R (column-major): one thread per column,
@@ -165,7 +165,7 @@ __global__ void k_trinv_upper(int m, const double *R, double *Rinv)
 
 void launch_trinv_upper(cudaStream_t s, int m, const double *R, double *Rinv)
 {
-    k_trinv_upper<<<ceil_div(m, 64), 64, 0, s>>>(m, R, Rinv);
+    WC4D_LAUNCH(k_trinv_upper<<<ceil_div(m, 64), 64, 0, s>>>(m, R, Rinv));
 }
 
 // RT = R^T (m x m column-major).
@@ -179,7 +179,7 @@ __global__ void k_transpose_small(int m, const double *R, double *RT)
 
 void launch_rrt(cudaStream_t s, int m, const double *R, double *RT)
 {
-    k_transpose_small<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, R, RT);
+    WC4D_LAUNCH(k_transpose_small<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, R, RT));
 }
 
 __global__ void k_symmetrize(int m, double *S)
@@ -196,7 +196,7 @@ __global__ void k_symmetrize(int m, double *S)
 
 void launch_symmetrize(cudaStream_t s, int m, double *S)
 {
-    k_symmetrize<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, S);
+    WC4D_LAUNCH(k_symmetrize<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, S));
 }
 
 // A[:, j] *= w_j^{-1/2} (inv_sqrt = 1) or 1/w_j (inv_sqrt = 0).
@@ -212,7 +212,7 @@ __global__ void k_scale_cols(int64_t rows, int m, double *A, int64_t lda, const 
 
 void launch_scale_cols(cudaStream_t s, int64_t rows, int m, double *A, int64_t lda, const double *w, int inv_sqrt)
 {
-    k_scale_cols<<<ceil_div(rows * m, 256), 256, 0, s>>>(rows, m, A, lda, w, inv_sqrt);
+    WC4D_LAUNCH(k_scale_cols<<<ceil_div(rows * m, 256), 256, 0, s>>>(rows, m, A, lda, w, inv_sqrt));
 }
 
 // ----------------------------------------------------------------------------
@@ -233,7 +233,7 @@ __global__ void k_jacobi_init(int m, int mp, const double *S, double *X, double 
 
 void launch_jacobi_init(cudaStream_t s, int m, int mp, const double *S, double *X, double *V)
 {
-    k_jacobi_init<<<ceil_div((int64_t)mp * mp, 256), 256, 0, s>>>(m, mp, S, X, V);
+    WC4D_LAUNCH(k_jacobi_init<<<ceil_div((int64_t)mp * mp, 256), 256, 0, s>>>(m, mp, S, X, V));
 }
 
 __global__ void __launch_bounds__(128) k_jacobi_round(int mp, double *X, double *V, int round, double tol, int *rot)
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(128) k_jacobi_round(int mp, double *X, double 
 
 void launch_jacobi_round(cudaStream_t s, int mp, double *X, double *V, int round, double tol, int *rot)
 {
-    k_jacobi_round<<<mp / 2, 128, 0, s>>>(mp, X, V, round, tol, rot);
+    WC4D_LAUNCH(k_jacobi_round<<<mp / 2, 128, 0, s>>>(mp, X, V, round, tol, rot));
 }
 
 // Column norms, sorted decreasing; Vout[:, rank] = V[0:m, j].
@@ -320,8 +320,8 @@ __global__ void k_sort_cols(int m, int mp, const double *wn, const double *V, do
 void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const double *V, double *w, double *Vout)
 {
     // w is used first as scratch for the unsorted norms (length m) at w + m
-    k_colnorm<<<m, 128, 0, s>>>(m, mp, X, w + m);
-    k_sort_cols<<<m, 128, 0, s>>>(m, mp, w + m, V, w, Vout);
+    WC4D_LAUNCH(k_colnorm<<<m, 128, 0, s>>>(m, mp, X, w + m));
+    WC4D_LAUNCH(k_sort_cols<<<m, 128, 0, s>>>(m, mp, w + m, V, w, Vout));
 }
 
 // ----------------------------------------------------------------------------
@@ -336,7 +336,7 @@ __global__ void k_lmp_coeffs(int k, const double *theta, double *c)
 
 void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c)
 {
-    k_lmp_coeffs<<<ceil_div(k, 128), 128, 0, s>>>(k, theta, c);
+    WC4D_LAUNCH(k_lmp_coeffs<<<ceil_div(k, 128), 128, 0, s>>>(k, theta, c));
 }
 
 constexpr int UTV_ROWS = 1024;
@@ -366,7 +366,7 @@ template <typename T>
 void launch_utv(cudaStream_t s, int num_sms, int64_t nA, int k, const T *U, const T *v, double *part, int *splits)
 {
     int S = ceil_div(nA, UTV_ROWS);
-    k_utv<T><<<S, 256, 0, s>>>(nA, k, U, v, part);
+    WC4D_LAUNCH(k_utv<T><<<S, 256, 0, s>>>(nA, k, U, v, part));
     *splits = S;
 }
 
@@ -406,8 +406,8 @@ void launch_lmp_combine(cudaStream_t s, int64_t nA, int k, const T *U, const dou
 {
     int grid = ceil_div(nA, 256);
     if (grid > 4096) grid = 4096;
-    k_lmp_combine<T><<<grid, 256, (size_t)k * sizeof(double), s>>>(nA, k, U, part, splits, cvec, coef, v, y, add,
-                                                                      beta_dev, skip);
+    WC4D_LAUNCH(k_lmp_combine<T><<<grid, 256, (size_t)k * sizeof(double), s>>>(nA, k, U, part, splits, cvec, coef, v, y, add,
+                                                                      beta_dev, skip));
 }
 
 template void launch_lmp_combine<double>(cudaStream_t, int64_t, int, const double *, const double *, int,
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const T *a, cons
 template <typename T>
 void launch_dot_partial(cudaStream_t s, int grid, int64_t n, const T *a, const T *b, double *part)
 {
-    k_dot_partial<T><<<grid, 256, 0, s>>>(n, a, b, part);
+    WC4D_LAUNCH(k_dot_partial<T><<<grid, 256, 0, s>>>(n, a, b, part));
 }
 
 template void launch_dot_partial<double>(cudaStream_t, int, int64_t, const double *, const double *, double *);
@@ -469,7 +469,7 @@ __global__ void k_pcg_init(int grid, const double *part_b, const double *part_rh
 
 void launch_pcg_init(cudaStream_t s, int grid, const double *part_b, const double *part_rh, double *scal, int *flags)
 {
-    k_pcg_init<<<1, 256, 0, s>>>(grid, part_b, part_rh, scal, flags);
+    WC4D_LAUNCH(k_pcg_init<<<1, 256, 0, s>>>(grid, part_b, part_rh, scal, flags));
 }
 
 __global__ void k_pcg_alpha(int grid, const double *part, double *scal, int *flags)
@@ -491,7 +491,7 @@ __global__ void k_pcg_alpha(int grid, const double *part, double *scal, int *fla
 
 void launch_pcg_alpha(cudaStream_t s, int grid, const double *part, double *scal, int *flags)
 {
-    k_pcg_alpha<<<1, 256, 0, s>>>(grid, part, scal, flags);
+    WC4D_LAUNCH(k_pcg_alpha<<<1, 256, 0, s>>>(grid, part, scal, flags));
 }
 
 // x += alpha p; r -= alpha q; partial |r|^2
@@ -515,7 +515,7 @@ template <typename T>
 void launch_pcg_xr(cudaStream_t s, int grid, int64_t n, const double *scal, T *x, T *r, const T *p, const T *q,
                    double *part)
 {
-    k_pcg_xr<T><<<grid, 256, 0, s>>>(n, scal, x, r, p, q, part);
+    WC4D_LAUNCH(k_pcg_xr<T><<<grid, 256, 0, s>>>(n, scal, x, r, p, q, part));
 }
 
 // rhat -= alpha t; partial rhat^T rhat
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(256) k_pcg_rh(int64_t n, const double *scal, T
 template <typename T>
 void launch_pcg_rh(cudaStream_t s, int grid, int64_t n, const double *scal, T *rh, const T *t, double *part)
 {
-    k_pcg_rh<T><<<grid, 256, 0, s>>>(n, scal, rh, t, part);
+    WC4D_LAUNCH(k_pcg_rh<T><<<grid, 256, 0, s>>>(n, scal, rh, t, part));
 }
 
 __global__ void k_pcg_beta(int grid, const double *part_rh, const double *part_r, double *scal, int *flags,
@@ -565,7 +565,7 @@ __global__ void k_pcg_beta(int grid, const double *part_rh, const double *part_r
 void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
                      int *flags, double tol, double *qcf_drop, int it)
 {
-    k_pcg_beta<<<1, 256, 0, s>>>(grid, part_rh, part_r, scal, flags, tol, qcf_drop, it);
+    WC4D_LAUNCH(k_pcg_beta<<<1, 256, 0, s>>>(grid, part_rh, part_r, scal, flags, tol, qcf_drop, it));
 }
 
 // p = t + beta p
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(256) k_pcg_p(int64_t n, const double *scal, T 
 template <typename T>
 void launch_pcg_p(cudaStream_t s, int grid, int64_t n, const double *scal, T *p, const T *t)
 {
-    k_pcg_p<T><<<grid, 256, 0, s>>>(n, scal, p, t);
+    WC4D_LAUNCH(k_pcg_p<T><<<grid, 256, 0, s>>>(n, scal, p, t));
 }
 
 template void launch_pcg_xr<double>(cudaStream_t, int, int64_t, const double *, double *, double *, const double *,
@@ -602,7 +602,7 @@ __global__ void k_copy(int64_t n, const T *a, T *b)
 template <typename T>
 void launch_copy(cudaStream_t s, int64_t n, const T *a, T *b)
 {
-    if (n > 0) k_copy<T><<<ceil_div(n, 256), 256, 0, s>>>(n, a, b);
+    if (n > 0) WC4D_LAUNCH(k_copy<T><<<ceil_div(n, 256), 256, 0, s>>>(n, a, b));
 }
 
 template void launch_copy<double>(cudaStream_t, int64_t, const double *, double *);
@@ -619,7 +619,7 @@ __global__ void k_axpby(int64_t n, double alpha, const T *x, double beta, T *y)
 template <typename T>
 void launch_axpby(cudaStream_t s, int64_t n, double alpha, const T *x, double beta, T *y)
 {
-    if (n > 0) k_axpby<T><<<ceil_div(n, 256), 256, 0, s>>>(n, alpha, x, beta, y);
+    if (n > 0) WC4D_LAUNCH(k_axpby<T><<<ceil_div(n, 256), 256, 0, s>>>(n, alpha, x, beta, y));
 }
 
 template void launch_axpby<double>(cudaStream_t, int64_t, double, const double *, double, double *);
@@ -633,7 +633,7 @@ __global__ void k_sub_f64(int64_t n, const double *a, const double *b, double *o
 
 void launch_sub_f64(cudaStream_t s, int64_t n, const double *a, const double *b, double *out)
 {
-    if (n > 0) k_sub_f64<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b, out);
+    if (n > 0) WC4D_LAUNCH(k_sub_f64<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b, out));
 }
 
 __global__ void k_add_f32_to_f64(int64_t n, const float *a, double *b)
@@ -644,5 +644,5 @@ __global__ void k_add_f32_to_f64(int64_t n, const float *a, double *b)
 
 void launch_add_f32_to_f64(cudaStream_t s, int64_t n, const float *a, double *b)
 {
-    if (n > 0) k_add_f32_to_f64<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b);
+    if (n > 0) WC4D_LAUNCH(k_add_f32_to_f64<<<ceil_div(n, 256), 256, 0, s>>>(n, a, b));
 }

@@ -46,7 +46,7 @@ void launch_gaussian(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, 
 {
     int64_t total = rows * cols;
     int64_t nctr = (total + 1) / 2;
-    k_gaussian<<<ceil_div(nctr, 256), 256, 0, s>>>(seed, rows, total, ld, G);
+    WC4D_LAUNCH(k_gaussian<<<ceil_div(nctr, 256), 256, 0, s>>>(seed, rows, total, ld, G));
 }
 
 // ----------------------------------------------------------------------------
@@ -68,7 +68,7 @@ __global__ void k_twiddles(int n, double2 *tab_full, double2 *tw64, float2 *tw32
 
 void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, float2 *tw32)
 {
-    k_twiddles<<<ceil_div(n, 256), 256, 0, s>>>(n, tab_full, tw64, tw32);
+    WC4D_LAUNCH(k_twiddles<<<ceil_div(n, 256), 256, 0, s>>>(n, tab_full, tw64, tw32));
 }
 
 // ----------------------------------------------------------------------------
@@ -88,7 +88,7 @@ __global__ void k_corr_row(int n, int kind, double L, double var, double *row)
 
 void launch_corr_row(cudaStream_t s, int n, int kind, double L, double var, double *row)
 {
-    k_corr_row<<<ceil_div(n, 256), 256, 0, s>>>(n, kind, L, var, row);
+    WC4D_LAUNCH(k_corr_row<<<ceil_div(n, 256), 256, 0, s>>>(n, kind, L, var, row));
 }
 
 // lam[m] = sum_s row[s] cos(2 pi m s / n): eigenvalues of the symmetric circulant.
@@ -128,9 +128,9 @@ __global__ void k_sqrt_row(int n, const double *lam, const double2 *tab, double 
 void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, const double *row, const double2 *tab,
                      double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32)
 {
-    k_circ_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, row, tab, lam_tmp);
-    if (fft) k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, logn, lam_tmp, spec64, spec32);
-    else k_sqrt_row<<<ceil_div(n, 128), 128, 0, s>>>(n, lam_tmp, tab, row64, row32);
+    WC4D_LAUNCH(k_circ_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, row, tab, lam_tmp));
+    if (fft) WC4D_LAUNCH(k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, logn, lam_tmp, spec64, spec32));
+    else WC4D_LAUNCH(k_sqrt_row<<<ceil_div(n, 128), 128, 0, s>>>(n, lam_tmp, tab, row64, row32));
 }
 
 // ----------------------------------------------------------------------------
@@ -180,8 +180,8 @@ __global__ void k_inverse_dft_real(int n, const double2 *sym, const double2 *tab
 void launch_advdiff_column(cudaStream_t s, int n, double kappa, double c, double dt, int steps,
                            const double2 *tab, double2 *sym_tmp, double *col)
 {
-    k_advdiff_symbol<<<ceil_div(n, 256), 256, 0, s>>>(n, kappa, c, dt, steps, tab, sym_tmp);
-    k_inverse_dft_real<<<ceil_div(n, 128), 128, 0, s>>>(n, sym_tmp, tab, col);
+    WC4D_LAUNCH(k_advdiff_symbol<<<ceil_div(n, 256), 256, 0, s>>>(n, kappa, c, dt, steps, tab, sym_tmp));
+    WC4D_LAUNCH(k_inverse_dft_real<<<ceil_div(n, 128), 128, 0, s>>>(n, sym_tmp, tab, col));
 }
 
 // M[s][s'] = col[(s - s') mod n], MT[s][s'] = col[(s' - s) mod n] (row-major).
@@ -197,7 +197,7 @@ __global__ void k_expand_circulant(int n, const double *col, double *M, double *
 void launch_expand_circulant(cudaStream_t s, int n, const double *col, double *M, double *MT)
 {
     int64_t tot = (int64_t)n * n;
-    k_expand_circulant<<<ceil_div(tot, 256), 256, 0, s>>>(n, col, M, MT);
+    WC4D_LAUNCH(k_expand_circulant<<<ceil_div(tot, 256), 256, 0, s>>>(n, col, M, MT));
 }
 
 __global__ void k_f64_f32(int64_t count, const double *a, float *b)
@@ -214,12 +214,12 @@ __global__ void k_f32_f64(int64_t count, const float *a, double *b)
 
 void launch_convert_f64_f32(cudaStream_t s, int64_t count, const double *a, float *b)
 {
-    if (count > 0) k_f64_f32<<<ceil_div(count, 256), 256, 0, s>>>(count, a, b);
+    if (count > 0) WC4D_LAUNCH(k_f64_f32<<<ceil_div(count, 256), 256, 0, s>>>(count, a, b));
 }
 
 void launch_convert_f32_f64(cudaStream_t s, int64_t count, const float *a, double *b)
 {
-    if (count > 0) k_f32_f64<<<ceil_div(count, 256), 256, 0, s>>>(count, a, b);
+    if (count > 0) WC4D_LAUNCH(k_f32_f64<<<ceil_div(count, 256), 256, 0, s>>>(count, a, b));
 }
 
 // 32x32 tiled transpose of a row-major n x n matrix.
@@ -241,5 +241,5 @@ __global__ void k_transpose(int n, const double *A, double *AT)
 void launch_transpose_f64(cudaStream_t s, int n, const double *A, double *AT)
 {
     dim3 g(ceil_div(n, 32), ceil_div(n, 32)), b(32, 8);
-    k_transpose<<<g, b, 0, s>>>(n, A, AT);
+    WC4D_LAUNCH(k_transpose<<<g, b, 0, s>>>(n, A, AT));
 }

@@ -159,8 +159,8 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
         int nB = (K + 1) / 2;
         int64_t nQ = ((int64_t)K * N + 1) / 2;
         int grid = (int)(nB + nQ);
-        k_circ_fft<T><<<grid, 256, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,
-                                              (const typename Cplx<T>::t *)tw, nB);
+        WC4D_LAUNCH(k_circ_fft<T><<<grid, 256, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,
+                                              (const typename Cplx<T>::t *)tw, nB));
     } else {
         size_t smem = 2 * (size_t)n * sizeof(T);
         static bool attr = false;
@@ -170,7 +170,7 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
             attr = true;
         }
         int64_t grid = (int64_t)K * (N + 1);
-        k_circ_direct<T><<<(unsigned)grid, 256, smem, s>>>(n, N, K, X, ldx, Y, ldy, addX, ld_add, rowB, rowQ);
+        WC4D_LAUNCH(k_circ_direct<T><<<(unsigned)grid, 256, smem, s>>>(n, N, K, X, ldx, Y, ldy, addX, ld_add, rowB, rowQ));
     }
 }
 
@@ -310,9 +310,9 @@ void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int
         constexpr int VEC = sizeof(T) == 8 ? 2 : 4;
         int grid = ceil_div((int64_t)n * 32, 256);
         if (n % VEC == 0 && aligned16(M) && aligned16(B))
-            k_gemv_rows<T, Acc, VEC><<<grid, 256, 0, s>>>(n, M, B, C, e);
+            WC4D_LAUNCH(k_gemv_rows<T, Acc, VEC><<<grid, 256, 0, s>>>(n, M, B, C, e));
         else
-            k_gemv_rows<T, Acc, 1><<<grid, 256, 0, s>>>(n, M, B, C, e);
+            WC4D_LAUNCH(k_gemv_rows<T, Acc, 1><<<grid, 256, 0, s>>>(n, M, B, C, e));
         return;
     }
     launch_gemm<T>(s, n, K, n, M, n, 1, B, ldb, C, ldc, e);
@@ -327,12 +327,12 @@ void launch_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int
     const bool kc = (sak == 1);
     if (Ncols <= 16) {
         dim3 g(ceil_div(Mrows, 64), ceil_div(Ncols, 16));
-        if (kc) k_gemm_simt<T, Acc, 64, 16, 16, 4, 4, true><<<g, 64, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
-        else k_gemm_simt<T, Acc, 64, 16, 16, 4, 4, false><<<g, 64, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
+        if (kc) WC4D_LAUNCH(k_gemm_simt<T, Acc, 64, 16, 16, 4, 4, true><<<g, 64, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e));
+        else WC4D_LAUNCH(k_gemm_simt<T, Acc, 64, 16, 16, 4, 4, false><<<g, 64, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e));
     } else {
         dim3 g(ceil_div(Mrows, 64), ceil_div(Ncols, 64));
-        if (kc) k_gemm_simt<T, Acc, 64, 64, 16, 4, 4, true><<<g, 256, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
-        else k_gemm_simt<T, Acc, 64, 64, 16, 4, 4, false><<<g, 256, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e);
+        if (kc) WC4D_LAUNCH(k_gemm_simt<T, Acc, 64, 64, 16, 4, 4, true><<<g, 256, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e));
+        else WC4D_LAUNCH(k_gemm_simt<T, Acc, 64, 64, 16, 4, 4, false><<<g, 256, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e));
     }
 }
 
@@ -362,7 +362,7 @@ template <typename T>
 void launch_obs_block(cudaStream_t s, int n, int K, T *W, int64_t ld, double scale, int stride)
 {
     int64_t tot = (int64_t)n * K;
-    k_obs_block<T><<<ceil_div(tot, 256), 256, 0, s>>>(n, K, W, ld, scale, stride);
+    WC4D_LAUNCH(k_obs_block<T><<<ceil_div(tot, 256), 256, 0, s>>>(n, K, W, ld, scale, stride));
 }
 
 template void launch_obs_block<double>(cudaStream_t, int, int, double *, int64_t, double, int);

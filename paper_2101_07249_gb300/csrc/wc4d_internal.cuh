@@ -27,6 +27,25 @@ struct Epi {
     int obs_stride;
 };
 
+// Kernel classes timed with CUDA events when profiling is enabled.
+enum ProfId {
+    PROF_GEMV = 0,   // sweep GEMV (one probe column, dense propagator)
+    PROF_GEMM,       // sweep SIMT GEMM (probe blocks)
+    PROF_TC,         // sweep tensor-core GEMM
+    PROF_CIRC,       // D^{1/2} circulant (FFT or direct)
+    PROF_LMP,        // spectral-LMP application
+    PROF_GRAM,       // A^T B Gram products
+    PROF_LA,         // other dense LA (Y R^{-1}, Z W, Cholesky, Jacobi)
+    PROF_L96_TLM,    // Lorenz-96 tangent-linear sweep
+    PROF_L96_ADJ,    // Lorenz-96 adjoint sweep
+    PROF_VEC,        // PCG vector kernels
+    PROF_N
+};
+struct ProfEntry {
+    int id;
+    cudaEvent_t e0, e1;
+};
+
 // ------------------------------------------------------------------ context
 struct wc4d_ctx {
     wc4d_problem prob{};
@@ -82,6 +101,28 @@ struct wc4d_ctx {
     std::vector<double> theta_host;
 
     int64_t hvp_count = 0;
+
+    // profiling (CUDA events per launch group)
+    bool prof_on = false;
+    std::vector<ProfEntry> prof_log;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+};
+
+// ------------------------------------------------------------------ launch accounting
+// Every kernel launch of the library goes through WC4D_LAUNCH, which counts
+// it (wc4d_launch_count).  Usage: WC4D_LAUNCH(kernel<<<g, b, smem, s>>>(args)).
+void wc4d_note_launch();
+#define WC4D_LAUNCH(...) (wc4d_note_launch(), __VA_ARGS__)
+
+// RAII: records an event pair around the launches in scope (no-op when
+// profiling is off).
+struct ProfScope {
+    wc4d_ctx *c;
+    int id;
+    int slot;
+    ProfScope(wc4d_ctx *ctx, int pid);
+    ~ProfScope();
 };
 
 // ------------------------------------------------------------------ helpers

