@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the randomised-LMP inner loop of weak-constraint 4D-Var.
+
+One step = one inner loop (Section 4): Gaussian probes, REVD with one power
+iteration (3 block Hessian products of 256 columns), CholeskyQR2, Rayleigh-
+Ritz, spectral LMP, PCG to relative residual 1e-6, on the large linear window
+(periodic advection-diffusion, n = 4096, N = 40 subwindows, control dimension
+167936, a dense propagator per subwindow).  The chosen form is the mixed
+path (FP32 sweeps and CG, FP64 Gram/Cholesky/Jacobi/CG scalars and true-
+residual refinement); the plain FP64 path is timed beside it.
+
+Prints ONE JSON line (rank 0).  value = inner loops per second over all ranks
+(one independent replica per GPU, weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "inner-loop time to rel-res 1e-6 and Hessian-vec products/s, mixed vs FP64 plain"
+
+# DRAM bytes per launch of the dominant kernel from `ncu` (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by kernel class and workload; see profiles/.
+# Set to None whenever the kernel changes until it is re-measured.
+NCU_TRAFFIC = {}
+
+# Mixed-path PCG iterations (incl. refinement products) measured on the large
+# window; used only to express the CPU oracle's column-product rate in inner
+# loops per second.
+REF_PCG_PRODUCTS = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), float(pk["bf16_tflops"]), float(pk["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_column_rate(cfg, cols=16):
+    """Column Hessian products per second of the FP64 oracle (plain C, OpenMP
+    over columns) on a `cols`-column block of the large window, dense-
+    propagator mode (the same algorithm as the library's sweeps)."""
+    import oracle
+    from paper_2101_07249_gb300 import inputs
+    row_b = oracle.corr_row(cfg.b_kind, cfg.n, cfg.b_L, cfg.b_var)
+    row_q = oracle.corr_row(cfg.q_kind, cfg.n, cfg.q_L, cfg.q_var)
+    M = oracle.advdiff_dense(cfg.n, cfg.kappa, cfg.u, cfg.dt, cfg.steps)
+    p = oracle.Problem(cfg.n, cfg.N, oracle.MODEL_DENSE, oracle.circulant_sqrt_row(row_b)[0],
+                       oracle.circulant_sqrt_row(row_q)[0], cfg.sigma_o2, cfg.obs_stride, cfg.obs_t0,
+                       M=M, M_shared=True)
+    X = inputs.block(1, cfg.nA, cols)
+    t0 = time.perf_counter()
+    oracle.hvp(p, X)
+    dt = time.perf_counter() - t0
+    return cols / dt, dt
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+def run_reference(args, cfg):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    products = REF_PCG_PRODUCTS if REF_PCG_PRODUCTS else 3 * cfg.K
+    times = []
+    for i in range(args.warmup + args.steps):
+        rate, dt = oracle_column_rate(cfg, cols=16)
+        if i >= args.warmup:
+            times.append(dt)
+    col_rate = 16 * len(times) / sum(times)
+    value = col_rate / products
+    sample = (f"16-column block Hessian product of the {cfg.name} window per step (FP64 oracle, dense "
+              f"propagator mode), scaled to inner loops/s by {products} column products per inner loop; "
+              "dense linear algebra of the sketch not included")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inner_loops/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value if value else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg.name, "n": cfg.n, "N": cfg.N, "K": cfg.K},
+            "cpu_baseline": {"value": value, "unit": "inner_loops/s", "cores": omp_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "inner_loops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wc4d", choices=["wc4d", "reference"])
+    ap.add_argument("--method", default="revd", choices=["revd", "nystrom", "ritzit"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="large", choices=["large", "tiny"])
+    args = ap.parse_args()
+
+    from paper_2101_07249_gb300 import inputs
+    cfg = inputs.LARGE if args.workload == "large" else inputs.TINY
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    import paper_2101_07249_gb300 as w
+
+    world, rank, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    w.load()
+    meth = w.METHODS[args.method]
+    cfg = cfg.replace(seed=rank)
+    tw = inputs.twin(cfg)
+    S = w.Solver(cfg, tw, M_shared=False)
+    ctx = S.ctx
+    nA = cfg.nA
+    x = torch.zeros(nA, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def inner(precision, seed):
+        return w.wc4d_inner_loop(ctx, meth, cfg.k, cfg.l, cfg.q_power, seed, cfg.tol, cfg.maxit, precision, x)
+
+    # ---- warm-up (mixed path)
+    for i in range(args.warmup):
+        inner(w.MIXED, 1000 + i)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(local)
+    clocks.start()
+    w.wc4d_launch_count(reset=True)
+    w.wc4d_hvp_count(ctx, reset=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, relres = [], []
+    e0.record(stream)
+    for i in range(args.steps):
+        it, rr = inner(w.MIXED, i)
+        iters.append(it)
+        relres.append(rr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_dev = e0.elapsed_time(e1) / 1e3
+    launches = w.wc4d_launch_count()
+    products_block = w.wc4d_hvp_count(ctx)
+    clk = clocks.stop()
+    t_max = max_over_ranks(world, t_dev)
+    value = world * args.steps / t_max
+
+    # ---- end to end through host buffers: H2D of x^b and y (pinned), the
+    # outer-loop set-up (innovations, rhs), the inner loop, D2H of x
+    xb_h = torch.from_numpy(tw.xb.copy()).pin_memory()
+    y_h = torch.from_numpy(tw.y.copy()).pin_memory()
+    x_h = torch.empty(nA, dtype=torch.float64).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        w.wc4d_set_background_obs(ctx, xb_h.numpy(), y_h.numpy())
+        inner(w.MIXED, 100 + i)
+        x_h.copy_(x)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * args.steps / t_e2e, "unit": "inner_loops/s",
+           "h2d_bytes_per_step": 8 * (cfg.n + cfg.nobs), "d2h_bytes_per_step": 8 * nA}
+
+    # ---- block Hessian products per second (K = 256 probe columns)
+    K = cfg.K
+    Xb = torch.randn(K, nA, dtype=torch.float32, device="cuda")
+    Yb = torch.empty_like(Xb)
+    w.wc4d_hvp(ctx, Xb, Yb, K, nA, w.MIXED)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps = 3
+    for _ in range(reps):
+        w.wc4d_hvp(ctx, Xb, Yb, K, nA, w.MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_hvp_mixed = e0.elapsed_time(e1) / 1e3 / reps
+    del Xb, Yb
+
+    # ---- live per-kernel-class timing of one more mixed inner loop
+    w.wc4d_profile(ctx, True)
+    it_p, _ = inner(w.MIXED, 77)
+    torch.cuda.synchronize()
+    classes = {}
+    for ci, name in enumerate(w.PROF_CLASSES):
+        ms, cnt = w.wc4d_profile_read(ctx, ci)
+        if cnt:
+            classes[name] = {"ms": ms, "launch_groups": cnt, "avg_us": 1e3 * ms / cnt}
+    w.wc4d_profile(ctx, False)
+
+    hbm, bf16, bf16_s, peak_src = _peaks()
+    dom = max(classes, key=lambda k: classes[k]["ms"]) if classes else None
+    roof = None
+    n = cfg.n
+    if dom == "gemv":
+        bytes_per = 4 * n * n + 3 * 4 * n                       # FP32 propagator + x, C_old, C
+        ach = bytes_per / (classes[dom]["avg_us"] * 1e-6) / 1e9
+        tr = NCU_TRAFFIC.get(("gemv_f32", cfg.name))
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": tr, "kernel": "k_gemv_rows<float> (sweep GEMV, one probe column)",
+                "algorithmic_bytes_per_launch": bytes_per, "peak_source": peak_src}
+    elif dom in ("gemm", "tc_gemm"):
+        flops = 2.0 * n * n * K
+        ach = flops / (classes[dom]["avg_us"] * 1e-6) / 1e12
+        if dom == "tc_gemm":
+            pk = bf16 * (1.1 / 2.25)
+            roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "kernel": "tcgen05 TF32 sweep GEMM", "peak_source": peak_src + " x TF32/BF16"}
+        else:
+            sm_mhz = (clk or {}).get("sm_mhz") or 1530.0
+            pk = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "kernel": "SIMT FP32 sweep GEMM",
+                    "peak_source": "152 SM x 128 FP32 lanes x 2 x median SM clock"}
+    elif dom is not None:
+        roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
+                "kernel": dom}
+
+    # ---- the plain FP64 method on the same GPU
+    fp64 = None
+    if not args.no_fp64:
+        inner(w.FP64, 5000)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it64, rr64 = inner(w.FP64, 5001)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        Xb = torch.randn(K, nA, dtype=torch.float64, device="cuda")
+        Yb = torch.empty_like(Xb)
+        e0.record(stream)
+        w.wc4d_hvp(ctx, Xb, Yb, K, nA, w.FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_hvp64 = e0.elapsed_time(e1) / 1e3
+        del Xb, Yb
+        fp64 = {"inner_loop_s": t64, "pcg_iters": it64, "relres": rr64, "hvp_block_s": t_hvp64,
+                "hvp_columns_per_s": K / t_hvp64}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        products = 3 * K + statistics.mean(iters) + 2
+        rate, dt = oracle_column_rate(cfg, cols=16)
+        cpu = {"value": rate / products, "unit": "inner_loops/s", "cores": omp_threads(), "kind": "oracle",
+               "sample": (f"16-column block Hessian product ({dt:.1f} s, FP64 oracle, dense-propagator mode) "
+                          f"scaled by {products:.0f} column products per inner loop; sketch linear algebra "
+                          "not counted")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "inner_loops/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "n": cfg.n, "N": cfg.N, "nA": nA, "K": K, "k": cfg.k,
+                       "l": cfg.l, "method": args.method, "q_power": cfg.q_power, "tol": cfg.tol,
+                       "precision": "mixed", "propagators": "one dense FP32/FP64 matrix per subwindow",
+                       "l2": "inputs larger than L2 (propagators 5.4 GB FP32)", "parallelism": "replicas"},
+            "inner_loop_ms": 1e3 * t_max / args.steps,
+            "pcg_iters": iters, "relres": relres,
+            "block_products_per_step": products_block / args.steps,
+            "hvp_columns_per_s": K / t_hvp_mixed, "hvp_block_ms": 1e3 * t_hvp_mixed,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64": (fp64["inner_loop_s"] / (t_max / args.steps)) if fp64 else None,
+            "kernel_classes": classes,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    S.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -110,8 +110,9 @@ wc4d_status wc4d_build_advdiff_propagator(wc4d_ctx *ctx, double kappa, double c,
  * subwindows).  Circulant on the periodic grid with first row
  * variance * rho(r), r the periodic distance in grid points:
  * SOAR (1 + r/L) e^{-r/L}, Gaussian e^{-r^2/(2 L^2)}, or DIAG (variance * I).
- * The symmetric square root D^{1/2} is formed from the DFT eigenvalues
- * sqrt(max(lambda, 0)) on the device. */
+ * The symmetric square root D^{1/2} is formed on the device from the DFT
+ * eigenvalues: sqrt(lambda), with eigenvalues below 1e-8 of the largest
+ * (where rounding dominates) taken as zero. */
 wc4d_status wc4d_set_covariance(wc4d_ctx *ctx, int32_t block, int32_t corr, double variance, double length);
 /* Same, from an explicit first row (host, n values, symmetric). */
 wc4d_status wc4d_set_covariance_row(wc4d_ctx *ctx, int32_t block, const double *row_host);

@@ -122,22 +122,26 @@ void o_corr_row(int32_t kind, int32_t n, double L, double variance, double *row)
 
 /* Symmetric square root of a symmetric circulant matrix given by its first
  * row: eigenvalues lam_m = sum_s row[s] cos(2 pi m s / n) (plain DFT), then
- * sqrt_row[s] = (1/n) sum_m sqrt(max(lam_m, 0)) cos(2 pi m s / n).
- * Returns the number of negative eigenvalues clamped to zero. */
+ * sqrt_row[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).  Eigenvalues below
+ * 1e-8 of the largest (negative ones included) are taken as zero: there the
+ * DFT's rounding (~1e-16 of the largest) is comparable to the eigenvalue and
+ * its square root would be noise.  Returns the number of eigenvalues zeroed. */
 int o_circulant_sqrt_row(int32_t n, const double *row, double *sqrt_row, double *min_eig)
 {
     double *cosv = (double *)malloc(sizeof(double) * n);
     double *lam = (double *)malloc(sizeof(double) * n);
     for (int32_t j = 0; j < n; ++j) cosv[j] = cos(2.0 * M_PI * (double)j / (double)n);
     int clamped = 0;
-    double mn = INFINITY;
+    double mn = INFINITY, mx = -INFINITY;
     for (int32_t m = 0; m < n; ++m) {
         double acc = 0.0;
         for (int32_t s = 0; s < n; ++s) acc += row[s] * cosv[(int64_t)m * s % n];
         lam[m] = acc;
         if (acc < mn) mn = acc;
-        if (acc < 0.0) { lam[m] = 0.0; ++clamped; }
+        if (acc > mx) mx = acc;
     }
+    for (int32_t m = 0; m < n; ++m)
+        if (!(lam[m] >= 1e-8 * mx)) { lam[m] = 0.0; ++clamped; }
     for (int32_t s = 0; s < n; ++s) {
         double acc = 0.0;
         for (int32_t m = 0; m < n; ++m) acc += sqrt(lam[m]) * cosv[(int64_t)m * s % n];

@@ -351,7 +351,7 @@ static wc4d_status ensure_M32(wc4d_ctx *c)
 static wc4d_status cov_from_row(wc4d_ctx *c, int block, const double *row_dev)
 {
     const int n = c->prob.n;
-    WC4D_TRY(ensure(c, c->small2, sizeof(double) * n));
+    WC4D_TRY(ensure(c, c->small2, sizeof(double) * (n + 1)));
     if (c->fft) {
         WC4D_TRY(ensure(c, c->spec64[block], sizeof(double) * n));
         WC4D_TRY(ensure(c, c->spec32[block], sizeof(float) * n));
@@ -1146,7 +1146,9 @@ extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxi
         for (int round = 0; round < 12 && st == WC4D_OK; ++round) {
             if (force == 0 && rel <= tol) break;
             if (total_it >= budget) break;
-            double inner_tol = (force > 0) ? 0.0 : std::max(0.5 * tol / rel, 1e-7);
+            // each FP32 round aims at the remaining reduction but at most 1e-5:
+            // below that the FP32 recurrence residual no longer tracks the true one
+            double inner_tol = (force > 0) ? 0.0 : std::max(0.5 * tol / rel, 1e-5);
             launch_convert_f64_f32(c->stream, nA, r64, b32);
             PcgOut o;
             st = pcg_core<float>(c, b32, d32, inner_tol, budget - total_it, (force > 0) ? force : 0, use_lmp != 0,

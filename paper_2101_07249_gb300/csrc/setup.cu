@@ -103,13 +103,32 @@ __global__ void k_circ_eig(int n, const double *row, const double2 *tab, double 
 
 __device__ __forceinline__ int bitrev(int v, int logn) { return (int)(__brev((unsigned)v) >> (32 - logn)); }
 
-// FFT path: spec[p] = sqrt(max(lam[bitrev(p)], 0)) / n.  Direct path: first
-// row of the square root, r[s] = (1/n) sum_m sqrt(max(lam_m,0)) cos(2 pi m s/n).
+// lam[n] = max_m lam[m] (one CTA).
+__global__ void k_eig_max(int n, double *lam)
+{
+    __shared__ double red[1024];
+    double m = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, lam[i]);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lam[n] = red[0];
+}
+
+// Eigenvalues below 1e-8 of the largest are taken as zero: there the DFT's
+// rounding is comparable to the eigenvalue and its square root is noise.
+__device__ __forceinline__ double kept_sqrt(double l, double lmax) { return (l >= 1e-8 * lmax) ? sqrt(l) : 0.0; }
+
+// FFT path: spec[p] = sqrt(lam[bitrev(p)]) / n.  Direct path: first row of
+// the square root, r[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).
 __global__ void k_sqrt_spec(int n, int logn, const double *lam, double *spec64, float *spec32)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    double v = sqrt(fmax(lam[bitrev(p, logn)], 0.0)) / (double)n;
+    double v = kept_sqrt(lam[bitrev(p, logn)], lam[n]) / (double)n;
     spec64[p] = v;
     spec32[p] = (float)v;
 }
@@ -118,8 +137,9 @@ __global__ void k_sqrt_row(int n, const double *lam, const double2 *tab, double 
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    const double lmax = lam[n];
     double acc = 0.0;
-    for (int m = 0; m < n; ++m) acc += sqrt(fmax(lam[m], 0.0)) * tab[(int)(((int64_t)m * s) % n)].x;
+    for (int m = 0; m < n; ++m) acc += kept_sqrt(lam[m], lmax) * tab[(int)(((int64_t)m * s) % n)].x;
     acc /= (double)n;
     row64[s] = acc;
     row32[s] = (float)acc;
@@ -129,6 +149,7 @@ void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, const double *ro
                      double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32)
 {
     WC4D_LAUNCH(k_circ_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, row, tab, lam_tmp));
+    WC4D_LAUNCH(k_eig_max<<<1, 1024, 0, s>>>(n, lam_tmp));
     if (fft) WC4D_LAUNCH(k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, logn, lam_tmp, spec64, spec32));
     else WC4D_LAUNCH(k_sqrt_row<<<ceil_div(n, 128), 128, 0, s>>>(n, lam_tmp, tab, row64, row32));
 }

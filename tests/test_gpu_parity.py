@@ -261,10 +261,11 @@ def test_pcg_fp64_matches_oracle(name, method):
         assert it2 == it_f
         assert relerr(host(x), ro["x"]) < 1e-9, it_f
         assert np.allclose(qcf2, ro["qcf_drop"], rtol=1e-9)
-    # (b) converged solution
-    ro = oracle.pcg(p, b, Uo, tho, tol=1e-12, maxit=5000)
-    w.wc4d_pcg(S.ctx, x, 1e-12, 5000, use, 0, w.FP64)
-    assert relerr(host(x), ro["x"]) < 1e-10
+    # (b) converged solution; without the LMP kappa(A) ~ 2.5e3 limits the
+    # attainable accuracy of x to ~kappa * 1e-13
+    ro = oracle.pcg(p, b, Uo, tho, tol=1e-13, maxit=5000)
+    w.wc4d_pcg(S.ctx, x, 1e-13, 5000, use, 0, w.FP64, raise_on_noconv=False)
+    assert relerr(host(x), ro["x"]) < (1e-10 if use else 5e-10)
     # (c) working tolerance
     ro = oracle.pcg(p, b, Uo, tho, tol=1e-6)
     it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, 0, w.FP64)
@@ -275,8 +276,12 @@ def test_pcg_fp64_matches_oracle(name, method):
 
 
 @pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
-@pytest.mark.parametrize("method", ["revd", "ritzit"])
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
 def test_pcg_mixed_meets_tolerance(name, method):
+    """Mixed path (FP32 sketch and CG, FP64 refinement): true relative
+    residual <= 1e-6 at tol 1e-6 (checked with the oracle's own product), and
+    the solution within 1e-5 of the oracle's when run to tol 1e-9 (at 1e-6 the
+    error of any method is bounded only by kappa(A) * 1e-6)."""
     cfg, S, p, tw = setup(name)
     d = oracle.innovation(p, tw.xb, tw.y)
     b = oracle.rhs(p, d)
@@ -285,10 +290,11 @@ def test_pcg_mixed_meets_tolerance(name, method):
     x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
     it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 1, 0, w.MIXED)
     assert rel <= 1e-6
-    assert relerr(host(x), xs) <= 1e-5
-    # the oracle's own residual of the GPU solution
     r = b - oracle.hvp(p, host(x)[None, :])[0]
-    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-6
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
+    it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-9, 5000, 1, 0, w.MIXED)
+    assert rel <= 1e-9
+    assert relerr(host(x), xs) <= 1e-5
 
 
 def test_inner_loop_entry_point():

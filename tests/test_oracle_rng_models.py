@@ -74,7 +74,7 @@ def _circ(row):
     return row[idx]
 
 
-@pytest.mark.parametrize("kind,n,L", [(0, 100, 5.0), (0, 256, 20.48), (1, 128, 4.0), (2, 50, 1.0)])
+@pytest.mark.parametrize("kind,n,L", [(0, 100, 5.0), (0, 256, 20.48), (0, 4096, 81.92), (1, 128, 4.0), (2, 50, 1.0)])
 def test_circulant_sqrt_squares_to_covariance(kind, n, L):
     row = oracle.corr_row(kind, n, L, 0.7)
     srow, clamped, mn = oracle.circulant_sqrt_row(row)
@@ -82,11 +82,14 @@ def test_circulant_sqrt_squares_to_covariance(kind, n, L):
     lam = np.fft.fft(row).real
     assert mn == pytest.approx(lam.min(), abs=1e-12 * abs(lam).max())
     assert np.allclose(S, S.T, atol=1e-15)
+    lam_t = np.where(lam >= 1e-8 * lam.max(), lam, 0.0)       # eigenvalues kept
+    assert clamped == int(np.sum(lam_t == 0.0))
     if clamped == 0:
         assert np.abs(S @ S - C).max() <= 1e-12 * np.abs(C).max()
-    else:  # clamped negative eigenvalues: S^2 is the PSD part of C
-        lam_c = np.fft.fft(np.real(np.fft.ifft(np.maximum(lam, 0.0)))).real
-        assert np.abs(np.fft.fft(srow).real ** 2 - np.maximum(lam, 0)).max() < 1e-10
+    # S^2 is C with the eigenvalues below 1e-8 of the largest removed
+    assert np.abs(np.fft.fft(srow).real ** 2 - lam_t).max() < 1e-12 * lam.max()
+    removed = np.real(np.fft.ifft(lam - lam_t))               # the zeroed part of C
+    assert np.abs(S @ S - (C - _circ(removed))).max() <= 1e-12 * lam.max()
 
 
 def test_circulant_apply_matches_fft_convolution():
