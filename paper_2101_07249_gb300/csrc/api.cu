@@ -1008,9 +1008,12 @@ struct PcgOut {
 };
 
 // CG on A x = b from x = 0 in precision T; b, x device vectors of the context.
+// stag_window > 0: stop early when the running minimum of the recurrence
+// residual has not halved over the last stag_window iterations (used by the
+// FP32 rounds of the mixed path, whose attainable accuracy is limited).
 template <typename T>
 static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit, int force, bool use_lmp,
-                            double *qcf_dev, PcgOut &out)
+                            double *qcf_dev, PcgOut &out, int stag_window = 0)
 {
     const int64_t nA = c->nA;
     DevBuf *vb = (sizeof(T) == 8) ? c->pcg64 : c->pcg32;
@@ -1034,9 +1037,12 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
     launch_pcg_init(c->stream, grid, pa, pb, scal, flags);
     WC4D_TRY(check_launch(c, "pcg init"));
     int *hflags = P<int>(c->pinned);
+    double *hrel = reinterpret_cast<double *>(P<char>(c->pinned) + 64);
     const double tol_k = (force > 0) ? 0.0 : tol;
     const int nit = (force > 0) ? force : maxit;
     out = PcgOut();
+    std::vector<double> best;   // running minimum of the recurrence residual
+    bool stagnated = false;
     for (int it = 0; it < nit; ++it) {
         WC4D_TRY(hvp_impl<T>(c, p, q, 1, nA, false));                       // q = A p
         launch_dot_partial<T>(c->stream, grid, nA, p, q, pa);
@@ -1051,14 +1057,24 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
         launch_pcg_p<T>(c->stream, grid, nA, scal, p, tr);                  // p = C rhat + beta p
         WC4D_TRY(check_launch(c, "pcg iteration"));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+        if (stag_window > 0)
+            WC4D_CUDA(c, cudaMemcpyAsync(hrel, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         WC4D_TRY(sync(c, "pcg iteration"));
         if (hflags[0]) break;
+        if (stag_window > 0) {
+            double bnow = best.empty() ? *hrel : std::min(best.back(), *hrel);
+            best.push_back(bnow);
+            if ((int)best.size() > stag_window && bnow > 0.5 * best[best.size() - 1 - stag_window]) {
+                stagnated = true;
+                break;
+            }
+        }
     }
     double hs[8];
     WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
     WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
     WC4D_TRY(sync(c, "pcg end"));
-    out.done = hflags[0] != 0;
+    out.done = hflags[0] != 0 || stagnated;
     out.breakdown = hflags[1];
     out.iters = hflags[2];
     out.relres_rec = hs[4];
@@ -1143,16 +1159,17 @@ extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxi
         }
         rel = bnorm > 0.0 ? 1.0 : 0.0;
         const int budget = (force > 0) ? force : maxit;
-        for (int round = 0; round < 12 && st == WC4D_OK; ++round) {
+        for (int round = 0; round < 40 && st == WC4D_OK; ++round) {
             if (force == 0 && rel <= tol) break;
             if (total_it >= budget) break;
-            // each FP32 round aims at the remaining reduction but at most 1e-5:
-            // below that the FP32 recurrence residual no longer tracks the true one
-            double inner_tol = (force > 0) ? 0.0 : std::max(0.5 * tol / rel, 1e-5);
+            // each FP32 round aims at the remaining reduction but at most 1e-4
+            // (FP32 CG on these operators attains ~1e-5), and ends early on
+            // stagnation; the FP64 residual then starts the next round
+            double inner_tol = (force > 0) ? 0.0 : std::max(0.5 * tol / rel, 1e-4);
             launch_convert_f64_f32(c->stream, nA, r64, b32);
             PcgOut o;
             st = pcg_core<float>(c, b32, d32, inner_tol, budget - total_it, (force > 0) ? force : 0, use_lmp != 0,
-                                 P<double>(qcf) + total_it, o);
+                                 P<double>(qcf) + total_it, o, (force > 0) ? 0 : 25);
             if (st != WC4D_OK) break;
             total_it += o.iters;
             launch_add_f32_to_f64(c->stream, nA, d32, x);
