@@ -190,11 +190,12 @@ def main():
     ap.add_argument("--method", default="revd", choices=["revd", "nystrom", "ritzit"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="large", choices=["large", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny"],
+                    help="large: n=4096 N=40 (the benchmark); medium: N=8 (profiling captures); tiny: n=100 N=5")
     args = ap.parse_args()
 
     from paper_2101_07249_gb300 import inputs
-    cfg = inputs.LARGE if args.workload == "large" else inputs.TINY
+    cfg = {"large": inputs.LARGE, "medium": inputs.MEDIUM, "tiny": inputs.TINY}[args.workload]
     if args.impl == "reference":
         run_reference(args, cfg)
         return

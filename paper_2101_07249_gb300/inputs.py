@@ -91,13 +91,17 @@ LARGE = Config(name="advdiff_n4096_N40", model=MODEL_ADVDIFF, n=4096, N=40, step
                q_kind=SOAR, q_var=0.1, q_L=0.02 * 4096, obs_stride=8, obs_t0=1,
                sigma_o2=0.01, k=240, l=16, q_power=1)
 
+# The same window shortened to N=8 subwindows (control dimension 36864): a
+# profiling case that keeps the device footprint to a few GB.
+MEDIUM = LARGE.replace(name="advdiff_n4096_N8", N=8)
+
 # Nonlinear Lorenz-96: n=8192, F=8, RK4 dt=0.025, 8 steps per subwindow, N=40,
 # B = 0.5 Gaussian(L=4 points), Q = 0.05 I, every 4th variable observed, R = 0.1 I.
 L96 = Config(name="l96_n8192_N40", model=MODEL_L96, n=8192, N=40, steps=8, dt=0.025, F=8.0,
              b_kind=GAUSS, b_var=0.5, b_L=4.0, q_kind=DIAG, q_var=0.05, q_L=1.0,
              obs_stride=4, obs_t0=1, sigma_o2=0.1, k=240, l=16, q_power=1)
 
-CONFIGS = {c.name: c for c in (TINY, LARGE, L96)}
+CONFIGS = {c.name: c for c in (TINY, MEDIUM, LARGE, L96)}
 
 
 def scaled(cfg: Config, n: int, N: int, k: int, l: int, **kw) -> Config:
