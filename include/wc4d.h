@@ -218,6 +218,22 @@ int64_t     wc4d_launch_count(int32_t reset);
  * tangent-linear sweep, 8 Lorenz-96 adjoint sweep, 9 PCG vector kernels. */
 wc4d_status wc4d_profile(wc4d_ctx *ctx, int32_t enable);
 wc4d_status wc4d_profile_read(wc4d_ctx *ctx, int32_t cls, double *total_ms, int64_t *launch_groups);
+/* Allocation-free spectral-LMP application, y = C v (the paper has no
+ * counterpart: it is an integration aid).  For callers that cannot allocate
+ * device memory where they apply the preconditioner -- code inside CUDA
+ * stream capture (cudaMalloc cannot be captured), systems that reserve their
+ * whole device memory budget up front, callers without a library context.
+ * U (device, nA x k column-major, orthonormal columns), theta (device, k
+ * values), v and y (device, nA doubles, distinct); queued on cuda_stream.
+ * Creates no context and allocates nothing: its scratch (coefficients and
+ * partial dot products) is one fixed 1 MiB + 8 KiB device array in the
+ * library, held by every GPU that loads it until exit.  k > 1024 returns
+ * WC4D_EINVAL.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make it before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller. */
+wc4d_status wc4d_lmp_apply_static(const double *U, const double *theta, int32_t k, int64_t nA, const double *v,
+                                  double *y, void *cuda_stream);
 /* Products with A issued so far (block products count once). */
 int64_t     wc4d_hvp_count(wc4d_ctx *ctx, int32_t reset);
 

@@ -81,6 +81,7 @@ _SIGS = {
     "wc4d_launch_count": (C.c_int64, [C.c_int32]),
     "wc4d_profile": (C.c_int, [_V, C.c_int32]),
     "wc4d_profile_read": (C.c_int, [_V, C.c_int32, _D, C.POINTER(C.c_int64)]),
+    "wc4d_lmp_apply_static": (C.c_int, [_V, _V, C.c_int32, C.c_int64, _V, _V, _V]),
 }
 PROF_CLASSES = ("gemv", "gemm", "tc_gemm", "circulant", "lmp", "gram", "la", "l96_tlm", "l96_adj", "pcg_vec")
 EXPORTS = tuple(_SIGS)
@@ -299,6 +300,13 @@ def wc4d_profile_read(ctx, cls):
     n = C.c_int64(0)
     _check(ctx, load().wc4d_profile_read(ctx, int(cls), C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def wc4d_lmp_apply_static(U, theta, k, nA, v, y, stream=None):
+    """y = C v without any device allocation (shared fixed scratch; see wc4d.h)."""
+    st = load().wc4d_lmp_apply_static(_ptr(U), _ptr(theta), int(k), int(nA), _ptr(v), _ptr(y), _stream(stream))
+    if st != OK:
+        raise WC4DError(st, "wc4d_lmp_apply_static")
 
 
 def wc4d_hvp_count(ctx, reset=False):
