@@ -734,8 +734,10 @@ int o_jacobi_eig(int32_t m, const double *A, double *w, double *V)
     memcpy(a, A, sizeof(double) * m * m);
     for (int32_t j = 0; j < m; ++j)
         for (int32_t i = 0; i < m; ++i) V[(int64_t)j * m + i] = (i == j) ? 1.0 : 0.0;
-    /* An off-diagonal entry is negligible once |a_pq| <= eps sqrt(|a_pp a_qq|)
-     * (relative criterion); the iteration stops after a sweep with no rotation. */
+    /* An off-diagonal entry is negligible once |a_pq| <= tol sqrt(|a_pp a_qq|)
+     * with tol = sqrt(m) eps (relative criterion, the rounding level of the
+     * m-term updates); the iteration stops after a sweep with no rotation. */
+    const double tol = 2.220446049250313e-16 * sqrt((double)m);
     int sweeps = -1;
     for (int sweep = 0; sweep < 100; ++sweep) {
         int rotated = 0;
@@ -743,7 +745,7 @@ int o_jacobi_eig(int32_t m, const double *A, double *w, double *V)
             for (int32_t q = p + 1; q < m; ++q) {
                 double apq = a[(int64_t)q * m + p];
                 double app = a[(int64_t)p * m + p], aqq = a[(int64_t)q * m + q];
-                if (fabs(apq) <= 1e-16 * sqrt(fabs(app * aqq)) || fabs(apq) < 1e-300) continue;
+                if (fabs(apq) <= tol * sqrt(fabs(app * aqq)) || fabs(apq) < 1e-300) continue;
                 rotated = 1;
                 double tau = (aqq - app) / (2.0 * apq);
                 double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
@@ -827,6 +829,7 @@ int o_jacobi_svd(int64_t rows, int32_t m, const double *A, int64_t lda, double *
     o_householder_qr(rows, m, A, lda, Q, rows, B);
     for (int32_t j = 0; j < m; ++j)
         for (int32_t i = 0; i < m; ++i) V[(int64_t)j * m + i] = (i == j) ? 1.0 : 0.0;
+    const double tol = 2.220446049250313e-16 * sqrt((double)m);   /* rounding level of m-term dots */
     int sweeps = -1;
     for (int sweep = 0; sweep < 100; ++sweep) {
         int rotated = 0;
@@ -835,7 +838,7 @@ int o_jacobi_svd(int64_t rows, int32_t m, const double *A, int64_t lda, double *
                 double *bp = B + (int64_t)p * m, *bq = B + (int64_t)q * m;
                 double al = 0.0, be = 0.0, ga = 0.0;
                 for (int32_t r = 0; r < m; ++r) { al += bp[r] * bp[r]; be += bq[r] * bq[r]; ga += bp[r] * bq[r]; }
-                if (ga == 0.0 || fabs(ga) <= 1e-16 * sqrt(al * be)) continue;
+                if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) continue;
                 rotated = 1;
                 double zeta = (be - al) / (2.0 * ga);
                 double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));

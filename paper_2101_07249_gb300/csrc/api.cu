@@ -420,6 +420,7 @@ template <> struct Ops<float> {
 
 // Dense-model sweeps on tensor cores (tc_gemm.cu); returns false when the
 // shape is not supported so the SIMT path is taken.
+bool tc_sweep_supported(const wc4d_ctx *c, int K);
 bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld);
 bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld);
 
@@ -444,8 +445,10 @@ static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allo
         return check_launch(c, "l96 tlm sweep");
     }
     if constexpr (sizeof(T) == 4) {
-        ProfScope ps(c, PROF_TC);
-        if (allow_tc && tc_sweep_forward(c, K, (float *)W, ld)) return check_launch(c, "tc forward sweep");
+        if (allow_tc && tc_sweep_supported(c, K)) {
+            ProfScope ps(c, PROF_TC);
+            if (tc_sweep_forward(c, K, (float *)W, ld)) return check_launch(c, "tc forward sweep");
+        }
     }
     Epi e{0, 1.0, 1.0, 0.0, 1};
     for (int t = 0; t < N; ++t) {
@@ -468,8 +471,10 @@ static wc4d_status adjoint_obs_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool 
         return check_launch(c, "l96 adjoint sweep");
     }
     if constexpr (sizeof(T) == 4) {
-        ProfScope ps(c, PROF_TC);
-        if (allow_tc && tc_sweep_adjoint(c, K, (float *)W, ld)) return check_launch(c, "tc adjoint sweep");
+        if (allow_tc && tc_sweep_supported(c, K)) {
+            ProfScope ps(c, PROF_TC);
+            if (tc_sweep_adjoint(c, K, (float *)W, ld)) return check_launch(c, "tc adjoint sweep");
+        }
     }
     launch_obs_block<T>(c->stream, n, K, W + (int64_t)N * n, ld, obs_scale(c, N), c->prob.obs_stride);
     for (int t = N - 1; t >= 0; --t) {
@@ -655,13 +660,16 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     const size_t mm = (size_t)m * m;
     WC4D_TRY(ensure(c, c->small0, sizeof(double) * mm));
     WC4D_TRY(ensure(c, c->small1, sizeof(double) * mm));
-    const int tiles = ceil_div(m, 32) * ceil_div(m, 32);
-    size_t part_need = sizeof(double) * mm * (size_t)std::max<int64_t>(1, (2 * c->num_sms + tiles - 1) / tiles + 1);
-    WC4D_TRY(ensure(c, c->part, part_need));
+    const size_t part_need = atb_part_doubles(c->num_sms, rows, m, m, 1);
+    WC4D_TRY(ensure(c, c->part, sizeof(double) * part_need));
     int S = 0;
     double *G = P<double>(c->small0);
-    ProfScope ps(c, PROF_GRAM);
-    launch_atb<T>(c->stream, c->num_sms, rows, m, m, Y, ld, Y, ld, P<double>(c->part), &S, G);   // G = Y^T Y
+    {
+        ProfScope ps(c, PROF_GRAM);
+        if (launch_atb<T>(c->stream, c->num_sms, rows, m, m, Y, ld, Y, ld, P<double>(c->part), c->part.bytes / 8,
+                          &S, G, 1) != 0)   // G = Y^T Y
+            return set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small");
+    }
     launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));                                // G = R^T R
     double *Rinv = P<double>(c->small1);
     launch_trinv_upper(c->stream, m, R, Rinv);
@@ -679,9 +687,8 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
         launch_gemm<float>(c->stream, (int)rows, m, m, Y, 1, ld, Rinv32, m, tmp, rows, e);
     }
     WC4D_TRY(check_launch(c, "cholqr gemm"));
-    for (int j = 0; j < m; ++j)
-        WC4D_CUDA(c, cudaMemcpyAsync(Y + (int64_t)j * ld, tmp + (int64_t)j * rows, sizeof(T) * rows,
-                                     cudaMemcpyDeviceToDevice, c->stream));
+    WC4D_CUDA(c, cudaMemcpy2DAsync(Y, sizeof(T) * ld, tmp, sizeof(T) * rows, sizeof(T) * rows, m,
+                                   cudaMemcpyDeviceToDevice, c->stream));
     return WC4D_OK;
 }
 
@@ -817,11 +824,16 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         // E = A Z
         T *E = Y;
         if ((st = hvp_impl<T>(c, Z, E, m, nA)) != WC4D_OK) return fail(st);
-        const int tiles = ceil_div(m, 32) * ceil_div(m, 32);
-        if ((st = ensure(c, c->part, sizeof(double) * mm * ((2 * c->num_sms + tiles - 1) / tiles + 1))) != WC4D_OK)
+        if ((st = ensure(c, c->part, sizeof(double) * atb_part_doubles(c->num_sms, nA, m, m, 1))) != WC4D_OK)
             return fail(st);
         int S = 0;
-        launch_atb<T>(c->stream, c->num_sms, nA, m, m, Z, nA, E, nA, P<double>(c->part), &S, Kmat);  // Z^T A Z
+        {
+            // Z^T A Z is symmetric: upper tiles only, mirrored
+            ProfScope psg(c, PROF_GRAM);
+            if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, Z, nA, E, nA, P<double>(c->part), c->part.bytes / 8,
+                              &S, Kmat, 1) != 0)
+                return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
+        }
         launch_symmetrize(c->stream, m, Kmat);
         if ((st = check_launch(c, "ZtAZ")) != WC4D_OK) return fail(st);
         if (method == WC4D_REVD) {
@@ -856,7 +868,9 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
                 launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, Ci32);
                 launch_gemm<float>(c->stream, (int)nA, m, m, E, 1, nA, Ci32, m, F, nA, e);
             }
-            launch_atb<T>(c->stream, c->num_sms, nA, m, m, F, nA, F, nA, P<double>(c->part), &S, Kmat);  // F^T F
+            if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, F, nA, F, nA, P<double>(c->part), c->part.bytes / 8,
+                              &S, Kmat, 1) != 0)   // F^T F
+                return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
             launch_symmetrize(c->stream, m, Kmat);
             if ((st = check_launch(c, "nystrom F")) != WC4D_OK) return fail(st);
             if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);   // F^T F = V Sigma^2 V^T
@@ -981,11 +995,12 @@ static wc4d_status lmp_apply_impl(wc4d_ctx *c, const T *v, T *y, const int *skip
     const int k = c->kU;
     const int64_t nA = c->nA;
     ProfScope ps(c, PROF_LMP);
-    int splits = ceil_div(nA, 1024);
-    WC4D_TRY(ensure(c, c->part, sizeof(double) * (size_t)splits * k + 64));
+    int splits = utv_splits(nA);
+    WC4D_TRY(ensure(c, c->part, sizeof(double) * ((size_t)splits * k + k) + 64));
     launch_utv<T>(c->stream, c->num_sms, nA, k, Ubuf<T>(c), v, P<double>(c->part), &splits);
-    launch_lmp_combine<T>(c->stream, nA, k, Ubuf<T>(c), P<double>(c->part), splits, P<double>(c->c64), 1.0, v, y,
-                          nullptr, nullptr, skip);
+    // the reduced t = U^T v sits after the partials
+    launch_lmp_combine<T>(c->stream, nA, k, Ubuf<T>(c), P<double>(c->part) + (size_t)splits * k, 1,
+                          P<double>(c->c64), 1.0, v, y, nullptr, nullptr, skip);
     return check_launch(c, "lmp apply");
 }
 

@@ -37,10 +37,20 @@ __device__ double block_sum(double v)
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_atb(int64_t rows, int ma, int mb, const T *__restrict__ A, int64_t lda, const T *__restrict__ B, int64_t ldb,
-      double *part, int64_t rows_per_split, int tiles_a)
+      double *part, int64_t rows_per_split, int tiles_a, int upper)
 {
     __shared__ double As[32][33], Bs[32][33];
-    const int tile = blockIdx.x, ti = tile % tiles_a, tj = tile / tiles_a, split = blockIdx.y;
+    const int tile = blockIdx.x, split = blockIdx.y;
+    int ti, tj;
+    if (upper) {   // tiles with ti <= tj only, enumerated column by column
+        tj = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+        while ((tj + 1) * (tj + 2) / 2 <= tile) ++tj;
+        while (tj * (tj + 1) / 2 > tile) --tj;
+        ti = tile - tj * (tj + 1) / 2;
+    } else {
+        ti = tile % tiles_a;
+        tj = tile / tiles_a;
+    }
     const int64_t r0 = (int64_t)split * rows_per_split;
     const int64_t r1 = min(rows, r0 + rows_per_split);
     const int i0 = ti * 32, j0 = tj * 32;
@@ -70,40 +80,75 @@ k_atb(int64_t rows, int ma, int mb, const T *__restrict__ A, int64_t lda, const 
     }
 }
 
-__global__ void k_reduce_part(int S, int64_t count, const double *part, double *out)
+// out[e] = sum_s part[s][e]; with `upper` (square, only tiles ti <= tj were
+// computed) the entries below the diagonal tiles take the mirrored sum.
+__global__ void k_reduce_part(int S, int64_t count, int m, int upper, const double *part, double *out)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
+    int64_t src = e;
+    if (upper) {
+        int i = (int)(e % m), j = (int)(e / m);
+        if (i / 32 > j / 32) src = (int64_t)i * m + j;
+    }
     double acc = 0.0;
-    for (int s = 0; s < S; ++s) acc += part[(int64_t)s * count + e];
+    for (int s = 0; s < S; ++s) acc += part[(int64_t)s * count + src];
     out[e] = acc;
 }
 
-template <typename T>
-void launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
-                int64_t ldb, double *part, int *splits_out, double *C)
+// Row splits of k_atb and the number of partial doubles they need.
+static void atb_plan(int num_sms, int64_t rows, int ma, int mb, int upper, int *tiles_out, int64_t *splits_out,
+                     int64_t *rps_out)
 {
-    const int ta = ceil_div(ma, 32), tb = ceil_div(mb, 32), tiles = ta * tb;
+    const int ta = ceil_div(ma, 32), tb = ceil_div(mb, 32);
+    if (ma != mb) upper = 0;
+    const int tiles = upper ? ta * (ta + 1) / 2 : ta * tb;
     int64_t max_splits = (rows + 31) / 32;
     int64_t S = (2 * (int64_t)num_sms + tiles - 1) / tiles;
     if (S > max_splits) S = max_splits;
     if (S < 1) S = 1;
     int64_t rps = ((rows + S - 1) / S + 31) / 32 * 32;
+    if (rps < 32) rps = 32;
     S = (rows + rps - 1) / rps;
     if (S < 1) S = 1;
+    *tiles_out = tiles;
+    *splits_out = S;
+    *rps_out = rps;
+}
+
+size_t atb_part_doubles(int num_sms, int64_t rows, int ma, int mb, int upper)
+{
+    int tiles;
+    int64_t S, rps;
+    atb_plan(num_sms, rows, ma, mb, upper, &tiles, &S, &rps);
+    return (size_t)S * ma * mb;
+}
+
+// Returns 0, or -1 (nothing launched) when part_capacity (doubles) is too small.
+template <typename T>
+int launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
+               int64_t ldb, double *part, size_t part_capacity, int *splits_out, double *C, int upper)
+{
+    if (ma != mb) upper = 0;
+    int tiles;
+    int64_t S, rps;
+    atb_plan(num_sms, rows, ma, mb, upper, &tiles, &S, &rps);
+    if ((size_t)S * ma * mb > part_capacity) return -1;
+    const int ta = ceil_div(ma, 32);
     dim3 g(tiles, (unsigned)S);
-    WC4D_LAUNCH(k_atb<T><<<g, 256, 0, s>>>(rows, ma, mb, A, lda, B, ldb, part, rps, ta));
+    WC4D_LAUNCH(k_atb<T><<<g, 256, 0, s>>>(rows, ma, mb, A, lda, B, ldb, part, rps, ta, upper));
     if (splits_out) *splits_out = (int)S;
     if (C) {
         int64_t cnt = (int64_t)ma * mb;
-        WC4D_LAUNCH(k_reduce_part<<<ceil_div(cnt, 256), 256, 0, s>>>((int)S, cnt, part, C));
+        WC4D_LAUNCH(k_reduce_part<<<ceil_div(cnt, 256), 256, 0, s>>>((int)S, cnt, ma, upper, part, C));
     }
+    return 0;
 }
 
-template void launch_atb<double>(cudaStream_t, int, int64_t, int, int, const double *, int64_t, const double *,
-                                 int64_t, double *, int *, double *);
-template void launch_atb<float>(cudaStream_t, int, int64_t, int, int, const float *, int64_t, const float *,
-                                int64_t, double *, int *, double *);
+template int launch_atb<double>(cudaStream_t, int, int64_t, int, int, const double *, int64_t, const double *,
+                                int64_t, double *, size_t, int *, double *, int);
+template int launch_atb<float>(cudaStream_t, int, int64_t, int, int, const float *, int64_t, const float *,
+                               int64_t, double *, size_t, int *, double *, int);
 
 // ----------------------------------------------------------------------------
 // Cholesky A = R^T R (R upper, column-major m x m), right-looking, one CTA.
@@ -339,10 +384,10 @@ void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c)
     WC4D_LAUNCH(k_lmp_coeffs<<<ceil_div(k, 128), 128, 0, s>>>(k, theta, c));
 }
 
-constexpr int UTV_ROWS = 1024;
+constexpr int UTV_ROWS = 256;
 
 // part[split][i] = sum over the split's rows of U[r, i] v[r]; one warp per
-// column at a time, v staged in shared memory.
+// column at a time (8 loads per lane in flight), v staged in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_utv(int64_t nA, int k, const T *__restrict__ U, const T *__restrict__ v,
                                              double *part)
@@ -350,23 +395,36 @@ __global__ void __launch_bounds__(256) k_utv(int64_t nA, int k, const T *__restr
     __shared__ T vs[UTV_ROWS];
     const int64_t r0 = (int64_t)blockIdx.x * UTV_ROWS;
     const int rows = (int)min((int64_t)UTV_ROWS, nA - r0);
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) vs[r] = v[r0 + r];
+    for (int r = threadIdx.x; r < UTV_ROWS; r += blockDim.x) vs[r] = (r < rows) ? v[r0 + r] : (T)0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = w; i < k; i += nw) {
         const T *u = U + (int64_t)i * nA + r0;
+        T vals[UTV_ROWS / 32];
+#pragma unroll
+        for (int q = 0; q < UTV_ROWS / 32; ++q) {
+            const int r = lane + 32 * q;
+            vals[q] = (r < rows) ? __ldcs(u + r) : (T)0;
+        }
         T acc = 0;
-        for (int r = lane; r < rows; r += 32) acc = fma(u[r], vs[r], acc);
+#pragma unroll
+        for (int q = 0; q < UTV_ROWS / 32; ++q) acc = fma(vals[q], vs[lane + 32 * q], acc);
         double d = warp_sum((double)acc);
         if (lane == 0) part[(int64_t)blockIdx.x * k + i] = d;
     }
 }
 
+int utv_splits(int64_t nA) { return ceil_div(nA, UTV_ROWS); }
+
+// t = U^T v: per-chunk partials part[0 .. S*k), then their sum in fixed order
+// at part[S*k .. S*k + k).  *splits returns S.
 template <typename T>
 void launch_utv(cudaStream_t s, int num_sms, int64_t nA, int k, const T *U, const T *v, double *part, int *splits)
 {
-    int S = ceil_div(nA, UTV_ROWS);
+    (void)num_sms;
+    const int S = utv_splits(nA);
     WC4D_LAUNCH(k_utv<T><<<S, 256, 0, s>>>(nA, k, U, v, part));
+    WC4D_LAUNCH(k_reduce_part<<<ceil_div(k, 256), 256, 0, s>>>(S, k, k, 0, part, part + (int64_t)S * k));
     *splits = S;
 }
 
@@ -393,7 +451,15 @@ k_lmp_combine(int64_t nA, int k, const T *__restrict__ U, const double *__restri
     // accumulate in the storage precision (FP32 vectors in the mixed path)
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nA; r += (int64_t)gridDim.x * blockDim.x) {
         T acc = v[r];
-        for (int i = 0; i < k; ++i) acc = fma(-U[(int64_t)i * nA + r], (T)ct[i], acc);
+        int i = 0;
+        for (; i + 8 <= k; i += 8) {
+            T u[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) u[q] = __ldcs(U + (int64_t)(i + q) * nA + r);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc = fma(-u[q], (T)ct[i + q], acc);
+        }
+        for (; i < k; ++i) acc = fma(-U[(int64_t)i * nA + r], (T)ct[i], acc);
         if (add) acc = fma(beta, add[r], acc);
         y[r] = acc;
     }

@@ -260,36 +260,80 @@ k_gemm_simt(int Mrows, int Ncols, int Kdim, const T *__restrict__ A, int64_t sam
         }
 }
 
-// y = epi(M x) with one warp per row of the row-major n x n M; VEC-wide loads.
-template <typename T, typename Acc, int VEC>
-__global__ void __launch_bounds__(256)
+// y = epi(M x) for the row-major n x n M.  Each warp owns RPW consecutive
+// rows; every lane keeps UNR vector loads per row in flight (the kernel is
+// bound by HBM latency x bytes in flight), M is read with evict-first
+// streaming loads so that x stays in L1 for all warps of the SM.  Small CTAs
+// (2 warps) spread the rows evenly over the 152 SMs.
+template <typename T, typename Acc, int RPW, int UNR>
+__global__ void __launch_bounds__(64)
 k_gemv_rows(int n, const T *__restrict__ M, const T *__restrict__ x, T *y, Epi e)
+{
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    constexpr int VEC = sizeof(V) / sizeof(T);
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int row0 = warp * RPW;
+    if (row0 >= n) return;
+    const int nv = n / VEC;
+    const V *x4 = reinterpret_cast<const V *>(x);
+    const V *r4[RPW];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) r4[r] = reinterpret_cast<const V *>(M + (int64_t)min(row0 + r, n - 1) * n);
+    Acc acc[RPW];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) acc[r] = 0;
+    for (int c0 = lane; c0 < nv; c0 += 32 * UNR) {
+        V a[RPW][UNR], b[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int idx = c0 + 32 * u;
+            if (idx < nv) {
+                b[u] = __ldg(x4 + idx);
+#pragma unroll
+                for (int r = 0; r < RPW; ++r) a[r][u] = __ldcs(r4[r] + idx);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (c0 + 32 * u < nv) {
+                const T *bf = reinterpret_cast<const T *>(&b[u]);
+#pragma unroll
+                for (int r = 0; r < RPW; ++r) {
+                    const T *af = reinterpret_cast<const T *>(&a[r][u]);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[r] = fma((Acc)af[v], (Acc)bf[v], acc[r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    }
+    if (lane < RPW && row0 + lane < n) {
+        Acc mine = acc[0];
+#pragma unroll
+        for (int r = 1; r < RPW; ++r)
+            if (lane == r) mine = acc[r];
+        const int row = row0 + lane;
+        Acc old = (e.mode == 1 || e.beta != 0.0) ? (Acc)y[row] : (Acc)0;
+        y[row] = (T)apply_epi<Acc>(e, mine, row, &old);
+    }
+}
+
+// Scalar fallback for n not a multiple of the vector width or unaligned operands.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256)
+k_gemv_scalar(int n, const T *__restrict__ M, const T *__restrict__ x, T *y, Epi e)
 {
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
     const T *row = M + (int64_t)warp * n;
     Acc acc = 0;
-    if (VEC == 1) {
-        for (int c = lane; c < n; c += 32) acc = fma((Acc)row[c], (Acc)__ldg(x + c), acc);
-    } else {
-        using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
-        const V *r4 = reinterpret_cast<const V *>(row);
-        const V *x4 = reinterpret_cast<const V *>(x);
-        const int nv = n / VEC;
-        for (int c = lane; c < nv; c += 32) {
-            V a = __ldg(r4 + c), b = __ldg(x4 + c);
-            if constexpr (sizeof(T) == 8) {
-                acc = fma((Acc)a.x, (Acc)b.x, acc);
-                acc = fma((Acc)a.y, (Acc)b.y, acc);
-            } else {
-                const float *af = reinterpret_cast<const float *>(&a);
-                const float *bf = reinterpret_cast<const float *>(&b);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc = fma((Acc)af[u], (Acc)bf[u], acc);
-            }
-        }
-    }
+    for (int c = lane; c < n; c += 32) acc = fma((Acc)row[c], (Acc)__ldg(x + c), acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
@@ -308,11 +352,13 @@ void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int
     using Acc = T;
     if (K == 1) {
         constexpr int VEC = sizeof(T) == 8 ? 2 : 4;
-        int grid = ceil_div((int64_t)n * 32, 256);
-        if (n % VEC == 0 && aligned16(M) && aligned16(B))
-            WC4D_LAUNCH(k_gemv_rows<T, Acc, VEC><<<grid, 256, 0, s>>>(n, M, B, C, e));
-        else
-            WC4D_LAUNCH(k_gemv_rows<T, Acc, 1><<<grid, 256, 0, s>>>(n, M, B, C, e));
+        constexpr int RPW = 2, UNR = 4;
+        if (n % VEC == 0 && aligned16(M) && aligned16(B)) {
+            const int warps = ceil_div(n, RPW);
+            WC4D_LAUNCH(k_gemv_rows<T, Acc, RPW, UNR><<<ceil_div(warps, 2), 64, 0, s>>>(n, M, B, C, e));
+        } else {
+            WC4D_LAUNCH(k_gemv_scalar<T, Acc><<<ceil_div((int64_t)n * 32, 256), 256, 0, s>>>(n, M, B, C, e));
+        }
         return;
     }
     launch_gemm<T>(s, n, K, n, M, n, 1, B, ldb, C, ldc, e);

@@ -178,9 +178,13 @@ void launch_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int
                  const T *B, int64_t ldb, T *C, int64_t ldc, const Epi &e);
 
 // linear algebra
+// C = A^T B with FP64 accumulation; `upper` (square products known to be
+// symmetric) computes the upper tiles only and mirrors them.  part must hold
+// atb_part_doubles(...) doubles; returns -1 without launching otherwise.
+size_t atb_part_doubles(int num_sms, int64_t rows, int ma, int mb, int upper);
 template <typename T>
-void launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
-                int64_t ldb, double *part, int *splits_out, double *C);
+int launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
+               int64_t ldb, double *part, size_t part_capacity, int *splits_out, double *C, int upper);
 void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *info);
 void launch_trinv_upper(cudaStream_t s, int m, const double *R, double *Rinv);
 void launch_jacobi_init(cudaStream_t s, int m, int mp, const double *S, double *X, double *V);
@@ -189,6 +193,8 @@ void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const 
 void launch_rrt(cudaStream_t s, int m, const double *R, double *RT);
 void launch_symmetrize(cudaStream_t s, int m, double *S);
 void launch_scale_cols(cudaStream_t s, int64_t rows, int m, double *A, int64_t lda, const double *w, int inv_sqrt);
+// number of row chunks (partial sums per column) of launch_utv
+int utv_splits(int64_t nA);
 template <typename T>
 void launch_utv(cudaStream_t s, int num_sms, int64_t nA, int k, const T *U, const T *v, double *part, int *splits);
 template <typename T>

@@ -361,3 +361,26 @@ def test_maxit_reports_no_convergence():
     x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
     it, rel, _, st = w.wc4d_pcg(S.ctx, x, 1e-12, 2, 0, 0, w.FP64, raise_on_noconv=False)
     assert st == w.ENOCONV and it == 2 and rel > 1e-12
+
+
+# ------------------------------------------------------------------ the benchmark's sketch width
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
+def test_sketch_256_columns_matches_oracle(method):
+    """k + l = 256 (the width used on the large window): multi-tile, multi-split
+    Gram products and a 256 x 256 one-sided Jacobi."""
+    cfg = AD_FFT.replace(k=240, l=16)
+    _, S, p, _ = setup("ad_fft")
+    k, m = cfg.k, cfg.K
+    G = inputs.probes(21, cfg.nA, m)
+    w.wc4d_sketch(S.ctx, w.METHODS[method], k, m - k, cfg.q_power, 0, dev(G), w.FP64)
+    fn = {"revd": lambda: oracle.revd(p, k, G, q=cfg.q_power), "nystrom": lambda: oracle.nystrom(p, k, G),
+          "ritzit": lambda: oracle.ritzit(p, k, G)}[method]
+    Uo, tho = fn()
+    U = torch.zeros(k, cfg.nA, dtype=torch.float64, device="cuda")
+    th = w.wc4d_get_ritz(S.ctx, U, k)
+    # the top Ritz values are well separated; the tail of 240 values near 1 is not
+    assert np.allclose(th[:40], tho[:40], rtol=1e-10)
+    assert np.allclose(th, tho, rtol=1e-8, atol=1e-8)
+    w.wc4d_sketch(S.ctx, w.METHODS[method], k, m - k, cfg.q_power, 0, dev(G), w.MIXED)
+    th32 = w.wc4d_get_ritz(S.ctx, U, k)
+    assert np.allclose(th32[:40], tho[:40], rtol=1e-4)
