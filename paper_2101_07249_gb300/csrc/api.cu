@@ -214,7 +214,8 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->spec32[0], &c->spec32[1], &c->row64[0], &c->row64[1], &c->row32[0], &c->row32[1],
                       &c->tw64, &c->tw32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
-                      &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32};
+                      &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
+                      &c->tc_part, &c->tc_err};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
@@ -445,10 +446,8 @@ static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allo
         return check_launch(c, "l96 tlm sweep");
     }
     if constexpr (sizeof(T) == 4) {
-        if (allow_tc && tc_sweep_supported(c, K)) {
-            ProfScope ps(c, PROF_TC);
-            if (tc_sweep_forward(c, K, (float *)W, ld)) return check_launch(c, "tc forward sweep");
-        }
+        if (allow_tc && tc_sweep_supported(c, K) && tc_sweep_forward(c, K, (float *)W, ld))
+            return check_launch(c, "tc forward sweep");
     }
     Epi e{0, 1.0, 1.0, 0.0, 1};
     for (int t = 0; t < N; ++t) {
@@ -471,10 +470,8 @@ static wc4d_status adjoint_obs_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool 
         return check_launch(c, "l96 adjoint sweep");
     }
     if constexpr (sizeof(T) == 4) {
-        if (allow_tc && tc_sweep_supported(c, K)) {
-            ProfScope ps(c, PROF_TC);
-            if (tc_sweep_adjoint(c, K, (float *)W, ld)) return check_launch(c, "tc adjoint sweep");
-        }
+        if (allow_tc && tc_sweep_supported(c, K) && tc_sweep_adjoint(c, K, (float *)W, ld))
+            return check_launch(c, "tc adjoint sweep");
     }
     launch_obs_block<T>(c->stream, n, K, W + (int64_t)N * n, ld, obs_scale(c, N), c->prob.obs_stride);
     for (int t = N - 1; t >= 0; --t) {

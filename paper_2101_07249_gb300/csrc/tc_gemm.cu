@@ -1,6 +1,401 @@
-// Tensor-core (tcgen05) sweep products for the mixed-precision dense model.
+// Tensor-core sweep products of the mixed path on sm_103a: for each
+// subwindow t, C_t = M_t W_t (forward, L^{-1}) or C_t = M_t^T W_{t+1}
+// (adjoint, L^{-T}), with M_t an n x n FP32 propagator and W a block of K
+// probe columns, as TF32 tcgen05.mma with FP32 accumulation in tensor memory.
+//
+// One CTA computes a 128-row block of C for all K columns over one K-range
+// (split-K across blockIdx.y so that n/128 x splits CTAs fill the 152 SMs):
+//   warp 0 lane 0: TMA producer, 4-stage shared-memory ring (128B swizzle),
+//   warp 1 lane 0: MMA issuer (M = 128, N = K, 4 x K = 8 per 32-float stage),
+//   warps 0-3    : epilogue, tensor memory -> registers -> FP32 partials.
+// A second kernel sums the split partials in fixed order and applies the
+// sweep epilogue (W_{t+1} += M_t W_t, or W_t = obs(W_t) + M_t^T W_{t+1}).
+// Every wait is bounded: on a timeout the CTA records an error, drains its
+// own copies with a bounded wait, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "wc4d_internal.cuh"
 
-bool tc_sweep_supported(const wc4d_ctx *, int) { return false; }
-bool tc_sweep_forward(wc4d_ctx *, int, float *, int64_t) { return false; }
-bool tc_sweep_adjoint(wc4d_ctx *, int, float *, int64_t) { return false; }
+namespace {
+
+constexpr int BM = 128;               // rows of C per CTA (MMA M)
+constexpr int BKF = 32;               // floats per stage along the reduction (128 bytes)
+constexpr int STAGES = 4;
+constexpr int A_STAGE_BYTES = BM * BKF * 4;          // 16 KiB
+constexpr int MAX_N = 256;                           // MMA N (probe columns)
+constexpr int B_STAGE_BYTES_MAX = MAX_N * BKF * 4;   // 32 KiB
+constexpr int SMEM_BYTES = 1024 + STAGES * (A_STAGE_BYTES + B_STAGE_BYTES_MAX) + 256;
+constexpr unsigned SPIN_LIMIT = 1u << 24;           // bounded waits (~seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded parity wait; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t addr = smem_u32(bar);
+    for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout written by TMA: rows of 128 bytes, 8-row groups 1024 bytes
+// apart (stride byte offset), descriptor version 1, swizzle mode 128B.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128B swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N.
+__device__ __forceinline__ uint32_t idesc_tf32(int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct TcArgs {
+    int n;          // rows of C and of M (multiple of 128)
+    int K;          // probe columns = MMA N (multiple of 16, <= 256)
+    int kchunk;     // reduction range per split (multiple of 32)
+    int a_row0;     // first row of this subwindow's propagator in the A map
+    int b_x0;       // first row of the source time block in the B map
+    float *part;    // [split][K][n] FP32 partial sums
+    int *err;       // set on a timeout
+};
+
+__global__ void __launch_bounds__(128, 1)
+k_tc_sweep(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int b_stage_bytes = a.K * BKF * 4;
+    unsigned char *sA = base;
+    unsigned char *sB = base + STAGES * A_STAGE_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_STAGE_BYTES_MAX);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ int failed;
+    __shared__ int n_issued, n_consumed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    const int kbeg = blockIdx.y * a.kchunk;
+    const int nk = a.kchunk / BKF;
+    const uint32_t ncols = 256;   // tensor-memory columns (power of two >= K)
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        n_issued = 0;
+        n_consumed = 0;
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES, round = kb / STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) { failed = 1; break; }
+            mbar_expect_tx(&full[s], A_STAGE_BYTES + b_stage_bytes);
+            const int kx = kbeg + kb * BKF;
+            tma_load_2d(sA + s * A_STAGE_BYTES, &tmA, kx, a.a_row0 + m0, &full[s]);
+            tma_load_2d(sB + s * B_STAGE_BYTES_MAX, &tmB, a.b_x0 + kx, 0, &full[s]);
+            n_issued = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_tf32(a.K);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES, round = kb / STAGES;
+            if (!mbar_wait(&full[s], round & 1)) { failed = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_addr = smem_u32(sA + s * A_STAGE_BYTES);
+            const uint32_t b_addr = smem_u32(sB + s * B_STAGE_BYTES_MAX);
+#pragma unroll
+            for (int kk = 0; kk < BKF / 8; ++kk)
+                mma_tf32(tmem, smem_desc_sw128(a_addr + kk * 32), smem_desc_sw128(b_addr + kk * 32), idesc,
+                         (kb | kk) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            n_consumed = kb + 1;
+        }
+        mma_commit(done);
+    }
+    __syncthreads();
+    // epilogue: all four warps; warp w owns tensor-memory lanes 32w .. 32w+31.
+    // The decision to read tensor memory is uniform per warp (tcgen05.ld is
+    // a warp-collective instruction).
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0) ? 1 : 0) && !failed;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        float *dst = a.part + ((size_t)blockIdx.y * a.K) * a.n + row;
+        for (int c0 = 0; c0 < a.K; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (c0 + j < a.K) dst[(size_t)(c0 + j) * a.n] = __uint_as_float(r[j]);
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        // drain the copies this CTA issued but never consumed (bounded)
+        for (int kb = n_consumed; kb < n_issued; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// C(i, j) = epi(sum_s part[s][j][i]) over the n x K output block.
+__global__ void __launch_bounds__(256)
+k_tc_reduce(int n, int K, int splits, const float *__restrict__ part, float *C, int64_t ldc, Epi e)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * K) return;
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    float acc = 0.f;
+    for (int s = 0; s < splits; ++s) acc += part[((int64_t)s * K + j) * n + i];
+    float *dst = C + (int64_t)j * ldc + i;
+    float out;
+    if (e.mode == 1) out = acc + ((i % e.obs_stride == 0) ? (float)e.obs_scale * (*dst) : 0.f);
+    else out = (float)e.alpha * acc + (e.beta != 0.0 ? (float)e.beta * (*dst) : 0.f);
+    *dst = out;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2D FP32 tensor map: inner dimension `inner` (contiguous), `outer` rows
+// `stride_elems` apart; box 32 x box_rows, 128-byte swizzle.
+bool make_map(CUtensorMap *map, const float *ptr, uint64_t inner, uint64_t outer, uint64_t stride_elems,
+              uint32_t box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {stride_elems * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)BKF, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int g_tc_enabled = -1;   // -1 unknown, 0 off, 1 on
+
+bool device_ok(const wc4d_ctx *c)
+{
+    if (g_tc_enabled < 0) {
+        int major = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+        const char *env = getenv("WC4D_NO_TC");
+        g_tc_enabled = (major == 10 && !(env && env[0] == '1') && encode_fn() != nullptr) ? 1 : 0;
+        if (g_tc_enabled)
+            cudaFuncSetAttribute(k_tc_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    }
+    return g_tc_enabled == 1;
+}
+
+// Split-K factor: as many CTAs as fit on the SMs, each with >= 256 reduction
+// columns (8 stages, so the 4-stage ring is reused).
+int choose_splits(const wc4d_ctx *c, int n)
+{
+    const int blocks = n / BM;
+    int best = 1;
+    for (int s = 1; s <= 16; ++s) {
+        if (n % (s * BKF) != 0 || n / s < 256) continue;
+        if (blocks * s <= c->num_sms) best = s;
+    }
+    return best;
+}
+
+// One subwindow product: part = M_blk(rows a_row0..) x W(rows b_x0..), then
+// C = epi(part) (C column-major, ldc).
+bool tc_product(wc4d_ctx *c, const CUtensorMap &mA, const CUtensorMap &mB, int K, int a_row0, int b_x0, float *C,
+                int64_t ldc, const Epi &e, int splits, float *part, int *err)
+{
+    const int n = c->prob.n;
+    TcArgs args{n, K, n / splits, a_row0, b_x0, part, err};
+    dim3 grid(n / BM, splits);
+    {
+        ProfScope ps(c, PROF_TC);
+        WC4D_LAUNCH(k_tc_sweep<<<grid, 128, SMEM_BYTES, c->stream>>>(mA, mB, args));
+    }
+    const int64_t tot = (int64_t)n * K;
+    WC4D_LAUNCH(k_tc_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(n, K, splits, part, C, ldc, e));
+    return true;
+}
+
+}  // namespace
+
+// Shapes the tensor-core path handles: dense model, n a multiple of 128,
+// K a multiple of 16 up to 256, on a compute capability 10.x device.
+bool tc_sweep_supported(const wc4d_ctx *c, int K)
+{
+    if (c->prob.model != WC4D_MODEL_DENSE || !c->have_M32) return false;
+    if (c->prob.n % BM != 0 || K < 16 || K > MAX_N || K % 16 != 0) return false;
+    return device_ok(c);
+}
+
+static bool tc_prepare(wc4d_ctx *c, int K, float *W, int64_t ld, const float *Mbase, CUtensorMap *mA,
+                       CUtensorMap *mB, int *splits, float **part, int **err)
+{
+    const int n = c->prob.n;
+    if (ld % 4 != 0 || ((uintptr_t)W & 15u) != 0) return false;
+    if (!make_map(mA, Mbase, (uint64_t)n, (uint64_t)c->nM * n, (uint64_t)n, BM)) return false;
+    if (!make_map(mB, W, (uint64_t)c->nA, (uint64_t)K, (uint64_t)ld, (uint32_t)K)) return false;
+    *splits = choose_splits(c, n);
+    if (ensure(c, c->tc_part, sizeof(float) * (size_t)(*splits) * K * n) != WC4D_OK) return false;
+    if (ensure(c, c->tc_err, sizeof(int)) != WC4D_OK) return false;
+    *part = reinterpret_cast<float *>(c->tc_part.p);
+    *err = reinterpret_cast<int *>(c->tc_err.p);
+    return true;
+}
+
+// W_{t+1} += M_t W_t for t = 0..N-1.
+bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld)
+{
+    CUtensorMap mA, mB;
+    int splits;
+    float *part;
+    int *err;
+    if (!tc_prepare(c, K, W, ld, reinterpret_cast<const float *>(c->M32.p), &mA, &mB, &splits, &part, &err))
+        return false;
+    const int n = c->prob.n, N = c->prob.N;
+    Epi e{0, 1.0, 1.0, 0.0, 1};
+    for (int t = 0; t < N; ++t) {
+        const int blk = (c->nM == 1) ? 0 : t;
+        tc_product(c, mA, mB, K, blk * n, t * n, W + (int64_t)(t + 1) * n, ld, e, splits, part, err);
+    }
+    return true;
+}
+
+// W_N = obs_N(W_N); W_t = obs_t(W_t) + M_t^T W_{t+1} for t = N-1..0.
+bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld)
+{
+    CUtensorMap mA, mB;
+    int splits;
+    float *part;
+    int *err;
+    if (!tc_prepare(c, K, W, ld, reinterpret_cast<const float *>(c->MT32.p), &mA, &mB, &splits, &part, &err))
+        return false;
+    const int n = c->prob.n, N = c->prob.N;
+    const wc4d_problem &p = c->prob;
+    auto obs_scale = [&](int t) {
+        const int ts = p.obs_tstride > 0 ? p.obs_tstride : 1;
+        return (t >= p.obs_t0 && (t - p.obs_t0) % ts == 0) ? 1.0 / p.sigma_o2 : 0.0;
+    };
+    launch_obs_block<float>(c->stream, n, K, W + (int64_t)N * n, ld, obs_scale(N), p.obs_stride);
+    for (int t = N - 1; t >= 0; --t) {
+        const int blk = (c->nM == 1) ? 0 : t;
+        Epi e{1, 1.0, 0.0, obs_scale(t), p.obs_stride};
+        tc_product(c, mA, mB, K, blk * n, (t + 1) * n, W + (int64_t)t * n, ld, e, splits, part, err);
+    }
+    return true;
+}
+
+// Error flag of the tensor-core kernels (1 after a timed-out wait); cleared on read.
+int tc_read_error(wc4d_ctx *c)
+{
+    if (!c->tc_err.p) return 0;
+    int h = 0;
+    cudaMemcpyAsync(&h, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (h) cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream);
+    return h;
+}

@@ -94,6 +94,9 @@ struct wc4d_ctx {
     // PCG vectors
     DevBuf pcg64[8], pcg32[8];
 
+    // tensor-core sweeps: split partials and the error flag of bounded waits
+    DevBuf tc_part, tc_err;
+
     // Ritz pairs
     int kU = 0;
     DevBuf U64, U32, theta64, c64, c32;
