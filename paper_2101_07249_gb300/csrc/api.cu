@@ -422,6 +422,7 @@ template <> struct Ops<float> {
 // Dense-model sweeps on tensor cores (tc_gemm.cu); returns false when the
 // shape is not supported so the SIMT path is taken.
 bool tc_sweep_supported(const wc4d_ctx *c, int K);
+int tc_read_error(wc4d_ctx *c);
 bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld);
 bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld);
 
@@ -495,6 +496,10 @@ static wc4d_status hvp_impl(wc4d_ctx *c, const T *X, T *Y, int K, int64_t ld, bo
     WC4D_TRY(adjoint_obs_sweep<T>(c, K, W, nA, allow_tc));              // W = L^{-T} H^T R^{-1} H W
     WC4D_TRY(apply_circ<T>(c, K, W, nA, Y, ld, X, ld));                 // Y = X + D^{1/2} W
     c->hvp_count++;
+    if constexpr (sizeof(T) == 4) {
+        if (allow_tc && tc_sweep_supported(c, K) && tc_read_error(c))
+            return set_err(c, WC4D_ETIMEOUT, "tensor-core sweep: a bounded wait timed out");
+    }
     return WC4D_OK;
 }
 
