@@ -342,6 +342,10 @@ static bool tc_prepare(wc4d_ctx *c, int K, float *W, int64_t ld, const float *Mb
     *splits = choose_splits(c, n);
     if (ensure(c, c->tc_part, sizeof(float) * (size_t)(*splits) * K * n) != WC4D_OK) return false;
     if (ensure(c, c->tc_err, sizeof(int)) != WC4D_OK) return false;
+    if (!c->tc_err_zeroed) {   // device allocations are not zero-initialised
+        if (cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream) != cudaSuccess) return false;
+        c->tc_err_zeroed = true;
+    }
     *part = reinterpret_cast<float *>(c->tc_part.p);
     *err = reinterpret_cast<int *>(c->tc_err.p);
     return true;
@@ -392,7 +396,7 @@ bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld)
 // Error flag of the tensor-core kernels (1 after a timed-out wait); cleared on read.
 int tc_read_error(wc4d_ctx *c)
 {
-    if (!c->tc_err.p) return 0;
+    if (!c->tc_err.p || !c->tc_err_zeroed) return 0;
     int h = 0;
     cudaMemcpyAsync(&h, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaStreamSynchronize(c->stream);

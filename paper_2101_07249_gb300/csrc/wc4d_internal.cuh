@@ -96,6 +96,7 @@ struct wc4d_ctx {
 
     // tensor-core sweeps: split partials and the error flag of bounded waits
     DevBuf tc_part, tc_err;
+    bool tc_err_zeroed = false;
 
     // Ritz pairs
     int kU = 0;
