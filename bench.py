@@ -294,12 +294,13 @@ def main():
     dom = max(classes, key=lambda k: classes[k]["ms"]) if classes else None
     roof = None
     n = cfg.n
-    if dom == "gemv":
-        bytes_per = 4 * n * n + 3 * 4 * n                       # FP32 propagator + x, C_old, C
+    if dom == "gemv_sweep":
+        # one timed group = one persistent launch of all N subwindow GEMVs
+        bytes_per = cfg.N * (4 * n * n + 3 * 4 * n)           # FP32 propagators + x, C_old, C
         ach = bytes_per / (classes[dom]["avg_us"] * 1e-6) / 1e9
-        tr = NCU_TRAFFIC.get(("gemv_f32", cfg.name))
+        tr = NCU_TRAFFIC.get(("gemv_sweep_f32", cfg.name))
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": tr, "kernel": "k_gemv_rows<float> (sweep GEMV, one probe column)",
+                "traffic": tr, "kernel": "k_gemv_sweep<float> (persistent one-column sweep, N GEMVs per launch)",
                 "algorithmic_bytes_per_launch": bytes_per, "peak_source": peak_src}
     elif dom in ("gemm", "tc_gemm"):
         flops = 2.0 * n * n * K

@@ -212,10 +212,12 @@ int64_t     wc4d_launch_count(int32_t reset);
  * wc4d_profile(ctx, 1) clears the log and starts recording an event pair
  * around every launch group of the classes below; wc4d_profile_read
  * synchronises and returns the summed device time (ms) and the number of
- * timed groups of one class.  Classes: 0 sweep GEMV (one probe column),
- * 1 sweep SIMT GEMM, 2 sweep tensor-core GEMM, 3 D^{1/2} circulant,
- * 4 LMP application, 5 Gram products, 6 other dense LA, 7 Lorenz-96
- * tangent-linear sweep, 8 Lorenz-96 adjoint sweep, 9 PCG vector kernels. */
+ * timed groups of one class.  Classes: 0 FP32 one-column sweep (all N
+ * subwindow GEMVs of L^{-1} or L^{-T} in one group), 1 sweep SIMT GEMM,
+ * 2 sweep tensor-core GEMM (one subwindow), 3 D^{1/2} circulant, 4 LMP
+ * application, 5 Gram products, 6 other dense LA, 7 Lorenz-96 tangent-
+ * linear sweep, 8 Lorenz-96 adjoint sweep, 9 PCG vector kernels, 10 FP64
+ * one-column sweep. */
 wc4d_status wc4d_profile(wc4d_ctx *ctx, int32_t enable);
 wc4d_status wc4d_profile_read(wc4d_ctx *ctx, int32_t cls, double *total_ms, int64_t *launch_groups);
 /* Allocation-free spectral-LMP application, y = C v (the paper has no

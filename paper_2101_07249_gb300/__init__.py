@@ -83,7 +83,8 @@ _SIGS = {
     "wc4d_profile_read": (C.c_int, [_V, C.c_int32, _D, C.POINTER(C.c_int64)]),
     "wc4d_lmp_apply_static": (C.c_int, [_V, _V, C.c_int32, C.c_int64, _V, _V, _V]),
 }
-PROF_CLASSES = ("gemv", "gemm", "tc_gemm", "circulant", "lmp", "gram", "la", "l96_tlm", "l96_adj", "pcg_vec")
+PROF_CLASSES = ("gemv_sweep", "gemm", "tc_gemm", "circulant", "lmp", "gram", "la", "l96_tlm", "l96_adj", "pcg_vec",
+                "gemv_sweep_f64")
 EXPORTS = tuple(_SIGS)
 
 _lock = threading.Lock()

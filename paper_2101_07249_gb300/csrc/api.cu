@@ -215,7 +215,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->tw64, &c->tw32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
-                      &c->tc_part, &c->tc_err};
+                      &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
@@ -436,6 +436,37 @@ static wc4d_status apply_circ(wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y,
     return check_launch(c, "circulant");
 }
 
+// One-column dense sweeps as one persistent launch; false = not applicable.
+template <typename T>
+static bool persistent_sweep(wc4d_ctx *c, T *W, int mode)
+{
+    if (c->prob.model != WC4D_MODEL_DENSE || getenv("WC4D_NO_PERSISTENT")) return false;
+    if (ensure(c, c->sweep_bar, 4 * sizeof(unsigned)) != WC4D_OK) return false;
+    unsigned *bar = P<unsigned>(c->sweep_bar);
+    if (!c->sweep_bar_zeroed) {   // [2] is the error flag, kept until read
+        if (cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), c->stream) != cudaSuccess) return false;
+        c->sweep_bar_zeroed = true;
+    }
+    if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess) return false;
+    const int n = c->prob.n;
+    const int64_t mstride = (c->nM == 1) ? 0 : (int64_t)n * n;
+    const T *M0 = (mode == 0) ? Ops<T>::M(c, 0) : Ops<T>::MT(c, 0);
+    return launch_gemv_sweep<T>(c->stream, c->num_sms, n, c->prob.N, M0, mstride, W, mode, 1.0 / c->prob.sigma_o2,
+                                c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride,
+                                bar, reinterpret_cast<int *>(bar + 2));
+}
+
+// Timeout flag of the persistent sweeps (cleared on read).
+static int sweep_error(wc4d_ctx *c)
+{
+    if (!c->sweep_bar.p || !c->sweep_bar_zeroed) return 0;
+    int h = 0;
+    cudaMemcpyAsync(&h, P<unsigned>(c->sweep_bar) + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (h) cudaMemsetAsync(P<unsigned>(c->sweep_bar) + 2, 0, sizeof(int), c->stream);
+    return h;
+}
+
 // W (nA x K, ld) <- L^{-1} W in place: W_{t+1} += M_t W_t.
 template <typename T>
 static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allow_tc)
@@ -449,6 +480,10 @@ static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allo
     if constexpr (sizeof(T) == 4) {
         if (allow_tc && tc_sweep_supported(c, K) && tc_sweep_forward(c, K, (float *)W, ld))
             return check_launch(c, "tc forward sweep");
+    }
+    if (K == 1) {
+        ProfScope ps(c, sizeof(T) == 4 ? PROF_GEMV : PROF_GEMV64);
+        if (persistent_sweep<T>(c, W, 0)) return check_launch(c, "forward sweep");
     }
     Epi e{0, 1.0, 1.0, 0.0, 1};
     for (int t = 0; t < N; ++t) {
@@ -475,6 +510,10 @@ static wc4d_status adjoint_obs_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool 
             return check_launch(c, "tc adjoint sweep");
     }
     launch_obs_block<T>(c->stream, n, K, W + (int64_t)N * n, ld, obs_scale(c, N), c->prob.obs_stride);
+    if (K == 1) {
+        ProfScope ps(c, sizeof(T) == 4 ? PROF_GEMV : PROF_GEMV64);
+        if (persistent_sweep<T>(c, W, 1)) return check_launch(c, "adjoint sweep");
+    }
     for (int t = N - 1; t >= 0; --t) {
         Epi e{1, 1.0, 0.0, obs_scale(c, t), c->prob.obs_stride};
         ProfScope ps(c, K == 1 ? PROF_GEMV : PROF_GEMM);
@@ -515,8 +554,11 @@ extern "C" wc4d_status wc4d_hvp(wc4d_ctx *c, const void *X, void *Y, int32_t K, 
     if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
     WC4D_TRY(require_operator(c));
     WC4D_TRY(prep_precision(c, precision));
-    if (precision == WC4D_FP64) return hvp_impl<double>(c, (const double *)X, (double *)Y, K, ld);
-    return hvp_impl<float>(c, (const float *)X, (float *)Y, K, ld);
+    wc4d_status st = (precision == WC4D_FP64) ? hvp_impl<double>(c, (const double *)X, (double *)Y, K, ld)
+                                              : hvp_impl<float>(c, (const float *)X, (float *)Y, K, ld);
+    if (st == WC4D_OK && K == 1 && sweep_error(c))
+        return set_err(c, WC4D_ETIMEOUT, "persistent sweep: a grid barrier timed out");
+    return st;
 }
 
 template <typename T>
@@ -939,6 +981,19 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     return st;
 }
 
+// Row-major, zero-padded copies of the Ritz vectors for the LMP kernels.
+static wc4d_status build_rowmajor_U(wc4d_ctx *c)
+{
+    const int k = c->kU, kp = (k + 3) / 4 * 4;
+    const int64_t nA = c->nA;
+    WC4D_TRY(ensure(c, c->Urm64, sizeof(double) * (size_t)nA * kp));
+    WC4D_TRY(ensure(c, c->Urm32, sizeof(float) * (size_t)nA * kp));
+    launch_to_rowmajor<double>(c->stream, nA, k, kp, P<double>(c->U64), P<double>(c->Urm64));
+    launch_to_rowmajor<float>(c->stream, nA, k, kp, P<float>(c->U32), P<float>(c->Urm32));
+    c->kp = kp;
+    return check_launch(c, "row-major U");
+}
+
 extern "C" wc4d_status wc4d_sketch(wc4d_ctx *c, int32_t method, int32_t k, int32_t l, int32_t q, uint64_t seed,
                                    const double *G, double *theta_host, int32_t precision)
 {
@@ -950,8 +1005,9 @@ extern "C" wc4d_status wc4d_sketch(wc4d_ctx *c, int32_t method, int32_t k, int32
     wc4d_status s = (precision == WC4D_FP64) ? sketch_impl<double>(c, method, k, l, q, seed, G)
                                              : sketch_impl<float>(c, method, k, l, q, seed, G);
     if (s != WC4D_OK) return s;
+    WC4D_TRY(build_rowmajor_U(c));
     if (theta_host) std::memcpy(theta_host, c->theta_host.data(), sizeof(double) * k);
-    return WC4D_OK;
+    return sync(c, "sketch");
 }
 
 extern "C" wc4d_status wc4d_get_ritz(wc4d_ctx *c, double *U, double *theta_host)
@@ -980,15 +1036,16 @@ extern "C" wc4d_status wc4d_set_ritz(wc4d_ctx *c, int32_t k, const double *U, co
     WC4D_TRY(check_launch(c, "set_ritz"));
     c->kU = k;
     c->theta_host.assign(theta_host, theta_host + k);
+    WC4D_TRY(build_rowmajor_U(c));
     return sync(c, "set_ritz");
 }
 
 // ============================================================================
 // Spectral LMP (eq. 16) and PCG (Alg. 1)
 // ============================================================================
-template <typename T> static T *Ubuf(wc4d_ctx *c);
-template <> double *Ubuf<double>(wc4d_ctx *c) { return P<double>(c->U64); }
-template <> float *Ubuf<float>(wc4d_ctx *c) { return P<float>(c->U32); }
+template <typename T> static T *Urm(wc4d_ctx *c);
+template <> double *Urm<double>(wc4d_ctx *c) { return P<double>(c->Urm64); }
+template <> float *Urm<float>(wc4d_ctx *c) { return P<float>(c->Urm32); }
 
 // y = C v (C^T = C for the closed form); skip: optional device flag
 template <typename T>
@@ -997,12 +1054,13 @@ static wc4d_status lmp_apply_impl(wc4d_ctx *c, const T *v, T *y, const int *skip
     const int k = c->kU;
     const int64_t nA = c->nA;
     ProfScope ps(c, PROF_LMP);
-    int splits = utv_splits(nA);
-    WC4D_TRY(ensure(c, c->part, sizeof(double) * ((size_t)splits * k + k) + 64));
-    launch_utv<T>(c->stream, c->num_sms, nA, k, Ubuf<T>(c), v, P<double>(c->part), &splits);
+    const int kp = c->kp;
+    int splits = utv_rm_splits(nA);
+    WC4D_TRY(ensure(c, c->part, sizeof(double) * ((size_t)splits * kp + kp) + 64));
+    launch_utv_rm<T>(c->stream, nA, kp, Urm<T>(c), v, P<double>(c->part), &splits);
     // the reduced t = U^T v sits after the partials
-    launch_lmp_combine<T>(c->stream, nA, k, Ubuf<T>(c), P<double>(c->part) + (size_t)splits * k, 1,
-                          P<double>(c->c64), 1.0, v, y, nullptr, nullptr, skip);
+    launch_lmp_combine_rm<T>(c->stream, c->num_sms, nA, k, kp, Urm<T>(c), P<double>(c->part) + (size_t)splits * kp,
+                             P<double>(c->c64), v, y, skip);
     return check_launch(c, "lmp apply");
 }
 
@@ -1092,6 +1150,7 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
     WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
     WC4D_TRY(sync(c, "pcg end"));
     out.done = hflags[0] != 0 || stagnated;
+    if (sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep: a grid barrier timed out");
     out.breakdown = hflags[1];
     out.iters = hflags[2];
     out.relres_rec = hs[4];

@@ -484,6 +484,158 @@ template void launch_lmp_combine<float>(cudaStream_t, int64_t, int, const float 
                                         const double *, const int *);
 
 // ----------------------------------------------------------------------------
+// Row-major LMP kernels.  Urm is nA x kp row-major (kp = k rounded up to a
+// multiple of 4, zero columns beyond k), so that U^T v accumulates one column
+// per thread lane with coalesced vector loads of whole rows, and C v reduces
+// one row per warp.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void k_to_rowmajor(int64_t nA, int k, int kp, const T *__restrict__ U, T *Urm)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nA * kp) return;
+    int64_t r = idx / kp;
+    int i = (int)(idx % kp);
+    Urm[idx] = (i < k) ? U[(int64_t)i * nA + r] : (T)0;
+}
+
+template <typename T>
+void launch_to_rowmajor(cudaStream_t s, int64_t nA, int k, int kp, const T *U, T *Urm)
+{
+    WC4D_LAUNCH(k_to_rowmajor<T><<<ceil_div(nA * kp, 256), 256, 0, s>>>(nA, k, kp, U, Urm));
+}
+
+template void launch_to_rowmajor<double>(cudaStream_t, int64_t, int, int, const double *, double *);
+template void launch_to_rowmajor<float>(cudaStream_t, int64_t, int, int, const float *, float *);
+
+constexpr int RM_ROWS = 512;   // rows per CTA of the row-major U^T v
+
+// Four consecutive values with evict-first loads (one float4, or two double2).
+template <typename T> struct Quad { T x, y, z, w; };
+__device__ __forceinline__ Quad<float> ld4cs(const float *p)
+{
+    float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> ld4cs(const double *p)
+{
+    double2 a = __ldcs(reinterpret_cast<const double2 *>(p)), b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+
+// part[chunk][i] = sum over the chunk's rows of Urm[r, i] v[r].  Thread
+// (ty, tx): column group 4 (cb + tx) .. + 3, rows ty, ty + 4, ...; the loop
+// over 64-group column blocks is uniform across the CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) k_utv_rm(int64_t nA, int kp, const T *__restrict__ Urm,
+                                                const T *__restrict__ v, double *part)
+{
+    __shared__ T vs[RM_ROWS];
+    __shared__ double acc4[4][256];
+    const int64_t r0 = (int64_t)blockIdx.x * RM_ROWS;
+    const int rows = (int)min((int64_t)RM_ROWS, nA - r0);
+    for (int r = threadIdx.x; r < RM_ROWS; r += blockDim.x) vs[r] = (r < rows) ? v[r0 + r] : (T)0;
+    __syncthreads();
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int kq = kp / 4;
+    for (int cb = 0; cb < kq; cb += 64) {
+        const int cg = cb + tx;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        if (cg < kq) {
+            const T *base = Urm + r0 * kp + 4 * cg;
+            int r = ty;
+            for (; r + 12 < rows; r += 16) {
+                Quad<T> u0 = ld4cs(base + (int64_t)r * kp), u1 = ld4cs(base + (int64_t)(r + 4) * kp);
+                Quad<T> u2 = ld4cs(base + (int64_t)(r + 8) * kp), u3 = ld4cs(base + (int64_t)(r + 12) * kp);
+                T x0 = vs[r], x1 = vs[r + 4], x2 = vs[r + 8], x3 = vs[r + 12];
+                a0 = fma(u0.x, x0, a0); a1 = fma(u0.y, x0, a1); a2 = fma(u0.z, x0, a2); a3 = fma(u0.w, x0, a3);
+                a0 = fma(u1.x, x1, a0); a1 = fma(u1.y, x1, a1); a2 = fma(u1.z, x1, a2); a3 = fma(u1.w, x1, a3);
+                a0 = fma(u2.x, x2, a0); a1 = fma(u2.y, x2, a1); a2 = fma(u2.z, x2, a2); a3 = fma(u2.w, x2, a3);
+                a0 = fma(u3.x, x3, a0); a1 = fma(u3.y, x3, a1); a2 = fma(u3.z, x3, a2); a3 = fma(u3.w, x3, a3);
+            }
+            for (; r < rows; r += 4) {
+                Quad<T> u = ld4cs(base + (int64_t)r * kp);
+                T x = vs[r];
+                a0 = fma(u.x, x, a0); a1 = fma(u.y, x, a1); a2 = fma(u.z, x, a2); a3 = fma(u.w, x, a3);
+            }
+        }
+        acc4[ty][4 * tx + 0] = (double)a0;
+        acc4[ty][4 * tx + 1] = (double)a1;
+        acc4[ty][4 * tx + 2] = (double)a2;
+        acc4[ty][4 * tx + 3] = (double)a3;
+        __syncthreads();
+        if (ty == 0 && cg < kq) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * tx + q;
+                part[(int64_t)blockIdx.x * kp + 4 * cg + q] = acc4[0][j] + acc4[1][j] + acc4[2][j] + acc4[3][j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int utv_rm_splits(int64_t nA) { return ceil_div(nA, RM_ROWS); }
+
+// t = U^T v into part[S*kp .. S*kp + kp) (partials first).
+template <typename T>
+void launch_utv_rm(cudaStream_t s, int64_t nA, int kp, const T *Urm, const T *v, double *part, int *splits)
+{
+    const int S = utv_rm_splits(nA);
+    WC4D_LAUNCH(k_utv_rm<T><<<S, 256, 0, s>>>(nA, kp, Urm, v, part));
+    WC4D_LAUNCH(k_reduce_part<<<ceil_div(kp, 256), 256, 0, s>>>(S, kp, kp, 0, part, part + (int64_t)S * kp));
+    *splits = S;
+}
+
+template void launch_utv_rm<double>(cudaStream_t, int64_t, int, const double *, const double *, double *, int *);
+template void launch_utv_rm<float>(cudaStream_t, int64_t, int, const float *, const float *, double *, int *);
+
+// y[r] = v[r] - sum_i Urm[r, i] c_i t_i; one warp per row, lanes over the
+// kp/4 vector groups of the row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lmp_combine_rm(int64_t nA, int k, int kp, const T *__restrict__ Urm,
+                                                        const double *__restrict__ t, const double *__restrict__ cvec,
+                                                        const T *v, T *y, const int *skip)
+{
+    extern __shared__ double ctd[];
+    if (skip && *skip) return;
+    T *ct = reinterpret_cast<T *>(ctd);
+    for (int i = threadIdx.x; i < kp; i += blockDim.x) ct[i] = (i < k) ? (T)(cvec[i] * t[i]) : (T)0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int kq = kp / 4;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nA; r += warps) {
+        const T *row = Urm + r * kp;
+        T acc = 0;
+        for (int g = lane; g < kq; g += 32) {
+            Quad<T> u = ld4cs(row + 4 * g);
+            acc = fma(u.x, ct[4 * g], acc);
+            acc = fma(u.y, ct[4 * g + 1], acc);
+            acc = fma(u.z, ct[4 * g + 2], acc);
+            acc = fma(u.w, ct[4 * g + 3], acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[r] = v[r] - acc;
+    }
+}
+
+template <typename T>
+void launch_lmp_combine_rm(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const double *t,
+                           const double *cvec, const T *v, T *y, const int *skip)
+{
+    int grid = std::min<int64_t>((int64_t)num_sms * 8, ceil_div(nA, 8));
+    WC4D_LAUNCH(k_lmp_combine_rm<T><<<grid, 256, (size_t)kp * sizeof(double), s>>>(nA, k, kp, Urm, t, cvec, v, y,
+                                                                                      skip));
+}
+
+template void launch_lmp_combine_rm<double>(cudaStream_t, int, int64_t, int, int, const double *, const double *,
+                                            const double *, const double *, double *, const int *);
+template void launch_lmp_combine_rm<float>(cudaStream_t, int, int64_t, int, int, const float *, const double *,
+                                           const double *, const float *, float *, const int *);
+
+// ----------------------------------------------------------------------------
 // PCG (Alg. 1) vector and scalar kernels.  Scalars live in device memory:
 // scal[0] rho = rhat^T rhat, [1] alpha, [2] beta, [3] |b|, [4] |r|/|b|,
 // [5] p^T A p, [6] |r|^2; flags[0] done, [1] breakdown, [2] iterations.

@@ -345,6 +345,165 @@ k_gemv_scalar(int n, const T *__restrict__ M, const T *__restrict__ x, T *y, Epi
 template <typename T>
 static bool aligned16(const T *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// ----------------------------------------------------------------------------
+// Persistent one-column sweep (the PCG matvec): all N subwindow GEMVs of
+// L^{-1} (mode 0) or of L^{-T} with the observation term (mode 1) in one
+// cooperative launch.  CTA b owns a fixed slice of rows of every M_t; after
+// its rows of step t are written it prefetches its rows of M_{t+1} into L2
+// and waits at a bounded grid barrier.  Vectors written by other SMs are read
+// through L2 (ld.global.cg), never through the non-coherent L1.
+// ----------------------------------------------------------------------------
+struct SweepArgs {
+    int n, N;
+    int64_t mstride;      // elements between consecutive subwindow propagators (0: shared)
+    int mode;             // 0 forward, 1 adjoint with observations
+    double obs_inv;       // 1 / sigma_o^2
+    int obs_stride, t0, ts;
+    int rows_per_cta;     // multiple of 2
+    unsigned *bar;        // [0] arrival count, [1] generation
+    int *err;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned it = 0;
+            while (*gen == g) {
+                if (++it > (1u << 26)) { ok = 0; atomicExch(err, 1); break; }
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(512)
+k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
+{
+    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    constexpr int VEC = sizeof(V) / sizeof(T), UNR = 4;
+    const int n = a.n, nv = n / VEC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int rbeg = blockIdx.x * a.rows_per_cta;
+    const int rend = min(n, rbeg + a.rows_per_cta);
+    for (int step = 0; step < a.N; ++step) {
+        const int t = (a.mode == 0) ? step : a.N - 1 - step;
+        const T *M = M0 + (int64_t)t * a.mstride;
+        const T *x = W + (int64_t)((a.mode == 0) ? t : t + 1) * n;       // source block
+        T *y = W + (int64_t)((a.mode == 0) ? t + 1 : t) * n;             // target block
+        const V *x4 = reinterpret_cast<const V *>(x);
+        double scale = 0.0;
+        if (a.mode == 1 && t >= a.t0 && (t - a.t0) % a.ts == 0) scale = a.obs_inv;
+        for (int r0 = rbeg + 2 * warp; r0 < rend; r0 += 2 * nwarps) {
+            const V *ra = reinterpret_cast<const V *>(M + (int64_t)r0 * n);
+            const V *rb = reinterpret_cast<const V *>(M + (int64_t)min(r0 + 1, n - 1) * n);
+            Acc acc0 = 0, acc1 = 0;
+            for (int c0 = lane; c0 < nv; c0 += 32 * UNR) {
+                V av[UNR], bv[UNR], xv[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    const int idx = c0 + 32 * u;
+                    if (idx < nv) { xv[u] = __ldcg(x4 + idx); av[u] = __ldcs(ra + idx); bv[u] = __ldcs(rb + idx); }
+                }
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    if (c0 + 32 * u < nv) {
+                        const T *xf = reinterpret_cast<const T *>(&xv[u]);
+                        const T *af = reinterpret_cast<const T *>(&av[u]);
+                        const T *bf = reinterpret_cast<const T *>(&bv[u]);
+#pragma unroll
+                        for (int q = 0; q < VEC; ++q) {
+                            acc0 = fma((Acc)af[q], (Acc)xf[q], acc0);
+                            acc1 = fma((Acc)bf[q], (Acc)xf[q], acc1);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+            }
+            if (lane < 2 && r0 + lane < rend) {
+                const int row = r0 + lane;
+                const Acc sum = lane ? acc1 : acc0;
+                const Acc old = (Acc)__ldcg(y + row);
+                Acc out;
+                if (a.mode == 0) out = old + sum;
+                else out = sum + ((row % a.obs_stride == 0) ? (Acc)scale * old : (Acc)0);
+                y[row] = (T)out;
+            }
+        }
+        if (step + 1 < a.N) {
+            // pull this CTA's rows of the next propagator into L2 while waiting
+            const int tn = (a.mode == 0) ? step + 1 : a.N - 2 - step;
+            const char *nb = reinterpret_cast<const char *>(M0 + (int64_t)tn * a.mstride + (int64_t)rbeg * n);
+            const int64_t bytes = (int64_t)(rend - rbeg) * n * sizeof(T);
+            for (int64_t off = (int64_t)threadIdx.x * 128; off < bytes; off += (int64_t)blockDim.x * 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + off));
+            if (!grid_barrier(a.bar, gridDim.x, a.err)) return;
+        }
+    }
+}
+
+// Launch configuration of the persistent sweep (one CTA of 512 threads per
+// SM, co-resident by cooperative launch).  Returns false if it cannot be used.
+template <typename T>
+bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, int64_t mstride, T *W, int mode,
+                       double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err)
+{
+    constexpr int VEC = sizeof(T) == 8 ? 2 : 4;
+    if (n % VEC != 0 || !aligned16(M0) || !aligned16(W) || ((int64_t)n * sizeof(T)) % 16 != 0) return false;
+    using Acc = T;
+    static int max_blocks = -1;
+    if (max_blocks < 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_sweep<T, Acc>, 512, 0);
+        max_blocks = per_sm * num_sms;
+    }
+    int grid = std::min(num_sms, max_blocks);
+    if (grid < 1) return false;
+    SweepArgs args;
+    args.n = n;
+    args.N = N;
+    args.mstride = mstride;
+    args.mode = mode;
+    args.obs_inv = obs_inv;
+    args.obs_stride = obs_stride;
+    args.t0 = t0;
+    args.ts = ts > 0 ? ts : 1;
+    int rpc = (n + grid - 1) / grid;
+    rpc = (rpc + 1) / 2 * 2;
+    grid = (n + rpc - 1) / rpc;
+    args.rows_per_cta = rpc;
+    args.bar = bar;
+    args.err = err;
+    void *params[] = {(void *)&M0, (void *)&W, (void *)&args};
+    wc4d_note_launch();
+    return cudaLaunchCooperativeKernel((const void *)k_gemv_sweep<T, Acc>, dim3(grid), dim3(512), params, 0, s) ==
+           cudaSuccess;
+}
+
+template bool launch_gemv_sweep<double>(cudaStream_t, int, int, int, const double *, int64_t, double *, int, double,
+                                        int, int, int, unsigned *, int *);
+template bool launch_gemv_sweep<float>(cudaStream_t, int, int, int, const float *, int64_t, float *, int, double,
+                                       int, int, int, unsigned *, int *);
+
 template <typename T>
 void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
                        const Epi &e)

@@ -29,7 +29,7 @@ struct Epi {
 
 // Kernel classes timed with CUDA events when profiling is enabled.
 enum ProfId {
-    PROF_GEMV = 0,   // sweep GEMV (one probe column, dense propagator)
+    PROF_GEMV = 0,   // FP32 one-column sweeps (dense propagators)
     PROF_GEMM,       // sweep SIMT GEMM (probe blocks)
     PROF_TC,         // sweep tensor-core GEMM
     PROF_CIRC,       // D^{1/2} circulant (FFT or direct)
@@ -39,6 +39,7 @@ enum ProfId {
     PROF_L96_TLM,    // Lorenz-96 tangent-linear sweep
     PROF_L96_ADJ,    // Lorenz-96 adjoint sweep
     PROF_VEC,        // PCG vector kernels
+    PROF_GEMV64,     // FP64 one-column sweeps (true residuals, set-up)
     PROF_N
 };
 struct ProfEntry {
@@ -98,9 +99,15 @@ struct wc4d_ctx {
     DevBuf tc_part, tc_err;
     bool tc_err_zeroed = false;
 
+    // persistent one-column sweeps: grid barrier words and error flag
+    DevBuf sweep_bar;
+    bool sweep_bar_zeroed = false;
+
     // Ritz pairs
     int kU = 0;
+    int kp = 0;                     // kU rounded up to a multiple of 4
     DevBuf U64, U32, theta64, c64, c32;
+    DevBuf Urm64, Urm32;            // row-major nA x kp copies for the LMP kernels
     bool have_U32 = false;
     std::vector<double> theta_host;
 
@@ -172,6 +179,11 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
 template <typename T>
 void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
                        const Epi &e);
+// Persistent one-column sweep over all subwindows (cooperative launch);
+// bar: 2 zeroed unsigned (arrival count, generation); err set on a timeout.
+template <typename T>
+bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, int64_t mstride, T *W, int mode,
+                       double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err);
 template <typename T>
 void launch_obs_block(cudaStream_t s, int n, int K, T *W, int64_t ld, double scale, int stride);
 
@@ -206,6 +218,14 @@ void launch_lmp_combine(cudaStream_t s, int64_t nA, int k, const T *U, const dou
                         const double *cvec, double coef, const T *v, T *y, const T *add, const double *beta_dev,
                         const int *skip);
 void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c);
+template <typename T>
+void launch_to_rowmajor(cudaStream_t s, int64_t nA, int k, int kp, const T *U, T *Urm);
+int utv_rm_splits(int64_t nA);
+template <typename T>
+void launch_utv_rm(cudaStream_t s, int64_t nA, int kp, const T *Urm, const T *v, double *part, int *splits);
+template <typename T>
+void launch_lmp_combine_rm(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const double *t,
+                           const double *cvec, const T *v, T *y, const int *skip);
 
 // PCG vector kernels
 template <typename T>
