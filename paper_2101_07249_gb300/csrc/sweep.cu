@@ -381,7 +381,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, in
         } else {
             unsigned it = 0;
             while (*gen == g) {
-                if (++it > (1u << 26)) { ok = 0; atomicExch(err, 1); break; }
+                if (++it > (1u << 22)) { ok = 0; atomicExch(err, 1); break; }
             }
         }
         __threadfence();
@@ -495,8 +495,12 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     args.err = err;
     void *params[] = {(void *)&M0, (void *)&W, (void *)&args};
     wc4d_note_launch();
-    return cudaLaunchCooperativeKernel((const void *)k_gemv_sweep<T, Acc>, dim3(grid), dim3(512), params, 0, s) ==
-           cudaSuccess;
+    if (cudaLaunchCooperativeKernel((const void *)k_gemv_sweep<T, Acc>, dim3(grid), dim3(512), params, 0, s) !=
+        cudaSuccess) {
+        cudaGetLastError();   // fall back to one launch per subwindow
+        return false;
+    }
+    return true;
 }
 
 template bool launch_gemv_sweep<double>(cudaStream_t, int, int, int, const double *, int64_t, double *, int, double,
