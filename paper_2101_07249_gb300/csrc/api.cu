@@ -857,7 +857,14 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     if (method == WC4D_REVD || method == WC4D_NYSTROM) {
         // Y = A G; Z = orth(Y)  (+ q power iterations for REVD)
         if ((st = hvp_impl<T>(c, A_, B_, m, nA)) != WC4D_OK) return fail(st);
-        if ((st = cholqr2<T>(c, B_, nA, m, nA, D_, nullptr)) != WC4D_OK) return fail(st);
+        // A basis of span(A G) that only feeds the power iteration needs one
+        // CholeskyQR pass; the basis used for Rayleigh-Ritz gets two.
+        if (method == WC4D_REVD && q > 0) {
+            WC4D_TRY(ensure(c, c->small2, sizeof(double) * mm));
+            if ((st = cholqr_pass<T>(c, B_, nA, m, nA, D_, P<double>(c->small2))) != WC4D_OK) return fail(st);
+        } else if ((st = cholqr2<T>(c, B_, nA, m, nA, D_, nullptr)) != WC4D_OK) {
+            return fail(st);
+        }
         T *Z = B_, *Y = A_;
         if (method == WC4D_REVD)
             for (int it = 0; it < q; ++it) {
