@@ -441,19 +441,21 @@ template <typename T>
 static bool persistent_sweep(wc4d_ctx *c, T *W, int mode)
 {
     if (c->prob.model != WC4D_MODEL_DENSE || getenv("WC4D_NO_PERSISTENT")) return false;
-    if (ensure(c, c->sweep_bar, 4 * sizeof(unsigned)) != WC4D_OK) return false;
+    const int N = c->prob.N;
+    // layout: [0] error flag (kept until read), [1 .. N] step counters
+    if (ensure(c, c->sweep_bar, (size_t)(N + 1) * sizeof(unsigned)) != WC4D_OK) return false;
     unsigned *bar = P<unsigned>(c->sweep_bar);
-    if (!c->sweep_bar_zeroed) {   // [2] is the error flag, kept until read
-        if (cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), c->stream) != cudaSuccess) return false;
+    if (!c->sweep_bar_zeroed) {
+        if (cudaMemsetAsync(bar, 0, sizeof(unsigned), c->stream) != cudaSuccess) return false;
         c->sweep_bar_zeroed = true;
     }
-    if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess) return false;
+    if (cudaMemsetAsync(bar + 1, 0, (size_t)N * sizeof(unsigned), c->stream) != cudaSuccess) return false;
     const int n = c->prob.n;
     const int64_t mstride = (c->nM == 1) ? 0 : (int64_t)n * n;
     const T *M0 = (mode == 0) ? Ops<T>::M(c, 0) : Ops<T>::MT(c, 0);
     return launch_gemv_sweep<T>(c->stream, c->num_sms, n, c->prob.N, M0, mstride, W, mode, 1.0 / c->prob.sigma_o2,
                                 c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride,
-                                bar, reinterpret_cast<int *>(bar + 2));
+                                bar + 1, reinterpret_cast<int *>(bar));
 }
 
 // Timeout flag of the persistent sweeps (cleared on read).
@@ -461,9 +463,9 @@ static int sweep_error(wc4d_ctx *c)
 {
     if (!c->sweep_bar.p || !c->sweep_bar_zeroed) return 0;
     int h = 0;
-    cudaMemcpyAsync(&h, P<unsigned>(c->sweep_bar) + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&h, P<unsigned>(c->sweep_bar), sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaStreamSynchronize(c->stream);
-    if (h) cudaMemsetAsync(P<unsigned>(c->sweep_bar) + 2, 0, sizeof(int), c->stream);
+    if (h) cudaMemsetAsync(P<unsigned>(c->sweep_bar), 0, sizeof(int), c->stream);
     return h;
 }
 

@@ -180,7 +180,7 @@ template <typename T>
 void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
                        const Epi &e);
 // Persistent one-column sweep over all subwindows (cooperative launch);
-// bar: 2 zeroed unsigned (arrival count, generation); err set on a timeout.
+// bar: N zeroed unsigned (one arrival counter per step); err set on a timeout.
 template <typename T>
 bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, int64_t mstride, T *W, int mode,
                        double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err);
