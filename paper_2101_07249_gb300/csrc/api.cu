@@ -215,7 +215,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->tw64, &c->tw32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
-                      &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar};
+                      &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
@@ -315,6 +315,7 @@ extern "C" wc4d_status wc4d_set_propagator(wc4d_ctx *c, int32_t t, const double 
     if (t < 0 || c->nM == 1) c->have_M = true;
     else c->have_M = true;  // caller is responsible for setting every subwindow
     c->have_M32 = false;
+    c->have_Mtf = false;
     return WC4D_OK;
 }
 
@@ -333,6 +334,7 @@ extern "C" wc4d_status wc4d_build_advdiff_propagator(wc4d_ctx *c, double kappa, 
     WC4D_TRY(replicate_M(c));
     c->have_M = true;
     c->have_M32 = false;
+    c->have_Mtf = false;
     return sync(c, "build_advdiff");
 }
 
@@ -1092,12 +1094,9 @@ struct PcgOut {
 };
 
 // CG on A x = b from x = 0 in precision T; b, x device vectors of the context.
-// stag_window > 0: stop early when the running minimum of the recurrence
-// residual has not halved over the last stag_window iterations (used by the
-// FP32 rounds of the mixed path, whose attainable accuracy is limited).
 template <typename T>
 static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit, int force, bool use_lmp,
-                            double *qcf_dev, PcgOut &out, int stag_window = 0)
+                            double *qcf_dev, PcgOut &out)
 {
     const int64_t nA = c->nA;
     DevBuf *vb = (sizeof(T) == 8) ? c->pcg64 : c->pcg32;
@@ -1121,12 +1120,9 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
     launch_pcg_init(c->stream, grid, pa, pb, scal, flags);
     WC4D_TRY(check_launch(c, "pcg init"));
     int *hflags = P<int>(c->pinned);
-    double *hrel = reinterpret_cast<double *>(P<char>(c->pinned) + 64);
     const double tol_k = (force > 0) ? 0.0 : tol;
     const int nit = (force > 0) ? force : maxit;
     out = PcgOut();
-    std::vector<double> best;   // running minimum of the recurrence residual
-    bool stagnated = false;
     for (int it = 0; it < nit; ++it) {
         WC4D_TRY(hvp_impl<T>(c, p, q, 1, nA, false));                       // q = A p
         launch_dot_partial<T>(c->stream, grid, nA, p, q, pa);
@@ -1141,24 +1137,14 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
         launch_pcg_p<T>(c->stream, grid, nA, scal, p, tr);                  // p = C rhat + beta p
         WC4D_TRY(check_launch(c, "pcg iteration"));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
-        if (stag_window > 0)
-            WC4D_CUDA(c, cudaMemcpyAsync(hrel, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         WC4D_TRY(sync(c, "pcg iteration"));
         if (hflags[0]) break;
-        if (stag_window > 0) {
-            double bnow = best.empty() ? *hrel : std::min(best.back(), *hrel);
-            best.push_back(bnow);
-            if ((int)best.size() > stag_window && bnow > 0.5 * best[best.size() - 1 - stag_window]) {
-                stagnated = true;
-                break;
-            }
-        }
     }
     double hs[8];
     WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
     WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
     WC4D_TRY(sync(c, "pcg end"));
-    out.done = hflags[0] != 0 || stagnated;
+    out.done = hflags[0] != 0;
     if (sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep: a grid barrier timed out");
     out.breakdown = hflags[1];
     out.iters = hflags[2];
@@ -1191,6 +1177,107 @@ static wc4d_status true_residual(wc4d_ctx *c, const double *x, double *r64, doub
     return WC4D_OK;
 }
 
+// Mixed-precision CG with reliable updates (Sleijpen and van der Vorst,
+// "Reliable updated residuals in hybrid Bi-CG methods", Computing 56, 1996):
+// the recurrences of Alg. 1 run in FP32 on a correction d.  When the
+// recurrence residual has fallen by kReliableDelta since the last update, or
+// claims convergence, the FP64 solution absorbs d (x += d, d = 0) and the
+// FP32 residual is replaced by the FP64 true residual rhs - A x, while the
+// search direction p is kept.  Unlike restarted refinement this keeps the
+// Krylov space, so the iteration count stays close to the FP64 solver's.
+constexpr double kReliableDelta = 1e-2;
+
+static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, int force, bool use_lmp,
+                                double *qcf_dev, int *iters_out, double *rel_out, bool *breakdown_out)
+{
+    const int64_t nA = c->nA;
+    DevBuf *vb = c->pcg32;
+    for (int i = 0; i < 6; ++i) WC4D_TRY(ensure(c, vb[i], sizeof(float) * nA));
+    WC4D_TRY(ensure(c, c->pcg64[7], sizeof(double) * nA));
+    float *d = P<float>(vb[0]), *r = P<float>(vb[1]), *rh = P<float>(vb[2]), *p = P<float>(vb[3]);
+    float *q = P<float>(vb[4]), *t = P<float>(vb[5]);
+    double *r64 = P<double>(c->pcg64[7]);
+    const int grid = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA + 255) / 256));
+    WC4D_TRY(ensure(c, c->small1, sizeof(double) * 4 * 1024));
+    double *pa = P<double>(c->small1), *pb = pa + 1024, *pc = pb + 1024;
+    double *scal = P<double>(c->scal);
+    int *flags = P<int>(c->counter) + 4;
+    const bool lmp = use_lmp && c->kU > 0;
+    int *hflags = P<int>(c->pinned);
+    double *hrel = reinterpret_cast<double *>(P<char>(c->pinned) + 64);
+
+    // x = 0, d = 0, r = rhs; rhat = C^T r, p = C rhat
+    WC4D_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * nA, c->stream));
+    WC4D_CUDA(c, cudaMemsetAsync(d, 0, sizeof(float) * nA, c->stream));
+    launch_convert_f64_f32(c->stream, nA, P<double>(c->rhs), r);
+    auto precondition_residual = [&]() -> wc4d_status {
+        if (lmp) {
+            WC4D_TRY(lmp_apply_impl<float>(c, r, rh, nullptr));
+            WC4D_TRY(lmp_apply_impl<float>(c, rh, p, nullptr));
+        } else {
+            launch_copy<float>(c->stream, nA, r, rh);
+            launch_copy<float>(c->stream, nA, rh, p);
+        }
+        return WC4D_OK;
+    };
+    WC4D_TRY(precondition_residual());
+    launch_dot_partial<double>(c->stream, grid, nA, P<double>(c->rhs), P<double>(c->rhs), pa);
+    launch_dot_partial<float>(c->stream, grid, nA, rh, rh, pb);
+    launch_pcg_init(c->stream, grid, pa, pb, scal, flags);
+    WC4D_TRY(check_launch(c, "pcg init"));
+    WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "pcg init"));
+    double rel = hflags[0] ? 0.0 : 1.0;   // |rhs| = 0: x = 0 is exact
+    double rmax = rel;
+    bool converged = (force == 0 && rel <= tol), breakdown = false, pending = false;
+    const double tol_k = (force > 0) ? 0.0 : tol;
+    const int nit = (force > 0) ? force : maxit;
+    int it = 0;
+    for (; it < nit && !converged; ++it) {
+        WC4D_TRY(hvp_impl<float>(c, p, q, 1, nA, false));                    // q = A p
+        launch_dot_partial<float>(c->stream, grid, nA, p, q, pa);
+        launch_pcg_alpha(c->stream, grid, pa, scal, flags);                  // alpha = rho / p^T A p
+        launch_pcg_xr<float>(c->stream, grid, nA, scal, d, r, p, q, pb);     // d += alpha p; r -= alpha q
+        const float *tq = q;
+        if (lmp) { WC4D_TRY(lmp_apply_impl<float>(c, q, t, flags)); tq = t; }
+        launch_pcg_rh<float>(c->stream, grid, nA, scal, rh, tq, pc);         // rhat -= alpha C^T A p
+        launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
+        const float *tr = rh;
+        if (lmp) { WC4D_TRY(lmp_apply_impl<float>(c, rh, t, flags)); tr = t; }
+        launch_pcg_p<float>(c->stream, grid, nA, scal, p, tr);               // p = C rhat + beta p
+        WC4D_TRY(check_launch(c, "pcg iteration"));
+        WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+        WC4D_CUDA(c, cudaMemcpyAsync(hrel, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        WC4D_TRY(sync(c, "pcg iteration"));
+        pending = true;
+        if (hflags[1]) { breakdown = true; ++it; break; }
+        if (!(hflags[0] || *hrel < kReliableDelta * rmax)) continue;
+        // reliable update
+        launch_add_f32_to_f64(c->stream, nA, d, x);
+        WC4D_CUDA(c, cudaMemsetAsync(d, 0, sizeof(float) * nA, c->stream));
+        pending = false;
+        WC4D_TRY(true_residual(c, x, r64, &rel, nullptr));
+        rmax = rel;
+        if (force == 0 && rel <= tol) { converged = true; ++it; break; }
+        launch_convert_f64_f32(c->stream, nA, r64, r);
+        if (lmp) WC4D_TRY(lmp_apply_impl<float>(c, r, rh, nullptr));
+        else launch_copy<float>(c->stream, nA, r, rh);
+        launch_dot_partial<float>(c->stream, grid, nA, rh, rh, pb);
+        launch_dot_partial<float>(c->stream, grid, nA, r, r, pc);
+        launch_pcg_restart(c->stream, grid, pb, pc, scal, flags);
+        WC4D_TRY(check_launch(c, "reliable update"));
+    }
+    if (pending) {   // iteration budget spent (or breakdown) between updates
+        launch_add_f32_to_f64(c->stream, nA, d, x);
+        WC4D_TRY(true_residual(c, x, r64, &rel, nullptr));
+    }
+    if (sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep: a grid barrier timed out");
+    *iters_out = it;
+    *rel_out = rel;
+    *breakdown_out = breakdown;
+    return WC4D_OK;
+}
+
 extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxit, int32_t use_lmp, int32_t force,
                                 int32_t precision, int32_t *iters, double *relres, double *qcf_host)
 {
@@ -1218,50 +1305,7 @@ extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxi
             st = true_residual(c, x, P<double>(c->pcg64[7]), &rel, nullptr);
         }
     } else {
-        // FP32 CG inside FP64 true-residual refinement
-        WC4D_TRY(ensure(c, c->pcg64[7], sizeof(double) * nA));
-        WC4D_TRY(ensure(c, c->pcg32[0], sizeof(float) * nA));
-        WC4D_TRY(ensure(c, c->pcg32[6], sizeof(float) * nA));
-        double *r64 = P<double>(c->pcg64[7]);
-        float *b32 = P<float>(c->pcg32[6]), *d32 = P<float>(c->pcg32[0]);
-        WC4D_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * nA, c->stream));
-        launch_copy<double>(c->stream, nA, P<double>(c->rhs), r64);
-        double bnorm = 0.0;
-        {
-            double dummy;
-            // |rhs| (x = 0: residual = rhs)
-            const int grid = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA + 255) / 256));
-            WC4D_TRY(ensure(c, c->small0, sizeof(double) * 2048));
-            launch_dot_partial<double>(c->stream, grid, nA, r64, r64, P<double>(c->small0));
-            std::vector<double> h(grid);
-            WC4D_CUDA(c, cudaMemcpyAsync(h.data(), c->small0.p, sizeof(double) * grid, cudaMemcpyDeviceToHost,
-                                         c->stream));
-            WC4D_TRY(sync(c, "bnorm"));
-            double bb = 0.0;
-            for (double v : h) bb += v;
-            bnorm = std::sqrt(bb);
-            (void)dummy;
-        }
-        rel = bnorm > 0.0 ? 1.0 : 0.0;
-        const int budget = (force > 0) ? force : maxit;
-        for (int round = 0; round < 40 && st == WC4D_OK; ++round) {
-            if (force == 0 && rel <= tol) break;
-            if (total_it >= budget) break;
-            // each FP32 round aims at the remaining reduction but at most 1e-4
-            // (FP32 CG on these operators attains ~1e-5), and ends early on
-            // stagnation; the FP64 residual then starts the next round
-            double inner_tol = (force > 0) ? 0.0 : std::max(0.5 * tol / rel, 1e-4);
-            launch_convert_f64_f32(c->stream, nA, r64, b32);
-            PcgOut o;
-            st = pcg_core<float>(c, b32, d32, inner_tol, budget - total_it, (force > 0) ? force : 0, use_lmp != 0,
-                                 P<double>(qcf) + total_it, o, (force > 0) ? 0 : 25);
-            if (st != WC4D_OK) break;
-            total_it += o.iters;
-            launch_add_f32_to_f64(c->stream, nA, d32, x);
-            st = true_residual(c, x, r64, &rel, nullptr);
-            if (o.breakdown) { breakdown = true; break; }
-            if (force > 0) break;
-        }
+        st = pcg_reliable(c, x, tol, maxit, force, use_lmp != 0, P<double>(qcf), &total_it, &rel, &breakdown);
     }
     if (st == WC4D_OK && qcf_host) {
         cudaMemcpyAsync(qcf_host, qcf.p, sizeof(double) * std::min(cap, std::max(total_it, 0)),

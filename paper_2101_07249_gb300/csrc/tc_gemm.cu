@@ -12,6 +12,13 @@
 // sweep epilogue (W_{t+1} += M_t W_t, or W_t = obs(W_t) + M_t^T W_{t+1}).
 // Every wait is bounded: on a timeout the CTA records an error, drains its
 // own copies with a bounded wait, frees its tensor memory and returns.
+//
+// The tensor cores read only the leading 19 bits of each FP32 operand, which
+// truncates toward zero.  Through a sweep of N = 40 products that bias
+// compounds (about 2.5% on the largest Ritz values of the sketch), so both
+// operands are rounded to the nearest TF32 value first: the propagators once
+// per model, and every block the sweep produces in the reduce kernel, which
+// writes the FP32 state and its rounded copy (the next product's B operand).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -226,9 +233,33 @@ k_tc_sweep(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
 }
 
-// C(i, j) = epi(sum_s part[s][j][i]) over the n x K output block.
+__device__ __forceinline__ float round_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void k_round_tf32(int64_t cnt, const float *__restrict__ src, float *__restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = round_tf32(src[i]);
+}
+
+// dst(i, j) = tf32(src(i, j)) over an n x K block.
+__global__ void k_round_block(int n, int K, const float *__restrict__ src, int64_t lds, float *dst, int64_t ldd)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * K) return;
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    dst[(int64_t)j * ldd + i] = round_tf32(src[(int64_t)j * lds + i]);
+}
+
+// C(i, j) = epi(sum_s part[s][j][i]) over the n x K output block, and
+// Cr(i, j) = tf32(C(i, j)).
 __global__ void __launch_bounds__(256)
-k_tc_reduce(int n, int K, int splits, const float *__restrict__ part, float *C, int64_t ldc, Epi e)
+k_tc_reduce(int n, int K, int splits, const float *__restrict__ part, float *C, int64_t ldc, float *Cr,
+            int64_t ldr, Epi e)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * K) return;
@@ -240,6 +271,7 @@ k_tc_reduce(int n, int K, int splits, const float *__restrict__ part, float *C, 
     if (e.mode == 1) out = acc + ((i % e.obs_stride == 0) ? (float)e.obs_scale * (*dst) : 0.f);
     else out = (float)e.alpha * acc + (e.beta != 0.0 ? (float)e.beta * (*dst) : 0.f);
     *dst = out;
+    Cr[(int64_t)j * ldr + i] = round_tf32(out);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -307,7 +339,7 @@ int choose_splits(const wc4d_ctx *c, int n)
 // One subwindow product: part = M_blk(rows a_row0..) x W(rows b_x0..), then
 // C = epi(part) (C column-major, ldc).
 bool tc_product(wc4d_ctx *c, const CUtensorMap &mA, const CUtensorMap &mB, int K, int a_row0, int b_x0, float *C,
-                int64_t ldc, const Epi &e, int splits, float *part, int *err)
+                int64_t ldc, float *Cr, const Epi &e, int splits, float *part, int *err)
 {
     const int n = c->prob.n;
     TcArgs args{n, K, n / splits, a_row0, b_x0, part, err};
@@ -317,7 +349,7 @@ bool tc_product(wc4d_ctx *c, const CUtensorMap &mA, const CUtensorMap &mB, int K
         WC4D_LAUNCH(k_tc_sweep<<<grid, 128, SMEM_BYTES, c->stream>>>(mA, mB, args));
     }
     const int64_t tot = (int64_t)n * K;
-    WC4D_LAUNCH(k_tc_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(n, K, splits, part, C, ldc, e));
+    WC4D_LAUNCH(k_tc_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(n, K, splits, part, C, ldc, Cr, c->nA, e));
     return true;
 }
 
@@ -332,13 +364,30 @@ bool tc_sweep_supported(const wc4d_ctx *c, int K)
     return device_ok(c);
 }
 
-static bool tc_prepare(wc4d_ctx *c, int K, float *W, int64_t ld, const float *Mbase, CUtensorMap *mA,
-                       CUtensorMap *mB, int *splits, float **part, int **err)
+// Tensor maps over the rounded propagators (forward: M, adjoint: M^T) and
+// the rounded copy of the block; builds the rounded propagators on first use.
+static bool tc_prepare(wc4d_ctx *c, int K, float *W, int64_t ld, bool adjoint, CUtensorMap *mA, CUtensorMap *mB,
+                       int *splits, float **part, int **err, float **Wr)
 {
     const int n = c->prob.n;
     if (ld % 4 != 0 || ((uintptr_t)W & 15u) != 0) return false;
+    const size_t cnt = (size_t)c->nM * n * n;
+    if (!c->have_Mtf) {
+        if (ensure(c, c->Mtf, sizeof(float) * cnt) != WC4D_OK) return false;
+        if (ensure(c, c->MTtf, sizeof(float) * cnt) != WC4D_OK) return false;
+        const int grid = 8 * c->num_sms;
+        WC4D_LAUNCH(k_round_tf32<<<grid, 256, 0, c->stream>>>((int64_t)cnt, reinterpret_cast<const float *>(c->M32.p),
+                                                              reinterpret_cast<float *>(c->Mtf.p)));
+        WC4D_LAUNCH(k_round_tf32<<<grid, 256, 0, c->stream>>>((int64_t)cnt, reinterpret_cast<const float *>(c->MT32.p),
+                                                              reinterpret_cast<float *>(c->MTtf.p)));
+        if (cudaGetLastError() != cudaSuccess) return false;
+        c->have_Mtf = true;
+    }
+    if (ensure(c, c->tc_round, sizeof(float) * (size_t)c->nA * K) != WC4D_OK) return false;
+    *Wr = reinterpret_cast<float *>(c->tc_round.p);
+    const float *Mbase = reinterpret_cast<const float *>(adjoint ? c->MTtf.p : c->Mtf.p);
     if (!make_map(mA, Mbase, (uint64_t)n, (uint64_t)c->nM * n, (uint64_t)n, BM)) return false;
-    if (!make_map(mB, W, (uint64_t)c->nA, (uint64_t)K, (uint64_t)ld, (uint32_t)K)) return false;
+    if (!make_map(mB, *Wr, (uint64_t)c->nA, (uint64_t)K, (uint64_t)c->nA, (uint32_t)K)) return false;
     *splits = choose_splits(c, n);
     if (ensure(c, c->tc_part, sizeof(float) * (size_t)(*splits) * K * n) != WC4D_OK) return false;
     if (ensure(c, c->tc_err, sizeof(int)) != WC4D_OK) return false;
@@ -351,20 +400,27 @@ static bool tc_prepare(wc4d_ctx *c, int K, float *W, int64_t ld, const float *Mb
     return true;
 }
 
+static void round_block(wc4d_ctx *c, int K, const float *src, int64_t lds, float *dst)
+{
+    const int64_t tot = (int64_t)c->prob.n * K;
+    WC4D_LAUNCH(k_round_block<<<ceil_div(tot, 256), 256, 0, c->stream>>>(c->prob.n, K, src, lds, dst, c->nA));
+}
+
 // W_{t+1} += M_t W_t for t = 0..N-1.
 bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld)
 {
     CUtensorMap mA, mB;
     int splits;
-    float *part;
+    float *part, *Wr;
     int *err;
-    if (!tc_prepare(c, K, W, ld, reinterpret_cast<const float *>(c->M32.p), &mA, &mB, &splits, &part, &err))
-        return false;
+    if (!tc_prepare(c, K, W, ld, false, &mA, &mB, &splits, &part, &err, &Wr)) return false;
     const int n = c->prob.n, N = c->prob.N;
     Epi e{0, 1.0, 1.0, 0.0, 1};
+    round_block(c, K, W, ld, Wr);
     for (int t = 0; t < N; ++t) {
         const int blk = (c->nM == 1) ? 0 : t;
-        tc_product(c, mA, mB, K, blk * n, t * n, W + (int64_t)(t + 1) * n, ld, e, splits, part, err);
+        tc_product(c, mA, mB, K, blk * n, t * n, W + (int64_t)(t + 1) * n, ld, Wr + (int64_t)(t + 1) * n, e, splits,
+                   part, err);
     }
     return true;
 }
@@ -374,10 +430,9 @@ bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld)
 {
     CUtensorMap mA, mB;
     int splits;
-    float *part;
+    float *part, *Wr;
     int *err;
-    if (!tc_prepare(c, K, W, ld, reinterpret_cast<const float *>(c->MT32.p), &mA, &mB, &splits, &part, &err))
-        return false;
+    if (!tc_prepare(c, K, W, ld, true, &mA, &mB, &splits, &part, &err, &Wr)) return false;
     const int n = c->prob.n, N = c->prob.N;
     const wc4d_problem &p = c->prob;
     auto obs_scale = [&](int t) {
@@ -385,10 +440,12 @@ bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld)
         return (t >= p.obs_t0 && (t - p.obs_t0) % ts == 0) ? 1.0 / p.sigma_o2 : 0.0;
     };
     launch_obs_block<float>(c->stream, n, K, W + (int64_t)N * n, ld, obs_scale(N), p.obs_stride);
+    round_block(c, K, W + (int64_t)N * n, ld, Wr + (int64_t)N * n);
     for (int t = N - 1; t >= 0; --t) {
         const int blk = (c->nM == 1) ? 0 : t;
         Epi e{1, 1.0, 0.0, obs_scale(t), p.obs_stride};
-        tc_product(c, mA, mB, K, blk * n, (t + 1) * n, W + (int64_t)t * n, ld, e, splits, part, err);
+        tc_product(c, mA, mB, K, blk * n, (t + 1) * n, W + (int64_t)t * n, ld, Wr + (int64_t)t * n, e, splits, part,
+                   err);
     }
     return true;
 }

@@ -98,6 +98,10 @@ struct wc4d_ctx {
     // tensor-core sweeps: split partials and the error flag of bounded waits
     DevBuf tc_part, tc_err;
     bool tc_err_zeroed = false;
+    // tensor-core operands rounded to TF32 (nearest): the propagators, and
+    // the probe block as the sweep produces it (nA x K, ld nA)
+    DevBuf Mtf, MTtf, tc_round;
+    bool have_Mtf = false;
 
     // persistent one-column sweeps: grid barrier words and error flag
     DevBuf sweep_bar;
@@ -238,6 +242,8 @@ void launch_pcg_rh(cudaStream_t s, int grid, int64_t n, const double *scal, T *r
 template <typename T>
 void launch_pcg_p(cudaStream_t s, int grid, int64_t n, const double *scal, T *p, const T *t);
 void launch_pcg_alpha(cudaStream_t s, int grid, const double *part, double *scal, int *flags);
+void launch_pcg_restart(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
+                        int *flags);
 void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
                      int *flags, double tol, double *qcf_drop, int it);
 void launch_pcg_init(cudaStream_t s, int grid, const double *part_b, const double *part_rh, double *scal,
