@@ -281,8 +281,13 @@ def main():
 
     # ---- live per-kernel-class timing of one more mixed inner loop
     w.wc4d_profile(ctx, True)
-    it_p, _ = inner(w.MIXED, 77)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    ev0.record()
+    it_p, _ = inner(w.MIXED, 77)
+    ev1.record()
+    torch.cuda.synchronize()
+    profiled_ms = ev0.elapsed_time(ev1)
     classes = {}
     for ci, name in enumerate(w.PROF_CLASSES):
         ms, cnt = w.wc4d_profile_read(ctx, ci)
@@ -366,6 +371,8 @@ def main():
             "fp64_plain": fp64,
             "speedup_vs_fp64": (fp64["inner_loop_s"] / (t_max / args.steps)) if fp64 else None,
             "kernel_classes": classes,
+            "profiled_inner_loop_ms": profiled_ms,
+            "unclassified_ms": profiled_ms - sum(v["ms"] for v in classes.values()),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -188,10 +188,16 @@ wc4d_status wc4d_inner_loop(wc4d_ctx *ctx, int32_t method, int32_t k, int32_t l,
 
 /* ---- small building blocks, exported for verification ------------------ */
 
-/* CholeskyQR2 in place: Y (device, rows x m, ld) becomes Z with orthonormal
- * columns and span(Z) = span(Y); R_host (m x m column-major, may be NULL)
- * receives the upper-triangular factor with Y = Z R, positive diagonal. */
-wc4d_status wc4d_orthonormalize(wc4d_ctx *ctx, double *Y, int64_t rows, int32_t m, int64_t ld, double *R_host);
+/* CholeskyQR2 in place (the orthonormalisation of Alg. 3-5): Y (device,
+ * rows x m, ld; double for WC4D_FP64, float for WC4D_MIXED) becomes Z with
+ * orthonormal columns and span(Z) = span(Y); R_host (m x m column-major,
+ * may be NULL) receives the upper-triangular factor with Y = Z R, positive
+ * diagonal.  Both precisions form the Gram matrix Y^T Y to about 48
+ * significant bits or more (FP64 accumulation; for float data, exact
+ * products with double-float sums) and factor it in FP64.
+ * WC4D_ENOTSPD when the Gram matrix is not numerically positive definite. */
+wc4d_status wc4d_orthonormalize(wc4d_ctx *ctx, void *Y, int64_t rows, int32_t m, int64_t ld, double *R_host,
+                                int32_t precision);
 /* Eigen-decomposition of a symmetric positive semi-definite m x m matrix
  * (device, column-major) by one-sided Jacobi: w_host decreasing, V_device
  * (m x m column-major) the eigenvectors. */
@@ -215,9 +221,10 @@ int64_t     wc4d_launch_count(int32_t reset);
  * timed groups of one class.  Classes: 0 FP32 one-column sweep (all N
  * subwindow GEMVs of L^{-1} or L^{-T} in one group), 1 sweep SIMT GEMM,
  * 2 sweep tensor-core GEMM (one subwindow), 3 D^{1/2} circulant, 4 LMP
- * application, 5 Gram products, 6 other dense LA, 7 Lorenz-96 tangent-
- * linear sweep, 8 Lorenz-96 adjoint sweep, 9 PCG vector kernels, 10 FP64
- * one-column sweep. */
+ * application, 5 Gram products, 6 tall-skinny products Y R^{-1} and Z W,
+ * 7 Lorenz-96 tangent-linear sweep, 8 Lorenz-96 adjoint sweep, 9 PCG vector
+ * kernels, 10 FP64 one-column sweep, 11 Jacobi EVD/SVD, 12 Cholesky and
+ * triangular inverse. */
 wc4d_status wc4d_profile(wc4d_ctx *ctx, int32_t enable);
 wc4d_status wc4d_profile_read(wc4d_ctx *ctx, int32_t cls, double *total_ms, int64_t *launch_groups);
 /* Allocation-free spectral-LMP application, y = C v (the paper has no

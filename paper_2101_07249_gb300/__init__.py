@@ -71,7 +71,7 @@ _SIGS = {
     "wc4d_pcg": (C.c_int, [_V, _V, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _I32, _D, _D]),
     "wc4d_inner_loop": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_double,
                                   C.c_int32, C.c_int32, _V, _I32, _D]),
-    "wc4d_orthonormalize": (C.c_int, [_V, _V, C.c_int64, C.c_int32, C.c_int64, _D]),
+    "wc4d_orthonormalize": (C.c_int, [_V, _V, C.c_int64, C.c_int32, C.c_int64, _D, C.c_int32]),
     "wc4d_symeig": (C.c_int, [_V, C.c_int32, _V, _D, _V]),
     "wc4d_hvp_count": (C.c_int64, [_V, C.c_int32]),
     "wc4d_apply_dsqrt": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
@@ -83,8 +83,8 @@ _SIGS = {
     "wc4d_profile_read": (C.c_int, [_V, C.c_int32, _D, C.POINTER(C.c_int64)]),
     "wc4d_lmp_apply_static": (C.c_int, [_V, _V, C.c_int32, C.c_int64, _V, _V, _V]),
 }
-PROF_CLASSES = ("gemv_sweep", "gemm", "tc_gemm", "circulant", "lmp", "gram", "la", "l96_tlm", "l96_adj", "pcg_vec",
-                "gemv_sweep_f64")
+PROF_CLASSES = ("gemv_sweep", "gemm", "tc_gemm", "circulant", "lmp", "gram", "tall_gemm", "l96_tlm", "l96_adj",
+                "pcg_vec", "gemv_sweep_f64", "jacobi", "chol")
 EXPORTS = tuple(_SIGS)
 
 _lock = threading.Lock()
@@ -259,9 +259,9 @@ def wc4d_inner_loop(ctx, method, k, l, q_power, seed, tol, maxit, precision, x):
     return it.value, rr.value
 
 
-def wc4d_orthonormalize(ctx, Y, rows, m, ld, want_R=True):
+def wc4d_orthonormalize(ctx, Y, rows, m, ld, want_R=True, precision=FP64):
     R = np.zeros(int(m) * int(m)) if want_R else None
-    _check(ctx, load().wc4d_orthonormalize(ctx, _ptr(Y), int(rows), int(m), int(ld), _hp(R)))
+    _check(ctx, load().wc4d_orthonormalize(ctx, _ptr(Y), int(rows), int(m), int(ld), _hp(R), int(precision)))
     return None if R is None else R.reshape(int(m), int(m)).T.copy()   # ordinary (row, col) indexing
 
 

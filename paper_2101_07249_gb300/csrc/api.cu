@@ -718,14 +718,18 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
                           &S, G, 1) != 0)   // G = Y^T Y
             return set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small");
     }
-    launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));                                // G = R^T R
     double *Rinv = P<double>(c->small1);
-    launch_trinv_upper(c->stream, m, R, Rinv);
-    WC4D_TRY(check_launch(c, "cholqr"));
     int info = 0;
-    WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    {
+        ProfScope psc(c, PROF_CHOL);
+        launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));                            // G = R^T R
+        launch_trinv_upper(c->stream, m, R, Rinv);
+        WC4D_TRY(check_launch(c, "cholqr"));
+        WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    }
     WC4D_TRY(sync(c, "cholqr info"));
     if (info != 0) return set_err(c, WC4D_ENOTSPD, "CholeskyQR: Gram matrix not positive definite at pivot %d", info);
+    ProfScope psl(c, PROF_LA);
     Epi e{0, 1.0, 0.0, 0.0, 1};
     if constexpr (sizeof(T) == 8) {
         launch_gemm<double>(c->stream, (int)rows, m, m, Y, 1, ld, Rinv, m, tmp, rows, e);
@@ -761,6 +765,7 @@ static wc4d_status cholqr2(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t ld, T
 // doubles) receives Sigma decreasing in w[0..m); Vout (m x m) the matching V.
 static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, double *Vout)
 {
+    ProfScope ps(c, PROF_JACOBI);
     const int mp = m + (m & 1);
     size_t mpmp = (size_t)mp * mp;
     DevBuf &xb = c->small3;
@@ -787,10 +792,13 @@ static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, d
     return check_launch(c, "jacobi finish");
 }
 
-extern "C" wc4d_status wc4d_orthonormalize(wc4d_ctx *c, double *Y, int64_t rows, int32_t m, int64_t ld, double *R_host)
+extern "C" wc4d_status wc4d_orthonormalize(wc4d_ctx *c, void *Y, int64_t rows, int32_t m, int64_t ld, double *R_host,
+                                           int32_t precision)
 {
     if (!c || !Y || rows < m || m < 1 || ld < rows) return WC4D_EINVAL;
-    WC4D_TRY(ensure(c, c->blkD, sizeof(double) * (size_t)rows * m));
+    if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
+    const size_t esz = (precision == WC4D_FP64) ? sizeof(double) : sizeof(float);
+    WC4D_TRY(ensure(c, c->blkD, esz * (size_t)rows * m));
     WC4D_TRY(ensure(c, c->small1, sizeof(double) * (size_t)m * m));
     DevBuf Rb;
     double *R = nullptr;
@@ -798,7 +806,9 @@ extern "C" wc4d_status wc4d_orthonormalize(wc4d_ctx *c, double *Y, int64_t rows,
         WC4D_TRY(ensure(c, Rb, sizeof(double) * (size_t)m * m));
         R = P<double>(Rb);
     }
-    wc4d_status s = cholqr2<double>(c, Y, rows, m, ld, P<double>(c->blkD), R);
+    wc4d_status s = (precision == WC4D_FP64)
+                        ? cholqr2<double>(c, static_cast<double *>(Y), rows, m, ld, P<double>(c->blkD), R)
+                        : cholqr2<float>(c, static_cast<float *>(Y), rows, m, ld, P<float>(c->blkD), R);
     if (s == WC4D_OK && R_host) {
         cudaMemcpyAsync(R_host, R, sizeof(double) * (size_t)m * m, cudaMemcpyDeviceToHost, c->stream);
         s = sync(c, "orthonormalize");
@@ -895,6 +905,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
             // EVD of K_1 (Alg. 3 step 5); U = Z W[:, :k]
             if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);
             U = C_;
+            ProfScope psl(c, PROF_LA);
             Epi e{0, 1.0, 0.0, 0.0, 1};
             if constexpr (sizeof(T) == 8) {
                 launch_gemm<double>(c->stream, (int)nA, k, m, Z, 1, nA, Wv, m, U, nA, e);
@@ -957,6 +968,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         if ((st = check_launch(c, "R^T")) != WC4D_OK) return fail(st);
         if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);   // singular values = Theta_3
         U = C_;
+        ProfScope psl(c, PROF_LA);
         Epi e{0, 1.0, 0.0, 0.0, 1};
         if constexpr (sizeof(T) == 8) {
             launch_gemm<double>(c->stream, (int)nA, k, m, B_, 1, nA, Wv, m, U, nA, e);
@@ -1235,16 +1247,25 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
     int it = 0;
     for (; it < nit && !converged; ++it) {
         WC4D_TRY(hvp_impl<float>(c, p, q, 1, nA, false));                    // q = A p
-        launch_dot_partial<float>(c->stream, grid, nA, p, q, pa);
-        launch_pcg_alpha(c->stream, grid, pa, scal, flags);                  // alpha = rho / p^T A p
-        launch_pcg_xr<float>(c->stream, grid, nA, scal, d, r, p, q, pb);     // d += alpha p; r -= alpha q
+        {
+            ProfScope ps(c, PROF_VEC);
+            launch_dot_partial<float>(c->stream, grid, nA, p, q, pa);
+            launch_pcg_alpha(c->stream, grid, pa, scal, flags);              // alpha = rho / p^T A p
+            launch_pcg_xr<float>(c->stream, grid, nA, scal, d, r, p, q, pb); // d += alpha p; r -= alpha q
+        }
         const float *tq = q;
         if (lmp) { WC4D_TRY(lmp_apply_impl<float>(c, q, t, flags)); tq = t; }
-        launch_pcg_rh<float>(c->stream, grid, nA, scal, rh, tq, pc);         // rhat -= alpha C^T A p
-        launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
+        {
+            ProfScope ps(c, PROF_VEC);
+            launch_pcg_rh<float>(c->stream, grid, nA, scal, rh, tq, pc);     // rhat -= alpha C^T A p
+            launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
+        }
         const float *tr = rh;
         if (lmp) { WC4D_TRY(lmp_apply_impl<float>(c, rh, t, flags)); tr = t; }
-        launch_pcg_p<float>(c->stream, grid, nA, scal, p, tr);               // p = C rhat + beta p
+        {
+            ProfScope ps(c, PROF_VEC);
+            launch_pcg_p<float>(c->stream, grid, nA, scal, p, tr);           // p = C rhat + beta p
+        }
         WC4D_TRY(check_launch(c, "pcg iteration"));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
         WC4D_CUDA(c, cudaMemcpyAsync(hrel, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -35,11 +35,13 @@ enum ProfId {
     PROF_CIRC,       // D^{1/2} circulant (FFT or direct)
     PROF_LMP,        // spectral-LMP application
     PROF_GRAM,       // A^T B Gram products
-    PROF_LA,         // other dense LA (Y R^{-1}, Z W, Cholesky, Jacobi)
+    PROF_LA,         // tall-skinny products Y R^{-1}, Z W (and Nystrom F)
     PROF_L96_TLM,    // Lorenz-96 tangent-linear sweep
     PROF_L96_ADJ,    // Lorenz-96 adjoint sweep
     PROF_VEC,        // PCG vector kernels
     PROF_GEMV64,     // FP64 one-column sweeps (true residuals, set-up)
+    PROF_JACOBI,     // one-sided Jacobi EVD / SVD of the small matrices
+    PROF_CHOL,       // Cholesky and triangular inverse of the small matrices
     PROF_N
 };
 struct ProfEntry {

@@ -150,6 +150,27 @@ def test_cholqr2_matches_householder(m):
     assert np.abs(host(Y) - Qo).max() < 1e-9
 
 
+@pytest.mark.parametrize("m", [64, 128, 200])
+def test_cholqr2_fp32_ill_conditioned(m):
+    """FP32 blocks (the mixed sketch's orthonormalisation) with condition
+    number 1e5: the Gram matrix must carry ~FP64 accuracy (kappa^2 = 1e10
+    exceeds what FP32 accumulation resolves), so CholeskyQR2 still returns
+    orthonormal columns to FP32 rounding and Y = Z R."""
+    cfg, S, _, _ = setup("ad_direct")
+    rows = 20000
+    g = np.random.default_rng(100 + m)
+    Q1, _ = np.linalg.qr(g.standard_normal((rows, m)))
+    V, _ = np.linalg.qr(g.standard_normal((m, m)))
+    A = (Q1 * np.logspace(0, -5, m)) @ V.T            # rows x m, kappa = 1e5
+    A32 = A.astype(np.float32).astype(np.float64)
+    Y = torch.tensor(A32.T.copy(), dtype=torch.float32, device="cuda")
+    R = w.wc4d_orthonormalize(S.ctx, Y, rows, m, rows, precision=w.MIXED)
+    Z = host(Y).astype(np.float64).T
+    assert np.abs(Z.T @ Z - np.eye(m)).max() < 2e-5
+    assert np.linalg.norm(A32 - Z @ R) / np.linalg.norm(A32) < 1e-5
+    assert np.all(np.diag(R) > 0)
+
+
 @pytest.mark.parametrize("m", [1, 2, 15, 40, 77])
 def test_symeig_matches_jacobi(m):
     cfg, S, _, _ = setup("ad_direct")
@@ -395,8 +416,10 @@ AD_TC = inputs.scaled(inputs.TINY, n=512, N=4, k=240, l=16, obs_stride=8)
 @pytest.mark.parametrize("K", [16, 48, 256])
 def test_tensor_core_sweeps_match_oracle(K):
     """Mixed sweeps with K a multiple of 16 and n a multiple of 128 run as
-    tcgen05 TF32 MMAs (8 pipeline stages per CTA here); TF32 operands carry
-    ~2^-11 relative rounding, so the tolerance is 1e-2."""
+    tcgen05 TF32 MMAs (8 pipeline stages per CTA here).  Operands are rounded
+    to the nearest TF32 value (2^-11 relative, unbiased), so the error stays
+    near 1e-4; the tensor cores' own truncation would bias every product by
+    about -1e-3 and fail both checks."""
     cfg = AD_TC
     tw = inputs.twin(cfg)
     S = w.Solver(cfg, tw)
@@ -404,9 +427,12 @@ def test_tensor_core_sweeps_match_oracle(K):
     X = inputs.block(40 + K, cfg.nA, K)
     W = dev(X, torch.float32)
     w.wc4d_apply_linv(S.ctx, W, K, cfg.nA, w.MIXED)
-    assert colrel(host(W), oracle.Linv(p, X)) < 1e-2
+    assert colrel(host(W), oracle.Linv(p, X)) < 1e-3
     Y = torch.zeros(K, cfg.nA, dtype=torch.float32, device="cuda")
     w.wc4d_hvp(S.ctx, dev(X, torch.float32), Y, K, cfg.nA, w.MIXED)
-    err = colrel(host(Y), oracle.hvp(p, X))
-    assert err < 1e-2, err
+    Ho = oracle.hvp(p, X)
+    err = colrel(host(Y), Ho)
+    assert err < 1e-3, err
+    bias = np.mean(np.sum((host(Y) - Ho) * Ho, axis=1) / np.sum(Ho * Ho, axis=1))
+    assert abs(bias) < 3e-4, bias
     S.close()
