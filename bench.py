@@ -192,6 +192,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny"],
                     help="large: n=4096 N=40 (the benchmark); medium: N=8 (profiling captures); tiny: n=100 N=5")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only --warmup inner loops and one more, then exit (a short program for ncu captures)")
     args = ap.parse_args()
 
     from paper_2101_07249_gb300 import inputs
@@ -222,6 +224,14 @@ def main():
     for i in range(args.warmup):
         inner(w.MIXED, 1000 + i)
     torch.cuda.synchronize()
+    if args.profile_run:
+        w.wc4d_launch_count(reset=True)
+        it, rr = inner(w.MIXED, 0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": cfg.name, "pcg_iters": it, "relres": rr,
+                          "gpu_launches": w.wc4d_launch_count()}))
+        S.close()
+        return
 
     # ---- timed region: device-resident inputs
     clocks = ClockSampler(local)

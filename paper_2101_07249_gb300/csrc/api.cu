@@ -197,6 +197,14 @@ extern "C" wc4d_status wc4d_create(wc4d_ctx **out, const wc4d_problem *prob, voi
         wc4d_destroy(c);
         return s;
     }
+    // counters that kernels expect at zero (the LMP coefficient kernel's
+    // arrival counter is counter[8])
+    if (cudaMemsetAsync(c->counter.p, 0, sizeof(int) * 16, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        wc4d_destroy(c);
+        return WC4D_ECUDA;
+    }
     launch_twiddles(c->stream, p.n, P<double2>(c->cosn), P<double2>(c->tw64), P<float2>(c->tw32));
     if ((s = check_launch(c, "twiddles")) != WC4D_OK || (s = sync(c, "create")) != WC4D_OK) {
         wc4d_destroy(c);
@@ -761,12 +769,37 @@ static wc4d_status cholqr2(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t ld, T
     return WC4D_OK;
 }
 
-// One-sided Jacobi on X0 (m x m, device): X0 V = U Sigma.  w (device, 2m
-// doubles) receives Sigma decreasing in w[0..m); Vout (m x m) the matching V.
-static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, double *Vout)
+// One-sided Jacobi in FP64 on X0 (m x m, device): X0 V = U Sigma.  m <= 256
+// runs as one persistent cooperative launch; larger m (or a refused
+// cooperative launch) as one launch per round of the round-robin ordering.
+// On return *X holds U Sigma and *V the accumulated rotations, both with
+// leading dimension *ld (columns in the order of X0).
+static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo, double **Vo, int *ld,
+                              bool want_v = true)
 {
-    ProfScope ps(c, PROF_JACOBI);
     const int mp = m + (m & 1);
+    const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
+    if (const int Pq = jacobi_coop_size(m)) {
+        const size_t nd = jacobi_coop_doubles(m);
+        WC4D_TRY(ensure(c, c->small3, sizeof(double) * nd + sizeof(int) * 128));
+        double *XV = P<double>(c->small3);
+        int *rot = reinterpret_cast<int *>(XV + nd);
+        unsigned *bar = reinterpret_cast<unsigned *>(rot + 64);
+        int *err = rot + 65;
+        int *status = rot + 66;
+        WC4D_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+        if (launch_jacobi_coop(c->stream, m, X0, XV, tol, 60, rot, bar, err, status, want_v)) {
+            int *h = P<int>(c->pinned);
+            WC4D_CUDA(c, cudaMemcpyAsync(h, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            WC4D_TRY(sync(c, "jacobi"));
+            if (h[0]) return set_err(c, WC4D_ETIMEOUT, "Jacobi: a grid barrier timed out");
+            if (h[1] < 0) return set_err(c, WC4D_ETIMEOUT, "one-sided Jacobi did not converge in 60 sweeps");
+            *Xo = XV;
+            *Vo = XV + (size_t)Pq * Pq;
+            *ld = Pq;
+            return WC4D_OK;
+        }
+    }
     size_t mpmp = (size_t)mp * mp;
     DevBuf &xb = c->small3;
     WC4D_TRY(ensure(c, xb, sizeof(double) * mpmp * 2));
@@ -774,7 +807,6 @@ static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, d
     launch_jacobi_init(c->stream, m, mp, X0, X, V);
     WC4D_TRY(check_launch(c, "jacobi init"));
     if (mp >= 2) {
-        const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
         int *rot = P<int>(c->counter) + 1;
         int *hrot = P<int>(c->pinned);
         bool conv = false;
@@ -788,8 +820,61 @@ static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, d
         }
         if (!conv) return set_err(c, WC4D_ETIMEOUT, "one-sided Jacobi did not converge in 60 sweeps");
     }
-    launch_jacobi_finish(c->stream, m, mp, X, V, w, Vout);
+    *Xo = X;
+    *Vo = V;
+    *ld = mp;
+    return WC4D_OK;
+}
+
+// SVD by one-sided Jacobi: w (device, 2m doubles) receives the singular
+// values of X0 decreasing in w[0..m), Vout (m x m) the matching right
+// singular vectors.  For symmetric positive semi-definite X0 these are its
+// eigenvalues and eigenvectors.
+static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, double *Vout)
+{
+    ProfScope ps(c, PROF_JACOBI);
+    double *X, *V;
+    int ld;
+    WC4D_TRY(jacobi_run(c, m, X0, &X, &V, &ld));
+    launch_jacobi_finish(c->stream, m, ld, X, V, w, Vout);
     return check_launch(c, "jacobi finish");
+}
+
+// Eigenpairs of a symmetric positive definite S (m x m, device): with
+// S = R^T R (Cholesky), one-sided Jacobi on R^T gives R^T = U Sigma V^T,
+// so S = U Sigma^2 U^T.  w receives Sigma^2 decreasing, Vout the matching U.
+// The Cholesky factor's columns are far closer to orthogonal than S's own
+// (about half the Jacobi sweeps on the sketch matrices).  Falls back to
+// Jacobi on S when S is not numerically positive definite.
+static wc4d_status spd_evd(wc4d_ctx *c, int m, const double *S, double *w, double *Vout)
+{
+    DevBuf rb;
+    WC4D_TRY(ensure(c, rb, sizeof(double) * 2 * (size_t)m * m));
+    double *R = P<double>(rb), *RT = R + (size_t)m * m;
+    int info = 0;
+    {
+        ProfScope psc(c, PROF_CHOL);
+        launch_chol_upper(c->stream, m, S, R, P<int>(c->counter));
+        launch_rrt(c->stream, m, R, RT);
+        wc4d_status st = check_launch(c, "spd_evd chol");
+        if (st != WC4D_OK) { free_buf(rb); return st; }
+        cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    }
+    wc4d_status st = sync(c, "spd_evd chol");
+    if (st == WC4D_OK && info == 0) {
+        ProfScope ps(c, PROF_JACOBI);
+        double *X, *V;
+        int ld;
+        st = jacobi_run(c, m, RT, &X, &V, &ld, false);
+        if (st == WC4D_OK) {
+            launch_jacobi_finish_left(c->stream, m, ld, X, w, Vout);
+            st = check_launch(c, "jacobi finish");
+        }
+    } else if (st == WC4D_OK) {
+        st = jacobi_svd(c, m, S, w, Vout);
+    }
+    free_buf(rb);
+    return st;
 }
 
 extern "C" wc4d_status wc4d_orthonormalize(wc4d_ctx *c, void *Y, int64_t rows, int32_t m, int64_t ld, double *R_host,
@@ -903,7 +988,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         if ((st = check_launch(c, "ZtAZ")) != WC4D_OK) return fail(st);
         if (method == WC4D_REVD) {
             // EVD of K_1 (Alg. 3 step 5); U = Z W[:, :k]
-            if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);
+            if ((st = spd_evd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);
             U = C_;
             ProfScope psl(c, PROF_LA);
             Epi e{0, 1.0, 0.0, 0.0, 1};
@@ -939,7 +1024,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
                 return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
             launch_symmetrize(c->stream, m, Kmat);
             if ((st = check_launch(c, "nystrom F")) != WC4D_OK) return fail(st);
-            if ((st = jacobi_svd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);   // F^T F = V Sigma^2 V^T
+            if ((st = spd_evd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);   // F^T F = V Sigma^2 V^T
             // U = F V[:, :k] Sigma^{-1}
             U = E;
             if constexpr (sizeof(T) == 8) {
@@ -1069,6 +1154,9 @@ extern "C" wc4d_status wc4d_set_ritz(wc4d_ctx *c, int32_t k, const double *U, co
 template <typename T> static T *Urm(wc4d_ctx *c);
 template <> double *Urm<double>(wc4d_ctx *c) { return P<double>(c->Urm64); }
 template <> float *Urm<float>(wc4d_ctx *c) { return P<float>(c->Urm32); }
+template <typename T> static T *Ucm(wc4d_ctx *c);   // column-major Ritz vectors, ld nA
+template <> double *Ucm<double>(wc4d_ctx *c) { return P<double>(c->U64); }
+template <> float *Ucm<float>(wc4d_ctx *c) { return P<float>(c->U32); }
 
 // y = C v (C^T = C for the closed form); skip: optional device flag
 template <typename T>
@@ -1105,6 +1193,32 @@ struct PcgOut {
     double relres_rec = 0.0;
 };
 
+// The LMP half of one CG iteration after q = A p (alpha; x += alpha p,
+// r -= alpha q; rhat -= alpha C q; t = C rhat; beta), fused into two passes
+// over the Ritz vectors.  qcf_dev may be null.
+template <typename T>
+static wc4d_status lmp_cg_step(wc4d_ctx *c, T *x, T *r, T *rh, const T *p, const T *q, T *t, double tol_k,
+                               double *qcf_dev, int it)
+{
+    const int64_t nA = c->nA;
+    const int kp = c->kp;
+    const int S = lmp_pass_a_splits(nA, c->num_sms), G = lmp_pass_b_grid(nA);
+    WC4D_TRY(ensure(c, c->part, sizeof(double) * ((size_t)S * (2 * kp + 1))));
+    WC4D_TRY(ensure(c, c->small2, sizeof(double) * (4 * (size_t)kp + 1 + 2 * (size_t)G)));
+    double *w = P<double>(c->small2), *partB = w + 4 * kp + 1;
+    double *scal = P<double>(c->scal);
+    int *flags = P<int>(c->counter) + 4;
+    unsigned *done = reinterpret_cast<unsigned *>(P<int>(c->counter) + 8);
+    {
+        ProfScope ps(c, PROF_LMP);
+        launch_lmp_fused<T>(c->stream, c->num_sms, nA, c->kU, kp, Urm<T>(c), Ucm<T>(c), P<double>(c->c64), q, p, rh,
+                            t, x, r, scal, flags, P<double>(c->part), w, partB, done);
+    }
+    ProfScope ps(c, PROF_VEC);
+    launch_pcg_beta(c->stream, G, partB, partB + G, scal, flags, tol_k, qcf_dev, it);
+    return WC4D_OK;
+}
+
 // CG on A x = b from x = 0 in precision T; b, x device vectors of the context.
 template <typename T>
 static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit, int force, bool use_lmp,
@@ -1137,16 +1251,17 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
     out = PcgOut();
     for (int it = 0; it < nit; ++it) {
         WC4D_TRY(hvp_impl<T>(c, p, q, 1, nA, false));                       // q = A p
-        launch_dot_partial<T>(c->stream, grid, nA, p, q, pa);
-        launch_pcg_alpha(c->stream, grid, pa, scal, flags);                 // alpha = rho / p^T A p
-        launch_pcg_xr<T>(c->stream, grid, nA, scal, x, r, p, q, pb);        // x += alpha p; r -= alpha q
-        const T *tq = q;
-        if (lmp) { WC4D_TRY(lmp_apply_impl<T>(c, q, t, flags)); tq = t; }   // C^T A p
-        launch_pcg_rh<T>(c->stream, grid, nA, scal, rh, tq, pc);            // rhat -= alpha C^T A p
-        launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
-        const T *tr = rh;
-        if (lmp) { WC4D_TRY(lmp_apply_impl<T>(c, rh, t, flags)); tr = t; }  // C rhat
-        launch_pcg_p<T>(c->stream, grid, nA, scal, p, tr);                  // p = C rhat + beta p
+        if (lmp) {
+            WC4D_TRY(lmp_cg_step<T>(c, x, r, rh, p, q, t, tol_k, qcf_dev, it));
+            launch_pcg_p<T>(c->stream, grid, nA, scal, p, t);               // p = C rhat + beta p
+        } else {
+            launch_dot_partial<T>(c->stream, grid, nA, p, q, pa);
+            launch_pcg_alpha(c->stream, grid, pa, scal, flags);             // alpha = rho / p^T A p
+            launch_pcg_xr<T>(c->stream, grid, nA, scal, x, r, p, q, pb);    // x += alpha p; r -= alpha q
+            launch_pcg_rh<T>(c->stream, grid, nA, scal, rh, q, pc);         // rhat -= alpha A p
+            launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
+            launch_pcg_p<T>(c->stream, grid, nA, scal, p, rh);              // p = rhat + beta p
+        }
         WC4D_TRY(check_launch(c, "pcg iteration"));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
         WC4D_TRY(sync(c, "pcg iteration"));
@@ -1197,7 +1312,7 @@ static wc4d_status true_residual(wc4d_ctx *c, const double *x, double *r64, doub
 // FP32 residual is replaced by the FP64 true residual rhs - A x, while the
 // search direction p is kept.  Unlike restarted refinement this keeps the
 // Krylov space, so the iteration count stays close to the FP64 solver's.
-constexpr double kReliableDelta = 1e-2;
+constexpr double kReliableDelta = 1e-3;
 
 static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, int force, bool use_lmp,
                                 double *qcf_dev, int *iters_out, double *rel_out, bool *breakdown_out)
@@ -1247,24 +1362,18 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
     int it = 0;
     for (; it < nit && !converged; ++it) {
         WC4D_TRY(hvp_impl<float>(c, p, q, 1, nA, false));                    // q = A p
-        {
+        if (lmp) {
+            WC4D_TRY(lmp_cg_step<float>(c, d, r, rh, p, q, t, tol_k, qcf_dev, it));
+            ProfScope ps(c, PROF_VEC);
+            launch_pcg_p<float>(c->stream, grid, nA, scal, p, t);            // p = C rhat + beta p
+        } else {
             ProfScope ps(c, PROF_VEC);
             launch_dot_partial<float>(c->stream, grid, nA, p, q, pa);
             launch_pcg_alpha(c->stream, grid, pa, scal, flags);              // alpha = rho / p^T A p
             launch_pcg_xr<float>(c->stream, grid, nA, scal, d, r, p, q, pb); // d += alpha p; r -= alpha q
-        }
-        const float *tq = q;
-        if (lmp) { WC4D_TRY(lmp_apply_impl<float>(c, q, t, flags)); tq = t; }
-        {
-            ProfScope ps(c, PROF_VEC);
-            launch_pcg_rh<float>(c->stream, grid, nA, scal, rh, tq, pc);     // rhat -= alpha C^T A p
+            launch_pcg_rh<float>(c->stream, grid, nA, scal, rh, q, pc);      // rhat -= alpha A p
             launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
-        }
-        const float *tr = rh;
-        if (lmp) { WC4D_TRY(lmp_apply_impl<float>(c, rh, t, flags)); tr = t; }
-        {
-            ProfScope ps(c, PROF_VEC);
-            launch_pcg_p<float>(c->stream, grid, nA, scal, p, tr);           // p = C rhat + beta p
+            launch_pcg_p<float>(c->stream, grid, nA, scal, p, rh);           // p = rhat + beta p
         }
         WC4D_TRY(check_launch(c, "pcg iteration"));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));

@@ -1,0 +1,211 @@
+// One-sided (Hestenes) Jacobi for the small eigenproblems of the sketch (the
+// EVD of K_1 in Alg. 3, of F^T F in Alg. 4, the SVD of R_3 in Alg. 5) with
+// m <= 256, as ONE persistent cooperative launch instead of one launch per
+// round plus a host synchronisation per sweep.
+//
+// CTA b rotates column pair b of the round-robin ordering (P/2 CTAs, one
+// per SM, P = m rounded up to a multiple of 2, zero padded), one row per
+// thread, in FP64.  The FP64 pipe of this GPU retires about 1.6 FMA per
+// clock per SM, so the rotations are spread over as many SMs as there are
+// pairs rather than packed into a few.  X and the accumulated rotations V
+// are double-buffered in global memory (L2-resident): round r reads buffer
+// r % 2 and writes every column, rotated or not, to the other, then a grid
+// barrier (release/acquire on one counter, bounded spin) ends the round.
+// Reads bypass L1 (the columns were written by other SMs).  Sweeps repeat
+// until one makes no rotation, or max_sweeps.  Zero padding columns never
+// rotate.
+#include "wc4d_internal.cuh"
+
+namespace {
+
+constexpr int JQ_MAXP = 256;
+constexpr int JQ_THREADS = 256;   // one row per thread
+constexpr unsigned JQ_SPIN = 1u << 22;
+
+// Arrive on the grid barrier and wait until `target` arrivals; false (and
+// *err = 1) when the bounded wait gives up.
+__device__ __forceinline__ bool jq_barrier(unsigned *bar, unsigned target, int *err)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        unsigned v = 0, it = 0;
+        int ok = 1;
+        do {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (++it > JQ_SPIN) { ok = 0; atomicExch(err, 1); break; }
+        } while (v < target);
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+struct JqArgs {
+    int m, P;
+    const double *X0;   // m x m, column-major, ld m
+    double *XV;         // four P x P buffers X_a, V_a, X_b, V_b; the result ends in X_a, V_a
+    double tol;
+    int max_sweeps;
+    int *rot;           // max_sweeps rotation counters (zeroed here)
+    unsigned *bar;      // barrier counter (zero at launch)
+    int *err;           // 1 after a barrier timeout
+    int *status;        // sweeps used, or -1 when not converged
+    int want_v;         // 0: V is neither accumulated nor written
+};
+
+__global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
+{
+    __shared__ double red[3][JQ_THREADS / 32];
+    __shared__ double cs[2];
+    __shared__ int doit_s, conv_s;
+    const int P = a.P, pair = blockIdx.x, r = threadIdx.x;
+    const unsigned G = gridDim.x;
+    const int64_t PP = (int64_t)P * P;
+    double *Xc = a.XV, *Vc = a.XV + PP, *Xn = a.XV + 2 * PP, *Vn = a.XV + 3 * PP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool wv = a.want_v != 0;
+    for (int k = 0; k < 2; ++k) {   // this CTA initialises columns 2 pair, 2 pair + 1
+        const int j = 2 * pair + k;
+        if (r < P) {
+            Xc[(int64_t)j * P + r] = (r < a.m && j < a.m) ? a.X0[(int64_t)j * a.m + r] : 0.0;
+            if (wv) Vc[(int64_t)j * P + r] = (r == j) ? 1.0 : 0.0;
+        }
+    }
+    if (pair == 0)
+        for (int s = r; s < a.max_sweeps; s += blockDim.x) a.rot[s] = 0;
+    unsigned target = G;
+    if (!jq_barrier(a.bar, target, a.err)) return;
+
+    int sweeps = 0;
+    bool converged = false;
+    for (; sweeps < a.max_sweeps && !converged; ++sweeps) {
+        for (int round = 0; round < P - 1; ++round) {
+            const int pos_b = P - 1 - pair;
+            const int ja = pair == 0 ? 0 : 1 + (pair - 1 + round) % (P - 1);
+            const int jb = 1 + (pos_b - 1 + round) % (P - 1);
+            const int p = min(ja, jb), q = max(ja, jb);
+            double u = 0.0, w = 0.0, y = 0.0, z = 0.0;
+            if (r < P) {
+                u = __ldcg(Xc + (int64_t)p * P + r);
+                w = __ldcg(Xc + (int64_t)q * P + r);
+                if (wv) {
+                    y = __ldcg(Vc + (int64_t)p * P + r);
+                    z = __ldcg(Vc + (int64_t)q * P + r);
+                }
+            }
+            double s0 = u * u, s1 = w * w, s2 = u * w;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            if (lane == 0) { red[0][warp] = s0; red[1][warp] = s1; red[2][warp] = s2; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double aa = 0.0, bb = 0.0, g = 0.0;
+                for (int i = 0; i < JQ_THREADS / 32; ++i) { aa += red[0][i]; bb += red[1][i]; g += red[2][i]; }
+                int doit = 0;
+                // |g| > tol sqrt(a b), squared: no FP64 square root or division
+                if (g * g > a.tol * a.tol * (aa * bb) && fabs(g) > 1e-300) {
+                    // The tangent only needs FP32 accuracy (the rotation then
+                    // leaves |g| ~1e-7 of its value instead of 0, and the next
+                    // sweep removes it); c = (1 + t^2)^{-1/2} is completed to
+                    // FP64 by two Newton steps so that c^2 + s^2 = 1 holds to
+                    // rounding and the column norms are preserved.
+                    // zeta = (b - a) / (2 g), both scaled by 2^-e into FP32 range
+                    const double d = bb - aa, g2 = 2.0 * g;
+                    const int e = ilogb(g2);
+                    const float zeta = (float)scalbn(d, -e) / (float)scalbn(g2, -e);
+                    double tn;
+                    if (isfinite(zeta) && fabsf(zeta) < 1e18f)
+                        tn = (double)(copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))));
+                    else
+                        tn = g2 / (2.0 * d);   // |zeta| huge: t = 1 / (2 zeta)
+                    const double h = fma(tn, tn, 1.0);
+                    double c = (double)rsqrtf((float)h);
+                    c = c * fma(-0.5 * h, c * c, 1.5);
+                    c = c * fma(-0.5 * h, c * c, 1.5);
+                    cs[0] = c;
+                    cs[1] = c * tn;
+                    doit = 1;
+                    atomicAdd(a.rot + sweeps, 1);
+                }
+                doit_s = doit;
+            }
+            __syncthreads();
+            if (r < P) {
+                if (doit_s) {
+                    const double c = cs[0], sn = cs[1];
+                    Xn[(int64_t)p * P + r] = c * u - sn * w;
+                    Xn[(int64_t)q * P + r] = sn * u + c * w;
+                    if (wv) {
+                        Vn[(int64_t)p * P + r] = c * y - sn * z;
+                        Vn[(int64_t)q * P + r] = sn * y + c * z;
+                    }
+                } else {
+                    Xn[(int64_t)p * P + r] = u;
+                    Xn[(int64_t)q * P + r] = w;
+                    if (wv) {
+                        Vn[(int64_t)p * P + r] = y;
+                        Vn[(int64_t)q * P + r] = z;
+                    }
+                }
+            }
+            target += G;
+            if (!jq_barrier(a.bar, target, a.err)) return;
+            double *t0 = Xc, *t1 = Vc;
+            Xc = Xn; Vc = Vn; Xn = t0; Vn = t1;
+        }
+        if (threadIdx.x == 0) conv_s = (__ldcg(a.rot + sweeps) == 0);
+        __syncthreads();
+        converged = conv_s != 0;
+    }
+    if (Xc != a.XV) {   // the result sits in the b buffers: move this CTA's two columns
+        for (int k = 0; k < 2; ++k) {
+            const int64_t j = 2 * pair + k;
+            if (r < P) {
+                a.XV[j * P + r] = __ldcg(Xc + j * P + r);
+                if (wv) a.XV[PP + j * P + r] = __ldcg(Vc + j * P + r);
+            }
+        }
+    }
+    if (pair == 0 && threadIdx.x == 0) *a.status = converged ? sweeps : -1;
+}
+
+}  // namespace
+
+int jacobi_coop_size(int m) { return (m >= 2 && m <= JQ_MAXP) ? m + (m & 1) : 0; }
+
+size_t jacobi_coop_doubles(int m)
+{
+    const size_t P = (size_t)jacobi_coop_size(m);
+    return 4 * P * P;
+}
+
+// Returns false (nothing runs, error state cleared) when the cooperative
+// launch is refused.  XV: jacobi_coop_doubles(m) doubles; the result is
+// X = XV[0, P^2), V = XV[P^2, 2 P^2).  rot: max_sweeps ints; bar: one
+// counter, zeroed here; err: set to 1 if a grid barrier times out.  With
+// want_v false only X is produced.
+bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, double tol, int max_sweeps, int *rot,
+                        unsigned *bar, int *err, int *status, bool want_v)
+{
+    const int P = jacobi_coop_size(m);
+    if (P == 0) return false;
+    if (cudaMemsetAsync(bar, 0, sizeof(unsigned), s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    JqArgs args{m, P, X0, XV, tol, max_sweeps, rot, bar, err, status, want_v ? 1 : 0};
+    void *params[] = {&args};
+    wc4d_note_launch();
+    if (cudaLaunchCooperativeKernel((const void *)k_jacobi_coop, dim3(P / 2), dim3(JQ_THREADS), params, 0, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}

@@ -293,66 +293,149 @@ template int launch_atb<float>(cudaStream_t, int, int64_t, int, int, const float
                                int64_t, double *, size_t, int *, double *, int);
 
 // ----------------------------------------------------------------------------
-// Cholesky A = R^T R (R upper, column-major m x m), right-looking, one CTA.
-// info = 0, or j+1 when pivot j is not positive / not finite.
+// Cholesky A = R^T R (R upper, column-major m x m), right-looking and
+// blocked by 32: per block step, one CTA factors the diagonal block in shared
+// memory, one CTA per block column solves the row panel R_kj = R_kk^{-T} A_kj,
+// and one CTA per trailing upper block applies A_ij -= R_ki^T R_kj.
+// info = 0, or j+1 when pivot j is not positive / not finite (later steps
+// then do nothing).
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_chol_upper(int m, const double *A, double *R, int *info)
+constexpr int CB = 32;
+
+__global__ void k_chol_copy(int m, const double *A, double *R, int *info)
 {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0) *info = 0;
+    if (idx >= (int64_t)m * m) return;
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    R[idx] = (i <= j) ? A[idx] : 0.0;
+}
+
+// Diagonal block k0 .. k0+nb-1 (nb <= 32), in place.
+__global__ void __launch_bounds__(1024) k_chol_diag(int m, int k0, double *R, int *info)
+{
+    __shared__ double a[CB][CB + 1];
+    __shared__ double rinv;
     __shared__ int bad;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int64_t idx = tid; idx < (int64_t)m * m; idx += nt) {
-        int i = (int)(idx % m), j = (int)(idx / m);
-        R[idx] = (i <= j) ? A[idx] : 0.0;
-    }
-    if (tid == 0) bad = 0;
+    if (*info) return;
+    const int nb = min(CB, m - k0);
+    const int ti = threadIdx.x % CB, tj = threadIdx.x / CB;   // row, column within the block
+    if (ti < nb && tj < nb && ti <= tj) a[ti][tj] = R[(int64_t)(k0 + tj) * m + k0 + ti];
+    if (threadIdx.x == 0) bad = 0;
     __syncthreads();
-    for (int j = 0; j < m; ++j) {
-        if (tid == 0) {
-            double d = R[(int64_t)j * m + j];
-            if (!(d > 0.0) || !isfinite(d)) bad = j + 1;
-            else R[(int64_t)j * m + j] = sqrt(d);
+    for (int c = 0; c < nb; ++c) {
+        if (threadIdx.x == 0) {
+            const double d = a[c][c];
+            if (!(d > 0.0) || !isfinite(d)) {
+                bad = k0 + c + 1;
+            } else {
+                const double r = sqrt(d);
+                a[c][c] = r;
+                rinv = 1.0 / r;
+            }
         }
         __syncthreads();
         if (bad) break;
-        const double rjj = R[(int64_t)j * m + j];
-        for (int i = j + 1 + tid; i < m; i += nt) R[(int64_t)i * m + j] /= rjj;
+        if (ti == c && tj > c && tj < nb) a[c][tj] *= rinv;
         __syncthreads();
-        const int w = m - j - 1;
-        for (int64_t idx = tid; idx < (int64_t)w * w; idx += nt) {
-            int a = (int)(idx % w), b = (int)(idx / w);
-            if (a > b) continue;
-            int ga = j + 1 + a, gb = j + 1 + b;
-            R[(int64_t)gb * m + ga] -= R[(int64_t)ga * m + j] * R[(int64_t)gb * m + j];
-        }
+        if (ti > c && ti <= tj && tj < nb) a[ti][tj] -= a[c][ti] * a[c][tj];
         __syncthreads();
     }
-    if (tid == 0) *info = bad;
+    if (bad) {
+        if (threadIdx.x == 0) *info = bad;
+        return;
+    }
+    if (ti < nb && tj < nb && ti <= tj) R[(int64_t)(k0 + tj) * m + k0 + ti] = a[ti][tj];
+}
+
+// Row panel: for block column j0 = k0 + nb + 32 blockIdx.x, R_kj = R_kk^{-T} A_kj.
+__global__ void __launch_bounds__(1024) k_chol_panel(int m, int k0, double *R, const int *info)
+{
+    __shared__ double l[CB][CB + 1], b[CB][CB + 1], rl[CB];
+    if (*info) return;
+    const int nb = min(CB, m - k0);
+    const int j0 = k0 + nb + CB * blockIdx.x;
+    const int nj = min(CB, m - j0);
+    const int ti = threadIdx.x % CB, tj = threadIdx.x / CB;
+    if (ti < nb && tj < nb) l[ti][tj] = (ti <= tj) ? R[(int64_t)(k0 + tj) * m + k0 + ti] : 0.0;   // R_kk
+    if (ti < nb && tj < nj) b[ti][tj] = R[(int64_t)(j0 + tj) * m + k0 + ti];
+    if (threadIdx.x < nb) rl[threadIdx.x] = 1.0 / R[(int64_t)(k0 + threadIdx.x) * m + k0 + threadIdx.x];
+    __syncthreads();
+    // forward substitution with R_kk^T (lower): row c of the solution, then
+    // eliminate it from the rows below
+    for (int c = 0; c < nb; ++c) {
+        if (ti == c && tj < nj) b[c][tj] *= rl[c];
+        __syncthreads();
+        if (ti > c && ti < nb && tj < nj) b[ti][tj] -= l[c][ti] * b[c][tj];
+        __syncthreads();
+    }
+    if (ti < nb && tj < nj) R[(int64_t)(j0 + tj) * m + k0 + ti] = b[ti][tj];
+}
+
+// Trailing update: CTA t -> upper block pair (bi <= bj) after block step k0.
+__global__ void __launch_bounds__(1024) k_chol_update(int m, int k0, double *R, const int *info)
+{
+    __shared__ double pi[CB][CB + 1], pj[CB][CB + 1];
+    if (*info) return;
+    const int nb = min(CB, m - k0);
+    const int t = blockIdx.x;
+    int bj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+    while (bj * (bj + 1) / 2 > t) --bj;
+    const int bi = t - bj * (bj + 1) / 2;
+    const int i0 = k0 + nb + CB * bi, j0 = k0 + nb + CB * bj;
+    const int ti = threadIdx.x % CB, tj = threadIdx.x / CB;
+    // pi[c][x] = R(k0 + c, i0 + x), pj[c][y] = R(k0 + c, j0 + y)
+    pi[ti][tj] = (ti < nb && i0 + tj < m) ? R[(int64_t)(i0 + tj) * m + k0 + ti] : 0.0;
+    pj[ti][tj] = (ti < nb && j0 + tj < m) ? R[(int64_t)(j0 + tj) * m + k0 + ti] : 0.0;
+    __syncthreads();
+    const int gi = i0 + ti, gj = j0 + tj;
+    if (gi < m && gj < m && gi <= gj) {
+        double acc = 0.0;
+        for (int c = 0; c < nb; ++c) acc = fma(pi[c][ti], pj[c][tj], acc);
+        R[(int64_t)gj * m + gi] -= acc;
+    }
 }
 
 void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *info)
 {
-    WC4D_LAUNCH(k_chol_upper<<<1, 1024, 0, s>>>(m, A, R, info));
+    WC4D_LAUNCH(k_chol_copy<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, A, R, info));
+    for (int k0 = 0; k0 < m; k0 += CB) {
+        WC4D_LAUNCH(k_chol_diag<<<1, CB * CB, 0, s>>>(m, k0, R, info));
+        const int rest = m - k0 - CB;
+        if (rest <= 0) break;
+        const int nbj = ceil_div(rest, CB);
+        WC4D_LAUNCH(k_chol_panel<<<nbj, CB * CB, 0, s>>>(m, k0, R, info));
+        WC4D_LAUNCH(k_chol_update<<<nbj * (nbj + 1) / 2, CB * CB, 0, s>>>(m, k0, R, info));
+    }
 }
 
-// Inverse of an upper-triangular R (column-major): one thread per column,
-// back substitution R x = e_j.
-__global__ void k_trinv_upper(int m, const double *R, double *Rinv)
+// Inverse of an upper-triangular R (column-major): one CTA per column j,
+// column-oriented back substitution of R x = e_j in shared memory.
+__global__ void __launch_bounds__(256) k_trinv_upper(int m, const double *R, double *Rinv)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    double *x = Rinv + (int64_t)j * m;
-    for (int i = j + 1; i < m; ++i) x[i] = 0.0;
-    x[j] = 1.0 / R[(int64_t)j * m + j];
-    for (int i = j - 1; i >= 0; --i) {
-        double acc = 0.0;
-        for (int c = i + 1; c <= j; ++c) acc = fma(R[(int64_t)c * m + i], x[c], acc);
-        x[i] = -acc / R[(int64_t)i * m + i];
+    extern __shared__ double xs[];
+    double *rinv = xs + m;
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        xs[i] = (i == j) ? 1.0 : 0.0;
+        rinv[i] = (i <= j) ? 1.0 / R[(int64_t)i * m + i] : 0.0;
     }
+    __syncthreads();
+    for (int c = j; c >= 0; --c) {
+        const double xc = xs[c] * rinv[c];
+        __syncthreads();
+        if (threadIdx.x == 0) xs[c] = xc;
+        for (int i = threadIdx.x; i < c; i += blockDim.x) xs[i] = fma(-R[(int64_t)c * m + i], xc, xs[i]);
+        __syncthreads();
+    }
+    double *x = Rinv + (int64_t)j * m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) x[i] = xs[i];
 }
 
 void launch_trinv_upper(cudaStream_t s, int m, const double *R, double *Rinv)
 {
-    WC4D_LAUNCH(k_trinv_upper<<<ceil_div(m, 64), 64, 0, s>>>(m, R, Rinv));
+    WC4D_LAUNCH(k_trinv_upper<<<m, 256, 2 * sizeof(double) * m, s>>>(m, R, Rinv));
 }
 
 // RT = R^T (m x m column-major).
@@ -502,6 +585,30 @@ __global__ void k_sort_cols(int m, int mp, const double *wn, const double *V, do
     }
     __syncthreads();
     for (int r = threadIdx.x; r < m; r += blockDim.x) Vout[(int64_t)rank * m + r] = V[(int64_t)j * mp + r];
+}
+
+// Left variant: w[rank] = |X_j|^2 (decreasing), Vout[:, rank] = X[0:m, j] / |X_j|.
+__global__ void k_sort_cols_left(int m, int mp, const double *wn, const double *X, double *w, double *Vout)
+{
+    int j = blockIdx.x;
+    __shared__ int rank;
+    if (threadIdx.x == 0) {
+        int r = 0;
+        double wj = wn[j];
+        for (int i = 0; i < m; ++i)
+            if (wn[i] > wj || (wn[i] == wj && i < j)) ++r;
+        rank = r;
+        w[r] = wj * wj;
+    }
+    __syncthreads();
+    const double inv = wn[j] > 0.0 ? 1.0 / wn[j] : 0.0;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) Vout[(int64_t)rank * m + r] = X[(int64_t)j * mp + r] * inv;
+}
+
+void launch_jacobi_finish_left(cudaStream_t s, int m, int mp, const double *X, double *w, double *Vout)
+{
+    WC4D_LAUNCH(k_colnorm<<<m, 128, 0, s>>>(m, mp, X, w + m));
+    WC4D_LAUNCH(k_sort_cols_left<<<m, 128, 0, s>>>(m, mp, w + m, X, w, Vout));
 }
 
 void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const double *V, double *w, double *Vout)
@@ -776,6 +883,270 @@ template void launch_lmp_combine_rm<double>(cudaStream_t, int, int64_t, int, int
                                             const double *, const double *, double *, const int *);
 template void launch_lmp_combine_rm<float>(cudaStream_t, int, int64_t, int, int, const float *, const double *,
                                            const double *, const float *, float *, const int *);
+
+// ----------------------------------------------------------------------------
+// One split-preconditioned CG iteration (Alg. 1 with the spectral LMP of
+// eq. 15) after q = A p, with two passes over the row-major Ritz vectors
+// instead of two LMP applications of two passes each:
+//   pass A : s = U^T q, e = U^T rhat, p^T q;
+//   coef   : alpha = rho / p^T q, w1 = alpha c o s,
+//            w2 = c o (e - alpha (1 - c) o s)   [= c o U^T rhat_new when
+//            U^T U = I; e is recomputed from rhat every iteration, so the
+//            identity enters one step only];
+//   pass B : rhat <- rhat - alpha C q = rhat - alpha q + U w1,
+//            t = C rhat = rhat - U w2, x += alpha p, r -= alpha q, with the
+//            partial sums of |rhat|^2 and |r|^2 for the beta kernel.
+// ----------------------------------------------------------------------------
+constexpr int PA_ROWS = 512;   // rows per CTA of pass A (at most)
+
+int lmp_pass_a_splits(int64_t nA, int num_sms)
+{
+    const int s = ceil_div(nA, PA_ROWS);
+    return ceil_div(s, num_sms) * num_sms;   // a whole number of CTAs per SM
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_lmp_pass_a(int64_t nA, int kp, int64_t rows_per, const T *__restrict__ Urm,
+                                                    const T *__restrict__ q, const T *__restrict__ rh,
+                                                    const T *__restrict__ p, double *part)
+{
+    __shared__ T qs[PA_ROWS], es[PA_ROWS];
+    __shared__ double acc[4][2][256];
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    const int rows = (int)max((int64_t)0, min(rows_per, nA - r0));
+    double pq = 0.0;
+    for (int r = threadIdx.x; r < PA_ROWS; r += blockDim.x) {
+        T qv = 0, ev = 0;
+        if (r < rows) {
+            qv = q[r0 + r];
+            ev = rh[r0 + r];
+            pq = fma((double)p[r0 + r], (double)qv, pq);
+        }
+        qs[r] = qv;
+        es[r] = ev;
+    }
+    pq = block_sum(pq);   // synchronises: qs, es are visible
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int kq = kp / 4;
+    for (int cb = 0; cb < kq; cb += 64) {
+        const int cg = cb + tx;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        if (cg < kq) {
+            const T *base = Urm + r0 * kp + 4 * cg;
+            int r = ty;
+            for (; r + 12 < rows; r += 16) {   // four rows of loads in flight per thread
+                Quad<T> u[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) u[h] = ld4cs(base + (int64_t)(r + 4 * h) * kp);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const T x = qs[r + 4 * h], y = es[r + 4 * h];
+                    a0 = fma(u[h].x, x, a0); a1 = fma(u[h].y, x, a1); a2 = fma(u[h].z, x, a2); a3 = fma(u[h].w, x, a3);
+                    b0 = fma(u[h].x, y, b0); b1 = fma(u[h].y, y, b1); b2 = fma(u[h].z, y, b2); b3 = fma(u[h].w, y, b3);
+                }
+            }
+            for (; r < rows; r += 4) {
+                Quad<T> u = ld4cs(base + (int64_t)r * kp);
+                const T x = qs[r], y = es[r];
+                a0 = fma(u.x, x, a0); a1 = fma(u.y, x, a1); a2 = fma(u.z, x, a2); a3 = fma(u.w, x, a3);
+                b0 = fma(u.x, y, b0); b1 = fma(u.y, y, b1); b2 = fma(u.z, y, b2); b3 = fma(u.w, y, b3);
+            }
+        }
+        acc[ty][0][4 * tx + 0] = (double)a0; acc[ty][0][4 * tx + 1] = (double)a1;
+        acc[ty][0][4 * tx + 2] = (double)a2; acc[ty][0][4 * tx + 3] = (double)a3;
+        acc[ty][1][4 * tx + 0] = (double)b0; acc[ty][1][4 * tx + 1] = (double)b1;
+        acc[ty][1][4 * tx + 2] = (double)b2; acc[ty][1][4 * tx + 3] = (double)b3;
+        __syncthreads();
+        if (ty < 2 && cg < kq) {   // ty 0 writes s, ty 1 writes e
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = 4 * tx + j;
+                part[((int64_t)ty * kp + 4 * cg + j) * gridDim.x + blockIdx.x] =
+                    acc[0][ty][c] + acc[1][ty][c] + acc[2][ty][c] + acc[3][ty][c];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[2 * (int64_t)kp * gridDim.x + blockIdx.x] = pq;
+}
+
+// Sums the pass-A partials (column c of the transposed layout: part[c S + b];
+// c < kp: s, kp <= c < 2 kp: e, c = 2 kp: p^T q), one warp per sum in a fixed
+// order, into sums[]; the last CTA to finish (counter *done, reset by it)
+// forms alpha, w1, w2 and publishes alpha (and the breakdown flag).
+__global__ void __launch_bounds__(256) k_lmp_coef(int S, int k, int kp, const double *part, const double *cvec,
+                                                  double *scal, int *flags, double *sums, double *w,
+                                                  unsigned *done)
+{
+    __shared__ int last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + warp;
+    if (c <= 2 * kp) {
+        const double *src = part + (int64_t)c * S;
+        double a0 = 0.0, a1 = 0.0;
+        int s = lane;
+        for (; s + 32 < S; s += 64) {
+            a0 += src[s];
+            a1 += src[s + 32];
+        }
+        if (s < S) a0 += src[s];
+        double a = warp_sum(a0 + a1);
+        if (lane == 0) sums[c] = a;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(done, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double pq = __ldcg(sums + 2 * kp);
+    const bool fin = flags[0] != 0;
+    const bool bad = !fin && (!(pq > 0.0) || !isfinite(pq));
+    const double alpha = (!fin && !bad) ? scal[0] / pq : 0.0;   // scal[0] = rho
+    for (int i = threadIdx.x; i < kp; i += blockDim.x) {
+        const double cc = (i < k) ? cvec[i] : 0.0;
+        const double si = __ldcg(sums + i), ei = __ldcg(sums + kp + i);
+        w[i] = alpha * cc * si;
+        w[kp + i] = cc * (ei - alpha * (1.0 - cc) * si);
+    }
+    if (threadIdx.x == 0) {
+        scal[5] = pq;
+        scal[1] = alpha;
+        if (bad) { flags[1] = 1; flags[0] = 1; }
+        *done = 0u;
+    }
+}
+
+// Four consecutive values of a 16-byte aligned shared-memory array.
+__device__ __forceinline__ Quad<float> ld4s(const float *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> ld4s(const double *p)
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    return {a.x, a.y, b.x, b.y};
+}
+
+// Pass B reads the column-major copy of U (ld nA) like a GEMV y = U w: a CTA
+// owns PB_ROWS consecutive rows; thread (g, ch) = (threadIdx.x % 32,
+// threadIdx.x / 32) accumulates rows 4g .. 4g+3 of the CTA (one 16-byte load
+// per column: a warp reads 512 contiguous bytes of a column) over the ch-th
+// eighth of the k columns, eight columns of loads in flight; the eight
+// partial sums of a row are added in shared memory and one thread per row
+// finishes it.
+constexpr int PB_ROWS = 128;
+constexpr int PB_CHUNKS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, const T *__restrict__ U,
+                                                    const double *__restrict__ w, const double *__restrict__ scal,
+                                                    const T *__restrict__ q, const T *__restrict__ p, T *rh, T *t,
+                                                    T *x, T *r, double *part)
+{
+    extern __shared__ __align__(16) double wsm[];
+    T *w1 = reinterpret_cast<T *>(wsm), *w2 = w1 + kp;
+    T (*red)[PB_CHUNKS][PB_ROWS] = reinterpret_cast<T (*)[PB_CHUNKS][PB_ROWS]>(w2 + kp);
+    for (int i = threadIdx.x; i < kp; i += blockDim.x) {
+        w1[i] = (T)w[i];
+        w2[i] = (T)w[kp + i];
+    }
+    __syncthreads();
+    const int g = threadIdx.x & 31, ch = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * PB_ROWS;
+    const int64_t row0 = base + 4 * g;
+    const int cpc = (k + PB_CHUNKS - 1) / PB_CHUNKS;
+    const int i0 = min(k, ch * cpc), i1 = min(k, i0 + cpc);
+    T a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};
+    if (row0 + 3 < nA && (nA & 3) == 0) {
+        const T *col = U + row0;
+        for (int i = i0; i < i1; i += 8) {
+            Quad<T> v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = (i + u < i1) ? ld4cs(col + (int64_t)(i + u) * nA) : Quad<T>{0, 0, 0, 0};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int ii = min(i + u, kp - 1);   // v[u] is zero past i1
+                const T c1 = w1[ii], c2 = w2[ii];
+                a1[0] = fma(v[u].x, c1, a1[0]); a1[1] = fma(v[u].y, c1, a1[1]);
+                a1[2] = fma(v[u].z, c1, a1[2]); a1[3] = fma(v[u].w, c1, a1[3]);
+                a2[0] = fma(v[u].x, c2, a2[0]); a2[1] = fma(v[u].y, c2, a2[1]);
+                a2[2] = fma(v[u].z, c2, a2[2]); a2[3] = fma(v[u].w, c2, a2[3]);
+            }
+        }
+    } else {   // ragged tail (or nA not a multiple of 4): one row at a time
+        for (int j = 0; j < 4; ++j) {
+            const int64_t row = row0 + j;
+            if (row >= nA) break;
+            for (int i = i0; i < i1; ++i) {
+                const T v = U[(int64_t)i * nA + row];
+                a1[j] = fma(v, w1[i], a1[j]);
+                a2[j] = fma(v, w2[i], a2[j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        red[0][ch][4 * g + j] = a1[j];
+        red[1][ch][4 * g + j] = a2[j];
+    }
+    __syncthreads();
+    const double alpha = scal[1];
+    double srh = 0.0, sr = 0.0;
+    if (threadIdx.x < PB_ROWS) {
+        const int rr = threadIdx.x;
+        const int64_t row = base + rr;
+        if (row < nA) {
+            T d1 = 0, d2 = 0;
+#pragma unroll
+            for (int c = 0; c < PB_CHUNKS; ++c) {
+                d1 += red[0][c][rr];
+                d2 += red[1][c][rr];
+            }
+            const double qv = (double)q[row];
+            const double rhn = (double)rh[row] - alpha * qv + (double)d1;
+            rh[row] = (T)rhn;
+            t[row] = (T)(rhn - (double)d2);
+            x[row] = (T)((double)x[row] + alpha * (double)p[row]);
+            const double rn = (double)r[row] - alpha * qv;
+            r[row] = (T)rn;
+            srh = rhn * rhn;
+            sr = rn * rn;
+        }
+    }
+    srh = block_sum(srh);
+    sr = block_sum(sr);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = srh;
+        part[gridDim.x + blockIdx.x] = sr;
+    }
+}
+
+int lmp_pass_b_grid(int64_t nA) { return ceil_div(nA, PB_ROWS); }
+
+template <typename T>
+void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const T *Ucm,
+                      const double *cvec, const T *q, const T *p, T *rh, T *t, T *x, T *r, double *scal, int *flags,
+                      double *partA, double *w, double *partB, unsigned *done)
+{
+    const int S = lmp_pass_a_splits(nA, num_sms);
+    const int64_t rows_per = (nA + S - 1) / S;
+    WC4D_LAUNCH(k_lmp_pass_a<T><<<S, 256, 0, s>>>(nA, kp, rows_per, Urm, q, rh, p, partA));
+    double *sums = w + 2 * kp;
+    WC4D_LAUNCH(k_lmp_coef<<<ceil_div(2 * kp + 1, 8), 256, 0, s>>>(S, k, kp, partA, cvec, scal, flags, sums, w, done));
+    const int G = lmp_pass_b_grid(nA);
+    const size_t smem = (2 * (size_t)kp + 2 * PB_CHUNKS * PB_ROWS) * sizeof(T);
+    WC4D_LAUNCH(k_lmp_pass_b<T><<<G, 256, smem, s>>>(nA, k, kp, Ucm, w, scal, q, p, rh, t, x, r, partB));
+}
+
+template void launch_lmp_fused<double>(cudaStream_t, int, int64_t, int, int, const double *, const double *,
+                                       const double *, const double *, const double *, double *, double *, double *,
+                                       double *, double *, int *, double *, double *, double *, unsigned *);
+template void launch_lmp_fused<float>(cudaStream_t, int, int64_t, int, int, const float *, const float *,
+                                      const double *, const float *, const float *, float *, float *, float *,
+                                      float *, double *, int *, double *, double *, double *, unsigned *);
 
 // ----------------------------------------------------------------------------
 // PCG (Alg. 1) vector and scalar kernels.  Scalars live in device memory:

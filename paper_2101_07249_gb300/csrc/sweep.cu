@@ -35,7 +35,7 @@ template <typename CT> __device__ __forceinline__ CT cmulconj(CT a, CT b)   // a
 // themselves; vectors of blocks 1..N use Q's.
 // ----------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy,
            const T *addX, int64_t ld_add, const T *__restrict__ specB, const T *__restrict__ specQ,
            const typename Cplx<T>::t *__restrict__ tw, int nBpairs)
@@ -64,6 +64,9 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
     }
     const T *xa = X + ja * ldx + ta * n;
     const T *xb = X + jb * ldx + tb * n;
+    const int half = n >> 1;
+    CT *tws = buf + n;   // twiddles W_n^k, k < n/2, staged once
+    for (int k = tid; k < half; k += nt) tws[k] = tw[k];
     for (int s = tid; s < n; s += nt) {
         CT v;
         v.x = xa[s];
@@ -71,16 +74,33 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
         buf[s] = v;
     }
     __syncthreads();
-    const int half = n >> 1;
-    // forward DIF: span h = n/2 .. 1, twiddle W_{2h}^{pos} = tw[pos * n/(2h)]
-    for (int lh = logn - 1; lh >= 0; --lh) {
-        const int h = 1 << lh, stride = half >> lh;
+    const int quarter = n >> 2;
+    // forward DIF, two radix-2 spans (h, h/2) per pass: each group of four
+    // points {j, j+h/2, j+h, j+3h/2} is closed under both butterfly layers
+    int lh = logn - 1;
+    for (; lh >= 1; lh -= 2) {
+        const int h = 1 << lh, hh = h >> 1;
+        const int s1 = half >> lh, s2 = n >> lh;   // W_{2h}^k = tws[k s1], W_h^k = tws[k s2]
+        for (int b = tid; b < quarter; b += nt) {
+            const int pos = b & (hh - 1);
+            const int j = ((b >> (lh - 1)) << (lh + 1)) + pos;
+            const CT e0 = buf[j], e1 = buf[j + hh], e2 = buf[j + h], e3 = buf[j + h + hh];
+            const CT a0 = cadd(e0, e2), a2 = cmul(csub(e0, e2), tws[pos * s1]);
+            const CT a1 = cadd(e1, e3), a3 = cmul(csub(e1, e3), tws[(pos + hh) * s1]);
+            const CT w = tws[pos * s2];
+            buf[j] = cadd(a0, a1);
+            buf[j + hh] = cmul(csub(a0, a1), w);
+            buf[j + h] = cadd(a2, a3);
+            buf[j + h + hh] = cmul(csub(a2, a3), w);
+        }
+        __syncthreads();
+    }
+    if (lh == 0) {   // odd log2 n: the last span-1 layer alone
         for (int b = tid; b < half; b += nt) {
-            int pos = b & (h - 1);
-            int j = ((b >> lh) << (lh + 1)) + pos;
-            CT a = buf[j], c = buf[j + h];
+            const int j = 2 * b;
+            const CT a = buf[j], c = buf[j + 1];
             buf[j] = cadd(a, c);
-            buf[j + h] = cmul(csub(a, c), tw[pos * stride]);
+            buf[j + 1] = csub(a, c);
         }
         __syncthreads();
     }
@@ -91,16 +111,30 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
         buf[p] = v;
     }
     __syncthreads();
-    // inverse DIT: span h = 1 .. n/2, twiddle conj(W_{2h}^{pos})
-    for (int lh = 0; lh < logn; ++lh) {
-        const int h = 1 << lh, stride = half >> lh;
+    // inverse DIT, spans (h, 2h) per pass on groups {j, j+h, j+2h, j+3h}
+    lh = 0;
+    for (; lh + 1 < logn; lh += 2) {
+        const int h = 1 << lh;
+        const int s1 = half >> lh, s2 = half >> (lh + 1);   // W_{2h}^k = tws[k s1], W_{4h}^k = tws[k s2]
+        for (int b = tid; b < quarter; b += nt) {
+            const int pos = b & (h - 1);
+            const int j = ((b >> lh) << (lh + 2)) + pos;
+            const CT e0 = buf[j], e1 = cmulconj(buf[j + h], tws[pos * s1]);
+            const CT e2 = buf[j + 2 * h], e3 = cmulconj(buf[j + 3 * h], tws[pos * s1]);
+            const CT a0 = cadd(e0, e1), a1 = csub(e0, e1), a2 = cadd(e2, e3), a3 = csub(e2, e3);
+            const CT c2 = cmulconj(a2, tws[pos * s2]), c3 = cmulconj(a3, tws[(pos + h) * s2]);
+            buf[j] = cadd(a0, c2);
+            buf[j + 2 * h] = csub(a0, c2);
+            buf[j + h] = cadd(a1, c3);
+            buf[j + 3 * h] = csub(a1, c3);
+        }
+        __syncthreads();
+    }
+    if (lh == logn - 1) {   // odd log2 n: the last span-n/2 layer alone
         for (int b = tid; b < half; b += nt) {
-            int pos = b & (h - 1);
-            int j = ((b >> lh) << (lh + 1)) + pos;
-            CT a = buf[j];
-            CT c = cmulconj(buf[j + h], tw[pos * stride]);
-            buf[j] = cadd(a, c);
-            buf[j + h] = csub(a, c);
+            const CT a = buf[b], c = cmulconj(buf[b + half], tws[b]);
+            buf[b] = cadd(a, c);
+            buf[b + half] = csub(a, c);
         }
         __syncthreads();
     }
@@ -150,17 +184,17 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
 {
     const int n = c->prob.n, N = c->prob.N;
     if (fft) {
-        size_t smem = (size_t)n * sizeof(typename Cplx<T>::t);
+        size_t smem = (size_t)(n + n / 2) * sizeof(typename Cplx<T>::t);
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_circ_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(WC4D_FFT_MAX_N * sizeof(typename Cplx<T>::t)));
+                                 (int)((WC4D_FFT_MAX_N + WC4D_FFT_MAX_N / 2) * sizeof(typename Cplx<T>::t)));
             attr = true;
         }
         int nB = (K + 1) / 2;
         int64_t nQ = ((int64_t)K * N + 1) / 2;
         int grid = (int)(nB + nQ);
-        WC4D_LAUNCH(k_circ_fft<T><<<grid, 256, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,
+        WC4D_LAUNCH(k_circ_fft<T><<<grid, 512, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,
                                               (const typename Cplx<T>::t *)tw, nB));
     } else {
         size_t smem = 2 * (size_t)n * sizeof(T);

@@ -211,6 +211,17 @@ void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *i
 void launch_trinv_upper(cudaStream_t s, int m, const double *R, double *Rinv);
 void launch_jacobi_init(cudaStream_t s, int m, int mp, const double *S, double *X, double *V);
 void launch_jacobi_round(cudaStream_t s, int mp, double *X, double *V, int round, double tol, int *rot);
+// One-launch cooperative FP64 Jacobi for 2 <= m <= 256 (P = jacobi_coop_size(m),
+// 0 otherwise): XV holds jacobi_coop_doubles(m) doubles, the result is
+// X = XV[0, P^2), V = XV[P^2, 2 P^2); rot holds max_sweeps ints, bar one
+// counter (zeroed by the launcher), err is set to 1 on a barrier timeout,
+// status receives the sweeps used or -1; false when the cooperative launch
+// is refused (nothing runs).
+int jacobi_coop_size(int m);
+size_t jacobi_coop_doubles(int m);
+bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, double tol, int max_sweeps, int *rot,
+                        unsigned *bar, int *err, int *status, bool want_v);
+void launch_jacobi_finish_left(cudaStream_t s, int m, int mp, const double *X, double *w, double *Vout);
 void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const double *V, double *w, double *Vout);
 void launch_rrt(cudaStream_t s, int m, const double *R, double *RT);
 void launch_symmetrize(cudaStream_t s, int m, double *S);
@@ -244,6 +255,18 @@ void launch_pcg_rh(cudaStream_t s, int grid, int64_t n, const double *scal, T *r
 template <typename T>
 void launch_pcg_p(cudaStream_t s, int grid, int64_t n, const double *scal, T *p, const T *t);
 void launch_pcg_alpha(cudaStream_t s, int grid, const double *part, double *scal, int *flags);
+// One fused split-preconditioned CG iteration after q = A p (one pass over
+// the row-major Ritz vectors Urm, one over the column-major copy Ucm, ld nA):
+// alpha in scal[1], rhat, t = C rhat, x, r updated, partials of |rhat|^2 and
+// |r|^2 in partB[0, G) and partB[G, 2G), G = lmp_pass_b_grid(nA).  partA:
+// lmp_pass_a_splits(nA, num_sms) x (2 kp + 1) doubles; w: 4 kp + 1 doubles;
+// done: a counter that is zero on entry (and is left at zero).
+int lmp_pass_a_splits(int64_t nA, int num_sms);
+int lmp_pass_b_grid(int64_t nA);
+template <typename T>
+void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const T *Ucm,
+                      const double *cvec, const T *q, const T *p, T *rh, T *t, T *x, T *r, double *scal, int *flags,
+                      double *partA, double *w, double *partB, unsigned *done);
 void launch_pcg_restart(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
                         int *flags);
 void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
