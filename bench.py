@@ -34,13 +34,16 @@ METRIC = "inner-loop time to rel-res 1e-6 and Hessian-vec products/s, mixed vs F
 
 # DRAM bytes per launch of the dominant kernel from `ncu` (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel class and workload; see profiles/.
-# Set to None whenever the kernel changes until it is re-measured.
-NCU_TRAFFIC = {}
+# k_gemv_sweep<float>: 540.4 MB per launch on the N = 8 window (8 subwindow
+# GEMVs), scaled by 40/8 to the N = 40 window (traffic grows with the number
+# of subwindows).  Reset to None whenever the kernel changes until re-measured.
+NCU_TRAFFIC = {("gemv_sweep_f32", "advdiff_n4096_N40"): 540.41e6 * 40 / 8}
 
-# Mixed-path PCG iterations (incl. refinement products) measured on the large
-# window; used only to express the CPU oracle's column-product rate in inner
-# loops per second.
-REF_PCG_PRODUCTS = None
+# Column Hessian products one mixed inner loop issues on the large window:
+# REVD with one power iteration (3 block products of k + l = 256 columns),
+# ~111 PCG iterations and 2 FP64 true residuals.  Used only to express the
+# CPU oracle's column-product rate in inner loops per second.
+INNER_LOOP_COLUMN_PRODUCTS = 3 * 256 + 111 + 2
 
 
 def _peaks():
@@ -101,15 +104,18 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- distributed
-def dist_init(n_gpus):
+def dist_init(n_gpus, backend=None):
+    """One process per GPU (torchrun env); NCCL on GPUs, gloo when asked (CPU tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        backend = backend or "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -120,13 +126,25 @@ def barrier(world):
 
 
 def max_over_ranks(world, v):
+    """Largest v over the ranks (the job's time is its slowest replica's)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Each replica solves its own independent problem (weak scaling)."""
+    return rank
+
+
+def job_throughput(world, steps, t_max):
+    """Inner loops per second of the whole job: every rank ran `steps`."""
+    return world * steps / t_max
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -159,7 +177,7 @@ def run_reference(args, cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    products = REF_PCG_PRODUCTS if REF_PCG_PRODUCTS else 3 * cfg.K
+    products = INNER_LOOP_COLUMN_PRODUCTS if cfg.name == "advdiff_n4096_N40" else 3 * cfg.K + 100
     times = []
     for i in range(args.warmup + args.steps):
         rate, dt = oracle_column_rate(cfg, cols=16)
@@ -209,7 +227,7 @@ def main():
     torch.cuda.set_device(local)
     w.load()
     meth = w.METHODS[args.method]
-    cfg = cfg.replace(seed=rank)
+    cfg = cfg.replace(seed=replica_seed(rank))
     tw = inputs.twin(cfg)
     S = w.Solver(cfg, tw, M_shared=False)
     ctx = S.ctx
@@ -255,7 +273,7 @@ def main():
     products_block = w.wc4d_hvp_count(ctx)
     clk = clocks.stop()
     t_max = max_over_ranks(world, t_dev)
-    value = world * args.steps / t_max
+    value = job_throughput(world, args.steps, t_max)
 
     # ---- end to end through host buffers: H2D of x^b and y (pinned), the
     # outer-loop set-up (innovations, rhs), the inner loop, D2H of x
