@@ -2,7 +2,6 @@
 // direct), the tangent-linear / adjoint sweeps as SIMT GEMM / GEMV over the
 // dense propagators, and the observation term H^T R^{-1} H.
 #include "wc4d_internal.cuh"
-#include "ptx.cuh"
 
 template <typename T> struct Cplx;
 template <> struct Cplx<double> { using t = double2; };
@@ -485,124 +484,6 @@ k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
     }
 }
 
-// Bulk-copy variant of the persistent sweep.  Each CTA streams its rows of
-// every M_t through a STAGES-deep ring of 32 KiB shared-memory chunks with
-// cp.async.bulk; the ring runs across subwindow boundaries, so the rows of
-// M_{t+1} are already in flight while the CTA waits at the grid barrier for
-// the vector of step t.  x (n values) is copied to shared memory through L2
-// after each barrier.  512 threads: half the threads per row of a 2-row
-// chunk (FP32, n = 4096), each reducing 16 values.
-constexpr int BULK_STAGES = 4;
-constexpr int BULK_CHUNK = 32768;
-
-template <typename T>
-__global__ void __launch_bounds__(512, 1)
-k_gemv_sweep_bulk(const T *__restrict__ M0, T *W, SweepArgs a)
-{
-    using namespace wc4d_ptx;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int n = a.n;
-    T *ring = reinterpret_cast<T *>(smem);                                  // BULK_STAGES x BULK_CHUNK bytes
-    T *xs = reinterpret_cast<T *>(smem + BULK_STAGES * BULK_CHUNK);         // n values
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + BULK_STAGES * BULK_CHUNK + (((size_t)n * sizeof(T) + 15) & ~size_t(15)));
-    __shared__ double part[16];
-    __shared__ int bad;
-    const int rows_per_chunk = max(1, BULK_CHUNK / (int)(n * sizeof(T)));
-    const int rbeg = blockIdx.x * a.rows_per_cta;
-    const int rend = min(n, rbeg + a.rows_per_cta);
-    const int my_rows = max(0, rend - rbeg);
-    const int chunks_per_step = (my_rows + rows_per_chunk - 1) / rows_per_chunk;
-    const int total = chunks_per_step * a.N;
-    const uint32_t LIM = 1u << 22;
-    if (threadIdx.x == 0) {
-        bad = 0;
-        for (int s = 0; s < BULK_STAGES; ++s) mbar_init(&full[s], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    // chunk g of the stream: step g / cps, rows rbeg + (g % cps) * rpc_chunk ...
-    auto issue = [&](int g) {
-        const int step = g / chunks_per_step, ci = g % chunks_per_step;
-        const int t = (a.mode == 0) ? step : a.N - 1 - step;
-        const int r0 = rbeg + ci * rows_per_chunk;
-        const int nr = min(rows_per_chunk, rend - r0);
-        const uint32_t bytes = (uint32_t)(nr * n * sizeof(T));
-        const int s = g % BULK_STAGES;
-        mbar_expect_tx(&full[s], bytes);
-        bulk_g2s(reinterpret_cast<unsigned char *>(ring) + (size_t)s * BULK_CHUNK,
-                 M0 + (int64_t)t * a.mstride + (int64_t)r0 * n, bytes, &full[s]);
-    };
-    if (threadIdx.x == 0)
-        for (int g = 0; g < min(BULK_STAGES, total); ++g) issue(g);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int g = 0;
-    for (int step = 0; step < a.N; ++step) {
-        const int t = (a.mode == 0) ? step : a.N - 1 - step;
-        const T *x = W + (int64_t)((a.mode == 0) ? t : t + 1) * n;
-        T *y = W + (int64_t)((a.mode == 0) ? t + 1 : t) * n;
-        double scale = 0.0;
-        if (a.mode == 1 && t >= a.t0 && (t - a.t0) % a.ts == 0) scale = a.obs_inv;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = __ldcg(x + i);
-        __syncthreads();
-        for (int ci = 0; ci < chunks_per_step; ++ci, ++g) {
-            const int s = g % BULK_STAGES;
-            const bool ok = mbar_wait(&full[s], (uint32_t)((g / BULK_STAGES) & 1), LIM);
-            if (!ok && lane == 0) atomicExch(&bad, 1);
-            const int r0 = rbeg + ci * rows_per_chunk;
-            const int nr = min(rows_per_chunk, rend - r0);
-            const T *chunk = reinterpret_cast<const T *>(reinterpret_cast<unsigned char *>(ring) + (size_t)s * BULK_CHUNK);
-            if (nr <= 16) {
-                // wpr warps share each row; one cross-warp reduction per chunk
-                const int wpr = 16 / nr;
-                const int q = warp / wpr, seg = warp % wpr;
-                if (q < nr) {
-                    const T *row = chunk + (size_t)q * n;
-                    T acc = 0;
-                    for (int e = seg * 32 + lane; e < n; e += wpr * 32) acc = fma(row[e], xs[e], acc);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                    if (lane == 0) part[warp] = (double)acc;
-                }
-                __syncthreads();
-                if (threadIdx.x < nr) {
-                    const int qq = threadIdx.x;
-                    double sum = 0.0;
-                    for (int i = 0; i < wpr; ++i) sum += part[qq * wpr + i];
-                    const int row_i = r0 + qq;
-                    const double old = (double)__ldcg(y + row_i);
-                    const double out = (a.mode == 0) ? old + sum : sum + ((row_i % a.obs_stride == 0) ? scale * old : 0.0);
-                    y[row_i] = (T)out;
-                }
-            } else {
-                // short rows: each warp reduces whole rows
-                for (int rr = warp; rr < nr; rr += 16) {
-                    const T *row = chunk + (size_t)rr * n;
-                    T acc = 0;
-                    for (int e = lane; e < n; e += 32) acc = fma(row[e], xs[e], acc);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                    if (lane == 0) {
-                        const int row_i = r0 + rr;
-                        const double old = (double)__ldcg(y + row_i);
-                        const double out = (a.mode == 0) ? old + (double)acc
-                                                         : (double)acc + ((row_i % a.obs_stride == 0) ? scale * old : 0.0);
-                        y[row_i] = (T)out;
-                    }
-                }
-            }
-            __syncthreads();   // the stage is free: refill it with chunk g + STAGES
-            if (threadIdx.x == 0 && g + BULK_STAGES < total) issue(g + BULK_STAGES);
-        }
-        if (bad) break;
-        if (step + 1 < a.N && !step_barrier(a.bar, step, gridDim.x, a.err)) { bad = 2; break; }
-    }
-    if (threadIdx.x == 0 && bad) {
-        atomicExch(a.err, 1);
-        // drain the copies still in flight (bounded)
-        for (int q = g; q < min(total, g + BULK_STAGES); ++q) mbar_wait(&full[q % BULK_STAGES], (q / BULK_STAGES) & 1, LIM);
-    }
-}
-
 // Launch configuration of the persistent sweep (one CTA of 512 threads per
 // SM, co-resident by cooperative launch).  Returns false if it cannot be used.
 template <typename T>
@@ -612,24 +493,11 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     constexpr int VEC = sizeof(T) == 8 ? 2 : 4;
     if (n % VEC != 0 || !aligned16(M0) || !aligned16(W) || ((int64_t)n * sizeof(T)) % 16 != 0) return false;
     using Acc = T;
-    // the register-load variant measured faster on GB300 (17 us vs 32 us per
-    // 4096^2 FP32 GEMV); the bulk-copy variant is kept behind WC4D_BULK=1
-    const char *bulk_env = getenv("WC4D_BULK");
-    const bool bulk = (int64_t)n * sizeof(T) <= BULK_CHUNK && bulk_env && bulk_env[0] == '1';
-    const size_t smem = bulk ? BULK_STAGES * BULK_CHUNK + (((size_t)n * sizeof(T) + 15) & ~size_t(15)) +
-                                   BULK_STAGES * sizeof(uint64_t)
-                             : 0;
-    static int max_blocks[2] = {-1, -1};
-    int &mb = max_blocks[bulk ? 1 : 0];
+    static int max_blocks = -1;
+    int &mb = max_blocks;
     if (mb < 0) {
         int per_sm = 0;
-        if (bulk) {
-            cudaFuncSetAttribute(k_gemv_sweep_bulk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(BULK_STAGES * BULK_CHUNK + 2 * BULK_CHUNK / 2 + 256));
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_sweep_bulk<T>, 512, smem);
-        } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_sweep<T, Acc>, 512, 0);
-        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_sweep<T, Acc>, 512, 0);
         mb = per_sm * num_sms;
     }
     int grid = std::min(num_sms, mb);
@@ -651,8 +519,8 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     args.err = err;
     void *params[] = {(void *)&M0, (void *)&W, (void *)&args};
     wc4d_note_launch();
-    const void *fn = bulk ? (const void *)k_gemv_sweep_bulk<T> : (const void *)k_gemv_sweep<T, Acc>;
-    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(512), params, smem, s) != cudaSuccess) {
+    if (cudaLaunchCooperativeKernel((const void *)k_gemv_sweep<T, Acc>, dim3(grid), dim3(512), params, 0, s) !=
+        cudaSuccess) {
         cudaGetLastError();   // fall back to one launch per subwindow
         return false;
     }
