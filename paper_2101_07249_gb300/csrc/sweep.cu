@@ -24,6 +24,10 @@ template <typename CT> __device__ __forceinline__ CT cmulconj(CT a, CT b)   // a
     return r;
 }
 
+// Shared-memory index of FFT element i: one complex pad after every 16, so
+// that the power-of-two strides of the butterfly layers spread over the banks.
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
 // ----------------------------------------------------------------------------
 // D^{1/2} on two real vectors at once: z = x_a + i x_b, radix-2 decimation-
 // in-frequency FFT (natural in, bit-reversed out) in shared memory, scale by
@@ -64,13 +68,16 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
     const T *xa = X + ja * ldx + ta * n;
     const T *xb = X + jb * ldx + tb * n;
     const int half = n >> 1;
-    CT *tws = buf + n;   // twiddles W_n^k, k < n/2, staged once
+    CT *tws = buf + n + (n >> 4);   // twiddles W_n^k, k < n/2, staged once
+    // the global loads of each loop are unrolled so that they are all in flight at once
+#pragma unroll 8
     for (int k = tid; k < half; k += nt) tws[k] = tw[k];
+#pragma unroll 8
     for (int s = tid; s < n; s += nt) {
         CT v;
         v.x = xa[s];
         v.y = hasb ? xb[s] : (T)0;
-        buf[s] = v;
+        buf[fpad(s)] = v;
     }
     __syncthreads();
     const int quarter = n >> 2;
@@ -83,31 +90,32 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
         for (int b = tid; b < quarter; b += nt) {
             const int pos = b & (hh - 1);
             const int j = ((b >> (lh - 1)) << (lh + 1)) + pos;
-            const CT e0 = buf[j], e1 = buf[j + hh], e2 = buf[j + h], e3 = buf[j + h + hh];
+            const CT e0 = buf[fpad(j)], e1 = buf[fpad(j + hh)], e2 = buf[fpad(j + h)], e3 = buf[fpad(j + h + hh)];
             const CT a0 = cadd(e0, e2), a2 = cmul(csub(e0, e2), tws[pos * s1]);
             const CT a1 = cadd(e1, e3), a3 = cmul(csub(e1, e3), tws[(pos + hh) * s1]);
             const CT w = tws[pos * s2];
-            buf[j] = cadd(a0, a1);
-            buf[j + hh] = cmul(csub(a0, a1), w);
-            buf[j + h] = cadd(a2, a3);
-            buf[j + h + hh] = cmul(csub(a2, a3), w);
+            buf[fpad(j)] = cadd(a0, a1);
+            buf[fpad(j + hh)] = cmul(csub(a0, a1), w);
+            buf[fpad(j + h)] = cadd(a2, a3);
+            buf[fpad(j + h + hh)] = cmul(csub(a2, a3), w);
         }
         __syncthreads();
     }
     if (lh == 0) {   // odd log2 n: the last span-1 layer alone
         for (int b = tid; b < half; b += nt) {
             const int j = 2 * b;
-            const CT a = buf[j], c = buf[j + 1];
-            buf[j] = cadd(a, c);
-            buf[j + 1] = csub(a, c);
+            const CT a = buf[fpad(j)], c = buf[fpad(j + 1)];
+            buf[fpad(j)] = cadd(a, c);
+            buf[fpad(j + 1)] = csub(a, c);
         }
         __syncthreads();
     }
+#pragma unroll 8
     for (int p = tid; p < n; p += nt) {
         T w = spec[p];
-        CT v = buf[p];
+        CT v = buf[fpad(p)];
         v.x *= w; v.y *= w;
-        buf[p] = v;
+        buf[fpad(p)] = v;
     }
     __syncthreads();
     // inverse DIT, spans (h, 2h) per pass on groups {j, j+h, j+2h, j+3h}
@@ -118,22 +126,22 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
         for (int b = tid; b < quarter; b += nt) {
             const int pos = b & (h - 1);
             const int j = ((b >> lh) << (lh + 2)) + pos;
-            const CT e0 = buf[j], e1 = cmulconj(buf[j + h], tws[pos * s1]);
-            const CT e2 = buf[j + 2 * h], e3 = cmulconj(buf[j + 3 * h], tws[pos * s1]);
+            const CT e0 = buf[fpad(j)], e1 = cmulconj(buf[fpad(j + h)], tws[pos * s1]);
+            const CT e2 = buf[fpad(j + 2 * h)], e3 = cmulconj(buf[fpad(j + 3 * h)], tws[pos * s1]);
             const CT a0 = cadd(e0, e1), a1 = csub(e0, e1), a2 = cadd(e2, e3), a3 = csub(e2, e3);
             const CT c2 = cmulconj(a2, tws[pos * s2]), c3 = cmulconj(a3, tws[(pos + h) * s2]);
-            buf[j] = cadd(a0, c2);
-            buf[j + 2 * h] = csub(a0, c2);
-            buf[j + h] = cadd(a1, c3);
-            buf[j + 3 * h] = csub(a1, c3);
+            buf[fpad(j)] = cadd(a0, c2);
+            buf[fpad(j + 2 * h)] = csub(a0, c2);
+            buf[fpad(j + h)] = cadd(a1, c3);
+            buf[fpad(j + 3 * h)] = csub(a1, c3);
         }
         __syncthreads();
     }
     if (lh == logn - 1) {   // odd log2 n: the last span-n/2 layer alone
         for (int b = tid; b < half; b += nt) {
-            const CT a = buf[b], c = cmulconj(buf[b + half], tws[b]);
-            buf[b] = cadd(a, c);
-            buf[b + half] = csub(a, c);
+            const CT a = buf[fpad(b)], c = cmulconj(buf[fpad(b + half)], tws[b]);
+            buf[fpad(b)] = cadd(a, c);
+            buf[fpad(b + half)] = csub(a, c);
         }
         __syncthreads();
     }
@@ -141,8 +149,9 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
     T *yb = Y + jb * ldy + tb * n;
     const T *aa = addX ? addX + ja * ld_add + ta * n : nullptr;
     const T *ab = addX ? addX + jb * ld_add + tb * n : nullptr;
+#pragma unroll 8
     for (int s = tid; s < n; s += nt) {
-        CT v = buf[s];
+        CT v = buf[fpad(s)];
         ya[s] = v.x + (aa ? aa[s] : (T)0);
         if (hasb) yb[s] = v.y + (ab ? ab[s] : (T)0);
     }
@@ -183,11 +192,12 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
 {
     const int n = c->prob.n, N = c->prob.N;
     if (fft) {
-        size_t smem = (size_t)(n + n / 2) * sizeof(typename Cplx<T>::t);
+        size_t smem = (size_t)(n + n / 16 + n / 2) * sizeof(typename Cplx<T>::t);
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_circ_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((WC4D_FFT_MAX_N + WC4D_FFT_MAX_N / 2) * sizeof(typename Cplx<T>::t)));
+                                 (int)((WC4D_FFT_MAX_N + WC4D_FFT_MAX_N / 16 + WC4D_FFT_MAX_N / 2) *
+                                       sizeof(typename Cplx<T>::t)));
             attr = true;
         }
         int nB = (K + 1) / 2;
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(512)
 k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
 {
     using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
-    constexpr int VEC = sizeof(V) / sizeof(T), UNR = 4;
+    constexpr int VEC = sizeof(V) / sizeof(T), UNR = sizeof(T) == 4 ? 8 : 4;   // 128 B of each row in flight per lane (FP32)
     const int n = a.n, nv = n / VEC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int rbeg = blockIdx.x * a.rows_per_cta;
