@@ -126,6 +126,15 @@ wc4d_status wc4d_set_covariance_row(wc4d_ctx *ctx, int32_t block, const double *
  * (+ D^{-1/2} b when Dm12b_host is not NULL). */
 wc4d_status wc4d_set_background_obs(wc4d_ctx *ctx, const double *xb_host, const double *y_host,
                                     const double *Dm12b_host);
+/* Next outer loop (Section 2.1, eq. 3): x_device (nA values, FP64) is the
+ * inner-loop solution of eq. 10, i.e. the preconditioned increment
+ * D^{-1/2} dp.  The linearisation point p = (x_0, eta_1..eta_N) becomes
+ * p + D^{1/2} x, D^{-1/2} b becomes D^{-1/2} b - x (b = p^b - p), and the
+ * model is re-run from the new point with the forcing eta added at the end
+ * of every subwindow (eq. 1); innovations and rhs are recomputed from the
+ * observations given to wc4d_set_background_obs.  WC4D_ESTATE before
+ * wc4d_set_background_obs. */
+wc4d_status wc4d_outer_update(wc4d_ctx *ctx, const double *x_device);
 /* Number of observations q of the problem. */
 int64_t     wc4d_nobs(const wc4d_ctx *ctx);
 /* Copy the right-hand side (nA values) to device memory. */

@@ -60,6 +60,7 @@ _SIGS = {
     "wc4d_set_covariance": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_double, C.c_double]),
     "wc4d_set_covariance_row": (C.c_int, [_V, C.c_int32, _D]),
     "wc4d_set_background_obs": (C.c_int, [_V, _D, _D, _D]),
+    "wc4d_outer_update": (C.c_int, [_V, _V]),
     "wc4d_nobs": (C.c_int64, [_V]),
     "wc4d_get_rhs": (C.c_int, [_V, _V]),
     "wc4d_hvp": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
@@ -197,6 +198,10 @@ def wc4d_set_background_obs(ctx, xb, y, Dm12b=None):
     y = np.ascontiguousarray(y, dtype=np.float64)
     Dm = None if Dm12b is None else np.ascontiguousarray(Dm12b, dtype=np.float64)
     _check(ctx, load().wc4d_set_background_obs(ctx, _hp(xb), _hp(y), _hp(Dm)))
+
+
+def wc4d_outer_update(ctx, x):
+    _check(ctx, load().wc4d_outer_update(ctx, _ptr(x)))
 
 
 def wc4d_nobs(ctx):

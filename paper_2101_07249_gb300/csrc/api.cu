@@ -223,7 +223,8 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->tw64, &c->tw32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
-                      &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round};
+                      &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
+                      &c->lin, &c->ydev};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
@@ -632,25 +633,26 @@ extern "C" wc4d_status wc4d_get_propagator(wc4d_ctx *c, int32_t t, double *M)
 // ============================================================================
 // Outer-loop quantities: innovations and right-hand side
 // ============================================================================
-extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, const double *y, const double *Dm12b)
+// Model run from the stored linearisation point p = (x_0, eta), innovations
+// d_t = y_t - H_t x_t and rhs = D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b).
+static wc4d_status relinearise(wc4d_ctx *c)
 {
-    if (!c || !xb || !y) return WC4D_EINVAL;
     const int n = c->prob.n, N = c->prob.N;
     const int64_t nA = c->nA;
-    if (!c->have_cov[0] || !c->have_cov[1]) return set_err(c, WC4D_ESTATE, "covariances are not set");
     WC4D_TRY(ensure(c, c->blkA, sizeof(double) * nA));
     WC4D_TRY(ensure(c, c->blkB, sizeof(double) * nA));
     WC4D_TRY(ensure(c, c->d, sizeof(double) * std::max<int64_t>(c->nobs, 1)));
     WC4D_TRY(ensure(c, c->rhs, sizeof(double) * nA));
-    WC4D_TRY(ensure(c, c->small2, sizeof(double) * std::max<int64_t>(c->nobs, 1)));
     double *xs = P<double>(c->blkA);
+    const double *lin = P<double>(c->lin);
     if (c->prob.model == WC4D_MODEL_L96) {
         const int64_t nsteps = (int64_t)N * c->prob.steps;
         WC4D_TRY(ensure(c, c->traj64, sizeof(double) * (size_t)(nsteps + 1) * n));
         WC4D_TRY(ensure(c, c->stage64, sizeof(double) * (size_t)4 * nsteps * n));
         WC4D_TRY(ensure(c, c->stage32, sizeof(float) * (size_t)4 * nsteps * n));
-        WC4D_CUDA(c, cudaMemcpyAsync(c->traj64.p, xb, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
-        launch_l96_run(c->stream, n, (int)nsteps, c->prob.F, c->prob.dt, P<double>(c->traj64), P<double>(c->stage64));
+        WC4D_CUDA(c, cudaMemcpyAsync(c->traj64.p, lin, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        launch_l96_run(c->stream, n, (int)nsteps, c->prob.F, c->prob.dt, P<double>(c->traj64), P<double>(c->stage64),
+                       lin, c->prob.steps);
         launch_convert_f64_f32(c->stream, 4 * nsteps * n, P<double>(c->stage64), P<float>(c->stage32));
         WC4D_TRY(check_launch(c, "l96 run"));
         for (int t = 0; t <= N; ++t)
@@ -659,18 +661,15 @@ extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, co
         c->have_traj = true;
     } else {
         if (!c->have_M) return set_err(c, WC4D_ESTATE, "propagator not set");
-        WC4D_CUDA(c, cudaMemsetAsync(xs, 0, sizeof(double) * nA, c->stream));
-        WC4D_CUDA(c, cudaMemcpyAsync(xs, xb, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
-        WC4D_TRY(forward_sweep<double>(c, 1, xs, nA, false));   // x_{t+1} = M_t x_t
+        // x_{t+1} = M_t x_t + eta_{t+1}: the sweep adds M_t x_t to block t+1
+        WC4D_CUDA(c, cudaMemcpyAsync(xs, lin, sizeof(double) * nA, cudaMemcpyDeviceToDevice, c->stream));
+        WC4D_TRY(forward_sweep<double>(c, 1, xs, nA, false));
     }
     // innovations
-    double *dy = P<double>(c->small2);
-    if (c->nobs > 0) {
-        WC4D_CUDA(c, cudaMemcpyAsync(dy, y, sizeof(double) * c->nobs, cudaMemcpyHostToDevice, c->stream));
+    if (c->nobs > 0)
         WC4D_LAUNCH(k_innovation<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
-                                                                     c->prob.obs_tstride, c->prob.obs_stride, n, dy,
-                                                                     xs, P<double>(c->d)));
-    }
+                                                                     c->prob.obs_tstride, c->prob.obs_stride, n,
+                                                                     P<double>(c->ydev), xs, P<double>(c->d)));
     // rhs = D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b)
     double *v = P<double>(c->blkB);
     WC4D_CUDA(c, cudaMemsetAsync(v, 0, sizeof(double) * nA, c->stream));
@@ -680,15 +679,48 @@ extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, co
                                                                       P<double>(c->d), 1.0 / c->prob.sigma_o2, v));
     WC4D_TRY(check_launch(c, "innovation"));
     WC4D_TRY(plain_adjoint_sweep<double>(c, 1, v, nA));    // S = L^{-T} H^T R^{-1} d
-    double *addb = nullptr;
+    WC4D_TRY(apply_circ<double>(c, 1, v, nA, P<double>(c->rhs), nA, c->have_Dm12b ? P<double>(c->Dm12b) : nullptr,
+                                nA));
+    c->have_rhs = true;
+    return sync(c, "relinearise");
+}
+
+extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, const double *y, const double *Dm12b)
+{
+    if (!c || !xb || !y) return WC4D_EINVAL;
+    if (!c->have_cov[0] || !c->have_cov[1]) return set_err(c, WC4D_ESTATE, "covariances are not set");
+    const int n = c->prob.n;
+    const int64_t nA = c->nA;
+    WC4D_TRY(ensure(c, c->lin, sizeof(double) * nA));
+    WC4D_TRY(ensure(c, c->ydev, sizeof(double) * std::max<int64_t>(c->nobs, 1)));
+    WC4D_CUDA(c, cudaMemsetAsync(c->lin.p, 0, sizeof(double) * nA, c->stream));   // eta = 0
+    WC4D_CUDA(c, cudaMemcpyAsync(c->lin.p, xb, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    if (c->nobs > 0)
+        WC4D_CUDA(c, cudaMemcpyAsync(c->ydev.p, y, sizeof(double) * c->nobs, cudaMemcpyHostToDevice, c->stream));
+    c->have_Dm12b = Dm12b != nullptr;
     if (Dm12b) {
         WC4D_TRY(ensure(c, c->Dm12b, sizeof(double) * nA));
         WC4D_CUDA(c, cudaMemcpyAsync(c->Dm12b.p, Dm12b, sizeof(double) * nA, cudaMemcpyHostToDevice, c->stream));
-        addb = P<double>(c->Dm12b);
     }
-    WC4D_TRY(apply_circ<double>(c, 1, v, nA, P<double>(c->rhs), nA, addb, nA));
-    c->have_rhs = true;
-    return sync(c, "set_background_obs");
+    c->have_lin = true;
+    return relinearise(c);
+}
+
+extern "C" wc4d_status wc4d_outer_update(wc4d_ctx *c, const double *x)
+{
+    if (!c || !x) return WC4D_EINVAL;
+    if (!c->have_lin) return set_err(c, WC4D_ESTATE, "no linearisation point (call wc4d_set_background_obs)");
+    const int64_t nA = c->nA;
+    WC4D_TRY(ensure(c, c->blkC, sizeof(double) * nA));
+    WC4D_TRY(ensure(c, c->Dm12b, sizeof(double) * nA));
+    if (!c->have_Dm12b) WC4D_CUDA(c, cudaMemsetAsync(c->Dm12b.p, 0, sizeof(double) * nA, c->stream));
+    double *dp = P<double>(c->blkC);
+    WC4D_TRY(apply_circ<double>(c, 1, x, nA, dp, nA, nullptr, 0));                       // dp = D^{1/2} x
+    launch_axpby<double>(c->stream, nA, 1.0, dp, 1.0, P<double>(c->lin));                  // p += dp (eq. 3)
+    launch_axpby<double>(c->stream, nA, -1.0, x, 1.0, P<double>(c->Dm12b));               // D^{-1/2} b -= x
+    WC4D_TRY(check_launch(c, "outer update"));
+    c->have_Dm12b = true;
+    return relinearise(c);
 }
 
 extern "C" wc4d_status wc4d_get_rhs(wc4d_ctx *c, double *rhs)

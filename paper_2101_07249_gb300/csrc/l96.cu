@@ -193,13 +193,16 @@ template void launch_l96_adj_sweep<float>(cudaStream_t, int, int, int, double, c
                                           int, double, int, int, int);
 
 // Nonlinear RK4 run in FP64 on one CTA: traj[g+1] = RK4(traj[g]) for
-// g < nsteps, storing the stage states of every step.
+// g < nsteps, storing the stage states of every step; with eta (forcing,
+// (N+1) x n, block t added at the end of subwindow t-1, eq. 1) the state
+// after every `steps` steps receives eta_t.
 __device__ __forceinline__ double l96f(const double *y, int j, int n, double F)
 {
     return (y[wrap(j + 1, n)] - y[wrap(j - 2, n)]) * y[wrap(j - 1, n)] - y[j] + F;
 }
 
-__global__ void __launch_bounds__(1024) k_l96_run(int n, int nsteps, double F, double h, double *traj, double *stages)
+__global__ void __launch_bounds__(1024) k_l96_run(int n, int nsteps, double F, double h, double *traj, double *stages,
+                                                 const double *eta, int steps)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     double *x = reinterpret_cast<double *>(sm);
@@ -238,10 +241,13 @@ __global__ void __launch_bounds__(1024) k_l96_run(int n, int nsteps, double F, d
                 }
             } else {
 #pragma unroll
+                const bool forced = eta && (g + 1) % steps == 0;
+                const double *eg = forced ? eta + (int64_t)((g + 1) / steps) * n : nullptr;
                 for (int r = 0; r < R; ++r) {
                     int j = tid + r * nt;
                     if (j < n) {
                         double v = x[j] + h / 6.0 * acc[r];
+                        if (forced) v += eg[j];
                         x[j] = v;
                         traj[(int64_t)(g + 1) * n + j] = v;
                     }
@@ -252,7 +258,8 @@ __global__ void __launch_bounds__(1024) k_l96_run(int n, int nsteps, double F, d
     }
 }
 
-void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages)
+void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages,
+                    const double *eta, int steps)
 {
     static bool attr = false;
     if (!attr) {
@@ -260,5 +267,6 @@ void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, doub
                              (int)(2 * WC4D_FFT_MAX_N * sizeof(double)));
         attr = true;
     }
-    WC4D_LAUNCH(k_l96_run<<<1, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, nsteps, F, dt, traj, stages));
+    WC4D_LAUNCH(k_l96_run<<<1, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, nsteps, F, dt, traj, stages, eta,
+                                                                           steps));
 }

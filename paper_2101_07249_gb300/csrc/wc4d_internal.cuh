@@ -84,6 +84,11 @@ struct wc4d_ctx {
     // observations and right-hand side
     DevBuf d, rhs, Dm12b;
     bool have_rhs = false;
+    // outer loop (Section 2.1): linearisation point p = (x_0, eta_1..eta_N)
+    // (lin: (N+1) x n, block 0 = x_0), observations y, and whether D^{-1/2} b
+    // is non-zero
+    DevBuf lin, ydev;
+    bool have_lin = false, have_Dm12b = false;
 
     // workspaces
     DevBuf work64, work32;          // sweep workspace nA x K
@@ -287,4 +292,5 @@ void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
 template <typename T>
 void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
                           int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride);
-void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages);
+void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages,
+                    const double *eta, int steps);

@@ -436,3 +436,55 @@ def test_tensor_core_sweeps_match_oracle(K):
     bias = np.mean(np.sum((host(Y) - Ho) * Ho, axis=1) / np.sum(Ho * Ho, axis=1))
     assert abs(bias) < 3e-4, bias
     S.close()
+
+
+# ------------------------------------------------------------------ outer loop (Section 2.1)
+def _forced_l96_traj(x0, eta, cfg):
+    """All RK4 states of the forced Lorenz-96 run (eq. 1): eta_t is added at
+    the end of subwindow t-1 (oracle primitives only)."""
+    n, traj = cfg.n, [np.array(x0, dtype=np.float64)]
+    x = traj[0].copy()
+    for t in range(cfg.N):
+        for k in range(cfg.steps):
+            x = oracle.l96_rk4(x, cfg.F, cfg.dt)
+            if k == cfg.steps - 1:
+                x = x + eta[(t + 1) * n:(t + 2) * n]
+            traj.append(x.copy())
+    return np.array(traj)
+
+
+@pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
+def test_outer_update_matches_oracle(name):
+    """Two outer-loop updates (eq. 3): p += D^{1/2} x, D^{-1/2} b -= x, model
+    re-run with forcing, innovations and rhs; compared with the oracle's
+    forward run with forcing, innovations and rhs, and (Lorenz-96) the
+    Hessian product along the new trajectory."""
+    cfg = CASES[name]
+    tw = inputs.twin(cfg)
+    S = w.Solver(cfg, tw)
+    p = oracle_problem(cfg, mode="stepping", xb=tw.xb)
+    n, nA = cfg.n, cfg.nA
+    x0, eta, Dm12b = tw.xb.copy(), np.zeros(nA), np.zeros(nA)
+    for j, scale in enumerate((0.05, 0.02)):
+        x = scale * inputs.block(300 + j, nA, 1)[0]
+        w.wc4d_outer_update(S.ctx, dev(x))
+        dp = oracle.Dsqrt(p, x[None, :])[0]
+        x0 = x0 + dp[:n]
+        eta[n:] += dp[n:]
+        Dm12b -= x
+        if cfg.model == inputs.MODEL_L96:
+            bs, qs = p.Bsqrt, p.Qsqrt
+            p = oracle.Problem(model=oracle.MODEL_L96, F=cfg.F, traj=_forced_l96_traj(x0, eta, cfg), n=n, N=cfg.N,
+                               Bsqrt=bs, Qsqrt=qs, sigma_o2=cfg.sigma_o2, obs_stride=cfg.obs_stride,
+                               obs_t0=cfg.obs_t0, steps=cfg.steps, dt=cfg.dt)
+        d = oracle.innovation(p, x0, tw.y, eta)
+        r = oracle.rhs(p, d, Dm12b)
+        got = torch.zeros(nA, dtype=torch.float64, device="cuda")
+        w.wc4d_get_rhs(S.ctx, got)
+        assert relerr(host(got), r) < 1e-10, (j, relerr(host(got), r))
+    if cfg.model == inputs.MODEL_L96:
+        X = inputs.block(310, nA, 3)
+        Y = torch.zeros(3, nA, dtype=torch.float64, device="cuda")
+        w.wc4d_hvp(S.ctx, dev(X), Y, 3, nA, w.FP64)
+        assert colrel(host(Y), oracle.hvp(p, X)) < 1e-11
+    S.close()
