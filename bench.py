@@ -253,6 +253,42 @@ def lorenz96_window(w, inputs, rank, stream, outer_loops=3, maxit=100):
                         "peak_source": "measured FP32 FMA rate (register-only FMA loop)"}}
 
 
+# ---------------------------------------------------------------- batched windows
+def batched_windows(w, inputs, count, workers=16):
+    """Uneven advection-diffusion windows (n in {256..4096}, N in [10, 80],
+    K in [32, 256], one propagator per window): all inner loops of the batch
+    (mixed path, REVD q = 1, tol 1e-6) driven concurrently, each window on
+    its own stream, against looping the plain FP64 single-window solver over
+    the same windows.  Wall-clock times around the host calls."""
+    import torch
+    cfgs = inputs.batch_configs(seed=0, count=count)
+    streams = [torch.cuda.Stream() for _ in cfgs]
+    solvers = [w.Solver(c, inputs.twin(c), M_shared=True, stream=st.cuda_stream) for c, st in zip(cfgs, streams)]
+    xs = [torch.zeros(c.nA, dtype=torch.float64, device="cuda") for c in cfgs]
+    ctxs = [S.ctx for S in solvers]
+    ks, ls = [c.k for c in cfgs], [c.l for c in cfgs]
+    torch.cuda.synchronize()
+    w.wc4d_batch_inner_loop(ctxs, w.REVD, ks, ls, 1, list(range(count)), 1e-6, 5000, w.MIXED, xs, workers)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_b, rr_b, st_b = w.wc4d_batch_inner_loop(ctxs, w.REVD, ks, ls, 1, list(range(count)), 1e-6, 5000, w.MIXED, xs,
+                                                workers)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    it_f = []
+    for S, c, x in zip(solvers, cfgs, xs):
+        it, _ = w.wc4d_inner_loop(S.ctx, w.REVD, c.k, c.l, 1, 0, 1e-6, 5000, w.FP64, x)
+        it_f.append(it)
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    for S in solvers:
+        S.close()
+    return {"windows": count, "workers": workers, "total_nA": int(sum(c.nA for c in cfgs)),
+            "batched_mixed_s": t_batch, "looped_fp64_s": t_fp64, "speedup": t_fp64 / t_batch,
+            "max_relres": max(rr_b), "pcg_iters_batched": it_b, "pcg_iters_fp64": it_f}
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -264,7 +300,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the method comparison and the Lorenz-96 window (reported beside the headline)")
+                    help="skip the method comparison, the Lorenz-96 window and the batched windows")
+    ap.add_argument("--batch-count", type=int, default=16,
+                    help="uneven windows in the batched comparison (64 in the full configuration)")
     ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny"],
                     help="large: n=4096 N=40 (the benchmark); medium: N=8 (profiling captures); tiny: n=100 N=5")
     ap.add_argument("--profile-run", action="store_true",
@@ -431,7 +469,7 @@ def main():
                 "hvp_columns_per_s": K / t_hvp64}
 
     # ---- the three sketching methods of Section 4 on the same window
-    methods, l96 = None, None
+    methods, l96, batched = None, None, None
     if not args.no_extra and args.workload == "large":
         methods = {}
         for mname in ("revd", "nystrom", "ritzit"):
@@ -444,6 +482,7 @@ def main():
             methods[mname] = {"inner_loop_ms": e0.elapsed_time(e1), "pcg_iters": it_m, "relres": rr_m,
                               "block_products": 3 if mname == "revd" else (2 if mname == "nystrom" else 1)}
         l96 = lorenz96_window(w, inputs, rank, stream)
+        batched = batched_windows(w, inputs, args.batch_count) if args.batch_count > 0 else None
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -480,6 +519,7 @@ def main():
             "clocks": clk,
             "methods": methods,
             "lorenz96": l96,
+            "batched": batched,
         }
         print(json.dumps(line))
     S.close()

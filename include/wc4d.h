@@ -195,6 +195,20 @@ wc4d_status wc4d_inner_loop(wc4d_ctx *ctx, int32_t method, int32_t k, int32_t l,
                             uint64_t seed, double tol, int32_t maxit, int32_t precision,
                             double *x_device, int32_t *iters, double *relres);
 
+/* Batched inner loops of `count` independent problems (windows of different
+ * sizes; the paper solves one window at a time, this is a throughput
+ * wrapper): instance i runs wc4d_inner_loop(ctxs[i], method, k[i], l[i],
+ * q_power, seeds[i], tol, maxit, precision, x[i], iters + i, relres + i) on
+ * its context's stream, driven by one of `workers` host threads (<= 0: 16),
+ * so that the instances' kernels overlap on the GPU.  Every context must have
+ * its own stream (WC4D_EINVAL otherwise); while in the batch a context uses
+ * the per-launch forms of its grid-synchronised kernels.  status[i] receives
+ * each instance's status; the call returns the first non-OK one. */
+wc4d_status wc4d_batch_inner_loop(wc4d_ctx *const *ctxs, int32_t count, int32_t method, const int32_t *k,
+                                  const int32_t *l, int32_t q_power, const uint64_t *seeds, double tol,
+                                  int32_t maxit, int32_t precision, double *const *x_device, int32_t *iters,
+                                  double *relres, int32_t *status, int32_t workers);
+
 /* ---- small building blocks, exported for verification ------------------ */
 
 /* CholeskyQR2 in place (the orthonormalisation of Alg. 3-5): Y (device,

@@ -61,6 +61,8 @@ _SIGS = {
     "wc4d_set_covariance_row": (C.c_int, [_V, C.c_int32, _D]),
     "wc4d_set_background_obs": (C.c_int, [_V, _D, _D, _D]),
     "wc4d_outer_update": (C.c_int, [_V, _V]),
+    "wc4d_batch_inner_loop": (C.c_int, [_V, C.c_int32, C.c_int32, _V, _V, C.c_int32, _V, C.c_double, C.c_int32,
+                                        C.c_int32, _V, _V, _V, _V, C.c_int32]),
     "wc4d_nobs": (C.c_int64, [_V]),
     "wc4d_get_rhs": (C.c_int, [_V, _V]),
     "wc4d_hvp": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
@@ -138,6 +140,12 @@ def _hp(a):
     return a.ctypes.data_as(_D)
 
 
+def _hv(a):
+    """Host pointer of a contiguous numpy array of any dtype."""
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
 def _stream(stream=None):
     if stream is not None:
         return C.c_void_p(int(stream))
@@ -202,6 +210,27 @@ def wc4d_set_background_obs(ctx, xb, y, Dm12b=None):
 
 def wc4d_outer_update(ctx, x):
     _check(ctx, load().wc4d_outer_update(ctx, _ptr(x)))
+
+
+def wc4d_batch_inner_loop(ctxs, method, ks, ls, q_power, seeds, tol, maxit, precision, xs, workers=0):
+    """Inner loops of independent contexts (each with its own stream) run
+    concurrently; returns (iters, relres, statuses) as lists."""
+    cnt = len(ctxs)
+    arr_ctx = (C.c_void_p * cnt)(*[C.c_void_p(c.value if isinstance(c, C.c_void_p) else c) for c in ctxs])
+    arr_x = (C.c_void_p * cnt)(*[_ptr(x).value for x in xs])
+    k = np.ascontiguousarray(ks, dtype=np.int32)
+    l = np.ascontiguousarray(ls, dtype=np.int32)
+    sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+    it = np.zeros(cnt, dtype=np.int32)
+    rr = np.zeros(cnt)
+    st = np.zeros(cnt, dtype=np.int32)
+    s = load().wc4d_batch_inner_loop(C.cast(arr_ctx, C.c_void_p), int(cnt), int(method), _hv(k), _hv(l),
+                                     int(q_power), _hv(sd), float(tol), int(maxit), int(precision),
+                                     C.cast(arr_x, C.c_void_p), _hv(it), _hv(rr), _hv(st), int(workers))
+    if s != OK and s != ENOCONV:
+        bad = [i for i in range(cnt) if st[i] != OK]
+        _check(ctxs[bad[0]] if bad else ctxs[0], s)
+    return it.tolist(), rr.tolist(), st.tolist()
 
 
 def wc4d_nobs(ctx):

@@ -224,7 +224,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
                       &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
-                      &c->lin, &c->ydev};
+                      &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
@@ -451,7 +451,7 @@ static wc4d_status apply_circ(wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y,
 template <typename T>
 static bool persistent_sweep(wc4d_ctx *c, T *W, int mode)
 {
-    if (c->prob.model != WC4D_MODEL_DENSE || getenv("WC4D_NO_PERSISTENT")) return false;
+    if (c->prob.model != WC4D_MODEL_DENSE || !c->allow_coop || getenv("WC4D_NO_PERSISTENT")) return false;
     const int N = c->prob.N;
     // layout: [0] error flag (kept until read), [1 .. N] step counters
     if (ensure(c, c->sweep_bar, (size_t)(N + 1) * sizeof(unsigned)) != WC4D_OK) return false;
@@ -811,7 +811,7 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
 {
     const int mp = m + (m & 1);
     const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
-    if (const int Pq = jacobi_coop_size(m)) {
+    if (const int Pq = c->allow_coop ? jacobi_coop_size(m) : 0) {
         const size_t nd = jacobi_coop_doubles(m);
         WC4D_TRY(ensure(c, c->small3, sizeof(double) * nd + sizeof(int) * 128));
         double *XV = P<double>(c->small3);
@@ -880,7 +880,7 @@ static wc4d_status jacobi_svd(wc4d_ctx *c, int m, const double *X0, double *w, d
 // Jacobi on S when S is not numerically positive definite.
 static wc4d_status spd_evd(wc4d_ctx *c, int m, const double *S, double *w, double *Vout)
 {
-    DevBuf rb;
+    DevBuf &rb = c->evd_r;
     WC4D_TRY(ensure(c, rb, sizeof(double) * 2 * (size_t)m * m));
     double *R = P<double>(rb), *RT = R + (size_t)m * m;
     int info = 0;
@@ -889,7 +889,7 @@ static wc4d_status spd_evd(wc4d_ctx *c, int m, const double *S, double *w, doubl
         launch_chol_upper(c->stream, m, S, R, P<int>(c->counter));
         launch_rrt(c->stream, m, R, RT);
         wc4d_status st = check_launch(c, "spd_evd chol");
-        if (st != WC4D_OK) { free_buf(rb); return st; }
+        if (st != WC4D_OK) return st;
         cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     }
     wc4d_status st = sync(c, "spd_evd chol");
@@ -905,7 +905,6 @@ static wc4d_status spd_evd(wc4d_ctx *c, int m, const double *S, double *w, doubl
     } else if (st == WC4D_OK) {
         st = jacobi_svd(c, m, S, w, Vout);
     }
-    free_buf(rb);
     return st;
 }
 
@@ -963,14 +962,14 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     WC4D_TRY(ensure(c, c->blkD, std::max(blk, sizeof(double) * (size_t)nA * m)));
     WC4D_TRY(ensure(c, c->theta64, sizeof(double) * 2 * m));
     const size_t mm = (size_t)m * m;
-    DevBuf kb, wb, Rb;
+    DevBuf &kb = c->sk_k, &wb = c->sk_w, &Rb = c->sk_r;
     WC4D_TRY(ensure(c, kb, sizeof(double) * mm * 2));
     WC4D_TRY(ensure(c, wb, sizeof(double) * 2 * m));
     WC4D_TRY(ensure(c, Rb, sizeof(double) * mm));
     double *Kmat = P<double>(kb), *Wv = Kmat + mm, *w = P<double>(wb), *R = P<double>(Rb);
     T *A_ = P<T>(c->blkA), *B_ = P<T>(c->blkB), *C_ = P<T>(c->blkC), *D_ = P<T>(c->blkD);
     wc4d_status st = WC4D_OK;
-    auto fail = [&](wc4d_status s) { free_buf(kb); free_buf(wb); free_buf(Rb); return s; };
+    auto fail = [&](wc4d_status s) { return s; };
 
     // step 1: Gaussian probes G (FP64), cast to the working precision
     double *G64 = P<double>(c->blkD);
@@ -1114,11 +1113,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     c->kU = k;
     c->theta_host.assign(k, 0.0);
     cudaMemcpyAsync(c->theta_host.data(), c->theta64.p, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream);
-    st = sync(c, "sketch");
-    free_buf(kb);
-    free_buf(wb);
-    free_buf(Rb);
-    return st;
+    return sync(c, "sketch");
 }
 
 // Row-major, zero-padded copies of the Ritz vectors for the LMP kernels.
@@ -1450,7 +1445,7 @@ extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxi
     WC4D_TRY(prep_precision(c, precision));
     const int64_t nA = c->nA;
     const int cap = std::max(1, std::max(maxit, force));
-    DevBuf qcf;
+    DevBuf &qcf = c->qcf;
     WC4D_TRY(ensure(c, qcf, sizeof(double) * cap));
     WC4D_CUDA(c, cudaMemsetAsync(qcf.p, 0, sizeof(double) * cap, c->stream));
     wc4d_status st = WC4D_OK;
@@ -1474,7 +1469,6 @@ extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxi
                         cudaMemcpyDeviceToHost, c->stream);
         st = sync(c, "qcf");
     }
-    free_buf(qcf);
     if (st != WC4D_OK) return st;
     if (iters) *iters = total_it;
     if (relres) *relres = rel;

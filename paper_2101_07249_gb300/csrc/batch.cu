@@ -1,0 +1,50 @@
+// Batched inner loops of independent problems (many windows of different
+// sizes solved together).  Each instance keeps its own context and CUDA
+// stream; a pool of host threads drives the instances' inner loops (sketch,
+// LMP, PCG: control flow that waits on the device between steps), so the
+// kernels of different instances overlap on the GPU and the small,
+// latency-bound windows fill the SMs together.  Grid-synchronised kernels
+// are replaced by their per-launch forms while a context runs in a batch:
+// a cooperative launch needs every CTA resident at once.
+#include <atomic>
+#include <thread>
+#include <vector>
+
+#include "wc4d_internal.cuh"
+
+extern "C" wc4d_status wc4d_inner_loop(wc4d_ctx *c, int32_t method, int32_t k, int32_t l, int32_t q, uint64_t seed,
+                                       double tol, int32_t maxit, int32_t precision, double *x, int32_t *iters,
+                                       double *relres);
+
+extern "C" wc4d_status wc4d_batch_inner_loop(wc4d_ctx *const *ctxs, int32_t count, int32_t method, const int32_t *k,
+                                             const int32_t *l, int32_t q_power, const uint64_t *seeds, double tol,
+                                             int32_t maxit, int32_t precision, double *const *x, int32_t *iters,
+                                             double *relres, int32_t *status, int32_t workers)
+{
+    if (!ctxs || count < 0 || !k || !l || !seeds || !x || !iters || !relres || !status) return WC4D_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i] || !x[i]) return WC4D_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return WC4D_EINVAL;   // one stream each
+    }
+    if (count == 0) return WC4D_OK;
+    const int nw = std::max(1, std::min<int>(workers > 0 ? workers : 16, count));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+            wc4d_ctx *c = ctxs[i];
+            cudaSetDevice(c->device);
+            const bool coop = c->allow_coop;
+            c->allow_coop = false;
+            status[i] = wc4d_inner_loop(c, method, k[i], l[i], q_power, seeds[i], tol, maxit, precision, x[i],
+                                        iters + i, relres + i);
+            c->allow_coop = coop;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nw; ++t) pool.emplace_back(worker);
+    for (auto &t : pool) t.join();
+    for (int i = 0; i < count; ++i)
+        if (status[i] != WC4D_OK) return (wc4d_status)status[i];
+    return WC4D_OK;
+}

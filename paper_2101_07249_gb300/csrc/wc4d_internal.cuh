@@ -88,6 +88,9 @@ struct wc4d_ctx {
     // (lin: (N+1) x n, block 0 = x_0), observations y, and whether D^{-1/2} b
     // is non-zero
     DevBuf lin, ydev;
+    // per-call scratch kept across calls (a cudaFree would synchronise the
+    // whole device): sketch small matrices, EVD factor, CG cost history
+    DevBuf sk_k, sk_w, sk_r, evd_r, qcf;
     bool have_lin = false, have_Dm12b = false;
 
     // workspaces
@@ -125,6 +128,9 @@ struct wc4d_ctx {
     int64_t hvp_count = 0;
 
     // profiling (CUDA events per launch group)
+    // cooperative (grid-synchronised) kernels need the whole GPU; off while
+    // the context runs concurrently with others (wc4d_batch_inner_loop)
+    bool allow_coop = true;
     bool prof_on = false;
     std::vector<ProfEntry> prof_log;
     std::vector<cudaEvent_t> ev_pool;

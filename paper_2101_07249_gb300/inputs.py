@@ -104,6 +104,23 @@ L96 = Config(name="l96_n8192_N40", model=MODEL_L96, n=8192, N=40, steps=8, dt=0.
 CONFIGS = {c.name: c for c in (TINY, MEDIUM, LARGE, L96)}
 
 
+def batch_configs(seed: int = 0, count: int = 64, sizes=(256, 512, 1024, 2048, 4096),
+                  N_range=(10, 80), K_range=(32, 256), l: int = 8):
+    """Uneven advection-diffusion windows (the physics of LARGE, correlation
+    lengths kept in domain units): n uniform over `sizes`, N uniform in
+    N_range, sketch width K = k + l uniform in K_range, instance i seeded
+    with i (its truth, background, observations and probes)."""
+    g = np.random.default_rng([int(seed), 4])
+    out = []
+    for i in range(count):
+        n = int(g.choice(sizes))
+        N = int(g.integers(N_range[0], N_range[1] + 1))
+        K = int(g.integers(K_range[0], K_range[1] + 1))
+        cfg = scaled(LARGE, n, N, K - l, l).replace(name=f"batch{i}_n{n}_N{N}_K{K}", seed=i)
+        out.append(cfg)
+    return out
+
+
 def scaled(cfg: Config, n: int, N: int, k: int, l: int, **kw) -> Config:
     """The same physics on a smaller grid/window, correlation lengths kept in
     domain units (advection-diffusion) or grid points (Lorenz-96)."""
