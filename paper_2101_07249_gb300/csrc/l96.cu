@@ -7,7 +7,11 @@
 // The RK4 stage states s1 = x, s2 = x + h/2 k1, s3 = x + h/2 k2, s4 = x + h k3
 // of every step are stored once by the nonlinear run and shared by all
 // probe columns (an L2-resident read-only table).
+#include <cooperative_groups.h>
+
 #include "wc4d_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 constexpr int L96_THREADS = 512;
 constexpr int L96_PPT = WC4D_FFT_MAX_N / L96_THREADS;   // points per thread (n <= 8192)
@@ -156,6 +160,135 @@ k_l96_adj(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, int6
     }
 }
 
+// ---------------------------------------------------------------------------
+// Few columns (the PCG matvec): one column per 8-CTA thread-block cluster.
+// CTA r of the cluster owns points r P .. r P + P - 1 (P = n / 8, one point
+// per thread); the stencils' neighbours beyond the slice are read from the
+// adjacent CTAs' shared memory (distributed shared memory), and a cluster
+// barrier separates the RK4 stages, as __syncthreads does in the one-CTA
+// kernels above.
+// ---------------------------------------------------------------------------
+constexpr int L96_CL = 8;
+
+// v at global point j of a vector distributed over the cluster (slices of P)
+template <typename T>
+__device__ __forceinline__ T cl_get(cg::cluster_group &cl, T *slice, int j, int P, int rank)
+{
+    const int owner = j / P, li = j - owner * P;
+    if (owner == rank) return slice[li];
+    return *cl.map_shared_rank(slice + li, owner);
+}
+
+template <typename T>
+__device__ __forceinline__ T jac_cl(cg::cluster_group &cl, const T *__restrict__ x, T *d, int j, int n, int P, int rank,
+                                    T dj)
+{
+    const int jm2 = wrap(j - 2, n), jm1 = wrap(j - 1, n), jp1 = wrap(j + 1, n);
+    return (cl_get(cl, d, jp1, P, rank) - cl_get(cl, d, jm2, P, rank)) * __ldg(x + jm1) +
+           (__ldg(x + jp1) - __ldg(x + jm2)) * cl_get(cl, d, jm1, P, rank) - dj;
+}
+
+template <typename T>
+__device__ __forceinline__ T jacT_cl(cg::cluster_group &cl, const T *__restrict__ x, T *a, int i, int n, int P,
+                                     int rank, T ai)
+{
+    const int im2 = wrap(i - 2, n), im1 = wrap(i - 1, n), ip1 = wrap(i + 1, n), ip2 = wrap(i + 2, n);
+    return __ldg(x + im2) * cl_get(cl, a, im1, P, rank) - __ldg(x + ip1) * cl_get(cl, a, ip2, P, rank) +
+           (__ldg(x + ip2) - __ldg(x + im1)) * cl_get(cl, a, ip1, P, rank) - ai;
+}
+
+template <typename T>
+__global__ void __cluster_dims__(L96_CL, 1, 1) __launch_bounds__(1024, 1)
+k_l96_tlm_cl(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, int64_t ld)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), P = n / L96_CL, tid = threadIdx.x;
+    T *dl = reinterpret_cast<T *>(sm), *ta = dl + P, *tb = ta + P;
+    T *w = W + (int64_t)(blockIdx.x / L96_CL) * ld;
+    const bool act = tid < P;
+    const int j = rank * P + tid;
+    if (act) dl[tid] = w[j];
+    cl.sync();
+    const T h2 = h * (T)0.5, h6 = h / (T)6;
+    for (int t = 0; t < N; ++t) {
+        for (int k = 0; k < steps; ++k) {
+            const int64_t g = (int64_t)t * steps + k;
+            const T *s1 = stages + (4 * g + 0) * n, *s2 = stages + (4 * g + 1) * n;
+            const T *s3 = stages + (4 * g + 2) * n, *s4 = stages + (4 * g + 3) * n;
+            T acc = 0;
+            if (act) { const T d = jac_cl(cl, s1, dl, j, n, P, rank, dl[tid]); acc = d; ta[tid] = dl[tid] + h2 * d; }
+            cl.sync();
+            if (act) { const T d = jac_cl(cl, s2, ta, j, n, P, rank, ta[tid]); acc += (T)2 * d; tb[tid] = dl[tid] + h2 * d; }
+            cl.sync();
+            if (act) { const T d = jac_cl(cl, s3, tb, j, n, P, rank, tb[tid]); acc += (T)2 * d; ta[tid] = dl[tid] + h * d; }
+            cl.sync();
+            if (act) { const T d = jac_cl(cl, s4, ta, j, n, P, rank, ta[tid]); acc += d; dl[tid] = dl[tid] + h6 * acc; }
+            cl.sync();
+        }
+        if (act) {
+            T *wn = w + (int64_t)(t + 1) * n;
+            const T v = dl[tid] + wn[j];
+            dl[tid] = v;
+            wn[j] = v;
+        }
+        cl.sync();
+    }
+}
+
+template <typename T>
+__global__ void __cluster_dims__(L96_CL, 1, 1) __launch_bounds__(1024, 1)
+k_l96_adj_cl(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, int64_t ld, int obs_mode, T obs_scale,
+             int obs_stride, int t0, int ts)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), P = n / L96_CL, tid = threadIdx.x;
+    T *lam = reinterpret_cast<T *>(sm), *aa = lam + P, *ab = aa + P;
+    T *w = W + (int64_t)(blockIdx.x / L96_CL) * ld;
+    const bool act = tid < P;
+    const int j = rank * P + tid;
+    auto obs_at = [&](int t) { return t >= t0 && (t - t0) % ts == 0; };
+    if (act) {
+        T *wN = w + (int64_t)N * n;
+        T v = wN[j];
+        if (obs_mode == 1) v = (obs_at(N) && j % obs_stride == 0) ? obs_scale * v : (T)0;
+        lam[tid] = v;
+        wN[j] = v;
+    }
+    cl.sync();
+    const T h2 = h * (T)0.5, h3 = h / (T)3, h6 = h / (T)6;
+    for (int t = N - 1; t >= 0; --t) {
+        for (int k = steps - 1; k >= 0; --k) {
+            const int64_t g = (int64_t)t * steps + k;
+            const T *s1 = stages + (4 * g + 0) * n, *s2 = stages + (4 * g + 1) * n;
+            const T *s3 = stages + (4 * g + 2) * n, *s4 = stages + (4 * g + 3) * n;
+            T acc = 0;
+            if (act) aa[tid] = h6 * lam[tid];                                   // a4
+            cl.sync();
+            if (act) { const T g4 = jacT_cl(cl, s4, aa, j, n, P, rank, aa[tid]); acc = lam[tid] + g4; ab[tid] = h3 * lam[tid] + h * g4; }
+            cl.sync();
+            if (act) { const T g3 = jacT_cl(cl, s3, ab, j, n, P, rank, ab[tid]); acc += g3; aa[tid] = h3 * lam[tid] + h2 * g3; }
+            cl.sync();
+            if (act) { const T g2 = jacT_cl(cl, s2, aa, j, n, P, rank, aa[tid]); acc += g2; ab[tid] = h6 * lam[tid] + h2 * g2; }
+            cl.sync();
+            if (act) { const T g1 = jacT_cl(cl, s1, ab, j, n, P, rank, ab[tid]); lam[tid] = acc + g1; }
+            cl.sync();
+        }
+        if (act) {
+            T *wt = w + (int64_t)t * n;
+            T v = wt[j];
+            if (obs_mode == 1) v = (obs_at(t) && j % obs_stride == 0) ? obs_scale * v : (T)0;
+            v += lam[tid];
+            lam[tid] = v;
+            wt[j] = v;
+        }
+        cl.sync();
+    }
+}
+
+static bool use_cluster(int n, int K) { return K <= 32 && n % L96_CL == 0 && n / L96_CL >= 2 && n / L96_CL <= 1024; }
+
 template <typename T>
 void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
                           int64_t ld)
@@ -165,6 +298,11 @@ void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
         cudaFuncSetAttribute(k_l96_tlm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
         attr = true;
+    }
+    if (use_cluster(n, K)) {
+        WC4D_LAUNCH(k_l96_tlm_cl<T><<<K * L96_CL, 1024, 3 * (size_t)(n / L96_CL) * sizeof(T), s>>>(n, N, steps, (T)dt,
+                                                                                                 stages, W, ld));
+        return;
     }
     WC4D_LAUNCH(k_l96_tlm<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld));
 }
@@ -178,6 +316,12 @@ void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
         cudaFuncSetAttribute(k_l96_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
         attr = true;
+    }
+    if (use_cluster(n, K)) {
+        WC4D_LAUNCH(k_l96_adj_cl<T><<<K * L96_CL, 1024, 3 * (size_t)(n / L96_CL) * sizeof(T), s>>>(
+            n, N, steps, (T)dt, stages, W, ld, obs_mode, (T)obs_scale, obs_stride, obs_t0,
+            obs_tstride > 0 ? obs_tstride : 1));
+        return;
     }
     WC4D_LAUNCH(k_l96_adj<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld, obs_mode,
                                                                      (T)obs_scale, obs_stride, obs_t0,
