@@ -253,6 +253,66 @@ def lorenz96_window(w, inputs, rank, stream, outer_loops=3, maxit=100):
                         "peak_source": "measured FP32 FMA rate (register-only FMA loop)"}}
 
 
+# ---------------------------------------------------------------- learned sketch
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_2101_07249_gb300", "learned", "l96_n8192_N10_m64.npz")
+
+
+def learned_windows(w, inputs, stream, seeds=(30000, 30001), m=64, l=32, maxit=5000):
+    """Lorenz-96 windows (n = 8192, N = 10, held-out seeds): the Gaussian
+    sketch (REVD q = 1, m + l probes) against the learned proposal (m network
+    columns + l Gaussian columns through the same REVD), each followed by
+    mixed PCG to 1e-6.  Gate: the learned block is used when the mean of its
+    top-m Ritz values is at least 0.9 x the Gaussian sketch's, else the
+    Gaussian sketch is."""
+    import torch
+    if not os.path.exists(LEARNED_WEIGHTS):
+        return None
+    z = np.load(LEARNED_WEIGHTS)
+    wdev = torch.as_tensor(np.concatenate([z[f"W{i}"].ravel() for i in range(4)]).view(np.int16), device="cuda")
+    bdev = torch.as_tensor(np.concatenate([z[f"b{i}"] for i in range(4)]).astype(np.float32), device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    rows = []
+    for sd in seeds:
+        cfg = inputs.L96.replace(N=10, name=f"l96_n8192_N10_s{sd}", seed=sd, k=m, l=l)
+        tw = inputs.twin(cfg, spinup=5.0)
+        S = w.Solver(cfg, tw)
+        x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+        th_g, t_sk_g = timed(lambda: w.wc4d_sketch(S.ctx, w.REVD, m, l, 1, sd, None, w.MIXED))
+        (it_g, rr_g, _, _), t_pcg_g = timed(lambda: w.wc4d_pcg(S.ctx, x, 1e-6, maxit, 1, 0, w.MIXED,
+                                                                 raise_on_noconv=False))
+        G = torch.zeros(m + l, cfg.nA, dtype=torch.float64, device="cuda")
+
+        def learned_sketch():
+            w.wc4d_learned_probes(S.ctx, wdev, bdev, m, G, cfg.nA)
+            w.wc4d_gaussian(S.ctx, sd, cfg.nA, l, cfg.nA, G[m:])
+            return w.wc4d_sketch(S.ctx, w.REVD, m, l, 1, sd, G, w.MIXED)
+
+        th_l, t_sk_l = timed(learned_sketch)
+        accept = float(np.mean(th_l)) >= 0.9 * float(np.mean(th_g))
+        row = {"seed": sd, "gaussian": {"sketch_ms": t_sk_g, "pcg_ms": t_pcg_g, "pcg_iters": it_g, "relres": rr_g,
+                                        "theta_mean": float(np.mean(th_g))},
+               "learned": {"sketch_ms": t_sk_l, "theta_mean": float(np.mean(th_l)), "accepted": accept}}
+        if accept:
+            x.zero_()
+            (it_l, rr_l, _, _), t_pcg_l = timed(lambda: w.wc4d_pcg(S.ctx, x, 1e-6, maxit, 1, 0, w.MIXED,
+                                                                     raise_on_noconv=False))
+            row["learned"].update({"pcg_ms": t_pcg_l, "pcg_iters": it_l, "relres": rr_l})
+        rows.append(row)
+        S.close()
+    return {"workload": "l96_n8192_N10 (held-out seeds)", "m": m, "l": l,
+            "held_out_captured": float(z["held_out_captured"]), "gaussian_captured": float(z["gaussian_captured"]),
+            "windows": rows}
+
+
 # ---------------------------------------------------------------- batched windows
 def batched_windows(w, inputs, count, workers=16):
     """Uneven advection-diffusion windows (n in {256..4096}, N in [10, 80],
@@ -469,7 +529,7 @@ def main():
                 "hvp_columns_per_s": K / t_hvp64}
 
     # ---- the three sketching methods of Section 4 on the same window
-    methods, l96, batched = None, None, None
+    methods, l96, batched, learned = None, None, None, None
     if not args.no_extra and args.workload == "large":
         methods = {}
         for mname in ("revd", "nystrom", "ritzit"):
@@ -483,6 +543,7 @@ def main():
                               "block_products": 3 if mname == "revd" else (2 if mname == "nystrom" else 1)}
         l96 = lorenz96_window(w, inputs, rank, stream)
         batched = batched_windows(w, inputs, args.batch_count) if args.batch_count > 0 else None
+        learned = learned_windows(w, inputs, stream)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -520,6 +581,7 @@ def main():
             "methods": methods,
             "lorenz96": l96,
             "batched": batched,
+            "learned_sketch": learned,
         }
         print(json.dumps(line))
     S.close()

@@ -446,3 +446,42 @@ def pcg(p, b, U=None, theta=None, tol=1e-6, maxit=5000, force_iters=0):
     it = iters.value
     return dict(x=x, iters=it, relres=rr.value, status=int(rc), qcf_drop=drop[:it].copy(),
                 relres_hist=hist[:it].copy())
+
+
+# ---------------------------------------------------------------------------
+# Learned sketch proposal (not in the paper): the same fixed 4-layer periodic
+# 1D convolutional encoder the library runs, written out plainly in numpy
+# FP64 from its definition (input: states at the subwindow boundaries / F and
+# the observation masks; layers 2(N+1)->64 (width 5, ReLU), 64->64 (width 5,
+# ReLU) twice, 64->m(N+1) (width 1); output channel j(N+1)+t = time block t of
+# column j).  Pinned by the periodic-convolution identities in the tests.
+# ---------------------------------------------------------------------------
+def bf16_to_f64(u16):
+    """BF16 bit patterns (uint16) to float64: the top 16 bits of an FP32."""
+    u = np.asarray(u16, dtype=np.uint16).astype(np.uint32) << 16
+    return u.view(np.float32).astype(np.float64)
+
+
+def periodic_conv1d(x, W, b):
+    """y[o, s] = b[o] + sum_{i,k} W[o, i, k] x[i, (s + k - width//2) mod n]."""
+    cout, cin, width = W.shape
+    n = x.shape[1]
+    h = width // 2
+    y = np.repeat(np.asarray(b, dtype=np.float64)[:, None], n, axis=1)
+    for k in range(width):
+        xs = np.roll(x, -(k - h), axis=1)           # xs[i, s] = x[i, (s + k - h) mod n]
+        y += W[:, :, k] @ xs
+    return y
+
+
+def learned_probes(traj_boundaries, F, mask, weights, biases, m):
+    """traj_boundaries: (N+1, n) states at the subwindow boundaries; mask:
+    (N+1, n) observation mask; weights: the four (out, in, width) arrays;
+    biases: the four bias vectors.  Returns S (m, (N+1) n)."""
+    Np1, n = traj_boundaries.shape
+    x = np.concatenate([np.asarray(traj_boundaries, dtype=np.float64) / F, np.asarray(mask, dtype=np.float64)])
+    for li in range(4):
+        x = periodic_conv1d(x, weights[li], biases[li])
+        if li < 3:
+            x = np.maximum(x, 0.0)
+    return x.reshape(m, Np1, n).reshape(m, Np1 * n)

@@ -61,6 +61,7 @@ _SIGS = {
     "wc4d_set_covariance_row": (C.c_int, [_V, C.c_int32, _D]),
     "wc4d_set_background_obs": (C.c_int, [_V, _D, _D, _D]),
     "wc4d_outer_update": (C.c_int, [_V, _V]),
+    "wc4d_learned_probes": (C.c_int, [_V, _V, _V, C.c_int32, _V, C.c_int64]),
     "wc4d_batch_inner_loop": (C.c_int, [_V, C.c_int32, C.c_int32, _V, _V, C.c_int32, _V, C.c_double, C.c_int32,
                                         C.c_int32, _V, _V, _V, _V, C.c_int32]),
     "wc4d_nobs": (C.c_int64, [_V]),
@@ -231,6 +232,12 @@ def wc4d_batch_inner_loop(ctxs, method, ks, ls, q_power, seeds, tol, maxit, prec
         bad = [i for i in range(cnt) if st[i] != OK]
         _check(ctxs[bad[0]] if bad else ctxs[0], s)
     return it.tolist(), rr.tolist(), st.tolist()
+
+
+def wc4d_learned_probes(ctx, w_bf16, bias, m, S, ld):
+    """S (m x ld device tensor, FP64) = learned start columns; w_bf16: device
+    int16/bfloat16 tensor of the packed weights, bias: device float32."""
+    _check(ctx, load().wc4d_learned_probes(ctx, _ptr(w_bf16), _ptr(bias), int(m), _ptr(S), int(ld)))
 
 
 def wc4d_nobs(ctx):

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwc4d.so")
-SOURCES = ["api.cu", "setup.cu", "sweep.cu", "linalg.cu", "l96.cu", "tc_gemm.cu", "lmp_static.cu", "jacobi_coop.cu", "batch.cu"]
+SOURCES = ["api.cu", "setup.cu", "sweep.cu", "linalg.cu", "l96.cu", "tc_gemm.cu", "lmp_static.cu", "jacobi_coop.cu", "batch.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -224,7 +224,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
                       &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
-                      &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf};
+                      &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);

@@ -91,6 +91,7 @@ struct wc4d_ctx {
     // per-call scratch kept across calls (a cudaFree would synchronise the
     // whole device): sketch small matrices, EVD factor, CG cost history
     DevBuf sk_k, sk_w, sk_r, evd_r, qcf;
+    DevBuf learn_buf;               // learned-probe network activations
     bool have_lin = false, have_Dm12b = false;
 
     // workspaces
