@@ -34,10 +34,11 @@ METRIC = "inner-loop time to rel-res 1e-6 and Hessian-vec products/s, mixed vs F
 
 # DRAM bytes per launch of the dominant kernel from `ncu` (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel class and workload; see profiles/.
-# k_gemv_sweep<float>: 540.4 MB per launch on the N = 8 window (8 subwindow
-# GEMVs), scaled by 40/8 to the N = 40 window (traffic grows with the number
-# of subwindows).  Reset to None whenever the kernel changes until re-measured.
-NCU_TRAFFIC = {("gemv_sweep_f32", "advdiff_n4096_N40"): 540.41e6 * 40 / 8}
+# k_gemv_sweep_staged<2>: measured on the N = 8 window (8 subwindow GEMVs) and
+# scaled by 40/8 to the N = 40 window (traffic grows with the number of
+# subwindows).  None whenever the kernel has changed since the counters were
+# taken.
+NCU_TRAFFIC = {("gemv_sweep_f32", "advdiff_n4096_N40"): None}
 
 # Column Hessian products one mixed inner loop issues on the large window:
 # REVD with one power iteration (3 block products of k + l = 256 columns),
@@ -488,7 +489,8 @@ def main():
         ach = bytes_per / (classes[dom]["avg_us"] * 1e-6) / 1e9
         tr = NCU_TRAFFIC.get(("gemv_sweep_f32", cfg.name))
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": tr, "kernel": "k_gemv_sweep<float> (persistent one-column sweep, N GEMVs per launch)",
+                "traffic": tr, "kernel": "k_gemv_sweep_staged<2> (persistent one-column FP32 sweep, bulk-copy ring, "
+                                          "N GEMVs per launch)",
                 "algorithmic_bytes_per_launch": bytes_per, "peak_source": peak_src}
     elif dom in ("gemm", "tc_gemm"):
         flops = 2.0 * n * n * K
@@ -563,7 +565,7 @@ def main():
             "config": {"workload": cfg.name, "n": cfg.n, "N": cfg.N, "nA": nA, "K": K, "k": cfg.k,
                        "l": cfg.l, "method": args.method, "q_power": cfg.q_power, "tol": cfg.tol,
                        "precision": "mixed", "propagators": "one dense FP32/FP64 matrix per subwindow",
-                       "l2": "inputs larger than L2 (propagators 5.4 GB FP32)", "parallelism": "replicas"},
+                       "l2": "inputs larger than L2 (propagators 2.7 GB FP32, 5.4 GB FP64)", "parallelism": "replicas"},
             "inner_loop_ms": 1e3 * t_max / args.steps,
             "pcg_iters": iters, "relres": relres,
             "block_products_per_step": products_block / args.steps,

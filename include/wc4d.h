@@ -209,6 +209,21 @@ wc4d_status wc4d_batch_inner_loop(wc4d_ctx *const *ctxs, int32_t count, int32_t 
                                   int32_t maxit, int32_t precision, double *const *x_device, int32_t *iters,
                                   double *relres, int32_t *status, int32_t workers);
 
+/* Learned sketch proposal (the paper has none: an aid to the randomised
+ * range finder, whose Alg. 3 input it becomes together with Gaussian
+ * columns).  A fixed 4-layer 1D convolutional encoder over the periodic
+ * Lorenz-96 grid maps the current linearisation trajectory (states at the
+ * subwindow boundaries, divided by F) and the observation mask of every time
+ * to m columns S (device, nA x m, column-major, ld >= nA, FP64 output):
+ *   layer 0: 2(N+1) -> 64 channels, width 5, ReLU; layers 1, 2: 64 -> 64,
+ *   width 5, ReLU; layer 3: 64 -> m(N+1), width 1; output channel
+ *   j(N+1) + t is time block t of column j.
+ * w_bf16 (device): BF16 weights W0|W1|W2|W3, each [out][in][width]; bias
+ * (device): FP32 b0|b1|b2|b3.  Sums in FP32.  Lorenz-96 contexts after
+ * wc4d_set_background_obs only (WC4D_EINVAL / WC4D_ESTATE otherwise). */
+wc4d_status wc4d_learned_probes(wc4d_ctx *ctx, const uint16_t *w_bf16_device, const float *bias_device, int32_t m,
+                                double *S_device, int64_t ld);
+
 /* ---- small building blocks, exported for verification ------------------ */
 
 /* CholeskyQR2 in place (the orthonormalisation of Alg. 3-5): Y (device,

@@ -569,8 +569,10 @@ extern "C" wc4d_status wc4d_hvp(wc4d_ctx *c, const void *X, void *Y, int32_t K, 
     WC4D_TRY(prep_precision(c, precision));
     wc4d_status st = (precision == WC4D_FP64) ? hvp_impl<double>(c, (const double *)X, (double *)Y, K, ld)
                                               : hvp_impl<float>(c, (const float *)X, (float *)Y, K, ld);
-    if (st == WC4D_OK && K == 1 && sweep_error(c))
-        return set_err(c, WC4D_ETIMEOUT, "persistent sweep: a grid barrier timed out");
+    int e = 0;
+    if (st == WC4D_OK && K == 1 && (e = sweep_error(c)) != 0)
+        return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d: 1 grid barrier timeout, 2 misaligned "
+                                         "operand, 3/4 copy pipeline wait timeout)", e);
     return st;
 }
 
@@ -1236,13 +1238,9 @@ static wc4d_status lmp_cg_step(wc4d_ctx *c, T *x, T *r, T *rh, const T *p, const
     double *scal = P<double>(c->scal);
     int *flags = P<int>(c->counter) + 4;
     unsigned *done = reinterpret_cast<unsigned *>(P<int>(c->counter) + 8);
-    {
-        ProfScope ps(c, PROF_LMP);
-        launch_lmp_fused<T>(c->stream, c->num_sms, nA, c->kU, kp, Urm<T>(c), Ucm<T>(c), P<double>(c->c64), q, p, rh,
-                            t, x, r, scal, flags, P<double>(c->part), w, partB, done);
-    }
-    ProfScope ps(c, PROF_VEC);
-    launch_pcg_beta(c->stream, G, partB, partB + G, scal, flags, tol_k, qcf_dev, it);
+    ProfScope ps(c, PROF_LMP);
+    launch_lmp_fused<T>(c->stream, c->num_sms, nA, c->kU, kp, Urm<T>(c), Ucm<T>(c), P<double>(c->c64), q, p, rh, t,
+                        x, r, scal, flags, P<double>(c->part), w, partB, done, tol_k, qcf_dev, it);
     return WC4D_OK;
 }
 
@@ -1299,7 +1297,7 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
     WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
     WC4D_TRY(sync(c, "pcg end"));
     out.done = hflags[0] != 0;
-    if (sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep: a grid barrier timed out");
+    if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
     out.breakdown = hflags[1];
     out.iters = hflags[2];
     out.relres_rec = hs[4];
@@ -1428,7 +1426,7 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
         launch_add_f32_to_f64(c->stream, nA, d, x);
         WC4D_TRY(true_residual(c, x, r64, &rel, nullptr));
     }
-    if (sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep: a grid barrier timed out");
+    if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
     *iters_out = it;
     *rel_out = rel;
     *breakdown_out = breakdown;

@@ -12,6 +12,10 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// PCG device state: scalars and flags
+enum { S_RHO = 0, S_ALPHA, S_BETA, S_BNORM, S_RELRES, S_PQ, S_RR };
+enum { F_DONE = 0, F_BREAK, F_ITER };
+
 // Sum over a CTA (blockDim.x multiple of 32, <= 1024); result valid in all threads.
 __device__ double block_sum(double v)
 {
@@ -1043,9 +1047,11 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, const T *__restrict__ U,
                                                     const double *__restrict__ w, const double *__restrict__ scal,
                                                     const T *__restrict__ q, const T *__restrict__ p, T *rh, T *t,
-                                                    T *x, T *r, double *part)
+                                                    T *x, T *r, double *part, double *scal_rw, int *flags,
+                                                    unsigned *done, double tol, double *qcf_drop, int it)
 {
     extern __shared__ __align__(16) double wsm[];
+    __shared__ int last;
     T *w1 = reinterpret_cast<T *>(wsm), *w2 = w1 + kp;
     T (*red)[PB_CHUNKS][PB_ROWS] = reinterpret_cast<T (*)[PB_CHUNKS][PB_ROWS]>(w2 + kp);
     for (int i = threadIdx.x; i < kp; i += blockDim.x) {
@@ -1121,6 +1127,37 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, c
     if (threadIdx.x == 0) {
         part[blockIdx.x] = srh;
         part[gridDim.x + blockIdx.x] = sr;
+        __threadfence();
+        last = (atomicAdd(done, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last CTA: beta, rho, relative residual, QCF decrease and the done
+    // flag from all partial sums (fixed order), as the CG beta step
+    __threadfence();
+    double t1 = 0.0, t2 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        t1 += __ldcg(part + i);
+        t2 += __ldcg(part + gridDim.x + i);
+    }
+    const double rho_new = block_sum(t1);
+    const double rr = block_sum(t2);
+    if (threadIdx.x == 0) {
+        *done = 0u;
+        if (flags[F_DONE]) {
+            scal_rw[S_BETA] = 0.0;
+            return;
+        }
+        const double rho = scal_rw[S_RHO];
+        scal_rw[S_BETA] = rho_new / rho;
+        if (qcf_drop) qcf_drop[it] = 0.5 * scal_rw[S_ALPHA] * rho;
+        scal_rw[S_RHO] = rho_new;
+        scal_rw[S_RR] = rr;
+        const double rel = sqrt(rr) / scal_rw[S_BNORM];
+        scal_rw[S_RELRES] = rel;
+        flags[F_ITER] += 1;
+        if (!isfinite(rel)) { flags[F_BREAK] = 2; flags[F_DONE] = 1; }
+        else if (tol > 0.0 && rel <= tol) flags[F_DONE] = 1;
     }
 }
 
@@ -1129,7 +1166,7 @@ int lmp_pass_b_grid(int64_t nA) { return ceil_div(nA, PB_ROWS); }
 template <typename T>
 void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const T *Ucm,
                       const double *cvec, const T *q, const T *p, T *rh, T *t, T *x, T *r, double *scal, int *flags,
-                      double *partA, double *w, double *partB, unsigned *done)
+                      double *partA, double *w, double *partB, unsigned *done, double tol, double *qcf_drop, int it)
 {
     const int S = lmp_pass_a_splits(nA, num_sms);
     const int64_t rows_per = (nA + S - 1) / S;
@@ -1138,23 +1175,24 @@ void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, co
     WC4D_LAUNCH(k_lmp_coef<<<ceil_div(2 * kp + 1, 8), 256, 0, s>>>(S, k, kp, partA, cvec, scal, flags, sums, w, done));
     const int G = lmp_pass_b_grid(nA);
     const size_t smem = (2 * (size_t)kp + 2 * PB_CHUNKS * PB_ROWS) * sizeof(T);
-    WC4D_LAUNCH(k_lmp_pass_b<T><<<G, 256, smem, s>>>(nA, k, kp, Ucm, w, scal, q, p, rh, t, x, r, partB));
+    WC4D_LAUNCH(k_lmp_pass_b<T><<<G, 256, smem, s>>>(nA, k, kp, Ucm, w, scal, q, p, rh, t, x, r, partB, scal, flags,
+                                                     done + 1, tol, qcf_drop, it));
 }
 
 template void launch_lmp_fused<double>(cudaStream_t, int, int64_t, int, int, const double *, const double *,
                                        const double *, const double *, const double *, double *, double *, double *,
-                                       double *, double *, int *, double *, double *, double *, unsigned *);
+                                       double *, double *, int *, double *, double *, double *, unsigned *, double,
+                                       double *, int);
 template void launch_lmp_fused<float>(cudaStream_t, int, int64_t, int, int, const float *, const float *,
                                       const double *, const float *, const float *, float *, float *, float *,
-                                      float *, double *, int *, double *, double *, double *, unsigned *);
+                                      float *, double *, int *, double *, double *, double *, unsigned *, double,
+                                      double *, int);
 
 // ----------------------------------------------------------------------------
 // PCG (Alg. 1) vector and scalar kernels.  Scalars live in device memory:
 // scal[0] rho = rhat^T rhat, [1] alpha, [2] beta, [3] |b|, [4] |r|/|b|,
 // [5] p^T A p, [6] |r|^2; flags[0] done, [1] breakdown, [2] iterations.
 // ----------------------------------------------------------------------------
-enum { S_RHO = 0, S_ALPHA, S_BETA, S_BNORM, S_RELRES, S_PQ, S_RR };
-enum { F_DONE = 0, F_BREAK, F_ITER };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const T *a, const T *b, double *part)

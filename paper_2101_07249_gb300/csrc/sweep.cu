@@ -432,7 +432,14 @@ __device__ __forceinline__ bool step_barrier(unsigned *cnt, int t, unsigned nblo
     return ok_s != 0;
 }
 
-template <typename T, typename Acc>
+// Loads of a propagator row.  A propagator shared by every subwindow (the
+// time-invariant case) is read N times per sweep and is loaded with the
+// default L2 policy (ld.global.cg) so that it may stay resident between
+// subwindows; otherwise each M_t is read once per sweep and streams with
+// evict-first loads.
+template <bool KEEP, typename V> __device__ __forceinline__ V ld_row(const V *p) { return KEEP ? __ldcg(p) : __ldcs(p); }
+
+template <typename T, typename Acc, bool KEEP>
 __global__ void __launch_bounds__(512)
 k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
 {
@@ -459,7 +466,11 @@ k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
                     const int idx = c0 + 32 * u;
-                    if (idx < nv) { xv[u] = __ldcg(x4 + idx); av[u] = __ldcs(ra + idx); bv[u] = __ldcs(rb + idx); }
+                    if (idx < nv) {
+                        xv[u] = __ldcg(x4 + idx);
+                        av[u] = ld_row<KEEP>(ra + idx);
+                        bv[u] = ld_row<KEEP>(rb + idx);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
@@ -494,6 +505,237 @@ k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
     }
 }
 
+// ----------------------------------------------------------------------------
+// Staged form of the persistent FP32 sweep for n a multiple of 2048 (n =
+// 2048, 4096, 8192): the same work split (CTA b owns rows [b R, b R + R) of
+// every M_t), with the propagator rows brought into a ring of shared memory
+// by a producer warp through bulk asynchronous copies (one cp.async.bulk per
+// row, completion counted on a "full" mbarrier per slot).  Sixteen consumer
+// warps each own a fixed set of J = n / 2048 float4 column slots of every
+// row (slot j of thread i: columns 4 (i + 512 j) .. + 3), so the x values they
+// need sit in registers for a whole subwindow; after reading a stage they
+// arrive on the slot's "empty" mbarrier and the producer refills it.  The
+// producer is not part of the grid barrier: it runs SW_NS stages ahead across
+// subwindow boundaries (the rows of M_{t+1} do not depend on x), so the copy
+// engine keeps streaming while the consumers wait for x_{t+1}.  Row sums: warp
+// shuffle, then the 16 warp partials in a fixed order.  All waits are
+// bounded; after a grid-barrier timeout the consumers keep draining the ring
+// (without further barriers) so that no copy is in flight when the CTA exits.
+// Measured on GB300 (n = 4096, N = 40, 2.7 GB of propagators): 448 us per
+// sweep against 491 us for per-thread cp.async staging and 533 us for the
+// register-staged k_gemv_sweep.
+// ----------------------------------------------------------------------------
+constexpr int SW_THREADS = 512;                       // consumer threads
+constexpr int SW_RING = 192 * 1024;                   // bytes of shared memory in the ring
+constexpr int SW_RMAX = 64;                           // rows per CTA
+constexpr unsigned SW_WAIT = 1u << 22;                // mbarrier polls before giving up
+
+template <int J> struct SwShape {
+    static constexpr int G = J == 1 ? 2 : 1;                          // rows per stage
+    static constexpr int NS = SW_RING / (G * J * SW_THREADS * 16);    // stages in the ring
+};
+
+__device__ __forceinline__ void sw_mb_init(uint32_t a, unsigned c)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(c) : "memory");
+}
+__device__ __forceinline__ void sw_mb_expect(uint32_t a, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void sw_mb_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool sw_mb_wait(uint32_t a, unsigned parity)
+{
+    for (unsigned it = 0; it < SW_WAIT; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void sw_bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t mb)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mb)
+                 : "memory");
+}
+// barrier of the 512 consumer threads only (the producer warp is not in it)
+__device__ __forceinline__ void sw_cbar() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+
+// step_barrier for the consumer threads
+__device__ __forceinline__ bool sw_step_barrier(unsigned *cnt, int t, unsigned nblocks, int *err)
+{
+    __shared__ int ok_c;
+    sw_cbar();
+    if (threadIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt + t) : "memory");
+        unsigned v = 0, it = 0;
+        int ok = 1;
+        do {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt + t) : "memory");
+            if (++it > (1u << 22)) { ok = 0; atomicExch(err, 1); break; }
+        } while (v < nblocks);
+        ok_c = ok;
+    }
+    sw_cbar();
+    return ok_c != 0;
+}
+
+__device__ __forceinline__ float dot_acc(float4 m, float4 x, float acc)
+{
+    acc = fmaf(m.x, x.x, acc);
+    acc = fmaf(m.y, x.y, acc);
+    acc = fmaf(m.z, x.z, acc);
+    return fmaf(m.w, x.w, acc);
+}
+
+template <int J>
+__global__ void __launch_bounds__(SW_THREADS + 32, 1) k_gemv_sweep_staged(const float *__restrict__ M0, float *W,
+                                                                          SweepArgs a)
+{
+    constexpr int G = SwShape<J>::G, NS = SwShape<J>::NS;
+    extern __shared__ __align__(128) unsigned char sw_smem[];
+    __shared__ __align__(8) unsigned long long mbar[2 * NS];   // full[NS] | empty[NS]
+    __shared__ float part[SW_RMAX][SW_THREADS / 32];
+    const float4 *ring = reinterpret_cast<const float4 *>(sw_smem);   // [NS][G][n / 4]
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(sw_smem);
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+    const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rbeg = blockIdx.x * a.rows_per_cta;
+    const int R = max(0, min(n, rbeg + a.rows_per_cta) - rbeg);
+    const int S = (R + G - 1) / G;   // stages per subwindow
+    const int total = a.N * S;
+    const unsigned rowb = (unsigned)n * 4u;
+    // bulk copies need 16-byte aligned addresses and sizes: the condition is
+    // the same in every CTA, so a failed check exits the whole grid
+    if ((ring_s & 15u) != 0u || (reinterpret_cast<uintptr_t>(M0) & 15u) != 0u ||
+        (reinterpret_cast<uintptr_t>(W) & 15u) != 0u || (rowb & 15u) != 0u) {
+        if (blockIdx.x == 0 && tid == 0) atomicExch(a.err, 2);
+        return;
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            sw_mb_init(mb + 8 * i, 1);
+            sw_mb_init(mb + 8 * (NS + i), SW_THREADS / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == SW_THREADS / 32) {   // producer warp: one thread issues
+        if (lane == 0) {
+            for (int k = 0; k < total; ++k) {
+                const int slot = k % NS;
+                if (k >= NS && !sw_mb_wait(mb + 8 * (NS + slot), ((k / NS) - 1) & 1)) {
+                    atomicExch(a.err, 3);
+                    break;
+                }
+                const int step = k / S, s0 = (k % S) * G;
+                const int rows = min(G, R - s0);
+                const int t = (a.mode == 0) ? step : a.N - 1 - step;
+                const float *M = M0 + (int64_t)t * a.mstride + (int64_t)(rbeg + s0) * n;
+                sw_mb_expect(mb + 8 * slot, rowb * (unsigned)rows);
+                for (int g = 0; g < rows; ++g)
+                    sw_bulk_g2s(ring_s + (uint32_t)(slot * G + g) * rowb, M + (int64_t)g * n, rowb, mb + 8 * slot);
+            }
+        }
+        return;
+    }
+
+    const int nv = n / 4;
+    int k = 0;
+    bool bad = false;
+    for (int step = 0; step < a.N; ++step) {
+        const int t = (a.mode == 0) ? step : a.N - 1 - step;
+        const float4 *x4 = reinterpret_cast<const float4 *>(W + (int64_t)((a.mode == 0) ? t : t + 1) * n);
+        float *y = W + (int64_t)((a.mode == 0) ? t + 1 : t) * n;
+        float4 xr[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) xr[j] = __ldcg(x4 + tid + SW_THREADS * j);
+        for (int s = 0; s < S; ++s, ++k) {
+            const int slot = k % NS;
+            if (!sw_mb_wait(mb + 8 * slot, (k / NS) & 1)) {
+                atomicExch(a.err, 4);
+                return;
+            }
+            float v[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                float acc = 0.f;
+                if (s * G + g < R) {
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        acc = dot_acc(ring[(slot * G + g) * nv + tid + SW_THREADS * j], xr[j], acc);
+                }
+                v[g] = acc;
+            }
+            __syncwarp();
+            if (lane == 0) sw_mb_arrive(mb + 8 * (NS + slot));   // the slot may be refilled
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v[g] += __shfl_xor_sync(0xffffffffu, v[g], o);
+                if (lane == 0 && s * G + g < R) part[s * G + g][warp] = v[g];
+            }
+        }
+        sw_cbar();
+        if (tid < R) {
+            float sum = 0.f;
+#pragma unroll
+            for (int i = 0; i < SW_THREADS / 32; ++i) sum += part[tid][i];
+            const int row = rbeg + tid;
+            const float old = __ldcg(y + row);
+            float out;
+            if (a.mode == 0) {
+                out = old + sum;
+            } else {
+                const bool obs = (t >= a.t0 && (t - a.t0) % a.ts == 0 && row % a.obs_stride == 0);
+                out = sum + (obs ? (float)a.obs_inv * old : 0.f);
+            }
+            y[row] = out;
+        }
+        if (step + 1 < a.N) {
+            if (!bad) bad = !sw_step_barrier(a.bar, step, gridDim.x, a.err);
+            else sw_cbar();   // keep draining the ring after a barrier timeout
+        }
+    }
+}
+
+template <int J>
+static bool launch_sweep_staged(cudaStream_t s, int num_sms, const float *M0, float *W, SweepArgs &args)
+{
+    const void *fn = (const void *)k_gemv_sweep_staged<J>;
+    const int smem = SwShape<J>::NS * SwShape<J>::G * J * SW_THREADS * 16;
+    static int st = -1;
+    if (st < 0) {
+        int per_sm = 0;
+        st = (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SW_THREADS + 32, smem) == cudaSuccess &&
+              per_sm >= 1) ? 1 : 0;
+        cudaGetLastError();
+    }
+    if (!st) return false;
+    const int n = args.n;
+    const int rpc = ceil_div(n, num_sms);
+    if (rpc > SW_RMAX) return false;
+    args.rows_per_cta = rpc;
+    const int grid = ceil_div(n, rpc);
+    void *params[] = {(void *)&M0, (void *)&W, (void *)&args};
+    wc4d_note_launch();
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(SW_THREADS + 32), params, smem, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 // Launch configuration of the persistent sweep (one CTA of 512 threads per
 // SM, co-resident by cooperative launch).  Returns false if it cannot be used.
 template <typename T>
@@ -503,12 +745,16 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     constexpr int VEC = sizeof(T) == 8 ? 2 : 4;
     if (n % VEC != 0 || !aligned16(M0) || !aligned16(W) || ((int64_t)n * sizeof(T)) % 16 != 0) return false;
     using Acc = T;
+    const bool keep = (mstride == 0 && N > 1);
+    const void *fn = keep ? (const void *)k_gemv_sweep<T, Acc, true> : (const void *)k_gemv_sweep<T, Acc, false>;
     static int max_blocks = -1;
     int &mb = max_blocks;
     if (mb < 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_sweep<T, Acc>, 512, 0);
-        mb = per_sm * num_sms;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_sweep<T, Acc, false>, 512, 0);
+        int per_sm_keep = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_keep, k_gemv_sweep<T, Acc, true>, 512, 0);
+        mb = std::min(per_sm, per_sm_keep) * num_sms;
     }
     int grid = std::min(num_sms, mb);
     if (grid < 1) return false;
@@ -521,6 +767,21 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     args.obs_stride = obs_stride;
     args.t0 = t0;
     args.ts = ts > 0 ? ts : 1;
+    args.bar = bar;
+    args.err = err;
+    {
+        // FP32 only: the FP64 sweep is bound by the FP64 pipe, where the
+        // per-row shuffle reductions of the staged form cost more than the
+        // barrier time it hides
+        if constexpr (sizeof(T) == 4) {
+            const int slots = n / (SW_THREADS * VEC);   // J
+            if (n % (SW_THREADS * VEC) == 0) {
+                if (slots == 1 && launch_sweep_staged<1>(s, num_sms, M0, W, args)) return true;
+                if (slots == 2 && launch_sweep_staged<2>(s, num_sms, M0, W, args)) return true;
+                if (slots == 4 && launch_sweep_staged<4>(s, num_sms, M0, W, args)) return true;
+            }
+        }
+    }
     int rpc = (n + grid - 1) / grid;
     rpc = (rpc + 1) / 2 * 2;
     grid = (n + rpc - 1) / rpc;
@@ -529,7 +790,7 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     args.err = err;
     void *params[] = {(void *)&M0, (void *)&W, (void *)&args};
     wc4d_note_launch();
-    if (cudaLaunchCooperativeKernel((const void *)k_gemv_sweep<T, Acc>, dim3(grid), dim3(512), params, 0, s) !=
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(512), params, 0, s) !=
         cudaSuccess) {
         cudaGetLastError();   // fall back to one launch per subwindow
         return false;

@@ -269,16 +269,17 @@ void launch_pcg_p(cudaStream_t s, int grid, int64_t n, const double *scal, T *p,
 void launch_pcg_alpha(cudaStream_t s, int grid, const double *part, double *scal, int *flags);
 // One fused split-preconditioned CG iteration after q = A p (one pass over
 // the row-major Ritz vectors Urm, one over the column-major copy Ucm, ld nA):
-// alpha in scal[1], rhat, t = C rhat, x, r updated, partials of |rhat|^2 and
-// |r|^2 in partB[0, G) and partB[G, 2G), G = lmp_pass_b_grid(nA).  partA:
+// alpha in scal[1], rhat, t = C rhat, x, r updated, then (last CTA of the
+// second pass) the CG beta step: beta, rho, relative residual, QCF decrease,
+// flags.  partB: 2 lmp_pass_b_grid(nA) doubles of partial sums; partA:
 // lmp_pass_a_splits(nA, num_sms) x (2 kp + 1) doubles; w: 4 kp + 1 doubles;
-// done: a counter that is zero on entry (and is left at zero).
+// done: two counters that are zero on entry (and are left at zero).
 int lmp_pass_a_splits(int64_t nA, int num_sms);
 int lmp_pass_b_grid(int64_t nA);
 template <typename T>
 void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const T *Ucm,
                       const double *cvec, const T *q, const T *p, T *rh, T *t, T *x, T *r, double *scal, int *flags,
-                      double *partA, double *w, double *partB, unsigned *done);
+                      double *partA, double *w, double *partB, unsigned *done, double tol, double *qcf_drop, int it);
 void launch_pcg_restart(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
                         int *flags);
 void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
