@@ -472,6 +472,7 @@ def main():
     ev1.record()
     torch.cuda.synchronize()
     profiled_ms = ev0.elapsed_time(ev1)
+    jacobi_sweeps = w.wc4d_jacobi_sweeps(ctx)
     classes = {}
     for ci, name in enumerate(w.PROF_CLASSES):
         ms, cnt = w.wc4d_profile_read(ctx, ci)
@@ -573,6 +574,7 @@ def main():
             "fp64_plain": fp64,
             "speedup_vs_fp64": (fp64["inner_loop_s"] / (t_max / args.steps)) if fp64 else None,
             "kernel_classes": classes,
+            "jacobi_sweeps": jacobi_sweeps,
             "profiled_inner_loop_ms": profiled_ms,
             "unclassified_ms": profiled_ms - sum(v["ms"] for v in classes.values()),
             "roofline": roof,

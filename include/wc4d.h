@@ -283,6 +283,12 @@ wc4d_status wc4d_lmp_apply_static(const double *U, const double *theta, int32_t 
                                   double *y, void *cuda_stream);
 /* Products with A issued so far (block products count once). */
 int64_t     wc4d_hvp_count(wc4d_ctx *ctx, int32_t reset);
+/* One-sided Jacobi sweeps used by the last small eigensolve or SVD of the
+   context (Alg. 2 EVD of K, Alg. 4 SVD of F, Alg. 5 SVD of R_3, or
+   wc4d_symeig), counting a final sweep without rotations when the solve ran
+   to convergence; -1 for a null context.  In a mixed-precision sketch the
+   solve stops after a sweep whose largest rotation had |cos| <= 1e-5. */
+int32_t     wc4d_jacobi_sweeps(const wc4d_ctx *ctx);
 
 #ifdef __cplusplus
 }

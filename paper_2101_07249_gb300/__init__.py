@@ -78,6 +78,7 @@ _SIGS = {
     "wc4d_orthonormalize": (C.c_int, [_V, _V, C.c_int64, C.c_int32, C.c_int64, _D, C.c_int32]),
     "wc4d_symeig": (C.c_int, [_V, C.c_int32, _V, _D, _V]),
     "wc4d_hvp_count": (C.c_int64, [_V, C.c_int32]),
+    "wc4d_jacobi_sweeps": (C.c_int32, [_V]),
     "wc4d_apply_dsqrt": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_apply_linv": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_apply_linvT": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
@@ -353,6 +354,10 @@ def wc4d_lmp_apply_static(U, theta, k, nA, v, y, stream=None):
 
 def wc4d_hvp_count(ctx, reset=False):
     return int(load().wc4d_hvp_count(ctx, 1 if reset else 0))
+
+
+def wc4d_jacobi_sweeps(ctx):
+    return int(load().wc4d_jacobi_sweeps(ctx))
 
 
 # --------------------------------------------------------------------------

@@ -275,6 +275,8 @@ extern "C" wc4d_status wc4d_profile_read(wc4d_ctx *c, int32_t cls, double *total
     return WC4D_OK;
 }
 
+extern "C" int32_t wc4d_jacobi_sweeps(const wc4d_ctx *c) { return c ? c->jacobi_sweeps : -1; }
+
 extern "C" int64_t wc4d_hvp_count(wc4d_ctx *c, int32_t reset)
 {
     if (!c) return -1;
@@ -815,19 +817,22 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
     const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
     if (const int Pq = c->allow_coop ? jacobi_coop_size(m) : 0) {
         const size_t nd = jacobi_coop_doubles(m);
-        WC4D_TRY(ensure(c, c->small3, sizeof(double) * nd + sizeof(int) * 128));
+        // XV | rot[64] | bar, err, status | maxm[64] (64-bit words)
+        WC4D_TRY(ensure(c, c->small3, sizeof(double) * nd + sizeof(int) * 128 + sizeof(unsigned long long) * 64));
         double *XV = P<double>(c->small3);
         int *rot = reinterpret_cast<int *>(XV + nd);
         unsigned *bar = reinterpret_cast<unsigned *>(rot + 64);
         int *err = rot + 65;
         int *status = rot + 66;
+        unsigned long long *maxm = reinterpret_cast<unsigned long long *>(rot + 128);
         WC4D_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
-        if (launch_jacobi_coop(c->stream, m, X0, XV, tol, 60, rot, bar, err, status, want_v)) {
+        if (launch_jacobi_coop(c->stream, m, X0, XV, tol, 60, rot, bar, err, status, want_v, c->jacobi_stop2, maxm)) {
             int *h = P<int>(c->pinned);
             WC4D_CUDA(c, cudaMemcpyAsync(h, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
             WC4D_TRY(sync(c, "jacobi"));
             if (h[0]) return set_err(c, WC4D_ETIMEOUT, "Jacobi: a grid barrier timed out");
             if (h[1] < 0) return set_err(c, WC4D_ETIMEOUT, "one-sided Jacobi did not converge in 60 sweeps");
+            c->jacobi_sweeps = h[1];
             *Xo = XV;
             *Vo = XV + (size_t)Pq * Pq;
             *ld = Pq;
@@ -850,7 +855,7 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
             WC4D_TRY(check_launch(c, "jacobi round"));
             WC4D_CUDA(c, cudaMemcpyAsync(hrot, rot, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
             WC4D_TRY(sync(c, "jacobi sweep"));
-            if (*hrot == 0) { conv = true; break; }
+            if (*hrot == 0) { conv = true; c->jacobi_sweeps = sweep + 1; break; }
         }
         if (!conv) return set_err(c, WC4D_ETIMEOUT, "one-sided Jacobi did not converge in 60 sweeps");
     }
@@ -972,6 +977,15 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     T *A_ = P<T>(c->blkA), *B_ = P<T>(c->blkB), *C_ = P<T>(c->blkC), *D_ = P<T>(c->blkD);
     wc4d_status st = WC4D_OK;
     auto fail = [&](wc4d_status s) { return s; };
+    // Mixed sketch: the small FP64 eigensolves stop after a sweep whose
+    // largest rotation had |cos| <= 1e-5 (columns then orthogonal to about
+    // 1e-10, far below the TF32 error of the sketch products) instead of
+    // running a last sweep that only confirms convergence.
+    struct StopGuard {
+        wc4d_ctx *c;
+        ~StopGuard() { c->jacobi_stop2 = 0.0; }
+    } stop_guard{c};
+    c->jacobi_stop2 = (sizeof(T) == 4) ? 1e-10 : 0.0;
 
     // step 1: Gaussian probes G (FP64), cast to the working precision
     double *G64 = P<double>(c->blkD);

@@ -53,6 +53,8 @@ struct JqArgs {
     int *err;           // 1 after a barrier timeout
     int *status;        // sweeps used, or -1 when not converged
     int want_v;         // 0: V is neither accumulated nor written
+    double stop2;       // > 0: early stop threshold on the largest g^2 / (a b) of a sweep
+    unsigned long long *maxm;   // max_sweeps largest g^2 / (a b) (double bits, zeroed here)
 };
 
 __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
@@ -74,7 +76,10 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
         }
     }
     if (pair == 0)
-        for (int s = r; s < a.max_sweeps; s += blockDim.x) a.rot[s] = 0;
+        for (int s = r; s < a.max_sweeps; s += blockDim.x) {
+            a.rot[s] = 0;
+            a.maxm[s] = 0ull;
+        }
     unsigned target = G;
     if (!jq_barrier(a.bar, target, a.err)) return;
 
@@ -132,6 +137,8 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
                     cs[1] = c * tn;
                     doit = 1;
                     atomicAdd(a.rot + sweeps, 1);
+                    if (a.stop2 > 0.0)   // non-negative doubles order as their bit patterns
+                        atomicMax(a.maxm + sweeps, (unsigned long long)__double_as_longlong((g * g) / (aa * bb)));
                 }
                 doit_s = doit;
             }
@@ -159,7 +166,9 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
             double *t0 = Xc, *t1 = Vc;
             Xc = Xn; Vc = Vn; Xn = t0; Vn = t1;
         }
-        if (threadIdx.x == 0) conv_s = (__ldcg(a.rot + sweeps) == 0);
+        if (threadIdx.x == 0)
+            conv_s = (__ldcg(a.rot + sweeps) == 0) ||
+                     (a.stop2 > 0.0 && __longlong_as_double((long long)__ldcg(a.maxm + sweeps)) <= a.stop2);
         __syncthreads();
         converged = conv_s != 0;
     }
@@ -189,9 +198,10 @@ size_t jacobi_coop_doubles(int m)
 // launch is refused.  XV: jacobi_coop_doubles(m) doubles; the result is
 // X = XV[0, P^2), V = XV[P^2, 2 P^2).  rot: max_sweeps ints; bar: one
 // counter, zeroed here; err: set to 1 if a grid barrier times out.  With
-// want_v false only X is produced.
+// want_v false only X is produced.  stop2 > 0 enables the early stop (maxm:
+// max_sweeps 64-bit words).
 bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, double tol, int max_sweeps, int *rot,
-                        unsigned *bar, int *err, int *status, bool want_v)
+                        unsigned *bar, int *err, int *status, bool want_v, double stop2, unsigned long long *maxm)
 {
     const int P = jacobi_coop_size(m);
     if (P == 0) return false;
@@ -199,7 +209,7 @@ bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, dou
         cudaGetLastError();
         return false;
     }
-    JqArgs args{m, P, X0, XV, tol, max_sweeps, rot, bar, err, status, want_v ? 1 : 0};
+    JqArgs args{m, P, X0, XV, tol, max_sweeps, rot, bar, err, status, want_v ? 1 : 0, stop2, maxm};
     void *params[] = {&args};
     wc4d_note_launch();
     if (cudaLaunchCooperativeKernel((const void *)k_jacobi_coop, dim3(P / 2), dim3(JQ_THREADS), params, 0, s) !=

@@ -157,6 +157,213 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
     }
 }
 
+// ----------------------------------------------------------------------------
+// D^{1/2} for 512 <= n <= 8192 (a power of two) with a Stockham auto-sort
+// FFT: n / 16 threads, each holding 16 complex values in registers per pass;
+// passes of radix 16 and one final pass of radix n / 16^P in {2, 4, 8} (n =
+// 4096: three radix-16 passes), one shared-memory exchange per pass instead
+// of one per radix-4 pair of layers.  Pass (radix R, span p): butterfly j
+// reads buf[j + r n / R] (r < R), scales value r by W_n^{r (j mod p) n / (p R)},
+// applies the R-point DFT and writes buf[(j / p) p R + j mod p + r p]; after
+// the last pass buf holds the transform in natural order.  The inverse uses
+// the same forward passes: y = conj(FFT(conj(s Z))) with the real spectrum s
+// (already divided by n), so the result's real part is D^{1/2} x_a and minus
+// its imaginary part D^{1/2} x_b.
+// ----------------------------------------------------------------------------
+template <typename CT> __device__ __forceinline__ CT cmuls(CT a, double c, double s)   // a * (c + i s)
+{
+    CT r;
+    r.x = a.x * (decltype(a.x))c - a.y * (decltype(a.x))s;
+    r.y = a.x * (decltype(a.x))s + a.y * (decltype(a.x))c;
+    return r;
+}
+template <typename CT> __device__ __forceinline__ CT cmul_mi(CT a)   // a * (-i)
+{
+    CT r;
+    r.x = a.y;
+    r.y = -a.x;
+    return r;
+}
+
+// in-place forward DFTs of size 2, 4, 8, 16 on v[0 .. R) (W_R = e^{-2 pi i / R})
+template <typename CT> __device__ __forceinline__ void dft2(CT &a, CT &b)
+{
+    const CT t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+template <typename CT> __device__ __forceinline__ void dft4(CT *v)
+{
+    const CT a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    const CT b0 = cadd(v[1], v[3]), b1 = cmul_mi(csub(v[1], v[3]));
+    v[0] = cadd(a0, b0);
+    v[2] = csub(a0, b0);
+    v[1] = cadd(a1, b1);
+    v[3] = csub(a1, b1);
+}
+template <typename CT> __device__ __forceinline__ void dft8(CT *v)
+{
+    CT e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft4(e);
+    dft4(o);
+    constexpr double h = 0.70710678118654752440;   // cos(pi / 4)
+    o[1] = cmuls(o[1], h, -h);
+    o[2] = cmul_mi(o[2]);
+    o[3] = cmuls(o[3], -h, -h);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = cadd(e[k], o[k]);
+        v[k + 4] = csub(e[k], o[k]);
+    }
+}
+template <typename CT> __device__ __forceinline__ void dft16(CT *v)
+{
+    CT e[8], o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        e[k] = v[2 * k];
+        o[k] = v[2 * k + 1];
+    }
+    dft8(e);
+    dft8(o);
+    constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173;   // cos, sin(pi / 8)
+    constexpr double h = 0.70710678118654752440;
+    o[1] = cmuls(o[1], c1, -s1);
+    o[2] = cmuls(o[2], h, -h);
+    o[3] = cmuls(o[3], s1, -c1);
+    o[4] = cmul_mi(o[4]);
+    o[5] = cmuls(o[5], -s1, -c1);
+    o[6] = cmuls(o[6], -h, -h);
+    o[7] = cmuls(o[7], -c1, -s1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[k] = cadd(e[k], o[k]);
+        v[k + 8] = csub(e[k], o[k]);
+    }
+}
+template <int R, typename CT> __device__ __forceinline__ void dftR(CT *v)
+{
+    if constexpr (R == 2) dft2(v[0], v[1]);
+    else if constexpr (R == 4) dft4(v);
+    else if constexpr (R == 8) dft8(v);
+    else dft16(v);
+}
+
+// one Stockham pass of radix R at span p; 16 / R butterflies per thread
+template <int R, typename CT>
+__device__ __forceinline__ void stockham_pass(CT *buf, const CT *tws, int n, int p, int tid, int nt)
+{
+    constexpr int B = 16 / R;
+    const int T = n / R, half = n >> 1;
+    CT v[B][R];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = tid + b * nt, k = j & (p - 1);
+        const int step = k * (n / (p * R));   // twiddle index of value r: r * step < n
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            CT x = buf[fpad(j + r * T)];
+            if (r > 0 && p > 1) {
+                const int q = r * step;
+                CT w = tws[q < half ? q : q - half];
+                if (q >= half) { w.x = -w.x; w.y = -w.y; }
+                x = cmul(x, w);
+            }
+            v[b][r] = x;
+        }
+        dftR<R>(v[b]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = tid + b * nt, k = j & (p - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[fpad(base + r * p)] = v[b][r];
+    }
+    __syncthreads();
+}
+
+template <typename CT> __device__ void stockham_fft(CT *buf, const CT *tws, int n, int tid, int nt)
+{
+    int p = 1;
+    while (p * 16 <= n) {
+        stockham_pass<16>(buf, tws, n, p, tid, nt);
+        p *= 16;
+    }
+    const int rest = n / p;
+    if (rest == 8) stockham_pass<8>(buf, tws, n, p, tid, nt);
+    else if (rest == 4) stockham_pass<4>(buf, tws, n, p, tid, nt);
+    else if (rest == 2) stockham_pass<2>(buf, tws, n, p, tid, nt);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_circ_stockham(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy,
+                const T *addX, int64_t ld_add, const T *__restrict__ specB, const T *__restrict__ specQ,
+                const typename Cplx<T>::t *__restrict__ tw, int nBpairs)
+{
+    using CT = typename Cplx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CT *buf = reinterpret_cast<CT *>(smem_raw);
+    const int tid = threadIdx.x, nt = blockDim.x;   // nt = n / 16
+    int pair = blockIdx.x;
+    const T *spec;
+    int64_t ja, ta, jb = 0, tb = 0;
+    bool hasb;
+    if (pair < nBpairs) {
+        int64_t va = 2 * (int64_t)pair, vb = va + 1;
+        spec = specB;
+        ja = va; ta = 0;
+        hasb = vb < K;
+        if (hasb) { jb = vb; tb = 0; }
+    } else {
+        int64_t p = pair - nBpairs;
+        int64_t va = 2 * p, vb = va + 1, cnt = (int64_t)K * N;
+        spec = specQ;
+        ja = va / N; ta = 1 + va % N;
+        hasb = vb < cnt;
+        if (hasb) { jb = vb / N; tb = 1 + vb % N; }
+    }
+    const T *xa = X + ja * ldx + ta * n;
+    const T *xb = X + jb * ldx + tb * n;
+    const int half = n >> 1;
+    CT *tws = buf + n + (n >> 4);
+#pragma unroll 4
+    for (int k = tid; k < half; k += nt) tws[k] = tw[k];
+#pragma unroll 16
+    for (int s = tid; s < n; s += nt) {
+        CT v;
+        v.x = xa[s];
+        v.y = hasb ? xb[s] : (T)0;
+        buf[fpad(s)] = v;
+    }
+    __syncthreads();
+    stockham_fft(buf, tws, n, tid, nt);
+    // scale by the real spectrum (stored bit-reversed) and conjugate
+    const int sh = 32 - logn;
+#pragma unroll 16
+    for (int q = tid; q < n; q += nt) {
+        const T w = spec[__brev((unsigned)q) >> sh];
+        CT v = buf[fpad(q)];
+        v.x *= w;
+        v.y *= -w;
+        buf[fpad(q)] = v;
+    }
+    __syncthreads();
+    stockham_fft(buf, tws, n, tid, nt);
+    T *ya = Y + ja * ldy + ta * n;
+    T *yb = Y + jb * ldy + tb * n;
+    const T *aa = addX ? addX + ja * ld_add + ta * n : nullptr;
+    const T *ab = addX ? addX + jb * ld_add + tb * n : nullptr;
+#pragma unroll 16
+    for (int s = tid; s < n; s += nt) {
+        const CT v = buf[fpad(s)];
+        ya[s] = v.x + (aa ? aa[s] : (T)0);
+        if (hasb) yb[s] = -v.y + (ab ? ab[s] : (T)0);
+    }
+}
+
 // Direct symmetric circulant product for any n: y_s = sum_r row[r] x[(s+r) mod n].
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -203,6 +410,19 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
         int nB = (K + 1) / 2;
         int64_t nQ = ((int64_t)K * N + 1) / 2;
         int grid = (int)(nB + nQ);
+        if (n >= 512) {   // n / 16 threads, 16 values each
+            static bool attr2 = false;
+            if (!attr2) {
+                cudaFuncSetAttribute(k_circ_stockham<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)((WC4D_FFT_MAX_N + WC4D_FFT_MAX_N / 16 + WC4D_FFT_MAX_N / 2) *
+                                           sizeof(typename Cplx<T>::t)));
+                attr2 = true;
+            }
+            WC4D_LAUNCH(k_circ_stockham<T><<<grid, n / 16, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add,
+                                                                       specB, specQ,
+                                                                       (const typename Cplx<T>::t *)tw, nB));
+            return;
+        }
         WC4D_LAUNCH(k_circ_fft<T><<<grid, 512, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,
                                               (const typename Cplx<T>::t *)tw, nB));
     } else {

@@ -131,6 +131,8 @@ struct wc4d_ctx {
     // profiling (CUDA events per launch group)
     // cooperative (grid-synchronised) kernels need the whole GPU; off while
     // the context runs concurrently with others (wc4d_batch_inner_loop)
+    double jacobi_stop2 = 0.0;      // early stop of the small eigensolves (0: run to a sweep without rotations)
+    int jacobi_sweeps = 0;          // sweeps used by the last one
     bool allow_coop = true;
     bool prof_on = false;
     std::vector<ProfEntry> prof_log;
@@ -232,7 +234,7 @@ void launch_jacobi_round(cudaStream_t s, int mp, double *X, double *V, int round
 int jacobi_coop_size(int m);
 size_t jacobi_coop_doubles(int m);
 bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, double tol, int max_sweeps, int *rot,
-                        unsigned *bar, int *err, int *status, bool want_v);
+                        unsigned *bar, int *err, int *status, bool want_v, double stop2, unsigned long long *maxm);
 void launch_jacobi_finish_left(cudaStream_t s, int m, int mp, const double *X, double *w, double *Vout);
 void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const double *V, double *w, double *Vout);
 void launch_rrt(cudaStream_t s, int m, const double *R, double *RT);

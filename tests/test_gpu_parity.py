@@ -183,6 +183,28 @@ def test_symeig_matches_jacobi(m):
     assert np.allclose(wv, wo, rtol=1e-12, atol=1e-12)
     Vg = host(V).T                                   # columns = eigenvectors
     assert np.abs(A @ Vg - Vg * wv).max() < 1e-11 * wo[0]
+    assert m < 2 or w.wc4d_jacobi_sweeps(S.ctx) >= 1
+
+
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
+def test_mixed_sketch_eigensolve_stops_early(method):
+    """The small eigensolve of a mixed sketch stops after the sweep that
+    brings the columns within |cos| <= 1e-5; the FP64 sketch runs to a sweep
+    without rotations.  Both orderings converge quadratically, so the mixed
+    one uses no more sweeps, and its Ritz values still agree to ~1e-5."""
+    cfg, S, _, _ = setup("ad_fft")
+    m = cfg.k + cfg.l
+    w.wc4d_sketch(S.ctx, w.METHODS[method], cfg.k, cfg.l, cfg.q_power, 23, None, w.FP64)
+    s64 = w.wc4d_jacobi_sweeps(S.ctx)
+    U = torch.zeros(cfg.k, cfg.nA, dtype=torch.float64, device="cuda")
+    th64 = w.wc4d_get_ritz(S.ctx, U, cfg.k)
+    w.wc4d_sketch(S.ctx, w.METHODS[method], cfg.k, cfg.l, cfg.q_power, 23, None, w.MIXED)
+    s32 = w.wc4d_jacobi_sweeps(S.ctx)
+    th32 = w.wc4d_get_ritz(S.ctx, U, cfg.k)
+    assert 1 <= s32 <= s64 <= 60
+    assert np.allclose(th32, th64, rtol=1e-3)
+    Ug = host(U)
+    assert np.abs(Ug @ Ug.T - np.eye(cfg.k)).max() < 1e-4
 
 
 # ------------------------------------------------------------------ eigensolvers
