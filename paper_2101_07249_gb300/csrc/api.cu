@@ -1245,7 +1245,7 @@ static wc4d_status lmp_cg_step(wc4d_ctx *c, T *x, T *r, T *rh, const T *p, const
 {
     const int64_t nA = c->nA;
     const int kp = c->kp;
-    const int S = lmp_pass_a_splits(nA, c->num_sms), G = lmp_pass_b_grid(nA);
+    const int S = lmp_pass_a_splits(nA, c->num_sms), G = std::max(S, lmp_pass_b_grid(nA));   // second-pass CTAs
     WC4D_TRY(ensure(c, c->part, sizeof(double) * ((size_t)S * (2 * kp + 1))));
     WC4D_TRY(ensure(c, c->small2, sizeof(double) * (4 * (size_t)kp + 1 + 2 * (size_t)G)));
     double *w = P<double>(c->small2), *partB = w + 4 * kp + 1;

@@ -59,9 +59,10 @@ struct JqArgs {
 
 __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
 {
-    __shared__ double red[3][JQ_THREADS / 32];
-    __shared__ double cs[2];
-    __shared__ int doit_s, conv_s;
+    __shared__ double prod[2][3][JQ_THREADS];      // double-buffered by round parity
+    __shared__ double red[2][3];
+    __shared__ double cs[2][2];
+    __shared__ int doit_s[2], conv_s;
     const int P = a.P, pair = blockIdx.x, r = threadIdx.x;
     const unsigned G = gridDim.x;
     const int64_t PP = (int64_t)P * P;
@@ -86,6 +87,8 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
     int sweeps = 0;
     bool converged = false;
     for (; sweeps < a.max_sweeps && !converged; ++sweeps) {
+        int nrot = 0;       // rotations and largest rotation measure of this CTA in this sweep (thread 0)
+        double mmax = 0.0;
         for (int round = 0; round < P - 1; ++round) {
             const int pos_b = P - 1 - pair;
             const int ja = pair == 0 ? 0 : 1 + (pair - 1 + round) % (P - 1);
@@ -100,18 +103,29 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
                     z = __ldcg(Vc + (int64_t)q * P + r);
                 }
             }
-            double s0 = u * u, s1 = w * w, s2 = u * w;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            }
-            if (lane == 0) { red[0][warp] = s0; red[1][warp] = s1; red[2][warp] = s2; }
+            // The FP64 pipe retires about 1.6 operations per clock per SM, so
+            // the three sums are not reduced by a butterfly over all 256
+            // threads (15 FP64 additions each): the products go to shared
+            // memory and warp v (v < 3) adds the 256 values of sum v (8
+            // per lane, then 5 shuffle levels), a third of the FP64 work.
+            const int par = round & 1;
+            prod[par][0][r] = u * u;
+            prod[par][1][r] = w * w;
+            prod[par][2][r] = u * w;
             __syncthreads();
+            if (warp < 3) {
+                double acc = 0.0;
+#pragma unroll
+                for (int i = lane; i < JQ_THREADS; i += 32) acc += prod[par][warp][i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) red[par][warp] = acc;
+            }
+            __syncthreads();
+            // thread 0 alone forms the rotation (256 redundant copies of this
+            // scalar FP64 work would cost more than the broadcast)
             if (threadIdx.x == 0) {
-                double aa = 0.0, bb = 0.0, g = 0.0;
-                for (int i = 0; i < JQ_THREADS / 32; ++i) { aa += red[0][i]; bb += red[1][i]; g += red[2][i]; }
+                const double aa = red[par][0], bb = red[par][1], g = red[par][2];
                 int doit = 0;
                 // |g| > tol sqrt(a b), squared: no FP64 square root or division
                 if (g * g > a.tol * a.tol * (aa * bb) && fabs(g) > 1e-300) {
@@ -133,19 +147,19 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
                     double c = (double)rsqrtf((float)h);
                     c = c * fma(-0.5 * h, c * c, 1.5);
                     c = c * fma(-0.5 * h, c * c, 1.5);
-                    cs[0] = c;
-                    cs[1] = c * tn;
+                    cs[par][0] = c;
+                    cs[par][1] = c * tn;
                     doit = 1;
-                    atomicAdd(a.rot + sweeps, 1);
-                    if (a.stop2 > 0.0)   // non-negative doubles order as their bit patterns
-                        atomicMax(a.maxm + sweeps, (unsigned long long)__double_as_longlong((g * g) / (aa * bb)));
+                    ++nrot;
+                    if (a.stop2 > 0.0) mmax = fmax(mmax, (g * g) / (aa * bb));
                 }
-                doit_s = doit;
+                doit_s[par] = doit;
             }
             __syncthreads();
+            const bool doit = doit_s[par] != 0;
+            const double c = cs[par][0], sn = cs[par][1];
             if (r < P) {
-                if (doit_s) {
-                    const double c = cs[0], sn = cs[1];
+                if (doit) {
                     Xn[(int64_t)p * P + r] = c * u - sn * w;
                     Xn[(int64_t)q * P + r] = sn * u + c * w;
                     if (wv) {
@@ -160,6 +174,11 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
                         Vn[(int64_t)q * P + r] = z;
                     }
                 }
+            }
+            if (round == P - 2 && threadIdx.x == 0) {   // this CTA's counts, before the sweep's last barrier
+                if (nrot) atomicAdd(a.rot + sweeps, nrot);
+                if (a.stop2 > 0.0 && mmax > 0.0)   // non-negative doubles order as their bit patterns
+                    atomicMax(a.maxm + sweeps, (unsigned long long)__double_as_longlong(mmax));
             }
             target += G;
             if (!jq_barrier(a.bar, target, a.err)) return;

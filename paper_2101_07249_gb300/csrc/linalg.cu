@@ -1,6 +1,8 @@
 // Dense linear algebra of the randomised eigensolvers and the LMP / PCG
 // vector kernels.  Reductions are two-stage (fixed partial layout, then a
 // single-CTA sum) so that results are bitwise reproducible run to run.
+#include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "wc4d_internal.cuh"
@@ -775,6 +777,16 @@ __device__ __forceinline__ Quad<double> ld4cs(const double *p)
     double2 a = __ldcs(reinterpret_cast<const double2 *>(p)), b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
     return {a.x, a.y, b.x, b.y};
 }
+__device__ __forceinline__ Quad<float> ld4cg(const float *p)
+{
+    float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> ld4cg(const double *p)
+{
+    double2 a = __ldcg(reinterpret_cast<const double2 *>(p)), b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
 
 // part[chunk][i] = sum over the chunk's rows of Urm[r, i] v[r].  Thread
 // (ty, tx): column group 4 (cb + tx) .. + 3, rows ty, ty + 4, ...; the loop
@@ -902,6 +914,7 @@ template void launch_lmp_combine_rm<float>(cudaStream_t, int, int64_t, int, int,
 //            partial sums of |rhat|^2 and |r|^2 for the beta kernel.
 // ----------------------------------------------------------------------------
 constexpr int PA_ROWS = 512;   // rows per CTA of pass A (at most)
+constexpr double LMP_L2_KEEP = 64.0 * 1024 * 1024;   // Ritz-vector bytes the first pass leaves in L2
 
 int lmp_pass_a_splits(int64_t nA, int num_sms)
 {
@@ -912,7 +925,7 @@ int lmp_pass_a_splits(int64_t nA, int num_sms)
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_lmp_pass_a(int64_t nA, int kp, int64_t rows_per, const T *__restrict__ Urm,
                                                     const T *__restrict__ q, const T *__restrict__ rh,
-                                                    const T *__restrict__ p, double *part)
+                                                    const T *__restrict__ p, double *part, int keep_from)
 {
     __shared__ T qs[PA_ROWS], es[PA_ROWS];
     __shared__ double acc[4][2][256];
@@ -940,8 +953,15 @@ __global__ void __launch_bounds__(256, 4) k_lmp_pass_a(int64_t nA, int kp, int64
             int r = ty;
             for (; r + 12 < rows; r += 16) {   // four rows of loads in flight per thread
                 Quad<T> u[4];
+                // rows from keep_from on stay in L2 for the second pass,
+                // which reads each CTA's rows from the end backwards
+                if (r >= keep_from) {
 #pragma unroll
-                for (int h = 0; h < 4; ++h) u[h] = ld4cs(base + (int64_t)(r + 4 * h) * kp);
+                    for (int h = 0; h < 4; ++h) u[h] = ld4cg(base + (int64_t)(r + 4 * h) * kp);
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) u[h] = ld4cs(base + (int64_t)(r + 4 * h) * kp);
+                }
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const T x = qs[r + 4 * h], y = es[r + 4 * h];
@@ -950,7 +970,7 @@ __global__ void __launch_bounds__(256, 4) k_lmp_pass_a(int64_t nA, int kp, int64
                 }
             }
             for (; r < rows; r += 4) {
-                Quad<T> u = ld4cs(base + (int64_t)r * kp);
+                Quad<T> u = ld4cg(base + (int64_t)r * kp);
                 const T x = qs[r], y = es[r];
                 a0 = fma(u.x, x, a0); a1 = fma(u.y, x, a1); a2 = fma(u.z, x, a2); a3 = fma(u.w, x, a3);
                 b0 = fma(u.x, y, b0); b1 = fma(u.y, y, b1); b2 = fma(u.z, y, b2); b3 = fma(u.w, y, b3);
@@ -1161,6 +1181,146 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, c
     }
 }
 
+// Second pass over the ROW-MAJOR Ritz vectors with the first pass's split
+// (CTA b: rows [b R, b R + R), R <= PA_ROWS), each CTA walking its rows from
+// the end backwards so that the rows the first pass read last -- still in L2
+// -- come first.  Phase 1: a warp takes LB consecutive rows at a time; lane l
+// reads column quads l and l + 32 of every row (kp / 4 <= 64), forms the
+// 2 LB partial sums (U w1, U w2 for each row), and a halving butterfly over
+// the lanes leaves each sum in two lanes (2 LB + 4 - log2(2 LB) shuffles
+// instead of 10 per row); the sums go to shared memory.  Phase 2: the CTA
+// updates its rows with coalesced vector accesses, as the column-major pass
+// does, and the last CTA takes the CG beta step.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lmp_pass_b_rm(int64_t nA, int kp, int64_t rows_per, const T *__restrict__ U,
+                                                       const double *__restrict__ w, const double *__restrict__ scal,
+                                                       const T *__restrict__ q, const T *__restrict__ p, T *rh, T *t,
+                                                       T *x, T *r, double *part, double *scal_rw, int *flags,
+                                                       unsigned *done, double tol, double *qcf_drop, int it)
+{
+    constexpr int LB = sizeof(T) == 4 ? 8 : 4;   // rows per warp step
+    constexpr int NV = 2 * LB;                    // sums per warp step
+    __shared__ T dsum[2][PA_ROWS];
+    __shared__ int last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kq = kp / 4;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    const int rows = (int)max((int64_t)0, min(rows_per, nA - r0));
+    // this lane's column quads and coefficients
+    const int c0 = lane, c1 = lane + 32;
+    const bool h0 = c0 < kq, h1 = c1 < kq;
+    Quad<T> w10{0, 0, 0, 0}, w20{0, 0, 0, 0}, w11{0, 0, 0, 0}, w21{0, 0, 0, 0};
+    if (h0) {
+        w10 = {(T)w[4 * c0], (T)w[4 * c0 + 1], (T)w[4 * c0 + 2], (T)w[4 * c0 + 3]};
+        w20 = {(T)w[kp + 4 * c0], (T)w[kp + 4 * c0 + 1], (T)w[kp + 4 * c0 + 2], (T)w[kp + 4 * c0 + 3]};
+    }
+    if (h1) {
+        w11 = {(T)w[4 * c1], (T)w[4 * c1 + 1], (T)w[4 * c1 + 2], (T)w[4 * c1 + 3]};
+        w21 = {(T)w[kp + 4 * c1], (T)w[kp + 4 * c1 + 1], (T)w[kp + 4 * c1 + 2], (T)w[kp + 4 * c1 + 3]};
+    }
+    const int nchunks = (rows + LB - 1) / LB;
+    for (int ci = warp; ci < nchunks; ci += 8) {
+        const int hi = rows - ci * LB;           // rows [lo, hi) of the range, walked from the end
+        const int lo = max(0, hi - LB);
+        T v[NV];
+        Quad<T> u0[LB], u1[LB];
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            const bool ok = lo + i < hi;
+            const T *row = U + (r0 + lo + i) * kp;
+            u0[i] = (ok && h0) ? ld4cs(row + 4 * c0) : Quad<T>{0, 0, 0, 0};
+            u1[i] = (ok && h1) ? ld4cs(row + 4 * c1) : Quad<T>{0, 0, 0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            T a = u0[i].x * w10.x, b = u0[i].x * w20.x;
+            a = fma(u0[i].y, w10.y, a); b = fma(u0[i].y, w20.y, b);
+            a = fma(u0[i].z, w10.z, a); b = fma(u0[i].z, w20.z, b);
+            a = fma(u0[i].w, w10.w, a); b = fma(u0[i].w, w20.w, b);
+            a = fma(u1[i].x, w11.x, a); b = fma(u1[i].x, w21.x, b);
+            a = fma(u1[i].y, w11.y, a); b = fma(u1[i].y, w21.y, b);
+            a = fma(u1[i].z, w11.z, a); b = fma(u1[i].z, w21.z, b);
+            a = fma(u1[i].w, w11.w, a); b = fma(u1[i].w, w21.w, b);
+            v[2 * i] = a;
+            v[2 * i + 1] = b;
+        }
+        // halving butterfly: afterwards lane l holds sum number
+        // sum over halving steps of (l & off ? h : 0)
+        int off = 16;
+#pragma unroll
+        for (int h = NV / 2; h >= 1; h >>= 1, off >>= 1) {
+            const bool upper = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const T send = upper ? v[i] : v[i + h];
+                const T keep = upper ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+        for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+        if ((lane & (32 / NV - 1)) == 0) {
+            int idx = 0, o = 16;
+#pragma unroll
+            for (int h = NV / 2; h >= 1; h >>= 1, o >>= 1)
+                if (lane & o) idx += h;
+            const int i = idx >> 1;   // row lo + i, sum idx & 1
+            if (lo + i < hi) dsum[idx & 1][lo + i] = v[0];
+        }
+    }
+    __syncthreads();
+    const double alpha = scal[1];
+    double srh = 0.0, sr = 0.0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const int64_t row = r0 + i;
+        const double qv = (double)q[row];
+        const double rhn = (double)rh[row] - alpha * qv + (double)dsum[0][i];
+        rh[row] = (T)rhn;
+        t[row] = (T)(rhn - (double)dsum[1][i]);
+        x[row] = (T)((double)x[row] + alpha * (double)p[row]);
+        const double rn = (double)r[row] - alpha * qv;
+        r[row] = (T)rn;
+        srh += rhn * rhn;
+        sr += rn * rn;
+    }
+    srh = block_sum(srh);
+    sr = block_sum(sr);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = srh;
+        part[gridDim.x + blockIdx.x] = sr;
+        __threadfence();
+        last = (atomicAdd(done, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last CTA: beta, rho, relative residual, QCF decrease and the done
+    // flag from all partial sums (fixed order), as the CG beta step
+    __threadfence();
+    double t1 = 0.0, t2 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        t1 += __ldcg(part + i);
+        t2 += __ldcg(part + gridDim.x + i);
+    }
+    const double rho_new = block_sum(t1);
+    const double rr = block_sum(t2);
+    if (threadIdx.x == 0) {
+        *done = 0u;
+        if (flags[F_DONE]) {
+            scal_rw[S_BETA] = 0.0;
+            return;
+        }
+        const double rho = scal_rw[S_RHO];
+        scal_rw[S_BETA] = rho_new / rho;
+        if (qcf_drop) qcf_drop[it] = 0.5 * scal_rw[S_ALPHA] * rho;
+        scal_rw[S_RHO] = rho_new;
+        scal_rw[S_RR] = rr;
+        const double rel = sqrt(rr) / scal_rw[S_BNORM];
+        scal_rw[S_RELRES] = rel;
+        flags[F_ITER] += 1;
+        if (!isfinite(rel)) { flags[F_BREAK] = 2; flags[F_DONE] = 1; }
+        else if (tol > 0.0 && rel <= tol) flags[F_DONE] = 1;
+    }
+}
+
 int lmp_pass_b_grid(int64_t nA) { return ceil_div(nA, PB_ROWS); }
 
 template <typename T>
@@ -1170,9 +1330,21 @@ void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, co
 {
     const int S = lmp_pass_a_splits(nA, num_sms);
     const int64_t rows_per = (nA + S - 1) / S;
-    WC4D_LAUNCH(k_lmp_pass_a<T><<<S, 256, 0, s>>>(nA, kp, rows_per, Urm, q, rh, p, partA));
+    // Row-major second pass (kp / 4 <= 64): the first pass leaves the last
+    // part of every CTA's rows in L2 -- at most LMP_L2_KEEP bytes in all --
+    // and the second pass reads those first.
+    const bool rm = kp / 4 <= 64;
+    const double ubytes = (double)nA * kp * sizeof(T);
+    const double keep = rm ? std::min(1.0, LMP_L2_KEEP / ubytes) : 0.0;
+    const int keep_from = (int)((double)rows_per * (1.0 - keep));
+    WC4D_LAUNCH(k_lmp_pass_a<T><<<S, 256, 0, s>>>(nA, kp, rows_per, Urm, q, rh, p, partA, rm ? keep_from : INT_MAX));
     double *sums = w + 2 * kp;
     WC4D_LAUNCH(k_lmp_coef<<<ceil_div(2 * kp + 1, 8), 256, 0, s>>>(S, k, kp, partA, cvec, scal, flags, sums, w, done));
+    if (rm) {
+        WC4D_LAUNCH(k_lmp_pass_b_rm<T><<<S, 256, 0, s>>>(nA, kp, rows_per, Urm, w, scal, q, p, rh, t, x, r, partB, scal,
+                                                         flags, done + 1, tol, qcf_drop, it));
+        return;
+    }
     const int G = lmp_pass_b_grid(nA);
     const size_t smem = (2 * (size_t)kp + 2 * PB_CHUNKS * PB_ROWS) * sizeof(T);
     WC4D_LAUNCH(k_lmp_pass_b<T><<<G, 256, smem, s>>>(nA, k, kp, Ucm, w, scal, q, p, rh, t, x, r, partB, scal, flags,

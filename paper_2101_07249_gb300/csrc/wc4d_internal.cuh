@@ -269,11 +269,14 @@ void launch_pcg_rh(cudaStream_t s, int grid, int64_t n, const double *scal, T *r
 template <typename T>
 void launch_pcg_p(cudaStream_t s, int grid, int64_t n, const double *scal, T *p, const T *t);
 void launch_pcg_alpha(cudaStream_t s, int grid, const double *part, double *scal, int *flags);
-// One fused split-preconditioned CG iteration after q = A p (one pass over
-// the row-major Ritz vectors Urm, one over the column-major copy Ucm, ld nA):
+// One fused split-preconditioned CG iteration after q = A p (two passes
+// over the row-major Ritz vectors Urm, the second from the end of each CTA's
+// rows so that it starts on rows still in L2; for kp > 256 the second pass
+// reads the column-major copy Ucm, ld nA):
 // alpha in scal[1], rhat, t = C rhat, x, r updated, then (last CTA of the
 // second pass) the CG beta step: beta, rho, relative residual, QCF decrease,
-// flags.  partB: 2 lmp_pass_b_grid(nA) doubles of partial sums; partA:
+// flags.  partB: 2 max(lmp_pass_b_grid(nA), lmp_pass_a_splits(nA, num_sms))
+// doubles of partial sums; partA:
 // lmp_pass_a_splits(nA, num_sms) x (2 kp + 1) doubles; w: 4 kp + 1 doubles;
 // done: two counters that are zero on entry (and are left at zero).
 int lmp_pass_a_splits(int64_t nA, int num_sms);
