@@ -747,7 +747,8 @@ extern "C" wc4d_status wc4d_gaussian(wc4d_ctx *c, uint64_t seed, int64_t rows, i
 // ============================================================================
 // Y (rows x m, ld) <- Y R^{-1} with Y = Z R; Rout (m x m, device FP64) = R.
 template <typename T>
-static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t ld, T *tmp, double *R)
+static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t ld, T *tmp, double *R,
+                               bool *shifted = nullptr)
 {
     const size_t mm = (size_t)m * m;
     WC4D_TRY(ensure(c, c->small0, sizeof(double) * mm));
@@ -756,6 +757,11 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     WC4D_TRY(ensure(c, c->part, sizeof(double) * part_need));
     int S = 0;
     double *G = P<double>(c->small0);
+    unsigned *rs_work = reinterpret_cast<unsigned *>(P<int>(c->counter) + 12);   // counter words 12, 13
+    if constexpr (sizeof(T) == 4) {
+        ProfScope ps(c, PROF_GRAM);
+        launch_range_scale_f32(c->stream, c->num_sms, rows, m, ld, Y, rs_work);
+    }
     {
         ProfScope ps(c, PROF_GRAM);
         if (launch_atb<T>(c->stream, c->num_sms, rows, m, m, Y, ld, Y, ld, P<double>(c->part), c->part.bytes / 8,
@@ -772,6 +778,25 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
         WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     }
     WC4D_TRY(sync(c, "cholqr info"));
+    // Numerically rank-deficient Y (the Gram is accurate to FP64 rounding,
+    // so this happens when its condition exceeds ~1e16, e.g. sketches of a
+    // Hessian whose eigenvalues span 1e17): shifted CholeskyQR -- factor
+    // G + s I with s = f trace(G), f from m 2^-52 up by factors of 100.  Y
+    // R^{-1} is then well conditioned but not orthonormal; the caller runs
+    // one more pass (shifted CholeskyQR3).  Y = (Y R^{-1}) R holds exactly
+    // whatever the shift.
+    for (double f = m * 0x1p-52; info != 0 && shifted && f < 1e-4; f *= 100.0) {
+        *shifted = true;
+        {
+            ProfScope psc(c, PROF_CHOL);
+            launch_shift_diag(c->stream, m, G, f);
+            launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));
+            launch_trinv_upper(c->stream, m, R, Rinv);
+            WC4D_TRY(check_launch(c, "shifted cholqr"));
+            WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        }
+        WC4D_TRY(sync(c, "shifted cholqr info"));
+    }
     if (info != 0) return set_err(c, WC4D_ENOTSPD, "CholeskyQR: Gram matrix not positive definite at pivot %d", info);
     ProfScope psl(c, PROF_LA);
     Epi e{0, 1.0, 0.0, 0.0, 1};
@@ -785,6 +810,7 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     WC4D_TRY(check_launch(c, "cholqr gemm"));
     WC4D_CUDA(c, cudaMemcpy2DAsync(Y, sizeof(T) * ld, tmp, sizeof(T) * rows, sizeof(T) * rows, m,
                                    cudaMemcpyDeviceToDevice, c->stream));
+    if constexpr (sizeof(T) == 4) launch_unscale_R(c->stream, m, R, rs_work);   // R of the unscaled Y
     return WC4D_OK;
 }
 
@@ -793,13 +819,21 @@ template <typename T>
 static wc4d_status cholqr2(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t ld, T *tmp, double *R)
 {
     const size_t mm = (size_t)m * m;
-    WC4D_TRY(ensure(c, c->small2, sizeof(double) * mm * 2));
-    double *R1 = P<double>(c->small2), *R2 = R1 + mm;
-    WC4D_TRY(cholqr_pass<T>(c, Y, rows, m, ld, tmp, R1));
-    WC4D_TRY(cholqr_pass<T>(c, Y, rows, m, ld, tmp, R2));
+    WC4D_TRY(ensure(c, c->small2, sizeof(double) * mm * 3));
+    double *R1 = P<double>(c->small2), *R2 = R1 + mm, *R3 = R2 + mm;
+    bool shifted = false;
+    WC4D_TRY(cholqr_pass<T>(c, Y, rows, m, ld, tmp, R1, &shifted));
+    WC4D_TRY(cholqr_pass<T>(c, Y, rows, m, ld, tmp, R2, &shifted));
+    if (shifted) WC4D_TRY(cholqr_pass<T>(c, Y, rows, m, ld, tmp, R3));   // shifted CholeskyQR3
     if (R) {
         Epi e{0, 1.0, 0.0, 0.0, 1};
-        launch_gemm<double>(c->stream, m, m, m, R2, 1, m, R1, m, R, m, e);   // R = R2 R1
+        if (shifted) {   // R = R3 R2 R1
+            launch_gemm<double>(c->stream, m, m, m, R3, 1, m, R2, m, R, m, e);
+            launch_gemm<double>(c->stream, m, m, m, R, 1, m, R1, m, R3, m, e);
+            WC4D_CUDA(c, cudaMemcpyAsync(R, R3, sizeof(double) * mm, cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            launch_gemm<double>(c->stream, m, m, m, R2, 1, m, R1, m, R, m, e);   // R = R2 R1
+        }
         WC4D_TRY(check_launch(c, "R2R1"));
     }
     return WC4D_OK;
@@ -1007,7 +1041,9 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         // CholeskyQR pass; the basis used for Rayleigh-Ritz gets two.
         if (method == WC4D_REVD && q > 0) {
             WC4D_TRY(ensure(c, c->small2, sizeof(double) * mm));
-            if ((st = cholqr_pass<T>(c, B_, nA, m, nA, D_, P<double>(c->small2))) != WC4D_OK) return fail(st);
+            bool shifted = false;   // a well-conditioned basis suffices here
+            if ((st = cholqr_pass<T>(c, B_, nA, m, nA, D_, P<double>(c->small2), &shifted)) != WC4D_OK)
+                return fail(st);
         } else if ((st = cholqr2<T>(c, B_, nA, m, nA, D_, nullptr)) != WC4D_OK) {
             return fail(st);
         }

@@ -416,6 +416,80 @@ void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *i
     }
 }
 
+// Power-of-two range scaling of an FP32 block before its Gram matrix: the
+// double-float Gram accumulates in FP32 pairs, which overflow once the
+// squared column norms pass ~3e38 (sketches of Hessians with eigenvalues
+// ~1e19).  k_absmax_f32 takes max |Y| (as ordered bits of a non-negative
+// float); k_scale_pow2 then multiplies Y by 2^-e (exact) when max |Y| lies
+// outside [2^-24, 2^24] and records e; k_scale_R_pow2 multiplies R by 2^e, so
+// that (2^-e Y)(2^-e R)^{-1} = Y R^{-1}.
+__global__ void __launch_bounds__(256) k_absmax_f32(int64_t rows, int m, int64_t ld, const float *Y, unsigned *mx)
+{
+    float v = 0.f;
+    const int64_t tot = rows * m;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / rows, r = i - j * rows;
+        v = fmaxf(v, fabsf(Y[j * ld + r]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, __float_as_uint(v));
+}
+
+__global__ void __launch_bounds__(256) k_scale_pow2(int64_t rows, int m, int64_t ld, float *Y, const unsigned *mx,
+                                                    int *e_out)
+{
+    const float v = __uint_as_float(*mx);
+    int e = 0;
+    if (v > 0.f && isfinite(v) && (v > 0x1p24f || v < 0x1p-24f)) e = ilogbf(v);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *e_out = e;
+    if (e == 0) return;
+    const float sc = scalbnf(1.f, -e);
+    const int64_t tot = rows * m;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / rows, r = i - j * rows;
+        Y[j * ld + r] *= sc;
+    }
+}
+
+__global__ void k_scale_R_pow2(int m, double *R, const int *e)
+{
+    if (*e == 0) return;
+    const double sc = scalbn(1.0, *e);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)m * m; i += (int64_t)gridDim.x * blockDim.x)
+        R[i] *= sc;
+}
+
+// work: 2 words of device scratch (max bits, exponent)
+void launch_range_scale_f32(cudaStream_t s, int num_sms, int64_t rows, int m, int64_t ld, float *Y, unsigned *work)
+{
+    cudaMemsetAsync(work, 0, sizeof(unsigned), s);
+    const int grid = 4 * num_sms;
+    WC4D_LAUNCH(k_absmax_f32<<<grid, 256, 0, s>>>(rows, m, ld, Y, work));
+    WC4D_LAUNCH(k_scale_pow2<<<grid, 256, 0, s>>>(rows, m, ld, Y, work, reinterpret_cast<int *>(work + 1)));
+}
+
+void launch_unscale_R(cudaStream_t s, int m, double *R, const unsigned *work)
+{
+    WC4D_LAUNCH(k_scale_R_pow2<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(m, R, reinterpret_cast<const int *>(work + 1)));
+}
+
+// A[i][i] += factor * trace(A) for the m x m column-major A (one CTA): the
+// shift of shifted CholeskyQR, after the unshifted factorisation failed.
+__global__ void __launch_bounds__(256) k_shift_diag(int m, double *A, double factor)
+{
+    double tr = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tr += A[(int64_t)i * m + i];
+    tr = block_sum(tr);
+    const double sft = factor * tr;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) A[(int64_t)i * m + i] += sft;
+}
+
+void launch_shift_diag(cudaStream_t s, int m, double *A, double factor)
+{
+    WC4D_LAUNCH(k_shift_diag<<<1, 256, 0, s>>>(m, A, factor));
+}
+
 // Inverse of an upper-triangular R (column-major): one CTA per column j,
 // column-oriented back substitution of R x = e_j in shared memory.
 __global__ void __launch_bounds__(256) k_trinv_upper(int m, const double *R, double *Rinv)

@@ -222,6 +222,11 @@ template <typename T>
 int launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
                int64_t ldb, double *part, size_t part_capacity, int *splits_out, double *C, int upper);
 void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *info);
+void launch_shift_diag(cudaStream_t s, int m, double *A, double factor);   // A_ii += factor * trace(A)
+// Y (FP32, rows x m, ld) *= 2^-e when max |Y| is outside [2^-24, 2^24] (e kept
+// in work[1]); launch_unscale_R: R *= 2^e.  work: 2 device words.
+void launch_range_scale_f32(cudaStream_t s, int num_sms, int64_t rows, int m, int64_t ld, float *Y, unsigned *work);
+void launch_unscale_R(cudaStream_t s, int m, double *R, const unsigned *work);
 void launch_trinv_upper(cudaStream_t s, int m, const double *R, double *Rinv);
 void launch_jacobi_init(cudaStream_t s, int m, int mp, const double *S, double *X, double *V);
 void launch_jacobi_round(cudaStream_t s, int mp, double *X, double *V, int round, double tol, int *rot);

@@ -171,6 +171,29 @@ def test_cholqr2_fp32_ill_conditioned(m):
     assert np.all(np.diag(R) > 0)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_shifted_cholqr3_numerically_rank_deficient(precision):
+    """A block whose singular values span 1e10 (FP32 data) or 1e15 (FP64):
+    the Gram matrix is numerically singular (condition beyond 1e16), the
+    unshifted Cholesky breaks down, and the shifted pass plus two more
+    (shifted CholeskyQR3) still return orthonormal columns with Y = Z R."""
+    cfg, S, _, _ = setup("ad_direct")
+    rows, m = 8000, 48
+    g = np.random.default_rng(7)
+    Q1, _ = np.linalg.qr(g.standard_normal((rows, m)))
+    V, _ = np.linalg.qr(g.standard_normal((m, m)))
+    span = -10 if precision == "mixed" else -15
+    A = (Q1 * np.logspace(0, span, m)) @ V.T
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    A_in = A.astype(np.float32).astype(np.float64) if precision == "mixed" else A
+    Y = torch.tensor(A_in.T.copy(), dtype=dt, device="cuda")
+    R = w.wc4d_orthonormalize(S.ctx, Y, rows, m, rows, precision=w.MIXED if precision == "mixed" else w.FP64)
+    Z = host(Y).T
+    ortho, recon = (1e-4, 1e-5) if precision == "mixed" else (1e-11, 1e-12)
+    assert np.abs(Z.T @ Z - np.eye(m)).max() < ortho
+    assert np.linalg.norm(A_in - Z @ R) / np.linalg.norm(A_in) < recon
+
+
 @pytest.mark.parametrize("m", [1, 2, 15, 40, 77])
 def test_symeig_matches_jacobi(m):
     cfg, S, _, _ = setup("ad_direct")
