@@ -289,6 +289,18 @@ int64_t     wc4d_hvp_count(wc4d_ctx *ctx, int32_t reset);
    to convergence; -1 for a null context.  In a mixed-precision sketch the
    solve stops after a sweep whose largest rotation had |cos| <= 1e-5. */
 int32_t     wc4d_jacobi_sweeps(const wc4d_ctx *ctx);
+/* CUDA-graph replay of the CG iteration (default on): after one eager
+   iteration, the body of Alg. 1's loop (the product with A, the LMP step and
+   the direction update) is captured once per solve and replayed; the
+   results are bitwise those of the eager launches.  enable = 0 keeps every
+   iteration eager.  EINVAL for a null context. */
+wc4d_status wc4d_set_graphs(wc4d_ctx *ctx, int32_t enable);
+/* Autotuned tile shapes of the SIMT propagator GEMMs (process-wide, default
+   on): the first product of a shape times every candidate tile (scratch
+   output) and keeps the fastest.  wc4d_autotune_choice returns the tile index
+   chosen for (fp64, rows, cols, kdim), or -1 if that shape was not tuned. */
+void        wc4d_set_autotune(int32_t enable);
+int32_t     wc4d_autotune_choice(int32_t fp64, int32_t rows, int32_t cols, int32_t kdim);
 
 #ifdef __cplusplus
 }

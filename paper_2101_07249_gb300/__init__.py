@@ -79,6 +79,9 @@ _SIGS = {
     "wc4d_symeig": (C.c_int, [_V, C.c_int32, _V, _D, _V]),
     "wc4d_hvp_count": (C.c_int64, [_V, C.c_int32]),
     "wc4d_jacobi_sweeps": (C.c_int32, [_V]),
+    "wc4d_set_graphs": (C.c_int32, [_V, C.c_int32]),
+    "wc4d_set_autotune": (None, [C.c_int32]),
+    "wc4d_autotune_choice": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "wc4d_apply_dsqrt": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_apply_linv": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_apply_linvT": (C.c_int, [_V, _V, C.c_int32, C.c_int64, C.c_int32]),
@@ -358,6 +361,18 @@ def wc4d_hvp_count(ctx, reset=False):
 
 def wc4d_jacobi_sweeps(ctx):
     return int(load().wc4d_jacobi_sweeps(ctx))
+
+
+def wc4d_set_graphs(ctx, enable):
+    _check(ctx, load().wc4d_set_graphs(ctx, 1 if enable else 0))
+
+
+def wc4d_set_autotune(enable):
+    load().wc4d_set_autotune(1 if enable else 0)
+
+
+def wc4d_autotune_choice(fp64, rows, cols, kdim):
+    return int(load().wc4d_autotune_choice(1 if fp64 else 0, int(rows), int(cols), int(kdim)))
 
 
 # --------------------------------------------------------------------------

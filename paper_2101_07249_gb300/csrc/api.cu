@@ -76,7 +76,80 @@ wc4d_status check_launch(wc4d_ctx *c, const char *what)
 }
 
 static std::atomic<int64_t> g_launches{0};
-void wc4d_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local int64_t tl_launches = 0;   // launches issued by this host thread (graph capture counts)
+void wc4d_note_launch()
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++tl_launches;
+}
+
+// ----------------------------------------------------------------------------
+// One CG iteration body (the Hessian product, the LMP step and the p update,
+// or the unpreconditioned vector kernels) as a CUDA graph.  The first
+// iteration of a solve runs eagerly (every workspace then exists and every
+// one-time function attribute is set); the second is captured on the
+// context's stream (thread-local capture mode, so other host threads driving
+// other contexts are unaffected), instantiated and launched; the rest of the
+// solve replays it, one graph launch instead of ~10 (or, when the sweeps run
+// per subwindow, 2 N + 10) kernel launches per iteration.  The body's
+// arguments are fixed for the whole solve (the QCF slot comes from the
+// device iteration counter).  Anything the capture cannot take -- a
+// cooperative launch on a driver that refuses it, an allocation -- makes the
+// capture fail; the iteration then runs eagerly and the solve stays eager.
+// Not used while kernel-class profiling is on (its events are host-driven).
+// ----------------------------------------------------------------------------
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;    // kernels per replay
+    int64_t hvps = 0;        // products with A per replay
+    bool failed = false;
+    IterGraph() = default;
+    IterGraph(const IterGraph &) = delete;
+    IterGraph &operator=(const IterGraph &) = delete;
+    ~IterGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+template <typename F> static wc4d_status run_iteration(wc4d_ctx *c, IterGraph &g, int it, F body)
+{
+    if (g.exec) {
+        if (cudaGraphLaunch(g.exec, c->stream) != cudaSuccess) return check_launch(c, "CG iteration graph");
+        g_launches.fetch_add(g.launches, std::memory_order_relaxed);
+        tl_launches += g.launches;
+        c->hvp_count += g.hvps;
+        return WC4D_OK;
+    }
+    if (it == 0 || g.failed || c->prof_on || !c->use_graphs) return body();
+    const int64_t l0 = tl_launches, h0 = c->hvp_count;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        g.failed = true;
+        return body();
+    }
+    const wc4d_status st = body();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+    const int64_t nl = tl_launches - l0, nh = c->hvp_count - h0;
+    // the captured kernels have not run: take them off the counters
+    g_launches.fetch_sub(nl, std::memory_order_relaxed);
+    tl_launches -= nl;
+    c->hvp_count = h0;
+    if (st != WC4D_OK || ec != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        g.exec = nullptr;
+        cudaGetLastError();
+        g.failed = true;
+        c->err.clear();
+        return body();   // run this iteration eagerly, and the rest of the solve too
+    }
+    cudaGraphDestroy(graph);
+    g.launches = nl;
+    g.hvps = nh;
+    return run_iteration(c, g, it, body);   // first replay
+}
 
 ProfScope::ProfScope(wc4d_ctx *ctx, int pid) : c(ctx), id(pid), slot(-1)
 {
@@ -276,6 +349,13 @@ extern "C" wc4d_status wc4d_profile_read(wc4d_ctx *c, int32_t cls, double *total
 }
 
 extern "C" int32_t wc4d_jacobi_sweeps(const wc4d_ctx *c) { return c ? c->jacobi_sweeps : -1; }
+
+extern "C" wc4d_status wc4d_set_graphs(wc4d_ctx *c, int32_t enable)
+{
+    if (!c) return WC4D_EINVAL;
+    c->use_graphs = enable != 0;
+    return WC4D_OK;
+}
 
 extern "C" int64_t wc4d_hvp_count(wc4d_ctx *c, int32_t reset)
 {
@@ -1277,7 +1357,7 @@ struct PcgOut {
 // over the Ritz vectors.  qcf_dev may be null.
 template <typename T>
 static wc4d_status lmp_cg_step(wc4d_ctx *c, T *x, T *r, T *rh, const T *p, const T *q, T *t, double tol_k,
-                               double *qcf_dev, int it)
+                               double *qcf_dev)
 {
     const int64_t nA = c->nA;
     const int kp = c->kp;
@@ -1290,7 +1370,7 @@ static wc4d_status lmp_cg_step(wc4d_ctx *c, T *x, T *r, T *rh, const T *p, const
     unsigned *done = reinterpret_cast<unsigned *>(P<int>(c->counter) + 8);
     ProfScope ps(c, PROF_LMP);
     launch_lmp_fused<T>(c->stream, c->num_sms, nA, c->kU, kp, Urm<T>(c), Ucm<T>(c), P<double>(c->c64), q, p, rh, t,
-                        x, r, scal, flags, P<double>(c->part), w, partB, done, tol_k, qcf_dev, it);
+                        x, r, scal, flags, P<double>(c->part), w, partB, done, tol_k, qcf_dev);
     return WC4D_OK;
 }
 
@@ -1324,20 +1404,24 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
     const double tol_k = (force > 0) ? 0.0 : tol;
     const int nit = (force > 0) ? force : maxit;
     out = PcgOut();
-    for (int it = 0; it < nit; ++it) {
+    IterGraph graph;
+    auto body = [&]() -> wc4d_status {
         WC4D_TRY(hvp_impl<T>(c, p, q, 1, nA, false));                       // q = A p
         if (lmp) {
-            WC4D_TRY(lmp_cg_step<T>(c, x, r, rh, p, q, t, tol_k, qcf_dev, it));
+            WC4D_TRY(lmp_cg_step<T>(c, x, r, rh, p, q, t, tol_k, qcf_dev));
             launch_pcg_p<T>(c->stream, grid, nA, scal, p, t);               // p = C rhat + beta p
         } else {
             launch_dot_partial<T>(c->stream, grid, nA, p, q, pa);
             launch_pcg_alpha(c->stream, grid, pa, scal, flags);             // alpha = rho / p^T A p
             launch_pcg_xr<T>(c->stream, grid, nA, scal, x, r, p, q, pb);    // x += alpha p; r -= alpha q
             launch_pcg_rh<T>(c->stream, grid, nA, scal, rh, q, pc);         // rhat -= alpha A p
-            launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
+            launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev);
             launch_pcg_p<T>(c->stream, grid, nA, scal, p, rh);              // p = rhat + beta p
         }
-        WC4D_TRY(check_launch(c, "pcg iteration"));
+        return check_launch(c, "pcg iteration");
+    };
+    for (int it = 0; it < nit; ++it) {
+        WC4D_TRY(run_iteration(c, graph, it, body));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
         WC4D_TRY(sync(c, "pcg iteration"));
         if (hflags[0]) break;
@@ -1435,10 +1519,11 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
     const double tol_k = (force > 0) ? 0.0 : tol;
     const int nit = (force > 0) ? force : maxit;
     int it = 0;
-    for (; it < nit && !converged; ++it) {
+    IterGraph graph;
+    auto body = [&]() -> wc4d_status {
         WC4D_TRY(hvp_impl<float>(c, p, q, 1, nA, false));                    // q = A p
         if (lmp) {
-            WC4D_TRY(lmp_cg_step<float>(c, d, r, rh, p, q, t, tol_k, qcf_dev, it));
+            WC4D_TRY(lmp_cg_step<float>(c, d, r, rh, p, q, t, tol_k, qcf_dev));
             ProfScope ps(c, PROF_VEC);
             launch_pcg_p<float>(c->stream, grid, nA, scal, p, t);            // p = C rhat + beta p
         } else {
@@ -1447,10 +1532,13 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
             launch_pcg_alpha(c->stream, grid, pa, scal, flags);              // alpha = rho / p^T A p
             launch_pcg_xr<float>(c->stream, grid, nA, scal, d, r, p, q, pb); // d += alpha p; r -= alpha q
             launch_pcg_rh<float>(c->stream, grid, nA, scal, rh, q, pc);      // rhat -= alpha A p
-            launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev, it);
+            launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol_k, qcf_dev);
             launch_pcg_p<float>(c->stream, grid, nA, scal, p, rh);           // p = rhat + beta p
         }
-        WC4D_TRY(check_launch(c, "pcg iteration"));
+        return check_launch(c, "pcg iteration");
+    };
+    for (; it < nit && !converged; ++it) {
+        WC4D_TRY(run_iteration(c, graph, it, body));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
         WC4D_CUDA(c, cudaMemcpyAsync(hrel, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         WC4D_TRY(sync(c, "pcg iteration"));

@@ -1142,7 +1142,7 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, c
                                                     const double *__restrict__ w, const double *__restrict__ scal,
                                                     const T *__restrict__ q, const T *__restrict__ p, T *rh, T *t,
                                                     T *x, T *r, double *part, double *scal_rw, int *flags,
-                                                    unsigned *done, double tol, double *qcf_drop, int it)
+                                                    unsigned *done, double tol, double *qcf_drop)
 {
     extern __shared__ __align__(16) double wsm[];
     __shared__ int last;
@@ -1244,7 +1244,7 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, c
         }
         const double rho = scal_rw[S_RHO];
         scal_rw[S_BETA] = rho_new / rho;
-        if (qcf_drop) qcf_drop[it] = 0.5 * scal_rw[S_ALPHA] * rho;
+        if (qcf_drop) qcf_drop[flags[F_ITER]] = 0.5 * scal_rw[S_ALPHA] * rho;   // iterations done so far
         scal_rw[S_RHO] = rho_new;
         scal_rw[S_RR] = rr;
         const double rel = sqrt(rr) / scal_rw[S_BNORM];
@@ -1270,7 +1270,7 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b_rm(int64_t nA, int kp, int64
                                                        const double *__restrict__ w, const double *__restrict__ scal,
                                                        const T *__restrict__ q, const T *__restrict__ p, T *rh, T *t,
                                                        T *x, T *r, double *part, double *scal_rw, int *flags,
-                                                       unsigned *done, double tol, double *qcf_drop, int it)
+                                                       unsigned *done, double tol, double *qcf_drop)
 {
     constexpr int LB = sizeof(T) == 4 ? 8 : 4;   // rows per warp step
     constexpr int NV = 2 * LB;                    // sums per warp step
@@ -1384,7 +1384,7 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b_rm(int64_t nA, int kp, int64
         }
         const double rho = scal_rw[S_RHO];
         scal_rw[S_BETA] = rho_new / rho;
-        if (qcf_drop) qcf_drop[it] = 0.5 * scal_rw[S_ALPHA] * rho;
+        if (qcf_drop) qcf_drop[flags[F_ITER]] = 0.5 * scal_rw[S_ALPHA] * rho;   // iterations done so far
         scal_rw[S_RHO] = rho_new;
         scal_rw[S_RR] = rr;
         const double rel = sqrt(rr) / scal_rw[S_BNORM];
@@ -1400,7 +1400,7 @@ int lmp_pass_b_grid(int64_t nA) { return ceil_div(nA, PB_ROWS); }
 template <typename T>
 void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const T *Ucm,
                       const double *cvec, const T *q, const T *p, T *rh, T *t, T *x, T *r, double *scal, int *flags,
-                      double *partA, double *w, double *partB, unsigned *done, double tol, double *qcf_drop, int it)
+                      double *partA, double *w, double *partB, unsigned *done, double tol, double *qcf_drop)
 {
     const int S = lmp_pass_a_splits(nA, num_sms);
     const int64_t rows_per = (nA + S - 1) / S;
@@ -1416,23 +1416,23 @@ void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, co
     WC4D_LAUNCH(k_lmp_coef<<<ceil_div(2 * kp + 1, 8), 256, 0, s>>>(S, k, kp, partA, cvec, scal, flags, sums, w, done));
     if (rm) {
         WC4D_LAUNCH(k_lmp_pass_b_rm<T><<<S, 256, 0, s>>>(nA, kp, rows_per, Urm, w, scal, q, p, rh, t, x, r, partB, scal,
-                                                         flags, done + 1, tol, qcf_drop, it));
+                                                         flags, done + 1, tol, qcf_drop));
         return;
     }
     const int G = lmp_pass_b_grid(nA);
     const size_t smem = (2 * (size_t)kp + 2 * PB_CHUNKS * PB_ROWS) * sizeof(T);
     WC4D_LAUNCH(k_lmp_pass_b<T><<<G, 256, smem, s>>>(nA, k, kp, Ucm, w, scal, q, p, rh, t, x, r, partB, scal, flags,
-                                                     done + 1, tol, qcf_drop, it));
+                                                     done + 1, tol, qcf_drop));
 }
 
 template void launch_lmp_fused<double>(cudaStream_t, int, int64_t, int, int, const double *, const double *,
                                        const double *, const double *, const double *, double *, double *, double *,
                                        double *, double *, int *, double *, double *, double *, unsigned *, double,
-                                       double *, int);
+                                       double *);
 template void launch_lmp_fused<float>(cudaStream_t, int, int64_t, int, int, const float *, const float *,
                                       const double *, const float *, const float *, float *, float *, float *,
                                       float *, double *, int *, double *, double *, double *, unsigned *, double,
-                                      double *, int);
+                                      double *);
 
 // ----------------------------------------------------------------------------
 // PCG (Alg. 1) vector and scalar kernels.  Scalars live in device memory:
@@ -1555,7 +1555,7 @@ void launch_pcg_rh(cudaStream_t s, int grid, int64_t n, const double *scal, T *r
 }
 
 __global__ void k_pcg_beta(int grid, const double *part_rh, const double *part_r, double *scal, int *flags,
-                           double tol, double *qcf_drop, int it)
+                           double tol, double *qcf_drop)
 {
     double rho_new = sum_part(grid, part_rh);
     double rr = sum_part(grid, part_r);
@@ -1566,7 +1566,7 @@ __global__ void k_pcg_beta(int grid, const double *part_rh, const double *part_r
         }
         double rho = scal[S_RHO];
         scal[S_BETA] = rho_new / rho;
-        if (qcf_drop) qcf_drop[it] = 0.5 * scal[S_ALPHA] * rho;
+        if (qcf_drop) qcf_drop[flags[F_ITER]] = 0.5 * scal[S_ALPHA] * rho;   // iterations done so far
         scal[S_RHO] = rho_new;
         scal[S_RR] = rr;
         double rel = sqrt(rr) / scal[S_BNORM];
@@ -1578,9 +1578,9 @@ __global__ void k_pcg_beta(int grid, const double *part_rh, const double *part_r
 }
 
 void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
-                     int *flags, double tol, double *qcf_drop, int it)
+                     int *flags, double tol, double *qcf_drop)
 {
-    WC4D_LAUNCH(k_pcg_beta<<<1, 256, 0, s>>>(grid, part_rh, part_r, scal, flags, tol, qcf_drop, it));
+    WC4D_LAUNCH(k_pcg_beta<<<1, 256, 0, s>>>(grid, part_rh, part_r, scal, flags, tol, qcf_drop));
 }
 
 // After a reliable update: rho and |r|^2 from the replaced residual; the

@@ -1,6 +1,11 @@
 // Kernels of the Hessian product (eq. 10): D^{1/2} (circulant, FFT or
 // direct), the tangent-linear / adjoint sweeps as SIMT GEMM / GEMV over the
 // dense propagators, and the observation term H^T R^{-1} H.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "wc4d_internal.cuh"
 
 template <typename T> struct Cplx;
@@ -1042,6 +1047,110 @@ void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int
     launch_gemm<T>(s, n, K, n, M, n, 1, B, ldb, C, ldc, e);
 }
 
+// ----------------------------------------------------------------------------
+// Autotuned tile shape of the SIMT GEMM when A is K-contiguous (the
+// propagator products of the sweeps, M row-major times a block of columns).
+// On the first call for a shape (rows, columns, reduction) every candidate
+// tile is timed -- three launches each with CUDA events on the caller's
+// stream, writing a scratch C so that the real output is untouched -- and the
+// fastest is kept in a process-wide table; later calls launch it directly.
+// Candidates trade reuse per thread (larger TM x TN) against the number of
+// CTAs (small n and few columns leave most SMs idle with 64 x 64 tiles).
+// Tuning is skipped (heuristic tile) while the stream is being captured into
+// a graph or when autotuning is off.
+// ----------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+    int kind, a, b, c;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(kind, a, b, c) < std::tie(o.kind, o.a, o.b, o.c);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+std::atomic<int> g_autotune{1};
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+void gemm_variant(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, const T *B, int64_t ldb,
+                  T *C, int64_t ldc, const Epi &e)
+{
+    dim3 g(ceil_div(Mrows, BM), ceil_div(Ncols, BN));
+    WC4D_LAUNCH(k_gemm_simt<T, T, BM, BN, BK, TM, TN, true>
+                <<<g, (BM / TM) * (BN / TN), 0, s>>>(Mrows, Ncols, Kdim, A, sam, 1, B, ldb, C, ldc, e));
+}
+
+constexpr int GEMM_CANDIDATES = 5;
+template <typename T>
+void gemm_candidate(int v, cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, const T *B,
+                    int64_t ldb, T *C, int64_t ldc, const Epi &e)
+{
+    switch (v) {
+    case 0: gemm_variant<T, 64, 64, 16, 4, 4>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
+    case 1: gemm_variant<T, 128, 64, 16, 8, 4>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
+    case 2: gemm_variant<T, 64, 32, 16, 4, 2>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
+    case 3: gemm_variant<T, 32, 32, 16, 2, 2>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
+    default: gemm_variant<T, 128, 128, 8, 8, 8>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
+    }
+}
+
+template <typename T>
+int tune_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, const T *B, int64_t ldb)
+{
+    const TuneKey key{sizeof(T) == 8 ? 1 : 0, Mrows, Ncols, Kdim};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!g_autotune.load() || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return -1;
+    T *scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int best = -1;
+    if (cudaMallocAsync(&scratch, sizeof(T) * (size_t)Mrows * Ncols, s) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        const Epi plain{0, 1.0, 0.0, 0.0, 1};
+        float best_ms = 0.f;
+        for (int v = 0; v < GEMM_CANDIDATES; ++v) {
+            gemm_candidate<T>(v, s, Mrows, Ncols, Kdim, A, sam, B, ldb, scratch, Mrows, plain);   // warm
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r)
+                gemm_candidate<T>(v, s, Mrows, Ncols, Kdim, A, sam, B, ldb, scratch, Mrows, plain);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                best = -1;
+                break;
+            }
+            if (best < 0 || ms < best_ms) {
+                best = v;
+                best_ms = ms;
+            }
+        }
+    }
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGetLastError();
+    if (best >= 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.emplace(key, best);
+    }
+    return best;
+}
+}  // namespace
+
+extern "C" void wc4d_set_autotune(int32_t enable) { g_autotune.store(enable != 0); }
+
+extern "C" int32_t wc4d_autotune_choice(int32_t fp64, int32_t rows, int32_t cols, int32_t kdim)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(TuneKey{fp64 ? 1 : 0, rows, cols, kdim});
+    return it == g_tune.end() ? -1 : it->second;
+}
+
 template <typename T>
 void launch_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, int64_t sak,
                  const T *B, int64_t ldb, T *C, int64_t ldc, const Epi &e)
@@ -1049,6 +1158,11 @@ void launch_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int
     using Acc = T;
     if (Mrows <= 0 || Ncols <= 0) return;
     const bool kc = (sak == 1);
+    if (kc && Ncols > 16 && Kdim >= 256) {   // sweep products: tuned tile
+        const int v = tune_gemm<T>(s, Mrows, Ncols, Kdim, A, sam, B, ldb);
+        gemm_candidate<T>(v < 0 ? 0 : v, s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e);
+        return;
+    }
     if (Ncols <= 16) {
         dim3 g(ceil_div(Mrows, 64), ceil_div(Ncols, 16));
         if (kc) WC4D_LAUNCH(k_gemm_simt<T, Acc, 64, 16, 16, 4, 4, true><<<g, 64, 0, s>>>(Mrows, Ncols, Kdim, A, sam, sak, B, ldb, C, ldc, e));

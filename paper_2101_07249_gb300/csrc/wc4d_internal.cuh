@@ -131,6 +131,7 @@ struct wc4d_ctx {
     // profiling (CUDA events per launch group)
     // cooperative (grid-synchronised) kernels need the whole GPU; off while
     // the context runs concurrently with others (wc4d_batch_inner_loop)
+    bool use_graphs = true;         // CG iterations replayed as a CUDA graph (wc4d_set_graphs)
     double jacobi_stop2 = 0.0;      // early stop of the small eigensolves (0: run to a sweep without rotations)
     int jacobi_sweeps = 0;          // sweeps used by the last one
     bool allow_coop = true;
@@ -289,11 +290,11 @@ int lmp_pass_b_grid(int64_t nA);
 template <typename T>
 void launch_lmp_fused(cudaStream_t s, int num_sms, int64_t nA, int k, int kp, const T *Urm, const T *Ucm,
                       const double *cvec, const T *q, const T *p, T *rh, T *t, T *x, T *r, double *scal, int *flags,
-                      double *partA, double *w, double *partB, unsigned *done, double tol, double *qcf_drop, int it);
+                      double *partA, double *w, double *partB, unsigned *done, double tol, double *qcf_drop);
 void launch_pcg_restart(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
                         int *flags);
 void launch_pcg_beta(cudaStream_t s, int grid, const double *part_rh, const double *part_r, double *scal,
-                     int *flags, double tol, double *qcf_drop, int it);
+                     int *flags, double tol, double *qcf_drop);
 void launch_pcg_init(cudaStream_t s, int grid, const double *part_b, const double *part_rh, double *scal,
                      int *flags);
 template <typename T>

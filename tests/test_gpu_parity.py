@@ -533,3 +533,25 @@ def test_outer_update_matches_oracle(name):
         w.wc4d_hvp(S.ctx, dev(X), Y, 3, nA, w.FP64)
         assert colrel(host(Y), oracle.hvp(p, X)) < 1e-11
     S.close()
+
+
+@pytest.mark.parametrize("name", ["ad_fft", "l96"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cg_graph_replay_is_bitwise_eager(name, precision):
+    """The CG iterations replayed from a captured CUDA graph compute exactly
+    what the eager launches compute: same iterates, counts and QCF history."""
+    cfg, S, p, tw = setup(name)
+    prec = w.FP64 if precision == "fp64" else w.MIXED
+    w.wc4d_sketch(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 41, None, prec)
+    out = []
+    for graphs in (False, True):
+        w.wc4d_set_graphs(S.ctx, graphs)
+        x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+        it, rel, qcf, _ = w.wc4d_pcg(S.ctx, x, 1e-9, 5000, 1, 0, prec, qcf=True)
+        out.append((it, rel, host(x), np.asarray(qcf)))
+    w.wc4d_set_graphs(S.ctx, True)
+    (i0, r0, x0, q0), (i1, r1, x1, q1) = out
+    assert i0 == i1 and i0 > 2
+    assert r0 == r1
+    assert np.array_equal(x0, x1)
+    assert np.array_equal(q0, q1)

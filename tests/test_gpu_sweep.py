@@ -81,3 +81,25 @@ def test_staged_sweep_repeatable():
     b = sweeps(S, cfg, X, w.MIXED)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
+
+
+def test_autotuned_sweep_gemm_matches_oracle():
+    """A block product whose propagator GEMMs take the SIMT path (K = 40 is
+    not a multiple of 16): the first product tunes the tile shape of the
+    (n, K, n) GEMM, every later product reuses it, and the results match the
+    oracle to FP32 rounding whichever tile won."""
+    n, N, K = 512, 3, 40
+    cfg = inputs.scaled(inputs.LARGE, n=n, N=N, k=8, l=4)
+    S = w.Solver(cfg, M_shared=True)
+    p = oracle_problem(cfg, mode="dense")
+    X = inputs.block(321, cfg.nA, K)
+    Y = torch.zeros(K, cfg.nA, dtype=torch.float32, device="cuda")
+    w.wc4d_hvp(S.ctx, torch.as_tensor(X, dtype=torch.float32, device="cuda"), Y, K, cfg.nA, w.MIXED)
+    choice = w.wc4d_autotune_choice(False, n, K, n)
+    assert 0 <= choice < 5
+    assert colrel(Y.double().cpu().numpy(), oracle.hvp(p, X)) < 2e-5
+    Y2 = torch.zeros_like(Y)
+    w.wc4d_hvp(S.ctx, torch.as_tensor(X, dtype=torch.float32, device="cuda"), Y2, K, cfg.nA, w.MIXED)
+    assert torch.equal(Y, Y2)                        # the cached tile: same launches, same bits
+    assert w.wc4d_autotune_choice(False, n, K, n) == choice
+    S.close()
