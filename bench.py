@@ -362,8 +362,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the method comparison, the Lorenz-96 window and the batched windows")
-    ap.add_argument("--batch-count", type=int, default=16,
-                    help="uneven windows in the batched comparison (64 in the full configuration)")
+    ap.add_argument("--batch-count", type=int, default=64,
+                    help="uneven windows in the batched comparison")
     ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny"],
                     help="large: n=4096 N=40 (the benchmark); medium: N=8 (profiling captures); tiny: n=100 N=5")
     ap.add_argument("--profile-run", action="store_true",
