@@ -1256,15 +1256,15 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, c
 }
 
 // Second pass over the ROW-MAJOR Ritz vectors with the first pass's split
-// (CTA b: rows [b R, b R + R), R <= PA_ROWS), each CTA walking its rows from
-// the end backwards so that the rows the first pass read last -- still in L2
-// -- come first.  Phase 1: a warp takes LB consecutive rows at a time; lane l
-// reads column quads l and l + 32 of every row (kp / 4 <= 64), forms the
-// 2 LB partial sums (U w1, U w2 for each row), and a halving butterfly over
-// the lanes leaves each sum in two lanes (2 LB + 4 - log2(2 LB) shuffles
-// instead of 10 per row); the sums go to shared memory.  Phase 2: the CTA
-// updates its rows with coalesced vector accesses, as the column-major pass
-// does, and the last CTA takes the CG beta step.
+// (CTA b: rows [b R, b R + R), R <= PA_ROWS), walked in blocks of 64 rows
+// from the end of the range backwards so that the rows the first pass read
+// last -- still in L2 -- come first.  Phase 1, per block: thread (tx, ty)
+// takes column quad tx (kp / 4 <= 64) of rows ty, ty + 4, ... (four rows of
+// loads in flight, as in the first pass) and stores its two partial dot
+// products (with w1 and w2) in shared memory; then two threads per row sum
+// the 64 partials of each product.  Phase 2: the CTA updates its rows with
+// coalesced vector accesses, as the column-major pass does, and the last CTA
+// takes the CG beta step.
 template <typename T>
 __global__ void __launch_bounds__(256) k_lmp_pass_b_rm(int64_t nA, int kp, int64_t rows_per, const T *__restrict__ U,
                                                        const double *__restrict__ w, const double *__restrict__ scal,
@@ -1272,76 +1272,56 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b_rm(int64_t nA, int kp, int64
                                                        T *x, T *r, double *part, double *scal_rw, int *flags,
                                                        unsigned *done, double tol, double *qcf_drop)
 {
-    constexpr int LB = sizeof(T) == 4 ? 8 : 4;   // rows per warp step
-    constexpr int NV = 2 * LB;                    // sums per warp step
+    constexpr int RB = sizeof(T) == 4 ? 64 : 32;   // rows per block (static shared memory <= 48 KB)
+    constexpr int TPS = 256 / (2 * RB);            // threads per (row, product) sum
     __shared__ T dsum[2][PA_ROWS];
+    __shared__ T ps[2][RB][65];
     __shared__ int last;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     const int kq = kp / 4;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int rows = (int)max((int64_t)0, min(rows_per, nA - r0));
-    // this lane's column quads and coefficients
-    const int c0 = lane, c1 = lane + 32;
-    const bool h0 = c0 < kq, h1 = c1 < kq;
-    Quad<T> w10{0, 0, 0, 0}, w20{0, 0, 0, 0}, w11{0, 0, 0, 0}, w21{0, 0, 0, 0};
-    if (h0) {
-        w10 = {(T)w[4 * c0], (T)w[4 * c0 + 1], (T)w[4 * c0 + 2], (T)w[4 * c0 + 3]};
-        w20 = {(T)w[kp + 4 * c0], (T)w[kp + 4 * c0 + 1], (T)w[kp + 4 * c0 + 2], (T)w[kp + 4 * c0 + 3]};
+    const bool hq = tx < kq;
+    Quad<T> w1{0, 0, 0, 0}, w2{0, 0, 0, 0};
+    if (hq) {
+        w1 = {(T)w[4 * tx], (T)w[4 * tx + 1], (T)w[4 * tx + 2], (T)w[4 * tx + 3]};
+        w2 = {(T)w[kp + 4 * tx], (T)w[kp + 4 * tx + 1], (T)w[kp + 4 * tx + 2], (T)w[kp + 4 * tx + 3]};
     }
-    if (h1) {
-        w11 = {(T)w[4 * c1], (T)w[4 * c1 + 1], (T)w[4 * c1 + 2], (T)w[4 * c1 + 3]};
-        w21 = {(T)w[kp + 4 * c1], (T)w[kp + 4 * c1 + 1], (T)w[kp + 4 * c1 + 2], (T)w[kp + 4 * c1 + 3]};
-    }
-    const int nchunks = (rows + LB - 1) / LB;
-    for (int ci = warp; ci < nchunks; ci += 8) {
-        const int hi = rows - ci * LB;           // rows [lo, hi) of the range, walked from the end
-        const int lo = max(0, hi - LB);
-        T v[NV];
-        Quad<T> u0[LB], u1[LB];
+    for (int hi = rows; hi > 0; hi -= RB) {
+        const int lo = max(0, hi - RB);   // block rows [lo, hi)
+        const T *base = U + (r0 + lo) * kp + 4 * tx;
 #pragma unroll
-        for (int i = 0; i < LB; ++i) {
-            const bool ok = lo + i < hi;
-            const T *row = U + (r0 + lo + i) * kp;
-            u0[i] = (ok && h0) ? ld4cs(row + 4 * c0) : Quad<T>{0, 0, 0, 0};
-            u1[i] = (ok && h1) ? ld4cs(row + 4 * c1) : Quad<T>{0, 0, 0, 0};
-        }
+        for (int rr = 0; rr < RB; rr += 16) {   // four rows of loads in flight per thread
+            Quad<T> u[4];
 #pragma unroll
-        for (int i = 0; i < LB; ++i) {
-            T a = u0[i].x * w10.x, b = u0[i].x * w20.x;
-            a = fma(u0[i].y, w10.y, a); b = fma(u0[i].y, w20.y, b);
-            a = fma(u0[i].z, w10.z, a); b = fma(u0[i].z, w20.z, b);
-            a = fma(u0[i].w, w10.w, a); b = fma(u0[i].w, w20.w, b);
-            a = fma(u1[i].x, w11.x, a); b = fma(u1[i].x, w21.x, b);
-            a = fma(u1[i].y, w11.y, a); b = fma(u1[i].y, w21.y, b);
-            a = fma(u1[i].z, w11.z, a); b = fma(u1[i].z, w21.z, b);
-            a = fma(u1[i].w, w11.w, a); b = fma(u1[i].w, w21.w, b);
-            v[2 * i] = a;
-            v[2 * i + 1] = b;
-        }
-        // halving butterfly: afterwards lane l holds sum number
-        // sum over halving steps of (l & off ? h : 0)
-        int off = 16;
+            for (int h = 0; h < 4; ++h) {
+                const int rl = rr + ty + 4 * h;
+                u[h] = (hq && lo + rl < hi) ? ld4cs(base + (int64_t)rl * kp) : Quad<T>{0, 0, 0, 0};
+            }
 #pragma unroll
-        for (int h = NV / 2; h >= 1; h >>= 1, off >>= 1) {
-            const bool upper = (lane & off) != 0;
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-                const T send = upper ? v[i] : v[i + h];
-                const T keep = upper ? v[i + h] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            for (int h = 0; h < 4; ++h) {
+                const int rl = rr + ty + 4 * h;
+                T a = u[h].x * w1.x, b = u[h].x * w2.x;
+                a = fma(u[h].y, w1.y, a); b = fma(u[h].y, w2.y, b);
+                a = fma(u[h].z, w1.z, a); b = fma(u[h].z, w2.z, b);
+                a = fma(u[h].w, w1.w, a); b = fma(u[h].w, w2.w, b);
+                ps[0][rl][tx] = a;
+                ps[1][rl][tx] = b;
             }
         }
-        for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
-        if ((lane & (32 / NV - 1)) == 0) {
-            int idx = 0, o = 16;
+        __syncthreads();
+        {   // TPS consecutive threads sum product sid / RB of row sid % RB
+            const int sid = threadIdx.x / TPS, part_i = threadIdx.x % TPS;
+            const int which = sid / RB, rl = sid % RB;
+            T acc = 0;
+#pragma unroll 8
+            for (int c = part_i * (64 / TPS); c < (part_i + 1) * (64 / TPS); ++c) acc += ps[which][rl][c];
 #pragma unroll
-            for (int h = NV / 2; h >= 1; h >>= 1, o >>= 1)
-                if (lane & o) idx += h;
-            const int i = idx >> 1;   // row lo + i, sum idx & 1
-            if (lo + i < hi) dsum[idx & 1][lo + i] = v[0];
+            for (int o = 1; o < TPS; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (part_i == 0 && lo + rl < hi) dsum[which][lo + rl] = acc;
         }
+        __syncthreads();
     }
-    __syncthreads();
     const double alpha = scal[1];
     double srh = 0.0, sr = 0.0;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {

@@ -254,24 +254,24 @@ template <int R, typename CT> __device__ __forceinline__ void dftR(CT *v)
     else dft16(v);
 }
 
-// one Stockham pass of radix R at span p; 16 / R butterflies per thread
-template <int R, typename CT>
-__device__ __forceinline__ void stockham_pass(CT *buf, const CT *tws, int n, int p, int tid, int nt)
+// one Stockham pass of radix R at span P of an NN-point transform; NN / 16
+// threads, 16 / R butterflies per thread (everything but the thread index is
+// a compile-time constant)
+template <int R, int NN, int P, typename CT>
+__device__ __forceinline__ void stockham_pass(CT *buf, const CT *tws, int tid)
 {
-    constexpr int B = 16 / R;
-    const int T = n / R, half = n >> 1;
+    constexpr int B = 16 / R, T = NN / R, NT = NN / 16, HALF = NN / 2, STEP = NN / (P * R);
     CT v[B][R];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int j = tid + b * nt, k = j & (p - 1);
-        const int step = k * (n / (p * R));   // twiddle index of value r: r * step < n
+        const int j = tid + b * NT, k = j & (P - 1);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             CT x = buf[fpad(j + r * T)];
-            if (r > 0 && p > 1) {
-                const int q = r * step;
-                CT w = tws[q < half ? q : q - half];
-                if (q >= half) { w.x = -w.x; w.y = -w.y; }
+            if (r > 0 && P > 1) {
+                const int q = r * k * STEP;   // < NN
+                CT w = tws[q < HALF ? q : q - HALF];
+                if (q >= HALF) { w.x = -w.x; w.y = -w.y; }
                 x = cmul(x, w);
             }
             v[b][r] = x;
@@ -281,37 +281,42 @@ __device__ __forceinline__ void stockham_pass(CT *buf, const CT *tws, int n, int
     __syncthreads();
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int j = tid + b * nt, k = j & (p - 1);
+        const int j = tid + b * NT, k = j & (P - 1);
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[fpad(base + r * p)] = v[b][r];
+        for (int r = 0; r < R; ++r) buf[fpad(base + r * P)] = v[b][r];
     }
     __syncthreads();
 }
 
-template <typename CT> __device__ void stockham_fft(CT *buf, const CT *tws, int n, int tid, int nt)
+template <typename CT, int NN, int P> __device__ __forceinline__ void stockham_passes(CT *buf, const CT *tws, int tid)
 {
-    int p = 1;
-    while (p * 16 <= n) {
-        stockham_pass<16>(buf, tws, n, p, tid, nt);
-        p *= 16;
+    if constexpr (P * 16 <= NN) {
+        stockham_pass<16, NN, P>(buf, tws, tid);
+        stockham_passes<CT, NN, P * 16>(buf, tws, tid);
+    } else if constexpr (NN / P > 1) {
+        stockham_pass<NN / P, NN, P>(buf, tws, tid);
     }
-    const int rest = n / p;
-    if (rest == 8) stockham_pass<8>(buf, tws, n, p, tid, nt);
-    else if (rest == 4) stockham_pass<4>(buf, tws, n, p, tid, nt);
-    else if (rest == 2) stockham_pass<2>(buf, tws, n, p, tid, nt);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512)
-k_circ_stockham(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy,
-                const T *addX, int64_t ld_add, const T *__restrict__ specB, const T *__restrict__ specQ,
-                const typename Cplx<T>::t *__restrict__ tw, int nBpairs)
+// the whole forward transform, not inlined: the kernel calls it twice and one
+// copy of the unrolled passes keeps the instruction footprint small
+template <typename CT, int NN> __device__ __noinline__ void stockham_fft(CT *buf, const CT *tws, int tid)
+{
+    stockham_passes<CT, NN, 1>(buf, tws, tid);
+}
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 16)
+k_circ_stockham(int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy, const T *addX, int64_t ld_add,
+                const T *__restrict__ specB, const T *__restrict__ specQ, const typename Cplx<T>::t *__restrict__ tw,
+                int nBpairs)
 {
     using CT = typename Cplx<T>::t;
+    constexpr int n = 1 << LOGN, nt = n / 16, half = n / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *buf = reinterpret_cast<CT *>(smem_raw);
-    const int tid = threadIdx.x, nt = blockDim.x;   // nt = n / 16
+    const int tid = threadIdx.x;
     int pair = blockIdx.x;
     const T *spec;
     int64_t ja, ta, jb = 0, tb = 0;
@@ -332,11 +337,10 @@ k_circ_stockham(int n, int logn, int N, int K, const T *__restrict__ X, int64_t 
     }
     const T *xa = X + ja * ldx + ta * n;
     const T *xb = X + jb * ldx + tb * n;
-    const int half = n >> 1;
     CT *tws = buf + n + (n >> 4);
-#pragma unroll 4
+#pragma unroll
     for (int k = tid; k < half; k += nt) tws[k] = tw[k];
-#pragma unroll 16
+#pragma unroll
     for (int s = tid; s < n; s += nt) {
         CT v;
         v.x = xa[s];
@@ -344,29 +348,42 @@ k_circ_stockham(int n, int logn, int N, int K, const T *__restrict__ X, int64_t 
         buf[fpad(s)] = v;
     }
     __syncthreads();
-    stockham_fft(buf, tws, n, tid, nt);
+    stockham_fft<CT, n>(buf, tws, tid);
     // scale by the real spectrum (stored bit-reversed) and conjugate
-    const int sh = 32 - logn;
-#pragma unroll 16
+#pragma unroll
     for (int q = tid; q < n; q += nt) {
-        const T w = spec[__brev((unsigned)q) >> sh];
+        const T w = spec[__brev((unsigned)q) >> (32 - LOGN)];
         CT v = buf[fpad(q)];
         v.x *= w;
         v.y *= -w;
         buf[fpad(q)] = v;
     }
     __syncthreads();
-    stockham_fft(buf, tws, n, tid, nt);
+    stockham_fft<CT, n>(buf, tws, tid);
     T *ya = Y + ja * ldy + ta * n;
     T *yb = Y + jb * ldy + tb * n;
     const T *aa = addX ? addX + ja * ld_add + ta * n : nullptr;
     const T *ab = addX ? addX + jb * ld_add + tb * n : nullptr;
-#pragma unroll 16
+#pragma unroll
     for (int s = tid; s < n; s += nt) {
         const CT v = buf[fpad(s)];
         ya[s] = v.x + (aa ? aa[s] : (T)0);
         if (hasb) yb[s] = -v.y + (ab ? ab[s] : (T)0);
     }
+}
+
+template <typename T, int LOGN>
+static void launch_stockham(cudaStream_t s, int grid, size_t smem, int N, int K, const T *X, int64_t ldx, T *Y,
+                            int64_t ldy, const T *addX, int64_t ld_add, const T *specB, const T *specQ,
+                            const void *tw, int nB)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_circ_stockham<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    WC4D_LAUNCH(k_circ_stockham<T, LOGN><<<grid, (1 << LOGN) / 16, smem, s>>>(
+        N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, (const typename Cplx<T>::t *)tw, nB));
 }
 
 // Direct symmetric circulant product for any n: y_s = sum_r row[r] x[(s+r) mod n].
@@ -415,18 +432,13 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
         int nB = (K + 1) / 2;
         int64_t nQ = ((int64_t)K * N + 1) / 2;
         int grid = (int)(nB + nQ);
-        if (n >= 512) {   // n / 16 threads, 16 values each
-            static bool attr2 = false;
-            if (!attr2) {
-                cudaFuncSetAttribute(k_circ_stockham<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((WC4D_FFT_MAX_N + WC4D_FFT_MAX_N / 16 + WC4D_FFT_MAX_N / 2) *
-                                           sizeof(typename Cplx<T>::t)));
-                attr2 = true;
-            }
-            WC4D_LAUNCH(k_circ_stockham<T><<<grid, n / 16, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add,
-                                                                       specB, specQ,
-                                                                       (const typename Cplx<T>::t *)tw, nB));
-            return;
+        switch (c->logn) {   // n / 16 threads, 16 values each
+        case 9: launch_stockham<T, 9>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
+        case 10: launch_stockham<T, 10>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
+        case 11: launch_stockham<T, 11>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
+        case 12: launch_stockham<T, 12>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
+        case 13: launch_stockham<T, 13>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
+        default: break;
         }
         WC4D_LAUNCH(k_circ_fft<T><<<grid, 512, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,
                                               (const typename Cplx<T>::t *)tw, nB));
