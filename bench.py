@@ -357,7 +357,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wc4d", choices=["wc4d", "reference"])
-    ap.add_argument("--method", default="revd", choices=["revd", "nystrom", "ritzit"])
+    ap.add_argument("--method", default="revd", choices=["revd", "nystrom", "ritzit", "nystrom1"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
@@ -531,11 +531,11 @@ def main():
         fp64 = {"inner_loop_s": t64, "pcg_iters": it64, "relres": rr64, "hvp_block_s": t_hvp64,
                 "hvp_columns_per_s": K / t_hvp64}
 
-    # ---- the three sketching methods of Section 4 on the same window
+    # ---- the three sketching methods of Section 4 and single-pass Nystrom (Section 6) on the same window
     methods, l96, batched, learned = None, None, None, None
     if not args.no_extra and args.workload == "large":
         methods = {}
-        for mname in ("revd", "nystrom", "ritzit"):
+        for mname in ("revd", "nystrom", "ritzit", "nystrom1"):
             torch.cuda.synchronize()
             e0.record(stream)
             it_m, rr_m = w.wc4d_inner_loop(ctx, w.METHODS[mname], cfg.k, cfg.l, cfg.q_power, 555, cfg.tol,
@@ -543,7 +543,7 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             methods[mname] = {"inner_loop_ms": e0.elapsed_time(e1), "pcg_iters": it_m, "relres": rr_m,
-                              "block_products": 3 if mname == "revd" else (2 if mname == "nystrom" else 1)}
+                              "block_products": {"revd": 1 + cfg.q_power + 1, "nystrom": 2}.get(mname, 1)}
         l96 = lorenz96_window(w, inputs, rank, stream)
         batched = batched_windows(w, inputs, args.batch_count) if args.batch_count > 0 else None
         learned = learned_windows(w, inputs, stream)

@@ -55,7 +55,7 @@ typedef enum {
 } wc4d_status;
 
 typedef enum { WC4D_FP64 = 0, WC4D_MIXED = 1 } wc4d_precision;
-typedef enum { WC4D_REVD = 0, WC4D_NYSTROM = 1, WC4D_RITZIT = 2 } wc4d_method;
+typedef enum { WC4D_REVD = 0, WC4D_NYSTROM = 1, WC4D_RITZIT = 2, WC4D_NYSTROM1 = 3 } wc4d_method;
 typedef enum { WC4D_MODEL_DENSE = 0, WC4D_MODEL_L96 = 1 } wc4d_model;
 typedef enum { WC4D_CORR_SOAR = 0, WC4D_CORR_GAUSS = 1, WC4D_CORR_DIAG = 2 } wc4d_corr;
 
@@ -158,7 +158,12 @@ wc4d_status wc4d_gaussian(wc4d_ctx *ctx, uint64_t seed, int64_t rows, int32_t co
 
 /* Randomised Ritz pairs of A (Section 4) kept in the context for the LMP:
  * method REVD (Alg. 3 with q_power extra products and orthonormalisations),
- * NYSTROM (Alg. 4) or RITZIT (Alg. 5), target rank k, oversampling l.
+ * NYSTROM (Alg. 4), RITZIT (Alg. 5) or NYSTROM1 (single-pass Nystrom, the
+ * one-product method Section 6 names as future work, after Tropp, Yurtsever,
+ * Udell and Cevher 2017: Omega = orth(G), Y = A Omega, shift nu = s ||Y||_F
+ * with s = sqrt(nA) 2^-52 (FP64) or 2^-22 (mixed), Omega^T (Y + nu Omega) =
+ * C^T C, (Y + nu Omega) C^{-1} = U Sigma V^T, theta = max(Sigma^2 - nu, 0)),
+ * target rank k, oversampling l.
  * G_device: explicit probes (nA x (k+l), ld = nA, FP64) or NULL to draw
  * them with wc4d_gaussian(seed).  theta_host: k Ritz values, decreasing.
  * Orthonormalisation is CholeskyQR2 with an FP64 Gram; the small

@@ -417,6 +417,53 @@ def ritzit(p, k, G):
     return _method(lib().o_ritzit, p, k, G)
 
 
+def nystrom_single_pass_core(apply_A, G, k, nu_scale):
+    """Single-pass randomised Nystrom approximation of a symmetric positive
+    semi-definite operator (Tropp, Yurtsever, Udell, Cevher, SIAM J. Matrix
+    Anal. Appl. 2017, fixed-rank PSD approximation from one sketch; the paper
+    names a single-pass Nystrom method as future work in Section 6).  Written
+    out step by step from that definition:
+
+        Omega = orth(G)                        Householder QR, m columns
+        Y     = A Omega                        the only product with A
+        nu    = nu_scale * ||Y||_F             stabilising shift
+        Y_nu  = Y + nu Omega
+        B     = Omega^T Y_nu, symmetrised      m x m
+        B     = C^T C                          Cholesky, C upper triangular
+        E     = Y_nu C^{-1}                    n x m
+        E     = U Sigma V^T                    thin SVD
+        theta = max(Sigma^2 - nu, 0)
+
+    apply_A maps a (m, n) block of rows to A applied to each row.  G is
+    (m, n).  Returns U (k, n) and theta (k) in decreasing order."""
+    G = _f64(np.atleast_2d(G))
+    Omega, _ = householder_qr(G)                    # rows = orthonormal columns
+    Y = np.asarray(apply_A(Omega), dtype=np.float64)
+    nu = nu_scale * np.linalg.norm(Y)
+    Ynu = Y + nu * Omega
+    B = Omega @ Ynu.T                               # Omega^T Y_nu (m x m)
+    B = 0.5 * (B + B.T)
+    Cu, rc = cholesky_upper(B)
+    if rc != 0:
+        raise RuntimeError(f"single-pass Nystrom: Omega^T Y_nu not positive definite (pivot {rc})")
+    E = solve_right_upper(Ynu.T, Cu)                # (n, m) = Y_nu C^{-1}
+    Ue, s, _, rc = jacobi_svd(E)                    # rc: sweeps used, < 0 if not converged
+    if rc < 0:
+        raise RuntimeError("single-pass Nystrom: SVD did not converge")
+    theta = np.maximum(s * s - nu, 0.0)
+    return Ue[:, :k].T.copy(), theta[:k].copy()
+
+
+NU_SCALE_FP64 = 2.0 ** -52   # times sqrt(n): the shift Tropp et al. use in double precision
+
+
+def nystrom_single_pass(p, k, G):
+    """Single-pass Nystrom on the preconditioned Hessian A of eq. 10 (one
+    product with A); nu = sqrt(n_A) 2^-52 ||Y||_F."""
+    G = _block(p, G)
+    return nystrom_single_pass_core(lambda X: hvp(p, X), G, k, NU_SCALE_FP64 * np.sqrt(p.nA))
+
+
 def lmp_apply(U, theta, v, transpose=False):
     """C v (or C^T v) for the spectral-LMP factor of eq. 16; U is (k, nA)."""
     U = _f64(np.atleast_2d(U)) if U is not None and len(theta) else np.zeros((0, len(v)))

@@ -25,10 +25,10 @@ LIB_PATH = os.path.join(_HERE, "libwc4d.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTSPD, EBREAKDOWN, ENOCONV, ETIMEOUT, ENAN, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 FP64, MIXED = 0, 1
-REVD, NYSTROM, RITZIT = 0, 1, 2
+REVD, NYSTROM, RITZIT, NYSTROM1 = 0, 1, 2, 3
 MODEL_DENSE, MODEL_L96 = 0, 1
 CORR_SOAR, CORR_GAUSS, CORR_DIAG = 0, 1, 2
-METHODS = {"revd": REVD, "nystrom": NYSTROM, "ritzit": RITZIT}
+METHODS = {"revd": REVD, "nystrom": NYSTROM, "ritzit": RITZIT, "nystrom1": NYSTROM1}
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTSPD", -5: "EBREAKDOWN",
            -6: "ENOCONV", -7: "ETIMEOUT", -8: "ENAN", -9: "ESTATE"}
 

@@ -1206,6 +1206,76 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
             WC4D_CUDA(c, cudaMemcpyAsync(P<double>(c->theta64), w, sizeof(double) * k, cudaMemcpyDeviceToDevice,
                                          c->stream));   // Theta = Sigma^2 (eigenvalues of F^T F)
         }
+    } else if (method == WC4D_NYSTROM1) {
+        // Single-pass Nystrom (Tropp, Yurtsever, Udell, Cevher 2017; named as
+        // future work in Section 6): Omega = orth(G); Y = A Omega (the only
+        // product with A); Y_nu = Y + nu Omega; Omega^T Y_nu = C^T C;
+        // E = Y_nu C^{-1} = U Sigma V^T; Theta = max(Sigma^2 - nu, 0).
+        T *Om = A_, *Yb = B_;
+        if ((st = cholqr2<T>(c, Om, nA, m, nA, D_, nullptr)) != WC4D_OK) return fail(st);
+        if ((st = hvp_impl<T>(c, Om, Yb, m, nA)) != WC4D_OK) return fail(st);
+        // nu = scale ||Y||_F: sqrt(n_A) 2^-52 in FP64 (Tropp et al.), in the mixed
+        // path 2^-22 (FP32 storage of Y rounds each entry by up to 2^-24)
+        const int gridn = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA * m + 255) / 256));
+        WC4D_TRY(ensure(c, c->small1, sizeof(double) * 4 * 1024));
+        launch_dot_partial<T>(c->stream, gridn, nA * m, Yb, Yb, P<double>(c->small1));
+        std::vector<double> hp(gridn);
+        WC4D_CUDA(c, cudaMemcpyAsync(hp.data(), c->small1.p, sizeof(double) * gridn, cudaMemcpyDeviceToHost,
+                                     c->stream));
+        if ((st = sync(c, "nystrom1 norm")) != WC4D_OK) return fail(st);
+        double yy = 0.0;
+        for (double v : hp) yy += v;
+        const double nu = ((sizeof(T) == 8) ? std::sqrt((double)nA) * 0x1p-52 : 0x1p-22) * std::sqrt(yy);
+        launch_axpy_block<T>(c->stream, c->num_sms, nA * m, nu, Om, Yb);                  // Y_nu
+        if ((st = ensure(c, c->part, sizeof(double) * atb_part_doubles(c->num_sms, nA, m, m, 1))) != WC4D_OK)
+            return fail(st);
+        int S = 0;
+        {
+            ProfScope psg(c, PROF_GRAM);
+            if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, Om, nA, Yb, nA, P<double>(c->part), c->part.bytes / 8,
+                              &S, Kmat, 1) != 0)   // Omega^T Y_nu, symmetric up to rounding: upper tiles
+                return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
+        }
+        launch_symmetrize(c->stream, m, Kmat);
+        double *Cc = R;
+        launch_chol_upper(c->stream, m, Kmat, Cc, P<int>(c->counter));
+        int info = 0;
+        WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        if ((st = sync(c, "nystrom1 chol")) != WC4D_OK) return fail(st);
+        if (info)
+            return fail(set_err(c, WC4D_ENOTSPD, "single-pass Nystrom: Omega^T Y_nu not positive definite (pivot %d)",
+                                info));
+        launch_trinv_upper(c->stream, m, Cc, Wv);              // Wv = C^{-1}
+        T *E = C_;
+        Epi e{0, 1.0, 0.0, 0.0, 1};
+        if constexpr (sizeof(T) == 8) {
+            launch_gemm<double>(c->stream, (int)nA, m, m, Yb, 1, nA, Wv, m, E, nA, e);
+        } else {
+            float *Ci32 = reinterpret_cast<float *>(Kmat);
+            launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, Ci32);
+            launch_gemm<float>(c->stream, (int)nA, m, m, Yb, 1, nA, Ci32, m, E, nA, e);
+        }
+        if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, E, nA, E, nA, P<double>(c->part), c->part.bytes / 8, &S,
+                          Kmat, 1) != 0)   // E^T E
+            return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
+        launch_symmetrize(c->stream, m, Kmat);
+        if ((st = check_launch(c, "nystrom1 E")) != WC4D_OK) return fail(st);
+        if ((st = spd_evd(c, m, Kmat, w, Wv)) != WC4D_OK) return fail(st);   // E^T E = V Sigma^2 V^T
+        // U = E V[:, :k] Sigma^{-1}
+        U = Yb;
+        if constexpr (sizeof(T) == 8) {
+            launch_gemm<double>(c->stream, (int)nA, k, m, E, 1, nA, Wv, m, U, nA, e);
+            launch_scale_cols(c->stream, nA, k, (double *)U, nA, w, 1);
+        } else {
+            float *V32 = reinterpret_cast<float *>(Kmat);
+            launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, V32);
+            launch_gemm<float>(c->stream, (int)nA, k, m, E, 1, nA, V32, m, U, nA, e);
+            double *U64t = reinterpret_cast<double *>(c->blkD.p);
+            launch_convert_f32_f64(c->stream, nA * k, (const float *)U, U64t);
+            launch_scale_cols(c->stream, nA, k, U64t, nA, w, 1);
+            launch_convert_f64_f32(c->stream, nA * k, U64t, (float *)U);
+        }
+        launch_theta_unshift(c->stream, k, w, nu, P<double>(c->theta64));          // Theta = max(Sigma^2 - nu, 0)
     } else {
         // REVD_ritzit (Alg. 5): G_3 = orth(G); Y_3 = A G_3 = Z_3 R_3; K_3 = R_3 R_3^T
         if ((st = cholqr2<T>(c, A_, nA, m, nA, D_, nullptr)) != WC4D_OK) return fail(st);
@@ -1264,7 +1334,7 @@ static wc4d_status build_rowmajor_U(wc4d_ctx *c)
 extern "C" wc4d_status wc4d_sketch(wc4d_ctx *c, int32_t method, int32_t k, int32_t l, int32_t q, uint64_t seed,
                                    const double *G, double *theta_host, int32_t precision)
 {
-    if (!c || k < 1 || l < 0 || q < 0 || method < 0 || method > 2) return WC4D_EINVAL;
+    if (!c || k < 1 || l < 0 || q < 0 || method < 0 || method > 3) return WC4D_EINVAL;
     if (k + l > 1024 || k + l > c->nA) return set_err(c, WC4D_EINVAL, "k + l = %d too large", k + l);
     if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
     WC4D_TRY(require_operator(c));

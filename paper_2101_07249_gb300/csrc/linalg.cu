@@ -708,6 +708,34 @@ __global__ void k_lmp_coeffs(int k, const double *theta, double *c)
     if (i < k) c[i] = theta[i] > 0.0 ? 1.0 - 1.0 / sqrt(theta[i]) : 0.0;
 }
 
+// y += alpha x over a whole block (count elements)
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpy_block(int64_t count, double alpha, const T *x, T *y)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (T)((double)y[i] + alpha * (double)x[i]);
+}
+
+template <typename T> void launch_axpy_block(cudaStream_t s, int num_sms, int64_t count, double alpha, const T *x, T *y)
+{
+    WC4D_LAUNCH(k_axpy_block<T><<<std::max(1, std::min(ceil_div(count, 256), 8 * num_sms)), 256, 0, s>>>(count, alpha,
+                                                                                                        x, y));
+}
+template void launch_axpy_block<double>(cudaStream_t, int, int64_t, double, const double *, double *);
+template void launch_axpy_block<float>(cudaStream_t, int, int64_t, double, const float *, float *);
+
+// theta[i] = max(w[i] - nu, 0): the single-pass Nystrom shift taken back off
+__global__ void k_theta_unshift(int k, const double *w, double nu, double *theta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) theta[i] = fmax(w[i] - nu, 0.0);
+}
+
+void launch_theta_unshift(cudaStream_t s, int k, const double *w, double nu, double *theta)
+{
+    WC4D_LAUNCH(k_theta_unshift<<<ceil_div(k, 256), 256, 0, s>>>(k, w, nu, theta));
+}
+
 void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c)
 {
     WC4D_LAUNCH(k_lmp_coeffs<<<ceil_div(k, 128), 128, 0, s>>>(k, theta, c));

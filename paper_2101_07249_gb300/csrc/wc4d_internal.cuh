@@ -255,6 +255,8 @@ void launch_lmp_combine(cudaStream_t s, int64_t nA, int k, const T *U, const dou
                         const double *cvec, double coef, const T *v, T *y, const T *add, const double *beta_dev,
                         const int *skip);
 void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c);
+template <typename T> void launch_axpy_block(cudaStream_t s, int num_sms, int64_t count, double alpha, const T *x, T *y);
+void launch_theta_unshift(cudaStream_t s, int k, const double *w, double nu, double *theta);
 template <typename T>
 void launch_to_rowmajor(cudaStream_t s, int64_t nA, int k, int kp, const T *U, T *Urm);
 int utv_rm_splits(int64_t nA);

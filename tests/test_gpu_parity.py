@@ -209,7 +209,7 @@ def test_symeig_matches_jacobi(m):
     assert m < 2 or w.wc4d_jacobi_sweeps(S.ctx) >= 1
 
 
-@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit", "nystrom1"])
 def test_mixed_sketch_eigensolve_stops_early(method):
     """The small eigensolve of a mixed sketch stops after the sweep that
     brings the columns within |cos| <= 1e-5; the FP64 sketch runs to a sweep
@@ -231,6 +231,17 @@ def test_mixed_sketch_eigensolve_stops_early(method):
 
 
 # ------------------------------------------------------------------ eigensolvers
+def oracle_pairs(method, p, k, G, q):
+    """The oracle's Ritz pairs for a sketch method on the same probes."""
+    if method == "revd":
+        return oracle.revd(p, k, G, q=q)
+    if method == "nystrom":
+        return oracle.nystrom(p, k, G)
+    if method == "nystrom1":
+        return oracle.nystrom_single_pass(p, k, G)
+    return oracle.ritzit(p, k, G)
+
+
 def _lmp_dense(U, th):
     c = 1.0 - 1.0 / np.sqrt(th)
     return np.eye(U.shape[1]) - (U.T * c) @ U
@@ -247,18 +258,13 @@ def _check_pairs(S, cfg, U_or, th_or, k, tol_theta=1e-10):
 
 
 @pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
-@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit", "nystrom1"])
 def test_sketch_fp64_matches_oracle(name, method):
     cfg, S, p, _ = setup(name)
     k, m = cfg.k, cfg.K
     G = inputs.probes(5, cfg.nA, m)
     w.wc4d_sketch(S.ctx, w.METHODS[method], k, m - k, cfg.q_power, 0, dev(G), w.FP64)
-    if method == "revd":
-        Uo, tho = oracle.revd(p, k, G, q=cfg.q_power)
-    elif method == "nystrom":
-        Uo, tho = oracle.nystrom(p, k, G)
-    else:
-        Uo, tho = oracle.ritzit(p, k, G)
+    Uo, tho = oracle_pairs(method, p, k, G, cfg.q_power)
     _check_pairs(S, cfg, Uo, tho, k)
 
 
@@ -273,7 +279,7 @@ def test_sketch_internal_probes_match_oracle_philox():
 
 def test_products_with_A_per_method():
     cfg, S, _, _ = setup("ad_direct")
-    for method, q, expect in (("revd", 0, 2), ("revd", 1, 3), ("nystrom", 0, 2), ("ritzit", 0, 1)):
+    for method, q, expect in (("revd", 0, 2), ("revd", 1, 3), ("nystrom", 0, 2), ("ritzit", 0, 1), ("nystrom1", 0, 1)):
         w.wc4d_hvp_count(S.ctx, reset=True)
         w.wc4d_sketch(S.ctx, w.METHODS[method], cfg.k, cfg.l, q, 3, None, w.FP64)
         assert w.wc4d_hvp_count(S.ctx) == expect, method
@@ -294,7 +300,7 @@ def test_lmp_apply_matches_oracle():
 
 # ------------------------------------------------------------------ PCG
 @pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
-@pytest.mark.parametrize("method", ["none", "revd", "nystrom", "ritzit"])
+@pytest.mark.parametrize("method", ["none", "revd", "nystrom", "ritzit", "nystrom1"])
 def test_pcg_fp64_matches_oracle(name, method):
     """Same probes, same LMP construction, PCG from x_0 = 0.
 
@@ -315,9 +321,7 @@ def test_pcg_fp64_matches_oracle(name, method):
         use = 0
     else:
         w.wc4d_sketch(S.ctx, w.METHODS[method], k, cfg.l, cfg.q_power, 0, dev(G), w.FP64)
-        fn = {"revd": lambda: oracle.revd(p, k, G, q=cfg.q_power), "nystrom": lambda: oracle.nystrom(p, k, G),
-              "ritzit": lambda: oracle.ritzit(p, k, G)}[method]
-        Uo, tho = fn()
+        Uo, tho = oracle_pairs(method, p, k, G, cfg.q_power)
         use = 1
     x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
     # (a) early iterates and their quadratic-cost decrease
@@ -342,7 +346,7 @@ def test_pcg_fp64_matches_oracle(name, method):
 
 
 @pytest.mark.parametrize("name", ["ad_direct", "ad_fft", "l96"])
-@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit", "nystrom1"])
 def test_pcg_mixed_meets_tolerance(name, method):
     """Mixed path (FP32 sketch and CG, FP64 refinement): true relative
     residual <= 1e-6 at tol 1e-6 (checked with the oracle's own product), and
@@ -430,7 +434,7 @@ def test_maxit_reports_no_convergence():
 
 
 # ------------------------------------------------------------------ the benchmark's sketch width
-@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit"])
+@pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit", "nystrom1"])
 def test_sketch_256_columns_matches_oracle(method):
     """k + l = 256 (the width used on the large window): multi-tile, multi-split
     Gram products and a 256 x 256 one-sided Jacobi."""
@@ -439,9 +443,7 @@ def test_sketch_256_columns_matches_oracle(method):
     k, m = cfg.k, cfg.K
     G = inputs.probes(21, cfg.nA, m)
     w.wc4d_sketch(S.ctx, w.METHODS[method], k, m - k, cfg.q_power, 0, dev(G), w.FP64)
-    fn = {"revd": lambda: oracle.revd(p, k, G, q=cfg.q_power), "nystrom": lambda: oracle.nystrom(p, k, G),
-          "ritzit": lambda: oracle.ritzit(p, k, G)}[method]
-    Uo, tho = fn()
+    Uo, tho = oracle_pairs(method, p, k, G, cfg.q_power)
     U = torch.zeros(k, cfg.nA, dtype=torch.float64, device="cuda")
     th = w.wc4d_get_ritz(S.ctx, U, k)
     # the top Ritz values are well separated; the tail of 240 values near 1 is not
