@@ -464,6 +464,75 @@ def nystrom_single_pass(p, k, G):
     return nystrom_single_pass_core(lambda X: hvp(p, X), G, k, NU_SCALE_FP64 * np.sqrt(p.nA))
 
 
+def lanczos_cg(p, b, iters, reorth=True, tol=0.0):
+    """Unpreconditioned CG (Alg. 1 with C = I) on A x = b from x_0 = 0 that
+    keeps what Section 3.3 needs for the Lanczos Ritz pairs: alpha_j, beta_j
+    and the normalised residuals, signed as Lanczos vectors: f_j = (-1)^j
+    r_j / ||r_j|| (f_0 = b / ||b||).  Section 3.3 writes f_j = r_j / ||r_j||
+    with tau_j = sqrt(beta_j) / alpha_j > 0; consecutive CG residuals point
+    in opposite senses along the Lanczos basis, so the unsigned vectors give
+    F^T A F with off-diagonals -tau_j (same eigenvalues, eigenvectors with
+    alternating signs) and the alternation is needed for u_i = F_J w_i.  With
+    reorth, every new residual is orthogonalised against all previous f
+    (classical Gram-Schmidt, twice) before its norm is taken -- the complete
+    reorthogonalisation the paper cites against ghost Ritz values.  Stops
+    after `iters` iterations or at relative residual tol.  Returns dict with
+    alpha, beta (length J), F (J + 1, n) and x."""
+    b = _f64(b)
+    n = b.size
+    x = np.zeros(n)
+    r = b.copy()
+    pdir = r.copy()
+    rho = float(r @ r)
+    bn = np.sqrt(rho)
+    F = [r / bn]
+    al, be = [], []
+    for _ in range(iters):
+        q = hvp(p, pdir[None, :])[0]
+        alpha = rho / float(pdir @ q)
+        x += alpha * pdir
+        r = r - alpha * q
+        if reorth:
+            Fm = np.array(F)
+            for _ in range(2):
+                r = r - Fm.T @ (Fm @ r)
+        rho_new = float(r @ r)
+        beta = rho_new / rho
+        al.append(alpha)
+        be.append(beta)
+        F.append((-1.0) ** len(al) * r / np.sqrt(rho_new))
+        pdir = r + beta * pdir
+        rho = rho_new
+        if tol > 0 and np.sqrt(rho) / bn <= tol:
+            break
+    return dict(alpha=np.array(al), beta=np.array(be), F=np.array(F), x=x)
+
+
+def lanczos_tridiag(alpha, beta):
+    """T_J of Section 3.3 from the CG coefficients (eq. 19-20): gamma_1 =
+    1/alpha_1, gamma_j = 1/alpha_j + beta_{j-1}/alpha_{j-1}; tau_j =
+    sqrt(beta_j)/alpha_j."""
+    J = len(alpha)
+    gam = np.empty(J)
+    gam[0] = 1.0 / alpha[0]
+    for j in range(1, J):
+        gam[j] = 1.0 / alpha[j] + beta[j - 1] / alpha[j - 1]
+    tau = np.sqrt(beta[:J - 1]) / alpha[:J - 1]
+    return np.diag(gam) + np.diag(tau, 1) + np.diag(tau, -1)
+
+
+def lanczos_ritz(alpha, beta, F, k):
+    """Ritz pairs from CG (Section 3.3): the eigenpairs (theta_i, w_i) of T_J,
+    decreasing, and u_i = F_J w_i with F_J = (f_0 .. f_{J-1}).  Returns U
+    (k, n) and theta (k)."""
+    T = lanczos_tridiag(alpha, beta)
+    w, V = np.linalg.eigh(T)
+    order = np.argsort(w)[::-1][:k]
+    J = len(alpha)
+    U = V[:, order].T @ np.asarray(F)[:J]
+    return U, w[order]
+
+
 def lmp_apply(U, theta, v, transpose=False):
     """C v (or C^T v) for the spectral-LMP factor of eq. 16; U is (k, nA)."""
     U = _f64(np.atleast_2d(U)) if U is not None and len(theta) else np.zeros((0, len(v)))
