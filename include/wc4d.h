@@ -286,6 +286,22 @@ wc4d_status wc4d_profile_read(wc4d_ctx *ctx, int32_t cls, double *total_ms, int6
  * other host threads) race and must be serialised by the caller. */
 wc4d_status wc4d_lmp_apply_static(const double *U, const double *theta, int32_t k, int64_t nA, const double *v,
                                   double *y, void *cuda_stream);
+/* Ritz pairs from CG (Section 3.3, eq. 18-20), the deterministic LMP built
+ * from the previous inner loop.  wc4d_lanczos_cg runs FP64 CG without a
+ * preconditioner (Alg. 1 with C = I) on the context's A x = rhs from x = 0
+ * until the relative residual reaches tol or maxit iterations, keeping
+ * alpha_j, beta_j and the Lanczos vectors f_j = (-1)^j r_j / |r_j| (nA x
+ * (maxit + 1) FP64 in the context); reorth != 0 reorthogonalises every new
+ * residual against all previous f (classical Gram-Schmidt twice).  iters,
+ * relres: iterations J and the recursive relative residual.
+ * wc4d_lanczos_tridiag: gamma_1..gamma_J, tau_1..tau_{J-1} of T_J.
+ * wc4d_lanczos_ritz: the k largest eigenpairs of T_J, u_i = F_J w_i,
+ * installed as the context's Ritz pairs (as wc4d_set_ritz); theta_host may
+ * be NULL.  ESTATE without Lanczos data; EINVAL for k > J. */
+wc4d_status wc4d_lanczos_cg(wc4d_ctx *ctx, double *x_device, double tol, int32_t maxit, int32_t reorth,
+                            int32_t *iters, double *relres);
+wc4d_status wc4d_lanczos_tridiag(wc4d_ctx *ctx, double *gamma_host, double *tau_host);
+wc4d_status wc4d_lanczos_ritz(wc4d_ctx *ctx, int32_t k, double *theta_host);
 /* Products with A issued so far (block products count once). */
 int64_t     wc4d_hvp_count(wc4d_ctx *ctx, int32_t reset);
 /* One-sided Jacobi sweeps used by the last small eigensolve or SVD of the

@@ -79,6 +79,10 @@ _SIGS = {
     "wc4d_symeig": (C.c_int, [_V, C.c_int32, _V, _D, _V]),
     "wc4d_hvp_count": (C.c_int64, [_V, C.c_int32]),
     "wc4d_jacobi_sweeps": (C.c_int32, [_V]),
+    "wc4d_lanczos_cg": (C.c_int32, [_V, _V, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_double)]),
+    "wc4d_lanczos_tridiag": (C.c_int32, [_V, _V, _V]),
+    "wc4d_lanczos_ritz": (C.c_int32, [_V, C.c_int32, _V]),
     "wc4d_set_graphs": (C.c_int32, [_V, C.c_int32]),
     "wc4d_set_autotune": (None, [C.c_int32]),
     "wc4d_autotune_choice": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
@@ -357,6 +361,28 @@ def wc4d_lmp_apply_static(U, theta, k, nA, v, y, stream=None):
 
 def wc4d_hvp_count(ctx, reset=False):
     return int(load().wc4d_hvp_count(ctx, 1 if reset else 0))
+
+
+def wc4d_lanczos_cg(ctx, x, tol, maxit, reorth=True):
+    """FP64 CG without a preconditioner recording the Lanczos data; returns (J, relres)."""
+    it = C.c_int32(0)
+    rr = C.c_double(0.0)
+    _check(ctx, load().wc4d_lanczos_cg(ctx, _ptr(x), float(tol), int(maxit), 1 if reorth else 0, C.byref(it),
+                                       C.byref(rr)))
+    return it.value, rr.value
+
+
+def wc4d_lanczos_tridiag(ctx, J):
+    g = np.zeros(int(J))
+    t = np.zeros(max(int(J) - 1, 1))
+    _check(ctx, load().wc4d_lanczos_tridiag(ctx, _hp(g), _hp(t)))
+    return g, t[:max(int(J) - 1, 0)]
+
+
+def wc4d_lanczos_ritz(ctx, k):
+    th = np.zeros(int(k))
+    _check(ctx, load().wc4d_lanczos_ritz(ctx, int(k), _hp(th)))
+    return th
 
 
 def wc4d_jacobi_sweeps(ctx):

@@ -297,7 +297,8 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
                       &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
-                      &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf};
+                      &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf,
+                      &c->lz_F, &c->lz_ab, &c->lz_h};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
@@ -1639,6 +1640,155 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
     *rel_out = rel;
     *breakdown_out = breakdown;
     return WC4D_OK;
+}
+
+// ============================================================================
+// Ritz pairs from CG (Section 3.3): the deterministic LMP of the previous
+// inner loop.  FP64 CG without a preconditioner (Alg. 1 with C = I) keeps
+// alpha_j, beta_j and the normalised residuals as Lanczos vectors
+// f_j = (-1)^j r_j / |r_j|, optionally reorthogonalised against all previous
+// f (classical Gram-Schmidt, twice; the complete reorthogonalisation the
+// paper cites against ghost values).  The tridiagonal T_J of eq. 18-20 is
+// then formed on the host, its eigenpairs come from the FP64 one-sided
+// Jacobi of the sketches, and u_i = F_J w_i.
+// ============================================================================
+extern "C" wc4d_status wc4d_lanczos_cg(wc4d_ctx *c, double *x, double tol, int32_t maxit, int32_t reorth,
+                                       int32_t *iters_out, double *relres_out)
+{
+    if (!c || !x || maxit < 1) return WC4D_EINVAL;
+    if (!c->have_rhs) return set_err(c, WC4D_ESTATE, "rhs not set (call wc4d_set_background_obs)");
+    WC4D_TRY(require_operator(c));
+    const int64_t nA = c->nA;
+    DevBuf *vb = c->pcg64;
+    for (int i = 1; i < 6; ++i) WC4D_TRY(ensure(c, vb[i], sizeof(double) * nA));
+    double *r = P<double>(vb[1]), *rh = P<double>(vb[2]), *p = P<double>(vb[3]), *q = P<double>(vb[4]);
+    const int cap = maxit + 1;
+    WC4D_TRY(ensure(c, c->lz_F, sizeof(double) * (size_t)nA * cap));
+    WC4D_TRY(ensure(c, c->lz_ab, sizeof(double) * 2 * (size_t)maxit));
+    WC4D_TRY(ensure(c, c->lz_h, sizeof(double) * (size_t)cap));
+    double *F = P<double>(c->lz_F), *ab = P<double>(c->lz_ab), *h = P<double>(c->lz_h);
+    const int grid = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA + 255) / 256));
+    WC4D_TRY(ensure(c, c->small1, sizeof(double) * 4 * 1024));
+    double *pa = P<double>(c->small1), *pb = pa + 1024, *pc = pb + 1024;
+    double *scal = P<double>(c->scal);
+    int *flags = P<int>(c->counter) + 4;
+    const double *b = P<double>(c->rhs);
+    c->lz_J = 0;
+
+    WC4D_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * nA, c->stream));
+    launch_copy<double>(c->stream, nA, b, r);
+    launch_copy<double>(c->stream, nA, r, rh);
+    launch_copy<double>(c->stream, nA, rh, p);
+    launch_dot_partial<double>(c->stream, grid, nA, b, b, pa);
+    launch_dot_partial<double>(c->stream, grid, nA, rh, rh, pb);
+    launch_pcg_init(c->stream, grid, pa, pb, scal, flags);
+    launch_lanczos_first(c->stream, grid, nA, b, scal, F);
+    WC4D_TRY(check_launch(c, "lanczos cg init"));
+    int *hflags = P<int>(c->pinned);
+    int it = 0;
+    for (; it < maxit; ++it) {
+        WC4D_TRY(hvp_impl<double>(c, p, q, 1, nA, false));                   // q = A p
+        launch_dot_partial<double>(c->stream, grid, nA, p, q, pa);
+        launch_pcg_alpha(c->stream, grid, pa, scal, flags);                  // alpha = rho / p^T A p
+        launch_pcg_xr<double>(c->stream, grid, nA, scal, x, r, p, q, pb);    // x += alpha p; r -= alpha q
+        if (reorth) {
+            // r -= F_{0..j} (F_{0..j}^T r), twice
+            const int cols = it + 1;
+            const size_t need = atb_part_doubles(c->num_sms, nA, cols, 1, 0);
+            WC4D_TRY(ensure(c, c->part, sizeof(double) * need));
+            for (int pass = 0; pass < 2; ++pass) {
+                if (launch_atb<double>(c->stream, c->num_sms, nA, cols, 1, F, nA, r, nA, P<double>(c->part),
+                                       c->part.bytes / 8, nullptr, h, 0) != 0)
+                    return set_err(c, WC4D_EINVAL, "internal: partial buffer too small");
+                Epi e{0, -1.0, 1.0, 0.0, 1};
+                launch_gemm<double>(c->stream, (int)nA, 1, cols, F, 1, nA, h, cols, r, nA, e);
+            }
+            launch_copy<double>(c->stream, nA, r, rh);
+            launch_dot_partial<double>(c->stream, grid, nA, r, r, pb);
+            launch_dot_partial<double>(c->stream, grid, nA, rh, rh, pc);
+        } else {
+            launch_pcg_rh<double>(c->stream, grid, nA, scal, rh, q, pc);     // rhat -= alpha A p (= r)
+        }
+        launch_pcg_beta(c->stream, grid, pc, pb, scal, flags, tol, nullptr);
+        launch_lanczos_record(c->stream, grid, nA, r, scal, flags, F, ab, cap);
+        launch_pcg_p<double>(c->stream, grid, nA, scal, p, rh);              // p = r + beta p
+        WC4D_TRY(check_launch(c, "lanczos cg iteration"));
+        WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+        WC4D_TRY(sync(c, "lanczos cg iteration"));
+        if (hflags[1]) return set_err(c, WC4D_EBREAKDOWN, "Lanczos CG: breakdown at iteration %d", it + 1);
+        if (hflags[0]) { ++it; break; }
+    }
+    double hs[8];
+    WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "lanczos cg end"));
+    if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
+    c->lz_J = hflags[2];
+    if (iters_out) *iters_out = hflags[2];
+    if (relres_out) *relres_out = hs[4];
+    return WC4D_OK;
+}
+
+// gamma (J) and tau (J - 1) of T_J (eq. 19-20) from the recorded alpha, beta.
+static wc4d_status lanczos_tridiag_host(wc4d_ctx *c, std::vector<double> &gam, std::vector<double> &tau)
+{
+    const int J = c->lz_J;
+    if (J < 1) return set_err(c, WC4D_ESTATE, "no Lanczos data (call wc4d_lanczos_cg)");
+    std::vector<double> ab(2 * (size_t)J);
+    WC4D_CUDA(c, cudaMemcpyAsync(ab.data(), c->lz_ab.p, sizeof(double) * 2 * J, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "lanczos coefficients"));
+    gam.assign(J, 0.0);
+    tau.assign(J > 1 ? J - 1 : 0, 0.0);
+    for (int j = 0; j < J; ++j) {
+        const double al = ab[2 * j];
+        gam[j] = 1.0 / al + (j > 0 ? ab[2 * (j - 1) + 1] / ab[2 * (j - 1)] : 0.0);
+        if (j + 1 < J) tau[j] = std::sqrt(ab[2 * j + 1]) / al;
+    }
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_lanczos_tridiag(wc4d_ctx *c, double *gamma_host, double *tau_host)
+{
+    if (!c || !gamma_host) return WC4D_EINVAL;
+    std::vector<double> gam, tau;
+    WC4D_TRY(lanczos_tridiag_host(c, gam, tau));
+    std::copy(gam.begin(), gam.end(), gamma_host);
+    if (tau_host) std::copy(tau.begin(), tau.end(), tau_host);
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_lanczos_ritz(wc4d_ctx *c, int32_t k, double *theta_host)
+{
+    if (!c || k < 1) return WC4D_EINVAL;
+    std::vector<double> gam, tau;
+    WC4D_TRY(lanczos_tridiag_host(c, gam, tau));
+    const int J = c->lz_J;
+    if (k > J) return set_err(c, WC4D_EINVAL, "lanczos_ritz: k = %d exceeds the %d CG iterations", k, J);
+    const int64_t nA = c->nA;
+    const size_t JJ = (size_t)J * J;
+    std::vector<double> T(JJ, 0.0);   // column-major, symmetric
+    for (int j = 0; j < J; ++j) {
+        T[(size_t)j * J + j] = gam[j];
+        if (j + 1 < J) T[(size_t)j * J + j + 1] = T[(size_t)(j + 1) * J + j] = tau[j];
+    }
+    WC4D_TRY(ensure(c, c->sk_k, sizeof(double) * JJ * 2));
+    WC4D_TRY(ensure(c, c->sk_w, sizeof(double) * 2 * J));
+    double *Td = P<double>(c->sk_k), *V = Td + JJ, *w = P<double>(c->sk_w);
+    WC4D_CUDA(c, cudaMemcpyAsync(Td, T.data(), sizeof(double) * JJ, cudaMemcpyHostToDevice, c->stream));
+    {
+        ProfScope ps(c, PROF_JACOBI);
+        WC4D_TRY(spd_evd(c, J, Td, w, V));   // T_J = W Theta W^T, decreasing
+    }
+    WC4D_TRY(ensure(c, c->blkC, sizeof(double) * (size_t)nA * k));
+    double *U = P<double>(c->blkC);
+    Epi e{0, 1.0, 0.0, 0.0, 1};
+    launch_gemm<double>(c->stream, (int)nA, k, J, P<double>(c->lz_F), 1, nA, V, J, U, nA, e);   // u_i = F_J w_i
+    WC4D_TRY(check_launch(c, "lanczos ritz vectors"));
+    std::vector<double> th(k);
+    WC4D_CUDA(c, cudaMemcpyAsync(th.data(), w, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "lanczos ritz values"));
+    if (theta_host) std::copy(th.begin(), th.end(), theta_host);
+    return wc4d_set_ritz(c, k, U, th.data());
 }
 
 extern "C" wc4d_status wc4d_pcg(wc4d_ctx *c, double *x, double tol, int32_t maxit, int32_t use_lmp, int32_t force,

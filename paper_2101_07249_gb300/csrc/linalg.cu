@@ -1611,6 +1611,45 @@ void launch_pcg_restart(cudaStream_t s, int grid, const double *part_rh, const d
     WC4D_LAUNCH(k_pcg_restart<<<1, 256, 0, s>>>(grid, part_rh, part_r, scal, flags));
 }
 
+// Lanczos vectors from CG (Section 3.3).  k_lanczos_first: F[:, 0] = b / |b|.
+// k_lanczos_record, after the beta step of iteration j (flags[F_ITER] = j + 1
+// iterations done): F[:, j + 1] = (-1)^(j+1) r / |r| (|r|^2 = scal[S_RR]; the
+// sign makes consecutive columns Lanczos vectors, whose tridiagonal has
+// positive off-diagonals) and ab[2 j], ab[2 j + 1] = alpha_j, beta_j.
+// cap: columns of F.
+__global__ void __launch_bounds__(256) k_lanczos_first(int64_t n, const double *b, const double *scal, double *F)
+{
+    const double s = 1.0 / scal[S_BNORM];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        F[i] = s * b[i];
+}
+
+__global__ void __launch_bounds__(256) k_lanczos_record(int64_t n, const double *r, const double *scal,
+                                                        const int *flags, double *F, double *ab, int cap)
+{
+    const int col = flags[F_ITER];
+    if (col < 1 || col >= cap) return;
+    const double s = ((col & 1) ? -1.0 : 1.0) / sqrt(scal[S_RR]);
+    double *f = F + (int64_t)col * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = s * r[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ab[2 * (col - 1)] = scal[S_ALPHA];
+        ab[2 * (col - 1) + 1] = scal[S_BETA];
+    }
+}
+
+void launch_lanczos_first(cudaStream_t s, int grid, int64_t n, const double *b, const double *scal, double *F)
+{
+    WC4D_LAUNCH(k_lanczos_first<<<grid, 256, 0, s>>>(n, b, scal, F));
+}
+
+void launch_lanczos_record(cudaStream_t s, int grid, int64_t n, const double *r, const double *scal, const int *flags,
+                           double *F, double *ab, int cap)
+{
+    WC4D_LAUNCH(k_lanczos_record<<<grid, 256, 0, s>>>(n, r, scal, flags, F, ab, cap));
+}
+
 // p = t + beta p
 template <typename T>
 __global__ void __launch_bounds__(256) k_pcg_p(int64_t n, const double *scal, T *p, const T *t)

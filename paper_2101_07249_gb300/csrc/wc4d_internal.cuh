@@ -131,6 +131,9 @@ struct wc4d_ctx {
     // profiling (CUDA events per launch group)
     // cooperative (grid-synchronised) kernels need the whole GPU; off while
     // the context runs concurrently with others (wc4d_batch_inner_loop)
+    // Lanczos data of the last wc4d_lanczos_cg: F (nA x (J + 1)), alpha/beta pairs
+    DevBuf lz_F, lz_ab, lz_h;
+    int lz_J = 0;
     bool use_graphs = true;         // CG iterations replayed as a CUDA graph (wc4d_set_graphs)
     double jacobi_stop2 = 0.0;      // early stop of the small eigensolves (0: run to a sweep without rotations)
     int jacobi_sweeps = 0;          // sweeps used by the last one
@@ -257,6 +260,9 @@ void launch_lmp_combine(cudaStream_t s, int64_t nA, int k, const T *U, const dou
 void launch_lmp_coeffs(cudaStream_t s, int k, const double *theta, double *c);
 template <typename T> void launch_axpy_block(cudaStream_t s, int num_sms, int64_t count, double alpha, const T *x, T *y);
 void launch_theta_unshift(cudaStream_t s, int k, const double *w, double nu, double *theta);
+void launch_lanczos_first(cudaStream_t s, int grid, int64_t n, const double *b, const double *scal, double *F);
+void launch_lanczos_record(cudaStream_t s, int grid, int64_t n, const double *r, const double *scal, const int *flags,
+                           double *F, double *ab, int cap);
 template <typename T>
 void launch_to_rowmajor(cudaStream_t s, int64_t nA, int k, int kp, const T *U, T *Urm);
 int utv_rm_splits(int64_t nA);
