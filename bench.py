@@ -532,7 +532,7 @@ def main():
                 "hvp_columns_per_s": K / t_hvp64}
 
     # ---- the three sketching methods of Section 4 and single-pass Nystrom (Section 6) on the same window
-    methods, l96, batched, learned = None, None, None, None
+    methods, l96, batched, learned, paper_adv = None, None, None, None, None
     if not args.no_extra and args.workload == "large":
         methods = {}
         for mname in ("revd", "nystrom", "ritzit", "nystrom1"):
@@ -547,6 +547,8 @@ def main():
         l96 = lorenz96_window(w, inputs, rank, stream)
         batched = batched_windows(w, inputs, args.batch_count) if args.batch_count > 0 else None
         learned = learned_windows(w, inputs, stream)
+        from paper_2101_07249_gb300 import paper_setups
+        paper_adv = paper_setups.spectral_study()
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -586,6 +588,7 @@ def main():
             "lorenz96": l96,
             "batched": batched,
             "learned_sketch": learned,
+            "paper_advection_window": paper_adv,
         }
         print(json.dumps(line))
     S.close()

@@ -1,0 +1,70 @@
+"""The paper's linear advection window (Section 5.1) built through the C-ABI
+with a user-supplied upwind propagator: its Hessian products match the
+oracle's on the same operator, and its spectrum has the structure the paper
+states below eq. 10 -- every eigenvalue at least 1, and at most q of them
+above 1 (A - I has rank <= q)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_07249_gb300 import paper_setups as ps
+
+torch = pytest.importorskip("torch")
+w = pytest.importorskip("paper_2101_07249_gb300")
+pytestmark = pytest.mark.gpu
+
+_ctx = {}
+
+
+def ctx():
+    if "c" not in _ctx:
+        _ctx["c"] = ps.advection_window(seed=0)
+    return _ctx["c"]
+
+
+def upwind_by_stepping(n, courant):
+    """The oracle side's propagator: one upwind step applied to each unit
+    vector, u_i <- u_i - C (u_i - u_{i-1}) with periodic u_{-1} = u_{n-1}."""
+    M = np.zeros((n, n))
+    for j in range(n):
+        u = np.zeros(n)
+        u[j] = 1.0
+        M[:, j] = u - courant * (u - np.roll(u, 1))
+    return M
+
+
+def oracle_problem():
+    n, N = ps.n_ADV, ps.N_ADV
+    bs, _, _ = oracle.circulant_sqrt_row(oracle.corr_row(0, n, 10.0, 0.1 ** 2))     # SOAR, 10 dz
+    qs, _, _ = oracle.circulant_sqrt_row(oracle.corr_row(0, n, 10.0, 0.05 ** 2))
+    return oracle.Problem(n=n, N=N, model=oracle.MODEL_DENSE, Bsqrt=bs, Qsqrt=qs, sigma_o2=0.05 ** 2,
+                          obs_stride=4, obs_t0=5, obs_tstride=5, steps=1, dt=1.0 / N,
+                          M=upwind_by_stepping(n, 0.8), M_shared=True)
+
+
+def test_upwind_window_hvp_matches_oracle():
+    c = ctx()
+    p = oracle_problem()
+    nA = ps.n_ADV * (ps.N_ADV + 1)
+    X = np.random.default_rng(3).standard_normal((6, nA))
+    Y = torch.zeros(6, nA, dtype=torch.float64, device="cuda")
+    w.wc4d_hvp(c, torch.as_tensor(X, device="cuda"), Y, 6, nA, w.FP64)
+    ref = oracle.hvp(p, X)
+    assert np.abs(Y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert w.wc4d_nobs(c) == 100
+
+
+def test_spectrum_has_q_eigenvalues_above_one():
+    c = ctx()
+    nA = ps.n_ADV * (ps.N_ADV + 1)
+    A = ps.dense_A(c, nA)
+    assert np.abs(A - A.T).max() <= 1e-10 * np.abs(A).max()
+    lam = np.linalg.eigvalsh(0.5 * (A + A.T))
+    # A - I = D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2} has rank at most q = 100
+    # (equal to q when H L^{-1} D^{1/2} has full row rank; here the SOAR
+    # spectra on 40 points decay below 1e-8 of their maxima and those modes
+    # of D^{1/2} are zero, so fewer directions see the observations)
+    assert lam[0] >= 1.0 - 1e-10
+    above = np.sum(lam > 1.0 + 1e-8)
+    assert 0 < above <= 100
+    assert np.sum(np.abs(lam - 1.0) <= 1e-8) == nA - above
