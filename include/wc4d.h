@@ -316,6 +316,11 @@ int32_t     wc4d_jacobi_sweeps(const wc4d_ctx *ctx);
    results are bitwise those of the eager launches.  enable = 0 keeps every
    iteration eager.  EINVAL for a null context. */
 wc4d_status wc4d_set_graphs(wc4d_ctx *ctx, int32_t enable);
+/* Mixed-precision CG (reliable updates): the FP32 recurrence residual must
+   fall by the factor delta (0 < delta <= 1, default 1e-3) since the last
+   update, or claim convergence, before the FP64 true residual replaces it.
+   EINVAL outside (0, 1]. */
+wc4d_status wc4d_set_reliable_delta(wc4d_ctx *ctx, double delta);
 /* Autotuned tile shapes of the SIMT propagator GEMMs (process-wide, default
    on): the first product of a shape times every candidate tile (scratch
    output) and keeps the fastest.  wc4d_autotune_choice returns the tile index

@@ -84,6 +84,7 @@ _SIGS = {
     "wc4d_lanczos_tridiag": (C.c_int32, [_V, _V, _V]),
     "wc4d_lanczos_ritz": (C.c_int32, [_V, C.c_int32, _V]),
     "wc4d_set_graphs": (C.c_int32, [_V, C.c_int32]),
+    "wc4d_set_reliable_delta": (C.c_int32, [_V, C.c_double]),
     "wc4d_set_autotune": (None, [C.c_int32]),
     "wc4d_autotune_choice": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "wc4d_apply_dsqrt": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
@@ -391,6 +392,10 @@ def wc4d_jacobi_sweeps(ctx):
 
 def wc4d_set_graphs(ctx, enable):
     _check(ctx, load().wc4d_set_graphs(ctx, 1 if enable else 0))
+
+
+def wc4d_set_reliable_delta(ctx, delta):
+    _check(ctx, load().wc4d_set_reliable_delta(ctx, float(delta)))
 
 
 def wc4d_set_autotune(enable):

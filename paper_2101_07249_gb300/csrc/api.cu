@@ -351,6 +351,13 @@ extern "C" wc4d_status wc4d_profile_read(wc4d_ctx *c, int32_t cls, double *total
 
 extern "C" int32_t wc4d_jacobi_sweeps(const wc4d_ctx *c) { return c ? c->jacobi_sweeps : -1; }
 
+extern "C" wc4d_status wc4d_set_reliable_delta(wc4d_ctx *c, double delta)
+{
+    if (!c || !(delta > 0.0 && delta <= 1.0)) return WC4D_EINVAL;
+    c->reliable_delta = delta;
+    return WC4D_OK;
+}
+
 extern "C" wc4d_status wc4d_set_graphs(wc4d_ctx *c, int32_t enable)
 {
     if (!c) return WC4D_EINVAL;
@@ -1542,7 +1549,7 @@ static wc4d_status true_residual(wc4d_ctx *c, const double *x, double *r64, doub
 // FP32 residual is replaced by the FP64 true residual rhs - A x, while the
 // search direction p is kept.  Unlike restarted refinement this keeps the
 // Krylov space, so the iteration count stays close to the FP64 solver's.
-constexpr double kReliableDelta = 1e-3;
+// The factor (default 1e-3) is c->reliable_delta (wc4d_set_reliable_delta).
 
 static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, int force, bool use_lmp,
                                 double *qcf_dev, int *iters_out, double *rel_out, bool *breakdown_out)
@@ -1615,7 +1622,7 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
         WC4D_TRY(sync(c, "pcg iteration"));
         pending = true;
         if (hflags[1]) { breakdown = true; ++it; break; }
-        if (!(hflags[0] || *hrel < kReliableDelta * rmax)) continue;
+        if (!(hflags[0] || *hrel < c->reliable_delta * rmax)) continue;
         // reliable update
         launch_add_f32_to_f64(c->stream, nA, d, x);
         WC4D_CUDA(c, cudaMemsetAsync(d, 0, sizeof(float) * nA, c->stream));

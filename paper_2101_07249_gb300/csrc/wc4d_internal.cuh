@@ -135,6 +135,7 @@ struct wc4d_ctx {
     DevBuf lz_F, lz_ab, lz_h;
     int lz_J = 0;
     bool use_graphs = true;         // CG iterations replayed as a CUDA graph (wc4d_set_graphs)
+    double reliable_delta = 1e-3;   // mixed CG: residual reduction between FP64 true-residual updates
     double jacobi_stop2 = 0.0;      // early stop of the small eigensolves (0: run to a sweep without rotations)
     int jacobi_sweeps = 0;          // sweeps used by the last one
     bool allow_coop = true;
