@@ -548,7 +548,7 @@ def main():
         batched = batched_windows(w, inputs, args.batch_count) if args.batch_count > 0 else None
         learned = learned_windows(w, inputs, stream)
         from paper_2101_07249_gb300 import paper_setups
-        paper_adv = paper_setups.spectral_study()
+        paper_adv = {"advection": paper_setups.spectral_study(), "lorenz96": paper_setups.lorenz96_study()}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -588,7 +588,7 @@ def main():
             "lorenz96": l96,
             "batched": batched,
             "learned_sketch": learned,
-            "paper_advection_window": paper_adv,
+            "paper_windows": paper_adv,
         }
         print(json.dumps(line))
     S.close()

@@ -140,3 +140,151 @@ def spectral_study(k: int = 25, l: int = 5, seeds=(0, 1, 2), ctx=None):
     if own:
         wc4d_destroy(ctx)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Section 5.2: Lorenz-96, n = 80, N = 150 one-step subwindows of an RK4 step
+# of 0.025, every 10th variable observed at every 10th step (t = 10, .., 150:
+# 120 observations), sigma_o = 0.15, B = 0.2^2 SOAR(2 dX), Q_t = 0.1^2 C_q with
+# length 2 dX (SOAR standing in for the undefined Laplacian correlation).
+# Inner loop 1 runs CG without a second-level preconditioner and keeps its
+# Lanczos data; the second inner loop compares, over the same PCG iterations,
+# no LMP, the deterministic LMP (Ritz pairs of inner loop 1, Section 3.3)
+# and the randomised LMPs of REVD, Nystrom and REVD_ritzit (k = 5, l = 5).
+# ---------------------------------------------------------------------------
+L96_n, L96_N, L96_DT, L96_F = 80, 150, 0.025, 8.0
+L96_SIG_O, L96_SIG_B, L96_SIG_Q, L96_LEN = 0.15, 0.2, 0.1, 2.0
+L96_OBS = 10
+
+
+def _l96_rhs(x, F=L96_F):
+    return (np.roll(x, -1) - np.roll(x, 2)) * np.roll(x, 1) - x + F
+
+
+def _l96_rk4(x, dt=L96_DT):
+    k1 = _l96_rhs(x)
+    k2 = _l96_rhs(x + 0.5 * dt * k1)
+    k3 = _l96_rhs(x + 0.5 * dt * k2)
+    k4 = _l96_rhs(x + dt * k3)
+    return x + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+
+
+def lorenz96_twin(seed: int = 0, spinup_steps: int = 2000):
+    """Truth (N + 1, n) after an RK4 spin-up from x = F (+ 0.01 noise),
+    background truth + B^{1/2} noise, observations (120,)."""
+    g = np.random.default_rng([int(seed), 52])
+    x = L96_F + 0.01 * g.standard_normal(L96_n)
+    for _ in range(spinup_steps):
+        x = _l96_rk4(x)
+    truth = np.zeros((L96_N + 1, L96_n))
+    truth[0] = x
+    for t in range(L96_N):
+        truth[t + 1] = _l96_rk4(truth[t])
+    row = soar_row(L96_n, L96_SIG_B ** 2, L96_LEN)
+    Bm = np.array([np.roll(row, i) for i in range(L96_n)])
+    lam, V = np.linalg.eigh(Bm)
+    Bh = (V * np.sqrt(np.maximum(lam, 0.0))) @ V.T
+    xb = truth[0] + Bh @ g.standard_normal(L96_n)
+    ys = []
+    for t in range(L96_OBS, L96_N + 1, L96_OBS):
+        pts = truth[t, ::L96_OBS]
+        ys.append(pts + L96_SIG_O * g.standard_normal(pts.size))
+    return truth, xb, np.concatenate(ys)
+
+
+def lorenz96_window(seed: int = 0, stream=None):
+    from . import (CORR_SOAR, MODEL_L96, Problem, wc4d_create, wc4d_set_background_obs, wc4d_set_covariance)
+    prob = Problem()
+    prob.n, prob.N, prob.model, prob.steps = L96_n, L96_N, MODEL_L96, 1
+    prob.dt, prob.F, prob.sigma_o2 = L96_DT, L96_F, L96_SIG_O ** 2
+    prob.obs_stride, prob.obs_t0, prob.obs_tstride = L96_OBS, L96_OBS, L96_OBS
+    prob.M_shared = 0
+    ctx = wc4d_create(prob, stream)
+    wc4d_set_covariance(ctx, 0, CORR_SOAR, L96_SIG_B ** 2, L96_LEN)
+    wc4d_set_covariance(ctx, 1, CORR_SOAR, L96_SIG_Q ** 2, L96_LEN)
+    _, xb, y = lorenz96_twin(seed)
+    wc4d_set_background_obs(ctx, xb, y)
+    return ctx
+
+
+def _lambda_min_CAC(ctx, nA, nobs, U, theta, seed=0):
+    """Smallest eigenvalue of C^T A C for the spectral LMP C = I - U diag(c)
+    U^T (c = 1 - theta^{-1/2}).  A - I has rank <= q (eq. 10) and C - I rank
+    <= k, so every eigenvector outside V = range(A - I) + range(U) has
+    eigenvalue 1 and V is invariant: the eigenvalues of Q^T C A C Q, Q an
+    orthonormal basis of V (from (A - I) G with q + 10 Gaussian columns and
+    U), are the rest.  Products with A: FP64 block Hessian products."""
+    import torch
+
+    from . import FP64, wc4d_hvp
+    g = np.random.default_rng(seed)
+    m = nobs + 10
+    G = torch.as_tensor(g.standard_normal((m, nA)), device="cuda")
+    Y = torch.zeros_like(G)
+    wc4d_hvp(ctx, G, Y, m, nA, FP64)
+    R = (Y - G).cpu().numpy()                        # rows span range(A - I)
+    Q, _ = np.linalg.qr(np.vstack([R, U]).T)         # nA x r
+    c = np.where(theta > 0, 1.0 - 1.0 / np.sqrt(np.maximum(theta, 1e-300)), 0.0)
+
+    def C(X):                                        # X: nA x r
+        return X - U.T @ (c[:, None] * (U @ X))
+
+    CQ = C(Q)
+    Xd = torch.as_tensor(np.ascontiguousarray(CQ.T), device="cuda")
+    Yd = torch.zeros_like(Xd)
+    wc4d_hvp(ctx, Xd, Yd, Xd.shape[0], nA, FP64)
+    CACQ = C(Yd.cpu().numpy().T)
+    S = Q.T @ CACQ
+    ev = np.linalg.eigvalsh(0.5 * (S + S.T))
+    return float(min(ev.min(), 1.0)) if Q.shape[1] < nA else float(ev.min())
+
+
+def lorenz96_study(k: int = 5, l: int = 5, iters: int = 10, seeds=(0, 1, 2), window_seed: int = 0):
+    """Section 5.2's comparison in the second inner loop: the quadratic-cost
+    decrease after each of `iters` PCG iterations (FP64) with no LMP, the
+    deterministic LMP and the three randomised LMPs (averaged over probe
+    seeds), and the smallest eigenvalue of C^T A C for each LMP."""
+    import torch
+
+    from . import (FP64, METHODS, wc4d_destroy, wc4d_get_ritz, wc4d_lanczos_cg, wc4d_lanczos_ritz,
+                   wc4d_outer_update, wc4d_pcg, wc4d_set_ritz, wc4d_sketch)
+    ctx = lorenz96_window(window_seed)
+    nA = L96_n * (L96_N + 1)
+    x = torch.zeros(nA, dtype=torch.float64, device="cuda")
+    J, rr1 = wc4d_lanczos_cg(ctx, x, 1e-6, 100, reorth=True)          # inner loop 1, no LMP
+    wc4d_lanczos_ritz(ctx, k)
+    Ud = torch.zeros(k, nA, dtype=torch.float64, device="cuda")
+    thd = wc4d_get_ritz(ctx, Ud, k)
+    wc4d_outer_update(ctx, x)                                          # second linearisation
+    out = {"nA": nA, "nobs": 120, "inner_loop_1": {"cg_iters": J, "relres": rr1}, "k": k, "l": l,
+           "qcf_decrease": {}, "lambda_min_CAC": {}}
+    y = torch.zeros(nA, dtype=torch.float64, device="cuda")
+
+    def qcf_curve(use):
+        _, _, drop, _ = wc4d_pcg(ctx, y, 1e-14, iters, use, iters, FP64, qcf=True, raise_on_noconv=False)
+        return np.cumsum(drop)
+
+    wc4d_set_ritz(ctx, 0, None, np.zeros(0))
+    out["qcf_decrease"]["none"] = qcf_curve(0).tolist()
+    wc4d_set_ritz(ctx, k, Ud, thd)
+    out["qcf_decrease"]["deterministic"] = qcf_curve(1).tolist()
+    out["lambda_min_CAC"]["deterministic"] = _lambda_min_CAC(ctx, nA, 120, Ud.cpu().numpy(), thd)
+    for name in ("revd", "nystrom", "ritzit"):
+        curves, lmins = [], []
+        for s in seeds:
+            th = wc4d_sketch(ctx, METHODS[name], k, l, 0, 200 + s, None, FP64)
+            curves.append(qcf_curve(1))
+            U = torch.zeros(k, nA, dtype=torch.float64, device="cuda")
+            th = wc4d_get_ritz(ctx, U, k)
+            lmins.append(_lambda_min_CAC(ctx, nA, 120, U.cpu().numpy(), th))
+        out["qcf_decrease"][name] = np.mean(curves, axis=0).tolist()
+        out["lambda_min_CAC"][name] = float(np.mean(lmins))
+    q = {m: v[-1] for m, v in out["qcf_decrease"].items()}
+    out["paper_claims"] = {
+        "randomised_beat_deterministic": all(q[m] > q["deterministic"] for m in ("revd", "nystrom", "ritzit")),
+        "ritzit_best": q["ritzit"] >= max(q["revd"], q["nystrom"]),
+        "revd_lambda_min_below_nystrom_ritzit": out["lambda_min_CAC"]["revd"] < min(
+            out["lambda_min_CAC"]["nystrom"], out["lambda_min_CAC"]["ritzit"]),
+    }
+    wc4d_destroy(ctx)
+    return out

@@ -68,3 +68,32 @@ def test_spectrum_has_q_eigenvalues_above_one():
     above = np.sum(lam > 1.0 + 1e-8)
     assert 0 < above <= 100
     assert np.sum(np.abs(lam - 1.0) <= 1e-8) == nA - above
+
+
+def test_lambda_min_through_invariant_subspace_matches_dense():
+    """The smallest eigenvalue of C^T A C from the rank argument (A - I has
+    rank <= q, C - I rank <= k) equals the dense eigendecomposition's."""
+    c = ctx()
+    nA = ps.n_ADV * (ps.N_ADV + 1)
+    k = 6
+    w.wc4d_sketch(c, w.REVD, k, 4, 0, 9, None, w.FP64)
+    U = torch.zeros(k, nA, dtype=torch.float64, device="cuda")
+    th = w.wc4d_get_ritz(c, U, k)
+    Uh = U.cpu().numpy()
+    lam_sub = ps._lambda_min_CAC(c, nA, 100, Uh, th)
+    A = ps.dense_A(c, nA)
+    cc = 1.0 - 1.0 / np.sqrt(th)
+    C = np.eye(nA) - (Uh.T * cc) @ Uh
+    lam_dense = np.linalg.eigvalsh(C @ (0.5 * (A + A.T)) @ C).min()
+    assert abs(lam_sub - lam_dense) <= 1e-9 * max(1.0, abs(lam_dense))
+
+
+def test_lorenz96_paper_window_study_runs():
+    r = ps.lorenz96_study(iters=3, seeds=(0,))
+    assert r["nA"] == 80 * 151 and r["nobs"] == 120
+    assert 0 < r["inner_loop_1"]["cg_iters"] <= 100
+    for m in ("none", "deterministic", "revd", "nystrom", "ritzit"):
+        assert len(r["qcf_decrease"][m]) == 3
+        assert np.all(np.diff(r["qcf_decrease"][m]) > 0)     # CG decreases the quadratic cost
+    for m, v in r["lambda_min_CAC"].items():
+        assert v <= 1.0 + 1e-9
