@@ -323,8 +323,8 @@ def batched_windows(w, inputs, count, workers=16):
     the same windows.  Wall-clock times around the host calls."""
     import torch
     cfgs = inputs.batch_configs(seed=0, count=count)
-    streams = [torch.cuda.Stream() for _ in cfgs]
-    solvers = [w.Solver(c, inputs.twin(c), M_shared=True, stream=st.cuda_stream) for c, st in zip(cfgs, streams)]
+    streams = [w.wc4d_stream_create() for _ in cfgs]   # torch's pool repeats streams past 32
+    solvers = [w.Solver(c, inputs.twin(c), M_shared=True, stream=st) for c, st in zip(cfgs, streams)]
     xs = [torch.zeros(c.nA, dtype=torch.float64, device="cuda") for c in cfgs]
     ctxs = [S.ctx for S in solvers]
     ks, ls = [c.k for c in cfgs], [c.l for c in cfgs]
@@ -345,6 +345,8 @@ def batched_windows(w, inputs, count, workers=16):
     t_fp64 = time.perf_counter() - t0
     for S in solvers:
         S.close()
+    for st in streams:
+        w.wc4d_stream_destroy(st)
     return {"windows": count, "workers": workers, "total_nA": int(sum(c.nA for c in cfgs)),
             "batched_mixed_s": t_batch, "looped_fp64_s": t_fp64, "speedup": t_fp64 / t_batch,
             "max_relres": max(rr_b), "pcg_iters_batched": it_b, "pcg_iters_fp64": it_f}

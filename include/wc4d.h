@@ -200,6 +200,11 @@ wc4d_status wc4d_inner_loop(wc4d_ctx *ctx, int32_t method, int32_t k, int32_t l,
                             uint64_t seed, double tol, int32_t maxit, int32_t precision,
                             double *x_device, int32_t *iters, double *relres);
 
+/* A non-blocking CUDA stream owned by the caller (wc4d_stream_destroy frees
+   it after the contexts using it are destroyed): one per batched instance.
+   ECUDA when the runtime refuses. */
+wc4d_status wc4d_stream_create(void **stream);
+wc4d_status wc4d_stream_destroy(void *stream);
 /* Batched inner loops of `count` independent problems (windows of different
  * sizes; the paper solves one window at a time, this is a throughput
  * wrapper): instance i runs wc4d_inner_loop(ctxs[i], method, k[i], l[i],

@@ -84,6 +84,8 @@ _SIGS = {
     "wc4d_lanczos_tridiag": (C.c_int32, [_V, _V, _V]),
     "wc4d_lanczos_ritz": (C.c_int32, [_V, C.c_int32, _V]),
     "wc4d_set_graphs": (C.c_int32, [_V, C.c_int32]),
+    "wc4d_stream_create": (C.c_int32, [C.POINTER(C.c_void_p)]),
+    "wc4d_stream_destroy": (C.c_int32, [_V]),
     "wc4d_set_reliable_delta": (C.c_int32, [_V, C.c_double]),
     "wc4d_set_autotune": (None, [C.c_int32]),
     "wc4d_autotune_choice": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
@@ -392,6 +394,19 @@ def wc4d_jacobi_sweeps(ctx):
 
 def wc4d_set_graphs(ctx, enable):
     _check(ctx, load().wc4d_set_graphs(ctx, 1 if enable else 0))
+
+
+def wc4d_stream_create():
+    """A new non-blocking CUDA stream (integer handle) for one batched instance."""
+    h = C.c_void_p()
+    st = load().wc4d_stream_create(C.byref(h))
+    if st != OK:
+        raise WC4DError(st, "wc4d_stream_create failed")
+    return h.value
+
+
+def wc4d_stream_destroy(handle):
+    load().wc4d_stream_destroy(C.c_void_p(handle))
 
 
 def wc4d_set_reliable_delta(ctx, delta):

@@ -25,7 +25,13 @@ extern "C" wc4d_status wc4d_batch_inner_loop(wc4d_ctx *const *ctxs, int32_t coun
     for (int i = 0; i < count; ++i) {
         if (!ctxs[i] || !x[i]) return WC4D_EINVAL;
         for (int j = 0; j < i; ++j)
-            if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return WC4D_EINVAL;   // one stream each
+            if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) {   // one context, one stream each
+                const char *what = ctxs[j] == ctxs[i] ? "context" : "stream";
+                const char *fmt = "batch: instance %d shares its %s with instance %d (each instance needs its own "
+                                  "context and stream; wc4d_stream_create makes one)";
+                set_err(ctxs[j], WC4D_EINVAL, fmt, i, what, j);   // the message on both contexts
+                return set_err(ctxs[i], WC4D_EINVAL, fmt, i, what, j);
+            }
     }
     if (count == 0) return WC4D_OK;
     const int nw = std::max(1, std::min<int>(workers > 0 ? workers : 16, count));
@@ -47,4 +53,22 @@ extern "C" wc4d_status wc4d_batch_inner_loop(wc4d_ctx *const *ctxs, int32_t coun
     for (int i = 0; i < count; ++i)
         if (status[i] != WC4D_OK) return (wc4d_status)status[i];
     return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_stream_create(void **stream)
+{
+    if (!stream) return WC4D_EINVAL;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return WC4D_ECUDA;
+    }
+    *stream = st;
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_stream_destroy(void *stream)
+{
+    if (!stream) return WC4D_EINVAL;
+    return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? WC4D_OK : WC4D_ECUDA;
 }

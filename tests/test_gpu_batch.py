@@ -56,3 +56,27 @@ def test_batch_rejects_shared_streams():
         w.wc4d_batch_inner_loop([S.ctx for S in solvers], w.REVD, [8, 8], [8, 8], 1, [1, 2], 1e-6, 100, w.MIXED, xs)
     for S in solvers:
         S.close()
+
+
+def test_library_streams_for_many_instances():
+    """More instances than torch's stream pool holds (32): library-created
+    streams are distinct; a shared stream is rejected with a message."""
+    cfgs = inputs.batch_configs(seed=5, count=36, sizes=(64,), N_range=(2, 3), K_range=(12, 16))
+    streams = [w.wc4d_stream_create() for _ in cfgs]
+    assert len(set(streams)) == len(streams)
+    solvers = [w.Solver(c, inputs.twin(c), M_shared=True, stream=s) for c, s in zip(cfgs, streams)]
+    xs = [torch.zeros(c.nA, dtype=torch.float64, device="cuda") for c in cfgs]
+    ctxs = [S.ctx for S in solvers]
+    torch.cuda.synchronize()
+    it, rr, st = w.wc4d_batch_inner_loop(ctxs, w.REVD, [c.k for c in cfgs], [c.l for c in cfgs], 1,
+                                         list(range(len(cfgs))), 1e-8, 5000, w.MIXED, xs, workers=8)
+    assert all(r <= 1e-8 for r in rr)
+    shared = w.Solver(cfgs[0], inputs.twin(cfgs[0]), M_shared=True, stream=streams[0])
+    with pytest.raises(w.WC4DError, match="shares its stream"):
+        w.wc4d_batch_inner_loop([ctxs[0], shared.ctx], w.REVD, [cfgs[0].k, cfgs[0].k], [cfgs[0].l, cfgs[0].l], 1,
+                                [0, 1], 1e-8, 100, w.MIXED, [xs[0], xs[1]], workers=2)
+    shared.close()
+    for S in solvers:
+        S.close()
+    for s in streams:
+        w.wc4d_stream_destroy(s)
