@@ -329,7 +329,9 @@ wc4d_status wc4d_set_reliable_delta(wc4d_ctx *ctx, double delta);
 /* Autotuned tile shapes of the SIMT propagator GEMMs (process-wide, default
    on): the first product of a shape times every candidate tile (scratch
    output) and keeps the fastest.  wc4d_autotune_choice returns the tile index
-   chosen for (fp64, rows, cols, kdim), or -1 if that shape was not tuned. */
+   chosen for (kind, rows, cols, kdim), or -1 if that shape was not tuned;
+   kind bit 0: FP64, bit 1: the tall-skinny products (A row-contiguous)
+   rather than the propagator sweeps. */
 void        wc4d_set_autotune(int32_t enable);
 int32_t     wc4d_autotune_choice(int32_t fp64, int32_t rows, int32_t cols, int32_t kdim);
 

@@ -417,8 +417,9 @@ def wc4d_set_autotune(enable):
     load().wc4d_set_autotune(1 if enable else 0)
 
 
-def wc4d_autotune_choice(fp64, rows, cols, kdim):
-    return int(load().wc4d_autotune_choice(1 if fp64 else 0, int(rows), int(cols), int(kdim)))
+def wc4d_autotune_choice(fp64, rows, cols, kdim, tall=False):
+    kind = (1 if fp64 else 0) + (2 if tall else 0)
+    return int(load().wc4d_autotune_choice(kind, int(rows), int(cols), int(kdim)))
 
 
 # --------------------------------------------------------------------------

@@ -1083,33 +1083,35 @@ std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
 std::atomic<int> g_autotune{1};
 
-template <typename T, int BM, int BN, int BK, int TM, int TN>
-void gemm_variant(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, const T *B, int64_t ldb,
+// KC: A is K-contiguous (A(i, k) = A[i sam + k]); otherwise row-contiguous
+// (A(i, k) = A[i + k sak], the tall-skinny products Y R^{-1}, Z W).
+template <typename T, bool KC, int BM, int BN, int BK, int TM, int TN>
+void gemm_variant(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sa, const T *B, int64_t ldb,
                   T *C, int64_t ldc, const Epi &e)
 {
     dim3 g(ceil_div(Mrows, BM), ceil_div(Ncols, BN));
-    WC4D_LAUNCH(k_gemm_simt<T, T, BM, BN, BK, TM, TN, true>
-                <<<g, (BM / TM) * (BN / TN), 0, s>>>(Mrows, Ncols, Kdim, A, sam, 1, B, ldb, C, ldc, e));
+    WC4D_LAUNCH(k_gemm_simt<T, T, BM, BN, BK, TM, TN, KC><<<g, (BM / TM) * (BN / TN), 0, s>>>(
+        Mrows, Ncols, Kdim, A, KC ? sa : 1, KC ? 1 : sa, B, ldb, C, ldc, e));
 }
 
 constexpr int GEMM_CANDIDATES = 5;
-template <typename T>
-void gemm_candidate(int v, cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, const T *B,
+template <typename T, bool KC>
+void gemm_candidate(int v, cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sa, const T *B,
                     int64_t ldb, T *C, int64_t ldc, const Epi &e)
 {
     switch (v) {
-    case 0: gemm_variant<T, 64, 64, 16, 4, 4>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
-    case 1: gemm_variant<T, 128, 64, 16, 8, 4>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
-    case 2: gemm_variant<T, 64, 32, 16, 4, 2>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
-    case 3: gemm_variant<T, 32, 32, 16, 2, 2>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
-    default: gemm_variant<T, 128, 128, 8, 8, 8>(s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e); break;
+    case 0: gemm_variant<T, KC, 64, 64, 16, 4, 4>(s, Mrows, Ncols, Kdim, A, sa, B, ldb, C, ldc, e); break;
+    case 1: gemm_variant<T, KC, 128, 64, 16, 8, 4>(s, Mrows, Ncols, Kdim, A, sa, B, ldb, C, ldc, e); break;
+    case 2: gemm_variant<T, KC, 64, 32, 16, 4, 2>(s, Mrows, Ncols, Kdim, A, sa, B, ldb, C, ldc, e); break;
+    case 3: gemm_variant<T, KC, 32, 32, 16, 2, 2>(s, Mrows, Ncols, Kdim, A, sa, B, ldb, C, ldc, e); break;
+    default: gemm_variant<T, KC, 128, 128, 8, 8, 8>(s, Mrows, Ncols, Kdim, A, sa, B, ldb, C, ldc, e); break;
     }
 }
 
-template <typename T>
-int tune_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sam, const T *B, int64_t ldb)
+template <typename T, bool KC>
+int tune_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_t sa, const T *B, int64_t ldb)
 {
-    const TuneKey key{sizeof(T) == 8 ? 1 : 0, Mrows, Ncols, Kdim};
+    const TuneKey key{(sizeof(T) == 8 ? 1 : 0) + (KC ? 0 : 2), Mrows, Ncols, Kdim};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -1126,10 +1128,10 @@ int tune_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int64_
         const Epi plain{0, 1.0, 0.0, 0.0, 1};
         float best_ms = 0.f;
         for (int v = 0; v < GEMM_CANDIDATES; ++v) {
-            gemm_candidate<T>(v, s, Mrows, Ncols, Kdim, A, sam, B, ldb, scratch, Mrows, plain);   // warm
+            gemm_candidate<T, KC>(v, s, Mrows, Ncols, Kdim, A, sa, B, ldb, scratch, Mrows, plain);   // warm
             cudaEventRecord(e0, s);
             for (int r = 0; r < 3; ++r)
-                gemm_candidate<T>(v, s, Mrows, Ncols, Kdim, A, sam, B, ldb, scratch, Mrows, plain);
+                gemm_candidate<T, KC>(v, s, Mrows, Ncols, Kdim, A, sa, B, ldb, scratch, Mrows, plain);
             cudaEventRecord(e1, s);
             float ms = 0.f;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -1159,7 +1161,7 @@ extern "C" void wc4d_set_autotune(int32_t enable) { g_autotune.store(enable != 0
 extern "C" int32_t wc4d_autotune_choice(int32_t fp64, int32_t rows, int32_t cols, int32_t kdim)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(TuneKey{fp64 ? 1 : 0, rows, cols, kdim});
+    auto it = g_tune.find(TuneKey{(fp64 & 1) + (fp64 & 2), rows, cols, kdim});
     return it == g_tune.end() ? -1 : it->second;
 }
 
@@ -1171,8 +1173,13 @@ void launch_gemm(cudaStream_t s, int Mrows, int Ncols, int Kdim, const T *A, int
     if (Mrows <= 0 || Ncols <= 0) return;
     const bool kc = (sak == 1);
     if (kc && Ncols > 16 && Kdim >= 256) {   // sweep products: tuned tile
-        const int v = tune_gemm<T>(s, Mrows, Ncols, Kdim, A, sam, B, ldb);
-        gemm_candidate<T>(v < 0 ? 0 : v, s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e);
+        const int v = tune_gemm<T, true>(s, Mrows, Ncols, Kdim, A, sam, B, ldb);
+        gemm_candidate<T, true>(v < 0 ? 0 : v, s, Mrows, Ncols, Kdim, A, sam, B, ldb, C, ldc, e);
+        return;
+    }
+    if (!kc && sam == 1 && Ncols > 16 && Mrows >= 16384) {   // tall-skinny block products: tuned tile
+        const int v = tune_gemm<T, false>(s, Mrows, Ncols, Kdim, A, sak, B, ldb);
+        gemm_candidate<T, false>(v < 0 ? 0 : v, s, Mrows, Ncols, Kdim, A, sak, B, ldb, C, ldc, e);
         return;
     }
     if (Ncols <= 16) {
