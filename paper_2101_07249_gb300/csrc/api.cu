@@ -298,7 +298,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
                       &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
                       &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf,
-                      &c->lz_F, &c->lz_ab, &c->lz_h};
+                      &c->lz_F, &c->lz_ab, &c->lz_h, &c->jq32};
     for (DevBuf *b : bufs) free_buf(*b);
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
@@ -938,6 +938,43 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
     const int mp = m + (m & 1);
     const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
     if (const int Pq = c->allow_coop ? jacobi_coop_size(m) : 0) {
+        // Without V (the left singular vectors only): an FP32 pre-rotation
+        // phase first.  One-sided Jacobi in FP32 (about 1.6 FP64 operations
+        // per clock per SM make the FP64 rounds several times dearer) runs
+        // until a sweep's largest rotation has |cos| <= 1e-4; its accumulated
+        // V is made orthogonal to FP64 rounding (two Newton-Schulz steps) and
+        // X0 V -- the same left singular vectors and singular values, columns
+        // orthogonal to ~1e-6 -- goes to the FP64 solve, which then needs one
+        // or two sweeps.  Any failure of the FP32 phase leaves X0 as it is.
+        if (!want_v) {
+            const size_t P2 = (size_t)Pq * Pq, mm = (size_t)m * m;
+            const size_t fbytes = sizeof(float) * 4 * P2, dbytes = sizeof(double) * (P2 + 3 * mm + 8);
+            const size_t ibytes = sizeof(int) * 128 + sizeof(unsigned long long) * 64;
+            if (ensure(c, c->jq32, fbytes + dbytes + ibytes) == WC4D_OK) {
+                float *XV32 = P<float>(c->jq32);
+                double *V64 = reinterpret_cast<double *>(P<char>(c->jq32) + fbytes);
+                double *X1 = V64 + P2, *tmp = X1 + mm, *scale = tmp + 2 * mm;
+                int *rot = reinterpret_cast<int *>(scale + 8);
+                unsigned *bar = reinterpret_cast<unsigned *>(rot + 64);
+                int *err = rot + 65, *status = rot + 66;
+                unsigned long long *maxm = reinterpret_cast<unsigned long long *>(rot + 128);
+                WC4D_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+                if (launch_jacobi_coop_f32(c->stream, m, X0, XV32, 1e-6, 30, rot, bar, err, status, 1e-8, maxm,
+                                           scale)) {
+                    int *h = P<int>(c->pinned);
+                    WC4D_CUDA(c, cudaMemcpyAsync(h, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+                    WC4D_TRY(sync(c, "jacobi fp32 phase"));
+                    if (h[0] == 0) {
+                        launch_convert_f32_f64(c->stream, (int64_t)P2, XV32 + P2, V64);     // V (ld P)
+                        launch_orthogonalise_ns(c->stream, m, V64, Pq, tmp);
+                        launch_small_gemm64(c->stream, m, X0, m, false, V64, Pq, X1, m, 1.0, 0.0);   // X0 V
+                        WC4D_TRY(check_launch(c, "jacobi fp32 phase"));
+                        c->jacobi_sweeps32 = h[1];
+                        X0 = X1;
+                    }
+                }
+            }
+        }
         const size_t nd = jacobi_coop_doubles(m);
         // XV | rot[64] | bar, err, status | maxm[64] (64-bit words)
         WC4D_TRY(ensure(c, c->small3, sizeof(double) * nd + sizeof(int) * 128 + sizeof(unsigned long long) * 64));

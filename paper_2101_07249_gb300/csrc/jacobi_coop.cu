@@ -42,10 +42,10 @@ __device__ __forceinline__ bool jq_barrier(unsigned *bar, unsigned target, int *
     return ok_s != 0;
 }
 
-struct JqArgs {
+template <typename T> struct JqArgs {
     int m, P;
-    const double *X0;   // m x m, column-major, ld m
-    double *XV;         // four P x P buffers X_a, V_a, X_b, V_b; the result ends in X_a, V_a
+    const double *X0;   // m x m, column-major, ld m (scaled by *x0_scale when not null)
+    T *XV;              // four P x P buffers X_a, V_a, X_b, V_b; the result ends in X_a, V_a
     double tol;
     int max_sweeps;
     int *rot;           // max_sweeps rotation counters (zeroed here)
@@ -55,25 +55,30 @@ struct JqArgs {
     int want_v;         // 0: V is neither accumulated nor written
     double stop2;       // > 0: early stop threshold on the largest g^2 / (a b) of a sweep
     unsigned long long *maxm;   // max_sweeps largest g^2 / (a b) (double bits, zeroed here)
+    const double *x0_scale;     // optional scale of X0 (an exact power of two)
 };
 
-__global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
+// T = double: the FP64 solve.  T = float: the FP32 pre-rotation phase (the
+// products, sums and rotations in FP32; V accumulated in FP32).
+template <typename T>
+__global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs<T> a)
 {
-    __shared__ double prod[2][3][JQ_THREADS];      // double-buffered by round parity
+    __shared__ T prod[2][3][JQ_THREADS];      // double-buffered by round parity
     __shared__ double red[2][3];
-    __shared__ double cs[2][2];
+    __shared__ T cs[2][2];
     __shared__ int doit_s[2], conv_s;
     const int P = a.P, pair = blockIdx.x, r = threadIdx.x;
     const unsigned G = gridDim.x;
     const int64_t PP = (int64_t)P * P;
-    double *Xc = a.XV, *Vc = a.XV + PP, *Xn = a.XV + 2 * PP, *Vn = a.XV + 3 * PP;
+    T *Xc = a.XV, *Vc = a.XV + PP, *Xn = a.XV + 2 * PP, *Vn = a.XV + 3 * PP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool wv = a.want_v != 0;
+    const double sc0 = a.x0_scale ? *a.x0_scale : 1.0;
     for (int k = 0; k < 2; ++k) {   // this CTA initialises columns 2 pair, 2 pair + 1
         const int j = 2 * pair + k;
         if (r < P) {
-            Xc[(int64_t)j * P + r] = (r < a.m && j < a.m) ? a.X0[(int64_t)j * a.m + r] : 0.0;
-            if (wv) Vc[(int64_t)j * P + r] = (r == j) ? 1.0 : 0.0;
+            Xc[(int64_t)j * P + r] = (r < a.m && j < a.m) ? (T)(sc0 * a.X0[(int64_t)j * a.m + r]) : (T)0;
+            if (wv) Vc[(int64_t)j * P + r] = (r == j) ? (T)1 : (T)0;
         }
     }
     if (pair == 0)
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
             const int ja = pair == 0 ? 0 : 1 + (pair - 1 + round) % (P - 1);
             const int jb = 1 + (pos_b - 1 + round) % (P - 1);
             const int p = min(ja, jb), q = max(ja, jb);
-            double u = 0.0, w = 0.0, y = 0.0, z = 0.0;
+            T u = 0, w = 0, y = 0, z = 0;
             if (r < P) {
                 u = __ldcg(Xc + (int64_t)p * P + r);
                 w = __ldcg(Xc + (int64_t)q * P + r);
@@ -114,12 +119,12 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
             prod[par][2][r] = u * w;
             __syncthreads();
             if (warp < 3) {
-                double acc = 0.0;
+                T acc = 0;
 #pragma unroll
                 for (int i = lane; i < JQ_THREADS; i += 32) acc += prod[par][warp][i];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) red[par][warp] = acc;
+                if (lane == 0) red[par][warp] = (double)acc;
             }
             __syncthreads();
             // thread 0 alone forms the rotation (256 redundant copies of this
@@ -146,9 +151,9 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
                     const double h = fma(tn, tn, 1.0);
                     double c = (double)rsqrtf((float)h);
                     c = c * fma(-0.5 * h, c * c, 1.5);
-                    c = c * fma(-0.5 * h, c * c, 1.5);
-                    cs[par][0] = c;
-                    cs[par][1] = c * tn;
+                    if (sizeof(T) == 8) c = c * fma(-0.5 * h, c * c, 1.5);
+                    cs[par][0] = (T)c;
+                    cs[par][1] = (T)(c * tn);
                     doit = 1;
                     ++nrot;
                     if (a.stop2 > 0.0) mmax = fmax(mmax, (g * g) / (aa * bb));
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
             }
             __syncthreads();
             const bool doit = doit_s[par] != 0;
-            const double c = cs[par][0], sn = cs[par][1];
+            const T c = cs[par][0], sn = cs[par][1];
             if (r < P) {
                 if (doit) {
                     Xn[(int64_t)p * P + r] = c * u - sn * w;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
             }
             target += G;
             if (!jq_barrier(a.bar, target, a.err)) return;
-            double *t0 = Xc, *t1 = Vc;
+            T *t0 = Xc, *t1 = Vc;
             Xc = Xn; Vc = Vn; Xn = t0; Vn = t1;
         }
         if (threadIdx.x == 0)
@@ -203,6 +208,30 @@ __global__ void __launch_bounds__(JQ_THREADS, 1) k_jacobi_coop(JqArgs a)
     if (pair == 0 && threadIdx.x == 0) *a.status = converged ? sweeps : -1;
 }
 
+__global__ void k_add_diag(int m, double *A, int lda, double v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) A[(int64_t)i * lda + i] += v;
+}
+
+// max |X0| -> the power of two 2^-e that brings it to [1, 2) (for the FP32
+// phase: squared column norms and their products stay in range)
+__global__ void k_x0_scale(int64_t count, const double *X0, double *scale)
+{
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) v = fmax(v, fabs(X0[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mx = fmax(mx, red[i]);
+        *scale = (mx > 0.0 && isfinite(mx)) ? scalbn(1.0, -ilogb(mx)) : 1.0;
+    }
+}
+
 }  // namespace
 
 int jacobi_coop_size(int m) { return (m >= 2 && m <= JQ_MAXP) ? m + (m & 1) : 0; }
@@ -211,6 +240,28 @@ size_t jacobi_coop_doubles(int m)
 {
     const size_t P = (size_t)jacobi_coop_size(m);
     return 4 * P * P;
+}
+
+template <typename T>
+static bool launch_coop(cudaStream_t s, int m, const double *X0, T *XV, double tol, int max_sweeps, int *rot,
+                        unsigned *bar, int *err, int *status, bool want_v, double stop2, unsigned long long *maxm,
+                        const double *x0_scale)
+{
+    const int P = jacobi_coop_size(m);
+    if (P == 0) return false;
+    if (cudaMemsetAsync(bar, 0, sizeof(unsigned), s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    JqArgs<T> args{m, P, X0, XV, tol, max_sweeps, rot, bar, err, status, want_v ? 1 : 0, stop2, maxm, x0_scale};
+    void *params[] = {&args};
+    wc4d_note_launch();
+    if (cudaLaunchCooperativeKernel((const void *)k_jacobi_coop<T>, dim3(P / 2), dim3(JQ_THREADS), params, 0, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
 }
 
 // Returns false (nothing runs, error state cleared) when the cooperative
@@ -222,19 +273,72 @@ size_t jacobi_coop_doubles(int m)
 bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, double tol, int max_sweeps, int *rot,
                         unsigned *bar, int *err, int *status, bool want_v, double stop2, unsigned long long *maxm)
 {
-    const int P = jacobi_coop_size(m);
-    if (P == 0) return false;
-    if (cudaMemsetAsync(bar, 0, sizeof(unsigned), s) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+    return launch_coop<double>(s, m, X0, XV, tol, max_sweeps, rot, bar, err, status, want_v, stop2, maxm, nullptr);
+}
+
+// FP32 pre-rotation: one-sided Jacobi in FP32 on 2^-e X0 (2^-e from max |X0|,
+// computed into *scale_work) accumulating V (FP32) until a sweep's largest
+// rotation has |cos| <= sqrt(stop2) or makes none at tol.  XV32: 4 P^2 floats,
+// V = XV32[P^2, 2 P^2) on return.  Same counters as launch_jacobi_coop.
+bool launch_jacobi_coop_f32(cudaStream_t s, int m, const double *X0, float *XV32, double tol, int max_sweeps,
+                            int *rot, unsigned *bar, int *err, int *status, double stop2, unsigned long long *maxm,
+                            double *scale_work)
+{
+    if (jacobi_coop_size(m) == 0) return false;
+    WC4D_LAUNCH(k_x0_scale<<<1, 256, 0, s>>>((int64_t)m * m, X0, scale_work));
+    return launch_coop<float>(s, m, X0, XV32, tol, max_sweeps, rot, bar, err, status, true, stop2, maxm, scale_work);
+}
+
+// C (m x m) = alpha A^T B + beta C or alpha A B + beta C for small column-major
+// FP64 matrices with leading dimensions lda, ldb, ldc: 16 x 16 output tiles, one
+// CTA each, so that an m = 256 product spreads over 256 SMs' worth of CTAs
+// (the FP64 pipe retires ~1.6 FMA per clock per SM).
+__global__ void __launch_bounds__(256) k_small_gemm64(int m, const double *A, int lda, int transA, const double *B,
+                                                      int ldb, double *C, int ldc, double alpha, double beta)
+{
+    __shared__ double As[16][17], Bs[16][17];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < m; k0 += 16) {
+        // As[kk][ii] = op(A)(blockIdx.x*16 + ii, k0 + kk)
+        const int ii = tx, kk = ty;
+        const int gi = blockIdx.x * 16 + ii, gk = k0 + kk;
+        double av = 0.0;
+        if (gi < m && gk < m) av = transA ? A[(int64_t)gi * lda + gk] : A[(int64_t)gk * lda + gi];
+        As[kk][ii] = av;
+        const int gj = blockIdx.y * 16 + ty, gk2 = k0 + tx;
+        Bs[ty][tx] = (gj < m && gk2 < m) ? B[(int64_t)gj * ldb + gk2] : 0.0;   // Bs[j][k]
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = fma(As[k][tx], Bs[ty][k], acc);
+        __syncthreads();
     }
-    JqArgs args{m, P, X0, XV, tol, max_sweeps, rot, bar, err, status, want_v ? 1 : 0, stop2, maxm};
-    void *params[] = {&args};
-    wc4d_note_launch();
-    if (cudaLaunchCooperativeKernel((const void *)k_jacobi_coop, dim3(P / 2), dim3(JQ_THREADS), params, 0, s) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return false;
+    if (i < m && j < m) {
+        double *dst = C + (int64_t)j * ldc + i;
+        *dst = alpha * acc + (beta != 0.0 ? beta * (*dst) : 0.0);
     }
-    return true;
+}
+
+void launch_small_gemm64(cudaStream_t s, int m, const double *A, int lda, bool transA, const double *B, int ldb,
+                         double *C, int ldc, double alpha, double beta)
+{
+    dim3 g(ceil_div(m, 16), ceil_div(m, 16));
+    WC4D_LAUNCH(k_small_gemm64<<<g, 256, 0, s>>>(m, A, lda, transA ? 1 : 0, B, ldb, C, ldc, alpha, beta));
+}
+
+// V (m x m, ld ldv) <- V (3 I - V^T V) / 2, twice: an FP32-accurate orthogonal
+// V becomes orthogonal to FP64 rounding (Newton-Schulz; the error e -> ~ e^2).
+// tmp: 2 m^2 doubles.
+void launch_orthogonalise_ns(cudaStream_t s, int m, double *V, int ldv, double *tmp)
+{
+    double *G = tmp, *W = tmp + (size_t)m * m;
+    // step 1: W = V (3 I - V^T V) / 2
+    launch_small_gemm64(s, m, V, ldv, true, V, ldv, G, m, -0.5, 0.0);
+    WC4D_LAUNCH(k_add_diag<<<ceil_div(m, 256), 256, 0, s>>>(m, G, m, 1.5));
+    launch_small_gemm64(s, m, V, ldv, false, G, m, W, m, 1.0, 0.0);
+    // step 2: V = W (3 I - W^T W) / 2
+    launch_small_gemm64(s, m, W, m, true, W, m, G, m, -0.5, 0.0);
+    WC4D_LAUNCH(k_add_diag<<<ceil_div(m, 256), 256, 0, s>>>(m, G, m, 1.5));
+    launch_small_gemm64(s, m, W, m, false, G, m, V, ldv, 1.0, 0.0);
 }

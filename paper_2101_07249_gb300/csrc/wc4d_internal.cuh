@@ -138,6 +138,8 @@ struct wc4d_ctx {
     double reliable_delta = 1e-3;   // mixed CG: residual reduction between FP64 true-residual updates
     double jacobi_stop2 = 0.0;      // early stop of the small eigensolves (0: run to a sweep without rotations)
     int jacobi_sweeps = 0;          // sweeps used by the last one
+    int jacobi_sweeps32 = 0;        // FP32 pre-rotation sweeps before it (0: none)
+    DevBuf jq32;                    // FP32 pre-rotation workspace
     bool allow_coop = true;
     bool prof_on = false;
     std::vector<ProfEntry> prof_log;
@@ -245,6 +247,12 @@ int jacobi_coop_size(int m);
 size_t jacobi_coop_doubles(int m);
 bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, double tol, int max_sweeps, int *rot,
                         unsigned *bar, int *err, int *status, bool want_v, double stop2, unsigned long long *maxm);
+bool launch_jacobi_coop_f32(cudaStream_t s, int m, const double *X0, float *XV32, double tol, int max_sweeps,
+                            int *rot, unsigned *bar, int *err, int *status, double stop2, unsigned long long *maxm,
+                            double *scale_work);
+void launch_small_gemm64(cudaStream_t s, int m, const double *A, int lda, bool transA, const double *B, int ldb,
+                         double *C, int ldc, double alpha, double beta);
+void launch_orthogonalise_ns(cudaStream_t s, int m, double *V, int ldv, double *tmp);
 void launch_jacobi_finish_left(cudaStream_t s, int m, int mp, const double *X, double *w, double *Vout);
 void launch_jacobi_finish(cudaStream_t s, int m, int mp, const double *X, const double *V, double *w, double *Vout);
 void launch_rrt(cudaStream_t s, int m, const double *R, double *RT);
