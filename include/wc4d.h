@@ -315,6 +315,9 @@ int64_t     wc4d_hvp_count(wc4d_ctx *ctx, int32_t reset);
    to convergence; -1 for a null context.  In a mixed-precision sketch the
    solve stops after a sweep whose largest rotation had |cos| <= 1e-5. */
 int32_t     wc4d_jacobi_sweeps(const wc4d_ctx *ctx);
+/* FP32 pre-rotation sweeps that preceded the last FP64 eigensolve of an SPD
+   matrix (0 when none ran; negative when it stopped at its sweep limit). */
+int32_t     wc4d_jacobi_sweeps_fp32(const wc4d_ctx *ctx);
 /* CUDA-graph replay of the CG iteration (default on): after one eager
    iteration, the body of Alg. 1's loop (the product with A, the LMP step and
    the direction update) is captured once per solve and replayed; the

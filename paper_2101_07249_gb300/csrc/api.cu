@@ -350,6 +350,7 @@ extern "C" wc4d_status wc4d_profile_read(wc4d_ctx *c, int32_t cls, double *total
 }
 
 extern "C" int32_t wc4d_jacobi_sweeps(const wc4d_ctx *c) { return c ? c->jacobi_sweeps : -1; }
+extern "C" int32_t wc4d_jacobi_sweeps_fp32(const wc4d_ctx *c) { return c ? c->jacobi_sweeps32 : -1; }
 
 extern "C" wc4d_status wc4d_set_reliable_delta(wc4d_ctx *c, double delta)
 {
@@ -937,6 +938,7 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
 {
     const int mp = m + (m & 1);
     const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
+    c->jacobi_sweeps32 = 0;
     if (const int Pq = c->allow_coop ? jacobi_coop_size(m) : 0) {
         // Without V (the left singular vectors only): an FP32 pre-rotation
         // phase first.  One-sided Jacobi in FP32 (about 1.6 FP64 operations
@@ -959,8 +961,11 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
                 int *err = rot + 65, *status = rot + 66;
                 unsigned long long *maxm = reinterpret_cast<unsigned long long *>(rot + 128);
                 WC4D_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
-                if (launch_jacobi_coop_f32(c->stream, m, X0, XV32, 1e-6, 30, rot, bar, err, status, 1e-8, maxm,
-                                           scale)) {
+                // one 16-CTA cluster (V written to XV32 + P^2); else the cooperative form
+                const bool on_cluster =
+                    launch_jacobi_cluster_f32(c->stream, m, X0, XV32 + P2, 1e-6, 30, status, 1e-8, scale);
+                if (on_cluster || launch_jacobi_coop_f32(c->stream, m, X0, XV32, 1e-6, 30, rot, bar, err, status,
+                                                         1e-8, maxm, scale)) {
                     int *h = P<int>(c->pinned);
                     WC4D_CUDA(c, cudaMemcpyAsync(h, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
                     WC4D_TRY(sync(c, "jacobi fp32 phase"));

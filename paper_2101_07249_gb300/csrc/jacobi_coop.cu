@@ -14,6 +14,8 @@
 // Reads bypass L1 (the columns were written by other SMs).  Sweeps repeat
 // until one makes no rotation, or max_sweeps.  Zero padding columns never
 // rotate.
+#include <cooperative_groups.h>
+
 #include "wc4d_internal.cuh"
 
 namespace {
@@ -341,4 +343,193 @@ void launch_orthogonalise_ns(cudaStream_t s, int m, double *V, int ldv, double *
     launch_small_gemm64(s, m, W, m, true, W, m, G, m, -0.5, 0.0);
     WC4D_LAUNCH(k_add_diag<<<ceil_div(m, 256), 256, 0, s>>>(m, G, m, 1.5));
     launch_small_gemm64(s, m, W, m, false, G, m, V, ldv, 1.0, 0.0);
+}
+
+// ----------------------------------------------------------------------------
+// FP32 pre-rotation on one thread-block cluster of 16 CTAs (distributed
+// shared memory) instead of the whole GPU: in FP32 the rotations are cheap,
+// and what limits the cooperative kernel's rounds is the grid barrier and the
+// L2 round trip of the columns.  Pair b of the round-robin ordering (warp
+// b % 8 of CTA b / 8) keeps its two columns -- and their V columns -- in its
+// own CTA's shared memory, so a round reads nothing remote: the warp rotates
+// its pair and writes the two results straight into the slots they occupy in
+// the next round (the ordering shifts the columns one position: the first
+// column of pair b moves to pair b - 1, the second to pair b + 1, with the
+// turn-arounds at both ends), a remote store only across a CTA boundary.
+// Double-buffered slots and one cluster barrier per round.  The columns end
+// in some order, which does not matter: only X0 V with V orthogonal is used.
+// Sweeps stop when a sweep's largest rotation has cos^2 <= stop2, makes no
+// rotation at tol, or after max_sweeps.  Output: V (P x P, FP32).
+// ----------------------------------------------------------------------------
+namespace {
+namespace cgx = cooperative_groups;
+constexpr int JC_CL = 16;
+constexpr int JC_THREADS = 256;   // 8 warps: one pair each
+
+__global__ void __launch_bounds__(JC_THREADS, 1)
+k_jacobi_cluster_f32(int m, int P, const double *__restrict__ X0, const double *x0_scale, float *Vout, float tol,
+                     float stop2, int max_sweeps, int *status)
+{
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int rank = (int)cl.block_rank();
+    // [buffer][x or v][local pair][top or bottom][row]
+    extern __shared__ __align__(16) float jcs[];
+    auto slot = [&](float *base, int buf, int xv, int lp, int tb) { return base + ((((buf * 2 + xv) * 8 + lp) * 2 + tb) * P); };
+    __shared__ int rot_s, conv_s;
+    __shared__ unsigned maxm_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int npairs = P / 2, b = rank * 8 + warp;
+    const float sc = (float)*x0_scale;
+    if (b < npairs) {   // round 0: pair b holds columns b and P - 1 - b
+        const int cols[2] = {b, P - 1 - b};
+        for (int tb = 0; tb < 2; ++tb) {
+            const int j = cols[tb];
+            float *xs = slot(jcs, 0, 0, warp, tb), *vs = slot(jcs, 0, 1, warp, tb);
+            for (int r = lane; r < P; r += 32) {
+                xs[r] = (j < m && r < m) ? sc * (float)X0[(int64_t)j * m + r] : 0.f;
+                vs[r] = (r == j) ? 1.f : 0.f;
+            }
+        }
+    }
+    if (tid == 0) { rot_s = 0; maxm_s = 0u; conv_s = 0; }
+    cl.sync();
+    // destinations of this pair's two columns for the next round
+    int dt_pair, dt_tb, db_pair, db_tb;
+    if (b == 0) { dt_pair = 0; dt_tb = 0; }
+    else if (b == 1) { dt_pair = 0; dt_tb = 1; }
+    else { dt_pair = b - 1; dt_tb = 0; }
+    if (b == npairs - 1) { db_pair = b; db_tb = 0; }
+    else { db_pair = b + 1; db_tb = 1; }
+    if (b == 0 && npairs == 1) { dt_pair = 0; dt_tb = 0; db_pair = 0; db_tb = 1; }
+    int buf = 0, sweeps = 0;
+    bool converged = false;
+    for (; sweeps < max_sweeps && !converged; ++sweeps) {
+        for (int round = 0; round < P - 1; ++round) {
+            if (b < npairs) {
+                const float *xp = slot(jcs, buf, 0, warp, 0), *xq = slot(jcs, buf, 0, warp, 1);
+                const float *vp = slot(jcs, buf, 1, warp, 0), *vq = slot(jcs, buf, 1, warp, 1);
+                float u[8], v[8], y[8], z[8];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = lane + 32 * i;
+                    u[i] = r < P ? xp[r] : 0.f;
+                    v[i] = r < P ? xq[r] : 0.f;
+                    y[i] = r < P ? vp[r] : 0.f;
+                    z[i] = r < P ? vq[r] : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    s0 = fmaf(u[i], u[i], s0);
+                    s1 = fmaf(v[i], v[i], s1);
+                    s2 = fmaf(u[i], v[i], s2);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                }
+                float c = 1.f, sn = 0.f;
+                if ((s2 * s2 > tol * tol * (s0 * s1)) && fabsf(s2) > 1e-30f) {   // the same in every lane
+                    const float zeta = (s1 - s0) / (2.f * s2);
+                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                    c = rsqrtf(fmaf(t, t, 1.f));
+                    sn = c * t;
+                    if (lane == 0) {
+                        atomicAdd(&rot_s, 1);
+                        atomicMax(&maxm_s, __float_as_uint((s2 * s2) / (s0 * s1)));
+                    }
+                }
+                const int nb = buf ^ 1;
+                float *tx = cl.map_shared_rank(slot(jcs, nb, 0, dt_pair & 7, dt_tb), dt_pair >> 3);
+                float *tv = cl.map_shared_rank(slot(jcs, nb, 1, dt_pair & 7, dt_tb), dt_pair >> 3);
+                float *bx = cl.map_shared_rank(slot(jcs, nb, 0, db_pair & 7, db_tb), db_pair >> 3);
+                float *bv = cl.map_shared_rank(slot(jcs, nb, 1, db_pair & 7, db_tb), db_pair >> 3);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = lane + 32 * i;
+                    if (r < P) {
+                        tx[r] = c * u[i] - sn * v[i];
+                        bx[r] = sn * u[i] + c * v[i];
+                        tv[r] = c * y[i] - sn * z[i];
+                        bv[r] = sn * y[i] + c * z[i];
+                    }
+                }
+            }
+            cl.sync();
+            buf ^= 1;
+        }
+        // sweep end: CTA 0 combines the counts of all CTAs
+        if (rank == 0 && tid == 0) {
+            int rot = 0;
+            unsigned mx = 0u;
+            for (int cta = 0; cta < JC_CL; ++cta) {
+                rot += *cl.map_shared_rank(&rot_s, cta);
+                mx = max(mx, *cl.map_shared_rank(&maxm_s, cta));
+            }
+            conv_s = (rot == 0 || __uint_as_float(mx) <= stop2) ? 1 : 0;
+        }
+        cl.sync();
+        converged = *cl.map_shared_rank(&conv_s, 0) != 0;
+        cl.sync();   // every CTA has read the decision (and CTA 0 all counts) before they are reset
+        if (tid == 0) { rot_s = 0; maxm_s = 0u; }
+        cl.sync();
+    }
+    if (b < npairs)   // V columns in slot order (any order: X0 V is all that is used)
+        for (int tb = 0; tb < 2; ++tb) {
+            const float *vs = slot(jcs, buf, 1, warp, tb);
+            for (int r = lane; r < P; r += 32) Vout[(int64_t)(2 * b + tb) * P + r] = vs[r];
+        }
+    if (rank == 0 && tid == 0) *status = converged ? sweeps : -1;
+}
+}  // namespace
+
+bool launch_jacobi_cluster_f32(cudaStream_t s, int m, const double *X0, float *Vout, double tol, int max_sweeps,
+                               int *status, double stop2, double *scale_work)
+{
+    const int P = jacobi_coop_size(m);
+    if (P == 0 || P > JC_CL * 16) return false;
+    const size_t smem = sizeof(float) * 2 * 2 * 8 * 2 * (size_t)P;   // [buf][x|v][pair][top|bottom][P]
+    static int ok = -1;
+    if (ok < 0) {
+        ok = (cudaFuncSetAttribute(k_jacobi_cluster_f32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+              cudaSuccess) ? 1 : 0;
+        cudaLaunchConfig_t q = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = JC_CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        q.gridDim = dim3(JC_CL);
+        q.blockDim = dim3(JC_THREADS);
+        q.dynamicSmemBytes = sizeof(float) * 2 * 2 * 8 * 2 * 256;
+        q.attrs = at;
+        q.numAttrs = 1;
+        int clusters = 0;
+        if (ok && (cudaOccupancyMaxActiveClusters(&clusters, k_jacobi_cluster_f32, &q) != cudaSuccess || clusters < 1))
+            ok = 0;
+        cudaGetLastError();
+    }
+    if (!ok) return false;
+    WC4D_LAUNCH(k_x0_scale<<<1, 256, 0, s>>>((int64_t)m * m, X0, scale_work));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = JC_CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(JC_CL);
+    cfg.blockDim = dim3(JC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    wc4d_note_launch();
+    if (cudaLaunchKernelEx(&cfg, k_jacobi_cluster_f32, m, P, X0, (const double *)scale_work, Vout, (float)tol,
+                           (float)stop2, max_sweeps, status) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
 }

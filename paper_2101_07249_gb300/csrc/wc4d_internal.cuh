@@ -250,6 +250,10 @@ bool launch_jacobi_coop(cudaStream_t s, int m, const double *X0, double *XV, dou
 bool launch_jacobi_coop_f32(cudaStream_t s, int m, const double *X0, float *XV32, double tol, int max_sweeps,
                             int *rot, unsigned *bar, int *err, int *status, double stop2, unsigned long long *maxm,
                             double *scale_work);
+// FP32 pre-rotation on one 16-CTA cluster; V (P x P FP32) and sweeps in *status
+// (-1: not converged).  false when the cluster launch is unavailable.
+bool launch_jacobi_cluster_f32(cudaStream_t s, int m, const double *X0, float *Vout, double tol, int max_sweeps,
+                               int *status, double stop2, double *scale_work);
 void launch_small_gemm64(cudaStream_t s, int m, const double *A, int lda, bool transA, const double *B, int ldb,
                          double *C, int ldc, double alpha, double beta);
 void launch_orthogonalise_ns(cudaStream_t s, int m, double *V, int ldv, double *tmp);
