@@ -38,7 +38,7 @@ METRIC = "inner-loop time to rel-res 1e-6 and Hessian-vec products/s, mixed vs F
 # scaled by 40/8 to the N = 40 window (traffic grows with the number of
 # subwindows).  None whenever the kernel has changed since the counters were
 # taken.
-NCU_TRAFFIC = {("gemv_sweep_f32", "advdiff_n4096_N40"): 540.44e6 * 40 / 8}
+NCU_TRAFFIC = {("gemv_sweep_f32", "advdiff_n4096_N40"): 540.49e6 * 40 / 8}
 
 # Column Hessian products one mixed inner loop issues on the large window:
 # REVD with one power iteration (3 block products of k + l = 256 columns),

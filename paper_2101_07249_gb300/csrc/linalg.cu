@@ -1284,15 +1284,34 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b(int64_t nA, int k, int kp, c
 }
 
 // Second pass over the ROW-MAJOR Ritz vectors with the first pass's split
-// (CTA b: rows [b R, b R + R), R <= PA_ROWS), walked in blocks of 64 rows
-// from the end of the range backwards so that the rows the first pass read
-// last -- still in L2 -- come first.  Phase 1, per block: thread (tx, ty)
-// takes column quad tx (kp / 4 <= 64) of rows ty, ty + 4, ... (four rows of
-// loads in flight, as in the first pass) and stores its two partial dot
-// products (with w1 and w2) in shared memory; then two threads per row sum
-// the 64 partials of each product.  Phase 2: the CTA updates its rows with
-// coalesced vector accesses, as the column-major pass does, and the last CTA
-// takes the CG beta step.
+// (CTA b: rows [b R, b R + R), R <= PA_ROWS), walked from the end of the
+// range backwards so that the rows the first pass read last -- still in L2 --
+// come first.  Each warp takes groups of RW consecutive rows on its own (no
+// CTA barrier until the range is done): lane l holds column quads l and
+// l + 32 of w1 and w2 and loads the same quads of the RW rows (2 RW loads in
+// flight per lane); the V = 2 RW row dot products are then summed over the
+// warp by a halving butterfly (V - 1 + log2(32 / V) shuffles instead of
+// 5 V).  Then the CTA updates its rows with
+// coalesced accesses, as the column-major pass does, and the last CTA takes
+// the CG beta step.
+template <int V, typename T> __device__ __forceinline__ void butterfly_sums(T (&v)[V], int lane)
+{
+    // V values per lane (V a power of two, 2 <= V <= 32); step o = 16, 8, ...
+    // sends half of the remaining values to lane l ^ o and adds the half it
+    // receives, so after log2(V) steps v[0] of lane l holds value
+    // l / (32 / V), summed over the lanes that share those high lane bits
+#pragma unroll
+    for (int h = V / 2, o = 16; h >= 1; h /= 2, o /= 2) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_lmp_pass_b_rm(int64_t nA, int kp, int64_t rows_per, const T *__restrict__ U,
                                                        const double *__restrict__ w, const double *__restrict__ scal,
@@ -1300,56 +1319,67 @@ __global__ void __launch_bounds__(256) k_lmp_pass_b_rm(int64_t nA, int kp, int64
                                                        T *x, T *r, double *part, double *scal_rw, int *flags,
                                                        unsigned *done, double tol, double *qcf_drop)
 {
-    constexpr int RB = sizeof(T) == 4 ? 64 : 32;   // rows per block (static shared memory <= 48 KB)
-    constexpr int TPS = 256 / (2 * RB);            // threads per (row, product) sum
+    constexpr int RW = sizeof(T) == 4 ? 8 : 4;   // rows per warp step (2 RW sums <= 16)
+    constexpr int V = 2 * RW;                    // sums per step: product 0 rows 0..RW-1, product 1 rows 0..RW-1
+    constexpr int NB = 32 / V;                   // lanes beyond the butterfly's reach: after log2(V) halvings
+    static_assert(V == 8 || V == 16, "butterfly width");
     __shared__ T dsum[2][PA_ROWS];
-    __shared__ T ps[2][RB][65];
     __shared__ int last;
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kq = kp / 4;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int rows = (int)max((int64_t)0, min(rows_per, nA - r0));
-    const bool hq = tx < kq;
-    Quad<T> w1{0, 0, 0, 0}, w2{0, 0, 0, 0};
-    if (hq) {
-        w1 = {(T)w[4 * tx], (T)w[4 * tx + 1], (T)w[4 * tx + 2], (T)w[4 * tx + 3]};
-        w2 = {(T)w[kp + 4 * tx], (T)w[kp + 4 * tx + 1], (T)w[kp + 4 * tx + 2], (T)w[kp + 4 * tx + 3]};
+    const bool h0 = lane < kq, h1 = lane + 32 < kq;
+    const Quad<T> z{0, 0, 0, 0};
+    Quad<T> w1a = z, w1b = z, w2a = z, w2b = z;
+    if (h0) {
+        w1a = {(T)w[4 * lane], (T)w[4 * lane + 1], (T)w[4 * lane + 2], (T)w[4 * lane + 3]};
+        w2a = {(T)w[kp + 4 * lane], (T)w[kp + 4 * lane + 1], (T)w[kp + 4 * lane + 2], (T)w[kp + 4 * lane + 3]};
     }
-    for (int hi = rows; hi > 0; hi -= RB) {
-        const int lo = max(0, hi - RB);   // block rows [lo, hi)
-        const T *base = U + (r0 + lo) * kp + 4 * tx;
-#pragma unroll
-        for (int rr = 0; rr < RB; rr += 16) {   // four rows of loads in flight per thread
-            Quad<T> u[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int rl = rr + ty + 4 * h;
-                u[h] = (hq && lo + rl < hi) ? ld4cs(base + (int64_t)rl * kp) : Quad<T>{0, 0, 0, 0};
-            }
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int rl = rr + ty + 4 * h;
-                T a = u[h].x * w1.x, b = u[h].x * w2.x;
-                a = fma(u[h].y, w1.y, a); b = fma(u[h].y, w2.y, b);
-                a = fma(u[h].z, w1.z, a); b = fma(u[h].z, w2.z, b);
-                a = fma(u[h].w, w1.w, a); b = fma(u[h].w, w2.w, b);
-                ps[0][rl][tx] = a;
-                ps[1][rl][tx] = b;
-            }
-        }
-        __syncthreads();
-        {   // TPS consecutive threads sum product sid / RB of row sid % RB
-            const int sid = threadIdx.x / TPS, part_i = threadIdx.x % TPS;
-            const int which = sid / RB, rl = sid % RB;
-            T acc = 0;
-#pragma unroll 8
-            for (int c = part_i * (64 / TPS); c < (part_i + 1) * (64 / TPS); ++c) acc += ps[which][rl][c];
-#pragma unroll
-            for (int o = 1; o < TPS; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (part_i == 0 && lo + rl < hi) dsum[which][lo + rl] = acc;
-        }
-        __syncthreads();
+    if (h1) {
+        const int c = 4 * (lane + 32);
+        w1b = {(T)w[c], (T)w[c + 1], (T)w[c + 2], (T)w[c + 3]};
+        w2b = {(T)w[kp + c], (T)w[kp + c + 1], (T)w[kp + c + 2], (T)w[kp + c + 3]};
     }
+    const int ngroups = (rows + RW - 1) / RW;
+    for (int gi = warp; gi < ngroups; gi += 8) {
+        const int hi = rows - RW * gi;   // rows hi - RW .. hi - 1 (those >= 0)
+        Quad<T> ua[RW], ub[RW];
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+            const int rl = hi - 1 - h;
+            const T *row = U + (r0 + max(rl, 0)) * kp;
+            ua[h] = (rl >= 0 && h0) ? ld4cs(row + 4 * lane) : z;
+            ub[h] = (rl >= 0 && h1) ? ld4cs(row + 4 * (lane + 32)) : z;
+        }
+        T v[V];
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+            T a = ua[h].x * w1a.x, b = ua[h].x * w2a.x;
+            a = fma(ua[h].y, w1a.y, a); b = fma(ua[h].y, w2a.y, b);
+            a = fma(ua[h].z, w1a.z, a); b = fma(ua[h].z, w2a.z, b);
+            a = fma(ua[h].w, w1a.w, a); b = fma(ua[h].w, w2a.w, b);
+            a = fma(ub[h].x, w1b.x, a); b = fma(ub[h].x, w2b.x, b);
+            a = fma(ub[h].y, w1b.y, a); b = fma(ub[h].y, w2b.y, b);
+            a = fma(ub[h].z, w1b.z, a); b = fma(ub[h].z, w2b.z, b);
+            a = fma(ub[h].w, w1b.w, a); b = fma(ub[h].w, w2b.w, b);
+            v[h] = a;
+            v[RW + h] = b;
+        }
+        butterfly_sums<V>(v, lane);
+        // after log2(V) halvings over lane bits 4, 3, ...: value index from
+        // those bits, most significant first; the remaining low lane bits
+        // hold partial sums of the same value
+#pragma unroll
+        for (int o = NB / 2; o >= 1; o /= 2) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        if ((lane & (NB - 1)) == 0) {
+            const int idx = lane / NB;   // 0 .. V-1
+            const int which = idx / RW, h = idx % RW;
+            const int rl = hi - 1 - h;
+            if (rl >= 0) dsum[which][rl] = v[0];
+        }
+    }
+    __syncthreads();
     const double alpha = scal[1];
     double srh = 0.0, sr = 0.0;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {

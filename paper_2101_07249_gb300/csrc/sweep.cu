@@ -364,11 +364,22 @@ k_circ_stockham(int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_
     T *yb = Y + jb * ldy + tb * n;
     const T *aa = addX ? addX + ja * ld_add + ta * n : nullptr;
     const T *ab = addX ? addX + jb * ld_add + tb * n : nullptr;
+    // the added vectors are read into registers before any store: Y may
+    // alias them as far as the compiler knows, which would otherwise
+    // serialise one global load latency per value
+    T ra[16], rb[16];
 #pragma unroll
-    for (int s = tid; s < n; s += nt) {
+    for (int i = 0; i < 16; ++i) {
+        const int s = tid + i * nt;
+        ra[i] = aa ? aa[s] : (T)0;
+        rb[i] = (hasb && ab) ? ab[s] : (T)0;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int s = tid + i * nt;
         const CT v = buf[fpad(s)];
-        ya[s] = v.x + (aa ? aa[s] : (T)0);
-        if (hasb) yb[s] = -v.y + (ab ? ab[s] : (T)0);
+        ya[s] = v.x + ra[i];
+        if (hasb) yb[s] = -v.y + rb[i];
     }
 }
 
@@ -643,6 +654,7 @@ struct SweepArgs {
     double obs_inv;       // 1 / sigma_o^2
     int obs_stride, t0, ts;
     int rows_per_cta;     // multiple of 2
+    int pf;               // staged form: stages prefetched into L2 ahead of the ring
     unsigned *bar;        // N zeroed arrival counters, one per step barrier
     int *err;
 };
@@ -754,18 +766,22 @@ k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
 // arrive on the slot's "empty" mbarrier and the producer refills it.  The
 // producer is not part of the grid barrier: it runs SW_NS stages ahead across
 // subwindow boundaries (the rows of M_{t+1} do not depend on x), so the copy
-// engine keeps streaming while the consumers wait for x_{t+1}.  Row sums: warp
-// shuffle, then the 16 warp partials in a fixed order.  All waits are
-// bounded; after a grid-barrier timeout the consumers keep draining the ring
-// (without further barriers) so that no copy is in flight when the CTA exits.
-// Measured on GB300 (n = 4096, N = 40, 2.7 GB of propagators): 448 us per
-// sweep against 491 us for per-thread cp.async staging and 533 us for the
+// engine keeps streaming while the consumers wait for x_{t+1}; once the ring
+// is full it prefetches a few further rows into L2, so that HBM does not
+// idle during the grid barrier either.  Row sums: warp shuffle, then the 16
+// warp partials in a fixed order.  All waits are bounded; after a
+// grid-barrier timeout the consumers keep draining the ring (without further
+// barriers) so that no copy is in flight when the CTA exits.  Measured on
+// GB300 (n = 4096, N = 40, 2.7 GB of propagators): 411 us per sweep with an
+// L2 look-ahead of 2 to 8 rows (447 us without, 434 us at 16 rows, 734 us at
+// 32) against 491 us for per-thread cp.async staging and 533 us for the
 // register-staged k_gemv_sweep.
 // ----------------------------------------------------------------------------
 constexpr int SW_THREADS = 512;                       // consumer threads
 constexpr int SW_RING = 192 * 1024;                   // bytes of shared memory in the ring
 constexpr int SW_RMAX = 64;                           // rows per CTA
 constexpr unsigned SW_WAIT = 1u << 22;                // mbarrier polls before giving up
+constexpr int SW_PF = 4;                              // default L2 look-ahead, stages
 
 template <int J> struct SwShape {
     static constexpr int G = J == 1 ? 2 : 1;                          // rows per stage
@@ -802,6 +818,11 @@ __device__ __forceinline__ void sw_bulk_g2s(uint32_t dst, const void *src, unsig
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(mb)
                  : "memory");
+}
+// bulk prefetch of global memory into L2 (no completion, no shared memory)
+__device__ __forceinline__ void sw_prefetch_l2(const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 // barrier of the 512 consumer threads only (the producer warp is not in it)
 __device__ __forceinline__ void sw_cbar() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
@@ -868,16 +889,35 @@ __global__ void __launch_bounds__(SW_THREADS + 32, 1) k_gemv_sweep_staged(const 
 
     if (warp == SW_THREADS / 32) {   // producer warp: one thread issues
         if (lane == 0) {
+            // rows of stage kk: M_t rows [rbeg + s0, rbeg + s0 + rows)
+            auto stage_rows = [&](int kk, int &rows) -> const float * {
+                const int step = kk / S, s0 = (kk % S) * G;
+                rows = min(G, R - s0);
+                const int t = (a.mode == 0) ? step : a.N - 1 - step;
+                return M0 + (int64_t)t * a.mstride + (int64_t)(rbeg + s0) * n;
+            };
+            // L2 look-ahead: stage k + pf is prefetched when stage k is
+            // copied, so HBM keeps streaming while the ring is full (during
+            // the grid barrier and the read of x_{t+1}); stages the ring
+            // takes straight away need none
+            for (int kk = NS; kk < min(a.pf, total); ++kk) {
+                int pr;
+                const float *P = stage_rows(kk, pr);
+                sw_prefetch_l2(P, rowb * (unsigned)pr);
+            }
             for (int k = 0; k < total; ++k) {
                 const int slot = k % NS;
+                if (a.pf > 0 && k + a.pf < total && k + a.pf >= NS) {
+                    int pr;
+                    const float *P = stage_rows(k + a.pf, pr);
+                    sw_prefetch_l2(P, rowb * (unsigned)pr);
+                }
                 if (k >= NS && !sw_mb_wait(mb + 8 * (NS + slot), ((k / NS) - 1) & 1)) {
                     atomicExch(a.err, 3);
                     break;
                 }
-                const int step = k / S, s0 = (k % S) * G;
-                const int rows = min(G, R - s0);
-                const int t = (a.mode == 0) ? step : a.N - 1 - step;
-                const float *M = M0 + (int64_t)t * a.mstride + (int64_t)(rbeg + s0) * n;
+                int rows;
+                const float *M = stage_rows(k, rows);
                 sw_mb_expect(mb + 8 * slot, rowb * (unsigned)rows);
                 for (int g = 0; g < rows; ++g)
                     sw_bulk_g2s(ring_s + (uint32_t)(slot * G + g) * rowb, M + (int64_t)g * n, rowb, mb + 8 * slot);
@@ -963,6 +1003,11 @@ static bool launch_sweep_staged(cudaStream_t s, int num_sms, const float *M0, fl
     const int rpc = ceil_div(n, num_sms);
     if (rpc > SW_RMAX) return false;
     args.rows_per_cta = rpc;
+    static const int pf = [] {
+        const char *e = getenv("WC4D_SWEEP_PF");
+        return e ? std::max(0, atoi(e)) : SW_PF;
+    }();
+    args.pf = pf;
     const int grid = ceil_div(n, rpc);
     void *params[] = {(void *)&M0, (void *)&W, (void *)&args};
     wc4d_note_launch();
@@ -998,6 +1043,7 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     SweepArgs args;
     args.n = n;
     args.N = N;
+    args.pf = 0;
     args.mstride = mstride;
     args.mode = mode;
     args.obs_inv = obs_inv;
