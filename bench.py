@@ -474,7 +474,8 @@ def main():
     ev1.record()
     torch.cuda.synchronize()
     profiled_ms = ev0.elapsed_time(ev1)
-    jacobi_sweeps = {"fp32": w.wc4d_jacobi_sweeps_fp32(ctx), "fp64": w.wc4d_jacobi_sweeps(ctx)}
+    jacobi_sweeps = {"fp32": w.wc4d_jacobi_sweeps_fp32(ctx), "fp64": w.wc4d_jacobi_sweeps(ctx),
+                     "fp32_kernel": {0: None, 1: "cluster16", 2: "cooperative"}.get(w.wc4d_jacobi_fp32_kernel(ctx))}
     classes = {}
     for ci, name in enumerate(w.PROF_CLASSES):
         ms, cnt = w.wc4d_profile_read(ctx, ci)

@@ -318,6 +318,11 @@ int32_t     wc4d_jacobi_sweeps(const wc4d_ctx *ctx);
 /* FP32 pre-rotation sweeps that preceded the last FP64 eigensolve of an SPD
    matrix (0 when none ran; negative when it stopped at its sweep limit). */
 int32_t     wc4d_jacobi_sweeps_fp32(const wc4d_ctx *ctx);
+/* Which kernel ran those FP32 sweeps: 1 = one 16-CTA thread-block cluster
+   (distributed shared memory), 2 = the cooperative whole-grid form (used when
+   the device cannot co-schedule such a cluster), 0 = none; -1 for a null
+   context. */
+int32_t     wc4d_jacobi_fp32_kernel(const wc4d_ctx *ctx);
 /* CUDA-graph replay of the CG iteration (default on): after one eager
    iteration, the body of Alg. 1's loop (the product with A, the LMP step and
    the direction update) is captured once per solve and replayed; the

@@ -80,6 +80,7 @@ _SIGS = {
     "wc4d_hvp_count": (C.c_int64, [_V, C.c_int32]),
     "wc4d_jacobi_sweeps": (C.c_int32, [_V]),
     "wc4d_jacobi_sweeps_fp32": (C.c_int32, [_V]),
+    "wc4d_jacobi_fp32_kernel": (C.c_int32, [_V]),
     "wc4d_lanczos_cg": (C.c_int32, [_V, _V, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
                                     C.POINTER(C.c_double)]),
     "wc4d_lanczos_tridiag": (C.c_int32, [_V, _V, _V]),
@@ -395,6 +396,11 @@ def wc4d_jacobi_sweeps(ctx):
 
 def wc4d_jacobi_sweeps_fp32(ctx):
     return int(load().wc4d_jacobi_sweeps_fp32(ctx))
+
+
+def wc4d_jacobi_fp32_kernel(ctx):
+    """1 = one 16-CTA cluster, 2 = cooperative grid, 0 = no FP32 phase."""
+    return int(load().wc4d_jacobi_fp32_kernel(ctx))
 
 
 def wc4d_set_graphs(ctx, enable):

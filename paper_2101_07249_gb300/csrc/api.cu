@@ -351,6 +351,7 @@ extern "C" wc4d_status wc4d_profile_read(wc4d_ctx *c, int32_t cls, double *total
 
 extern "C" int32_t wc4d_jacobi_sweeps(const wc4d_ctx *c) { return c ? c->jacobi_sweeps : -1; }
 extern "C" int32_t wc4d_jacobi_sweeps_fp32(const wc4d_ctx *c) { return c ? c->jacobi_sweeps32 : -1; }
+extern "C" int32_t wc4d_jacobi_fp32_kernel(const wc4d_ctx *c) { return c ? c->jacobi_kernel32 : -1; }
 
 extern "C" wc4d_status wc4d_set_reliable_delta(wc4d_ctx *c, double delta)
 {
@@ -939,6 +940,7 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
     const int mp = m + (m & 1);
     const double tol = 4.0 * 2.220446049250313e-16 * std::sqrt((double)mp);
     c->jacobi_sweeps32 = 0;
+    c->jacobi_kernel32 = 0;
     if (const int Pq = c->allow_coop ? jacobi_coop_size(m) : 0) {
         // Without V (the left singular vectors only): an FP32 pre-rotation
         // phase first.  One-sided Jacobi in FP32 (about 1.6 FP64 operations
@@ -970,6 +972,7 @@ static wc4d_status jacobi_run(wc4d_ctx *c, int m, const double *X0, double **Xo,
                     WC4D_CUDA(c, cudaMemcpyAsync(h, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
                     WC4D_TRY(sync(c, "jacobi fp32 phase"));
                     if (h[0] == 0) {
+                        c->jacobi_kernel32 = on_cluster ? 1 : 2;
                         launch_convert_f32_f64(c->stream, (int64_t)P2, XV32 + P2, V64);     // V (ld P)
                         launch_orthogonalise_ns(c->stream, m, V64, Pq, tmp);
                         launch_small_gemm64(c->stream, m, X0, m, false, V64, Pq, X1, m, 1.0, 0.0);   // X0 V

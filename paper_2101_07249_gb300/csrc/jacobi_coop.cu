@@ -356,8 +356,8 @@ void launch_orthogonalise_ns(cudaStream_t s, int m, double *V, int ldv, double *
 // the next round (the ordering shifts the columns one position: the first
 // column of pair b moves to pair b - 1, the second to pair b + 1, with the
 // turn-arounds at both ends), a remote store only across a CTA boundary.
-// Double-buffered slots and one cluster barrier per round.  The columns end
-// in some order, which does not matter: only X0 V with V orthogonal is used.
+// Double-buffered slots and one cluster barrier per round; a whole sweep
+// brings every column back to its starting slot.
 // Sweeps stop when a sweep's largest rotation has cos^2 <= stop2, makes no
 // rotation at tol, or after max_sweeps.  Output: V (P x P, FP32).
 // ----------------------------------------------------------------------------
@@ -476,10 +476,15 @@ k_jacobi_cluster_f32(int m, int P, const double *__restrict__ X0, const double *
         if (tid == 0) { rot_s = 0; maxm_s = 0u; }
         cl.sync();
     }
-    if (b < npairs)   // V columns in slot order (any order: X0 V is all that is used)
+    // after each whole sweep (P - 1 rounds) every column is back in the slot
+    // it started in, so V is written in column order -- which matters: the
+    // caller uses the leading m x m block of V, and for odd m column P - 1 is
+    // the zero padding column
+    if (b < npairs)
         for (int tb = 0; tb < 2; ++tb) {
             const float *vs = slot(jcs, buf, 1, warp, tb);
-            for (int r = lane; r < P; r += 32) Vout[(int64_t)(2 * b + tb) * P + r] = vs[r];
+            const int j = tb == 0 ? b : P - 1 - b;
+            for (int r = lane; r < P; r += 32) Vout[(int64_t)j * P + r] = vs[r];
         }
     if (rank == 0 && tid == 0) *status = converged ? sweeps : -1;
 }
@@ -493,8 +498,11 @@ bool launch_jacobi_cluster_f32(cudaStream_t s, int m, const double *X0, float *V
     const size_t smem = sizeof(float) * 2 * 2 * 8 * 2 * (size_t)P;   // [buf][x|v][pair][top|bottom][P]
     static int ok = -1;
     if (ok < 0) {
+        const int smem_max = (int)(sizeof(float) * 2 * 2 * 8 * 2 * 256);   // 64 KB: above the default 48 KB
         ok = (cudaFuncSetAttribute(k_jacobi_cluster_f32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-              cudaSuccess) ? 1 : 0;
+                  cudaSuccess &&
+              cudaFuncSetAttribute(k_jacobi_cluster_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) ==
+                  cudaSuccess) ? 1 : 0;
         cudaLaunchConfig_t q = {};
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;

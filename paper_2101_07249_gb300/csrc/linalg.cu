@@ -423,32 +423,52 @@ void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *i
 // float); k_scale_pow2 then multiplies Y by 2^-e (exact) when max |Y| lies
 // outside [2^-24, 2^24] and records e; k_scale_R_pow2 multiplies R by 2^e, so
 // that (2^-e Y)(2^-e R)^{-1} = Y R^{-1}.
-__global__ void __launch_bounds__(256) k_absmax_f32(int64_t rows, int m, int64_t ld, const float *Y, unsigned *mx)
+// Both take column blockIdx.y with a grid-stride loop over its rows (16-byte
+// accesses when the columns allow them), so no index division per element.
+__device__ __forceinline__ bool cols_vec4(int64_t rows, int64_t ld, const float *Y)
+{
+    return (rows & 3) == 0 && (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
+}
+
+__global__ void __launch_bounds__(256) k_absmax_f32(int64_t rows, int64_t ld, const float *Y, unsigned *mx)
 {
     float v = 0.f;
-    const int64_t tot = rows * m;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / rows, r = i - j * rows;
-        v = fmaxf(v, fabsf(Y[j * ld + r]));
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    const float *col = Y + (int64_t)blockIdx.y * ld;
+    if (cols_vec4(rows, ld, Y)) {
+        const float4 *c = reinterpret_cast<const float4 *>(col);
+        for (int64_t i = t0; i < rows / 4; i += st) {
+            const float4 q = __ldcg(c + i);
+            v = fmaxf(v, fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(q.z), fabsf(q.w))));
+        }
+    } else {
+        for (int64_t i = t0; i < rows; i += st) v = fmaxf(v, fabsf(col[i]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomicMax(mx, __float_as_uint(v));
 }
 
-__global__ void __launch_bounds__(256) k_scale_pow2(int64_t rows, int m, int64_t ld, float *Y, const unsigned *mx,
+__global__ void __launch_bounds__(256) k_scale_pow2(int64_t rows, int64_t ld, float *Y, const unsigned *mx,
                                                     int *e_out)
 {
     const float v = __uint_as_float(*mx);
     int e = 0;
     if (v > 0.f && isfinite(v) && (v > 0x1p24f || v < 0x1p-24f)) e = ilogbf(v);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *e_out = e;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *e_out = e;
     if (e == 0) return;
     const float sc = scalbnf(1.f, -e);
-    const int64_t tot = rows * m;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / rows, r = i - j * rows;
-        Y[j * ld + r] *= sc;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    float *col = Y + (int64_t)blockIdx.y * ld;
+    if (cols_vec4(rows, ld, Y)) {
+        float4 *c = reinterpret_cast<float4 *>(col);
+        for (int64_t i = t0; i < rows / 4; i += st) {
+            float4 q = c[i];
+            q.x *= sc; q.y *= sc; q.z *= sc; q.w *= sc;
+            c[i] = q;
+        }
+    } else {
+        for (int64_t i = t0; i < rows; i += st) col[i] *= sc;
     }
 }
 
@@ -464,9 +484,10 @@ __global__ void k_scale_R_pow2(int m, double *R, const int *e)
 void launch_range_scale_f32(cudaStream_t s, int num_sms, int64_t rows, int m, int64_t ld, float *Y, unsigned *work)
 {
     cudaMemsetAsync(work, 0, sizeof(unsigned), s);
-    const int grid = 4 * num_sms;
-    WC4D_LAUNCH(k_absmax_f32<<<grid, 256, 0, s>>>(rows, m, ld, Y, work));
-    WC4D_LAUNCH(k_scale_pow2<<<grid, 256, 0, s>>>(rows, m, ld, Y, work, reinterpret_cast<int *>(work + 1)));
+    // columns on grid.y; about four 16-byte loads per thread along a column
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 4096), 4 * num_sms)), (unsigned)m);
+    WC4D_LAUNCH(k_absmax_f32<<<grid, 256, 0, s>>>(rows, ld, Y, work));
+    WC4D_LAUNCH(k_scale_pow2<<<grid, 256, 0, s>>>(rows, ld, Y, work, reinterpret_cast<int *>(work + 1)));
 }
 
 void launch_unscale_R(cudaStream_t s, int m, double *R, const unsigned *work)

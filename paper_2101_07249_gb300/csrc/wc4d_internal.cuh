@@ -139,6 +139,7 @@ struct wc4d_ctx {
     double jacobi_stop2 = 0.0;      // early stop of the small eigensolves (0: run to a sweep without rotations)
     int jacobi_sweeps = 0;          // sweeps used by the last one
     int jacobi_sweeps32 = 0;        // FP32 pre-rotation sweeps before it (0: none)
+    int jacobi_kernel32 = 0;        // its kernel: 1 one 16-CTA cluster, 2 cooperative grid (0: none)
     DevBuf jq32;                    // FP32 pre-rotation workspace
     bool allow_coop = true;
     bool prof_on = false;

@@ -225,6 +225,12 @@ def test_mixed_sketch_eigensolve_stops_early(method):
     s32 = w.wc4d_jacobi_sweeps(S.ctx)
     th32 = w.wc4d_get_ritz(S.ctx, U, cfg.k)
     assert 1 <= s32 <= s64 <= 60
+    # the FP32 pre-rotation (eigensolves of SPD matrices from their Cholesky
+    # factor: not ritzit's SVD of R_3) ran on one 16-CTA cluster (a GB300
+    # schedules clusters of 16 with 64 KB of shared memory each)
+    if method != "ritzit":
+        assert w.wc4d_jacobi_sweeps_fp32(S.ctx) != 0
+        assert w.wc4d_jacobi_fp32_kernel(S.ctx) == 1
     assert np.allclose(th32, th64, rtol=1e-3)
     Ug = host(U)
     assert np.abs(Ug @ Ug.T - np.eye(cfg.k)).max() < 1e-4
