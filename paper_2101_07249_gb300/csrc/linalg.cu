@@ -446,7 +446,14 @@ __global__ void __launch_bounds__(256) k_absmax_f32(int64_t rows, int64_t ld, co
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(mx, __float_as_uint(v));
+    // one atomic per CTA: thousands of same-address atomics would serialise
+    __shared__ float wmax[8];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) v = fmaxf(v, wmax[i]);
+        atomicMax(mx, __float_as_uint(v));
+    }
 }
 
 __global__ void __launch_bounds__(256) k_scale_pow2(int64_t rows, int64_t ld, float *Y, const unsigned *mx,
@@ -484,8 +491,8 @@ __global__ void k_scale_R_pow2(int m, double *R, const int *e)
 void launch_range_scale_f32(cudaStream_t s, int num_sms, int64_t rows, int m, int64_t ld, float *Y, unsigned *work)
 {
     cudaMemsetAsync(work, 0, sizeof(unsigned), s);
-    // columns on grid.y; about four 16-byte loads per thread along a column
-    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 4096), 4 * num_sms)), (unsigned)m);
+    // columns on grid.y; about sixteen 16-byte loads per thread along a column
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 16384), 4 * num_sms)), (unsigned)m);
     WC4D_LAUNCH(k_absmax_f32<<<grid, 256, 0, s>>>(rows, ld, Y, work));
     WC4D_LAUNCH(k_scale_pow2<<<grid, 256, 0, s>>>(rows, ld, Y, work, reinterpret_cast<int *>(work + 1)));
 }
