@@ -496,13 +496,15 @@ bool launch_jacobi_cluster_f32(cudaStream_t s, int m, const double *X0, float *V
     const int P = jacobi_coop_size(m);
     if (P == 0 || P > JC_CL * 16) return false;
     const size_t smem = sizeof(float) * 2 * 2 * 8 * 2 * (size_t)P;   // [buf][x|v][pair][top|bottom][P]
-    static int ok = -1;
-    if (ok < 0) {
+    // once (a function-local static is initialised once even when host
+    // threads launch concurrently): attributes, then whether one 16-CTA
+    // cluster with 64 KB of shared memory per CTA can be scheduled
+    static const bool ok = [] {
         const int smem_max = (int)(sizeof(float) * 2 * 2 * 8 * 2 * 256);   // 64 KB: above the default 48 KB
-        ok = (cudaFuncSetAttribute(k_jacobi_cluster_f32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                  cudaSuccess &&
-              cudaFuncSetAttribute(k_jacobi_cluster_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) ==
-                  cudaSuccess) ? 1 : 0;
+        bool r = cudaFuncSetAttribute(k_jacobi_cluster_f32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                     cudaSuccess &&
+                 cudaFuncSetAttribute(k_jacobi_cluster_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) ==
+                     cudaSuccess;
         cudaLaunchConfig_t q = {};
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -511,14 +513,15 @@ bool launch_jacobi_cluster_f32(cudaStream_t s, int m, const double *X0, float *V
         at[0].val.clusterDim.z = 1;
         q.gridDim = dim3(JC_CL);
         q.blockDim = dim3(JC_THREADS);
-        q.dynamicSmemBytes = sizeof(float) * 2 * 2 * 8 * 2 * 256;
+        q.dynamicSmemBytes = smem_max;
         q.attrs = at;
         q.numAttrs = 1;
         int clusters = 0;
-        if (ok && (cudaOccupancyMaxActiveClusters(&clusters, k_jacobi_cluster_f32, &q) != cudaSuccess || clusters < 1))
-            ok = 0;
+        if (r && (cudaOccupancyMaxActiveClusters(&clusters, k_jacobi_cluster_f32, &q) != cudaSuccess || clusters < 1))
+            r = false;
         cudaGetLastError();
-    }
+        return r;
+    }();
     if (!ok) return false;
     WC4D_LAUNCH(k_x0_scale<<<1, 256, 0, s>>>((int64_t)m * m, X0, scale_work));
     cudaLaunchConfig_t cfg = {};

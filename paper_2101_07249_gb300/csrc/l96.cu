@@ -293,12 +293,11 @@ template <typename T>
 void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
                           int64_t ld)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_l96_tlm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
-        attr = true;
-    }
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_l96_tlm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(3 * WC4D_FFT_MAX_N * sizeof(T))) == cudaSuccess;
+    }();   // once, thread-safe
+    (void)attr;
     if (use_cluster(n, K)) {
         WC4D_LAUNCH(k_l96_tlm_cl<T><<<K * L96_CL, 1024, 3 * (size_t)(n / L96_CL) * sizeof(T), s>>>(n, N, steps, (T)dt,
                                                                                                  stages, W, ld));
@@ -311,12 +310,11 @@ template <typename T>
 void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
                           int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_l96_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(3 * WC4D_FFT_MAX_N * sizeof(T)));
-        attr = true;
-    }
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_l96_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(3 * WC4D_FFT_MAX_N * sizeof(T))) == cudaSuccess;
+    }();   // once, thread-safe
+    (void)attr;
     if (use_cluster(n, K)) {
         WC4D_LAUNCH(k_l96_adj_cl<T><<<K * L96_CL, 1024, 3 * (size_t)(n / L96_CL) * sizeof(T), s>>>(
             n, N, steps, (T)dt, stages, W, ld, obs_mode, (T)obs_scale, obs_stride, obs_t0,
@@ -405,12 +403,11 @@ __global__ void __launch_bounds__(1024) k_l96_run(int n, int nsteps, double F, d
 void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages,
                     const double *eta, int steps)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_l96_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * WC4D_FFT_MAX_N * sizeof(double)));
-        attr = true;
-    }
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_l96_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(2 * WC4D_FFT_MAX_N * sizeof(double))) == cudaSuccess;
+    }();   // once, thread-safe
+    (void)attr;
     WC4D_LAUNCH(k_l96_run<<<1, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, nsteps, F, dt, traj, stages, eta,
                                                                            steps));
 }

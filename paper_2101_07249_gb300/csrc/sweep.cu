@@ -388,11 +388,13 @@ static void launch_stockham(cudaStream_t s, int grid, size_t smem, int N, int K,
                             int64_t ldy, const T *addX, int64_t ld_add, const T *specB, const T *specQ,
                             const void *tw, int nB)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_circ_stockham<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // once per instantiation (smem is fixed by T and LOGN); a function-local
+    // static is initialised once even when host threads launch concurrently
+    static const bool attr = [smem] {
+        return cudaFuncSetAttribute(k_circ_stockham<T, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem) == cudaSuccess;
+    }();
+    (void)attr;
     WC4D_LAUNCH(k_circ_stockham<T, LOGN><<<grid, (1 << LOGN) / 16, smem, s>>>(
         N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, (const typename Cplx<T>::t *)tw, nB));
 }
@@ -433,13 +435,12 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
     const int n = c->prob.n, N = c->prob.N;
     if (fft) {
         size_t smem = (size_t)(n + n / 16 + n / 2) * sizeof(typename Cplx<T>::t);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_circ_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((WC4D_FFT_MAX_N + WC4D_FFT_MAX_N / 16 + WC4D_FFT_MAX_N / 2) *
-                                       sizeof(typename Cplx<T>::t)));
-            attr = true;
-        }
+        static const bool attr = [] {
+            return cudaFuncSetAttribute(k_circ_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((WC4D_FFT_MAX_N + WC4D_FFT_MAX_N / 16 + WC4D_FFT_MAX_N / 2) *
+                                              sizeof(typename Cplx<T>::t))) == cudaSuccess;
+        }();
+        (void)attr;
         int nB = (K + 1) / 2;
         int64_t nQ = ((int64_t)K * N + 1) / 2;
         int grid = (int)(nB + nQ);
@@ -455,12 +456,11 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
                                               (const typename Cplx<T>::t *)tw, nB));
     } else {
         size_t smem = 2 * (size_t)n * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_circ_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * WC4D_FFT_MAX_N * sizeof(T)));
-            attr = true;
-        }
+        static const bool attr = [] {
+            return cudaFuncSetAttribute(k_circ_direct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(2 * WC4D_FFT_MAX_N * sizeof(T))) == cudaSuccess;
+        }();
+        (void)attr;
         int64_t grid = (int64_t)K * (N + 1);
         WC4D_LAUNCH(k_circ_direct<T><<<(unsigned)grid, 256, smem, s>>>(n, N, K, X, ldx, Y, ldy, addX, ld_add, rowB, rowQ));
     }
@@ -990,14 +990,15 @@ static bool launch_sweep_staged(cudaStream_t s, int num_sms, const float *M0, fl
 {
     const void *fn = (const void *)k_gemv_sweep_staged<J>;
     const int smem = SwShape<J>::NS * SwShape<J>::G * J * SW_THREADS * 16;
-    static int st = -1;
-    if (st < 0) {
+    static const bool st = [fn, smem] {
         int per_sm = 0;
-        st = (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
-              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SW_THREADS + 32, smem) == cudaSuccess &&
-              per_sm >= 1) ? 1 : 0;
+        const bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SW_THREADS + 32, smem) ==
+                            cudaSuccess &&
+                        per_sm >= 1;
         cudaGetLastError();
-    }
+        return ok;
+    }();
     if (!st) return false;
     const int n = args.n;
     const int rpc = ceil_div(n, num_sms);
@@ -1029,15 +1030,13 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     using Acc = T;
     const bool keep = (mstride == 0 && N > 1);
     const void *fn = keep ? (const void *)k_gemv_sweep<T, Acc, true> : (const void *)k_gemv_sweep<T, Acc, false>;
-    static int max_blocks = -1;
-    int &mb = max_blocks;
-    if (mb < 0) {
+    static const int mb = [num_sms] {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_sweep<T, Acc, false>, 512, 0);
         int per_sm_keep = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_keep, k_gemv_sweep<T, Acc, true>, 512, 0);
-        mb = std::min(per_sm, per_sm_keep) * num_sms;
-    }
+        return std::min(per_sm, per_sm_keep) * num_sms;
+    }();
     int grid = std::min(num_sms, mb);
     if (grid < 1) return false;
     SweepArgs args;
