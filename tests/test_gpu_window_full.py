@@ -1,0 +1,64 @@
+"""The benchmark's own workload at full size -- advection-diffusion, n = 4096,
+N = 40 (n_A = 167 936), one propagator per subwindow, REVD with q = 1 and
+k + l = 256 probe columns, CG to relative residual 1e-6: the launch
+configuration the benchmark times (persistent staged sweeps, tensor-core
+sketch products, cluster eigensolve).  The oracle cannot run this inner loop,
+but it can compute what is checked here one Hessian product at a time, in
+FP64 with Crank-Nicolson stepping (a different route from the library's
+propagator matrices): the innovations, the right-hand side and the true
+residual of the returned solution (Alg. 1's stopping rule), and the Rayleigh
+quotients of sampled Ritz vectors, which equal their Ritz values for
+Rayleigh-Ritz (Alg. 3)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_07249_gb300 import inputs
+from problems import oracle_problem
+
+torch = pytest.importorskip("torch")
+w = pytest.importorskip("paper_2101_07249_gb300")
+pytestmark = pytest.mark.gpu
+
+_state = {}
+
+
+def setup():
+    if not _state:
+        cfg = inputs.LARGE
+        tw = inputs.twin(cfg)
+        S = w.Solver(cfg, tw, M_shared=False)
+        p = oracle_problem(cfg, mode="stepping")
+        b = oracle.rhs(p, oracle.innovation(p, tw.xb, tw.y))
+        _state.update(cfg=cfg, S=S, p=p, b=b)
+    return _state["cfg"], _state["S"], _state["p"], _state["b"]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_window_inner_loop_meets_tolerance_by_the_oracle(precision):
+    cfg, S, p, b = setup()
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    prec = w.MIXED if precision == "mixed" else w.FP64
+    it, rel = w.wc4d_inner_loop(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 7, cfg.tol, cfg.maxit, prec, x)
+    assert 0 < it < 300 and rel <= cfg.tol
+    r = b - oracle.hvp(p, x.cpu().numpy()[None, :])[0]
+    # the two FP64 operators differ by ~1e-12 relative (propagator matrix
+    # against stepping), i.e. by at most ~1e-8 of |b| in the residual
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05 * cfg.tol
+
+
+def test_full_window_ritz_pairs_by_the_oracle():
+    cfg, S, p, _ = setup()
+    w.wc4d_sketch(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 11, None, w.MIXED)
+    U = torch.zeros(cfg.k, cfg.nA, dtype=torch.float64, device="cuda")
+    th = np.asarray(w.wc4d_get_ritz(S.ctx, U, cfg.k))
+    assert np.all(np.diff(th) <= 0)
+    assert th[-1] > 0.99                     # Ritz values of A >= I (TF32 products: ~1e-4 errors)
+    idx = [0, 1, 2, cfg.k // 2, cfg.k - 1]
+    Us = U[idx].cpu().numpy()
+    assert np.abs(Us @ Us.T - np.eye(len(idx))).max() < 1e-4
+    AU = oracle.hvp(p, Us)
+    rq = np.sum(Us * AU, axis=1) / np.sum(Us * Us, axis=1)
+    # theta_i = u_i^T A u_i for Rayleigh-Ritz; the mixed sketch forms
+    # Z^T (A Z) from TF32 tensor-core products (~1e-4 relative each)
+    assert np.allclose(rq, th[idx], rtol=1e-2), (rq, th[idx])
