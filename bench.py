@@ -148,6 +148,16 @@ def job_throughput(world, steps, t_max):
     return world * steps / t_max
 
 
+def workload_config(cfg, method):
+    """The workload both arms report (the same dict in both lines)."""
+    return {"workload": cfg.name, "n": cfg.n, "N": cfg.N, "nA": cfg.nA, "K": cfg.K, "k": cfg.k, "l": cfg.l,
+            "method": method, "q_power": cfg.q_power, "tol": cfg.tol,
+            "propagators": "one dense matrix per subwindow",
+            "l2": (f"inputs larger than L2 (propagators {cfg.N * cfg.n * cfg.n * 4 / 1e9:.2f} GB FP32, "
+                   f"{cfg.N * cfg.n * cfg.n * 8 / 1e9:.2f} GB FP64)"),
+            "parallelism": "replicas"}
+
+
 # ---------------------------------------------------------------- CPU oracle sample
 def oracle_column_rate(cfg, cols=16):
     """Column Hessian products per second of the FP64 oracle (plain C, OpenMP
@@ -192,7 +202,7 @@ def run_reference(args, cfg):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inner_loops/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value if value else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": cfg.name, "n": cfg.n, "N": cfg.N, "K": cfg.K},
+            "data": "synthetic", "config": workload_config(cfg, args.method), "precision": "fp64",
             "cpu_baseline": {"value": value, "unit": "inner_loops/s", "cores": omp_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "inner_loops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -568,10 +578,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "inner_loops/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "n": cfg.n, "N": cfg.N, "nA": nA, "K": K, "k": cfg.k,
-                       "l": cfg.l, "method": args.method, "q_power": cfg.q_power, "tol": cfg.tol,
-                       "precision": "mixed", "propagators": "one dense FP32/FP64 matrix per subwindow",
-                       "l2": "inputs larger than L2 (propagators 2.7 GB FP32, 5.4 GB FP64)", "parallelism": "replicas"},
+            "config": workload_config(cfg, args.method), "precision": "mixed",
             "inner_loop_ms": 1e3 * t_max / args.steps,
             "pcg_iters": iters, "relres": relres,
             "block_products_per_step": products_block / args.steps,
