@@ -166,8 +166,11 @@ wc4d_status wc4d_gaussian(wc4d_ctx *ctx, uint64_t seed, int64_t rows, int32_t co
  * target rank k, oversampling l.
  * G_device: explicit probes (nA x (k+l), ld = nA, FP64) or NULL to draw
  * them with wc4d_gaussian(seed).  theta_host: k Ritz values, decreasing.
- * Orthonormalisation is CholeskyQR2 with an FP64 Gram; the small
- * eigenproblems are solved by one-sided Jacobi in FP64. */
+ * Orthonormalisation is CholeskyQR2 with an FP64-accurate Gram (double-float
+ * for FP32 blocks; shifted CholeskyQR3 when the Gram is singular to working
+ * precision); the small eigenproblems are solved by one-sided Jacobi, in FP64
+ * for the result, after FP32 pre-rotation sweeps for the SPD ones (REVD's K_1,
+ * Nystrom's F^T F). */
 wc4d_status wc4d_sketch(wc4d_ctx *ctx, int32_t method, int32_t k, int32_t l, int32_t q_power,
                         uint64_t seed, const double *G_device, double *theta_host, int32_t precision);
 /* Copy the current Ritz vectors (nA x k, column-major, FP64) and values. */
