@@ -526,7 +526,7 @@ def lanczos_ritz(alpha, beta, F, k):
     decreasing, and u_i = F_J w_i with F_J = (f_0 .. f_{J-1}).  Returns U
     (k, n) and theta (k)."""
     T = lanczos_tridiag(alpha, beta)
-    w, V = np.linalg.eigh(T)
+    w, V, _ = jacobi_eig(T)             # the oracle's own cyclic Jacobi (numpy's eigh stays a test cross-check)
     order = np.argsort(w)[::-1][:k]
     J = len(alpha)
     U = V[:, order].T @ np.asarray(F)[:J]
