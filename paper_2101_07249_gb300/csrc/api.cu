@@ -1581,7 +1581,8 @@ static wc4d_status true_residual(wc4d_ctx *c, const double *x, double *r64, doub
     WC4D_TRY(sync(c, "true residual"));
     double rr = 0.0, bb = 0.0;
     for (int i = 0; i < grid; ++i) { rr += h[i]; bb += h[grid + i]; }
-    *rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    // non-finite sums give a non-finite relative residual (a zero rhs gives 0)
+    *rel = !(std::isfinite(rr) && std::isfinite(bb)) ? std::nan("") : (bb > 0.0 ? std::sqrt(rr / bb) : 0.0);
     if (bnorm_out) *bnorm_out = std::sqrt(bb);
     return WC4D_OK;
 }
@@ -1636,11 +1637,12 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
     WC4D_TRY(check_launch(c, "pcg init"));
     WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
     WC4D_TRY(sync(c, "pcg init"));
-    double rel = hflags[0] ? 0.0 : 1.0;   // |rhs| = 0: x = 0 is exact
+    const bool init_bad = hflags[1] != 0;   // non-finite rhs: a breakdown, no iteration
+    double rel = init_bad ? std::nan("") : (hflags[0] ? 0.0 : 1.0);   // |rhs| = 0: x = 0 is exact
     double rmax = rel;
-    bool converged = (force == 0 && rel <= tol), breakdown = false, pending = false;
+    bool converged = (force == 0 && rel <= tol), breakdown = init_bad, pending = false;
     const double tol_k = (force > 0) ? 0.0 : tol;
-    const int nit = (force > 0) ? force : maxit;
+    const int nit = init_bad ? 0 : ((force > 0) ? force : maxit);
     int it = 0;
     IterGraph graph;
     auto body = [&]() -> wc4d_status {

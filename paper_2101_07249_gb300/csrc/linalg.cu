@@ -1537,13 +1537,16 @@ __global__ void k_pcg_init(int grid, const double *part_b, const double *part_rh
     double bb = sum_part(grid, part_b);
     double rho = sum_part(grid, part_rh);
     if (threadIdx.x == 0) {
+        // a non-finite right-hand side (or preconditioned residual) is a
+        // breakdown before the first iteration, not a zero right-hand side
+        const bool bad = !isfinite(bb) || !isfinite(rho);
         scal[S_RHO] = rho;
         scal[S_BNORM] = sqrt(bb);
         scal[S_RELRES] = bb > 0.0 ? 1.0 : 0.0;
         scal[S_ALPHA] = 0.0;
         scal[S_BETA] = 0.0;
-        flags[F_DONE] = (bb > 0.0) ? 0 : 1;
-        flags[F_BREAK] = 0;
+        flags[F_DONE] = (bb > 0.0 && !bad) ? 0 : 1;
+        flags[F_BREAK] = bad ? 2 : 0;
         flags[F_ITER] = 0;
     }
 }

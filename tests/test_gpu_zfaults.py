@@ -1,0 +1,51 @@
+"""Host-visible failure statuses for non-finite inputs, injected on the host
+(a NaN in one probe column, a NaN observation): the library must return an
+error status -- not trap, hang or report success -- and the context must stay
+usable, giving the same results afterwards as before the fault."""
+import numpy as np
+import pytest
+
+from paper_2101_07249_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+w = pytest.importorskip("paper_2101_07249_gb300")
+pytestmark = pytest.mark.gpu
+
+
+def _solver():
+    cfg = inputs.TINY
+    tw = inputs.twin(cfg)
+    return cfg, tw, w.Solver(cfg, tw)
+
+
+def test_nan_probe_column_is_reported_and_the_context_recovers():
+    cfg, tw, S = _solver()
+    m = cfg.k + cfg.l
+    G = inputs.probes(5, cfg.nA, m)
+    th0 = w.wc4d_sketch(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 0,
+                        torch.as_tensor(G, device="cuda"), w.FP64)
+    Gbad = G.copy()
+    Gbad[3, 17] = np.nan                       # one entry of probe column 3
+    with pytest.raises(w.WC4DError) as e:
+        w.wc4d_sketch(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 0, torch.as_tensor(Gbad, device="cuda"), w.FP64)
+    assert e.value.status in (w.ENOTSPD, w.ENAN, w.EBREAKDOWN)
+    th1 = w.wc4d_sketch(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 0,
+                        torch.as_tensor(G, device="cuda"), w.FP64)
+    assert np.allclose(th1, th0, rtol=1e-12, atol=0)
+    S.close()
+
+
+def test_nan_observation_is_reported_and_the_context_recovers():
+    cfg, tw, S = _solver()
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    it0, rel0, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 0, 0, w.FP64)
+    ybad = np.array(tw.y, dtype=np.float64).copy()
+    ybad[7] = np.nan
+    w.wc4d_set_background_obs(S.ctx, tw.xb, ybad)
+    with pytest.raises(w.WC4DError) as e:
+        w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 0, 0, w.FP64)
+    assert e.value.status in (w.EBREAKDOWN, w.ENAN)
+    w.wc4d_set_background_obs(S.ctx, tw.xb, tw.y)
+    it1, rel1, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 0, 0, w.FP64)
+    assert it1 == it0 and rel1 <= 1e-6 and abs(rel1 - rel0) <= 1e-12
+    S.close()
