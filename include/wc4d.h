@@ -137,6 +137,13 @@ wc4d_status wc4d_set_background_obs(wc4d_ctx *ctx, const double *xb_host, const 
 wc4d_status wc4d_outer_update(wc4d_ctx *ctx, const double *x_device);
 /* Number of observations q of the problem. */
 int64_t     wc4d_nobs(const wc4d_ctx *ctx);
+/* Dimension n_A = n (N + 1) of the control vector (eq. 10's A is n_A x n_A):
+   the length of every control-space vector and the least leading dimension
+   of every block passed to the library; -1 for a null context. */
+int64_t     wc4d_control_dim(const wc4d_ctx *ctx);
+/* Number of Ritz pairs currently installed (what wc4d_get_ritz copies:
+   n_A x count values and count Ritz values); -1 for a null context. */
+int32_t     wc4d_ritz_count(const wc4d_ctx *ctx);
 /* Copy the right-hand side (nA values) to device memory. */
 wc4d_status wc4d_get_rhs(wc4d_ctx *ctx, double *rhs_device);
 

@@ -65,6 +65,8 @@ _SIGS = {
     "wc4d_batch_inner_loop": (C.c_int, [_V, C.c_int32, C.c_int32, _V, _V, C.c_int32, _V, C.c_double, C.c_int32,
                                         C.c_int32, _V, _V, _V, _V, C.c_int32]),
     "wc4d_nobs": (C.c_int64, [_V]),
+    "wc4d_control_dim": (C.c_int64, [_V]),
+    "wc4d_ritz_count": (C.c_int32, [_V]),
     "wc4d_get_rhs": (C.c_int, [_V, _V]),
     "wc4d_hvp": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_gaussian": (C.c_int, [_V, C.c_uint64, C.c_int64, C.c_int32, C.c_int64, _V]),
@@ -144,6 +146,34 @@ def _ptr(t):
             raise ValueError("device argument must be contiguous")
         return C.c_void_p(t.data_ptr())
     return C.c_void_p(int(t))
+
+
+def _dev(t, dtype, count, name):
+    """_ptr after checking what the C ABI cannot see behind a bare pointer: the
+    element type (None: any) and at least `count` elements (count <= 0: left to
+    the library's own argument checks).  Raw integer addresses pass unchecked."""
+    import torch
+    if isinstance(t, torch.Tensor):
+        if dtype is not None and t.dtype != dtype:
+            raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+        if count > 0 and t.numel() < count:
+            raise ValueError(f"{name}: needs at least {count} elements, has {t.numel()}")
+    return _ptr(t)
+
+
+def _fdtype(precision):
+    """Element type of the blocks of a call in this precision (None: invalid,
+    left to the library's EINVAL)."""
+    import torch
+    return {FP64: torch.float64, MIXED: torch.float32}.get(int(precision))
+
+
+def _block(ctx, K, ld):
+    """Elements an n_A x K block with leading dimension ld spans (0 when K or
+    ld are invalid: the library rejects those itself)."""
+    nA = int(load().wc4d_control_dim(ctx))
+    K, ld = int(K), int(ld)
+    return (K - 1) * ld + nA if K >= 1 and nA >= 1 and ld >= nA else 0
 
 
 def _hp(a):
@@ -257,12 +287,21 @@ def wc4d_nobs(ctx):
     return int(load().wc4d_nobs(ctx))
 
 
+def wc4d_control_dim(ctx):
+    return int(load().wc4d_control_dim(ctx))
+
+
+def wc4d_ritz_count(ctx):
+    return int(load().wc4d_ritz_count(ctx))
+
+
 def wc4d_get_rhs(ctx, rhs):
     _check(ctx, load().wc4d_get_rhs(ctx, _ptr(rhs)))
 
 
 def wc4d_hvp(ctx, X, Y, K, ld, precision=FP64):
-    _check(ctx, load().wc4d_hvp(ctx, _ptr(X), _ptr(Y), int(K), int(ld), int(precision)))
+    dt, n = _fdtype(precision), _block(ctx, K, ld)
+    _check(ctx, load().wc4d_hvp(ctx, _dev(X, dt, n, "X"), _dev(Y, dt, n, "Y"), int(K), int(ld), int(precision)))
 
 
 def wc4d_gaussian(ctx, seed, rows, cols, ld, G):
@@ -270,25 +309,38 @@ def wc4d_gaussian(ctx, seed, rows, cols, ld, G):
 
 
 def wc4d_sketch(ctx, method, k, l, q_power, seed, G=None, precision=FP64):
-    th = np.zeros(int(k))
-    _check(ctx, load().wc4d_sketch(ctx, int(method), int(k), int(l), int(q_power), int(seed), _ptr(G),
+    import torch
+    th = np.zeros(max(int(k), 0))
+    Gp = _dev(G, torch.float64, _block(ctx, int(k) + int(l), load().wc4d_control_dim(ctx)), "G")
+    _check(ctx, load().wc4d_sketch(ctx, int(method), int(k), int(l), int(q_power), int(seed), Gp,
                                    _hp(th), int(precision)))
     return th
 
 
 def wc4d_get_ritz(ctx, U, k):
-    th = np.zeros(int(k))
-    _check(ctx, load().wc4d_get_ritz(ctx, _ptr(U), _hp(th)))
-    return th
+    """Ritz values (the first k) and, into U, all installed Ritz vectors."""
+    import torch
+    kU = int(load().wc4d_ritz_count(ctx))
+    th = np.zeros(max(int(k), kU, 0))     # the library writes all kU values
+    nA = int(load().wc4d_control_dim(ctx))
+    _check(ctx, load().wc4d_get_ritz(ctx, _dev(U, torch.float64, kU * nA, "U"), _hp(th)))
+    return th[:int(k)]
 
 
 def wc4d_set_ritz(ctx, k, U, theta):
+    import torch
     theta = np.ascontiguousarray(theta, dtype=np.float64)
-    _check(ctx, load().wc4d_set_ritz(ctx, int(k), _ptr(U), _hp(theta)))
+    if theta.size < int(k):
+        raise ValueError(f"theta: needs {int(k)} values, has {theta.size}")
+    n = int(k) * int(load().wc4d_control_dim(ctx))
+    _check(ctx, load().wc4d_set_ritz(ctx, int(k), _dev(U, torch.float64, n, "U"), _hp(theta)))
 
 
 def wc4d_lmp_apply(ctx, v, y, transpose=0):
-    _check(ctx, load().wc4d_lmp_apply(ctx, _ptr(v), _ptr(y), int(transpose)))
+    import torch
+    n = int(load().wc4d_control_dim(ctx))
+    _check(ctx, load().wc4d_lmp_apply(ctx, _dev(v, torch.float64, n, "v"), _dev(y, torch.float64, n, "y"),
+                                      int(transpose)))
 
 
 def wc4d_pcg(ctx, x, tol=1e-6, maxit=5000, use_lmp=1, force_iters=0, precision=FP64, qcf=False,
@@ -298,7 +350,9 @@ def wc4d_pcg(ctx, x, tol=1e-6, maxit=5000, use_lmp=1, force_iters=0, precision=F
     rr = C.c_double(0.0)
     cap = max(int(maxit), int(force_iters), 1)
     q = np.zeros(cap) if qcf else None
-    st = load().wc4d_pcg(ctx, _ptr(x), float(tol), int(maxit), int(use_lmp), int(force_iters), int(precision),
+    import torch
+    xp = _dev(x, torch.float64, int(load().wc4d_control_dim(ctx)), "x")
+    st = load().wc4d_pcg(ctx, xp, float(tol), int(maxit), int(use_lmp), int(force_iters), int(precision),
                          C.byref(it), C.byref(rr), _hp(q))
     if st != OK and (raise_on_noconv or st != ENOCONV):
         _check(ctx, st)
@@ -308,8 +362,10 @@ def wc4d_pcg(ctx, x, tol=1e-6, maxit=5000, use_lmp=1, force_iters=0, precision=F
 def wc4d_inner_loop(ctx, method, k, l, q_power, seed, tol, maxit, precision, x):
     it = C.c_int32(0)
     rr = C.c_double(0.0)
+    import torch
+    xp = _dev(x, torch.float64, int(load().wc4d_control_dim(ctx)), "x")
     _check(ctx, load().wc4d_inner_loop(ctx, int(method), int(k), int(l), int(q_power), int(seed), float(tol),
-                                       int(maxit), int(precision), _ptr(x), C.byref(it), C.byref(rr)))
+                                       int(maxit), int(precision), xp, C.byref(it), C.byref(rr)))
     return it.value, rr.value
 
 
@@ -326,15 +382,19 @@ def wc4d_symeig(ctx, m, S, V):
 
 
 def wc4d_apply_dsqrt(ctx, X, Y, K, ld, precision=FP64):
-    _check(ctx, load().wc4d_apply_dsqrt(ctx, _ptr(X), _ptr(Y), int(K), int(ld), int(precision)))
+    dt, n = _fdtype(precision), _block(ctx, K, ld)
+    _check(ctx, load().wc4d_apply_dsqrt(ctx, _dev(X, dt, n, "X"), _dev(Y, dt, n, "Y"), int(K), int(ld),
+                                        int(precision)))
 
 
 def wc4d_apply_linv(ctx, W, K, ld, precision=FP64):
-    _check(ctx, load().wc4d_apply_linv(ctx, _ptr(W), int(K), int(ld), int(precision)))
+    Wp = _dev(W, _fdtype(precision), _block(ctx, K, ld), "W")
+    _check(ctx, load().wc4d_apply_linv(ctx, Wp, int(K), int(ld), int(precision)))
 
 
 def wc4d_apply_linvT(ctx, W, K, ld, precision=FP64):
-    _check(ctx, load().wc4d_apply_linvT(ctx, _ptr(W), int(K), int(ld), int(precision)))
+    Wp = _dev(W, _fdtype(precision), _block(ctx, K, ld), "W")
+    _check(ctx, load().wc4d_apply_linvT(ctx, Wp, int(K), int(ld), int(precision)))
 
 
 def wc4d_get_propagator(ctx, t, M):

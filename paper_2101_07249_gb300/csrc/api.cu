@@ -316,6 +316,8 @@ extern "C" wc4d_status wc4d_set_stream(wc4d_ctx *c, void *stream)
 }
 
 extern "C" int64_t wc4d_nobs(const wc4d_ctx *c) { return c ? c->nobs : -1; }
+extern "C" int64_t wc4d_control_dim(const wc4d_ctx *c) { return c ? c->nA : -1; }
+extern "C" int32_t wc4d_ritz_count(const wc4d_ctx *c) { return c ? c->kU : -1; }
 
 extern "C" int64_t wc4d_launch_count(int32_t reset)
 {
