@@ -63,6 +63,8 @@ _SIGS = {
     "o_gaussian": (None, [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, _D]),
     "o_corr_row": (None, [C.c_int32, C.c_int32, C.c_double, C.c_double, _D]),
     "o_circulant_sqrt_row": (C.c_int, [C.c_int32, _D, _D, _D]),
+    "o_cov_eigs": (None, [C.c_int32, C.c_int32, C.c_double, C.c_double, _D]),
+    "o_cov_sqrt_row": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, _D, _D]),
     "o_circulant_apply": (None, [C.c_int32, _D, _D, _D]),
     "o_advdiff_step": (None, [C.c_int32, C.c_double, C.c_double, C.c_double, _D, _D]),
     "o_advdiff_step_T": (None, [C.c_int32, C.c_double, C.c_double, C.c_double, _D, _D]),
@@ -196,10 +198,31 @@ def corr_row(kind, n, L, variance):
 
 
 def circulant_sqrt_row(row):
+    """First row of the symmetric square root of the circulant with first row
+    `row` (Section 5 covariances): eigenvalues by an extended-precision DFT of
+    the row, negative ones clamped to zero.  Returns (row, clamped, min_eig)."""
     row = _f64(row)
     out = np.zeros_like(row)
     mn = C.c_double(0.0)
     clamped = lib().o_circulant_sqrt_row(len(row), _dp(row), _dp(out), C.byref(mn))
+    return out, int(clamped), mn.value
+
+
+def cov_eigs(kind, n, L, variance):
+    """Eigenvalues of variance * C(kind, L) (the circulant of corr_row), from
+    the correlation function: extended-precision DFT for SOAR, the Poisson
+    summation closed form for the Gaussian."""
+    lam = np.zeros(n)
+    lib().o_cov_eigs(int(kind), int(n), float(L), float(variance), _dp(lam))
+    return lam
+
+
+def cov_sqrt_row(kind, n, L, variance):
+    """First row of (variance * C(kind, L))^{1/2} from cov_eigs, negative
+    eigenvalues clamped to zero.  Returns (row, clamped, min_eig)."""
+    out = np.zeros(n)
+    mn = C.c_double(0.0)
+    clamped = lib().o_cov_sqrt_row(int(kind), int(n), float(L), float(variance), _dp(out), C.byref(mn))
     return out, int(clamped), mn.value
 
 

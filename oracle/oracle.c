@@ -10,7 +10,8 @@
  *
  * Parity status (what each part is pinned to, all in tests/test_oracle_*.py):
  *   Philox4x32-10     published known-answer vectors + normality statistics
- *   correlation rows  closed forms; (C^{1/2})^2 = C; eigenvalues vs numpy FFT
+ *   correlation rows  closed forms; (C^{1/2})^2 = C; eigenvalues vs a 40-digit
+ *                     DFT (mpmath) of the correlation function, tiny ones included
  *   advection-diff.   Fourier closed form of the Crank-Nicolson symbol;
  *                     residual of the cyclic tridiagonal solve
  *   Lorenz-96         fixed point x=F; RK4 order-4 convergence vs scipy;
@@ -120,35 +121,136 @@ void o_corr_row(int32_t kind, int32_t n, double L, double variance, double *row)
     }
 }
 
-/* Symmetric square root of a symmetric circulant matrix given by its first
- * row: eigenvalues lam_m = sum_s row[s] cos(2 pi m s / n) (plain DFT), then
- * sqrt_row[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).  Eigenvalues below
- * 1e-8 of the largest (negative ones included) are taken as zero: there the
- * DFT's rounding (~1e-16 of the largest) is comparable to the eigenvalue and
- * its square root would be noise.  Returns the number of eigenvalues zeroed. */
-int o_circulant_sqrt_row(int32_t n, const double *row, double *sqrt_row, double *min_eig)
+/* Eigenvalues of the symmetric circulant with first row `row`, by the plain
+ * DFT lam_m = sum_s row[s] cos(2 pi m s / n), evaluated in long double with the
+ * angle index m s reduced mod n exactly (integer arithmetic), so that
+ * eigenvalues far below the largest keep their relative accuracy. */
+/* pi to the precision of long double (M_PI is a double) */
+static const long double PI_LD = 3.14159265358979323846264338327950288419716939937510L;
+
+static void circ_eigs_ld(int32_t n, const long double *row, long double *lam)
 {
-    double *cosv = (double *)malloc(sizeof(double) * n);
-    double *lam = (double *)malloc(sizeof(double) * n);
-    for (int32_t j = 0; j < n; ++j) cosv[j] = cos(2.0 * M_PI * (double)j / (double)n);
-    int clamped = 0;
-    double mn = INFINITY, mx = -INFINITY;
+    long double *cosv = (long double *)malloc(sizeof(long double) * n);
+    for (int32_t j = 0; j < n; ++j) cosv[j] = cosl(2.0L * PI_LD * (long double)j / (long double)n);
     for (int32_t m = 0; m < n; ++m) {
-        double acc = 0.0;
+        long double acc = 0.0L;
         for (int32_t s = 0; s < n; ++s) acc += row[s] * cosv[(int64_t)m * s % n];
         lam[m] = acc;
-        if (acc < mn) mn = acc;
-        if (acc > mx) mx = acc;
     }
-    for (int32_t m = 0; m < n; ++m)
-        if (!(lam[m] >= 1e-8 * mx)) { lam[m] = 0.0; ++clamped; }
+    free(cosv);
+}
+
+/* First row of the symmetric square root from the eigenvalues (X13 reading:
+ * negative eigenvalues, which a periodically wrapped correlation function can
+ * have, are clamped to zero; every non-negative one is kept):
+ * sqrt_row[s] = (1/n) sum_m sqrt(max(lam_m, 0)) cos(2 pi m s / n), in long
+ * double.  Returns the number of clamped (negative) eigenvalues. */
+static int circ_sqrt_from_eigs(int32_t n, const long double *lam, double *sqrt_row, double *min_eig)
+{
+    long double *cosv = (long double *)malloc(sizeof(long double) * n);
+    long double *rt = (long double *)malloc(sizeof(long double) * n);
+    for (int32_t j = 0; j < n; ++j) cosv[j] = cosl(2.0L * PI_LD * (long double)j / (long double)n);
+    int clamped = 0;
+    long double mn = INFINITY;
+    for (int32_t m = 0; m < n; ++m) {
+        if (lam[m] < mn) mn = lam[m];
+        if (lam[m] < 0.0L) { rt[m] = 0.0L; ++clamped; }
+        else rt[m] = sqrtl(lam[m]);
+    }
     for (int32_t s = 0; s < n; ++s) {
-        double acc = 0.0;
-        for (int32_t m = 0; m < n; ++m) acc += sqrt(lam[m]) * cosv[(int64_t)m * s % n];
-        sqrt_row[s] = acc / (double)n;
+        long double acc = 0.0L;
+        for (int32_t m = 0; m < n; ++m) acc += rt[m] * cosv[(int64_t)m * s % n];
+        sqrt_row[s] = (double)(acc / (long double)n);
     }
-    if (min_eig) *min_eig = mn;
-    free(cosv); free(lam);
+    if (min_eig) *min_eig = (double)mn;
+    free(cosv); free(rt);
+    return clamped;
+}
+
+/* Symmetric square root of a symmetric circulant matrix given by its first
+ * row (double): eigenvalues by the long-double DFT of that row, negative ones
+ * clamped to zero.  Returns the number clamped; *min_eig the smallest
+ * eigenvalue before clamping. */
+int o_circulant_sqrt_row(int32_t n, const double *row, double *sqrt_row, double *min_eig)
+{
+    long double *r = (long double *)malloc(sizeof(long double) * n);
+    long double *lam = (long double *)malloc(sizeof(long double) * n);
+    for (int32_t s = 0; s < n; ++s) r[s] = row[s];
+    circ_eigs_ld(n, r, lam);
+    int clamped = circ_sqrt_from_eigs(n, lam, sqrt_row, min_eig);
+    free(r); free(lam);
+    return clamped;
+}
+
+/* Eigenvalues of the covariance variance * C(kind, L) of o_corr_row, computed
+ * from the correlation function itself rather than from its double row:
+ *  - SOAR: the long-double DFT of the row evaluated in long double;
+ *  - Gaussian: the Poisson summation formula for the periodic sum,
+ *      sum_{r in Z} e^{-r^2/(2L^2)} cos(theta r)
+ *        = L sqrt(2 pi) sum_{j in Z} e^{-L^2 (theta - 2 pi j)^2 / 2},
+ *    a sum of positive terms (so even eigenvalues of 1e-35 keep full relative
+ *    accuracy, which no DFT of rounded row values can give), minus the images
+ *    that the periodic-distance row does not contain: offsets r outside
+ *    (-n/2, n/2], i.e. 2 sum_{r > n/2} g(r) cos(theta r) + [n even] g(n/2)
+ *    cos(theta n/2) (odd n: 2 sum_{r >= (n+1)/2});
+ *  - identity: variance.
+ * theta_m = 2 pi m / n; lam has n entries. */
+static void cov_eigs_ld(int32_t kind, int32_t n, double L, double variance, long double *lam)
+{
+    if (kind == 0) {
+        long double *row = (long double *)malloc(sizeof(long double) * n);
+        long double Ll = L;
+        for (int32_t s = 0; s < n; ++s) {
+            long double r = (long double)(s < n - s ? s : n - s);
+            row[s] = (long double)variance * (1.0L + r / Ll) * expl(-r / Ll);
+        }
+        circ_eigs_ld(n, row, lam);
+        free(row);
+    } else if (kind == 1) {
+        const long double Ll = L, twopi = 2.0L * PI_LD;
+        const int jmax = 2 + (int)(3.5 / L);
+        for (int32_t m = 0; m < n; ++m) {
+            long double th = twopi * (long double)m / (long double)n;
+            long double P = 0.0L;
+            for (int j = -jmax; j <= jmax + 1; ++j) {
+                long double d = th - twopi * (long double)j;
+                P += expl(-Ll * Ll * d * d / 2.0L);
+            }
+            P *= Ll * sqrtl(twopi);
+            long double T = 0.0L;
+            int32_t r0 = n / 2 + 1;                 /* first offset beyond (-n/2, n/2] */
+            if (n % 2 == 0) T += expl(-(long double)(n / 2) * (n / 2) / (2.0L * Ll * Ll))
+                                 * cosl(th * (long double)(n / 2));
+            for (int64_t r = r0;; ++r) {
+                long double e = (long double)r * (long double)r / (2.0L * Ll * Ll);
+                if (e > 1000.0L) break;
+                T += 2.0L * expl(-e) * cosl(th * (long double)r);
+            }
+            lam[m] = (long double)variance * (P - T);
+        }
+    } else {
+        for (int32_t m = 0; m < n; ++m) lam[m] = variance;
+    }
+}
+
+/* Eigenvalues of variance * C(kind, L) as doubles (cov_eigs_ld). */
+void o_cov_eigs(int32_t kind, int32_t n, double L, double variance, double *lam)
+{
+    long double *l = (long double *)malloc(sizeof(long double) * n);
+    cov_eigs_ld(kind, n, L, variance, l);
+    for (int32_t m = 0; m < n; ++m) lam[m] = (double)l[m];
+    free(l);
+}
+
+/* First row of (variance * C(kind, L))^{1/2}: the accurate eigenvalues of
+ * cov_eigs_ld, negative ones clamped to zero (Section 5 covariances; X13
+ * reading).  Returns the number clamped. */
+int o_cov_sqrt_row(int32_t kind, int32_t n, double L, double variance, double *sqrt_row, double *min_eig)
+{
+    long double *lam = (long double *)malloc(sizeof(long double) * n);
+    cov_eigs_ld(kind, n, L, variance, lam);
+    int clamped = circ_sqrt_from_eigs(n, lam, sqrt_row, min_eig);
+    free(lam);
     return clamped;
 }
 

@@ -15,7 +15,8 @@
  *     t*n + s holds grid point s of time block t (t = 0 is x_0, t >= 1 is
  *     eta_t).
  *   - Dense propagators are row-major n x n.
- *   - Everything is double precision.
+ *   - Everything is double precision, except the covariance eigenvalue sums
+ *     (long double, so that eigenvalues far below the largest stay accurate).
  */
 #ifndef WC4D_ORACLE_H
 #define WC4D_ORACLE_H
@@ -54,6 +55,8 @@ void o_philox_words(uint64_t seed, int64_t count, uint32_t *out);
 /* ---- covariance rows ---------------------------------------------------- */
 void o_corr_row(int32_t kind, int32_t n, double L_points, double variance, double *row);
 int  o_circulant_sqrt_row(int32_t n, const double *row, double *sqrt_row, double *min_eig);
+void o_cov_eigs(int32_t kind, int32_t n, double L_points, double variance, double *lam);
+int  o_cov_sqrt_row(int32_t kind, int32_t n, double L_points, double variance, double *sqrt_row, double *min_eig);
 void o_circulant_apply(int32_t n, const double *row, const double *x, double *y);
 
 /* ---- models ------------------------------------------------------------- */

@@ -6,10 +6,8 @@ from paper_2101_07249_gb300 import inputs
 
 
 def cov_sqrt_rows(cfg):
-    b = oracle.corr_row(cfg.b_kind, cfg.n, cfg.b_L, cfg.b_var)
-    q = oracle.corr_row(cfg.q_kind, cfg.n, cfg.q_L, cfg.q_var)
-    bs, _, _ = oracle.circulant_sqrt_row(b)
-    qs, _, _ = oracle.circulant_sqrt_row(q)
+    bs, _, _ = oracle.cov_sqrt_row(cfg.b_kind, cfg.n, cfg.b_L, cfg.b_var)
+    qs, _, _ = oracle.cov_sqrt_row(cfg.q_kind, cfg.n, cfg.q_L, cfg.q_var)
     return bs, qs
 
 

@@ -99,10 +99,8 @@ def test_spectrum_of_A_paper_advection_size():
     """The paper's advection size (n=40, N=50, 2040 x 2040, 100 observations,
     Section 5.1) with the configured advection-diffusion physics."""
     cfg = inputs.scaled(inputs.TINY, n=40, N=50, k=25, l=5, obs_stride=4, steps=1, obs_t0=5)
-    row = oracle.corr_row(0, 40, 10.0 * 1, 0.1 ** 2)
-    bs, _, _ = oracle.circulant_sqrt_row(row)
-    qrow = oracle.corr_row(0, 40, 10.0, 0.05 ** 2)
-    qs, _, _ = oracle.circulant_sqrt_row(qrow)
+    bs, _, _ = oracle.cov_sqrt_row(0, 40, 10.0, 0.1 ** 2)
+    qs, _, _ = oracle.cov_sqrt_row(0, 40, 10.0, 0.05 ** 2)
     p = oracle.Problem(40, 50, oracle.MODEL_ADVDIFF, bs, qs, 0.05 ** 2, 4, obs_t0=5, obs_tstride=5,
                        steps=1, dt=0.02, kappa=1e-3, u=0.8)
     assert p.nA == 2040 and p.nobs == 100

@@ -74,22 +74,86 @@ def _circ(row):
     return row[idx]
 
 
-@pytest.mark.parametrize("kind,n,L", [(0, 100, 5.0), (0, 256, 20.48), (0, 4096, 81.92), (1, 128, 4.0), (2, 50, 1.0)])
-def test_circulant_sqrt_squares_to_covariance(kind, n, L):
+def _mp_eigs(kind, n, L, variance, dps=50):
+    """Eigenvalues of the periodic-distance correlation circulant by a DFT of
+    the correlation function evaluated at `dps` digits (mpmath): an
+    independent, rounding-free statement of the definition."""
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp.clone() if hasattr(mpmath.mp, "clone") else mpmath.mp
+    mp.dps = dps
+    Lm = mp.mpf(L)
+    row = []
+    for s in range(n):
+        r = mp.mpf(min(s, n - s))
+        row.append((1 + r / Lm) * mp.exp(-r / Lm) if kind == 0 else mp.exp(-r * r / (2 * Lm * Lm)))
+    cosv = [mp.cos(2 * mp.pi * j / n) for j in range(n)]
+    return np.array([float(variance * mp.fsum(row[s] * cosv[(m * s) % n] for s in range(n))) for m in range(n)])
+
+
+@pytest.mark.parametrize("kind,n,L", [(0, 64, 5.0), (0, 40, 10.0), (0, 63, 2.5), (1, 64, 4.0), (1, 63, 0.7),
+                                      (1, 64, 20.0), (1, 128, 4.0), (1, 50, 1.5)])
+def test_cov_eigs_match_high_precision_dft(kind, n, L):
+    """Every eigenvalue, the smallest and the negative ones included, against
+    a 50-digit DFT of the correlation function: relative 1e-14 for those
+    above 1e-6 of the largest, and absolute 1e-17 of the largest below (SOAR
+    is summed from its row in long double; the Gaussian's Poisson form has
+    relative accuracy even at 1e-35)."""
+    ref = _mp_eigs(kind, n, L, 0.7)
+    lam = oracle.cov_eigs(kind, n, L, 0.7)
+    big = np.abs(ref) > 1e-6 * ref.max()
+    assert np.all(np.abs(lam - ref)[big] <= 1e-14 * np.abs(ref)[big])
+    assert np.all(np.abs(lam - ref)[~big] <= 1e-17 * ref.max())
+    if kind == 1:       # all-positive Poisson terms: relative accuracy everywhere it is positive
+        pos = ref > 1e-300
+        assert np.all(np.abs(lam - ref)[pos] <= 1e-12 * np.abs(ref)[pos] + 1e-20 * ref.max())
+        assert np.array_equal(lam < 0, ref < 0)       # the clamping decisions agree
+
+
+@pytest.mark.parametrize("kind,n,L", [(0, 100, 5.0), (0, 1024, 20.48), (0, 4096, 81.92), (1, 128, 4.0),
+                                      (1, 8192, 4.0), (2, 50, 1.0)])
+def test_cov_sqrt_squares_to_covariance(kind, n, L):
+    """Positive-definite covariances (every eigenvalue > 0, nothing clamped):
+    (C^{1/2})^2 = C to 1e-13 of the largest eigenvalue, in the Fourier basis
+    (every circulant is diagonal there) and, for n <= 256, as dense matrices;
+    the spectrum of the root is the square root of C's, mode by mode."""
     row = oracle.corr_row(kind, n, L, 0.7)
-    srow, clamped, mn = oracle.circulant_sqrt_row(row)
-    C, S = _circ(row), _circ(srow)
+    srow, clamped, mn = oracle.cov_sqrt_row(kind, n, L, 0.7)
     lam = np.fft.fft(row).real
-    assert mn == pytest.approx(lam.min(), abs=1e-12 * abs(lam).max())
-    assert np.allclose(S, S.T, atol=1e-15)
-    lam_t = np.where(lam >= 1e-8 * lam.max(), lam, 0.0)       # eigenvalues kept
-    assert clamped == int(np.sum(lam_t == 0.0))
-    if clamped == 0:
-        assert np.abs(S @ S - C).max() <= 1e-12 * np.abs(C).max()
-    # S^2 is C with the eigenvalues below 1e-8 of the largest removed
-    assert np.abs(np.fft.fft(srow).real ** 2 - lam_t).max() < 1e-12 * lam.max()
-    removed = np.real(np.fft.ifft(lam - lam_t))               # the zeroed part of C
-    assert np.abs(S @ S - (C - _circ(removed))).max() <= 1e-12 * lam.max()
+    assert clamped == 0 and mn > 0.0
+    sig = np.fft.fft(srow).real                          # eigenvalues of the root
+    assert np.abs(sig ** 2 - lam).max() <= 1e-13 * lam.max()
+    assert np.all(sig > -1e-15 * np.sqrt(lam.max()))
+    if n <= 256:
+        C, S = _circ(row), _circ(srow)
+        assert np.allclose(S, S.T, atol=1e-15)
+        assert np.abs(S @ S - C).max() <= 1e-13 * lam.max()
+    # every mode, the ones below 1e-8 of the largest included, against the
+    # accurate eigenvalues (the square root is ill-conditioned only through
+    # the rounding of the transform of the root's row, ~1e-16 of its largest)
+    ex = np.sqrt(np.maximum(oracle.cov_eigs(kind, n, L, 0.7), 0.0))
+    assert np.abs(sig - ex).max() <= 1e-14 * ex.max()
+
+
+def test_cov_sqrt_clamps_only_negative_eigenvalues():
+    """A periodically wrapped SOAR with a long length scale (40 points,
+    L = 10, the paper's advection window) and a Gaussian whose truncated
+    images make the highest wavenumbers slightly negative: the root squares
+    to C with exactly the negative part of its spectrum removed, and the
+    clamp count is the number of negative eigenvalues (taken from the
+    50-digit DFT)."""
+    for kind, n, L in [(0, 40, 10.0), (0, 256, 20.48), (1, 64, 4.0)]:
+        ref = _mp_eigs(kind, n, L, 0.7)
+        srow, clamped, mn = oracle.cov_sqrt_row(kind, n, L, 0.7)
+        assert clamped == int(np.sum(ref < 0)) > 0
+        assert mn == pytest.approx(ref.min(), rel=1e-9)
+        C_pos = np.real(np.fft.ifft(np.maximum(ref, 0.0)))      # first row of C with the negative part removed
+        S = _circ(srow)
+        assert np.abs(S @ S - _circ(C_pos)).max() <= 1e-13 * ref.max()
+    # the same from an explicit row (extended-precision DFT of the row)
+    row = oracle.corr_row(0, 40, 10.0, 0.7)
+    srow2, clamped2, _ = oracle.circulant_sqrt_row(row)
+    srow1, clamped1, _ = oracle.cov_sqrt_row(0, 40, 10.0, 0.7)
+    assert clamped2 == clamped1 and np.abs(srow2 - srow1).max() <= 1e-14 * np.abs(srow1).max()
 
 
 def test_circulant_apply_matches_fft_convolution():
