@@ -110,11 +110,18 @@ wc4d_status wc4d_build_advdiff_propagator(wc4d_ctx *ctx, double kappa, double c,
  * subwindows).  Circulant on the periodic grid with first row
  * variance * rho(r), r the periodic distance in grid points:
  * SOAR (1 + r/L) e^{-r/L}, Gaussian e^{-r^2/(2 L^2)}, or DIAG (variance * I).
- * The symmetric square root D^{1/2} is formed on the device from the DFT
- * eigenvalues: sqrt(lambda), with eigenvalues below 1e-8 of the largest
- * (where rounding dominates) taken as zero. */
+ * The symmetric square root D^{1/2} is formed on the device from the
+ * eigenvalues of the circulant, computed in closed form so that the smallest
+ * keep their relative accuracy (SOAR: finite geometric sums; Gaussian: the
+ * Poisson summation formula less the images the periodic row omits):
+ * sqrt(lambda) for lambda >= 0, and zero for the negative eigenvalues that a
+ * periodically wrapped correlation function can have.  EINVAL for a block
+ * outside {0, 1}, an unknown corr, a negative variance or L <= 0. */
 wc4d_status wc4d_set_covariance(wc4d_ctx *ctx, int32_t block, int32_t corr, double variance, double length);
-/* Same, from an explicit first row (host, n values, symmetric). */
+/* Same, from an explicit first row (host, n values, symmetric): eigenvalues
+ * by an FP64 DFT of the row (errors ~1e-16 of the largest eigenvalue, which
+ * the square root amplifies where the spectrum is tiny), negative ones
+ * clamped to zero. */
 wc4d_status wc4d_set_covariance_row(wc4d_ctx *ctx, int32_t block, const double *row_host);
 
 /* Outer-loop quantities (Section 2.1): run the model from the background
@@ -287,18 +294,22 @@ wc4d_status wc4d_profile(wc4d_ctx *ctx, int32_t enable);
 wc4d_status wc4d_profile_read(wc4d_ctx *ctx, int32_t cls, double *total_ms, int64_t *launch_groups);
 /* Allocation-free spectral-LMP application, y = C v (the paper has no
  * counterpart: it is an integration aid).  For callers that cannot allocate
- * device memory where they apply the preconditioner -- code inside CUDA
- * stream capture (cudaMalloc cannot be captured), systems that reserve their
- * whole device memory budget up front, callers without a library context.
- * U (device, nA x k column-major, orthonormal columns), theta (device, k
- * values), v and y (device, nA doubles, distinct); queued on cuda_stream.
- * Creates no context and allocates nothing: its scratch (coefficients and
- * partial dot products) is one fixed 1 MiB + 8 KiB device array in the
- * library, held by every GPU that loads it until exit.  k > 1024 returns
- * WC4D_EINVAL.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress), so make it before any stream capture.
- * All calls share the array: calls that overlap on the GPU (other streams,
- * other host threads) race and must be serialised by the caller. */
+ * device memory where they apply the preconditioner: systems that reserve
+ * their whole device memory budget up front and forbid later allocations,
+ * code that must not take the device-wide synchronisation an allocation or
+ * free can cause in the middle of a solve, and callers without a library
+ * context.  U (device, nA x k column-major, orthonormal columns), theta
+ * (device, k values), v and y (device, nA doubles, distinct); queued on
+ * cuda_stream.  Creates no context and allocates nothing: its scratch
+ * (weighted coefficients and partial dot products) is one fixed
+ * 1 MiB + 8 KiB device array in the library, held by every GPU that loads it
+ * until exit.  k > 1024 returns WC4D_EINVAL.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) and caches it,
+ * so make that first call before any stream capture; resetting the device
+ * (cudaDeviceReset) after it is not supported.  All calls share the array,
+ * which keeps the last call's contents: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller. */
 wc4d_status wc4d_lmp_apply_static(const double *U, const double *theta, int32_t k, int64_t nA, const double *v,
                                   double *y, void *cuda_stream);
 /* Ritz pairs from CG (Section 3.3, eq. 18-20), the deterministic LMP built

@@ -454,7 +454,9 @@ static wc4d_status ensure_M32(wc4d_ctx *c)
     return WC4D_OK;
 }
 
-static wc4d_status cov_from_row(wc4d_ctx *c, int block, const double *row_dev)
+// kind >= 0: eigenvalues of variance * C(kind, L) in closed form; kind < 0:
+// from the explicit first row row_dev.
+static wc4d_status cov_sqrt_setup(wc4d_ctx *c, int block, int kind, double L, double variance, const double *row_dev)
 {
     const int n = c->prob.n;
     WC4D_TRY(ensure(c, c->small2, sizeof(double) * (n + 1)));
@@ -465,9 +467,9 @@ static wc4d_status cov_from_row(wc4d_ctx *c, int block, const double *row_dev)
         WC4D_TRY(ensure(c, c->row64[block], sizeof(double) * n));
         WC4D_TRY(ensure(c, c->row32[block], sizeof(float) * n));
     }
-    launch_cov_sqrt(c->stream, n, c->logn, c->fft, row_dev, P<double2>(c->cosn), P<double>(c->small2),
-                    P<double>(c->spec64[block]), P<float>(c->spec32[block]), P<double>(c->row64[block]),
-                    P<float>(c->row32[block]));
+    launch_cov_sqrt(c->stream, n, c->logn, c->fft, kind, L, variance, row_dev, P<double2>(c->cosn),
+                    P<double>(c->small2), P<double>(c->spec64[block]), P<float>(c->spec32[block]),
+                    P<double>(c->row64[block]), P<float>(c->row32[block]));
     WC4D_TRY(check_launch(c, "cov_sqrt"));
     c->have_cov[block] = true;
     return sync(c, "cov_sqrt");
@@ -476,11 +478,8 @@ static wc4d_status cov_from_row(wc4d_ctx *c, int block, const double *row_dev)
 extern "C" wc4d_status wc4d_set_covariance(wc4d_ctx *c, int32_t block, int32_t corr, double variance, double L)
 {
     if (!c || block < 0 || block > 1 || corr < 0 || corr > 2 || !(variance >= 0.0)) return WC4D_EINVAL;
-    if (corr != WC4D_CORR_DIAG && !(L > 0.0)) return WC4D_EINVAL;
-    WC4D_TRY(ensure(c, c->small3, sizeof(double) * c->prob.n));
-    launch_corr_row(c->stream, c->prob.n, corr, L, variance, P<double>(c->small3));
-    WC4D_TRY(check_launch(c, "corr_row"));
-    return cov_from_row(c, block, P<double>(c->small3));
+    if (corr != WC4D_CORR_DIAG && !(L > 0.0 && L < 1e300)) return WC4D_EINVAL;
+    return cov_sqrt_setup(c, block, corr, L, variance, nullptr);
 }
 
 extern "C" wc4d_status wc4d_set_covariance_row(wc4d_ctx *c, int32_t block, const double *row_host)
@@ -489,7 +488,7 @@ extern "C" wc4d_status wc4d_set_covariance_row(wc4d_ctx *c, int32_t block, const
     WC4D_TRY(ensure(c, c->small3, sizeof(double) * c->prob.n));
     WC4D_CUDA(c, cudaMemcpyAsync(c->small3.p, row_host, sizeof(double) * c->prob.n, cudaMemcpyHostToDevice,
                                  c->stream));
-    return cov_from_row(c, block, P<double>(c->small3));
+    return cov_sqrt_setup(c, block, -1, 0.0, 1.0, P<double>(c->small3));
 }
 
 static wc4d_status require_operator(wc4d_ctx *c)

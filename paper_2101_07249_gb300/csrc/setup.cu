@@ -71,27 +71,9 @@ void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, fl
     WC4D_LAUNCH(k_twiddles<<<ceil_div(n, 256), 256, 0, s>>>(n, tab_full, tw64, tw32));
 }
 
-// ----------------------------------------------------------------------------
-// Correlation rows on the periodic grid (distance in grid points).
-// ----------------------------------------------------------------------------
-__global__ void k_corr_row(int n, int kind, double L, double var, double *row)
-{
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    double r = (double)min(s, n - s);
-    double rho;
-    if (kind == WC4D_CORR_SOAR) rho = (1.0 + r / L) * exp(-r / L);
-    else if (kind == WC4D_CORR_GAUSS) rho = exp(-r * r / (2.0 * L * L));
-    else rho = (s == 0) ? 1.0 : 0.0;
-    row[s] = var * rho;
-}
-
-void launch_corr_row(cudaStream_t s, int n, int kind, double L, double var, double *row)
-{
-    WC4D_LAUNCH(k_corr_row<<<ceil_div(n, 256), 256, 0, s>>>(n, kind, L, var, row));
-}
-
-// lam[m] = sum_s row[s] cos(2 pi m s / n): eigenvalues of the symmetric circulant.
+// lam[m] = sum_s row[s] cos(2 pi m s / n): eigenvalues of the symmetric
+// circulant given by an explicit first row (FP64 DFT; the angle index m s is
+// reduced mod n exactly through the table).
 __global__ void k_circ_eig(int n, const double *row, const double2 *tab, double *lam)
 {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,26 +83,83 @@ __global__ void k_circ_eig(int n, const double *row, const double2 *tab, double 
     lam[m] = acc;
 }
 
-__device__ __forceinline__ int bitrev(int v, int logn) { return (int)(__brev((unsigned)v) >> (32 - logn)); }
-
-// lam[n] = max_m lam[m] (one CTA).
-__global__ void k_eig_max(int n, double *lam)
+// Eigenvalues of var * C(kind, L) in closed form, so that the smallest ones
+// keep their relative accuracy (a DFT of the rounded row leaves errors of
+// ~1e-16 of the largest eigenvalue, which the square root turns into
+// ~1e-8 of its largest value where the spectrum is tiny).  The row holds
+// offsets r in (-n/2, n/2] once each (r = n/2 only for even n); theta = 2 pi m / n.
+//  SOAR, c(r) = (1 + r/L) a^r with a = e^{-1/L}: with z = a e^{i theta} and
+//    h the last offset of the doubled sum (n/2 - 1 even, (n-1)/2 odd),
+//    sum_{r=1..h} z^r = z (1 - z^h) / (1 - z),
+//    sum_{r=1..h} r z^r = z (1 - (h+1) z^h + h z^{h+1}) / (1 - z)^2,
+//    lam = 1 + 2 Re(S0 + S1 / L) [+ c(n/2) (-1)^m for even n].
+//  Gaussian, g(r) = e^{-r^2/(2L^2)}: Poisson summation of the periodic sum,
+//    sum_{r in Z} g(r) cos(theta r) = L sqrt(2 pi) sum_j e^{-L^2 (theta - 2 pi j)^2 / 2}
+//    (positive terms), minus the images the row does not hold:
+//    2 sum_{r > n/2} g(r) cos(theta r) [+ g(n/2) cos(theta n/2) for even n].
+//  DIAG: var.
+__global__ void k_corr_eig(int n, int kind, double L, double var, double *lam)
 {
-    __shared__ double red[1024];
-    double m = -INFINITY;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, lam[i]);
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double out;
+    if (kind == WC4D_CORR_SOAR) {
+        const int h = (n % 2 == 0) ? n / 2 - 1 : (n - 1) / 2;
+        const double a = exp(-1.0 / L);
+        double sn, cs;
+        sincospi(2.0 * (double)m / (double)n, &sn, &cs);
+        const double zr = a * cs, zi = a * sn;                        // z
+        sincospi(2.0 * (double)(((int64_t)m * h) % n) / (double)n, &sn, &cs);
+        const double ah = exp(-(double)h / L);
+        const double hr = ah * cs, hi = ah * sn;                      // z^h
+        const double h1r = hr * zr - hi * zi, h1i = hr * zi + hi * zr;  // z^{h+1}
+        const double dr = 1.0 - zr, di = -zi;                         // 1 - z
+        const double d2 = dr * dr + di * di;
+        // S0 = z (1 - z^h) / (1 - z)
+        double nr = zr - h1r, ni = zi - h1i;                          // z - z^{h+1}
+        const double s0r = (nr * dr + ni * di) / d2;
+        // S1 = z (1 - (h+1) z^h + h z^{h+1}) / (1 - z)^2
+        double tr = 1.0 - (h + 1.0) * hr + h * h1r, ti = -(h + 1.0) * hi + h * h1i;
+        nr = zr * tr - zi * ti;
+        ni = zr * ti + zi * tr;
+        const double q2r = dr * dr - di * di, q2i = 2.0 * dr * di;    // (1 - z)^2
+        const double s1r = (nr * q2r + ni * q2i) / (d2 * d2);
+        out = 1.0 + 2.0 * (s0r + s1r / L);
+        if (n % 2 == 0) {
+            const double hh = 0.5 * n;
+            out += (1.0 + hh / L) * exp(-hh / L) * ((m & 1) ? -1.0 : 1.0);
+        }
+    } else if (kind == WC4D_CORR_GAUSS) {
+        const double th = 2.0 * (double)m / (double)n;               // theta / pi
+        const int jmax = 2 + (int)(3.5 / L);
+        double P = 0.0;
+        for (int j = -jmax; j <= jmax + 1; ++j) {
+            const double d = M_PI * (th - 2.0 * j);
+            P += exp(-0.5 * L * L * d * d);
+        }
+        P *= L * sqrt(2.0 * M_PI);
+        double T = 0.0;
+        if (n % 2 == 0) {
+            const int hh = n / 2;
+            T += exp(-(double)hh * hh / (2.0 * L * L)) * ((((int64_t)m * hh) % n == 0) ? 1.0 : -1.0);
+        }
+        for (int64_t r = n / 2 + 1;; ++r) {
+            const double e = (double)r * (double)r / (2.0 * L * L);
+            if (e > 745.0) break;
+            T += 2.0 * exp(-e) * cospi(2.0 * (double)(((int64_t)m * r) % n) / (double)n);
+        }
+        out = P - T;
+    } else {
+        out = 1.0;
     }
-    if (threadIdx.x == 0) lam[n] = red[0];
+    lam[m] = var * out;
 }
 
-// Eigenvalues below 1e-8 of the largest are taken as zero: there the DFT's
-// rounding is comparable to the eigenvalue and its square root is noise.
-__device__ __forceinline__ double kept_sqrt(double l, double lmax) { return (l >= 1e-8 * lmax) ? sqrt(l) : 0.0; }
+__device__ __forceinline__ int bitrev(int v, int logn) { return (int)(__brev((unsigned)v) >> (32 - logn)); }
+
+// Negative eigenvalues (a periodically wrapped correlation function can have
+// them) are clamped to zero; every non-negative one is kept.
+__device__ __forceinline__ double kept_sqrt(double l) { return (l > 0.0) ? sqrt(l) : 0.0; }
 
 // FFT path: spec[p] = sqrt(lam[bitrev(p)]) / n.  Direct path: first row of
 // the square root, r[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).
@@ -128,7 +167,7 @@ __global__ void k_sqrt_spec(int n, int logn, const double *lam, double *spec64, 
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    double v = kept_sqrt(lam[bitrev(p, logn)], lam[n]) / (double)n;
+    double v = kept_sqrt(lam[bitrev(p, logn)]) / (double)n;
     spec64[p] = v;
     spec32[p] = (float)v;
 }
@@ -137,19 +176,21 @@ __global__ void k_sqrt_row(int n, const double *lam, const double2 *tab, double 
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const double lmax = lam[n];
     double acc = 0.0;
-    for (int m = 0; m < n; ++m) acc += kept_sqrt(lam[m], lmax) * tab[(int)(((int64_t)m * s) % n)].x;
+    for (int m = 0; m < n; ++m) acc += kept_sqrt(lam[m]) * tab[(int)(((int64_t)m * s) % n)].x;
     acc /= (double)n;
     row64[s] = acc;
     row32[s] = (float)acc;
 }
 
-void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, const double *row, const double2 *tab,
-                     double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32)
+// Square root of a circulant covariance: eigenvalues from the correlation
+// function (kind >= 0; k_corr_eig) or from an explicit row (kind < 0;
+// k_circ_eig), then the spectrum (FFT path) or first row (direct path).
+void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, int kind, double L, double var, const double *row,
+                     const double2 *tab, double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32)
 {
-    WC4D_LAUNCH(k_circ_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, row, tab, lam_tmp));
-    WC4D_LAUNCH(k_eig_max<<<1, 1024, 0, s>>>(n, lam_tmp));
+    if (kind >= 0) WC4D_LAUNCH(k_corr_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, kind, L, var, lam_tmp));
+    else WC4D_LAUNCH(k_circ_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, row, tab, lam_tmp));
     if (fft) WC4D_LAUNCH(k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, logn, lam_tmp, spec64, spec32));
     else WC4D_LAUNCH(k_sqrt_row<<<ceil_div(n, 128), 128, 0, s>>>(n, lam_tmp, tab, row64, row32));
 }

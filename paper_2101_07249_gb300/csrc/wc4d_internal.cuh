@@ -189,9 +189,8 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 // set-up
 void launch_gaussian(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, int64_t ld, double *G);
 void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, float2 *tw32);
-void launch_corr_row(cudaStream_t s, int n, int kind, double L, double var, double *row);
-void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, const double *row, const double2 *tab,
-                     double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32);
+void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, int kind, double L, double var, const double *row,
+                     const double2 *tab, double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32);
 void launch_advdiff_column(cudaStream_t s, int n, double kappa, double c, double dt, int steps,
                            const double2 *tab, double2 *sym_tmp, double *col);
 void launch_expand_circulant(cudaStream_t s, int n, const double *col, double *M, double *MT);

@@ -35,8 +35,8 @@ def upwind_by_stepping(n, courant):
 
 def oracle_problem():
     n, N = ps.n_ADV, ps.N_ADV
-    bs, _, _ = oracle.circulant_sqrt_row(oracle.corr_row(0, n, 10.0, 0.1 ** 2))     # SOAR, 10 dz
-    qs, _, _ = oracle.circulant_sqrt_row(oracle.corr_row(0, n, 10.0, 0.05 ** 2))
+    bs, _, _ = oracle.cov_sqrt_row(0, n, 10.0, 0.1 ** 2)      # SOAR, 10 dz
+    qs, _, _ = oracle.cov_sqrt_row(0, n, 10.0, 0.05 ** 2)
     return oracle.Problem(n=n, N=N, model=oracle.MODEL_DENSE, Bsqrt=bs, Qsqrt=qs, sigma_o2=0.05 ** 2,
                           obs_stride=4, obs_t0=5, obs_tstride=5, steps=1, dt=1.0 / N,
                           M=upwind_by_stepping(n, 0.8), M_shared=True)
@@ -54,20 +54,26 @@ def test_upwind_window_hvp_matches_oracle():
     assert w.wc4d_nobs(c) == 100
 
 
-def test_spectrum_has_q_eigenvalues_above_one():
+def test_spectrum_matches_oracle_dense_A():
+    """The whole spectrum of the library's A against the oracle's dense A on
+    the same window.  A - I = D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2} has
+    rank at most q = 100; here D^{1/2} is singular (the wrapped 40-point
+    SOAR has 19 negative eigenvalues, clamped to zero), so fewer directions
+    see the observations: the count of eigenvalues above one is the oracle's
+    (60), every other eigenvalue is one, and the leading ones agree."""
     c = ctx()
     nA = ps.n_ADV * (ps.N_ADV + 1)
     A = ps.dense_A(c, nA)
     assert np.abs(A - A.T).max() <= 1e-10 * np.abs(A).max()
     lam = np.linalg.eigvalsh(0.5 * (A + A.T))
-    # A - I = D^{1/2} L^{-T} H^T R^{-1} H L^{-1} D^{1/2} has rank at most q = 100
-    # (equal to q when H L^{-1} D^{1/2} has full row rank; here the SOAR
-    # spectra on 40 points decay below 1e-8 of their maxima and those modes
-    # of D^{1/2} are zero, so fewer directions see the observations)
+    p = oracle_problem()
+    Ao = oracle.hvp(p, np.eye(nA)).T
+    lam_o = np.linalg.eigvalsh(0.5 * (Ao + Ao.T))
+    above, above_o = np.sum(lam > 1.0 + 1e-8), np.sum(lam_o > 1.0 + 1e-8)
+    assert above == above_o and 0 < above <= 100
     assert lam[0] >= 1.0 - 1e-10
-    above = np.sum(lam > 1.0 + 1e-8)
-    assert 0 < above <= 100
     assert np.sum(np.abs(lam - 1.0) <= 1e-8) == nA - above
+    assert np.abs(lam - lam_o).max() <= 1e-11 * lam_o.max()
 
 
 def test_lambda_min_through_invariant_subspace_matches_dense():
