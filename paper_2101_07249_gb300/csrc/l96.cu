@@ -287,12 +287,332 @@ k_l96_adj_cl(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-blocked FP32 sweeps (n = 8 nt with nt a multiple of 32, nt <= 1024):
+// thread tau owns the contiguous run of points 8 tau .. 8 tau + 7 of C probe
+// columns.  The running stage input u and the RK4 accumulator live in
+// registers; the step's base state (d for the tangent-linear sweep, lambda
+// for the adjoint) is thread-private and kept in shared memory laid out
+// [c][p][tau] (consecutive lanes, consecutive words).  The stage state x of
+// the trajectory is staged in shared memory, double-buffered: each thread
+// copies its 32-byte slice of the next stage's x with cp.async while the
+// current stage computes, so the L2 latency is off the critical path, and
+// x serves all C columns.  The stencils' halos of u and x come from the
+// neighbouring lanes by warp shuffles and, at warp boundaries, from a small
+// double-buffered edge table (u) or the staged x; one __syncthreads per RK4
+// stage orders it all.
+// ---------------------------------------------------------------------------
+constexpr int L96_RB_P = 8;   // points per thread
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Stage this thread's 8 points of the stage state x into xb.
+__device__ __forceinline__ void stage_x_async(float *xb, const float *__restrict__ x, int j0)
+{
+    cp_async16(xb + j0, x + j0);
+    cp_async16(xb + j0 + 4, x + j0 + 4);
+    cp_async_commit();
+}
+
+// x at points j0 - 2 .. j0 + 9 from the staged vector xs (v[q] = x[j0 - 2 + q]).
+__device__ __forceinline__ void read_xwin(float v[12], const float *xs, int j0, int n, int lane)
+{
+    const float4 a = *reinterpret_cast<const float4 *>(xs + j0);
+    const float4 b = *reinterpret_cast<const float4 *>(xs + j0 + 4);
+    v[2] = a.x; v[3] = a.y; v[4] = a.z; v[5] = a.w;
+    v[6] = b.x; v[7] = b.y; v[8] = b.z; v[9] = b.w;
+    v[0] = __shfl_up_sync(0xffffffffu, v[8], 1);
+    v[1] = __shfl_up_sync(0xffffffffu, v[9], 1);
+    v[10] = __shfl_down_sync(0xffffffffu, v[2], 1);
+    v[11] = __shfl_down_sync(0xffffffffu, v[3], 1);
+    if (lane == 0) { v[0] = xs[wrap(j0 - 2, n)]; v[1] = xs[wrap(j0 - 1, n)]; }
+    if (lane == 31) { v[10] = xs[wrap(j0 + 8, n)]; v[11] = xs[wrap(j0 + 9, n)]; }
+}
+
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// Shared memory of the register-blocked sweeps: [C][8][nt] base state, two
+// staged stage states of n floats, [2][C][nw][3] warp edges.
+template <int C>
+static size_t rb_smem(int n)
+{
+    return sizeof(float) * ((size_t)C * n + 2 * (size_t)n + (size_t)2 * C * (n / L96_RB_P / 32) * 3);
+}
+
+// Forward sweep L^{-1} (w_{t+1} += M_t w_t) for columns blockIdx.x*C .. +C-1 (< K).
+template <int C>
+__global__ void __launch_bounds__(1024, 1)
+k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K)
+{
+    constexpr int P = L96_RB_P;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    float *dsm = reinterpret_cast<float *>(sm);          // [C][P][nt]: d
+    float *xbuf = dsm + (size_t)C * n;                     // [2][n]: staged stage states
+    float *edge = xbuf + 2 * (size_t)n;                    // [2][C][nw][3]: warp edges of u
+    const int j0 = tid * P;
+    const int G = N * steps;
+    stage_x_async(xbuf, stages, j0);                       // stage (g = 0, i = 0)
+    float u[C][P], acc[C][P];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int col = blockIdx.x * C + c;
+        const float *w = W + (int64_t)min(col, K - 1) * ld;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float v = (col < K) ? w[j0 + p] : 0.f;
+            u[c][p] = v;
+            dsm[((size_t)c * P + p) * nt + tid] = v;
+        }
+    }
+    const float h2 = h * 0.5f, h6 = h / 6.f;
+    int sidx = 0;
+    for (int t = 0; t < N; ++t) {
+        for (int k = 0; k < steps; ++k) {
+            const int g = t * steps + k;
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i, ++sidx) {
+                cp_async_wait_all();
+                float L2[C], L1[C], R1[C];
+                float *eb = edge + (size_t)(sidx & 1) * C * nw * 3;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    L2[c] = shfl_up1(u[c][P - 2]);
+                    L1[c] = shfl_up1(u[c][P - 1]);
+                    R1[c] = shfl_dn1(u[c][0]);
+                    if (lane == 31) { eb[(c * nw + wid) * 3 + 0] = u[c][P - 2]; eb[(c * nw + wid) * 3 + 1] = u[c][P - 1]; }
+                    if (lane == 0) eb[(c * nw + wid) * 3 + 2] = u[c][0];
+                }
+                __syncthreads();
+                {   // stage the next stage state into the other buffer
+                    const int gn = (i < 3) ? g : g + 1, in = (i < 3) ? i + 1 : 0;
+                    if (gn < G) stage_x_async(xbuf + (size_t)((sidx + 1) & 1) * n, stages + (int64_t)(4 * gn + in) * n, j0);
+                }
+                if (lane == 0) {
+                    const int wp = (wid == 0) ? nw - 1 : wid - 1;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) { L2[c] = eb[(c * nw + wp) * 3 + 0]; L1[c] = eb[(c * nw + wp) * 3 + 1]; }
+                }
+                if (lane == 31) {
+                    const int wn = (wid == nw - 1) ? 0 : wid + 1;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) R1[c] = eb[(c * nw + wn) * 3 + 2];
+                }
+                float xv[12];
+                read_xwin(xv, xbuf + (size_t)(sidx & 1) * n, j0, n, lane);
+                const float wgt = (i == 0 || i == 3) ? 1.f : 2.f;
+                const float cf = (i == 2) ? h : h2;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float um2 = L2[c], um1 = L1[c];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const float up1 = (p + 1 < P) ? u[c][p + 1] : R1[c];
+                        const float cur = u[c][p];
+                        // (J u)_j = (u_{j+1} - u_{j-2}) x_{j-1} + (x_{j+1} - x_{j-2}) u_{j-1} - u_j
+                        const float kk = (up1 - um2) * xv[p + 1] + (xv[p + 3] - xv[p]) * um1 - cur;
+                        um2 = um1;
+                        um1 = cur;
+                        const float d = dsm[((size_t)c * P + p) * nt + tid];
+                        if (i == 0) {
+                            acc[c][p] = kk;
+                            u[c][p] = d + cf * kk;
+                        } else if (i < 3) {
+                            acc[c][p] += wgt * kk;
+                            u[c][p] = d + cf * kk;
+                        } else {
+                            const float dn = d + h6 * (acc[c][p] + kk);
+                            u[c][p] = dn;
+                            dsm[((size_t)c * P + p) * nt + tid] = dn;
+                        }
+                    }
+                }
+            }
+        }
+        // subwindow boundary: w_{t+1} += d, d = w_{t+1}
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int col = blockIdx.x * C + c;
+            if (col >= K) continue;
+            float *wn = W + (int64_t)col * ld + (int64_t)(t + 1) * n;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float v = u[c][p] + wn[j0 + p];
+                wn[j0 + p] = v;
+                u[c][p] = v;
+                dsm[((size_t)c * P + p) * nt + tid] = v;
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
+// Adjoint sweep L^{-T} for columns blockIdx.x*C .. +C-1 (< K); obs_mode as
+// k_l96_adj.  Per RK4 step (stage states 4..1): a4 = h/6 lam, g4 = J4^T a4,
+// acc = lam + g4, a3 = h/3 lam + h g4, g3 = J3^T a3, acc += g3,
+// a2 = h/3 lam + h/2 g3, g2 = J2^T a2, acc += g2, a1 = h/6 lam + h/2 g2,
+// g1 = J1^T a1, lam = acc + g1.
+template <int C>
+__global__ void __launch_bounds__(1024, 1)
+k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K,
+             int obs_mode, float obs_scale, int obs_stride, int t0, int ts)
+{
+    constexpr int P = L96_RB_P;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    float *lsm = reinterpret_cast<float *>(sm);           // [C][P][nt]: lambda
+    float *xbuf = lsm + (size_t)C * n;                     // [2][n]: staged stage states
+    float *edge = xbuf + 2 * (size_t)n;                    // [2][C][nw][3]: warp edges of the stage input
+    const int j0 = tid * P;
+    const int G = N * steps;
+    stage_x_async(xbuf, stages + (int64_t)(4 * (G - 1) + 3) * n, j0);   // stage (g = G - 1, i = 3)
+    auto obs_at = [&](int t) { return t >= t0 && (t - t0) % ts == 0; };
+    float u[C][P], acc[C][P];
+    {
+        const bool ob = obs_at(N);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int col = blockIdx.x * C + c;
+            float *wN = W + (int64_t)min(col, K - 1) * ld + (int64_t)N * n;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float v = (col < K) ? wN[j0 + p] : 0.f;
+                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
+                if (col < K) wN[j0 + p] = v;
+                lsm[((size_t)c * P + p) * nt + tid] = v;
+            }
+        }
+    }
+    const float h2 = h * 0.5f, h3 = h / 3.f, h6 = h / 6.f;
+    int sidx = 0;
+    for (int t = N - 1; t >= 0; --t) {
+        for (int k = steps - 1; k >= 0; --k) {
+            const int g = t * steps + k;
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int p = 0; p < P; ++p) u[c][p] = h6 * lsm[((size_t)c * P + p) * nt + tid];
+#pragma unroll 1
+            for (int i = 3; i >= 0; --i, ++sidx) {
+                cp_async_wait_all();
+                float L1[C], R1[C], R2[C];
+                float *eb = edge + (size_t)(sidx & 1) * C * nw * 3;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    L1[c] = shfl_up1(u[c][P - 1]);
+                    R1[c] = shfl_dn1(u[c][0]);
+                    R2[c] = shfl_dn1(u[c][1]);
+                    if (lane == 31) eb[(c * nw + wid) * 3 + 0] = u[c][P - 1];
+                    if (lane == 0) { eb[(c * nw + wid) * 3 + 1] = u[c][0]; eb[(c * nw + wid) * 3 + 2] = u[c][1]; }
+                }
+                __syncthreads();
+                {   // stage the next stage state (backwards) into the other buffer
+                    const int gn = (i > 0) ? g : g - 1, in = (i > 0) ? i - 1 : 3;
+                    if (gn >= 0) stage_x_async(xbuf + (size_t)((sidx + 1) & 1) * n, stages + (int64_t)(4 * gn + in) * n, j0);
+                }
+                if (lane == 0) {
+                    const int wp = (wid == 0) ? nw - 1 : wid - 1;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) L1[c] = eb[(c * nw + wp) * 3 + 0];
+                }
+                if (lane == 31) {
+                    const int wn = (wid == nw - 1) ? 0 : wid + 1;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) { R1[c] = eb[(c * nw + wn) * 3 + 1]; R2[c] = eb[(c * nw + wn) * 3 + 2]; }
+                }
+                float xv[12];
+                read_xwin(xv, xbuf + (size_t)(sidx & 1) * n, j0, n, lane);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float am1 = L1[c];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const float ap1 = (p + 1 < P) ? u[c][p + 1] : R1[c];
+                        const float ap2 = (p + 2 < P) ? u[c][p + 2] : ((p + 2 == P) ? R1[c] : R2[c]);
+                        const float cur = u[c][p];
+                        // (J^T a)_i = x_{i-2} a_{i-1} - x_{i+1} a_{i+2} + (x_{i+2} - x_{i-1}) a_{i+1} - a_i
+                        const float gg = xv[p] * am1 - xv[p + 3] * ap2 + (xv[p + 4] - xv[p + 1]) * ap1 - cur;
+                        am1 = cur;
+                        const float lam = lsm[((size_t)c * P + p) * nt + tid];
+                        if (i == 3) {
+                            acc[c][p] = lam + gg;
+                            u[c][p] = h3 * lam + h * gg;
+                        } else if (i == 2) {
+                            acc[c][p] += gg;
+                            u[c][p] = h3 * lam + h2 * gg;
+                        } else if (i == 1) {
+                            acc[c][p] += gg;
+                            u[c][p] = h6 * lam + h2 * gg;
+                        } else {
+                            lsm[((size_t)c * P + p) * nt + tid] = acc[c][p] + gg;
+                        }
+                    }
+                }
+            }
+        }
+        // subwindow boundary: lam = obs(w_t) + lam, w_t = lam
+        const bool ob = obs_at(t);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int col = blockIdx.x * C + c;
+            if (col >= K) continue;
+            float *wt = W + (int64_t)col * ld + (int64_t)t * n;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float v = wt[j0 + p];
+                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
+                v += lsm[((size_t)c * P + p) * nt + tid];
+                lsm[((size_t)c * P + p) * nt + tid] = v;
+                wt[j0 + p] = v;
+            }
+        }
+    }
+    cp_async_wait_all();
+}
+
+// Register-blocked form: FP32, n = 8 nt with nt a multiple of 32 and at most 1024.
+template <typename T> static bool use_rb(int n)
+{
+    return sizeof(T) == 4 && n % (32 * L96_RB_P) == 0 && n / L96_RB_P <= 1024;
+}
+// Columns per CTA: two for blocks (the staged stage states then serve both),
+// one for few columns, where the CTAs are the parallelism.
+static int rb_cols(int K) { return K >= 64 ? 2 : 1; }
+
 static bool use_cluster(int n, int K) { return K <= 32 && n % L96_CL == 0 && n / L96_CL >= 2 && n / L96_CL <= 1024; }
+
+template <int C>
+static void launch_tlm_rb(cudaStream_t s, int n, int N, int steps, double dt, const float *stages, int K, float *W,
+                          int64_t ld)
+{
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_l96_tlm_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
+    }();   // once, thread-safe
+    (void)attr;
+    WC4D_LAUNCH(k_l96_tlm_rb<C><<<ceil_div(K, C), n / L96_RB_P, rb_smem<C>(n), s>>>(n, N, steps, (float)dt, stages, W,
+                                                                                   ld, K));
+}
 
 template <typename T>
 void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
                           int64_t ld)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (use_rb<T>(n)) {
+            if (rb_cols(K) == 2) launch_tlm_rb<2>(s, n, N, steps, dt, stages, K, W, ld);
+            else launch_tlm_rb<1>(s, n, N, steps, dt, stages, K, W, ld);
+            return;
+        }
+    }
     static const bool attr = [] {
         return cudaFuncSetAttribute(k_l96_tlm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(3 * WC4D_FFT_MAX_N * sizeof(T))) == cudaSuccess;
@@ -306,10 +626,35 @@ void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
     WC4D_LAUNCH(k_l96_tlm<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld));
 }
 
+template <int C>
+static void launch_adj_rb(cudaStream_t s, int n, int N, int steps, double dt, const float *stages, int K, float *W,
+                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
+{
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_l96_adj_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
+    }();   // once, thread-safe
+    (void)attr;
+    WC4D_LAUNCH(k_l96_adj_rb<C><<<ceil_div(K, C), n / L96_RB_P, rb_smem<C>(n), s>>>(
+        n, N, steps, (float)dt, stages, W, ld, K, obs_mode, (float)obs_scale, obs_stride, obs_t0,
+        obs_tstride > 0 ? obs_tstride : 1));
+}
+
 template <typename T>
 void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
                           int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (use_rb<T>(n)) {
+            if (rb_cols(K) == 2)
+                launch_adj_rb<2>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0,
+                                 obs_tstride);
+            else
+                launch_adj_rb<1>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0,
+                                 obs_tstride);
+            return;
+        }
+    }
     static const bool attr = [] {
         return cudaFuncSetAttribute(k_l96_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(3 * WC4D_FFT_MAX_N * sizeof(T))) == cudaSuccess;
