@@ -190,6 +190,11 @@ def _hv(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def torch_f64():
+    import torch
+    return torch.float64
+
+
 def _stream(stream=None):
     if stream is not None:
         return C.c_void_p(int(stream))
@@ -418,8 +423,12 @@ def wc4d_profile_read(ctx, cls):
 
 
 def wc4d_lmp_apply_static(U, theta, k, nA, v, y, stream=None):
-    """y = C v without any device allocation (shared fixed scratch; see wc4d.h)."""
-    st = load().wc4d_lmp_apply_static(_ptr(U), _ptr(theta), int(k), int(nA), _ptr(v), _ptr(y), _stream(stream))
+    """y = C v without any device allocation (shared fixed scratch; see wc4d.h).
+    U: FP64, k*nA elements (column-major nA x k); theta: FP64, k; v, y: FP64, nA."""
+    k, nA = int(k), int(nA)
+    args = (_dev(U, torch_f64(), k * nA, "U"), _dev(theta, torch_f64(), k, "theta"), k, nA,
+            _dev(v, torch_f64(), nA, "v"), _dev(y, torch_f64(), nA, "y"), _stream(stream))
+    st = load().wc4d_lmp_apply_static(*args)
     if st != OK:
         raise WC4DError(st, "wc4d_lmp_apply_static")
 
