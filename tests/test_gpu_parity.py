@@ -345,7 +345,13 @@ def test_pcg_fp64_matches_oracle(name, method):
     # (c) working tolerance
     ro = oracle.pcg(p, b, Uo, tho, tol=1e-6)
     it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, use, 0, w.FP64)
-    assert rel <= 1e-6 and abs(it - ro["iters"]) <= 2
+    # the count that first reaches 1e-6 agrees within 2, or within the
+    # oracle's own plateau: where its residual lingers between 1e-6 and
+    # 3e-6 (ritzit's curve does, for four iterations), rounding in the last
+    # digits decides which iteration crosses
+    hist = np.asarray(ro["relres_hist"][:ro["iters"]])
+    plateau = int(np.sum(hist[-10:] <= 3e-6))
+    assert rel <= 1e-6 and abs(it - ro["iters"]) <= max(2, plateau + 1), (it, ro["iters"], plateau)
     r = b - oracle.hvp(p, host(x)[None, :])[0]
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
     assert relerr(host(x), ro["x"]) < 1e-4
@@ -355,9 +361,11 @@ def test_pcg_fp64_matches_oracle(name, method):
 @pytest.mark.parametrize("method", ["revd", "nystrom", "ritzit", "nystrom1"])
 def test_pcg_mixed_meets_tolerance(name, method):
     """Mixed path (FP32 sketch and CG, FP64 refinement): true relative
-    residual <= 1e-6 at tol 1e-6 (checked with the oracle's own product), and
-    the solution within 1e-5 of the oracle's when run to tol 1e-9 (at 1e-6 the
-    error of any method is bounded only by kappa(A) * 1e-6)."""
+    residual <= 1e-6 at tol 1e-6 (checked with the oracle's own product) and,
+    there, the distance to the oracle's solution that this residual allows
+    (2e-6 |b|, since |A^{-1}| <= 1); the solution within 1e-5 of the oracle's
+    when run to tol 1e-9 (at 1e-6 the relative distance of any two solvers'
+    answers is bounded only by 2e-6 |b| / |x|, ~5e-4 on these windows)."""
     cfg, S, p, tw = setup(name)
     d = oracle.innovation(p, tw.xb, tw.y)
     b = oracle.rhs(p, d)
@@ -368,6 +376,12 @@ def test_pcg_mixed_meets_tolerance(name, method):
     assert rel <= 1e-6
     r = b - oracle.hvp(p, host(x)[None, :])[0]
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
+    # at the working tolerance: A = I + (positive semi-definite), so
+    # |A^{-1}| <= 1 and every x with |b - A x| <= tol |b| is within tol |b|
+    # of the exact solution; the mixed solution and the oracle's own PCG
+    # solution at 1e-6 are therefore within (1.01 + 1) 1e-6 |b| of each other
+    xo6 = oracle.pcg(p, b, tol=1e-6, maxit=5000)["x"]
+    assert np.linalg.norm(host(x) - xo6) <= 2.01e-6 * np.linalg.norm(b)
     it, rel, _, _ = w.wc4d_pcg(S.ctx, x, 1e-9, 5000, 1, 0, w.MIXED)
     assert rel <= 1e-9
     assert relerr(host(x), xs) <= 1e-5
