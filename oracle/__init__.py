@@ -58,6 +58,7 @@ _I32 = C.POINTER(C.c_int32)
 _P = C.POINTER(OProblem)
 
 _SIGS = {
+    "o_threads": (C.c_int, [C.c_int]),
     "o_philox4x32_10": (None, [_U32, _U32, _U32]),
     "o_philox_words": (None, [C.c_uint64, C.c_int64, _U32]),
     "o_gaussian": (None, [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, _D]),
@@ -189,6 +190,12 @@ def gaussian(seed, rows, cols):
     G = np.zeros((cols, rows))
     lib().o_gaussian(int(seed), int(rows), int(cols), int(rows), _dp(G))
     return G
+
+
+def threads(n=0):
+    """Set (n > 0) the threads of the oracle's column loops; returns the count
+    the next loop will use."""
+    return int(lib().o_threads(int(n)))
 
 
 def corr_row(kind, n, L, variance):

@@ -32,6 +32,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -62,6 +65,19 @@ void o_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[
         x0 = y0; x1 = y1; x2 = y2; x3 = y3;
     }
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Threads of the OpenMP loops over independent columns (n > 0 sets them);
+ * returns the number the next parallel loop will use. */
+int o_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Raw words of the stream used for the probes: counter c = (c_lo, c_hi, 0, 0),

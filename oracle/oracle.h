@@ -47,6 +47,9 @@ typedef struct {
     const double *traj; /* L96 linearisation states, (N*steps+1)*n              */
 } o_problem;
 
+/* ---- threads of the column loops (OpenMP; 1 without it) -------------- */
+int o_threads(int n);
+
 /* ---- random numbers (Philox4x32-10, Box-Muller) ---------------------- */
 void o_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void o_gaussian(uint64_t seed, int64_t rows, int64_t cols, int64_t ld, double *G);

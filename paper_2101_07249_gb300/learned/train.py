@@ -3,12 +3,17 @@ encoder that `wc4d_learned_probes` runs) and writes its BF16 weights.
 
 Targets: the top-64 Ritz vectors that the library's own randomised EVD
 (REVD, q = 1, 64 + 32 Gaussian probes) produces for seeded Lorenz-96 windows
-(n = 8192, N = 10 subwindows of 8 RK4 steps; seeds 20000 + i).  Loss: one
-minus the captured fraction ||U^T orth(S)||_F^2 / 64 of the target subspace.
+(n = 8192, N = 10 subwindows of 8 RK4 steps; seeds 20000 + i).  The Hessian
+depends on the background (the linearisation trajectory) and the observation
+network, not on the observed values, so a training window needs only a
+background: a state spun up on the attractor by RK4 (5 time units from
+F + 0.01 N(0, 1)) plus a smooth random field of the background-error
+covariance's length and variance, as in the synthetic twin.  Loss: one minus
+the captured fraction ||U^T orth(S)||_F^2 / 64 of the target subspace.
 Training uses PyTorch's autograd (offline; the inference on the hot path runs
 in the library's kernels).
 
-    python -m paper_2101_07249_gb300.learned.train --count 256 --epochs 30
+    python -m paper_2101_07249_gb300.learned.train --count 2000 --epochs 8
 """
 from __future__ import annotations
 
@@ -42,6 +47,26 @@ def rk4_boundaries(x0, F, dt, N, steps):
     return np.array(out)
 
 
+def rk4_run(x0, F, dt, nsteps):
+    def f(x):
+        return (np.roll(x, -1) - np.roll(x, 2)) * np.roll(x, 1) - x + F
+    x = np.array(x0, dtype=np.float64)
+    for _ in range(nsteps):
+        k1 = f(x); k2 = f(x + 0.5 * dt * k1); k3 = f(x + 0.5 * dt * k2); k4 = f(x + dt * k3)
+        x = x + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return x
+
+
+def background(cfg, spinup=5.0):
+    """A training window's background: an RK4 spin-up onto the attractor plus
+    a smooth field of variance b_var and length b_L (the twin's recipe)."""
+    from paper_2101_07249_gb300 import inputs
+    g = inputs.rng(cfg.seed, 1)
+    x0 = cfg.F + 0.01 * g.standard_normal(cfg.n)
+    xs = rk4_run(x0, cfg.F, cfg.dt, int(round(spinup / cfg.dt)))
+    return xs + inputs._smooth_field(g, cfg.n, cfg.b_L, cfg.b_var)
+
+
 def features(cfg, xb):
     traj = rk4_boundaries(xb, cfg.F, cfg.dt, cfg.N, cfg.steps) / cfg.F
     mask = np.zeros((cfg.N + 1, cfg.n))
@@ -71,9 +96,9 @@ def captured(net, x, U, m, Np1):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--count", type=int, default=256)
-    ap.add_argument("--holdout", type=int, default=16)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--count", type=int, default=2000)
+    ap.add_argument("--holdout", type=int, default=32)
+    ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--out", default=WEIGHTS)
     args = ap.parse_args()
 
@@ -86,13 +111,16 @@ def main():
     t0 = time.time()
     for i in range(args.count + args.holdout):
         cfg = window(20000 + i)
-        tw = inputs.twin(cfg, spinup=5.0)
-        S = w.Solver(cfg, tw)
+        xb = background(cfg)
+        S = w.Solver(cfg)
+        w.wc4d_set_background_obs(S.ctx, xb, np.zeros(cfg.nobs))
         w.wc4d_sketch(S.ctx, w.REVD, m, cfg.l, 1, 7 + i, None, w.MIXED)
         U = torch.zeros(m, cfg.nA, dtype=torch.float64, device="cuda")
         w.wc4d_get_ritz(S.ctx, U, m)
         S.close()
-        data.append((torch.as_tensor(features(cfg, tw.xb), device="cuda"), U.float()))
+        data.append((torch.as_tensor(features(cfg, xb), device="cuda"), U.float()))
+        if (i + 1) % 250 == 0:
+            print(f"  {i + 1} windows, {time.time() - t0:.0f} s", flush=True)
     print(f"targets: {len(data)} windows in {time.time() - t0:.0f} s", flush=True)
 
     cfg = window(0)
