@@ -3,6 +3,7 @@
 // runs in the kernels of setup.cu / sweep.cu / linalg.cu / tc_gemm.cu /
 // l96.cu; this file only sequences them on the context's stream.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -362,6 +363,13 @@ extern "C" wc4d_status wc4d_set_reliable_delta(wc4d_ctx *c, double delta)
     return WC4D_OK;
 }
 
+extern "C" wc4d_status wc4d_set_wait_limit(wc4d_ctx *c, int64_t polls)
+{
+    if (!c || polls > (int64_t)UINT32_MAX) return WC4D_EINVAL;
+    c->wait_limit = polls < 0 ? (1u << 22) : (unsigned)polls;
+    return WC4D_OK;
+}
+
 extern "C" wc4d_status wc4d_set_graphs(wc4d_ctx *c, int32_t enable)
 {
     if (!c) return WC4D_EINVAL;
@@ -479,12 +487,14 @@ extern "C" wc4d_status wc4d_set_covariance(wc4d_ctx *c, int32_t block, int32_t c
 {
     if (!c || block < 0 || block > 1 || corr < 0 || corr > 2 || !(variance >= 0.0)) return WC4D_EINVAL;
     if (corr != WC4D_CORR_DIAG && !(L > 0.0 && L < 1e300)) return WC4D_EINVAL;
+    c->cov_sd[block] = (corr == WC4D_CORR_DIAG) ? std::sqrt(variance) : -1.0;
     return cov_sqrt_setup(c, block, corr, L, variance, nullptr);
 }
 
 extern "C" wc4d_status wc4d_set_covariance_row(wc4d_ctx *c, int32_t block, const double *row_host)
 {
     if (!c || block < 0 || block > 1 || !row_host) return WC4D_EINVAL;
+    c->cov_sd[block] = -1.0;
     WC4D_TRY(ensure(c, c->small3, sizeof(double) * c->prob.n));
     WC4D_CUDA(c, cudaMemcpyAsync(c->small3.p, row_host, sizeof(double) * c->prob.n, cudaMemcpyHostToDevice,
                                  c->stream));
@@ -559,7 +569,7 @@ static bool persistent_sweep(wc4d_ctx *c, T *W, int mode)
     const T *M0 = (mode == 0) ? Ops<T>::M(c, 0) : Ops<T>::MT(c, 0);
     return launch_gemv_sweep<T>(c->stream, c->num_sms, n, c->prob.N, M0, mstride, W, mode, 1.0 / c->prob.sigma_o2,
                                 c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride,
-                                bar + 1, reinterpret_cast<int *>(bar));
+                                bar + 1, reinterpret_cast<int *>(bar), c->wait_limit);
 }
 
 // Timeout flag of the persistent sweeps (cleared on read).
@@ -1120,6 +1130,68 @@ extern "C" wc4d_status wc4d_symeig(wc4d_ctx *c, int32_t m, const double *S, doub
     }
     free_buf(wb);
     return s;
+}
+
+// Pieces of the orthonormalisation and Rayleigh-Ritz steps of Alg. 3-5 for
+// callers that distribute the rows of a block over several devices and sum
+// the partial Gram matrices themselves (the column-sharded sketch).
+extern "C" wc4d_status wc4d_gram(wc4d_ctx *c, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t rows,
+                                 int32_t ma, int32_t mb, double *C, int32_t precision)
+{
+    if (!c || !A || !B || !C || rows < 1 || ma < 1 || mb < 1 || lda < rows || ldb < rows) return WC4D_EINVAL;
+    if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
+    const size_t need = atb_part_doubles(c->num_sms, rows, ma, mb, 0);
+    WC4D_TRY(ensure(c, c->part, sizeof(double) * need));
+    int S = 0;
+    ProfScope ps(c, PROF_GRAM);
+    int r;
+    if (precision == WC4D_FP64)
+        r = launch_atb<double>(c->stream, c->num_sms, rows, ma, mb, static_cast<const double *>(A), lda,
+                               static_cast<const double *>(B), ldb, P<double>(c->part), c->part.bytes / 8, &S, C, 0);
+    else
+        r = launch_atb<float>(c->stream, c->num_sms, rows, ma, mb, static_cast<const float *>(A), lda,
+                              static_cast<const float *>(B), ldb, P<double>(c->part), c->part.bytes / 8, &S, C, 0);
+    if (r != 0) return set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small");
+    return check_launch(c, "gram");
+}
+
+extern "C" wc4d_status wc4d_chol_inverse(wc4d_ctx *c, int32_t m, const double *G, double *Rinv)
+{
+    if (!c || !G || !Rinv || m < 1) return WC4D_EINVAL;
+    WC4D_TRY(ensure(c, c->small1, sizeof(double) * (size_t)m * m));
+    double *R = P<double>(c->small1);
+    int info = 0;
+    {
+        ProfScope psc(c, PROF_CHOL);
+        launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));
+        launch_trinv_upper(c->stream, m, R, Rinv);
+        WC4D_TRY(check_launch(c, "chol_inverse"));
+        WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    }
+    WC4D_TRY(sync(c, "chol_inverse"));
+    if (info != 0) return set_err(c, WC4D_ENOTSPD, "Cholesky: matrix not positive definite at pivot %d", info);
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_tall_times_small(wc4d_ctx *c, const void *Y, int64_t ldy, int64_t rows, int32_t m,
+                                             const double *W, int32_t k, void *Z, int64_t ldz, int32_t precision)
+{
+    if (!c || !Y || !W || !Z || rows < 1 || m < 1 || k < 1 || ldy < rows || ldz < rows) return WC4D_EINVAL;
+    if (rows > INT32_MAX) return set_err(c, WC4D_EINVAL, "tall_times_small: more than 2^31 - 1 rows");
+    if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
+    ProfScope psl(c, PROF_LA);
+    Epi e{0, 1.0, 0.0, 0.0, 1};
+    if (precision == WC4D_FP64) {
+        launch_gemm<double>(c->stream, (int)rows, k, m, static_cast<const double *>(Y), 1, ldy, W, m,
+                            static_cast<double *>(Z), ldz, e);
+    } else {
+        WC4D_TRY(ensure(c, c->small3, sizeof(float) * (size_t)m * k));
+        float *W32 = P<float>(c->small3);
+        launch_convert_f64_f32(c->stream, (int64_t)m * k, W, W32);
+        launch_gemm<float>(c->stream, (int)rows, k, m, static_cast<const float *>(Y), 1, ldy, W32, m,
+                           static_cast<float *>(Z), ldz, e);
+    }
+    return check_launch(c, "tall_times_small");
 }
 
 // ============================================================================

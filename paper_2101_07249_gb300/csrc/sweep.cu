@@ -6,6 +6,8 @@
 #include <mutex>
 #include <tuple>
 
+#include <algorithm>
+
 #include "wc4d_internal.cuh"
 
 template <typename T> struct Cplx;
@@ -427,12 +429,43 @@ k_circ_direct(int n, int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, i
     }
 }
 
+// Y = sd X (+ addX) on time blocks t0 .. t1-1 of K columns: a covariance
+// block that is a multiple of the identity needs no transform.
+template <typename T>
+__global__ void k_diag_blocks(int n, int t0, int t1, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy,
+                              const T *addX, int64_t ld_add, T sd)
+{
+    const int64_t per = (int64_t)(t1 - t0) * n, tot = per * K;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / per, r = (int64_t)t0 * n + e % per;
+        const T v = sd * X[j * ldx + r];
+        Y[j * ldy + r] = addX ? v + addX[j * ld_add + r] : v;
+    }
+}
+
+template <typename T>
+static void launch_diag_blocks(cudaStream_t s, const wc4d_ctx *c, int t0, int t1, int K, const T *X, int64_t ldx,
+                               T *Y, int64_t ldy, const T *addX, int64_t ld_add, double sd)
+{
+    const int64_t tot = (int64_t)(t1 - t0) * c->prob.n * K;
+    const int grid = (int)std::min<int64_t>((tot + 255) / 256, 8 * (int64_t)c->num_sms);
+    WC4D_LAUNCH(k_diag_blocks<T><<<grid, 256, 0, s>>>(c->prob.n, t0, t1, K, X, ldx, Y, ldy, addX, ld_add, (T)sd));
+}
+
 template <typename T>
 void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy,
                       const T *addX, int64_t ld_add, bool fft, const T *specB, const T *specQ, const T *rowB,
                       const T *rowQ, const void *tw)
 {
     const int n = c->prob.n, N = c->prob.N;
+    // the FFT path transforms only the non-diagonal covariance blocks
+    // (Lorenz-96: Q = 0.05 I needs no transform for its N blocks)
+    const double sdB = c->cov_sd[0], sdQ = c->cov_sd[1];
+    if (fft && (sdB >= 0.0 || sdQ >= 0.0)) {
+        if (sdB >= 0.0) launch_diag_blocks<T>(s, c, 0, 1, K, X, ldx, Y, ldy, addX, ld_add, sdB);
+        if (sdQ >= 0.0) launch_diag_blocks<T>(s, c, 1, N + 1, K, X, ldx, Y, ldy, addX, ld_add, sdQ);
+        if (sdB >= 0.0 && sdQ >= 0.0) return;
+    }
     if (fft) {
         size_t smem = (size_t)(n + n / 16 + n / 2) * sizeof(typename Cplx<T>::t);
         static const bool attr = [] {
@@ -444,6 +477,8 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
         int nB = (K + 1) / 2;
         int64_t nQ = ((int64_t)K * N + 1) / 2;
         int grid = (int)(nB + nQ);
+        if (sdQ >= 0.0) grid = nB;                 // block 0 only (pairs < nB are B's)
+        else if (sdB >= 0.0) { grid = (int)nQ; nB = 0; }   // Q blocks only
         switch (c->logn) {   // n / 16 threads, 16 values each
         case 9: launch_stockham<T, 9>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
         case 10: launch_stockham<T, 10>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
@@ -657,13 +692,15 @@ struct SweepArgs {
     int pf;               // staged form: stages prefetched into L2 ahead of the ring
     unsigned *bar;        // N zeroed arrival counters, one per step barrier
     int *err;
+    unsigned wait_limit;  // polls of a barrier before it gives up (0: fail unless already complete)
 };
 
 // Grid barrier of step t: every CTA adds one to its own counter cnt[t]
 // (release) and waits until it reads nblocks (acquire).  Counters are zeroed
-// before each launch, so no reset or generation word is needed.  Bounded: a
-// timeout records the error and returns false.
-__device__ __forceinline__ bool step_barrier(unsigned *cnt, int t, unsigned nblocks, int *err)
+// before each launch, so no reset or generation word is needed.  Bounded: after
+// `limit` unsuccessful polls it records the error and returns false (limit 0:
+// fail unless the barrier is already complete at the first poll).
+__device__ __forceinline__ bool step_barrier(unsigned *cnt, int t, unsigned nblocks, int *err, unsigned limit)
 {
     __shared__ int ok_s;
     __syncthreads();
@@ -671,10 +708,11 @@ __device__ __forceinline__ bool step_barrier(unsigned *cnt, int t, unsigned nblo
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt + t) : "memory");
         unsigned v = 0, it = 0;
         int ok = 1;
-        do {
+        for (;;) {
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt + t) : "memory");
-            if (++it > (1u << 22)) { ok = 0; atomicExch(err, 1); break; }
-        } while (v < nblocks);
+            if (v >= nblocks) break;
+            if (it++ >= limit) { ok = 0; atomicExch(err, 1); break; }
+        }
         ok_s = ok;
     }
     __syncthreads();
@@ -750,7 +788,7 @@ k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
                 y[row] = (T)out;
             }
         }
-        if (step + 1 < a.N && !step_barrier(a.bar, step, gridDim.x, a.err)) return;
+        if (step + 1 < a.N && !step_barrier(a.bar, step, gridDim.x, a.err, a.wait_limit)) return;
     }
 }
 
@@ -1023,7 +1061,7 @@ static bool launch_sweep_staged(cudaStream_t s, int num_sms, const float *M0, fl
 // SM, co-resident by cooperative launch).  Returns false if it cannot be used.
 template <typename T>
 bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, int64_t mstride, T *W, int mode,
-                       double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err)
+                       double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err, unsigned wait_limit)
 {
     constexpr int VEC = sizeof(T) == 8 ? 2 : 4;
     if (n % VEC != 0 || !aligned16(M0) || !aligned16(W) || ((int64_t)n * sizeof(T)) % 16 != 0) return false;
@@ -1051,6 +1089,7 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
     args.ts = ts > 0 ? ts : 1;
     args.bar = bar;
     args.err = err;
+    args.wait_limit = wait_limit;
     {
         // FP32 only: the FP64 sweep is bound by the FP64 pipe, where the
         // per-row shuffle reductions of the staged form cost more than the
@@ -1081,9 +1120,9 @@ bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, i
 }
 
 template bool launch_gemv_sweep<double>(cudaStream_t, int, int, int, const double *, int64_t, double *, int, double,
-                                        int, int, int, unsigned *, int *);
+                                        int, int, int, unsigned *, int *, unsigned);
 template bool launch_gemv_sweep<float>(cudaStream_t, int, int, int, const float *, int64_t, float *, int, double,
-                                       int, int, int, unsigned *, int *);
+                                       int, int, int, unsigned *, int *, unsigned);
 
 template <typename T>
 void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,

@@ -80,6 +80,7 @@ struct wc4d_ctx {
     DevBuf row64[2], row32[2];      // direct path: first row of the square root
     DevBuf tw64, tw32;              // FFT twiddles e^{-2 pi i j / n}, j < n/2
     DevBuf cosn;                    // cos/sin table e^{2 pi i j/n}, j < n (set-up DFTs)
+    double cov_sd[2] = {-1.0, -1.0};  // sqrt(variance) of a block that is variance * I, else -1
 
     // observations and right-hand side
     DevBuf d, rhs, Dm12b;
@@ -117,6 +118,7 @@ struct wc4d_ctx {
     // persistent one-column sweeps: grid barrier words and error flag
     DevBuf sweep_bar;
     bool sweep_bar_zeroed = false;
+    unsigned wait_limit = 1u << 22;   // polls of the persistent sweeps' grid barriers (wc4d_set_wait_limit)
 
     // Ritz pairs
     int kU = 0;
@@ -207,10 +209,12 @@ template <typename T>
 void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
                        const Epi &e);
 // Persistent one-column sweep over all subwindows (cooperative launch);
-// bar: N zeroed unsigned (one arrival counter per step); err set on a timeout.
+// bar: N zeroed unsigned (one arrival counter per step); err set on a timeout
+// (a grid barrier that stays incomplete for wait_limit polls; the staged FP32
+// form keeps its own limit).
 template <typename T>
 bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, int64_t mstride, T *W, int mode,
-                       double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err);
+                       double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err, unsigned wait_limit);
 template <typename T>
 void launch_obs_block(cudaStream_t s, int n, int K, T *W, int64_t ld, double scale, int stride);
 

@@ -25,7 +25,9 @@ def setup(n, N, gauss=False):
     key = (n, N, gauss)
     if key not in _cache:
         cfg = inputs.scaled(inputs.LARGE, n=n, N=N, k=8, l=4)
-        if gauss:       # the Lorenz-96 covariances on the advection-diffusion model
+        if gauss == "bdiag":    # B a multiple of the identity, Q SOAR (no transform of block 0)
+            cfg = cfg.replace(b_kind=inputs.DIAG, b_var=0.3)
+        elif gauss:     # the Lorenz-96 covariances on the advection-diffusion model (no transform of Q's blocks)
             L96 = inputs.L96
             cfg = cfg.replace(b_kind=L96.b_kind, b_var=L96.b_var, b_L=L96.b_L, q_kind=L96.q_kind,
                               q_var=L96.q_var, q_L=L96.q_L)
@@ -40,7 +42,7 @@ def colrel(A, B):
 
 
 @pytest.mark.parametrize("n,N,gauss", [(512, 3, False), (1024, 2, False), (2048, 3, False), (4096, 2, False),
-                                       (8192, 2, False), (1024, 2, True), (8192, 2, True)])
+                                       (8192, 2, False), (1024, 2, True), (8192, 2, True), (2048, 3, "bdiag")])
 @pytest.mark.parametrize("K", [1, 3, 8])
 def test_dsqrt_stockham_matches_oracle(n, N, gauss, K):
     cfg, S, p = setup(n, N, gauss)
