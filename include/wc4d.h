@@ -275,6 +275,28 @@ wc4d_status wc4d_symeig(wc4d_ctx *ctx, int32_t m, const double *S_device, double
 wc4d_status wc4d_apply_dsqrt(wc4d_ctx *ctx, const void *X, void *Y, int32_t K, int64_t ld, int32_t precision);
 wc4d_status wc4d_apply_linv(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int32_t precision);
 wc4d_status wc4d_apply_linvT(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int32_t precision);
+/* Pieces of the orthonormalisation (CholeskyQR) and Rayleigh-Ritz steps of
+ * Alg. 3-5, for callers that distribute the rows of a block over several
+ * devices and sum the partial Gram matrices themselves (the column-sharded
+ * sketch; the paper notes that the products with A and the block work can be
+ * parallelised).  All pointers are device memory of the context's device;
+ * blocks are column-major.
+ *   wc4d_gram: C = A^T B (ma x mb, ld ma, FP64) for A (rows x ma, lda) and B
+ *     (rows x mb, ldb): FP64 data with FP64 sums (WC4D_FP64), or FP32 data
+ *     with exact products and double-float sums (WC4D_MIXED; entries of
+ *     magnitude up to ~2^60, so that products and partial sums stay finite
+ *     in FP32's exponent range).
+ *   wc4d_chol_inverse: G = R^T R (m x m SPD, FP64) and Rinv = R^{-1} (upper
+ *     triangular, m x m, ld m); ENOTSPD when G is not numerically positive
+ *     definite.
+ *   wc4d_tall_times_small: Z = Y W for Y (rows x m, ldy; FP64, or FP32 with
+ *     WC4D_MIXED) and W (m x k FP64, ld m; rounded to FP32 for FP32 data); Z
+ *     (rows x k, ldz) in Y's precision; Z must not overlap Y; rows < 2^31. */
+wc4d_status wc4d_gram(wc4d_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t rows, int32_t ma,
+                      int32_t mb, double *C, int32_t precision);
+wc4d_status wc4d_chol_inverse(wc4d_ctx *ctx, int32_t m, const double *G, double *Rinv);
+wc4d_status wc4d_tall_times_small(wc4d_ctx *ctx, const void *Y, int64_t ldy, int64_t rows, int32_t m, const double *W,
+                                  int32_t k, void *Z, int64_t ldz, int32_t precision);
 /* Copy the FP64 propagator of subwindow t (dense model) to device memory. */
 wc4d_status wc4d_get_propagator(wc4d_ctx *ctx, int32_t t, double *M_device);
 /* Kernel launches issued by the library in this process (all contexts). */
@@ -350,6 +372,15 @@ int32_t     wc4d_jacobi_fp32_kernel(const wc4d_ctx *ctx);
    results are bitwise those of the eager launches.  enable = 0 keeps every
    iteration eager.  EINVAL for a null context. */
 wc4d_status wc4d_set_graphs(wc4d_ctx *ctx, int32_t enable);
+/* Polls of the grid barriers of the persistent one-column sweeps (the FP64
+   sweep, and the FP32 sweep when n is not a multiple of 2048) before a wait
+   gives up: the kernel then records the failure and returns, and the call
+   that ran it (wc4d_pcg, wc4d_inner_loop) returns WC4D_ETIMEOUT with the
+   context still usable.  No asynchronous copy is in flight at these waits.
+   polls < 0 restores the default (2^22, seconds); 0 makes any barrier that
+   is not already complete at its first poll fail at once, which exercises
+   the timeout path.  EINVAL for a null context or polls >= 2^32. */
+wc4d_status wc4d_set_wait_limit(wc4d_ctx *ctx, int64_t polls);
 /* Mixed-precision CG (reliable updates): the FP32 recurrence residual must
    fall by the factor delta (0 < delta <= 1, default 1e-3) since the last
    update, or claim convergence, before the FP64 true residual replaces it.

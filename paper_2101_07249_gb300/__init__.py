@@ -79,6 +79,11 @@ _SIGS = {
                                   C.c_int32, C.c_int32, _V, _I32, _D]),
     "wc4d_orthonormalize": (C.c_int, [_V, _V, C.c_int64, C.c_int32, C.c_int64, _D, C.c_int32]),
     "wc4d_symeig": (C.c_int, [_V, C.c_int32, _V, _D, _V]),
+    "wc4d_set_wait_limit": (C.c_int, [_V, C.c_int64]),
+    "wc4d_gram": (C.c_int, [_V, _V, C.c_int64, _V, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _V, C.c_int32]),
+    "wc4d_chol_inverse": (C.c_int, [_V, C.c_int32, _V, _V]),
+    "wc4d_tall_times_small": (C.c_int, [_V, _V, C.c_int64, C.c_int64, C.c_int32, _V, C.c_int32, _V, C.c_int64,
+                                        C.c_int32]),
     "wc4d_hvp_count": (C.c_int64, [_V, C.c_int32]),
     "wc4d_jacobi_sweeps": (C.c_int32, [_V]),
     "wc4d_jacobi_sweeps_fp32": (C.c_int32, [_V]),
@@ -384,6 +389,38 @@ def wc4d_symeig(ctx, m, S, V):
     w = np.zeros(int(m))
     _check(ctx, load().wc4d_symeig(ctx, int(m), _ptr(S), _hp(w), _ptr(V)))
     return w
+
+
+def wc4d_set_wait_limit(ctx, polls):
+    """Polls of the persistent sweeps' grid barriers before a timeout (< 0: default)."""
+    _check(ctx, load().wc4d_set_wait_limit(ctx, int(polls)))
+
+
+def wc4d_gram(ctx, A, lda, B, ldb, rows, ma, mb, C_out, precision=FP64):
+    """C_out = A^T B (ma x mb FP64, column-major) for column-major blocks A
+    (rows x ma, lda) and B (rows x mb, ldb) of the given precision."""
+    import torch
+    dt, rows, ma, mb, lda, ldb = _fdtype(precision), int(rows), int(ma), int(mb), int(lda), int(ldb)
+    _check(ctx, load().wc4d_gram(ctx, _dev(A, dt, (ma - 1) * lda + rows, "A"), lda,
+                                 _dev(B, dt, (mb - 1) * ldb + rows, "B"), ldb, rows, ma, mb,
+                                 _dev(C_out, torch.float64, ma * mb, "C"), int(precision)))
+
+
+def wc4d_chol_inverse(ctx, m, G, Rinv):
+    """G = R^T R (m x m FP64 SPD): Rinv = R^{-1} (FP64, m x m)."""
+    import torch
+    m = int(m)
+    _check(ctx, load().wc4d_chol_inverse(ctx, m, _dev(G, torch.float64, m * m, "G"),
+                                         _dev(Rinv, torch.float64, m * m, "Rinv")))
+
+
+def wc4d_tall_times_small(ctx, Y, ldy, rows, m, W, k, Z, ldz, precision=FP64):
+    """Z = Y W: Y (rows x m, ldy) in the given precision, W (m x k FP64), Z (rows x k, ldz)."""
+    import torch
+    dt, rows, m, k, ldy, ldz = _fdtype(precision), int(rows), int(m), int(k), int(ldy), int(ldz)
+    _check(ctx, load().wc4d_tall_times_small(ctx, _dev(Y, dt, (m - 1) * ldy + rows, "Y"), ldy, rows, m,
+                                             _dev(W, torch.float64, m * k, "W"), k,
+                                             _dev(Z, dt, (k - 1) * ldz + rows, "Z"), ldz, int(precision)))
 
 
 def wc4d_apply_dsqrt(ctx, X, Y, K, ld, precision=FP64):

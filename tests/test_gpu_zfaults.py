@@ -49,3 +49,26 @@ def test_nan_observation_is_reported_and_the_context_recovers():
     it1, rel1, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 0, 0, w.FP64)
     assert it1 == it0 and rel1 <= 1e-6 and abs(rel1 - rel0) <= 1e-12
     S.close()
+
+
+def test_grid_barrier_timeout_is_reported_and_the_context_recovers():
+    """A bounded device-side wait that runs out: with a wait limit of 0 the
+    persistent FP64 sweep's grid barrier gives up at its first incomplete
+    poll (no asynchronous copy is in flight there), the kernel records the
+    failure and returns, and the solve returns WC4D_ETIMEOUT; with the
+    default limit restored the context reproduces its earlier result
+    bit for bit."""
+    cfg, tw, S = _solver()
+    x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
+    it0, rel0, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 0, 8, w.FP64)
+    x0 = x.cpu().numpy().copy()
+    w.wc4d_set_wait_limit(S.ctx, 0)
+    with pytest.raises(w.WC4DError) as e:
+        w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 0, 8, w.FP64)
+    assert e.value.status == w.ETIMEOUT
+    w.wc4d_set_wait_limit(S.ctx, -1)
+    x.zero_()
+    it1, rel1, _, _ = w.wc4d_pcg(S.ctx, x, 1e-6, 5000, 0, 8, w.FP64)
+    assert it1 == it0 == 8 and rel1 == rel0
+    assert np.array_equal(x.cpu().numpy(), x0)
+    S.close()
