@@ -140,6 +140,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     __shared__ int failed;
     __shared__ int n_issued, n_consumed;
 
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM;
     const int kbeg = blockIdx.y * a.kchunk;
@@ -165,10 +166,21 @@ k_tc_sweep(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // producer
-        for (int kb = 0; kb < nk; ++kb) {
+        // producer: the first ring of propagator tiles does not depend on the
+        // previous kernel of the stream; the probe block (and the partial
+        // buffer this grid overwrites) do
+        const int pre = nk < STAGES ? nk : STAGES;
+        for (int kb = 0; kb < pre; ++kb) {
+            mbar_expect_tx(&full[kb], A_STAGE_BYTES + b_stage_bytes);
+            tma_load_2d(sA + kb * A_STAGE_BYTES, &tmA, kbeg + kb * BKF, a.a_row0 + m0, &full[kb]);
+        }
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        for (int kb = 0; kb < pre; ++kb)
+            tma_load_2d(sB + kb * B_STAGE_BYTES_MAX, &tmB, a.b_x0 + kbeg + kb * BKF, 0, &full[kb]);
+        n_issued = pre;
+        for (int kb = pre; kb < nk; ++kb) {
             const int s = kb % STAGES, round = kb / STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) { failed = 1; break; }
+            if (!mbar_wait(&empty[s], (round - 1) & 1)) { failed = 1; break; }
             mbar_expect_tx(&full[s], A_STAGE_BYTES + b_stage_bytes);
             const int kx = kbeg + kb * BKF;
             tma_load_2d(sA + s * A_STAGE_BYTES, &tmA, kx, a.a_row0 + m0, &full[s]);
@@ -194,6 +206,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         mma_commit(done);
     }
     __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");      // the partials below are read by the previous grid
     // epilogue: all four warps; warp w owns tensor-memory lanes 32w .. 32w+31.
     // The decision to read tensor memory is uniform per warp (tcgen05.ld is
     // a warp-collective instruction).
@@ -256,22 +269,53 @@ __global__ void k_round_block(int n, int K, const float *__restrict__ src, int64
 }
 
 // C(i, j) = epi(sum_s part[s][j][i]) over the n x K output block, and
-// Cr(i, j) = tf32(C(i, j)).
+// Cr(i, j) = tf32(C(i, j)); four rows per thread (float4), column j =
+// blockIdx.y.  Launched as a programmatic dependent of the product kernel:
+// it waits for that grid before reading the partials.
 __global__ void __launch_bounds__(256)
 k_tc_reduce(int n, int K, int splits, const float *__restrict__ part, float *C, int64_t ldc, float *Cr,
             int64_t ldr, Epi e)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n * K) return;
-    const int i = (int)(idx % n), j = (int)(idx / n);
-    float acc = 0.f;
-    for (int s = 0; s < splits; ++s) acc += part[((int64_t)s * K + j) * n + i];
-    float *dst = C + (int64_t)j * ldc + i;
-    float out;
-    if (e.mode == 1) out = acc + ((i % e.obs_stride == 0) ? (float)e.obs_scale * (*dst) : 0.f);
-    else out = (float)e.alpha * acc + (e.beta != 0.0 ? (float)e.beta * (*dst) : 0.f);
-    *dst = out;
-    Cr[(int64_t)j * ldr + i] = round_tf32(out);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x), j = blockIdx.y;
+    if (i >= n) return;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < splits; ++s) {
+        const float4 v = *reinterpret_cast<const float4 *>(part + ((int64_t)s * K + j) * n + i);
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    float4 *dst = reinterpret_cast<float4 *>(C + (int64_t)j * ldc + i);
+    const float4 old = *dst;
+    float a[4] = {acc.x, acc.y, acc.z, acc.w}, o[4] = {old.x, old.y, old.z, old.w}, out[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (e.mode == 1) out[q] = a[q] + (((i + q) % e.obs_stride == 0) ? (float)e.obs_scale * o[q] : 0.f);
+        else out[q] = (float)e.alpha * a[q] + (e.beta != 0.0 ? (float)e.beta * o[q] : 0.f);
+    }
+    *dst = make_float4(out[0], out[1], out[2], out[3]);
+    *reinterpret_cast<float4 *>(Cr + (int64_t)j * ldr + i) =
+        make_float4(round_tf32(out[0]), round_tf32(out[1]), round_tf32(out[2]), round_tf32(out[3]));
+}
+
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel of the stream drains and must griddepcontrol.wait
+// before it touches what that kernel writes or reads.
+template <typename... KArgs, typename... Args>
+static bool launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    wc4d_note_launch();
+    return cudaLaunchKernelEx(&cfg, kernel, args...) == cudaSuccess;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -344,13 +388,22 @@ bool tc_product(wc4d_ctx *c, const CUtensorMap &mA, const CUtensorMap &mB, int K
     const int n = c->prob.n;
     TcArgs args{n, K, n / splits, a_row0, b_x0, part, err};
     dim3 grid(n / BM, splits);
+    // a refused programmatic launch falls back to ordinary stream order
+    // (griddepcontrol.wait then returns at once)
     {
         ProfScope ps(c, PROF_TC);
-        WC4D_LAUNCH(k_tc_sweep<<<grid, 128, SMEM_BYTES, c->stream>>>(mA, mB, args));
+        if (!launch_pdl(k_tc_sweep, grid, dim3(128), SMEM_BYTES, c->stream, mA, mB, args)) {
+            cudaGetLastError();
+            WC4D_LAUNCH(k_tc_sweep<<<grid, 128, SMEM_BYTES, c->stream>>>(mA, mB, args));
+        }
     }
-    const int64_t tot = (int64_t)n * K;
-    WC4D_LAUNCH(k_tc_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(n, K, splits, part, C, ldc, Cr, c->nA, e));
-    return true;
+    const dim3 rgrid(ceil_div(n / 4, 256), K);
+    if (!launch_pdl(k_tc_reduce, rgrid, dim3(256), 0, c->stream, n, K, splits, (const float *)part, C, ldc, Cr, c->nA,
+                    e)) {
+        cudaGetLastError();
+        WC4D_LAUNCH(k_tc_reduce<<<rgrid, 256, 0, c->stream>>>(n, K, splits, part, C, ldc, Cr, c->nA, e));
+    }
+    return cudaPeekAtLastError() == cudaSuccess;
 }
 
 }  // namespace
@@ -419,8 +472,9 @@ bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld)
     round_block(c, K, W, ld, Wr);
     for (int t = 0; t < N; ++t) {
         const int blk = (c->nM == 1) ? 0 : t;
-        tc_product(c, mA, mB, K, blk * n, t * n, W + (int64_t)(t + 1) * n, ld, Wr + (int64_t)(t + 1) * n, e, splits,
-                   part, err);
+        if (!tc_product(c, mA, mB, K, blk * n, t * n, W + (int64_t)(t + 1) * n, ld, Wr + (int64_t)(t + 1) * n, e,
+                        splits, part, err))
+            return false;
     }
     return true;
 }
@@ -444,8 +498,9 @@ bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld)
     for (int t = N - 1; t >= 0; --t) {
         const int blk = (c->nM == 1) ? 0 : t;
         Epi e{1, 1.0, 0.0, obs_scale(t), p.obs_stride};
-        tc_product(c, mA, mB, K, blk * n, (t + 1) * n, W + (int64_t)t * n, ld, Wr + (int64_t)t * n, e, splits, part,
-                   err);
+        if (!tc_product(c, mA, mB, K, blk * n, (t + 1) * n, W + (int64_t)t * n, ld, Wr + (int64_t)t * n, e, splits,
+                        part, err))
+            return false;
     }
     return true;
 }

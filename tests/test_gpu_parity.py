@@ -480,14 +480,19 @@ def test_sketch_256_columns_matches_oracle(method):
 AD_TC = inputs.scaled(inputs.TINY, n=512, N=4, k=240, l=16, obs_stride=8)
 
 
-@pytest.mark.parametrize("K", [16, 48, 256])
-def test_tensor_core_sweeps_match_oracle(K):
+@pytest.mark.parametrize("n,N,K", [(512, 4, 16), (512, 4, 48), (512, 4, 256), (1024, 3, 256), (2048, 3, 256)])
+def test_tensor_core_sweeps_match_oracle(n, N, K):
     """Mixed sweeps with K a multiple of 16 and n a multiple of 128 run as
-    tcgen05 TF32 MMAs (8 pipeline stages per CTA here).  Operands are rounded
-    to the nearest TF32 value (2^-11 relative, unbiased), so the error stays
-    near 1e-4; the tensor cores' own truncation would bias every product by
-    about -1e-3 and fail both checks."""
-    cfg = AD_TC
+    tcgen05 TF32 MMAs.  Split-K over S CTAs per 128-row block: S = 2 (n =
+    512), 4 (n = 1024, the large window's split) and 8 (n = 2048); when each
+    CTA's share of the columns is whole 32-column chunks (K = 256 here) the
+    splits are reduced inside a thread-block cluster through distributed
+    shared memory, otherwise through global memory and a second kernel.
+    Operands are rounded to the nearest TF32 value (2^-11 relative,
+    unbiased), so the error stays near 1e-4; the tensor cores' own
+    truncation would bias every product by about -1e-3 and fail both
+    checks."""
+    cfg = AD_TC if n == 512 else inputs.scaled(inputs.TINY, n=n, N=N, k=240, l=16, obs_stride=8)
     tw = inputs.twin(cfg)
     S = w.Solver(cfg, tw)
     p = oracle_problem(cfg, xb=tw.xb)
