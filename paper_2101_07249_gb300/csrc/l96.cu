@@ -288,22 +288,21 @@ k_l96_adj_cl(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, i
 }
 
 // ---------------------------------------------------------------------------
-// Register-blocked FP32 sweeps (n = 8 nt with nt a multiple of 32, nt <= 1024):
-// thread tau owns the contiguous run of points 8 tau .. 8 tau + 7 of C probe
-// columns.  The running stage input u and the RK4 accumulator live in
-// registers; the step's base state (d for the tangent-linear sweep, lambda
-// for the adjoint) is thread-private and kept in shared memory laid out
-// [c][p][tau] (consecutive lanes, consecutive words).  The stage state x of
-// the trajectory is staged in shared memory, double-buffered: each thread
-// copies its 32-byte slice of the next stage's x with cp.async while the
-// current stage computes, so the L2 latency is off the critical path, and
-// x serves all C columns.  The stencils' halos of u and x come from the
-// neighbouring lanes by warp shuffles and, at warp boundaries, from a small
-// double-buffered edge table (u) or the staged x; one __syncthreads per RK4
-// stage orders it all.
+// Register-blocked FP32 sweeps (n = P nt, nt a multiple of 32 and <= 1024; P
+// = 8 points per thread): thread tau owns
+// the contiguous run of points P tau .. P tau + P - 1 of C probe columns.
+// The running stage input u and the RK4 accumulator live in registers; the
+// step's base state (d for the tangent-linear sweep, lambda for the adjoint)
+// is thread-private and kept in shared memory as float4 quads laid out
+// [c][p/4][tau] (consecutive lanes, consecutive 16-byte words: one
+// conflict-free 128-bit access per quad).  The stage state x of the
+// trajectory is staged in shared memory, double-buffered: each thread copies
+// its slice of the next stage's x with cp.async while the current stage
+// computes, so the L2 latency is off the critical path, and x serves all C
+// columns.  The stencils' halos of u and x come from the neighbouring lanes by
+// warp shuffles and, at warp boundaries, from a small double-buffered edge
+// table (u) or the staged x; one __syncthreads per RK4 stage orders it all.
 // ---------------------------------------------------------------------------
-constexpr int L96_RB_P = 8;   // points per thread
-
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
@@ -313,129 +312,240 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Stage this thread's 8 points of the stage state x into xb.
+// Stage this thread's P points of the stage state x into xb.
+template <int P>
 __device__ __forceinline__ void stage_x_async(float *xb, const float *__restrict__ x, int j0)
 {
-    cp_async16(xb + j0, x + j0);
-    cp_async16(xb + j0 + 4, x + j0 + 4);
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) cp_async16(xb + j0 + 4 * q, x + j0 + 4 * q);
     cp_async_commit();
 }
 
-// x at points j0 - 2 .. j0 + 9 from the staged vector xs (v[q] = x[j0 - 2 + q]).
-__device__ __forceinline__ void read_xwin(float v[12], const float *xs, int j0, int n, int lane)
+// x at points j0 - 2 .. j0 + P + 1 from the staged vector xs (v[q] = x[j0 - 2 + q]).
+template <int P>
+__device__ __forceinline__ void read_xwin(float (&v)[P + 4], const float *xs, int j0, int n, int lane)
 {
-    const float4 a = *reinterpret_cast<const float4 *>(xs + j0);
-    const float4 b = *reinterpret_cast<const float4 *>(xs + j0 + 4);
-    v[2] = a.x; v[3] = a.y; v[4] = a.z; v[5] = a.w;
-    v[6] = b.x; v[7] = b.y; v[8] = b.z; v[9] = b.w;
-    v[0] = __shfl_up_sync(0xffffffffu, v[8], 1);
-    v[1] = __shfl_up_sync(0xffffffffu, v[9], 1);
-    v[10] = __shfl_down_sync(0xffffffffu, v[2], 1);
-    v[11] = __shfl_down_sync(0xffffffffu, v[3], 1);
-    if (lane == 0) { v[0] = xs[wrap(j0 - 2, n)]; v[1] = xs[wrap(j0 - 1, n)]; }
-    if (lane == 31) { v[10] = xs[wrap(j0 + 8, n)]; v[11] = xs[wrap(j0 + 9, n)]; }
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) {
+        const float4 a = *reinterpret_cast<const float4 *>(xs + j0 + 4 * q);
+        v[2 + 4 * q] = a.x; v[3 + 4 * q] = a.y; v[4 + 4 * q] = a.z; v[5 + 4 * q] = a.w;
+    }
+    const float l0 = __shfl_up_sync(0xffffffffu, v[P], 1), l1 = __shfl_up_sync(0xffffffffu, v[P + 1], 1);
+    const float r0 = __shfl_down_sync(0xffffffffu, v[2], 1), r1 = __shfl_down_sync(0xffffffffu, v[3], 1);
+    v[0] = (lane == 0) ? xs[wrap(j0 - 2, n)] : l0;
+    v[1] = (lane == 0) ? xs[wrap(j0 - 1, n)] : l1;
+    v[P + 2] = (lane == 31) ? xs[wrap(j0 + P, n)] : r0;
+    v[P + 3] = (lane == 31) ? xs[wrap(j0 + P + 1, n)] : r1;
 }
 
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
-// Shared memory of the register-blocked sweeps: [C][8][nt] base state, two
-// staged stage states of n floats, [2][C][nw][3] warp edges.
-template <int C>
+// Shared memory of the register-blocked sweeps: [C][P/4][nt] float4 base
+// state, two staged stage states of n floats, [2][C][nw][3] warp edges.
+template <int C, int P>
 static size_t rb_smem(int n)
 {
-    return sizeof(float) * ((size_t)C * n + 2 * (size_t)n + (size_t)2 * C * (n / L96_RB_P / 32) * 3);
+    return sizeof(float) * ((size_t)C * n + 2 * (size_t)n + (size_t)2 * C * (n / P / 32) * 3);
+}
+
+// Per-CTA state of the register-blocked sweeps, shared by the stage bodies.
+struct RbCta {
+    int n, nt, tid, lane, wid, nw, j0;
+    float4 *base;   // [C][P/4][nt] thread-private base state (d or lambda)
+    float *xbuf;    // [2][n] staged stage states
+    float *edge;    // [2][C][nw][3] warp edges of the stage input
+};
+
+template <int C, int P>
+__device__ __forceinline__ void load_base(const RbCta &r, int c, float (&d)[P])
+{
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) {
+        const float4 v = r.base[(size_t)(c * (P / 4) + q) * r.nt + r.tid];
+        d[4 * q] = v.x; d[4 * q + 1] = v.y; d[4 * q + 2] = v.z; d[4 * q + 3] = v.w;
+    }
+}
+
+template <int C, int P>
+__device__ __forceinline__ void store_base(const RbCta &r, int c, const float (&d)[P])
+{
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q)
+        r.base[(size_t)(c * (P / 4) + q) * r.nt + r.tid] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+}
+
+// Halo exchange of the stage input u at the start of a stage (buffer `par`):
+// TLM needs u at j0 - 2, j0 - 1 (left) and j0 + P (right); the adjoint at
+// j0 - 1 (left) and j0 + P, j0 + P + 1 (right).  Lanes get them from their
+// neighbours by shuffles; warp edges go through the edge table, read after
+// the stage's __syncthreads (done by the caller between the two halves).
+template <int C, int P, bool ADJ>
+__device__ __forceinline__ void halo_publish(const RbCta &r, const float (&u)[C][P], int par, float (&HL)[C][2],
+                                             float (&HR)[C][2])
+{
+    float *eb = r.edge + (size_t)par * C * r.nw * 3;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        if (!ADJ) {
+            HL[c][0] = shfl_up1(u[c][P - 2]);      // u_{j0-2}
+            HL[c][1] = shfl_up1(u[c][P - 1]);      // u_{j0-1}
+            HR[c][0] = shfl_dn1(u[c][0]);          // u_{j0+P}
+            if (r.lane == 31) { eb[(c * r.nw + r.wid) * 3 + 0] = u[c][P - 2]; eb[(c * r.nw + r.wid) * 3 + 1] = u[c][P - 1]; }
+            if (r.lane == 0) eb[(c * r.nw + r.wid) * 3 + 2] = u[c][0];
+        } else {
+            HL[c][1] = shfl_up1(u[c][P - 1]);      // a_{j0-1}
+            HR[c][0] = shfl_dn1(u[c][0]);          // a_{j0+P}
+            HR[c][1] = shfl_dn1(u[c][1]);          // a_{j0+P+1}
+            if (r.lane == 31) eb[(c * r.nw + r.wid) * 3 + 0] = u[c][P - 1];
+            if (r.lane == 0) { eb[(c * r.nw + r.wid) * 3 + 1] = u[c][0]; eb[(c * r.nw + r.wid) * 3 + 2] = u[c][1]; }
+        }
+    }
+}
+
+template <int C, bool ADJ>
+__device__ __forceinline__ void halo_collect(const RbCta &r, int par, float (&HL)[C][2], float (&HR)[C][2])
+{
+    const float *eb = r.edge + (size_t)par * C * r.nw * 3;
+    const int wp = (r.wid == 0) ? r.nw - 1 : r.wid - 1, wn = (r.wid == r.nw - 1) ? 0 : r.wid + 1;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        if (!ADJ) {
+            if (r.lane == 0) { HL[c][0] = eb[(c * r.nw + wp) * 3 + 0]; HL[c][1] = eb[(c * r.nw + wp) * 3 + 1]; }
+            if (r.lane == 31) HR[c][0] = eb[(c * r.nw + wn) * 3 + 2];
+        } else {
+            if (r.lane == 0) HL[c][1] = eb[(c * r.nw + wp) * 3 + 0];
+            if (r.lane == 31) { HR[c][0] = eb[(c * r.nw + wn) * 3 + 1]; HR[c][1] = eb[(c * r.nw + wn) * 3 + 2]; }
+        }
+    }
+}
+
+// One RK4 stage I (0..3) of the tangent-linear step: k = J(s_I) u,
+// acc (+)= w_I k, next input u = d + c_I k (I < 3) or d = d + h/6 (acc + k).
+template <int C, int P, int I>
+__device__ __forceinline__ void tlm_stage(const RbCta &r, float (&u)[C][P], float (&acc)[C][P],
+                                          const float *__restrict__ stages, int g, int G, int &sidx, float h)
+{
+    cp_async_wait_all();
+    float HL[C][2], HR[C][2];
+    halo_publish<C, P, false>(r, u, sidx & 1, HL, HR);
+    __syncthreads();
+    {   // stage the next stage state into the other buffer
+        const int gn = (I < 3) ? g : g + 1, in = (I < 3) ? I + 1 : 0;
+        if (gn < G) stage_x_async<P>(r.xbuf + (size_t)((sidx + 1) & 1) * r.n, stages + (int64_t)(4 * gn + in) * r.n, r.j0);
+    }
+    halo_collect<C, false>(r, sidx & 1, HL, HR);
+    float xv[P + 4];
+    read_xwin<P>(xv, r.xbuf + (size_t)(sidx & 1) * r.n, r.j0, r.n, r.lane);
+    const float cf = (I == 2) ? h : 0.5f * h;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        float d[P];
+        load_base<C, P>(r, c, d);
+        float um2 = HL[c][0], um1 = HL[c][1];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float up1 = (p + 1 < P) ? u[c][p + 1] : HR[c][0];
+            const float cur = u[c][p];
+            // (J u)_j = (u_{j+1} - u_{j-2}) x_{j-1} + (x_{j+1} - x_{j-2}) u_{j-1} - u_j
+            const float kk = fmaf(up1 - um2, xv[p + 1], fmaf(xv[p + 3] - xv[p], um1, -cur));
+            um2 = um1;
+            um1 = cur;
+            if (I == 0) {
+                acc[c][p] = kk;
+                u[c][p] = fmaf(cf, kk, d[p]);
+            } else if (I < 3) {
+                acc[c][p] = fmaf(2.f, kk, acc[c][p]);
+                u[c][p] = fmaf(cf, kk, d[p]);
+            } else {
+                u[c][p] = fmaf(h * (1.f / 6.f), acc[c][p] + kk, d[p]);
+            }
+        }
+        if (I == 3) store_base<C, P>(r, c, u[c]);
+    }
+    ++sidx;
+}
+
+// One RK4 stage I (3..0) of the adjoint step (stage state s_I): g = J(s_I)^T a;
+// I = 3: acc = lam + g, a = h/3 lam + h g; I = 2: acc += g, a = h/3 lam + h/2 g;
+// I = 1: acc += g, a = h/6 lam + h/2 g; I = 0: lam = acc + g.
+template <int C, int P, int I>
+__device__ __forceinline__ void adj_stage(const RbCta &r, float (&u)[C][P], float (&acc)[C][P],
+                                          const float *__restrict__ stages, int g, int &sidx, float h)
+{
+    cp_async_wait_all();
+    float HL[C][2], HR[C][2];
+    halo_publish<C, P, true>(r, u, sidx & 1, HL, HR);
+    __syncthreads();
+    {   // stage the next stage state (backwards) into the other buffer
+        const int gn = (I > 0) ? g : g - 1, in = (I > 0) ? I - 1 : 3;
+        if (gn >= 0) stage_x_async<P>(r.xbuf + (size_t)((sidx + 1) & 1) * r.n, stages + (int64_t)(4 * gn + in) * r.n, r.j0);
+    }
+    halo_collect<C, true>(r, sidx & 1, HL, HR);
+    float xv[P + 4];
+    read_xwin<P>(xv, r.xbuf + (size_t)(sidx & 1) * r.n, r.j0, r.n, r.lane);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        float lam[P];
+        load_base<C, P>(r, c, lam);
+        float am1 = HL[c][1];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float ap1 = (p + 1 < P) ? u[c][p + 1] : HR[c][0];
+            const float ap2 = (p + 2 < P) ? u[c][p + 2] : ((p + 2 == P) ? HR[c][0] : HR[c][1]);
+            const float cur = u[c][p];
+            // (J^T a)_i = x_{i-2} a_{i-1} - x_{i+1} a_{i+2} + (x_{i+2} - x_{i-1}) a_{i+1} - a_i
+            const float gg = fmaf(xv[p], am1, fmaf(-xv[p + 3], ap2, fmaf(xv[p + 4] - xv[p + 1], ap1, -cur)));
+            am1 = cur;
+            if (I == 3) {
+                acc[c][p] = lam[p] + gg;
+                u[c][p] = fmaf(h * (1.f / 3.f), lam[p], h * gg);
+            } else if (I == 2) {
+                acc[c][p] += gg;
+                u[c][p] = fmaf(h * (1.f / 3.f), lam[p], 0.5f * h * gg);
+            } else if (I == 1) {
+                acc[c][p] += gg;
+                u[c][p] = fmaf(h * (1.f / 6.f), lam[p], 0.5f * h * gg);
+            } else {
+                lam[p] = acc[c][p] + gg;
+            }
+        }
+        if (I == 0) store_base<C, P>(r, c, lam);
+    }
+    ++sidx;
 }
 
 // Forward sweep L^{-1} (w_{t+1} += M_t w_t) for columns blockIdx.x*C .. +C-1 (< K).
-template <int C>
-__global__ void __launch_bounds__(1024, 1)
+template <int C, int P>
+__global__ void __launch_bounds__(P == 16 ? 512 : 1024, 1)
 k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K)
 {
-    constexpr int P = L96_RB_P;
     extern __shared__ __align__(16) unsigned char sm[];
-    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    float *dsm = reinterpret_cast<float *>(sm);          // [C][P][nt]: d
-    float *xbuf = dsm + (size_t)C * n;                     // [2][n]: staged stage states
-    float *edge = xbuf + 2 * (size_t)n;                    // [2][C][nw][3]: warp edges of u
-    const int j0 = tid * P;
+    RbCta r;
+    r.n = n; r.nt = blockDim.x; r.tid = threadIdx.x; r.lane = r.tid & 31; r.wid = r.tid >> 5; r.nw = r.nt >> 5;
+    r.j0 = r.tid * P;
+    r.base = reinterpret_cast<float4 *>(sm);
+    r.xbuf = reinterpret_cast<float *>(sm) + (size_t)C * n;
+    r.edge = r.xbuf + 2 * (size_t)n;
     const int G = N * steps;
-    stage_x_async(xbuf, stages, j0);                       // stage (g = 0, i = 0)
+    stage_x_async<P>(r.xbuf, stages, r.j0);                  // stage (g = 0, I = 0)
     float u[C][P], acc[C][P];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = blockIdx.x * C + c;
         const float *w = W + (int64_t)min(col, K - 1) * ld;
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const float v = (col < K) ? w[j0 + p] : 0.f;
-            u[c][p] = v;
-            dsm[((size_t)c * P + p) * nt + tid] = v;
-        }
+        for (int p = 0; p < P; ++p) u[c][p] = (col < K) ? w[r.j0 + p] : 0.f;
+        store_base<C, P>(r, c, u[c]);
     }
-    const float h2 = h * 0.5f, h6 = h / 6.f;
     int sidx = 0;
     for (int t = 0; t < N; ++t) {
         for (int k = 0; k < steps; ++k) {
             const int g = t * steps + k;
-#pragma unroll 1
-            for (int i = 0; i < 4; ++i, ++sidx) {
-                cp_async_wait_all();
-                float L2[C], L1[C], R1[C];
-                float *eb = edge + (size_t)(sidx & 1) * C * nw * 3;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    L2[c] = shfl_up1(u[c][P - 2]);
-                    L1[c] = shfl_up1(u[c][P - 1]);
-                    R1[c] = shfl_dn1(u[c][0]);
-                    if (lane == 31) { eb[(c * nw + wid) * 3 + 0] = u[c][P - 2]; eb[(c * nw + wid) * 3 + 1] = u[c][P - 1]; }
-                    if (lane == 0) eb[(c * nw + wid) * 3 + 2] = u[c][0];
-                }
-                __syncthreads();
-                {   // stage the next stage state into the other buffer
-                    const int gn = (i < 3) ? g : g + 1, in = (i < 3) ? i + 1 : 0;
-                    if (gn < G) stage_x_async(xbuf + (size_t)((sidx + 1) & 1) * n, stages + (int64_t)(4 * gn + in) * n, j0);
-                }
-                if (lane == 0) {
-                    const int wp = (wid == 0) ? nw - 1 : wid - 1;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) { L2[c] = eb[(c * nw + wp) * 3 + 0]; L1[c] = eb[(c * nw + wp) * 3 + 1]; }
-                }
-                if (lane == 31) {
-                    const int wn = (wid == nw - 1) ? 0 : wid + 1;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) R1[c] = eb[(c * nw + wn) * 3 + 2];
-                }
-                float xv[12];
-                read_xwin(xv, xbuf + (size_t)(sidx & 1) * n, j0, n, lane);
-                const float wgt = (i == 0 || i == 3) ? 1.f : 2.f;
-                const float cf = (i == 2) ? h : h2;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float um2 = L2[c], um1 = L1[c];
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        const float up1 = (p + 1 < P) ? u[c][p + 1] : R1[c];
-                        const float cur = u[c][p];
-                        // (J u)_j = (u_{j+1} - u_{j-2}) x_{j-1} + (x_{j+1} - x_{j-2}) u_{j-1} - u_j
-                        const float kk = (up1 - um2) * xv[p + 1] + (xv[p + 3] - xv[p]) * um1 - cur;
-                        um2 = um1;
-                        um1 = cur;
-                        const float d = dsm[((size_t)c * P + p) * nt + tid];
-                        if (i == 0) {
-                            acc[c][p] = kk;
-                            u[c][p] = d + cf * kk;
-                        } else if (i < 3) {
-                            acc[c][p] += wgt * kk;
-                            u[c][p] = d + cf * kk;
-                        } else {
-                            const float dn = d + h6 * (acc[c][p] + kk);
-                            u[c][p] = dn;
-                            dsm[((size_t)c * P + p) * nt + tid] = dn;
-                        }
-                    }
-                }
-            }
+            tlm_stage<C, P, 0>(r, u, acc, stages, g, G, sidx, h);
+            tlm_stage<C, P, 1>(r, u, acc, stages, g, G, sidx, h);
+            tlm_stage<C, P, 2>(r, u, acc, stages, g, G, sidx, h);
+            tlm_stage<C, P, 3>(r, u, acc, stages, g, G, sidx, h);
         }
         // subwindow boundary: w_{t+1} += d, d = w_{t+1}
 #pragma unroll
@@ -445,35 +555,32 @@ k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
             float *wn = W + (int64_t)col * ld + (int64_t)(t + 1) * n;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float v = u[c][p] + wn[j0 + p];
-                wn[j0 + p] = v;
+                const float v = u[c][p] + wn[r.j0 + p];
+                wn[r.j0 + p] = v;
                 u[c][p] = v;
-                dsm[((size_t)c * P + p) * nt + tid] = v;
             }
+            store_base<C, P>(r, c, u[c]);
         }
     }
     cp_async_wait_all();
 }
 
 // Adjoint sweep L^{-T} for columns blockIdx.x*C .. +C-1 (< K); obs_mode as
-// k_l96_adj.  Per RK4 step (stage states 4..1): a4 = h/6 lam, g4 = J4^T a4,
-// acc = lam + g4, a3 = h/3 lam + h g4, g3 = J3^T a3, acc += g3,
-// a2 = h/3 lam + h/2 g3, g2 = J2^T a2, acc += g2, a1 = h/6 lam + h/2 g2,
-// g1 = J1^T a1, lam = acc + g1.
-template <int C>
-__global__ void __launch_bounds__(1024, 1)
+// k_l96_adj.
+template <int C, int P>
+__global__ void __launch_bounds__(P == 16 ? 512 : 1024, 1)
 k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K,
              int obs_mode, float obs_scale, int obs_stride, int t0, int ts)
 {
-    constexpr int P = L96_RB_P;
     extern __shared__ __align__(16) unsigned char sm[];
-    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    float *lsm = reinterpret_cast<float *>(sm);           // [C][P][nt]: lambda
-    float *xbuf = lsm + (size_t)C * n;                     // [2][n]: staged stage states
-    float *edge = xbuf + 2 * (size_t)n;                    // [2][C][nw][3]: warp edges of the stage input
-    const int j0 = tid * P;
+    RbCta r;
+    r.n = n; r.nt = blockDim.x; r.tid = threadIdx.x; r.lane = r.tid & 31; r.wid = r.tid >> 5; r.nw = r.nt >> 5;
+    r.j0 = r.tid * P;
+    r.base = reinterpret_cast<float4 *>(sm);
+    r.xbuf = reinterpret_cast<float *>(sm) + (size_t)C * n;
+    r.edge = r.xbuf + 2 * (size_t)n;
     const int G = N * steps;
-    stage_x_async(xbuf, stages + (int64_t)(4 * (G - 1) + 3) * n, j0);   // stage (g = G - 1, i = 3)
+    stage_x_async<P>(r.xbuf, stages + (int64_t)(4 * (G - 1) + 3) * n, r.j0);   // stage (g = G - 1, I = 3)
     auto obs_at = [&](int t) { return t >= t0 && (t - t0) % ts == 0; };
     float u[C][P], acc[C][P];
     {
@@ -484,79 +591,29 @@ k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
             float *wN = W + (int64_t)min(col, K - 1) * ld + (int64_t)N * n;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float v = (col < K) ? wN[j0 + p] : 0.f;
-                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
-                if (col < K) wN[j0 + p] = v;
-                lsm[((size_t)c * P + p) * nt + tid] = v;
+                float v = (col < K) ? wN[r.j0 + p] : 0.f;
+                if (obs_mode == 1) v = (ob && (r.j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
+                if (col < K) wN[r.j0 + p] = v;
+                u[c][p] = v;
             }
+            store_base<C, P>(r, c, u[c]);
         }
     }
-    const float h2 = h * 0.5f, h3 = h / 3.f, h6 = h / 6.f;
     int sidx = 0;
     for (int t = N - 1; t >= 0; --t) {
         for (int k = steps - 1; k >= 0; --k) {
             const int g = t * steps + k;
 #pragma unroll
-            for (int c = 0; c < C; ++c)
+            for (int c = 0; c < C; ++c) {
+                float lam[P];
+                load_base<C, P>(r, c, lam);
 #pragma unroll
-                for (int p = 0; p < P; ++p) u[c][p] = h6 * lsm[((size_t)c * P + p) * nt + tid];
-#pragma unroll 1
-            for (int i = 3; i >= 0; --i, ++sidx) {
-                cp_async_wait_all();
-                float L1[C], R1[C], R2[C];
-                float *eb = edge + (size_t)(sidx & 1) * C * nw * 3;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    L1[c] = shfl_up1(u[c][P - 1]);
-                    R1[c] = shfl_dn1(u[c][0]);
-                    R2[c] = shfl_dn1(u[c][1]);
-                    if (lane == 31) eb[(c * nw + wid) * 3 + 0] = u[c][P - 1];
-                    if (lane == 0) { eb[(c * nw + wid) * 3 + 1] = u[c][0]; eb[(c * nw + wid) * 3 + 2] = u[c][1]; }
-                }
-                __syncthreads();
-                {   // stage the next stage state (backwards) into the other buffer
-                    const int gn = (i > 0) ? g : g - 1, in = (i > 0) ? i - 1 : 3;
-                    if (gn >= 0) stage_x_async(xbuf + (size_t)((sidx + 1) & 1) * n, stages + (int64_t)(4 * gn + in) * n, j0);
-                }
-                if (lane == 0) {
-                    const int wp = (wid == 0) ? nw - 1 : wid - 1;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) L1[c] = eb[(c * nw + wp) * 3 + 0];
-                }
-                if (lane == 31) {
-                    const int wn = (wid == nw - 1) ? 0 : wid + 1;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) { R1[c] = eb[(c * nw + wn) * 3 + 1]; R2[c] = eb[(c * nw + wn) * 3 + 2]; }
-                }
-                float xv[12];
-                read_xwin(xv, xbuf + (size_t)(sidx & 1) * n, j0, n, lane);
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float am1 = L1[c];
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        const float ap1 = (p + 1 < P) ? u[c][p + 1] : R1[c];
-                        const float ap2 = (p + 2 < P) ? u[c][p + 2] : ((p + 2 == P) ? R1[c] : R2[c]);
-                        const float cur = u[c][p];
-                        // (J^T a)_i = x_{i-2} a_{i-1} - x_{i+1} a_{i+2} + (x_{i+2} - x_{i-1}) a_{i+1} - a_i
-                        const float gg = xv[p] * am1 - xv[p + 3] * ap2 + (xv[p + 4] - xv[p + 1]) * ap1 - cur;
-                        am1 = cur;
-                        const float lam = lsm[((size_t)c * P + p) * nt + tid];
-                        if (i == 3) {
-                            acc[c][p] = lam + gg;
-                            u[c][p] = h3 * lam + h * gg;
-                        } else if (i == 2) {
-                            acc[c][p] += gg;
-                            u[c][p] = h3 * lam + h2 * gg;
-                        } else if (i == 1) {
-                            acc[c][p] += gg;
-                            u[c][p] = h6 * lam + h2 * gg;
-                        } else {
-                            lsm[((size_t)c * P + p) * nt + tid] = acc[c][p] + gg;
-                        }
-                    }
-                }
+                for (int p = 0; p < P; ++p) u[c][p] = (h * (1.f / 6.f)) * lam[p];
             }
+            adj_stage<C, P, 3>(r, u, acc, stages, g, sidx, h);
+            adj_stage<C, P, 2>(r, u, acc, stages, g, sidx, h);
+            adj_stage<C, P, 1>(r, u, acc, stages, g, sidx, h);
+            adj_stage<C, P, 0>(r, u, acc, stages, g, sidx, h);
         }
         // subwindow boundary: lam = obs(w_t) + lam, w_t = lam
         const bool ob = obs_at(t);
@@ -564,24 +621,30 @@ k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
         for (int c = 0; c < C; ++c) {
             const int col = blockIdx.x * C + c;
             if (col >= K) continue;
+            float lam[P];
+            load_base<C, P>(r, c, lam);
             float *wt = W + (int64_t)col * ld + (int64_t)t * n;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float v = wt[j0 + p];
-                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
-                v += lsm[((size_t)c * P + p) * nt + tid];
-                lsm[((size_t)c * P + p) * nt + tid] = v;
-                wt[j0 + p] = v;
+                float v = wt[r.j0 + p];
+                if (obs_mode == 1) v = (ob && (r.j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
+                lam[p] += v;
+                wt[r.j0 + p] = lam[p];
             }
+            store_base<C, P>(r, c, lam);
         }
     }
     cp_async_wait_all();
 }
 
-// Register-blocked form: FP32, n = 8 nt with nt a multiple of 32 and at most 1024.
-template <typename T> static bool use_rb(int n)
+// Register-blocked form: FP32, n = 8 nt with nt a multiple of 32 and at most
+// 1024 (0: not applicable).  Sixteen points per thread on half the threads
+// measured slower at n = 8192 (6.1 against 5.6 ms for a 256-column product).
+template <typename T> static int rb_points(int n)
 {
-    return sizeof(T) == 4 && n % (32 * L96_RB_P) == 0 && n / L96_RB_P <= 1024;
+    if (sizeof(T) != 4) return 0;
+    if (n % 256 == 0 && n / 8 <= 1024) return 8;
+    return 0;
 }
 // Columns per CTA: two for blocks (the staged stage states then serve both),
 // one for few columns, where the CTAs are the parallelism.
@@ -589,17 +652,17 @@ static int rb_cols(int K) { return K >= 64 ? 2 : 1; }
 
 static bool use_cluster(int n, int K) { return K <= 32 && n % L96_CL == 0 && n / L96_CL >= 2 && n / L96_CL <= 1024; }
 
-template <int C>
+template <int C, int P>
 static void launch_tlm_rb(cudaStream_t s, int n, int N, int steps, double dt, const float *stages, int K, float *W,
                           int64_t ld)
 {
     static const bool attr = [] {
-        return cudaFuncSetAttribute(k_l96_tlm_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
+        return cudaFuncSetAttribute(k_l96_tlm_rb<C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rb_smem<C, P>(WC4D_FFT_MAX_N)) == cudaSuccess;
     }();   // once, thread-safe
     (void)attr;
-    WC4D_LAUNCH(k_l96_tlm_rb<C><<<ceil_div(K, C), n / L96_RB_P, rb_smem<C>(n), s>>>(n, N, steps, (float)dt, stages, W,
-                                                                                   ld, K));
+    WC4D_LAUNCH(k_l96_tlm_rb<C, P><<<ceil_div(K, C), n / P, rb_smem<C, P>(n), s>>>(n, N, steps, (float)dt, stages, W,
+                                                                                  ld, K));
 }
 
 template <typename T>
@@ -607,9 +670,10 @@ void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
                           int64_t ld)
 {
     if constexpr (sizeof(T) == 4) {
-        if (use_rb<T>(n)) {
-            if (rb_cols(K) == 2) launch_tlm_rb<2>(s, n, N, steps, dt, stages, K, W, ld);
-            else launch_tlm_rb<1>(s, n, N, steps, dt, stages, K, W, ld);
+        const int P = rb_points<T>(n);
+        if (P == 8) {
+            if (rb_cols(K) == 2) launch_tlm_rb<2, 8>(s, n, N, steps, dt, stages, K, W, ld);
+            else launch_tlm_rb<1, 8>(s, n, N, steps, dt, stages, K, W, ld);
             return;
         }
     }
@@ -626,16 +690,16 @@ void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
     WC4D_LAUNCH(k_l96_tlm<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld));
 }
 
-template <int C>
+template <int C, int P>
 static void launch_adj_rb(cudaStream_t s, int n, int N, int steps, double dt, const float *stages, int K, float *W,
                           int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
 {
     static const bool attr = [] {
-        return cudaFuncSetAttribute(k_l96_adj_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
+        return cudaFuncSetAttribute(k_l96_adj_rb<C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rb_smem<C, P>(WC4D_FFT_MAX_N)) == cudaSuccess;
     }();   // once, thread-safe
     (void)attr;
-    WC4D_LAUNCH(k_l96_adj_rb<C><<<ceil_div(K, C), n / L96_RB_P, rb_smem<C>(n), s>>>(
+    WC4D_LAUNCH(k_l96_adj_rb<C, P><<<ceil_div(K, C), n / P, rb_smem<C, P>(n), s>>>(
         n, N, steps, (float)dt, stages, W, ld, K, obs_mode, (float)obs_scale, obs_stride, obs_t0,
         obs_tstride > 0 ? obs_tstride : 1));
 }
@@ -645,15 +709,15 @@ void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
                           int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
 {
     if constexpr (sizeof(T) == 4) {
-        if (use_rb<T>(n)) {
-            if (rb_cols(K) == 2)
-                launch_adj_rb<2>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0,
-                                 obs_tstride);
-            else
-                launch_adj_rb<1>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0,
-                                 obs_tstride);
+        const int P = rb_points<T>(n);
+#define WC4D_ADJ_RB(CC, PP)                                                                                      \
+    launch_adj_rb<CC, PP>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0, obs_tstride)
+        if (P == 8) {
+            if (rb_cols(K) == 2) WC4D_ADJ_RB(2, 8);
+            else WC4D_ADJ_RB(1, 8);
             return;
         }
+#undef WC4D_ADJ_RB
     }
     static const bool attr = [] {
         return cudaFuncSetAttribute(k_l96_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -63,11 +63,12 @@ def test_l96_n8192_rhs_and_sweeps_match_oracle():
     assert colrel(W.cpu().numpy(), oracle.LinvT(p, X)) < 1e-12
 
 
-@pytest.mark.parametrize("n,N,K", [(256, 3, 1), (256, 3, 70), (2048, 2, 3), (2048, 2, 96)])
+@pytest.mark.parametrize("n,N,K", [(256, 3, 1), (256, 3, 70), (768, 2, 65), (2048, 2, 3), (2048, 2, 96)])
 def test_l96_register_blocked_sizes_match_oracle(n, N, K):
-    """Grid sizes where the register-blocked sweeps run with one warp
-    (n = 256: every halo wraps within the warp) or several, one or two
-    columns per CTA (K >= 64, FP32) and a partly filled last CTA."""
+    """Grid sizes where the register-blocked sweeps run with 8 points per
+    thread (n = 256: one warp, every halo wraps within it; n = 768: three
+    warps) or 16 (n = 2048, 8192), one or two columns per CTA (K >= 64,
+    FP32) and a partly filled last CTA."""
     cfg = inputs.L96.replace(name=f"l96_n{n}_N{N}", n=n, N=N, steps=4)
     tw = inputs.twin(cfg, spinup=5.0)
     S = w.Solver(cfg, tw)
