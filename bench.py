@@ -390,8 +390,10 @@ def batched_windows(w, inputs, count, workers=16):
     """Uneven advection-diffusion windows (n in {256..4096}, N in [10, 80],
     K in [32, 256], one propagator per window): all inner loops of the batch
     (mixed path, REVD q = 1, tol 1e-6) driven concurrently, each window on
-    its own stream, against looping the plain FP64 single-window solver over
-    the same windows.  Wall-clock times around the host calls."""
+    its own stream, against the same mixed inner loops run one window after
+    another (the gain of batching alone) and against looping the plain FP64
+    single-window solver over the same windows.  Wall-clock times around the
+    host calls."""
     import torch
     cfgs = inputs.batch_configs(seed=0, count=count)
     streams = [w.wc4d_stream_create() for _ in cfgs]   # torch's pool repeats streams past 32
@@ -407,20 +409,27 @@ def batched_windows(w, inputs, count, workers=16):
                                                 workers)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    it_f = []
-    for S, c, x in zip(solvers, cfgs, xs):
-        it, _ = w.wc4d_inner_loop(S.ctx, w.REVD, c.k, c.l, 1, 0, 1e-6, 5000, w.FP64, x)
-        it_f.append(it)
-    torch.cuda.synchronize()
-    t_fp64 = time.perf_counter() - t0
+    def looped(precision):
+        its = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, (S, c, x) in enumerate(zip(solvers, cfgs, xs)):
+            it, _ = w.wc4d_inner_loop(S.ctx, w.REVD, c.k, c.l, 1, i, 1e-6, 5000, precision, x)
+            its.append(it)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, its
+
+    t_mixed, it_m = looped(w.MIXED)      # the same mixed inner loops one window after another
+    t_fp64, it_f = looped(w.FP64)
     for S in solvers:
         S.close()
     for st in streams:
         w.wc4d_stream_destroy(st)
     return {"windows": count, "workers": workers, "total_nA": int(sum(c.nA for c in cfgs)),
-            "batched_mixed_s": t_batch, "looped_fp64_s": t_fp64, "speedup": t_fp64 / t_batch,
-            "max_relres": max(rr_b), "pcg_iters_batched": it_b, "pcg_iters_fp64": it_f}
+            "batched_mixed_s": t_batch, "looped_mixed_s": t_mixed, "looped_fp64_s": t_fp64,
+            "speedup_batching": t_mixed / t_batch, "speedup_vs_looped_fp64": t_fp64 / t_batch,
+            "max_relres": max(rr_b), "pcg_iters_batched": it_b, "pcg_iters_looped_mixed": it_m,
+            "pcg_iters_fp64": it_f}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -622,7 +631,8 @@ def main():
         batched = batched_windows(w, inputs, args.batch_count) if args.batch_count > 0 else None
         learned = learned_windows(w, inputs, stream)
         from paper_2101_07249_gb300 import paper_setups
-        paper_adv = {"advection": paper_setups.spectral_study(), "lorenz96": paper_setups.lorenz96_study()}
+        paper_adv = {"advection": paper_setups.spectral_study(), "lorenz96": paper_setups.lorenz96_study(),
+                     "lorenz96_networks": paper_setups.lorenz96_networks()}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None

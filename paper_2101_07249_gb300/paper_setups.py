@@ -169,9 +169,10 @@ def _l96_rk4(x, dt=L96_DT):
     return x + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
 
 
-def lorenz96_twin(seed: int = 0, spinup_steps: int = 2000):
+def lorenz96_twin(seed: int = 0, spinup_steps: int = 2000, obs: int = L96_OBS):
     """Truth (N + 1, n) after an RK4 spin-up from x = F (+ 0.01 noise),
-    background truth + B^{1/2} noise, observations (120,)."""
+    background truth + B^{1/2} noise, observations of every `obs`-th
+    variable at every `obs`-th step (obs = 10: 120, 5: 480, 2: 3000)."""
     g = np.random.default_rng([int(seed), 52])
     x = L96_F + 0.01 * g.standard_normal(L96_n)
     for _ in range(spinup_steps):
@@ -186,23 +187,23 @@ def lorenz96_twin(seed: int = 0, spinup_steps: int = 2000):
     Bh = (V * np.sqrt(np.maximum(lam, 0.0))) @ V.T
     xb = truth[0] + Bh @ g.standard_normal(L96_n)
     ys = []
-    for t in range(L96_OBS, L96_N + 1, L96_OBS):
-        pts = truth[t, ::L96_OBS]
+    for t in range(obs, L96_N + 1, obs):
+        pts = truth[t, ::obs]
         ys.append(pts + L96_SIG_O * g.standard_normal(pts.size))
     return truth, xb, np.concatenate(ys)
 
 
-def lorenz96_window(seed: int = 0, stream=None):
+def lorenz96_window(seed: int = 0, stream=None, obs: int = L96_OBS):
     from . import (CORR_SOAR, MODEL_L96, Problem, wc4d_create, wc4d_set_background_obs, wc4d_set_covariance)
     prob = Problem()
     prob.n, prob.N, prob.model, prob.steps = L96_n, L96_N, MODEL_L96, 1
     prob.dt, prob.F, prob.sigma_o2 = L96_DT, L96_F, L96_SIG_O ** 2
-    prob.obs_stride, prob.obs_t0, prob.obs_tstride = L96_OBS, L96_OBS, L96_OBS
+    prob.obs_stride, prob.obs_t0, prob.obs_tstride = obs, obs, obs
     prob.M_shared = 0
     ctx = wc4d_create(prob, stream)
     wc4d_set_covariance(ctx, 0, CORR_SOAR, L96_SIG_B ** 2, L96_LEN)
     wc4d_set_covariance(ctx, 1, CORR_SOAR, L96_SIG_Q ** 2, L96_LEN)
-    _, xb, y = lorenz96_twin(seed)
+    _, xb, y = lorenz96_twin(seed, obs=obs)
     wc4d_set_background_obs(ctx, xb, y)
     return ctx
 
@@ -239,25 +240,30 @@ def _lambda_min_CAC(ctx, nA, nobs, U, theta, seed=0):
     return float(min(ev.min(), 1.0)) if Q.shape[1] < nA else float(ev.min())
 
 
-def lorenz96_study(k: int = 5, l: int = 5, iters: int = 10, seeds=(0, 1, 2), window_seed: int = 0):
+def lorenz96_study(k: int = 5, l: int = 5, iters: int = 10, seeds=(0, 1, 2), window_seed: int = 0,
+                   obs: int = L96_OBS, k_det=None, lmin: bool = True):
     """Section 5.2's comparison in the second inner loop: the quadratic-cost
     decrease after each of `iters` PCG iterations (FP64) with no LMP, the
-    deterministic LMP and the three randomised LMPs (averaged over probe
-    seeds), and the smallest eigenvalue of C^T A C for each LMP."""
+    deterministic LMP (k_det Ritz pairs of inner loop 1, default k) and the
+    three randomised LMPs (k pairs, l oversampling; averaged over probe
+    seeds), and (lmin) the smallest eigenvalue of C^T A C for each LMP.  obs:
+    the observation network (every obs-th variable at every obs-th step)."""
     import torch
 
-    from . import (FP64, METHODS, wc4d_destroy, wc4d_get_ritz, wc4d_lanczos_cg, wc4d_lanczos_ritz,
+    from . import (FP64, METHODS, wc4d_destroy, wc4d_get_ritz, wc4d_lanczos_cg, wc4d_lanczos_ritz, wc4d_nobs,
                    wc4d_outer_update, wc4d_pcg, wc4d_set_ritz, wc4d_sketch)
-    ctx = lorenz96_window(window_seed)
+    k_det = k if k_det is None else k_det
+    ctx = lorenz96_window(window_seed, obs=obs)
     nA = L96_n * (L96_N + 1)
+    nobs = int(wc4d_nobs(ctx))
     x = torch.zeros(nA, dtype=torch.float64, device="cuda")
     J, rr1 = wc4d_lanczos_cg(ctx, x, 1e-6, 100, reorth=True)          # inner loop 1, no LMP
-    wc4d_lanczos_ritz(ctx, k)
-    Ud = torch.zeros(k, nA, dtype=torch.float64, device="cuda")
-    thd = wc4d_get_ritz(ctx, Ud, k)
+    wc4d_lanczos_ritz(ctx, k_det)
+    Ud = torch.zeros(k_det, nA, dtype=torch.float64, device="cuda")
+    thd = wc4d_get_ritz(ctx, Ud, k_det)
     wc4d_outer_update(ctx, x)                                          # second linearisation
-    out = {"nA": nA, "nobs": 120, "inner_loop_1": {"cg_iters": J, "relres": rr1}, "k": k, "l": l,
-           "qcf_decrease": {}, "lambda_min_CAC": {}}
+    out = {"nA": nA, "nobs": nobs, "inner_loop_1": {"cg_iters": J, "relres": rr1}, "k": k, "l": l,
+           "k_deterministic": k_det, "qcf_decrease": {}, "lambda_min_CAC": {}}
     y = torch.zeros(nA, dtype=torch.float64, device="cuda")
 
     def qcf_curve(use):
@@ -266,25 +272,56 @@ def lorenz96_study(k: int = 5, l: int = 5, iters: int = 10, seeds=(0, 1, 2), win
 
     wc4d_set_ritz(ctx, 0, None, np.zeros(0))
     out["qcf_decrease"]["none"] = qcf_curve(0).tolist()
-    wc4d_set_ritz(ctx, k, Ud, thd)
+    wc4d_set_ritz(ctx, k_det, Ud, thd)
     out["qcf_decrease"]["deterministic"] = qcf_curve(1).tolist()
-    out["lambda_min_CAC"]["deterministic"] = _lambda_min_CAC(ctx, nA, 120, Ud.cpu().numpy(), thd)
+    if lmin:
+        out["lambda_min_CAC"]["deterministic"] = _lambda_min_CAC(ctx, nA, nobs, Ud.cpu().numpy(), thd)
     for name in ("revd", "nystrom", "ritzit"):
         curves, lmins = [], []
         for s in seeds:
             th = wc4d_sketch(ctx, METHODS[name], k, l, 0, 200 + s, None, FP64)
             curves.append(qcf_curve(1))
-            U = torch.zeros(k, nA, dtype=torch.float64, device="cuda")
-            th = wc4d_get_ritz(ctx, U, k)
-            lmins.append(_lambda_min_CAC(ctx, nA, 120, U.cpu().numpy(), th))
+            if lmin:
+                U = torch.zeros(k, nA, dtype=torch.float64, device="cuda")
+                th = wc4d_get_ritz(ctx, U, k)
+                lmins.append(_lambda_min_CAC(ctx, nA, nobs, U.cpu().numpy(), th))
         out["qcf_decrease"][name] = np.mean(curves, axis=0).tolist()
-        out["lambda_min_CAC"][name] = float(np.mean(lmins))
+        if lmin:
+            out["lambda_min_CAC"][name] = float(np.mean(lmins))
     q = {m: v[-1] for m, v in out["qcf_decrease"].items()}
     out["paper_claims"] = {
         "randomised_beat_deterministic": all(q[m] > q["deterministic"] for m in ("revd", "nystrom", "ritzit")),
         "ritzit_best": q["ritzit"] >= max(q["revd"], q["nystrom"]),
-        "revd_lambda_min_below_nystrom_ritzit": out["lambda_min_CAC"]["revd"] < min(
-            out["lambda_min_CAC"]["nystrom"], out["lambda_min_CAC"]["ritzit"]),
     }
+    if lmin:
+        out["paper_claims"]["revd_lambda_min_below_nystrom_ritzit"] = out["lambda_min_CAC"]["revd"] < min(
+            out["lambda_min_CAC"]["nystrom"], out["lambda_min_CAC"]["ritzit"])
     wc4d_destroy(ctx)
+    return out
+
+
+def lorenz96_networks(networks=(5, 2), ks=(5, 15), l: int = 5, iters: int = 10, seeds=(0, 1, 2)):
+    """Section 5.2's denser observation networks: every 5th variable at every
+    5th step (480 observations) and every 2nd at every 2nd step (3000), each
+    with k = 5 and k = 15 (l = 5), plus the randomised LMPs with k = 5 against
+    the deterministic LMP with k = 15.  Reported per network and k: the
+    quadratic-cost decrease after `iters` PCG iterations of each LMP, and the
+    spread of the three randomised LMPs relative to their mean (the paper:
+    little difference between them when k is small relative to q)."""
+    out = {}
+    for obs in networks:
+        rows = {}
+        for k in ks:
+            r = lorenz96_study(k=k, l=l, iters=iters, seeds=seeds, obs=obs, lmin=False)
+            q = {m: v[-1] for m, v in r["qcf_decrease"].items()}
+            rnd = [q["revd"], q["nystrom"], q["ritzit"]]
+            rows[f"k{k}"] = {"nobs": r["nobs"], "qcf_final": q,
+                             "randomised_spread": (max(rnd) - min(rnd)) / float(np.mean(rnd)),
+                             "randomised_beat_deterministic": r["paper_claims"]["randomised_beat_deterministic"]}
+        # randomised LMPs with k = 5 against the deterministic LMP with k = 15
+        r = lorenz96_study(k=min(ks), l=l, iters=iters, seeds=seeds, obs=obs, k_det=max(ks), lmin=False)
+        q = {m: v[-1] for m, v in r["qcf_decrease"].items()}
+        rows[f"randomised_k{min(ks)}_vs_deterministic_k{max(ks)}"] = {
+            "qcf_final": q, "randomised_beat_deterministic": r["paper_claims"]["randomised_beat_deterministic"]}
+        out[f"q{rows[f'k{min(ks)}']['nobs']}"] = rows
     return out

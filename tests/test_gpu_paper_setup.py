@@ -103,3 +103,18 @@ def test_lorenz96_paper_window_study_runs():
         assert np.all(np.diff(r["qcf_decrease"][m]) > 0)     # CG decreases the quadratic cost
     for m, v in r["lambda_min_CAC"].items():
         assert v <= 1.0 + 1e-9
+
+
+@pytest.mark.parametrize("obs,q", [(5, 480), (2, 3000)])
+def test_lorenz96_denser_networks(obs, q):
+    """Section 5.2's denser networks (every 5th variable at every 5th step:
+    480 observations; every 2nd at every 2nd: 3000), k = 5 with the
+    deterministic LMP of k = 15 pairs: observation counts, monotone
+    quadratic-cost decrease, and (480 observations) lambda_min(C^T A C) <= 1
+    for every LMP."""
+    r = ps.lorenz96_study(k=5, l=5, iters=3, seeds=(0,), obs=obs, k_det=15, lmin=(q == 480))
+    assert r["nobs"] == q and r["k_deterministic"] == 15
+    for m in ("none", "deterministic", "revd", "nystrom", "ritzit"):
+        assert np.all(np.diff(r["qcf_decrease"][m]) > 0)
+    for m, v in r["lambda_min_CAC"].items():
+        assert v <= 1.0 + 1e-9
