@@ -124,6 +124,18 @@ wc4d_status wc4d_set_covariance(wc4d_ctx *ctx, int32_t block, int32_t corr, doub
  * clamped to zero. */
 wc4d_status wc4d_set_covariance_row(wc4d_ctx *ctx, int32_t block, const double *row_host);
 
+/* A covariance block of D given by its square root (Section 2.2, eq. 10
+ * needs only D^{1/2}): block 0 = B, 1 = Q_t (all subwindows).
+ *   kind 0: circulant, data = first row of the symmetric square root (host,
+ *           n values; applied by FFT for power-of-two n, directly otherwise);
+ *   kind 1: dense, data = the n x n square root (device, row-major; applied
+ *           by one n x n by n x K product per time block; FP32 copy for the
+ *           mixed path);
+ *   kind 2: scalar, data = sigma (host, one value >= 0): the block is
+ *           sigma^2 I, applied by scaling.
+ * EINVAL for an unknown kind, a negative or non-finite sigma. */
+wc4d_status wc4d_set_cov_sqrt(wc4d_ctx *ctx, int32_t block, int32_t kind, const double *data);
+
 /* Outer-loop quantities (Section 2.1): run the model from the background
  * xb (host, n values) over the window (the nonlinear RK4 model for
  * Lorenz-96, which also stores the linearisation trajectory in FP64 and
@@ -142,12 +154,25 @@ wc4d_status wc4d_set_background_obs(wc4d_ctx *ctx, const double *xb_host, const 
  * observations given to wc4d_set_background_obs.  WC4D_ESTATE before
  * wc4d_set_background_obs. */
 wc4d_status wc4d_outer_update(wc4d_ctx *ctx, const double *x_device);
+/* The linearisation trajectory of a Lorenz-96 context given by the caller
+ * (its own nonlinear run, eq. 1), in place of the library's run from the
+ * background: X (device) holds the N steps + 1 states x_0 .. x_{N steps},
+ * n values each; the RK4 stage states of every step are recomputed from
+ * them for the tangent-linear and adjoint sweeps.  EINVAL for a dense model.
+ * wc4d_set_innovation then supplies the innovations d (device, nobs values,
+ * time-major over the observed times) and optionally D^{-1/2} b (device,
+ * nA values, or NULL), and forms the right-hand side of eq. 10,
+ * D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b), with the current operator. */
+wc4d_status wc4d_set_trajectory(wc4d_ctx *ctx, const double *X_device);
+wc4d_status wc4d_set_innovation(wc4d_ctx *ctx, const double *d_device, const double *Dm12b_device);
 /* Number of observations q of the problem. */
 int64_t     wc4d_nobs(const wc4d_ctx *ctx);
 /* Dimension n_A = n (N + 1) of the control vector (eq. 10's A is n_A x n_A):
    the length of every control-space vector and the least leading dimension
    of every block passed to the library; -1 for a null context. */
 int64_t     wc4d_control_dim(const wc4d_ctx *ctx);
+/* The problem statement the context was created with (host copy). */
+wc4d_status wc4d_get_problem(const wc4d_ctx *ctx, wc4d_problem *out);
 /* Number of Ritz pairs currently installed (what wc4d_get_ritz copies:
    n_A x count values and count Ritz values); -1 for a null context. */
 int32_t     wc4d_ritz_count(const wc4d_ctx *ctx);

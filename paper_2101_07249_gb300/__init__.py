@@ -59,6 +59,10 @@ _SIGS = {
     "wc4d_build_advdiff_propagator": (C.c_int, [_V, C.c_double, C.c_double, C.c_double, C.c_int32]),
     "wc4d_set_covariance": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_double, C.c_double]),
     "wc4d_set_covariance_row": (C.c_int, [_V, C.c_int32, _D]),
+    "wc4d_set_cov_sqrt": (C.c_int, [_V, C.c_int32, C.c_int32, _V]),
+    "wc4d_get_problem": (C.c_int, [_V, C.c_void_p]),
+    "wc4d_set_trajectory": (C.c_int, [_V, _V]),
+    "wc4d_set_innovation": (C.c_int, [_V, _V, _V]),
     "wc4d_set_background_obs": (C.c_int, [_V, _D, _D, _D]),
     "wc4d_outer_update": (C.c_int, [_V, _V]),
     "wc4d_learned_probes": (C.c_int, [_V, _V, _V, C.c_int32, _V, C.c_int64]),
@@ -248,6 +252,50 @@ def wc4d_build_advdiff_propagator(ctx, kappa, c, dt, steps):
 
 def wc4d_set_covariance(ctx, block, corr, variance, length):
     _check(ctx, load().wc4d_set_covariance(ctx, int(block), int(corr), float(variance), float(length)))
+
+
+COV_SQRT_CIRCULANT, COV_SQRT_DENSE, COV_SQRT_SCALAR = 0, 1, 2
+
+
+def wc4d_set_cov_sqrt(ctx, block, kind, data):
+    """Covariance block given by its square root: kind 0 circulant first row
+    (host, n values), 1 dense n x n row-major (device FP64 tensor), 2 scalar
+    sigma (host)."""
+    import torch
+    kind = int(kind)
+    n = wc4d_get_problem(ctx).n
+    if kind == COV_SQRT_DENSE:
+        ptr = _dev(data, torch.float64, n * n, "data")
+    elif kind == COV_SQRT_SCALAR:
+        buf = np.array([float(data)], dtype=np.float64)
+        ptr = buf.ctypes.data_as(_D)
+    else:
+        buf = np.ascontiguousarray(data, dtype=np.float64)
+        if buf.size < n:
+            raise ValueError(f"data: needs at least {n} values, has {buf.size}")
+        ptr = buf.ctypes.data_as(_D)
+    _check(ctx, load().wc4d_set_cov_sqrt(ctx, int(block), kind, ptr))
+
+
+def wc4d_get_problem(ctx):
+    """The context's problem statement (a Problem structure)."""
+    pr = Problem()
+    _check(ctx, load().wc4d_get_problem(ctx, C.byref(pr)))
+    return pr
+
+
+def wc4d_set_trajectory(ctx, X):
+    """External Lorenz-96 linearisation trajectory (device FP64, (N steps + 1) x n)."""
+    import torch
+    pr = wc4d_get_problem(ctx)
+    _check(ctx, load().wc4d_set_trajectory(ctx, _dev(X, torch.float64, (pr.N * pr.steps + 1) * pr.n, "X")))
+
+
+def wc4d_set_innovation(ctx, d, Dm12b=None):
+    """Innovations d (device FP64, nobs) and optional D^{-1/2} b (device FP64, nA); forms the rhs."""
+    import torch
+    _check(ctx, load().wc4d_set_innovation(ctx, _dev(d, torch.float64, int(load().wc4d_nobs(ctx)), "d"),
+                                           _dev(Dm12b, torch.float64, int(load().wc4d_control_dim(ctx)), "Dm12b")))
 
 
 def wc4d_set_covariance_row(ctx, block, row):

@@ -318,6 +318,12 @@ extern "C" wc4d_status wc4d_set_stream(wc4d_ctx *c, void *stream)
 
 extern "C" int64_t wc4d_nobs(const wc4d_ctx *c) { return c ? c->nobs : -1; }
 extern "C" int64_t wc4d_control_dim(const wc4d_ctx *c) { return c ? c->nA : -1; }
+extern "C" wc4d_status wc4d_get_problem(const wc4d_ctx *c, wc4d_problem *out)
+{
+    if (!c || !out) return WC4D_EINVAL;
+    *out = c->prob;
+    return WC4D_OK;
+}
 extern "C" int32_t wc4d_ritz_count(const wc4d_ctx *c) { return c ? c->kU : -1; }
 
 extern "C" int64_t wc4d_launch_count(int32_t reset)
@@ -464,7 +470,8 @@ static wc4d_status ensure_M32(wc4d_ctx *c)
 
 // kind >= 0: eigenvalues of variance * C(kind, L) in closed form; kind < 0:
 // from the explicit first row row_dev.
-static wc4d_status cov_sqrt_setup(wc4d_ctx *c, int block, int kind, double L, double variance, const double *row_dev)
+static wc4d_status cov_sqrt_setup(wc4d_ctx *c, int block, int kind, double L, double variance, const double *row_dev,
+                                  bool root_given = false)
 {
     const int n = c->prob.n;
     WC4D_TRY(ensure(c, c->small2, sizeof(double) * (n + 1)));
@@ -477,7 +484,7 @@ static wc4d_status cov_sqrt_setup(wc4d_ctx *c, int block, int kind, double L, do
     }
     launch_cov_sqrt(c->stream, n, c->logn, c->fft, kind, L, variance, row_dev, P<double2>(c->cosn),
                     P<double>(c->small2), P<double>(c->spec64[block]), P<float>(c->spec32[block]),
-                    P<double>(c->row64[block]), P<float>(c->row32[block]));
+                    P<double>(c->row64[block]), P<float>(c->row32[block]), root_given);
     WC4D_TRY(check_launch(c, "cov_sqrt"));
     c->have_cov[block] = true;
     return sync(c, "cov_sqrt");
@@ -488,6 +495,7 @@ extern "C" wc4d_status wc4d_set_covariance(wc4d_ctx *c, int32_t block, int32_t c
     if (!c || block < 0 || block > 1 || corr < 0 || corr > 2 || !(variance >= 0.0)) return WC4D_EINVAL;
     if (corr != WC4D_CORR_DIAG && !(L > 0.0 && L < 1e300)) return WC4D_EINVAL;
     c->cov_sd[block] = (corr == WC4D_CORR_DIAG) ? std::sqrt(variance) : -1.0;
+    c->cov_dense[block] = false;
     return cov_sqrt_setup(c, block, corr, L, variance, nullptr);
 }
 
@@ -495,10 +503,45 @@ extern "C" wc4d_status wc4d_set_covariance_row(wc4d_ctx *c, int32_t block, const
 {
     if (!c || block < 0 || block > 1 || !row_host) return WC4D_EINVAL;
     c->cov_sd[block] = -1.0;
+    c->cov_dense[block] = false;
     WC4D_TRY(ensure(c, c->small3, sizeof(double) * c->prob.n));
     WC4D_CUDA(c, cudaMemcpyAsync(c->small3.p, row_host, sizeof(double) * c->prob.n, cudaMemcpyHostToDevice,
                                  c->stream));
     return cov_sqrt_setup(c, block, -1, 0.0, 1.0, P<double>(c->small3));
+}
+
+extern "C" wc4d_status wc4d_set_cov_sqrt(wc4d_ctx *c, int32_t block, int32_t kind, const double *data)
+{
+    if (!c || block < 0 || block > 1 || !data) return WC4D_EINVAL;
+    const int n = c->prob.n;
+    if (kind == 0) {                                   // first row of the circulant square root (host)
+        c->cov_sd[block] = -1.0;
+        c->cov_dense[block] = false;
+        WC4D_TRY(ensure(c, c->small3, sizeof(double) * n));
+        WC4D_CUDA(c, cudaMemcpyAsync(c->small3.p, data, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        return cov_sqrt_setup(c, block, -1, 0.0, 1.0, P<double>(c->small3), true);
+    }
+    if (kind == 1) {                                   // dense n x n square root (device, row-major)
+        const size_t nn = (size_t)n * n;
+        WC4D_TRY(ensure(c, c->dense64[block], sizeof(double) * nn));
+        WC4D_TRY(ensure(c, c->dense32[block], sizeof(float) * nn));
+        WC4D_CUDA(c, cudaMemcpyAsync(c->dense64[block].p, data, sizeof(double) * nn, cudaMemcpyDeviceToDevice,
+                                     c->stream));
+        launch_convert_f64_f32(c->stream, (int64_t)nn, P<double>(c->dense64[block]), P<float>(c->dense32[block]));
+        WC4D_TRY(check_launch(c, "dense square root"));
+        c->cov_sd[block] = -1.0;
+        c->cov_dense[block] = true;
+        c->have_cov[block] = true;
+        return sync(c, "dense square root");
+    }
+    if (kind == 2) {                                   // scalar: the block is sigma^2 I (host, one value sigma)
+        const double sd = data[0];
+        if (!(sd >= 0.0) || !std::isfinite(sd)) return WC4D_EINVAL;
+        WC4D_TRY(wc4d_set_covariance(c, block, WC4D_CORR_DIAG, sd * sd, 1.0));
+        c->cov_sd[block] = sd;
+        return WC4D_OK;
+    }
+    return WC4D_EINVAL;
 }
 
 static wc4d_status require_operator(wc4d_ctx *c)
@@ -540,13 +583,35 @@ int tc_read_error(wc4d_ctx *c);
 bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld);
 bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld);
 
+template <typename T> static const T *dense_sqrt(wc4d_ctx *c, int b);
+template <> const double *dense_sqrt<double>(wc4d_ctx *c, int b) { return P<double>(c->dense64[b]); }
+template <> const float *dense_sqrt<float>(wc4d_ctx *c, int b) { return P<float>(c->dense32[b]); }
+
+// Y = D^{1/2} X (+ addX): circulant blocks by FFT or direct products,
+// diagonal blocks by scaling, dense square roots (wc4d_set_cov_sqrt kind 1)
+// by one n x n by n x K product per time block.
 template <typename T>
 static wc4d_status apply_circ(wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy, const T *addX,
                               int64_t ld_add)
 {
     ProfScope ps(c, PROF_CIRC);
-    launch_circulant<T>(c->stream, c, K, X, ldx, Y, ldy, addX, ld_add, c->fft, Ops<T>::spec(c, 0),
-                        Ops<T>::spec(c, 1), Ops<T>::row(c, 0), Ops<T>::row(c, 1), Ops<T>::tw(c));
+    const int skip = (c->cov_dense[0] ? 1 : 0) | (c->cov_dense[1] ? 2 : 0);
+    if (skip != 3)
+        launch_circulant<T>(c->stream, c, K, X, ldx, Y, ldy, addX, ld_add, c->fft, Ops<T>::spec(c, 0),
+                            Ops<T>::spec(c, 1), Ops<T>::row(c, 0), Ops<T>::row(c, 1), Ops<T>::tw(c), skip);
+    if (skip) {
+        const int n = c->prob.n;
+        for (int t = 0; t <= c->prob.N; ++t) {
+            const int b = (t == 0) ? 0 : 1;
+            if (!c->cov_dense[b]) continue;
+            T *y = Y + (int64_t)t * n;
+            if (addX)
+                WC4D_CUDA(c, cudaMemcpy2DAsync(y, sizeof(T) * ldy, addX + (int64_t)t * n, sizeof(T) * ld_add,
+                                               sizeof(T) * n, K, cudaMemcpyDeviceToDevice, c->stream));
+            Epi e{0, 1.0, addX ? 1.0 : 0.0, 0.0, 1};
+            launch_gemm<T>(c->stream, n, K, n, dense_sqrt<T>(c, b), n, 1, X + (int64_t)t * n, ldx, y, ldy, e);
+        }
+    }
     return check_launch(c, "circulant");
 }
 
@@ -740,6 +805,27 @@ extern "C" wc4d_status wc4d_get_propagator(wc4d_ctx *c, int32_t t, double *M)
 // ============================================================================
 // Model run from the stored linearisation point p = (x_0, eta), innovations
 // d_t = y_t - H_t x_t and rhs = D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b).
+// rhs = D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b) from the innovations in c->d.
+static wc4d_status compute_rhs(wc4d_ctx *c)
+{
+    const int n = c->prob.n;
+    const int64_t nA = c->nA;
+    WC4D_TRY(ensure(c, c->blkB, sizeof(double) * nA));
+    WC4D_TRY(ensure(c, c->rhs, sizeof(double) * nA));
+    double *v = P<double>(c->blkB);
+    WC4D_CUDA(c, cudaMemsetAsync(v, 0, sizeof(double) * nA, c->stream));
+    if (c->nobs > 0)
+        WC4D_LAUNCH(k_scatter_obs<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
+                                                                      c->prob.obs_tstride, c->prob.obs_stride, n,
+                                                                      P<double>(c->d), 1.0 / c->prob.sigma_o2, v));
+    WC4D_TRY(check_launch(c, "innovation"));
+    WC4D_TRY(plain_adjoint_sweep<double>(c, 1, v, nA));    // S = L^{-T} H^T R^{-1} d
+    WC4D_TRY(apply_circ<double>(c, 1, v, nA, P<double>(c->rhs), nA, c->have_Dm12b ? P<double>(c->Dm12b) : nullptr,
+                                nA));
+    c->have_rhs = true;
+    return sync(c, "rhs");
+}
+
 static wc4d_status relinearise(wc4d_ctx *c)
 {
     const int n = c->prob.n, N = c->prob.N;
@@ -775,19 +861,7 @@ static wc4d_status relinearise(wc4d_ctx *c)
         WC4D_LAUNCH(k_innovation<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
                                                                      c->prob.obs_tstride, c->prob.obs_stride, n,
                                                                      P<double>(c->ydev), xs, P<double>(c->d)));
-    // rhs = D^{1/2} L^{-T} H^T R^{-1} d (+ D^{-1/2} b)
-    double *v = P<double>(c->blkB);
-    WC4D_CUDA(c, cudaMemsetAsync(v, 0, sizeof(double) * nA, c->stream));
-    if (c->nobs > 0)
-        WC4D_LAUNCH(k_scatter_obs<<<ceil_div(c->nobs, 256), 256, 0, c->stream>>>(c->nobs, c->obs_per_time, c->prob.obs_t0,
-                                                                      c->prob.obs_tstride, c->prob.obs_stride, n,
-                                                                      P<double>(c->d), 1.0 / c->prob.sigma_o2, v));
-    WC4D_TRY(check_launch(c, "innovation"));
-    WC4D_TRY(plain_adjoint_sweep<double>(c, 1, v, nA));    // S = L^{-T} H^T R^{-1} d
-    WC4D_TRY(apply_circ<double>(c, 1, v, nA, P<double>(c->rhs), nA, c->have_Dm12b ? P<double>(c->Dm12b) : nullptr,
-                                nA));
-    c->have_rhs = true;
-    return sync(c, "relinearise");
+    return compute_rhs(c);
 }
 
 extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, const double *y, const double *Dm12b)
@@ -809,6 +883,40 @@ extern "C" wc4d_status wc4d_set_background_obs(wc4d_ctx *c, const double *xb, co
     }
     c->have_lin = true;
     return relinearise(c);
+}
+
+extern "C" wc4d_status wc4d_set_trajectory(wc4d_ctx *c, const double *X)
+{
+    if (!c || !X) return WC4D_EINVAL;
+    if (c->prob.model != WC4D_MODEL_L96) return set_err(c, WC4D_EINVAL, "set_trajectory: Lorenz-96 model only");
+    const int n = c->prob.n;
+    const int64_t nsteps = (int64_t)c->prob.N * c->prob.steps;
+    WC4D_TRY(ensure(c, c->traj64, sizeof(double) * (size_t)(nsteps + 1) * n));
+    WC4D_TRY(ensure(c, c->stage64, sizeof(double) * (size_t)4 * nsteps * n));
+    WC4D_TRY(ensure(c, c->stage32, sizeof(float) * (size_t)4 * nsteps * n));
+    WC4D_CUDA(c, cudaMemcpyAsync(c->traj64.p, X, sizeof(double) * (size_t)(nsteps + 1) * n, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    launch_l96_stages(c->stream, n, (int)nsteps, c->prob.F, c->prob.dt, P<double>(c->traj64), P<double>(c->stage64));
+    launch_convert_f64_f32(c->stream, 4 * nsteps * n, P<double>(c->stage64), P<float>(c->stage32));
+    WC4D_TRY(check_launch(c, "set_trajectory"));
+    c->have_traj = true;
+    return sync(c, "set_trajectory");
+}
+
+extern "C" wc4d_status wc4d_set_innovation(wc4d_ctx *c, const double *d, const double *Dm12b)
+{
+    if (!c || (!d && c->nobs > 0)) return WC4D_EINVAL;
+    WC4D_TRY(require_operator(c));
+    const int64_t nA = c->nA;
+    WC4D_TRY(ensure(c, c->d, sizeof(double) * std::max<int64_t>(c->nobs, 1)));
+    if (c->nobs > 0)
+        WC4D_CUDA(c, cudaMemcpyAsync(c->d.p, d, sizeof(double) * c->nobs, cudaMemcpyDeviceToDevice, c->stream));
+    c->have_Dm12b = Dm12b != nullptr;
+    if (Dm12b) {
+        WC4D_TRY(ensure(c, c->Dm12b, sizeof(double) * nA));
+        WC4D_CUDA(c, cudaMemcpyAsync(c->Dm12b.p, Dm12b, sizeof(double) * nA, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return compute_rhs(c);
 }
 
 extern "C" wc4d_status wc4d_outer_update(wc4d_ctx *c, const double *x)

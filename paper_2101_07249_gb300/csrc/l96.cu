@@ -820,3 +820,54 @@ void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, doub
     WC4D_LAUNCH(k_l96_run<<<1, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, nsteps, F, dt, traj, stages, eta,
                                                                            steps));
 }
+
+// Stage states of every RK4 step from a given trajectory (states x_g, g <
+// nsteps): s1 = x_g, s2 = x_g + h/2 f(s1), s3 = x_g + h/2 f(s2), s4 = x_g + h
+// f(s3), the convention of k_l96_run; one CTA per step, two n-vectors of
+// shared memory.
+__global__ void __launch_bounds__(1024) k_l96_stages(int n, double F, double h, const double *traj, double *stages)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    double *x = reinterpret_cast<double *>(sm);
+    double *st = x + n;
+    const int64_t g = blockIdx.x;
+    const double *xg = traj + g * n;
+    double *sg = stages + 4 * g * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        x[j] = xg[j];
+        st[j] = xg[j];
+        sg[j] = xg[j];
+    }
+    __syncthreads();
+    const double cf[3] = {0.5 * h, 0.5 * h, h};
+    for (int i = 0; i < 3; ++i) {
+        double d[WC4D_FFT_MAX_N / 1024];
+#pragma unroll
+        for (int r = 0; r < WC4D_FFT_MAX_N / 1024; ++r) {
+            const int j = threadIdx.x + r * blockDim.x;
+            if (j < n) d[r] = l96f(st, j, n, F);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < WC4D_FFT_MAX_N / 1024; ++r) {
+            const int j = threadIdx.x + r * blockDim.x;
+            if (j < n) {
+                const double v = x[j] + cf[i] * d[r];
+                st[j] = v;
+                sg[(int64_t)(i + 1) * n + j] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void launch_l96_stages(cudaStream_t s, int n, int nsteps, double F, double dt, const double *traj, double *stages)
+{
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_l96_stages, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(2 * WC4D_FFT_MAX_N * sizeof(double))) == cudaSuccess;
+    }();   // once, thread-safe
+    (void)attr;
+    WC4D_LAUNCH(k_l96_stages<<<nsteps, 1024, 2 * (size_t)n * sizeof(double), s>>>(n, F, dt, traj, stages));
+}
+

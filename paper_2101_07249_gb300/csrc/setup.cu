@@ -161,13 +161,15 @@ __device__ __forceinline__ int bitrev(int v, int logn) { return (int)(__brev((un
 // them) are clamped to zero; every non-negative one is kept.
 __device__ __forceinline__ double kept_sqrt(double l) { return (l > 0.0) ? sqrt(l) : 0.0; }
 
-// FFT path: spec[p] = sqrt(lam[bitrev(p)]) / n.  Direct path: first row of
-// the square root, r[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).
-__global__ void k_sqrt_spec(int n, int logn, const double *lam, double *spec64, float *spec32)
+// FFT path: spec[p] = sqrt(lam[bitrev(p)]) / n (root = 1: the eigenvalues are
+// those of the square root already, spec[p] = lam[bitrev(p)] / n).  Direct
+// path: first row of the square root, r[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).
+__global__ void k_sqrt_spec(int n, int logn, const double *lam, double *spec64, float *spec32, int root)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    double v = kept_sqrt(lam[bitrev(p, logn)]) / (double)n;
+    const double l = lam[bitrev(p, logn)];
+    double v = (root ? l : kept_sqrt(l)) / (double)n;
     spec64[p] = v;
     spec32[p] = (float)v;
 }
@@ -183,15 +185,29 @@ __global__ void k_sqrt_row(int n, const double *lam, const double2 *tab, double 
     row32[s] = (float)acc;
 }
 
+__global__ void k_copy_row(int n, const double *row, double *row64, float *row32)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    row64[s] = row[s];
+    row32[s] = (float)row[s];
+}
+
 // Square root of a circulant covariance: eigenvalues from the correlation
 // function (kind >= 0; k_corr_eig) or from an explicit row (kind < 0;
 // k_circ_eig), then the spectrum (FFT path) or first row (direct path).
+// root_given: the explicit row is the first row of the square root itself.
 void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, int kind, double L, double var, const double *row,
-                     const double2 *tab, double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32)
+                     const double2 *tab, double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32,
+                     bool root_given)
 {
+    if (root_given && !fft) {
+        WC4D_LAUNCH(k_copy_row<<<ceil_div(n, 256), 256, 0, s>>>(n, row, row64, row32));
+        return;
+    }
     if (kind >= 0) WC4D_LAUNCH(k_corr_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, kind, L, var, lam_tmp));
     else WC4D_LAUNCH(k_circ_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, row, tab, lam_tmp));
-    if (fft) WC4D_LAUNCH(k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, logn, lam_tmp, spec64, spec32));
+    if (fft) WC4D_LAUNCH(k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, logn, lam_tmp, spec64, spec32, root_given ? 1 : 0));
     else WC4D_LAUNCH(k_sqrt_row<<<ceil_div(n, 128), 128, 0, s>>>(n, lam_tmp, tab, row64, row32));
 }
 

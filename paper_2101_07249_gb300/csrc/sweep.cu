@@ -405,13 +405,14 @@ static void launch_stockham(cudaStream_t s, int grid, size_t smem, int N, int K,
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_circ_direct(int n, int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy, const T *addX,
-              int64_t ld_add, const T *__restrict__ rowB, const T *__restrict__ rowQ)
+              int64_t ld_add, const T *__restrict__ rowB, const T *__restrict__ rowQ, int skip)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);
     T *rs = xs + n;
     int64_t v = blockIdx.x;
     int64_t j = v / (N + 1), t = v % (N + 1);
+    if (skip & (t == 0 ? 1 : 2)) return;   // block handled elsewhere (dense square root)
     const T *row = (t == 0) ? rowB : rowQ;
     const T *x = X + j * ldx + t * n;
     for (int s = threadIdx.x; s < n; s += blockDim.x) { xs[s] = x[s]; rs[s] = row[s]; }
@@ -455,16 +456,18 @@ static void launch_diag_blocks(cudaStream_t s, const wc4d_ctx *c, int t0, int t1
 template <typename T>
 void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy,
                       const T *addX, int64_t ld_add, bool fft, const T *specB, const T *specQ, const T *rowB,
-                      const T *rowQ, const void *tw)
+                      const T *rowQ, const void *tw, int skip)
 {
     const int n = c->prob.n, N = c->prob.N;
     // the FFT path transforms only the non-diagonal covariance blocks
-    // (Lorenz-96: Q = 0.05 I needs no transform for its N blocks)
-    const double sdB = c->cov_sd[0], sdQ = c->cov_sd[1];
-    if (fft && (sdB >= 0.0 || sdQ >= 0.0)) {
+    // (Lorenz-96: Q = 0.05 I needs no transform for its N blocks); blocks in
+    // `skip` are left to the caller
+    const double sdB = (skip & 1) ? -2.0 : c->cov_sd[0], sdQ = (skip & 2) ? -2.0 : c->cov_sd[1];
+    const bool doneB = (skip & 1) || sdB >= 0.0, doneQ = (skip & 2) || sdQ >= 0.0;
+    if (fft && (doneB || doneQ)) {
         if (sdB >= 0.0) launch_diag_blocks<T>(s, c, 0, 1, K, X, ldx, Y, ldy, addX, ld_add, sdB);
         if (sdQ >= 0.0) launch_diag_blocks<T>(s, c, 1, N + 1, K, X, ldx, Y, ldy, addX, ld_add, sdQ);
-        if (sdB >= 0.0 && sdQ >= 0.0) return;
+        if (doneB && doneQ) return;
     }
     if (fft) {
         size_t smem = (size_t)(n + n / 16 + n / 2) * sizeof(typename Cplx<T>::t);
@@ -477,8 +480,8 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
         int nB = (K + 1) / 2;
         int64_t nQ = ((int64_t)K * N + 1) / 2;
         int grid = (int)(nB + nQ);
-        if (sdQ >= 0.0) grid = nB;                 // block 0 only (pairs < nB are B's)
-        else if (sdB >= 0.0) { grid = (int)nQ; nB = 0; }   // Q blocks only
+        if (doneQ) grid = nB;                      // block 0 only (pairs < nB are B's)
+        else if (doneB) { grid = (int)nQ; nB = 0; }  // Q blocks only
         switch (c->logn) {   // n / 16 threads, 16 values each
         case 9: launch_stockham<T, 9>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
         case 10: launch_stockham<T, 10>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
@@ -497,16 +500,17 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
         }();
         (void)attr;
         int64_t grid = (int64_t)K * (N + 1);
-        WC4D_LAUNCH(k_circ_direct<T><<<(unsigned)grid, 256, smem, s>>>(n, N, K, X, ldx, Y, ldy, addX, ld_add, rowB, rowQ));
+        WC4D_LAUNCH(k_circ_direct<T><<<(unsigned)grid, 256, smem, s>>>(n, N, K, X, ldx, Y, ldy, addX, ld_add, rowB, rowQ,
+                                                                       skip));
     }
 }
 
 template void launch_circulant<double>(cudaStream_t, const wc4d_ctx *, int, const double *, int64_t, double *,
                                        int64_t, const double *, int64_t, bool, const double *, const double *,
-                                       const double *, const double *, const void *);
+                                       const double *, const double *, const void *, int);
 template void launch_circulant<float>(cudaStream_t, const wc4d_ctx *, int, const float *, int64_t, float *,
                                       int64_t, const float *, int64_t, bool, const float *, const float *,
-                                      const float *, const float *, const void *);
+                                      const float *, const float *, const void *, int);
 
 // ----------------------------------------------------------------------------
 // SIMT GEMM: C(i,j) = epi(sum_k A(i,k) B(k,j)); A(i,k) = A[i*sam + k*sak],

@@ -81,6 +81,8 @@ struct wc4d_ctx {
     DevBuf tw64, tw32;              // FFT twiddles e^{-2 pi i j / n}, j < n/2
     DevBuf cosn;                    // cos/sin table e^{2 pi i j/n}, j < n (set-up DFTs)
     double cov_sd[2] = {-1.0, -1.0};  // sqrt(variance) of a block that is variance * I, else -1
+    bool cov_dense[2] = {false, false};   // dense square root given (wc4d_set_cov_sqrt kind 1)
+    DevBuf dense64[2], dense32[2];        // its n x n row-major FP64 and FP32 copies
 
     // observations and right-hand side
     DevBuf d, rhs, Dm12b;
@@ -192,7 +194,8 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 void launch_gaussian(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, int64_t ld, double *G);
 void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, float2 *tw32);
 void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, int kind, double L, double var, const double *row,
-                     const double2 *tab, double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32);
+                     const double2 *tab, double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32,
+                     bool root_given = false);
 void launch_advdiff_column(cudaStream_t s, int n, double kappa, double c, double dt, int steps,
                            const double2 *tab, double2 *sym_tmp, double *col);
 void launch_expand_circulant(cudaStream_t s, int n, const double *col, double *M, double *MT);
@@ -201,10 +204,12 @@ void launch_convert_f32_f64(cudaStream_t s, int64_t count, const float *a, doubl
 void launch_transpose_f64(cudaStream_t s, int n, const double *A, double *AT);
 
 // sweeps
+// skip: bit 0 leaves block 0 (B) untouched, bit 1 blocks 1..N (Q) -- blocks
+// whose square root is dense and applied by GEMMs instead.
 template <typename T>
 void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int64_t ldx, T *Y, int64_t ldy,
                       const T *addX, int64_t ld_add, bool fft, const T *specB, const T *specQ,
-                      const T *rowB, const T *rowQ, const void *tw);
+                      const T *rowB, const T *rowQ, const void *tw, int skip = 0);
 template <typename T>
 void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
                        const Epi &e);
@@ -338,3 +343,4 @@ void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
                           int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride);
 void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages,
                     const double *eta, int steps);
+void launch_l96_stages(cudaStream_t s, int n, int nsteps, double F, double dt, const double *traj, double *stages);
