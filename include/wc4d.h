@@ -391,12 +391,27 @@ int32_t     wc4d_jacobi_sweeps_fp32(const wc4d_ctx *ctx);
    the device cannot co-schedule such a cluster), 0 = none; -1 for a null
    context. */
 int32_t     wc4d_jacobi_fp32_kernel(const wc4d_ctx *ctx);
-/* CUDA-graph replay of the CG iteration (default on): after one eager
-   iteration, the body of Alg. 1's loop (the product with A, the LMP step and
-   the direction update) is captured once per solve and replayed; the
-   results are bitwise those of the eager launches.  enable = 0 keeps every
-   iteration eager.  EINVAL for a null context. */
+/* CUDA graphs for the CG iterations (Alg. 1's loop body: the product with A,
+   the LMP step and the direction update), built once per solve after one
+   eager iteration; the results are bitwise those of eager launches.
+   enable = 1 (default): one graph whose conditional WHILE node runs the
+   iterations on the device, the host waking only when CG stops, the limit is
+   reached or a reliable update is due (falls back to the next form if the
+   driver refuses it); 2: one graph launch per iteration, the host reading
+   the stopping flags after each; 0: every iteration eager.  The graphs are
+   captured on a private stream of the context and launched on its stream.
+   EINVAL for a null context or enable outside 0..2. */
 wc4d_status wc4d_set_graphs(wc4d_ctx *ctx, int32_t enable);
+/* How the last wc4d_pcg / wc4d_inner_loop solve ran the CG iterations after
+   the first: 0 = eager launches (graphs off, profiling on, or both graph
+   forms refused), 1 = one graph launch per iteration, the host reading the
+   stopping flags after each, 2 = a graph with a conditional WHILE node that
+   runs iterations on the device until CG stops, the iteration limit is
+   reached or (mixed path) a reliable update is due.  If the WHILE-node graph
+   could not be built, note (when not NULL; note_len bytes, NUL-terminated,
+   truncated) receives the failing CUDA call and its error, else "".
+   -1 for a null context. */
+int32_t     wc4d_iteration_mode(const wc4d_ctx *ctx, char *note, int32_t note_len);
 /* Polls of the grid barriers of the persistent one-column sweeps (the FP64
    sweep, and the FP32 sweep when n is not a multiple of 2048) before a wait
    gives up: the kernel then records the failure and returns, and the call

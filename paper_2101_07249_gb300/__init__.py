@@ -97,6 +97,7 @@ _SIGS = {
     "wc4d_lanczos_tridiag": (C.c_int32, [_V, _V, _V]),
     "wc4d_lanczos_ritz": (C.c_int32, [_V, C.c_int32, _V]),
     "wc4d_set_graphs": (C.c_int32, [_V, C.c_int32]),
+    "wc4d_iteration_mode": (C.c_int32, [_V, C.c_char_p, C.c_int32]),
     "wc4d_stream_create": (C.c_int32, [C.POINTER(C.c_void_p)]),
     "wc4d_stream_destroy": (C.c_int32, [_V]),
     "wc4d_set_reliable_delta": (C.c_int32, [_V, C.c_double]),
@@ -558,7 +559,21 @@ def wc4d_jacobi_fp32_kernel(ctx):
 
 
 def wc4d_set_graphs(ctx, enable):
-    _check(ctx, load().wc4d_set_graphs(ctx, 1 if enable else 0))
+    """enable: True / 1 device-side loop graph, 2 one graph per iteration, False / 0 eager."""
+    _check(ctx, load().wc4d_set_graphs(ctx, int(enable)))
+
+
+ITER_EAGER, ITER_GRAPH_PER_ITERATION, ITER_DEVICE_LOOP = 0, 1, 2
+
+
+def wc4d_iteration_mode(ctx):
+    """(mode, note): how the last solve ran its CG iterations (ITER_*) and,
+    if the device-side loop graph could not be built, the failing call."""
+    buf = C.create_string_buffer(256)
+    mode = load().wc4d_iteration_mode(ctx, buf, len(buf))
+    if mode < 0:
+        raise WC4DError(EINVAL, "wc4d_iteration_mode: null context")
+    return mode, buf.value.decode(errors="replace")
 
 
 def wc4d_stream_create():

@@ -113,6 +113,29 @@ struct IterGraph {
     }
 };
 
+// The stream the iteration bodies are captured on.  The legacy and
+// per-thread default streams cannot be captured, and the caller's stream is
+// often one of them, so capture runs on a private non-blocking stream of the
+// context (nullptr if it cannot be created); capture executes nothing, and
+// the instantiated graph is launched on c->stream.
+static cudaStream_t capture_stream(wc4d_ctx *c)
+{
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_stream = nullptr;
+    }
+    return c->cap_stream;
+}
+
+// c->stream points at the capture stream while a body is captured (every
+// launch of the body reads c->stream), and back at the caller's stream after.
+struct CaptureStreamScope {
+    wc4d_ctx *c;
+    cudaStream_t user;
+    CaptureStreamScope(wc4d_ctx *ctx, cudaStream_t cs) : c(ctx), user(ctx->stream) { c->stream = cs; }
+    ~CaptureStreamScope() { c->stream = user; }
+};
+
 template <typename F> static wc4d_status run_iteration(wc4d_ctx *c, IterGraph &g, int it, F body)
 {
     if (g.exec) {
@@ -123,15 +146,21 @@ template <typename F> static wc4d_status run_iteration(wc4d_ctx *c, IterGraph &g
         return WC4D_OK;
     }
     if (it == 0 || g.failed || c->prof_on || !c->use_graphs) return body();
+    cudaStream_t cs = capture_stream(c);
     const int64_t l0 = tl_launches, h0 = c->hvp_count;
-    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         g.failed = true;
         return body();
     }
-    const wc4d_status st = body();
+    wc4d_status st;
     cudaGraph_t graph = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+    cudaError_t ec;
+    {
+        CaptureStreamScope scope(c, cs);
+        st = body();
+        ec = cudaStreamEndCapture(cs, &graph);
+    }
     const int64_t nl = tl_launches - l0, nh = c->hvp_count - h0;
     // the captured kernels have not run: take them off the counters
     g_launches.fetch_sub(nl, std::memory_order_relaxed);
@@ -182,6 +211,142 @@ static wc4d_status sync(wc4d_ctx *c, const char *what)
 }
 
 template <typename T> static T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+// ----------------------------------------------------------------------------
+// The CG loop on the device: a CUDA graph whose single node is a conditional
+// WHILE node; its body is one iteration (the same launches as IterGraph's)
+// followed by k_cg_continue, which sets the node's condition from the device
+// flags.  One graph launch then runs iterations until CG converges or breaks
+// down, the iteration limit is reached, or -- for the mixed path's reliable
+// updates -- the recurrence residual falls below the update threshold
+// (scal[8]); only then does the host look at the flags, so no host round trip
+// separates the iterations.  The decisions are those the host loop takes
+// after every iteration, so the iterates are bitwise those of the eager
+// launches.  A guard counter (counter word 14, set by the host before each
+// launch) bounds the loop whatever the flags say.  Built after the first
+// eager iteration of a solve; if the driver refuses any part of it, the
+// solve continues with IterGraph (one graph launch per iteration).
+// ----------------------------------------------------------------------------
+__global__ void k_cg_continue(cudaGraphConditionalHandle h, const int *flags, const double *scal, int it_end,
+                              int use_thresh, int *guard)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int g = guard[0] - 1;
+    guard[0] = g;
+    bool go = flags[0] == 0 && flags[1] == 0 && flags[2] < it_end && g > 0;
+    if (use_thresh && !(scal[4] >= scal[8])) go = false;   // a reliable update is due (or the residual is NaN)
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+struct LoopGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;    // kernels per iteration (the decision kernel included)
+    int64_t hvps = 0;        // products with A per iteration
+    bool failed = false;
+    LoopGraph() = default;
+    LoopGraph(const LoopGraph &) = delete;
+    LoopGraph &operator=(const LoopGraph &) = delete;
+    ~LoopGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+// Builds the loop graph around `body` (false: not available; the caller
+// keeps iterating one iteration at a time).
+template <typename F>
+static bool build_loop(wc4d_ctx *c, LoopGraph &L, F body, int it_end, bool use_thresh)
+{
+    if (L.exec) return true;
+    if (L.failed || c->prof_on || !c->use_graphs || !c->use_loop_graph) return false;
+    // the first call that fails names the reason in c->loop_note
+    const char *step = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r, const char *what) {
+        if (!step && r != cudaSuccess) {
+            step = what;
+            e = r;
+        }
+        return !step;
+    };
+    cudaGraph_t outer = nullptr;
+    chk(cudaGraphCreate(&outer, 0), "cudaGraphCreate");
+    cudaGraphConditionalHandle h{};
+    if (!step) chk(cudaGraphConditionalHandleCreate(&h, outer, 1, cudaGraphCondAssignDefault),
+                   "cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (!step) chk(cudaGraphAddNode(&node, outer, nullptr, nullptr, 0, &np), "cudaGraphAddNode (conditional)");
+    const int64_t l0 = tl_launches, h0 = c->hvp_count;
+    cudaStream_t cs = step ? nullptr : capture_stream(c);
+    if (!step && !cs) {
+        step = "cudaStreamCreateWithFlags (capture stream)";
+        e = cudaErrorUnknown;
+    }
+    if (!step) {
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        if (chk(cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                "cudaStreamBeginCaptureToGraph")) {
+            CaptureStreamScope scope(c, cs);
+            const wc4d_status st = body();
+            WC4D_LAUNCH(k_cg_continue<<<1, 32, 0, cs>>>(h, P<int>(c->counter) + 4, P<double>(c->scal), it_end,
+                                                      use_thresh ? 1 : 0, P<int>(c->counter) + 14));
+            const cudaError_t el = cudaGetLastError();
+            cudaGraph_t got = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(cs, &got);
+            if (st != WC4D_OK && !step) {
+                step = "capture of the iteration body";
+                e = el != cudaSuccess ? el : cudaErrorUnknown;
+            }
+            chk(el, "capture of the decision kernel");
+            chk(ec, "cudaStreamEndCapture");
+        }
+    }
+    const int64_t nl = tl_launches - l0, nh = c->hvp_count - h0;
+    g_launches.fetch_sub(nl, std::memory_order_relaxed);   // captured, not run
+    tl_launches -= nl;
+    c->hvp_count = h0;
+    if (!step) chk(cudaGraphInstantiate(&L.exec, outer, 0), "cudaGraphInstantiate");
+    if (outer) cudaGraphDestroy(outer);
+    if (step) {
+        if (L.exec) cudaGraphExecDestroy(L.exec);
+        L.exec = nullptr;
+        cudaGetLastError();
+        c->err.clear();
+        c->loop_note = std::string(step) + ": " + cudaGetErrorString(e);
+        L.failed = true;
+        return false;
+    }
+    L.launches = nl;
+    L.hvps = nh;
+    return true;
+}
+
+// Runs the loop graph for at most `max_iters` iterations; *done_iters receives
+// the device iteration counter afterwards (flags and residual are read into
+// the pinned slots hflags[0..2], hrel).
+static wc4d_status run_loop(wc4d_ctx *c, LoopGraph &L, int max_iters, int it_before, int *hflags, double *hrel,
+                            int *iters_after)
+{
+    int *hguard = reinterpret_cast<int *>(P<char>(c->pinned) + 128);
+    *hguard = max_iters;   // at most max_iters iterations whatever the flags say
+    WC4D_CUDA(c, cudaMemcpyAsync(P<int>(c->counter) + 14, hguard, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    if (cudaGraphLaunch(L.exec, c->stream) != cudaSuccess) return check_launch(c, "CG loop graph");
+    WC4D_CUDA(c, cudaMemcpyAsync(hflags, P<int>(c->counter) + 4, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+    WC4D_CUDA(c, cudaMemcpyAsync(hrel, P<double>(c->scal) + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WC4D_TRY(sync(c, "CG loop"));
+    const int ran = hflags[2] - it_before;
+    g_launches.fetch_add(L.launches * ran, std::memory_order_relaxed);
+    tl_launches += L.launches * ran;
+    c->hvp_count += L.hvps * ran;
+    *iters_after = hflags[2];
+    return WC4D_OK;
+}
+
 
 static bool observed_time(const wc4d_problem &p, int t)
 {
@@ -304,6 +469,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
     for (int i = 0; i < 8; ++i) { free_buf(c->pcg64[i]); free_buf(c->pcg32[i]); }
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -376,10 +542,23 @@ extern "C" wc4d_status wc4d_set_wait_limit(wc4d_ctx *c, int64_t polls)
     return WC4D_OK;
 }
 
+extern "C" int32_t wc4d_iteration_mode(const wc4d_ctx *c, char *note, int32_t note_len)
+{
+    if (!c) return -1;
+    if (note && note_len > 0) {
+        const size_t m = std::min<size_t>(c->loop_note.size(), (size_t)note_len - 1);
+        std::memcpy(note, c->loop_note.data(), m);
+        note[m] = '\0';
+    }
+    return c->iter_mode;
+}
+
 extern "C" wc4d_status wc4d_set_graphs(wc4d_ctx *c, int32_t enable)
 {
     if (!c) return WC4D_EINVAL;
+    if (enable < 0 || enable > 2) return WC4D_EINVAL;
     c->use_graphs = enable != 0;
+    c->use_loop_graph = enable == 1;
     return WC4D_OK;
 }
 
@@ -1724,12 +1903,20 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
         }
         return check_launch(c, "pcg iteration");
     };
-    for (int it = 0; it < nit; ++it) {
+    LoopGraph loop;
+    for (int it = 0; it < nit;) {
+        if (it > 0 && build_loop(c, loop, body, nit, false)) {   // the remaining iterations on the device
+            double hrel_unused;
+            WC4D_TRY(run_loop(c, loop, nit - it, it, hflags, &hrel_unused, &it));
+            break;
+        }
         WC4D_TRY(run_iteration(c, graph, it, body));
         WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
         WC4D_TRY(sync(c, "pcg iteration"));
+        ++it;
         if (hflags[0]) break;
     }
+    c->iter_mode = loop.exec ? 2 : graph.exec ? 1 : 0;
     double hs[8];
     WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
     WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1843,14 +2030,26 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
         }
         return check_launch(c, "pcg iteration");
     };
+    LoopGraph loop;
     for (; it < nit && !converged; ++it) {
-        WC4D_TRY(run_iteration(c, graph, it, body));
-        WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
-        WC4D_CUDA(c, cudaMemcpyAsync(hrel, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        WC4D_TRY(sync(c, "pcg iteration"));
+        const double thresh = c->reliable_delta * rmax;
+        if (it > 0 && build_loop(c, loop, body, nit, true)) {
+            // iterations on the device until an update is due, CG ends or the limit
+            double *hth = reinterpret_cast<double *>(P<char>(c->pinned) + 192);
+            *hth = thresh;
+            WC4D_CUDA(c, cudaMemcpyAsync(scal + 8, hth, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            int after = it;
+            WC4D_TRY(run_loop(c, loop, nit - it, it, hflags, hrel, &after));
+            it = after - 1;   // the loop's ++it makes it the device count
+        } else {
+            WC4D_TRY(run_iteration(c, graph, it, body));
+            WC4D_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+            WC4D_CUDA(c, cudaMemcpyAsync(hrel, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            WC4D_TRY(sync(c, "pcg iteration"));
+        }
         pending = true;
         if (hflags[1]) { breakdown = true; ++it; break; }
-        if (!(hflags[0] || *hrel < c->reliable_delta * rmax)) continue;
+        if (!(hflags[0] || *hrel < thresh)) continue;
         // reliable update
         launch_add_f32_to_f64(c->stream, nA, d, x);
         WC4D_CUDA(c, cudaMemsetAsync(d, 0, sizeof(float) * nA, c->stream));
@@ -1866,6 +2065,7 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
         launch_pcg_restart(c->stream, grid, pb, pc, scal, flags);
         WC4D_TRY(check_launch(c, "reliable update"));
     }
+    c->iter_mode = loop.exec ? 2 : graph.exec ? 1 : 0;
     if (pending) {   // iteration budget spent (or breakdown) between updates
         launch_add_f32_to_f64(c->stream, nA, d, x);
         WC4D_TRY(true_residual(c, x, r64, &rel, nullptr));

@@ -139,6 +139,10 @@ struct wc4d_ctx {
     DevBuf lz_F, lz_ab, lz_h;
     int lz_J = 0;
     bool use_graphs = true;         // CG iterations replayed as a CUDA graph (wc4d_set_graphs)
+    bool use_loop_graph = true;     // ... as one graph with a device-side WHILE loop
+    cudaStream_t cap_stream = nullptr;   // private stream CUDA-graph captures run on
+    int iter_mode = 0;              // how the last solve ran its iterations (wc4d_iteration_mode)
+    std::string loop_note;          // why the device-side loop graph could not be built ("" if it could)
     double reliable_delta = 1e-3;   // mixed CG: residual reduction between FP64 true-residual updates
     double jacobi_stop2 = 0.0;      // early stop of the small eigensolves (0: run to a sweep without rotations)
     int jacobi_sweeps = 0;          // sweeps used by the last one

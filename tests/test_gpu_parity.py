@@ -565,20 +565,26 @@ def test_outer_update_matches_oracle(name):
 @pytest.mark.parametrize("name", ["ad_fft", "l96"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_cg_graph_replay_is_bitwise_eager(name, precision):
-    """The CG iterations replayed from a captured CUDA graph compute exactly
-    what the eager launches compute: same iterates, counts and QCF history."""
+    """The CG iterations run from captured CUDA graphs -- the device-side
+    WHILE loop and one graph launch per iteration -- compute exactly what the
+    eager launches compute: same iterates, counts and QCF history.  The
+    solver's stream is the legacy default stream, which cannot be captured:
+    the graphs must still engage (captured on the context's own stream)."""
     cfg, S, p, tw = setup(name)
     prec = w.FP64 if precision == "fp64" else w.MIXED
     w.wc4d_sketch(S.ctx, w.REVD, cfg.k, cfg.l, cfg.q_power, 41, None, prec)
     out = []
-    for graphs in (False, True):
+    for graphs, mode in ((0, w.ITER_EAGER), (1, w.ITER_DEVICE_LOOP), (2, w.ITER_GRAPH_PER_ITERATION)):
         w.wc4d_set_graphs(S.ctx, graphs)
         x = torch.zeros(cfg.nA, dtype=torch.float64, device="cuda")
         it, rel, qcf, _ = w.wc4d_pcg(S.ctx, x, 1e-9, 5000, 1, 0, prec, qcf=True)
+        assert w.wc4d_iteration_mode(S.ctx) == (mode, ""), (graphs, w.wc4d_iteration_mode(S.ctx))
         out.append((it, rel, host(x), np.asarray(qcf)))
     w.wc4d_set_graphs(S.ctx, True)
-    (i0, r0, x0, q0), (i1, r1, x1, q1) = out
-    assert i0 == i1 and i0 > 2
-    assert r0 == r1
-    assert np.array_equal(x0, x1)
-    assert np.array_equal(q0, q1)
+    i0, r0, x0, q0 = out[0]
+    assert i0 > 2
+    for i1, r1, x1, q1 in out[1:]:
+        assert i0 == i1
+        assert r0 == r1
+        assert np.array_equal(x0, x1)
+        assert np.array_equal(q0, q1)
