@@ -430,6 +430,8 @@ extern "C" wc4d_status wc4d_create(wc4d_ctx **out, const wc4d_problem *prob, voi
     if ((s = ensure(c, c->cosn, sizeof(double2) * p.n)) != WC4D_OK ||
         (s = ensure(c, c->tw64, sizeof(double2) * (p.n / 2 + 1))) != WC4D_OK ||
         (s = ensure(c, c->tw32, sizeof(float2) * (p.n / 2 + 1))) != WC4D_OK ||
+        (s = ensure(c, c->twp64, sizeof(double2) * p.n)) != WC4D_OK ||
+        (s = ensure(c, c->twp32, sizeof(float2) * p.n)) != WC4D_OK ||
         (s = ensure(c, c->scal, sizeof(double) * 32)) != WC4D_OK ||
         (s = ensure(c, c->counter, sizeof(int) * 16)) != WC4D_OK ||
         (s = ensure_host(c, c->pinned, 4096)) != WC4D_OK) {
@@ -445,6 +447,7 @@ extern "C" wc4d_status wc4d_create(wc4d_ctx **out, const wc4d_problem *prob, voi
         return WC4D_ECUDA;
     }
     launch_twiddles(c->stream, p.n, P<double2>(c->cosn), P<double2>(c->tw64), P<float2>(c->tw32));
+    if (c->fft) launch_pass_twiddles(c->stream, p.n, P<double2>(c->twp64), P<float2>(c->twp32));
     if ((s = check_launch(c, "twiddles")) != WC4D_OK || (s = sync(c, "create")) != WC4D_OK) {
         wc4d_destroy(c);
         return s;
@@ -459,7 +462,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->M64, &c->MT64, &c->M32, &c->MT32, &c->traj64, &c->stage64, &c->stage32, &c->spec64[0], &c->spec64[1],
                       &c->spec32[0], &c->spec32[1], &c->row64[0], &c->row64[1], &c->row32[0], &c->row32[1],
-                      &c->tw64, &c->tw32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
+                      &c->tw64, &c->tw32, &c->twp64, &c->twp32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
                       &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,

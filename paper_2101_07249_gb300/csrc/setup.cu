@@ -71,6 +71,40 @@ void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, fl
     WC4D_LAUNCH(k_twiddles<<<ceil_div(n, 256), 256, 0, s>>>(n, tab_full, tw64, tw32));
 }
 
+// Per-pass twiddles of the radix-16 Stockham FFT (n a power of two >= 16):
+// the passes have spans P = 1, 16, 256, ... with radix 16 while 16 P <= n,
+// then one pass of radix n / P.  The pass at span P >= 16 needs
+// W_n^{r k n / (P R)} for 1 <= r < R, k < P, stored at P - 16 + (r - 1) P + k
+// (the passes before it, all radix 16, take 15 (16 + 256 + ... + P / 16) =
+// P - 16 entries); n - 16 entries in all, the rest of the n-entry table is
+// zero.
+__global__ void k_pass_twiddles(int n, double2 *twp64, float2 *twp32)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double2 v = make_double2(0.0, 0.0);
+    for (int P = 16; P < n;) {
+        const int R = min(16, n / P);
+        const int off = P - 16, cnt = (R - 1) * P;
+        if (e >= off && e < off + cnt) {
+            const int r = 1 + (e - off) / P, k = (e - off) % P;
+            const int64_t q = (int64_t)r * k * (n / (P * R));   // < n
+            double sn, cs;
+            sincospi(2.0 * (double)q / (double)n, &sn, &cs);
+            v = make_double2(cs, -sn);
+            break;
+        }
+        P *= R;
+    }
+    twp64[e] = v;
+    twp32[e] = make_float2((float)v.x, (float)v.y);
+}
+
+void launch_pass_twiddles(cudaStream_t s, int n, double2 *twp64, float2 *twp32)
+{
+    WC4D_LAUNCH(k_pass_twiddles<<<ceil_div(n, 256), 256, 0, s>>>(n, twp64, twp32));
+}
+
 // lam[m] = sum_s row[s] cos(2 pi m s / n): eigenvalues of the symmetric
 // circulant given by an explicit first row (FP64 DFT; the angle index m s is
 // reduced mod n exactly through the table).
@@ -155,20 +189,18 @@ __global__ void k_corr_eig(int n, int kind, double L, double var, double *lam)
     lam[m] = var * out;
 }
 
-__device__ __forceinline__ int bitrev(int v, int logn) { return (int)(__brev((unsigned)v) >> (32 - logn)); }
-
 // Negative eigenvalues (a periodically wrapped correlation function can have
 // them) are clamped to zero; every non-negative one is kept.
 __device__ __forceinline__ double kept_sqrt(double l) { return (l > 0.0) ? sqrt(l) : 0.0; }
 
-// FFT path: spec[p] = sqrt(lam[bitrev(p)]) / n (root = 1: the eigenvalues are
-// those of the square root already, spec[p] = lam[bitrev(p)] / n).  Direct
-// path: first row of the square root, r[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).
-__global__ void k_sqrt_spec(int n, int logn, const double *lam, double *spec64, float *spec32, int root)
+// FFT path: spec[p] = sqrt(lam[p]) / n in natural frequency order (root = 1:
+// the eigenvalues are those of the square root already, spec[p] = lam[p] / n).
+// Direct path: first row of the square root, r[s] = (1/n) sum_m sqrt(lam_m) cos(2 pi m s / n).
+__global__ void k_sqrt_spec(int n, const double *lam, double *spec64, float *spec32, int root)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const double l = lam[bitrev(p, logn)];
+    const double l = lam[p];
     double v = (root ? l : kept_sqrt(l)) / (double)n;
     spec64[p] = v;
     spec32[p] = (float)v;
@@ -207,7 +239,7 @@ void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, int kind, double
     }
     if (kind >= 0) WC4D_LAUNCH(k_corr_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, kind, L, var, lam_tmp));
     else WC4D_LAUNCH(k_circ_eig<<<ceil_div(n, 128), 128, 0, s>>>(n, row, tab, lam_tmp));
-    if (fft) WC4D_LAUNCH(k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, logn, lam_tmp, spec64, spec32, root_given ? 1 : 0));
+    if (fft) WC4D_LAUNCH(k_sqrt_spec<<<ceil_div(n, 256), 256, 0, s>>>(n, lam_tmp, spec64, spec32, root_given ? 1 : 0));
     else WC4D_LAUNCH(k_sqrt_row<<<ceil_div(n, 128), 128, 0, s>>>(n, lam_tmp, tab, row64, row32));
 }
 

@@ -119,7 +119,7 @@ k_circ_fft(int n, int logn, int N, int K, const T *__restrict__ X, int64_t ldx, 
     }
 #pragma unroll 8
     for (int p = tid; p < n; p += nt) {
-        T w = spec[p];
+        T w = spec[__brev((unsigned)p) >> (32 - logn)];   // the DIF output is in bit-reversed order
         CT v = buf[fpad(p)];
         v.x *= w; v.y *= w;
         buf[fpad(p)] = v;
@@ -258,23 +258,29 @@ template <int R, typename CT> __device__ __forceinline__ void dftR(CT *v)
 
 // one Stockham pass of radix R at span P of an NN-point transform; NN / 16
 // threads, 16 / R butterflies per thread (everything but the thread index is
-// a compile-time constant)
+// a compile-time constant).  The twiddles W_NN^{r k NN / (P R)} of the pass
+// come from its own slice of the per-pass table (built by
+// launch_pass_twiddles): entry P - 16 + (r - 1) P + k, so that neighbouring
+// threads (neighbouring k) read neighbouring entries through L1 instead of
+// the strided, bank-conflicted reads of a shared W^q table.
 template <int R, int NN, int P, typename CT>
-__device__ __forceinline__ void stockham_pass(CT *buf, const CT *tws, int tid)
+__device__ __forceinline__ void stockham_pass(CT *buf, const CT *__restrict__ twp, int tid)
 {
-    constexpr int B = 16 / R, T = NN / R, NT = NN / 16, HALF = NN / 2, STEP = NN / (P * R);
+    constexpr int B = 16 / R, T = NN / R, NT = NN / 16;
     CT v[B][R];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int j = tid + b * NT, k = j & (P - 1);
+        CT w[R];
+        if constexpr (P > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) w[r] = __ldg(twp + (P - 16) + (r - 1) * P + k);
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             CT x = buf[fpad(j + r * T)];
-            if (r > 0 && P > 1) {
-                const int q = r * k * STEP;   // < NN
-                CT w = tws[q < HALF ? q : q - HALF];
-                if (q >= HALF) { w.x = -w.x; w.y = -w.y; }
-                x = cmul(x, w);
+            if constexpr (P > 1) {
+                if (r > 0) x = cmul(x, w[r]);
             }
             v[b][r] = x;
         }
@@ -291,31 +297,31 @@ __device__ __forceinline__ void stockham_pass(CT *buf, const CT *tws, int tid)
     __syncthreads();
 }
 
-template <typename CT, int NN, int P> __device__ __forceinline__ void stockham_passes(CT *buf, const CT *tws, int tid)
+template <typename CT, int NN, int P> __device__ __forceinline__ void stockham_passes(CT *buf, const CT *twp, int tid)
 {
     if constexpr (P * 16 <= NN) {
-        stockham_pass<16, NN, P>(buf, tws, tid);
-        stockham_passes<CT, NN, P * 16>(buf, tws, tid);
+        stockham_pass<16, NN, P>(buf, twp, tid);
+        stockham_passes<CT, NN, P * 16>(buf, twp, tid);
     } else if constexpr (NN / P > 1) {
-        stockham_pass<NN / P, NN, P>(buf, tws, tid);
+        stockham_pass<NN / P, NN, P>(buf, twp, tid);
     }
 }
 
 // the whole forward transform, not inlined: the kernel calls it twice and one
 // copy of the unrolled passes keeps the instruction footprint small
-template <typename CT, int NN> __device__ __noinline__ void stockham_fft(CT *buf, const CT *tws, int tid)
+template <typename CT, int NN> __device__ __noinline__ void stockham_fft(CT *buf, const CT *twp, int tid)
 {
-    stockham_passes<CT, NN, 1>(buf, tws, tid);
+    stockham_passes<CT, NN, 1>(buf, twp, tid);
 }
 
 template <typename T, int LOGN>
 __global__ void __launch_bounds__((1 << LOGN) / 16)
 k_circ_stockham(int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_t ldy, const T *addX, int64_t ld_add,
-                const T *__restrict__ specB, const T *__restrict__ specQ, const typename Cplx<T>::t *__restrict__ tw,
+                const T *__restrict__ specB, const T *__restrict__ specQ, const typename Cplx<T>::t *__restrict__ twp,
                 int nBpairs)
 {
     using CT = typename Cplx<T>::t;
-    constexpr int n = 1 << LOGN, nt = n / 16, half = n / 2;
+    constexpr int n = 1 << LOGN, nt = n / 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *buf = reinterpret_cast<CT *>(smem_raw);
     const int tid = threadIdx.x;
@@ -339,9 +345,6 @@ k_circ_stockham(int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_
     }
     const T *xa = X + ja * ldx + ta * n;
     const T *xb = X + jb * ldx + tb * n;
-    CT *tws = buf + n + (n >> 4);
-#pragma unroll
-    for (int k = tid; k < half; k += nt) tws[k] = tw[k];
 #pragma unroll
     for (int s = tid; s < n; s += nt) {
         CT v;
@@ -350,18 +353,19 @@ k_circ_stockham(int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_
         buf[fpad(s)] = v;
     }
     __syncthreads();
-    stockham_fft<CT, n>(buf, tws, tid);
-    // scale by the real spectrum (stored bit-reversed) and conjugate
+    stockham_fft<CT, n>(buf, twp, tid);
+    // scale by the real spectrum (natural order, like the self-sorting
+    // transform's output) and conjugate
 #pragma unroll
     for (int q = tid; q < n; q += nt) {
-        const T w = spec[__brev((unsigned)q) >> (32 - LOGN)];
+        const T w = spec[q];
         CT v = buf[fpad(q)];
         v.x *= w;
         v.y *= -w;
         buf[fpad(q)] = v;
     }
     __syncthreads();
-    stockham_fft<CT, n>(buf, tws, tid);
+    stockham_fft<CT, n>(buf, twp, tid);
     T *ya = Y + ja * ldy + ta * n;
     T *yb = Y + jb * ldy + tb * n;
     const T *aa = addX ? addX + ja * ld_add + ta * n : nullptr;
@@ -388,7 +392,7 @@ k_circ_stockham(int N, int K, const T *__restrict__ X, int64_t ldx, T *Y, int64_
 template <typename T, int LOGN>
 static void launch_stockham(cudaStream_t s, int grid, size_t smem, int N, int K, const T *X, int64_t ldx, T *Y,
                             int64_t ldy, const T *addX, int64_t ld_add, const T *specB, const T *specQ,
-                            const void *tw, int nB)
+                            const void *twp, int nB)
 {
     // once per instantiation (smem is fixed by T and LOGN); a function-local
     // static is initialised once even when host threads launch concurrently
@@ -398,7 +402,7 @@ static void launch_stockham(cudaStream_t s, int grid, size_t smem, int N, int K,
     }();
     (void)attr;
     WC4D_LAUNCH(k_circ_stockham<T, LOGN><<<grid, (1 << LOGN) / 16, smem, s>>>(
-        N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, (const typename Cplx<T>::t *)tw, nB));
+        N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, (const typename Cplx<T>::t *)twp, nB));
 }
 
 // Direct symmetric circulant product for any n: y_s = sum_r row[r] x[(s+r) mod n].
@@ -482,12 +486,14 @@ void launch_circulant(cudaStream_t s, const wc4d_ctx *c, int K, const T *X, int6
         int grid = (int)(nB + nQ);
         if (doneQ) grid = nB;                      // block 0 only (pairs < nB are B's)
         else if (doneB) { grid = (int)nQ; nB = 0; }  // Q blocks only
+        const void *twp = sizeof(T) == 8 ? c->twp64.p : c->twp32.p;   // per-pass twiddles (n >= 512)
+        const size_t smem_s = (size_t)(n + n / 16) * sizeof(typename Cplx<T>::t);
         switch (c->logn) {   // n / 16 threads, 16 values each
-        case 9: launch_stockham<T, 9>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
-        case 10: launch_stockham<T, 10>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
-        case 11: launch_stockham<T, 11>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
-        case 12: launch_stockham<T, 12>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
-        case 13: launch_stockham<T, 13>(s, grid, smem, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, tw, nB); return;
+        case 9: launch_stockham<T, 9>(s, grid, smem_s, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, twp, nB); return;
+        case 10: launch_stockham<T, 10>(s, grid, smem_s, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, twp, nB); return;
+        case 11: launch_stockham<T, 11>(s, grid, smem_s, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, twp, nB); return;
+        case 12: launch_stockham<T, 12>(s, grid, smem_s, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, twp, nB); return;
+        case 13: launch_stockham<T, 13>(s, grid, smem_s, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ, twp, nB); return;
         default: break;
         }
         WC4D_LAUNCH(k_circ_fft<T><<<grid, 512, smem, s>>>(n, c->logn, N, K, X, ldx, Y, ldy, addX, ld_add, specB, specQ,

@@ -79,6 +79,7 @@ struct wc4d_ctx {
     DevBuf spec64[2], spec32[2];    // FFT path: sqrt spectrum in bit-reversed order, / n
     DevBuf row64[2], row32[2];      // direct path: first row of the square root
     DevBuf tw64, tw32;              // FFT twiddles e^{-2 pi i j / n}, j < n/2
+    DevBuf twp64, twp32;            // per-pass twiddles of the radix-16 Stockham FFT (n entries)
     DevBuf cosn;                    // cos/sin table e^{2 pi i j/n}, j < n (set-up DFTs)
     double cov_sd[2] = {-1.0, -1.0};  // sqrt(variance) of a block that is variance * I, else -1
     bool cov_dense[2] = {false, false};   // dense square root given (wc4d_set_cov_sqrt kind 1)
@@ -197,6 +198,7 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 // set-up
 void launch_gaussian(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, int64_t ld, double *G);
 void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, float2 *tw32);
+void launch_pass_twiddles(cudaStream_t s, int n, double2 *twp64, float2 *twp32);
 void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, int kind, double L, double var, const double *row,
                      const double2 *tab, double *lam_tmp, double *spec64, float *spec32, double *row64, float *row32,
                      bool root_given = false);
