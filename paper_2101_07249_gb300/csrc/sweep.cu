@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "wc4d_internal.cuh"
+#include "bulk.cuh"
 
 template <typename T> struct Cplx;
 template <> struct Cplx<double> { using t = double2; };
@@ -828,7 +829,6 @@ k_gemv_sweep(const T *__restrict__ M0, T *W, SweepArgs a)
 constexpr int SW_THREADS = 512;                       // consumer threads
 constexpr int SW_RING = 192 * 1024;                   // bytes of shared memory in the ring
 constexpr int SW_RMAX = 64;                           // rows per CTA
-constexpr unsigned SW_WAIT = 1u << 22;                // mbarrier polls before giving up
 constexpr int SW_PF = 4;                              // default L2 look-ahead, stages
 
 template <int J> struct SwShape {
@@ -836,42 +836,6 @@ template <int J> struct SwShape {
     static constexpr int NS = SW_RING / (G * J * SW_THREADS * 16);    // stages in the ring
 };
 
-__device__ __forceinline__ void sw_mb_init(uint32_t a, unsigned c)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(c) : "memory");
-}
-__device__ __forceinline__ void sw_mb_expect(uint32_t a, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void sw_mb_arrive(uint32_t a)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool sw_mb_wait(uint32_t a, unsigned parity)
-{
-    for (unsigned it = 0; it < SW_WAIT; ++it) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void sw_bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t mb)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mb)
-                 : "memory");
-}
-// bulk prefetch of global memory into L2 (no completion, no shared memory)
-__device__ __forceinline__ void sw_prefetch_l2(const void *src, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 // barrier of the 512 consumer threads only (the producer warp is not in it)
 __device__ __forceinline__ void sw_cbar() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
@@ -976,7 +940,8 @@ __global__ void __launch_bounds__(SW_THREADS + 32, 1) k_gemv_sweep_staged(const 
 
     const int nv = n / 4;
     int k = 0;
-    bool bad = false;
+    bool bad = false;    // a grid barrier timed out
+    bool dead = false;   // a ring wait of this thread timed out
     for (int step = 0; step < a.N; ++step) {
         const int t = (a.mode == 0) ? step : a.N - 1 - step;
         const float4 *x4 = reinterpret_cast<const float4 *>(W + (int64_t)((a.mode == 0) ? t : t + 1) * n);
@@ -986,9 +951,13 @@ __global__ void __launch_bounds__(SW_THREADS + 32, 1) k_gemv_sweep_staged(const 
         for (int j = 0; j < J; ++j) xr[j] = __ldcg(x4 + tid + SW_THREADS * j);
         for (int s = 0; s < S; ++s, ++k) {
             const int slot = k % NS;
-            if (!sw_mb_wait(mb + 8 * slot, (k / NS) & 1)) {
+            // after a timed-out wait the thread stops waiting but follows the
+            // same path on the stale slot, so that every lane reaches every
+            // __syncwarp and CTA barrier; the copies still in flight are
+            // waited for (bounded) before the CTA exits
+            if (!dead && !sw_mb_wait(mb + 8 * slot, (k / NS) & 1)) {
+                dead = true;
                 atomicExch(a.err, 4);
-                return;
             }
             float v[G];
 #pragma unroll
@@ -1030,6 +999,9 @@ __global__ void __launch_bounds__(SW_THREADS + 32, 1) k_gemv_sweep_staged(const 
             if (!bad) bad = !sw_step_barrier(a.bar, step, gridDim.x, a.err);
             else sw_cbar();   // keep draining the ring after a barrier timeout
         }
+    }
+    if (dead) {   // copies may still be in flight into the ring: wait (bounded) for the last one of every slot
+        for (int kk = max(0, total - NS); kk < total; ++kk) sw_mb_wait(mb + 8 * (kk % NS), (kk / NS) & 1);
     }
 }
 
