@@ -148,6 +148,20 @@ def job_throughput(world, steps, t_max):
     return world * steps / t_max
 
 
+def hvp_block_roofline(cfg, t_s):
+    """The K-column block Hessian product against both roofs: the propagator
+    GEMMs of both sweeps (2 N x 2 n^2 K flop) against the TF32 tensor peak
+    (the measured BF16 burst x the nominal TF32/BF16 ratio 1.1/2.25), and the
+    TF32-rounded FP32 propagators read once per sweep plus the block read and
+    written (2 N n^2 x 4 + 2 nA K x 4 bytes) against the measured HBM copy."""
+    hbm, bf16, _, src = _peaks()
+    flops = 2.0 * cfg.N * 2.0 * cfg.n * cfg.n * cfg.K
+    nbytes = 2.0 * cfg.N * cfg.n * cfg.n * 4 + 2.0 * cfg.nA * cfg.K * 4
+    tf32 = bf16 * 1.1 / 2.25
+    return {"tflops": flops / t_s / 1e12, "tf32_peak": tf32, "tensor_frac": flops / t_s / 1e12 / tf32,
+            "gbs": nbytes / t_s / 1e9, "hbm_peak": hbm, "hbm_frac": nbytes / t_s / 1e9 / hbm, "peak_source": src}
+
+
 def workload_config(cfg, method):
     """The workload both arms report (the same dict in both lines)."""
     return {"workload": cfg.name, "n": cfg.n, "N": cfg.N, "nA": cfg.nA, "K": cfg.K, "k": cfg.k, "l": cfg.l,
@@ -264,7 +278,12 @@ def run_reference(args, cfg):
 
 
 # ---------------------------------------------------------------- Lorenz-96 window
-def lorenz96_window(w, inputs, rank, stream, outer_loops=3, maxit=100):
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 lanes x 2 flop per cycle."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def lorenz96_window(w, inputs, rank, stream, outer_loops=3, maxit=100, sm_mhz=2070.0):
     """The nonlinear window (n = 8192, N = 40 subwindows of 8 RK4 steps,
     K = 256): three outer loops, each a mixed inner loop (REVD q = 1, LMP,
     PCG) followed by the outer update (eq. 3), plus the block Hessian
@@ -274,7 +293,7 @@ def lorenz96_window(w, inputs, rank, stream, outer_loops=3, maxit=100):
     and 1e-6 is out of reach of any CG; the relative residual and the
     quadratic-cost decrease reached are reported.  The sweeps are RK4
     tangent-linear / adjoint stencils: FP32 ALU work, reported against the
-    measured FP32 FMA rate."""
+    FP32 FMA peak from the unit counts and the sampled SM clock."""
     import torch
     c3 = inputs.L96.replace(seed=replica_seed(rank))
     tw3 = inputs.twin(c3)
@@ -314,8 +333,30 @@ def lorenz96_window(w, inputs, rank, stream, outer_loops=3, maxit=100):
     S3.close()
     return {"workload": c3.name, "nA": c3.nA, "K": K, "pcg_maxit": maxit, "outer_loops": loops,
             "hvp_block_ms": 1e3 * t_hvp, "hvp_columns_per_s": K / t_hvp,
-            "hvp_alu": {"bound": "alu", "achieved_tflops": flop_col * K / t_hvp / 1e12, "peak_tflops": 65.0,
-                        "peak_source": "measured FP32 FMA rate (register-only FMA loop)"}}
+            "hvp_alu": {"bound": "alu", "achieved_tflops": flop_col * K / t_hvp / 1e12,
+                        "peak_tflops": fp32_peak_tflops(sm_mhz),
+                        "frac": flop_col * K / t_hvp / 1e12 / fp32_peak_tflops(sm_mhz),
+                        "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock of "
+                                       "the timed region)"}}
+
+
+def profile_l96_hvp(inputs, K=256, blocks=2):
+    """A short program for ncu captures of the Lorenz-96 stencil sweeps: the
+    n = 8192 window cut to N = 2 subwindows, two K-column FP32 Hessian blocks."""
+    import torch
+    import paper_2101_07249_gb300 as w
+    w.load()
+    c = inputs.L96.replace(N=2, name="l96_n8192_N2")
+    S = w.Solver(c, inputs.twin(c, spinup=2.0))
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(K, c.nA, dtype=torch.float32, device="cuda", generator=gen)
+    Y = torch.empty_like(X)
+    w.wc4d_launch_count(reset=True)
+    for _ in range(blocks):
+        w.wc4d_hvp(S.ctx, X, Y, K, c.nA, w.MIXED)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": c.name, "K": K, "blocks": blocks, "gpu_launches": w.wc4d_launch_count()}))
+    S.close()
 
 
 # ---------------------------------------------------------------- learned sketch
@@ -446,13 +487,23 @@ def main():
                     help="skip the method comparison, the Lorenz-96 window and the batched windows")
     ap.add_argument("--batch-count", type=int, default=64,
                     help="uneven windows in the batched comparison")
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny"],
-                    help="large: n=4096 N=40 (the benchmark); medium: N=8 (profiling captures); tiny: n=100 N=5")
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny", "l96_hvp"],
+                    help="large: n=4096 N=40 (the benchmark); medium: N=8 (profiling captures); tiny: n=100 N=5; "
+                         "l96_hvp: two K=256 FP32 Hessian blocks on a 2-subwindow Lorenz-96 window "
+                         "(profiling captures of the stencil sweeps, with --profile-run)")
     ap.add_argument("--profile-run", action="store_true",
                     help="only --warmup inner loops and one more, then exit (a short program for ncu captures)")
+    ap.add_argument("--eager", action="store_true",
+                    help="with --profile-run: CG iterations as eager launches, not CUDA graphs (the same kernels; "
+                         "ncu does not list the kernels inside the graphs' conditional loop)")
     args = ap.parse_args()
 
     from paper_2101_07249_gb300 import inputs
+    if args.workload == "l96_hvp":
+        if not args.profile_run:
+            ap.error("--workload l96_hvp is a profiling case: give --profile-run")
+        profile_l96_hvp(inputs)
+        return
     cfg = {"large": inputs.LARGE, "medium": inputs.MEDIUM, "tiny": inputs.TINY}[args.workload]
     if args.impl == "reference":
         run_reference(args, cfg)
@@ -470,6 +521,8 @@ def main():
     S = w.Solver(cfg, tw, M_shared=False)
     ctx = S.ctx
     nA = cfg.nA
+    if args.profile_run and args.eager:
+        w.wc4d_set_graphs(ctx, 0)
     x = torch.zeros(nA, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -584,8 +637,8 @@ def main():
             roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                     "traffic": None, "kernel": "tcgen05 TF32 sweep GEMM", "peak_source": peak_src + " x TF32/BF16"}
         else:
-            sm_mhz = (clk or {}).get("sm_mhz") or 1530.0
-            pk = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+            pk = fp32_peak_tflops(sm_mhz)
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                     "traffic": None, "kernel": "SIMT FP32 sweep GEMM",
                     "peak_source": "152 SM x 128 FP32 lanes x 2 x median SM clock"}
@@ -627,7 +680,7 @@ def main():
             torch.cuda.synchronize()
             methods[mname] = {"inner_loop_ms": e0.elapsed_time(e1), "pcg_iters": it_m, "relres": rr_m,
                               "block_products": {"revd": 1 + cfg.q_power + 1, "nystrom": 2}.get(mname, 1)}
-        l96 = lorenz96_window(w, inputs, rank, stream)
+        l96 = lorenz96_window(w, inputs, rank, stream, sm_mhz=(clk or {}).get("sm_mhz") or 2070.0)
         batched = batched_windows(w, inputs, args.batch_count) if args.batch_count > 0 else None
         learned = learned_windows(w, inputs, stream)
         from paper_2101_07249_gb300 import paper_setups
@@ -657,6 +710,7 @@ def main():
             "pcg_iters": iters, "relres": relres,
             "block_products_per_step": products_block / args.steps,
             "hvp_columns_per_s": K / t_hvp_mixed, "hvp_block_ms": 1e3 * t_hvp_mixed,
+            "hvp_block_roofline": hvp_block_roofline(cfg, t_hvp_mixed),
             "fp64_plain": fp64,
             "speedup_vs_fp64": (fp64["inner_loop_s"] / (t_max / args.steps)) if fp64 else None,
             "kernel_classes": classes,
