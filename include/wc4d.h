@@ -254,7 +254,8 @@ wc4d_status wc4d_stream_destroy(void *stream);
  * its context's stream, driven by one of `workers` host threads (<= 0: 16),
  * so that the instances' kernels overlap on the GPU.  Every context must have
  * its own stream (WC4D_EINVAL otherwise); while in the batch a context uses
- * the per-launch forms of its grid-synchronised kernels.  status[i] receives
+ * the per-launch forms of its grid-synchronised kernels and one CG graph
+ * launch per iteration (not the device-side loop).  status[i] receives
  * each instance's status; the call returns the first non-OK one. */
 wc4d_status wc4d_batch_inner_loop(wc4d_ctx *const *ctxs, int32_t count, int32_t method, const int32_t *k,
                                   const int32_t *l, int32_t q_power, const uint64_t *seeds, double tol,

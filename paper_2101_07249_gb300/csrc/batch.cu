@@ -5,7 +5,11 @@
 // kernels of different instances overlap on the GPU and the small,
 // latency-bound windows fill the SMs together.  Grid-synchronised kernels
 // are replaced by their per-launch forms while a context runs in a batch:
-// a cooperative launch needs every CTA resident at once.
+// a cooperative launch needs every CTA resident at once.  The CG iterations
+// run as one graph launch each (the host reading the flags in between), not
+// as the device-side loop graph: with 64 uneven windows on 16 threads the
+// per-iteration launches interleave better across the streams (GB300: 8.3 s
+// against 10.3 s for the loop graph and 9.1 s eager).
 #include <atomic>
 #include <thread>
 #include <vector>
@@ -40,11 +44,13 @@ extern "C" wc4d_status wc4d_batch_inner_loop(wc4d_ctx *const *ctxs, int32_t coun
         for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
             wc4d_ctx *c = ctxs[i];
             cudaSetDevice(c->device);
-            const bool coop = c->allow_coop;
+            const bool coop = c->allow_coop, loop = c->use_loop_graph;
             c->allow_coop = false;
+            c->use_loop_graph = false;
             status[i] = wc4d_inner_loop(c, method, k[i], l[i], q_power, seeds[i], tol, maxit, precision, x[i],
                                         iters + i, relres + i);
             c->allow_coop = coop;
+            c->use_loop_graph = loop;
         }
     };
     std::vector<std::thread> pool;

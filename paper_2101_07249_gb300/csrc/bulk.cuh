@@ -1,7 +1,6 @@
-// Inline-PTX helpers shared by the kernels that stream through a ring of
+// Inline-PTX helpers of the kernels that stream through a ring of
 // shared-memory slots filled by bulk asynchronous copies (cp.async.bulk,
-// completion counted on mbarriers), and the programmatic-dependent-launch
-// controls.  Every wait is bounded.
+// completion counted on mbarriers).  Every wait is bounded.
 #pragma once
 #include <cstdint>
 
@@ -43,35 +42,3 @@ __device__ __forceinline__ void sw_prefetch_l2(const void *src, unsigned bytes)
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
-// L2 eviction priorities for the bulk copies: evict_first for data read
-// once, evict_normal for data a later kernel will read again
-__device__ __forceinline__ uint64_t l2_policy_evict_first()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_normal()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ void sw_bulk_g2s_hint(uint32_t dst, const void *src, unsigned bytes, uint32_t mb,
-                                                 uint64_t policy)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(dst),
-        "l"(src), "r"(bytes), "r"(mb), "l"(policy)
-        : "memory");
-}
-
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialisation may start once every CTA of the previous kernel has called
-// pdl_trigger (or exited); it must pdl_wait -- which returns when the
-// previous kernel has completed and its writes are visible -- before it
-// touches anything that kernel writes or reads.  Both are no-ops for a
-// kernel launched without the attribute.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
