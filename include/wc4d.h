@@ -320,6 +320,15 @@ wc4d_status wc4d_apply_linvT(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int3
  *     (rows x k, ldz) in Y's precision; Z must not overlap Y; rows < 2^31. */
 wc4d_status wc4d_gram(wc4d_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t rows, int32_t ma,
                       int32_t mb, double *C, int32_t precision);
+/* C = A^T B (m x m, FP64, column-major) for products known to be symmetric
+   -- a Gram matrix (B = A) or Z^T (A Z) -- from the upper 64 x 64 tiles,
+   mirrored (paper Alg. 3 step 4; CholeskyQR Grams of Alg. 3-5).  A and B
+   column-major (rows x m, leading dimensions lda, ldb >= rows), FP64 or --
+   precision WC4D_MIXED -- FP32, on the device.  FP32 blocks take the path
+   wc4d_set_gram_path selects.  Synchronises the context's stream.  EINVAL
+   for bad arguments, ETIMEOUT if a bounded device wait ran out. */
+wc4d_status wc4d_gram_sym(wc4d_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t rows,
+                          int32_t m, double *C, int32_t precision);
 wc4d_status wc4d_chol_inverse(wc4d_ctx *ctx, int32_t m, const double *G, double *Rinv);
 wc4d_status wc4d_tall_times_small(wc4d_ctx *ctx, const void *Y, int64_t ldy, int64_t rows, int32_t m, const double *W,
                                   int32_t k, void *Z, int64_t ldz, int32_t precision);
@@ -413,6 +422,18 @@ wc4d_status wc4d_set_graphs(wc4d_ctx *ctx, int32_t enable);
    truncated) receives the failing CUDA call and its error, else "".
    -1 for a null context. */
 int32_t     wc4d_iteration_mode(const wc4d_ctx *ctx, char *note, int32_t note_len);
+/* Gram-type products of FP32 blocks in the mixed path -- the CholeskyQR
+   Gram Y^T Y (Alg. 3-5, orthonormalisation), the Rayleigh-Ritz matrix
+   Z^T (A Z) (Alg. 3 step 4, Alg. 4 step 4) and the Nystrom products --
+   computed to FP64-class accuracy.  tensor_cores = 1 (default): when the
+   block has a multiple of 128 columns and at least 512 rows, each FP32
+   column is split (scaled by a power of two) into six 7-bit integer slices
+   held exactly in BF16, the 21 slice products that matter are summed
+   exactly by tcgen05 BF16 MMAs in FP32 tensor memory over 512-row chunks,
+   and the chunks are combined in double-float and FP64 (relative accuracy
+   about 2^-41 of the largest entries); 0: the FP32-pipe double-float
+   product (about 2^-44) for every shape.  EINVAL for a null context. */
+wc4d_status wc4d_set_gram_path(wc4d_ctx *ctx, int32_t tensor_cores);
 /* Polls of the grid barriers of the persistent one-column sweeps (the FP64
    sweep, and the FP32 sweep when n is not a multiple of 2048) before a wait
    gives up: the kernel then records the failure and returns, and the call

@@ -98,6 +98,8 @@ _SIGS = {
     "wc4d_lanczos_ritz": (C.c_int32, [_V, C.c_int32, _V]),
     "wc4d_set_graphs": (C.c_int32, [_V, C.c_int32]),
     "wc4d_iteration_mode": (C.c_int32, [_V, C.c_char_p, C.c_int32]),
+    "wc4d_set_gram_path": (C.c_int32, [_V, C.c_int32]),
+    "wc4d_gram_sym": (C.c_int32, [_V, _V, C.c_int64, _V, C.c_int64, C.c_int64, C.c_int32, _V, C.c_int32]),
     "wc4d_stream_create": (C.c_int32, [C.POINTER(C.c_void_p)]),
     "wc4d_stream_destroy": (C.c_int32, [_V]),
     "wc4d_set_reliable_delta": (C.c_int32, [_V, C.c_double]),
@@ -455,6 +457,17 @@ def wc4d_gram(ctx, A, lda, B, ldb, rows, ma, mb, C_out, precision=FP64):
                                  _dev(C_out, torch.float64, ma * mb, "C"), int(precision)))
 
 
+def wc4d_gram_sym(ctx, A, lda, B, ldb, rows, m, C_out, precision=FP64):
+    """C_out = A^T B (m x m FP64) for a product known to be symmetric (B = A,
+    or Z^T A Z): upper 64 x 64 tiles, mirrored.  FP32 blocks (MIXED) take
+    the path wc4d_set_gram_path selects."""
+    import torch
+    dt, rows, m, lda, ldb = _fdtype(precision), int(rows), int(m), int(lda), int(ldb)
+    _check(ctx, load().wc4d_gram_sym(ctx, _dev(A, dt, (m - 1) * lda + rows, "A"), lda,
+                                     _dev(B, dt, (m - 1) * ldb + rows, "B"), ldb, rows, m,
+                                     _dev(C_out, torch.float64, m * m, "C"), int(precision)))
+
+
 def wc4d_chol_inverse(ctx, m, G, Rinv):
     """G = R^T R (m x m FP64 SPD): Rinv = R^{-1} (FP64, m x m)."""
     import torch
@@ -561,6 +574,11 @@ def wc4d_jacobi_fp32_kernel(ctx):
 def wc4d_set_graphs(ctx, enable):
     """enable: True / 1 device-side loop graph, 2 one graph per iteration, False / 0 eager."""
     _check(ctx, load().wc4d_set_graphs(ctx, int(enable)))
+
+
+def wc4d_set_gram_path(ctx, tensor_cores):
+    """True: FP32 Gram products on the tensor cores (sliced, exact chunks) where the shape allows; False: FP32 pipe."""
+    _check(ctx, load().wc4d_set_gram_path(ctx, 1 if tensor_cores else 0))
 
 
 ITER_EAGER, ITER_GRAPH_PER_ITERATION, ITER_DEVICE_LOOP = 0, 1, 2

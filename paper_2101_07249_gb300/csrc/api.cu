@@ -465,7 +465,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->tw64, &c->tw32, &c->twp64, &c->twp32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
-                      &c->tc_part, &c->tc_err, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
+                      &c->tc_part, &c->tc_err, &c->oz_slices, &c->oz_work, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
                       &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf,
                       &c->lz_F, &c->lz_ab, &c->lz_h, &c->jq32};
     for (DevBuf *b : bufs) free_buf(*b);
@@ -542,6 +542,13 @@ extern "C" wc4d_status wc4d_set_wait_limit(wc4d_ctx *c, int64_t polls)
 {
     if (!c || polls > (int64_t)UINT32_MAX) return WC4D_EINVAL;
     c->wait_limit = polls < 0 ? (1u << 22) : (unsigned)polls;
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_set_gram_path(wc4d_ctx *c, int32_t tensor_cores)
+{
+    if (!c) return WC4D_EINVAL;
+    c->gram_tc = tensor_cores != 0;
     return WC4D_OK;
 }
 
@@ -762,6 +769,48 @@ template <> struct Ops<float> {
 // shape is not supported so the SIMT path is taken.
 bool tc_sweep_supported(const wc4d_ctx *c, int K);
 int tc_read_error(wc4d_ctx *c);
+bool oz_gram_supported(const wc4d_ctx *c, int64_t rows, int m);
+size_t oz_gram_part_doubles(const wc4d_ctx *c, int64_t rows, int m);
+int64_t oz_rows_pad(int64_t rows);
+bool launch_oz_gram(wc4d_ctx *c, int64_t rows, int m, const float *A, int64_t lda, const float *B, int64_t ldb,
+                    uint16_t *slices, int *work, double *part, size_t part_cap, double *C, int *err);
+
+// Symmetric Gram-type product G = A^T B (m x m, FP64; upper tiles computed
+// and mirrored): FP32 blocks go to the tensor-core sliced product when the
+// shape allows it (m a multiple of 128, at least 512 rows) and the context
+// has not switched it off, otherwise (and for FP64 blocks) to the FP32- or
+// FP64-pipe kernels.  Returns 0, or -1 when the partial buffer is too small.
+template <typename T>
+static int gram_sym(wc4d_ctx *c, int64_t rows, int m, const T *A, int64_t lda, const T *B, int64_t ldb, double *G,
+                    int *S)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (c->gram_tc && oz_gram_supported(c, rows, m)) {
+            const size_t per = (size_t)6 * m * (size_t)oz_rows_pad(rows);
+            const size_t sl = per * ((A == B && lda == ldb) ? 1 : 2);
+            if (ensure(c, c->oz_slices, sizeof(uint16_t) * sl) == WC4D_OK &&
+                ensure(c, c->oz_work, sizeof(int) * 4 * (size_t)m) == WC4D_OK &&
+                ensure(c, c->part, sizeof(double) * oz_gram_part_doubles(c, rows, m)) == WC4D_OK &&
+                ensure(c, c->tc_err, sizeof(int)) == WC4D_OK) {
+                bool zero_ok = true;
+                if (!c->tc_err_zeroed) {
+                    zero_ok = cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream) == cudaSuccess;
+                    c->tc_err_zeroed = zero_ok;
+                }
+                if (zero_ok &&
+                    launch_oz_gram(c, rows, m, A, lda, B, ldb, P<uint16_t>(c->oz_slices), P<int>(c->oz_work),
+                                   P<double>(c->part), c->part.bytes / 8, G, P<int>(c->tc_err))) {
+                    if (S) *S = 1;
+                    c->gram_tc_used = true;
+                    return 0;
+                }
+                cudaGetLastError();
+            }
+        }
+    }
+    return launch_atb<T>(c->stream, c->num_sms, rows, m, m, A, lda, B, ldb, P<double>(c->part), c->part.bytes / 8, S,
+                         G, 1);
+}
 bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld);
 bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld);
 
@@ -1155,8 +1204,7 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     }
     {
         ProfScope ps(c, PROF_GRAM);
-        if (launch_atb<T>(c->stream, c->num_sms, rows, m, m, Y, ld, Y, ld, P<double>(c->part), c->part.bytes / 8,
-                          &S, G, 1) != 0)   // G = Y^T Y
+        if (gram_sym<T>(c, rows, m, Y, ld, Y, ld, G, &S) != 0)   // G = Y^T Y
             return set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small");
     }
     double *Rinv = P<double>(c->small1);
@@ -1169,8 +1217,13 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
         WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     }
     WC4D_TRY(sync(c, "cholqr info"));
-    // Numerically rank-deficient Y (the Gram is accurate to FP64 rounding,
-    // so this happens when its condition exceeds ~1e16, e.g. sketches of a
+    if (c->gram_tc_used) {
+        c->gram_tc_used = false;
+        if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
+    }
+    // Numerically rank-deficient Y (the Gram is accurate to FP64 rounding --
+    // to ~1e-12 relative on the tensor-core path -- so this happens when its
+    // condition exceeds ~1e16 (~1e12), e.g. sketches of a
     // Hessian whose eigenvalues span 1e17): shifted CholeskyQR -- factor
     // G + s I with s = f trace(G), f from m 2^-52 up by factors of 100.  Y
     // R^{-1} is then well conditioned but not orthonormal; the caller runs
@@ -1445,6 +1498,32 @@ extern "C" wc4d_status wc4d_gram(wc4d_ctx *c, const void *A, int64_t lda, const 
     return check_launch(c, "gram");
 }
 
+extern "C" wc4d_status wc4d_gram_sym(wc4d_ctx *c, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t rows,
+                                     int32_t m, double *C, int32_t precision)
+{
+    if (!c || !A || !B || !C || rows < 1 || m < 1 || lda < rows || ldb < rows) return WC4D_EINVAL;
+    if (precision != WC4D_FP64 && precision != WC4D_MIXED) return WC4D_EINVAL;
+    WC4D_TRY(ensure(c, c->part, sizeof(double) * atb_part_doubles(c->num_sms, rows, m, m, 1)));
+    int S = 0, r;
+    {
+        ProfScope ps(c, PROF_GRAM);
+        if (precision == WC4D_FP64)
+            r = gram_sym<double>(c, rows, m, static_cast<const double *>(A), lda, static_cast<const double *>(B), ldb,
+                                 C, &S);
+        else
+            r = gram_sym<float>(c, rows, m, static_cast<const float *>(A), lda, static_cast<const float *>(B), ldb, C,
+                                &S);
+    }
+    if (r != 0) return set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small");
+    WC4D_TRY(check_launch(c, "gram_sym"));
+    WC4D_TRY(sync(c, "gram_sym"));
+    if (c->gram_tc_used) {
+        c->gram_tc_used = false;
+        if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
+    }
+    return WC4D_OK;
+}
+
 extern "C" wc4d_status wc4d_chol_inverse(wc4d_ctx *c, int32_t m, const double *G, double *Rinv)
 {
     if (!c || !G || !Rinv || m < 1) return WC4D_EINVAL;
@@ -1559,8 +1638,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         {
             // Z^T A Z is symmetric: upper tiles only, mirrored
             ProfScope psg(c, PROF_GRAM);
-            if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, Z, nA, E, nA, P<double>(c->part), c->part.bytes / 8,
-                              &S, Kmat, 1) != 0)
+            if (gram_sym<T>(c, nA, m, Z, nA, E, nA, Kmat, &S) != 0)
                 return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
         }
         launch_symmetrize(c->stream, m, Kmat);
@@ -1598,8 +1676,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
                 launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, Ci32);
                 launch_gemm<float>(c->stream, (int)nA, m, m, E, 1, nA, Ci32, m, F, nA, e);
             }
-            if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, F, nA, F, nA, P<double>(c->part), c->part.bytes / 8,
-                              &S, Kmat, 1) != 0)   // F^T F
+            if (gram_sym<T>(c, nA, m, F, nA, F, nA, Kmat, &S) != 0)   // F^T F
                 return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
             launch_symmetrize(c->stream, m, Kmat);
             if ((st = check_launch(c, "nystrom F")) != WC4D_OK) return fail(st);
@@ -1648,8 +1725,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         int S = 0;
         {
             ProfScope psg(c, PROF_GRAM);
-            if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, Om, nA, Yb, nA, P<double>(c->part), c->part.bytes / 8,
-                              &S, Kmat, 1) != 0)   // Omega^T Y_nu, symmetric up to rounding: upper tiles
+            if (gram_sym<T>(c, nA, m, Om, nA, Yb, nA, Kmat, &S) != 0)   // Omega^T Y_nu, symmetric up to rounding: upper tiles
                 return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
         }
         launch_symmetrize(c->stream, m, Kmat);
@@ -1671,8 +1747,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
             launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, Ci32);
             launch_gemm<float>(c->stream, (int)nA, m, m, Yb, 1, nA, Ci32, m, E, nA, e);
         }
-        if (launch_atb<T>(c->stream, c->num_sms, nA, m, m, E, nA, E, nA, P<double>(c->part), c->part.bytes / 8, &S,
-                          Kmat, 1) != 0)   // E^T E
+        if (gram_sym<T>(c, nA, m, E, nA, E, nA, Kmat, &S) != 0)   // E^T E
             return fail(set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small"));
         launch_symmetrize(c->stream, m, Kmat);
         if ((st = check_launch(c, "nystrom1 E")) != WC4D_OK) return fail(st);
@@ -1731,7 +1806,12 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     c->kU = k;
     c->theta_host.assign(k, 0.0);
     cudaMemcpyAsync(c->theta_host.data(), c->theta64.p, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream);
-    return sync(c, "sketch");
+    WC4D_TRY(sync(c, "sketch"));
+    if (c->gram_tc_used) {
+        c->gram_tc_used = false;
+        if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
+    }
+    return WC4D_OK;
 }
 
 // Row-major, zero-padded copies of the Ritz vectors for the LMP kernels.

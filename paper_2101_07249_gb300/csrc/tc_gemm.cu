@@ -51,6 +51,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive_one(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Bounded parity wait; returns false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
@@ -514,4 +519,378 @@ int tc_read_error(wc4d_ctx *c)
     cudaStreamSynchronize(c->stream);
     if (h) cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream);
     return h;
+}
+
+// ============================================================================
+// FP64-accurate Gram matrices of FP32 blocks on the tensor cores:
+// C = A^T B for tall column-major A, B (rows x m, m a multiple of 128), as
+// used by CholeskyQR (B = A) and the Rayleigh-Ritz matrix Z^T (A Z), exact
+// up to a relative 2^-41 truncation of the inputs.
+//
+// Splitting (after Ozaki's error-free splitting of matrix products): column
+// j of an operand, scaled by 2^-e_j with max |x| < 2^e_j, is written as
+//     x 2^-e_j = sum_{a=1..6} d_a 2^-(6 + 7 (a - 1)),   d_a integers, |d_a| <= 64,
+// each d_a exactly a BF16 value (k_oz_slice).  A product of two slices is an
+// integer of at most 2^12, so the tensor cores sum slice products of one
+// "level" L = a + b (at most 6 pairs) over 512 rows exactly in FP32 (below
+// 2^24).  The 21 pairs with a + b <= 7 go to six accumulators in tensor
+// memory, one per level; after every 512 rows the epilogue warps fold the
+// level sums, scaled by 2^-(12 + 7 (L - 2)), into double-float register
+// accumulators (TwoSum), and at the end write 2^(e_i + e_j) (hi + lo) as a
+// split-K partial; k_oz_reduce sums the partials in fixed order.  Pairs
+// with a + b > 7 are dropped: with the 41-bit truncation of the slices they
+// bound the error at about 2^-41 of max|x_i| max|y_j| per term.
+//
+// One CTA: a 128 x 64 tile of C (upper tiles only: the result is mirrored,
+// as the FP32-pipe Gram does) over one range of rows.  Warp 4 lane 0 is the
+// TMA producer (per 64-row block and slice a: A slice a, 128 x 64 BF16, and
+// B slices 1 .. 7 - a, 64 x 64 each, into one of three 64 KB slots), warp 9
+// lane 0 the MMA issuer (kind::f16, M = 128, N = 64, K = 16), warps 0-7 the
+// epilogue (warp w: tensor-memory lanes 32 (w mod 4) .., columns 32 (w / 4)
+// ..).  All waits are bounded.
+// ============================================================================
+namespace {
+
+constexpr int OZ_SLICES = 6;
+constexpr int OZ_LEVELS = OZ_SLICES;          // levels L = 2 .. 7
+constexpr int OZ_KB = 64;                     // rows per block (128 bytes of BF16: one swizzle row)
+constexpr int OZ_CHUNK_KB = 8;                // blocks per exact chunk (512 rows)
+constexpr int OZ_N = 64;                      // columns of C per tile
+constexpr int OZ_SLOT = 64 * 1024;            // A slice (16 KB) + up to six B slices (8 KB each)
+constexpr int OZ_NSLOT = 3;
+constexpr int OZ_A_BYTES = BM * OZ_KB * 2;    // 16 KB
+constexpr int OZ_B_BYTES = OZ_N * OZ_KB * 2;  // 8 KB
+constexpr int OZ_SMEM = 1024 + OZ_NSLOT * OZ_SLOT + 256;
+
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N.
+__device__ __forceinline__ uint32_t idesc_bf16(int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// colmax[j] = bits of max_r |X(r, j)| (non-negative floats order as
+// unsigned integers); colmax zeroed beforehand.  Grid (m, splits).
+__global__ void k_oz_colmax(int64_t rows, int64_t rows_per, const float *__restrict__ X, int64_t ld, unsigned *colmax)
+{
+    const int j = blockIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per, r1 = min(rows, r0 + rows_per);
+    float mx = 0.f;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) mx = fmaxf(mx, fabsf(X[(int64_t)j * ld + r]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(colmax + j, __float_as_uint(mx));
+}
+
+// Exponent e with max < 2^e (0 for an all-zero column or a non-finite max:
+// a NaN or Inf then reaches the slices and the Gram as it is).
+__device__ __forceinline__ int oz_exponent(unsigned bits)
+{
+    const float mx = __uint_as_float(bits);
+    if (!(mx > 0.f) || !isfinite(mx)) return 0;
+    int e;
+    frexpf(mx, &e);   // mx = f 2^e, 0.5 <= f < 1
+    return e;
+}
+
+// S[a][j][r] (BF16 bits, rows padded with zeros to rows_pad) and exps[j].
+__global__ void k_oz_slice(int64_t rows, int64_t rows_pad, int m, const float *__restrict__ X, int64_t ld,
+                           const unsigned *__restrict__ colmax, uint16_t *S, int *exps)
+{
+    const int j = blockIdx.y;
+    const int e = oz_exponent(colmax[j]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) exps[j] = e;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows_pad; r += (int64_t)gridDim.x * blockDim.x) {
+        const float x = r < rows ? X[(int64_t)j * ld + r] : 0.f;
+        float v = ldexpf(x, 6 - e);   // |v| < 64: exact scaling by a power of two
+#pragma unroll
+        for (int a = 0; a < OZ_SLICES; ++a) {
+            const float d = rintf(v);                     // |d| <= 64: an exact BF16 value
+            S[((int64_t)a * m + j) * rows_pad + r] = (uint16_t)(__float_as_uint(d) >> 16);
+            v = (v - d) * 128.f;                          // exact: |v - d| <= 1/2
+        }
+    }
+}
+
+struct OzArgs {
+    int m;
+    int nkb;            // 64-row blocks per split
+    int tiles_i;        // 128-row tiles of C
+    const int *ea, *eb; // column exponents of A and B
+    double *part;       // [split][j m + i]
+    int *err;
+};
+
+// upper tile t -> (i0, j0): row tile ib, column tiles jb >= 2 ib
+__device__ __forceinline__ void oz_tile(int t, int m, int &i0, int &j0)
+{
+    const int nj = m / OZ_N;
+    int ib = 0;
+    while (t >= nj - 2 * ib) { t -= nj - 2 * ib; ++ib; }
+    i0 = ib * BM;
+    j0 = (2 * ib + t) * OZ_N;
+}
+
+constexpr int OZ_THREADS = 320;   // 8 epilogue warps, producer, issuer
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+k_oz_gram(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + OZ_NSLOT * OZ_SLOT);
+    uint64_t *empty = full + OZ_NSLOT;
+    uint64_t *chunk_done = empty + OZ_NSLOT;
+    uint64_t *tmem_free = chunk_done + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_free + 1);
+    __shared__ int failed;
+    __shared__ int n_issued, n_consumed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int i0, j0;
+    oz_tile(blockIdx.x, a.m, i0, j0);
+    const int xbeg = blockIdx.y * a.nkb * OZ_KB;   // first row of this split
+    const int nstages = a.nkb * OZ_SLICES;
+    const int nchunks = (a.nkb + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+    const uint32_t ncols = 512;   // six 64-column level accumulators
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        n_issued = 0;
+        n_consumed = 0;
+        for (int s = 0; s < OZ_NSLOT; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(chunk_done, 1);
+        mbar_init(tmem_free, 8);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 8) {
+        if (lane == 0) {   // producer: stage st = (block kb, A slice sa)
+            for (int st = 0; st < nstages; ++st) {
+                const int kb = st / OZ_SLICES, sa = st % OZ_SLICES, s = st % OZ_NSLOT, round = st / OZ_NSLOT;
+                if (st >= OZ_NSLOT && !mbar_wait(&empty[s], (round - 1) & 1)) { failed = 1; break; }
+                const int nb = OZ_SLICES - sa;   // B slices 0 .. 5 - sa pair with A slice sa
+                unsigned char *slot = base + s * OZ_SLOT;
+                mbar_expect_tx(&full[s], OZ_A_BYTES + nb * OZ_B_BYTES);
+                const int x = xbeg + kb * OZ_KB;
+                tma_load_2d(slot, &tmA, x, sa * a.m + i0, &full[s]);
+                for (int sb = 0; sb < nb; ++sb)
+                    tma_load_2d(slot + OZ_A_BYTES + sb * OZ_B_BYTES, &tmB, x, sb * a.m + j0, &full[s]);
+                n_issued = st + 1;
+            }
+        }
+    } else if (warp == 9) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = idesc_bf16(OZ_N);
+            unsigned started = 0;   // bit L: level L has had its first MMA of the chunk
+            for (int st = 0; st < nstages && !failed; ++st) {
+                const int kb = st / OZ_SLICES, sa = st % OZ_SLICES, s = st % OZ_NSLOT, round = st / OZ_NSLOT;
+                const int chunk = kb / OZ_CHUNK_KB;
+                if (sa == 0 && kb % OZ_CHUNK_KB == 0) {   // a new exact chunk: accumulators free again
+                    if (chunk > 0 && !mbar_wait(tmem_free, (chunk - 1) & 1)) { failed = 1; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    started = 0;
+                }
+                if (!mbar_wait(&full[s], round & 1)) { failed = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a_addr = smem_u32(base + s * OZ_SLOT);
+                const int nb = OZ_SLICES - sa;
+                for (int sb = 0; sb < nb; ++sb) {
+                    const int L = sa + sb;   // level index 0 .. 5 (a + b - 2)
+                    const uint32_t b_addr = a_addr + OZ_A_BYTES + sb * OZ_B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < OZ_KB / 16; ++kk) {
+                        mma_bf16(tmem + (uint32_t)(L * OZ_N), smem_desc_sw128(a_addr + kk * 32),
+                                 smem_desc_sw128(b_addr + kk * 32), idesc, (started >> L) & 1u);
+                        started |= 1u << L;
+                    }
+                }
+                mma_commit(&empty[s]);
+                n_consumed = st + 1;
+                if (sa == OZ_SLICES - 1 && (kb % OZ_CHUNK_KB == OZ_CHUNK_KB - 1 || kb == a.nkb - 1))
+                    mma_commit(chunk_done);
+            }
+        }
+    } else {
+        // epilogue: warp w reads tensor-memory lanes 32 (w mod 4) .. + 31 (row
+        // i0 + 32 (w mod 4) + lane of C) and columns 32 (w / 4) .. + 31 of every level
+        const int quad = warp & 3, half = warp >> 2;
+        float hi[32], lo[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            ok = __all_sync(0xffffffffu, mbar_wait(chunk_done, c & 1) ? 1 : 0) != 0;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int L = 0; L < OZ_LEVELS; ++L) {
+                const float scale = __uint_as_float((uint32_t)(127 - 12 - 7 * L) << 23);   // 2^-(12 + 7 L)
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N + 32 * half);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const float v = __fmul_rn(__uint_as_float(r[q]), scale);   // exact: a power of two
+                    const float s = __fadd_rn(hi[q], v), bp = __fsub_rn(s, hi[q]);
+                    lo[q] = __fadd_rn(lo[q], __fadd_rn(__fsub_rn(hi[q], __fsub_rn(s, bp)), __fsub_rn(v, bp)));
+                    hi[q] = s;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive_one(tmem_free);
+        }
+        if (ok && !failed) {
+            const int i = i0 + quad * 32 + lane;
+            const int ei = a.ea[i];
+            double *dst = a.part + (size_t)blockIdx.y * a.m * a.m;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int j = j0 + 32 * half + q;
+                dst[(size_t)j * a.m + i] = ldexp((double)hi[q] + (double)lo[q], ei + a.eb[j]);
+            }
+        } else if (warp == 0 && lane == 0) {
+            atomicExch(a.err, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (failed && threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        // the MMAs of the last consumed stage complete before the tensor
+        // memory is freed; the copies issued but never consumed land before
+        // the CTA exits (both bounded)
+        if (n_consumed > 0) mbar_wait(&empty[(n_consumed - 1) % OZ_NSLOT], ((n_consumed - 1) / OZ_NSLOT) & 1);
+        for (int st = n_consumed; st < n_issued; ++st) mbar_wait(&full[st % OZ_NSLOT], (st / OZ_NSLOT) & 1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// C = sum_s part[s] (fixed order); entries below the diagonal 64-tiles take
+// the mirrored sum (those tiles were not computed).
+__global__ void k_oz_reduce(int S, int m, const double *part, double *C)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int i = (int)(e % m), j = (int)(e / m);
+    const int64_t src = (i / OZ_N > j / OZ_N) ? (int64_t)i * m + j : e;
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) acc += part[(int64_t)s * m * m + src];
+    C[e] = acc;
+}
+
+// 2D BF16 tensor map: inner dimension `inner` (contiguous), `outer` rows
+// `stride_elems` apart; box 64 x box_rows, 128-byte swizzle.
+bool make_map_bf16(CUtensorMap *map, const void *ptr, uint64_t inner, uint64_t outer, uint64_t stride_elems,
+                   uint32_t box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {stride_elems * 2};
+    cuuint32_t box[2] = {(cuuint32_t)OZ_KB, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int oz_tiles(int m) { const int nj = m / OZ_N, ni = m / BM; return ni * nj - ni * (ni - 1); }
+
+}  // namespace
+
+int64_t oz_rows_pad(int64_t rows) { return (rows + OZ_KB - 1) / OZ_KB * OZ_KB; }
+
+bool oz_gram_supported(const wc4d_ctx *c, int64_t rows, int m)
+{
+    if (m < BM || m % BM != 0 || rows < 512 || rows > INT32_MAX - OZ_KB) return false;
+    if (!device_ok(c)) return false;
+    static const bool attr =
+        cudaFuncSetAttribute(k_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM) == cudaSuccess;
+    if (!attr) cudaGetLastError();
+    return attr;
+}
+
+size_t oz_gram_part_doubles(const wc4d_ctx *c, int64_t rows, int m)
+{
+    const int tiles = oz_tiles(m);
+    const int64_t kbs = oz_rows_pad(rows) / OZ_KB;
+    const int64_t S = std::max<int64_t>(1, std::min<int64_t>(kbs, c->num_sms / std::max(1, tiles)));
+    return (size_t)S * m * m;
+}
+
+// C (m x m, FP64) = A^T B, mirrored from the upper tiles.  slices: BF16
+// workspace of 6 m oz_rows_pad(rows) entries per distinct operand (two when
+// A != B); work: 4 m ints.  Returns false (nothing launched) if a tensor map
+// cannot be made or part_cap is too small.
+bool launch_oz_gram(wc4d_ctx *c, int64_t rows, int m, const float *A, int64_t lda, const float *B, int64_t ldb,
+                    uint16_t *slices, int *work, double *part, size_t part_cap, double *C, int *err)
+{
+    const int64_t rp = oz_rows_pad(rows);
+    const int tiles = oz_tiles(m);
+    const int64_t kbs = rp / OZ_KB;
+    int64_t S = std::max<int64_t>(1, std::min<int64_t>(kbs, c->num_sms / std::max(1, tiles)));
+    const int nkb = (int)((kbs + S - 1) / S);
+    S = (kbs + nkb - 1) / nkb;
+    if ((size_t)S * m * m > part_cap) return false;
+    const bool same = (A == B && lda == ldb);
+    uint16_t *SA = slices, *SB = same ? slices : slices + (size_t)OZ_SLICES * m * rp;
+    unsigned *cmA = reinterpret_cast<unsigned *>(work), *cmB = cmA + m;
+    int *eA = work + 2 * m, *eB = same ? eA : eA + m;
+    CUtensorMap mA, mB;
+    if (!make_map_bf16(&mA, SA, (uint64_t)rp, (uint64_t)OZ_SLICES * m, (uint64_t)rp, BM)) return false;
+    if (!make_map_bf16(&mB, SB, (uint64_t)rp, (uint64_t)OZ_SLICES * m, (uint64_t)rp, OZ_N)) return false;
+    const int64_t rows_per = 16384;
+    const dim3 cg((unsigned)m, (unsigned)((rows + rows_per - 1) / rows_per));
+    const dim3 sg((unsigned)std::min<int64_t>(64, (rp + 255) / 256), (unsigned)m);
+    if (cudaMemsetAsync(cmA, 0, sizeof(unsigned) * 2 * m, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    WC4D_LAUNCH(k_oz_colmax<<<cg, 256, 0, c->stream>>>(rows, rows_per, A, lda, cmA));
+    WC4D_LAUNCH(k_oz_slice<<<sg, 256, 0, c->stream>>>(rows, rp, m, A, lda, cmA, SA, eA));
+    if (!same) {
+        WC4D_LAUNCH(k_oz_colmax<<<cg, 256, 0, c->stream>>>(rows, rows_per, B, ldb, cmB));
+        WC4D_LAUNCH(k_oz_slice<<<sg, 256, 0, c->stream>>>(rows, rp, m, B, ldb, cmB, SB, eB));
+    }
+    OzArgs args{m, nkb, m / BM, eA, eB, part, err};
+    WC4D_LAUNCH(k_oz_gram<<<dim3((unsigned)tiles, (unsigned)S), OZ_THREADS, OZ_SMEM, c->stream>>>(mA, mB, args));
+    const int64_t cnt = (int64_t)m * m;
+    WC4D_LAUNCH(k_oz_reduce<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>((int)S, m, part, C));
+    return cudaPeekAtLastError() == cudaSuccess;
 }

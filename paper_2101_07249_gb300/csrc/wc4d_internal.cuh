@@ -113,6 +113,9 @@ struct wc4d_ctx {
     // tensor-core sweeps: split partials and the error flag of bounded waits
     DevBuf tc_part, tc_err;
     bool tc_err_zeroed = false;
+    bool gram_tc = true;        // FP32 Gram products on the tensor cores when the shape allows (wc4d_set_gram_path)
+    bool gram_tc_used = false;  // ... and one ran since the error flag was last read
+    DevBuf oz_slices, oz_work;  // BF16 slices of the Gram operands; column maxima and exponents
     // tensor-core operands rounded to TF32 (nearest): the propagators, and
     // the probe block as the sweep produces it (nA x K, ld nA)
     DevBuf Mtf, MTtf, tc_round;
