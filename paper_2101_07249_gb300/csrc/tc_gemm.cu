@@ -542,9 +542,10 @@ int tc_read_error(wc4d_ctx *c)
 // bound the error at about 2^-41 of max|x_i| max|y_j| per term.
 //
 // One CTA: a 128 x 64 tile of C (upper tiles only: the result is mirrored,
-// as the FP32-pipe Gram does) over one range of rows.  Warp 4 lane 0 is the
-// TMA producer (per 64-row block and slice a: A slice a, 128 x 64 BF16, and
-// B slices 1 .. 7 - a, 64 x 64 each, into one of three 64 KB slots), warp 9
+// as the FP32-pipe Gram does) over one range of rows.  Warp 8 lane 0 is the
+// TMA producer (per 64-row block: the six B slices, 64 x 64 BF16 each, into
+// one of two 48 KB buffers, then the six A slices, 128 x 64 each, through a
+// six-slot ring, so every tile is read once per block), warp 9
 // lane 0 the MMA issuer (kind::f16, M = 128, N = 64, K = 16), warps 0-7 the
 // epilogue (warp w: tensor-memory lanes 32 (w mod 4) .., columns 32 (w / 4)
 // ..).  All waits are bounded.
@@ -556,11 +557,12 @@ constexpr int OZ_LEVELS = OZ_SLICES;          // levels L = 2 .. 7
 constexpr int OZ_KB = 64;                     // rows per block (128 bytes of BF16: one swizzle row)
 constexpr int OZ_CHUNK_KB = 8;                // blocks per exact chunk (512 rows)
 constexpr int OZ_N = 64;                      // columns of C per tile
-constexpr int OZ_SLOT = 64 * 1024;            // A slice (16 KB) + up to six B slices (8 KB each)
-constexpr int OZ_NSLOT = 3;
-constexpr int OZ_A_BYTES = BM * OZ_KB * 2;    // 16 KB
-constexpr int OZ_B_BYTES = OZ_N * OZ_KB * 2;  // 8 KB
-constexpr int OZ_SMEM = 1024 + OZ_NSLOT * OZ_SLOT + 256;
+constexpr int OZ_A_BYTES = BM * OZ_KB * 2;    // 16 KB: one A slice of a 64-row block
+constexpr int OZ_B_BYTES = OZ_N * OZ_KB * 2;  // 8 KB: one B slice
+constexpr int OZ_NA = 6;                      // A ring slots (one block's slices)
+constexpr int OZ_NBB = 2;                     // B buffers (all six slices of a block each)
+constexpr int OZ_BBUF = OZ_SLICES * OZ_B_BYTES;   // 48 KB
+constexpr int OZ_SMEM = 1024 + OZ_NA * OZ_A_BYTES + OZ_NBB * OZ_BBUF + 256;
 
 // Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N.
 __device__ __forceinline__ uint32_t idesc_bf16(int N)
@@ -580,13 +582,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 }
 
 // colmax[j] = bits of max_r |X(r, j)| (non-negative floats order as
-// unsigned integers); colmax zeroed beforehand.  Grid (m, splits).
-__global__ void k_oz_colmax(int64_t rows, int64_t rows_per, const float *__restrict__ X, int64_t ld, unsigned *colmax)
+// unsigned integers); colmax zeroed beforehand.  Grid (m, splits); vec4:
+// rows read as float4 (X 16-byte aligned, ld a multiple of 4).
+__global__ void k_oz_colmax(int64_t rows, int64_t rows_per, const float *__restrict__ X, int64_t ld, unsigned *colmax,
+                            int vec4)
 {
     const int j = blockIdx.x;
     const int64_t r0 = (int64_t)blockIdx.y * rows_per, r1 = min(rows, r0 + rows_per);
+    const float *col = X + (int64_t)j * ld;
     float mx = 0.f;
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) mx = fmaxf(mx, fabsf(X[(int64_t)j * ld + r]));
+    if (vec4) {   // rows_per is a multiple of 4
+        const int64_t q1 = r1 / 4;
+        for (int64_t q = r0 / 4 + threadIdx.x; q < q1; q += blockDim.x) {
+            const float4 v = __ldcs(reinterpret_cast<const float4 *>(col) + q);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        for (int64_t r = q1 * 4 + threadIdx.x; r < r1; r += blockDim.x) mx = fmaxf(mx, fabsf(col[r]));
+    } else {
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) mx = fmaxf(mx, fabsf(col[r]));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(colmax + j, __float_as_uint(mx));
@@ -603,21 +617,47 @@ __device__ __forceinline__ int oz_exponent(unsigned bits)
     return e;
 }
 
-// S[a][j][r] (BF16 bits, rows padded with zeros to rows_pad) and exps[j].
+// The six slices of one value, as BF16 bits: x 2^(6-e) = sum_a d_a 2^(-7a).
+__device__ __forceinline__ void oz_split(float x, int e, uint32_t (&d)[OZ_SLICES])
+{
+    float v = ldexpf(x, 6 - e);   // |v| < 64: exact scaling by a power of two
+#pragma unroll
+    for (int a = 0; a < OZ_SLICES; ++a) {
+        const float q = rintf(v);                 // |q| <= 64: an exact BF16 value
+        d[a] = __float_as_uint(q) >> 16;
+        v = (v - q) * 128.f;                      // exact: |v - q| <= 1/2
+    }
+}
+
+// S[a][j][r] (BF16 bits, rows padded with zeros to rows_pad, a multiple of
+// 4) and exps[j]; four rows per thread, one 8-byte store per slice.
 __global__ void k_oz_slice(int64_t rows, int64_t rows_pad, int m, const float *__restrict__ X, int64_t ld,
-                           const unsigned *__restrict__ colmax, uint16_t *S, int *exps)
+                           const unsigned *__restrict__ colmax, uint16_t *S, int *exps, int vec4)
 {
     const int j = blockIdx.y;
     const int e = oz_exponent(colmax[j]);
     if (blockIdx.x == 0 && threadIdx.x == 0) exps[j] = e;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows_pad; r += (int64_t)gridDim.x * blockDim.x) {
-        const float x = r < rows ? X[(int64_t)j * ld + r] : 0.f;
-        float v = ldexpf(x, 6 - e);   // |v| < 64: exact scaling by a power of two
+    const float *col = X + (int64_t)j * ld;
+    const int64_t nq = rows_pad / 4;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = 4 * q;
+        float x[4];
+        if (vec4 && r + 3 < rows) {
+            const float4 v = __ldcs(reinterpret_cast<const float4 *>(col) + q);
+            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[t] = (r + t < rows) ? col[r + t] : 0.f;
+        }
+        uint32_t d[4][OZ_SLICES];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) oz_split(x[t], e, d[t]);
 #pragma unroll
         for (int a = 0; a < OZ_SLICES; ++a) {
-            const float d = rintf(v);                     // |d| <= 64: an exact BF16 value
-            S[((int64_t)a * m + j) * rows_pad + r] = (uint16_t)(__float_as_uint(d) >> 16);
-            v = (v - d) * 128.f;                          // exact: |v - d| <= 1/2
+            uint2 w;
+            w.x = d[0][a] | (d[1][a] << 16);
+            w.y = d[2][a] | (d[3][a] << 16);
+            *reinterpret_cast<uint2 *>(S + ((int64_t)a * m + j) * rows_pad + r) = w;
         }
     }
 }
@@ -649,27 +689,30 @@ k_oz_gram(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + OZ_NSLOT * OZ_SLOT);
-    uint64_t *empty = full + OZ_NSLOT;
-    uint64_t *chunk_done = empty + OZ_NSLOT;
+    unsigned char *sA = base;                              // [OZ_NA][16 KB]
+    unsigned char *sB = base + OZ_NA * OZ_A_BYTES;         // [OZ_NBB][6][8 KB]
+    uint64_t *afull = reinterpret_cast<uint64_t *>(sB + OZ_NBB * OZ_BBUF);
+    uint64_t *aempty = afull + OZ_NA;
+    uint64_t *bfull = aempty + OZ_NA;
+    uint64_t *bempty = bfull + OZ_NBB;
+    uint64_t *chunk_done = bempty + OZ_NBB;
     uint64_t *tmem_free = chunk_done + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tmem_free + 1);
     __shared__ int failed;
-    __shared__ int n_issued, n_consumed;
+    __shared__ int a_issued, a_consumed, b_issued, b_consumed;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int i0, j0;
     oz_tile(blockIdx.x, a.m, i0, j0);
     const int xbeg = blockIdx.y * a.nkb * OZ_KB;   // first row of this split
-    const int nstages = a.nkb * OZ_SLICES;
     const int nchunks = (a.nkb + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
     const uint32_t ncols = 512;   // six 64-column level accumulators
 
     if (threadIdx.x == 0) {
         failed = 0;
-        n_issued = 0;
-        n_consumed = 0;
-        for (int s = 0; s < OZ_NSLOT; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        a_issued = a_consumed = b_issued = b_consumed = 0;
+        for (int s = 0; s < OZ_NA; ++s) { mbar_init(&afull[s], 1); mbar_init(&aempty[s], 1); }
+        for (int s = 0; s < OZ_NBB; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
         mbar_init(chunk_done, 1);
         mbar_init(tmem_free, 8);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -685,50 +728,60 @@ k_oz_gram(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 8) {
-        if (lane == 0) {   // producer: stage st = (block kb, A slice sa)
-            for (int st = 0; st < nstages; ++st) {
-                const int kb = st / OZ_SLICES, sa = st % OZ_SLICES, s = st % OZ_NSLOT, round = st / OZ_NSLOT;
-                if (st >= OZ_NSLOT && !mbar_wait(&empty[s], (round - 1) & 1)) { failed = 1; break; }
-                const int nb = OZ_SLICES - sa;   // B slices 0 .. 5 - sa pair with A slice sa
-                unsigned char *slot = base + s * OZ_SLOT;
-                mbar_expect_tx(&full[s], OZ_A_BYTES + nb * OZ_B_BYTES);
+        if (lane == 0) {   // producer
+            for (int kb = 0; kb < a.nkb && !failed; ++kb) {
                 const int x = xbeg + kb * OZ_KB;
-                tma_load_2d(slot, &tmA, x, sa * a.m + i0, &full[s]);
-                for (int sb = 0; sb < nb; ++sb)
-                    tma_load_2d(slot + OZ_A_BYTES + sb * OZ_B_BYTES, &tmB, x, sb * a.m + j0, &full[s]);
-                n_issued = st + 1;
+                const int bs = kb % OZ_NBB;
+                if (kb >= OZ_NBB && !mbar_wait(&bempty[bs], ((kb / OZ_NBB) - 1) & 1)) { failed = 1; break; }
+                mbar_expect_tx(&bfull[bs], OZ_BBUF);
+                for (int sb = 0; sb < OZ_SLICES; ++sb)
+                    tma_load_2d(sB + bs * OZ_BBUF + sb * OZ_B_BYTES, &tmB, x, sb * a.m + j0, &bfull[bs]);
+                b_issued = kb + 1;
+                for (int sa = 0; sa < OZ_SLICES; ++sa) {
+                    const int st = kb * OZ_SLICES + sa, as = st % OZ_NA;
+                    if (st >= OZ_NA && !mbar_wait(&aempty[as], ((st / OZ_NA) - 1) & 1)) { failed = 1; break; }
+                    mbar_expect_tx(&afull[as], OZ_A_BYTES);
+                    tma_load_2d(sA + as * OZ_A_BYTES, &tmA, x, sa * a.m + i0, &afull[as]);
+                    a_issued = st + 1;
+                }
             }
         }
     } else if (warp == 9) {
         if (lane == 0) {   // MMA issuer
             const uint32_t idesc = idesc_bf16(OZ_N);
-            unsigned started = 0;   // bit L: level L has had its first MMA of the chunk
-            for (int st = 0; st < nstages && !failed; ++st) {
-                const int kb = st / OZ_SLICES, sa = st % OZ_SLICES, s = st % OZ_NSLOT, round = st / OZ_NSLOT;
-                const int chunk = kb / OZ_CHUNK_KB;
-                if (sa == 0 && kb % OZ_CHUNK_KB == 0) {   // a new exact chunk: accumulators free again
+            const uint64_t a_desc0 = smem_desc_sw128(smem_u32(sA)), b_desc0 = smem_desc_sw128(smem_u32(sB));
+            for (int kb = 0; kb < a.nkb; ++kb) {
+                const int chunk = kb / OZ_CHUNK_KB, bs = kb % OZ_NBB;
+                const bool first = kb % OZ_CHUNK_KB == 0;   // a new exact chunk: accumulators free again
+                if (first) {
                     if (chunk > 0 && !mbar_wait(tmem_free, (chunk - 1) & 1)) { failed = 1; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    started = 0;
                 }
-                if (!mbar_wait(&full[s], round & 1)) { failed = 1; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a_addr = smem_u32(base + s * OZ_SLOT);
-                const int nb = OZ_SLICES - sa;
-                for (int sb = 0; sb < nb; ++sb) {
-                    const int L = sa + sb;   // level index 0 .. 5 (a + b - 2)
-                    const uint32_t b_addr = a_addr + OZ_A_BYTES + sb * OZ_B_BYTES;
-#pragma unroll
-                    for (int kk = 0; kk < OZ_KB / 16; ++kk) {
-                        mma_bf16(tmem + (uint32_t)(L * OZ_N), smem_desc_sw128(a_addr + kk * 32),
-                                 smem_desc_sw128(b_addr + kk * 32), idesc, (started >> L) & 1u);
-                        started |= 1u << L;
+                if (!mbar_wait(&bfull[bs], (kb / OZ_NBB) & 1)) { failed = 1; break; }
+                // descriptors advance by (bytes >> 4) in the start-address field
+                const uint64_t b_desc = b_desc0 + (uint64_t)((bs * OZ_BBUF) >> 4);
+                bool bad = false;
+                for (int sa = 0; sa < OZ_SLICES; ++sa) {
+                    const int st = kb * OZ_SLICES + sa, as = st % OZ_NA;
+                    if (!mbar_wait(&afull[as], (st / OZ_NA) & 1)) { bad = true; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t a_desc = a_desc0 + (uint64_t)((as * OZ_A_BYTES) >> 4);
+                    // every level starts (accumulate = 0) at slice 0 of a chunk's first block
+                    for (int sb = 0; sb < OZ_SLICES - sa; ++sb) {
+                        const uint32_t d = tmem + (uint32_t)((sa + sb) * OZ_N);
+                        const uint64_t bd = b_desc + (uint64_t)((sb * OZ_B_BYTES) >> 4);
+                        mma_bf16(d, a_desc, bd, idesc, (first && sa == 0) ? 0u : 1u);
+                        mma_bf16(d, a_desc + 2, bd + 2, idesc, 1u);
+                        mma_bf16(d, a_desc + 4, bd + 4, idesc, 1u);
+                        mma_bf16(d, a_desc + 6, bd + 6, idesc, 1u);
                     }
+                    mma_commit(&aempty[as]);
+                    a_consumed = st + 1;
                 }
-                mma_commit(&empty[s]);
-                n_consumed = st + 1;
-                if (sa == OZ_SLICES - 1 && (kb % OZ_CHUNK_KB == OZ_CHUNK_KB - 1 || kb == a.nkb - 1))
-                    mma_commit(chunk_done);
+                if (bad) { failed = 1; break; }
+                mma_commit(&bempty[bs]);
+                b_consumed = kb + 1;
+                if (kb % OZ_CHUNK_KB == OZ_CHUNK_KB - 1 || kb == a.nkb - 1) mma_commit(chunk_done);
             }
         }
     } else {
@@ -788,11 +841,12 @@ k_oz_gram(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __syncthreads();
     if (failed && threadIdx.x == 0) {
         atomicExch(a.err, 1);
-        // the MMAs of the last consumed stage complete before the tensor
+        // the MMAs of the last consumed A slice complete before the tensor
         // memory is freed; the copies issued but never consumed land before
-        // the CTA exits (both bounded)
-        if (n_consumed > 0) mbar_wait(&empty[(n_consumed - 1) % OZ_NSLOT], ((n_consumed - 1) / OZ_NSLOT) & 1);
-        for (int st = n_consumed; st < n_issued; ++st) mbar_wait(&full[st % OZ_NSLOT], (st / OZ_NSLOT) & 1);
+        // the CTA exits (all bounded)
+        if (a_consumed > 0) mbar_wait(&aempty[(a_consumed - 1) % OZ_NA], ((a_consumed - 1) / OZ_NA) & 1);
+        for (int st = a_consumed; st < a_issued; ++st) mbar_wait(&afull[st % OZ_NA], (st / OZ_NA) & 1);
+        for (int kb = b_consumed; kb < b_issued; ++kb) mbar_wait(&bfull[kb % OZ_NBB], (kb / OZ_NBB) & 1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -877,16 +931,18 @@ bool launch_oz_gram(wc4d_ctx *c, int64_t rows, int m, const float *A, int64_t ld
     if (!make_map_bf16(&mB, SB, (uint64_t)rp, (uint64_t)OZ_SLICES * m, (uint64_t)rp, OZ_N)) return false;
     const int64_t rows_per = 16384;
     const dim3 cg((unsigned)m, (unsigned)((rows + rows_per - 1) / rows_per));
-    const dim3 sg((unsigned)std::min<int64_t>(64, (rp + 255) / 256), (unsigned)m);
+    const dim3 sg((unsigned)std::min<int64_t>(64, (rp / 4 + 255) / 256), (unsigned)m);
+    const int vA = (lda % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15u) == 0) ? 1 : 0;
+    const int vB = (ldb % 4 == 0 && (reinterpret_cast<uintptr_t>(B) & 15u) == 0) ? 1 : 0;
     if (cudaMemsetAsync(cmA, 0, sizeof(unsigned) * 2 * m, c->stream) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    WC4D_LAUNCH(k_oz_colmax<<<cg, 256, 0, c->stream>>>(rows, rows_per, A, lda, cmA));
-    WC4D_LAUNCH(k_oz_slice<<<sg, 256, 0, c->stream>>>(rows, rp, m, A, lda, cmA, SA, eA));
+    WC4D_LAUNCH(k_oz_colmax<<<cg, 256, 0, c->stream>>>(rows, rows_per, A, lda, cmA, vA));
+    WC4D_LAUNCH(k_oz_slice<<<sg, 256, 0, c->stream>>>(rows, rp, m, A, lda, cmA, SA, eA, vA));
     if (!same) {
-        WC4D_LAUNCH(k_oz_colmax<<<cg, 256, 0, c->stream>>>(rows, rows_per, B, ldb, cmB));
-        WC4D_LAUNCH(k_oz_slice<<<sg, 256, 0, c->stream>>>(rows, rp, m, B, ldb, cmB, SB, eB));
+        WC4D_LAUNCH(k_oz_colmax<<<cg, 256, 0, c->stream>>>(rows, rows_per, B, ldb, cmB, vB));
+        WC4D_LAUNCH(k_oz_slice<<<sg, 256, 0, c->stream>>>(rows, rp, m, B, ldb, cmB, SB, eB, vB));
     }
     OzArgs args{m, nkb, m / BM, eA, eB, part, err};
     WC4D_LAUNCH(k_oz_gram<<<dim3((unsigned)tiles, (unsigned)S), OZ_THREADS, OZ_SMEM, c->stream>>>(mA, mB, args));
