@@ -194,6 +194,12 @@ wc4d_status wc4d_hvp(wc4d_ctx *ctx, const void *X, void *Y, int32_t K, int64_t l
  * element e = col*rows + row taking Box-Muller output (e & 1) of counter
  * e >> 1, with uniforms (hi27:lo26 of two words + 1) / 2^53. */
 wc4d_status wc4d_gaussian(wc4d_ctx *ctx, uint64_t seed, int64_t rows, int32_t cols, int64_t ld, double *G);
+/* The same probes computed in FP32 arithmetic (the mixed sketch's own
+   probes): the same Philox counters and 53-bit uniforms, each rounded once
+   to FP32, Box-Muller in FP32; equal to the FP64 probes to FP32 rounding
+   of log, sqrt, sin and cos (an absolute ~1e-4 where u1 is within a few
+   FP32 ulp of 1).  G: device FP32, column-major rows x cols, ld >= rows. */
+wc4d_status wc4d_gaussian_f32(wc4d_ctx *ctx, uint64_t seed, int64_t rows, int32_t cols, int64_t ld, float *G);
 
 /* Randomised Ritz pairs of A (Section 4) kept in the context for the LMP:
  * method REVD (Alg. 3 with q_power extra products and orthonormalisations),

@@ -74,6 +74,7 @@ _SIGS = {
     "wc4d_get_rhs": (C.c_int, [_V, _V]),
     "wc4d_hvp": (C.c_int, [_V, _V, _V, C.c_int32, C.c_int64, C.c_int32]),
     "wc4d_gaussian": (C.c_int, [_V, C.c_uint64, C.c_int64, C.c_int32, C.c_int64, _V]),
+    "wc4d_gaussian_f32": (C.c_int32, [_V, C.c_uint64, C.c_int64, C.c_int32, C.c_int64, _V]),
     "wc4d_sketch": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _V, _D, C.c_int32]),
     "wc4d_get_ritz": (C.c_int, [_V, _V, _D]),
     "wc4d_set_ritz": (C.c_int, [_V, C.c_int32, _V, _D]),
@@ -367,6 +368,16 @@ def wc4d_hvp(ctx, X, Y, K, ld, precision=FP64):
 
 def wc4d_gaussian(ctx, seed, rows, cols, ld, G):
     _check(ctx, load().wc4d_gaussian(ctx, int(seed), int(rows), int(cols), int(ld), _ptr(G)))
+
+
+def wc4d_gaussian_f32(ctx, seed, rows, cols, ld, G):
+    """The mixed sketch's FP32 probes (same Philox stream as wc4d_gaussian) into FP32 G."""
+    import torch
+    rows, cols, ld = int(rows), int(cols), int(ld)
+    if cols < 1 or rows < 1 or ld < rows:
+        raise WC4DError(EINVAL, "wc4d_gaussian_f32: bad shape")
+    _check(ctx, load().wc4d_gaussian_f32(ctx, int(seed), rows, cols, ld,
+                                         _dev(G, torch.float32, (cols - 1) * ld + rows, "G")))
 
 
 def wc4d_sketch(ctx, method, k, l, q_power, seed, G=None, precision=FP64):

@@ -465,7 +465,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->tw64, &c->tw32, &c->twp64, &c->twp32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
-                      &c->tc_part, &c->tc_err, &c->oz_slices, &c->oz_work, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
+                      &c->tc_part, &c->tc_err, &c->oz_slices, &c->oz_work, &c->chol_bar, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
                       &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf,
                       &c->lz_F, &c->lz_ab, &c->lz_h, &c->jq32};
     for (DevBuf *b : bufs) free_buf(*b);
@@ -810,6 +810,19 @@ static int gram_sym(wc4d_ctx *c, int64_t rows, int m, const T *A, int64_t lda, c
     }
     return launch_atb<T>(c->stream, c->num_sms, rows, m, m, A, lda, B, ldb, P<double>(c->part), c->part.bytes / 8, S,
                          G, 1);
+}
+
+// Cholesky A = R^T R into R (info in counter word 0: 0, the failing pivot,
+// or -1 when a grid barrier of the cooperative form timed out): one
+// cooperative launch when the context may use them, else one launch per
+// phase of every block step.
+static void chol_upper(wc4d_ctx *c, int m, const double *A, double *R)
+{
+    int *info = P<int>(c->counter);
+    if (c->allow_coop && ensure(c, c->chol_bar, sizeof(unsigned)) == WC4D_OK &&
+        launch_chol_upper_coop(c->stream, c->num_sms, m, A, R, info, P<unsigned>(c->chol_bar)))
+        return;
+    launch_chol_upper(c->stream, m, A, R, info);
 }
 bool tc_sweep_forward(wc4d_ctx *c, int K, float *W, int64_t ld);
 bool tc_sweep_adjoint(wc4d_ctx *c, int K, float *W, int64_t ld);
@@ -1182,6 +1195,14 @@ extern "C" wc4d_status wc4d_gaussian(wc4d_ctx *c, uint64_t seed, int64_t rows, i
     return check_launch(c, "gaussian");
 }
 
+extern "C" wc4d_status wc4d_gaussian_f32(wc4d_ctx *c, uint64_t seed, int64_t rows, int32_t cols, int64_t ld,
+                                         float *G)
+{
+    if (!c || !G || rows < 1 || cols < 1 || ld < rows) return WC4D_EINVAL;
+    launch_gaussian_f32(c->stream, seed, rows, cols, ld, G);
+    return check_launch(c, "gaussian f32");
+}
+
 // ============================================================================
 // CholeskyQR2 and the small symmetric eigenproblem
 // ============================================================================
@@ -1211,12 +1232,13 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     int info = 0;
     {
         ProfScope psc(c, PROF_CHOL);
-        launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));                            // G = R^T R
+        chol_upper(c, m, G, R);                            // G = R^T R
         launch_trinv_upper(c->stream, m, R, Rinv);
         WC4D_TRY(check_launch(c, "cholqr"));
         WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     }
     WC4D_TRY(sync(c, "cholqr info"));
+    if (info < 0) return set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out");
     if (c->gram_tc_used) {
         c->gram_tc_used = false;
         if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
@@ -1234,12 +1256,13 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
         {
             ProfScope psc(c, PROF_CHOL);
             launch_shift_diag(c->stream, m, G, f);
-            launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));
+            chol_upper(c, m, G, R);
             launch_trinv_upper(c->stream, m, R, Rinv);
             WC4D_TRY(check_launch(c, "shifted cholqr"));
             WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         }
         WC4D_TRY(sync(c, "shifted cholqr info"));
+        if (info < 0) return set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out");
     }
     if (info != 0) return set_err(c, WC4D_ENOTSPD, "CholeskyQR: Gram matrix not positive definite at pivot %d", info);
     ProfScope psl(c, PROF_LA);
@@ -1414,13 +1437,14 @@ static wc4d_status spd_evd(wc4d_ctx *c, int m, const double *S, double *w, doubl
     int info = 0;
     {
         ProfScope psc(c, PROF_CHOL);
-        launch_chol_upper(c->stream, m, S, R, P<int>(c->counter));
+        chol_upper(c, m, S, R);
         launch_rrt(c->stream, m, R, RT);
         wc4d_status st = check_launch(c, "spd_evd chol");
         if (st != WC4D_OK) return st;
         cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     }
     wc4d_status st = sync(c, "spd_evd chol");
+    if (st == WC4D_OK && info < 0) return set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out");
     if (st == WC4D_OK && info == 0) {
         ProfScope ps(c, PROF_JACOBI);
         double *X, *V;
@@ -1532,12 +1556,13 @@ extern "C" wc4d_status wc4d_chol_inverse(wc4d_ctx *c, int32_t m, const double *G
     int info = 0;
     {
         ProfScope psc(c, PROF_CHOL);
-        launch_chol_upper(c->stream, m, G, R, P<int>(c->counter));
+        chol_upper(c, m, G, R);
         launch_trinv_upper(c->stream, m, R, Rinv);
         WC4D_TRY(check_launch(c, "chol_inverse"));
         WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     }
     WC4D_TRY(sync(c, "chol_inverse"));
+    if (info < 0) return set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out");
     if (info != 0) return set_err(c, WC4D_ENOTSPD, "Cholesky: matrix not positive definite at pivot %d", info);
     return WC4D_OK;
 }
@@ -1596,14 +1621,17 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     } stop_guard{c};
     c->jacobi_stop2 = (sizeof(T) == 4) ? 1e-10 : 0.0;
 
-    // step 1: Gaussian probes G (FP64), cast to the working precision
+    // step 1: Gaussian probes G in the working precision (given probes are
+    // FP64 and cast; the mixed path draws its own in FP32 arithmetic)
     double *G64 = P<double>(c->blkD);
-    if (Gdev) WC4D_CUDA(c, cudaMemcpyAsync(G64, Gdev, sizeof(double) * nA * m, cudaMemcpyDeviceToDevice, c->stream));
-    else launch_gaussian(c->stream, seed, nA, m, nA, G64);
     if constexpr (sizeof(T) == 8) {
-        WC4D_CUDA(c, cudaMemcpyAsync(A_, G64, blk, cudaMemcpyDeviceToDevice, c->stream));
-    } else {
+        if (Gdev) WC4D_CUDA(c, cudaMemcpyAsync(A_, Gdev, blk, cudaMemcpyDeviceToDevice, c->stream));
+        else launch_gaussian(c->stream, seed, nA, m, nA, (double *)A_);
+    } else if (Gdev) {
+        WC4D_CUDA(c, cudaMemcpyAsync(G64, Gdev, sizeof(double) * nA * m, cudaMemcpyDeviceToDevice, c->stream));
         launch_convert_f64_f32(c->stream, nA * m, G64, (float *)A_);
+    } else {
+        launch_gaussian_f32(c->stream, seed, nA, m, nA, (float *)A_);
     }
     if ((st = check_launch(c, "probes")) != WC4D_OK) return fail(st);
 
@@ -1661,10 +1689,11 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         } else {
             // Nystrom (Alg. 4): E2 = C^T C; F = E1 C^{-1}; F = U Sigma V^T
             double *Cc = R;
-            launch_chol_upper(c->stream, m, Kmat, Cc, P<int>(c->counter));
+            chol_upper(c, m, Kmat, Cc);
             int info = 0;
             WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
             if ((st = sync(c, "nystrom chol")) != WC4D_OK) return fail(st);
+            if (info < 0) return fail(set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out"));
             if (info) return fail(set_err(c, WC4D_ENOTSPD, "Nystrom: Z^T A Z not positive definite (pivot %d)", info));
             launch_trinv_upper(c->stream, m, Cc, Wv);              // Wv = C^{-1}
             T *F = C_;
@@ -1730,10 +1759,11 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
         }
         launch_symmetrize(c->stream, m, Kmat);
         double *Cc = R;
-        launch_chol_upper(c->stream, m, Kmat, Cc, P<int>(c->counter));
+        chol_upper(c, m, Kmat, Cc);
         int info = 0;
         WC4D_CUDA(c, cudaMemcpyAsync(&info, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         if ((st = sync(c, "nystrom1 chol")) != WC4D_OK) return fail(st);
+        if (info < 0) return fail(set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out"));
         if (info)
             return fail(set_err(c, WC4D_ENOTSPD, "single-pass Nystrom: Omega^T Y_nu not positive definite (pivot %d)",
                                 info));

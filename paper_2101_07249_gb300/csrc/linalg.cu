@@ -317,16 +317,21 @@ __global__ void k_chol_copy(int m, const double *A, double *R, int *info)
     R[idx] = (i <= j) ? A[idx] : 0.0;
 }
 
-// Diagonal block k0 .. k0+nb-1 (nb <= 32), in place.
-__global__ void __launch_bounds__(1024) k_chol_diag(int m, int k0, double *R, int *info)
+// R is read through L2 (ld.cg) in the phases below: in the cooperative form
+// a CTA may read, after a grid barrier, blocks another CTA rewrote since it
+// last read them.
+__device__ __forceinline__ double rld(const double *p) { return __ldcg(p); }
+
+// Diagonal block k0 .. k0+nb-1 (nb <= 32), in place; 1024 threads.
+// Returns the failing pivot (k0 + c + 1) or 0.
+__device__ int chol_diag_block(int m, int k0, double *R)
 {
     __shared__ double a[CB][CB + 1];
     __shared__ double rinv;
     __shared__ int bad;
-    if (*info) return;
     const int nb = min(CB, m - k0);
     const int ti = threadIdx.x % CB, tj = threadIdx.x / CB;   // row, column within the block
-    if (ti < nb && tj < nb && ti <= tj) a[ti][tj] = R[(int64_t)(k0 + tj) * m + k0 + ti];
+    if (ti < nb && tj < nb && ti <= tj) a[ti][tj] = rld(R + (int64_t)(k0 + tj) * m + k0 + ti);
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     for (int c = 0; c < nb; ++c) {
@@ -347,25 +352,24 @@ __global__ void __launch_bounds__(1024) k_chol_diag(int m, int k0, double *R, in
         if (ti > c && ti <= tj && tj < nb) a[ti][tj] -= a[c][ti] * a[c][tj];
         __syncthreads();
     }
-    if (bad) {
-        if (threadIdx.x == 0) *info = bad;
-        return;
-    }
-    if (ti < nb && tj < nb && ti <= tj) R[(int64_t)(k0 + tj) * m + k0 + ti] = a[ti][tj];
+    const int b = bad;
+    if (!b && ti < nb && tj < nb && ti <= tj) R[(int64_t)(k0 + tj) * m + k0 + ti] = a[ti][tj];
+    __syncthreads();   // the shared arrays are reused by the next call
+    return b;
 }
 
-// Row panel: for block column j0 = k0 + nb + 32 blockIdx.x, R_kj = R_kk^{-T} A_kj.
-__global__ void __launch_bounds__(1024) k_chol_panel(int m, int k0, double *R, const int *info)
+// Row panel block bj (columns k0 + nb + 32 bj ..) of block step k0:
+// R_kj = R_kk^{-T} A_kj; 1024 threads.
+__device__ void chol_panel_block(int m, int k0, int bj, double *R)
 {
     __shared__ double l[CB][CB + 1], b[CB][CB + 1], rl[CB];
-    if (*info) return;
     const int nb = min(CB, m - k0);
-    const int j0 = k0 + nb + CB * blockIdx.x;
+    const int j0 = k0 + nb + CB * bj;
     const int nj = min(CB, m - j0);
     const int ti = threadIdx.x % CB, tj = threadIdx.x / CB;
-    if (ti < nb && tj < nb) l[ti][tj] = (ti <= tj) ? R[(int64_t)(k0 + tj) * m + k0 + ti] : 0.0;   // R_kk
-    if (ti < nb && tj < nj) b[ti][tj] = R[(int64_t)(j0 + tj) * m + k0 + ti];
-    if (threadIdx.x < nb) rl[threadIdx.x] = 1.0 / R[(int64_t)(k0 + threadIdx.x) * m + k0 + threadIdx.x];
+    if (ti < nb && tj < nb) l[ti][tj] = (ti <= tj) ? rld(R + (int64_t)(k0 + tj) * m + k0 + ti) : 0.0;   // R_kk
+    if (ti < nb && tj < nj) b[ti][tj] = rld(R + (int64_t)(j0 + tj) * m + k0 + ti);
+    if (threadIdx.x < nb) rl[threadIdx.x] = 1.0 / rld(R + (int64_t)(k0 + threadIdx.x) * m + k0 + threadIdx.x);
     __syncthreads();
     // forward substitution with R_kk^T (lower): row c of the solution, then
     // eliminate it from the rows below
@@ -376,15 +380,14 @@ __global__ void __launch_bounds__(1024) k_chol_panel(int m, int k0, double *R, c
         __syncthreads();
     }
     if (ti < nb && tj < nj) R[(int64_t)(j0 + tj) * m + k0 + ti] = b[ti][tj];
+    __syncthreads();
 }
 
-// Trailing update: CTA t -> upper block pair (bi <= bj) after block step k0.
-__global__ void __launch_bounds__(1024) k_chol_update(int m, int k0, double *R, const int *info)
+// Trailing update of block step k0 for upper block pair t (bi <= bj).
+__device__ void chol_update_block(int m, int k0, int t, double *R)
 {
     __shared__ double pi[CB][CB + 1], pj[CB][CB + 1];
-    if (*info) return;
     const int nb = min(CB, m - k0);
-    const int t = blockIdx.x;
     int bj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
     while (bj * (bj + 1) / 2 > t) --bj;
@@ -392,14 +395,97 @@ __global__ void __launch_bounds__(1024) k_chol_update(int m, int k0, double *R, 
     const int i0 = k0 + nb + CB * bi, j0 = k0 + nb + CB * bj;
     const int ti = threadIdx.x % CB, tj = threadIdx.x / CB;
     // pi[c][x] = R(k0 + c, i0 + x), pj[c][y] = R(k0 + c, j0 + y)
-    pi[ti][tj] = (ti < nb && i0 + tj < m) ? R[(int64_t)(i0 + tj) * m + k0 + ti] : 0.0;
-    pj[ti][tj] = (ti < nb && j0 + tj < m) ? R[(int64_t)(j0 + tj) * m + k0 + ti] : 0.0;
+    pi[ti][tj] = (ti < nb && i0 + tj < m) ? rld(R + (int64_t)(i0 + tj) * m + k0 + ti) : 0.0;
+    pj[ti][tj] = (ti < nb && j0 + tj < m) ? rld(R + (int64_t)(j0 + tj) * m + k0 + ti) : 0.0;
     __syncthreads();
     const int gi = i0 + ti, gj = j0 + tj;
     if (gi < m && gj < m && gi <= gj) {
         double acc = 0.0;
         for (int c = 0; c < nb; ++c) acc = fma(pi[c][ti], pj[c][tj], acc);
-        R[(int64_t)gj * m + gi] -= acc;
+        R[(int64_t)gj * m + gi] = rld(R + (int64_t)gj * m + gi) - acc;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_chol_diag(int m, int k0, double *R, int *info)
+{
+    if (*info) return;
+    const int b = chol_diag_block(m, k0, R);
+    if (b && threadIdx.x == 0) *info = b;
+}
+
+__global__ void __launch_bounds__(1024) k_chol_panel(int m, int k0, double *R, const int *info)
+{
+    if (*info) return;
+    chol_panel_block(m, k0, blockIdx.x, R);
+}
+
+// Trailing update: CTA t -> upper block pair (bi <= bj) after block step k0.
+__global__ void __launch_bounds__(1024) k_chol_update(int m, int k0, double *R, const int *info)
+{
+    if (*info) return;
+    chol_update_block(m, k0, blockIdx.x, R);
+}
+
+// Grid barrier of the cooperative Cholesky (monotonic counter; bounded).
+__device__ __forceinline__ bool chol_barrier(unsigned *bar, unsigned target)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        unsigned v = 0, it = 0;
+        int ok = 1;
+        do {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (++it > (1u << 22)) { ok = 0; break; }
+        } while (v < target);
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// The whole factorisation as one cooperative launch: the copy, then per
+// block step the diagonal block (CTA 0), the row panel (CTAs over its
+// blocks) and the trailing update (CTAs over the upper block pairs), each
+// phase followed by a grid barrier.  A failed pivot stops every CTA after
+// the next barrier (*info = pivot); a barrier that times out sets *info =
+// -1 and returns.  bar: zero at launch.
+__global__ void __launch_bounds__(1024, 1) k_chol_coop(int m, const double *A, double *R, int *info, unsigned *bar)
+{
+    __shared__ int stop;
+    const unsigned G = gridDim.x;
+    unsigned target = 0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)m * m;
+         idx += (int64_t)G * blockDim.x) {
+        const int i = (int)(idx % m), j = (int)(idx / m);
+        R[idx] = (i <= j) ? A[idx] : 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *info = 0;
+    auto sync_all = [&]() -> bool {
+        target += G;
+        if (chol_barrier(bar, target)) return true;
+        if (threadIdx.x == 0) atomicExch(info, -1);
+        return false;
+    };
+    if (!sync_all()) return;
+    for (int k0 = 0; k0 < m; k0 += CB) {
+        if (blockIdx.x == 0) {
+            const int b = chol_diag_block(m, k0, R);
+            if (b && threadIdx.x == 0) atomicExch(info, b);
+        }
+        if (!sync_all()) return;
+        if (threadIdx.x == 0) stop = __ldcg(info);
+        __syncthreads();
+        if (stop) return;   // the same value in every CTA: written before the barrier
+        const int rest = m - k0 - CB;
+        if (rest <= 0) return;
+        const int nbj = (rest + CB - 1) / CB;
+        for (int b = blockIdx.x; b < nbj; b += G) chol_panel_block(m, k0, b, R);
+        if (!sync_all()) return;
+        for (int t = blockIdx.x; t < nbj * (nbj + 1) / 2; t += G) chol_update_block(m, k0, t, R);
+        if (!sync_all()) return;
     }
 }
 
@@ -414,6 +500,35 @@ void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *i
         WC4D_LAUNCH(k_chol_panel<<<nbj, CB * CB, 0, s>>>(m, k0, R, info));
         WC4D_LAUNCH(k_chol_update<<<nbj * (nbj + 1) / 2, CB * CB, 0, s>>>(m, k0, R, info));
     }
+}
+
+// The cooperative form (bar: one counter, zeroed here); false (nothing
+// launched, error state cleared) if the launch is refused.
+bool launch_chol_upper_coop(cudaStream_t s, int num_sms, int m, const double *A, double *R, int *info, unsigned *bar)
+{
+    static const int per_sm = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chol_coop, CB * CB, 0) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        return n;
+    }();
+    if (per_sm < 1) return false;
+    const int nb0 = ceil_div(std::max(m - CB, 0), CB);
+    const int want = std::max(1, std::max(nb0 * (nb0 + 1) / 2, ceil_div((int64_t)m * m, CB * CB)));
+    const int G = std::min(want, num_sms * per_sm);
+    if (cudaMemsetAsync(bar, 0, sizeof(unsigned), s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    void *params[] = {(void *)&m, (void *)&A, (void *)&R, (void *)&info, (void *)&bar};
+    wc4d_note_launch();
+    if (cudaLaunchCooperativeKernel((const void *)k_chol_coop, dim3(G), dim3(CB * CB), params, 0, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
 }
 
 // Power-of-two range scaling of an FP32 block before its Gram matrix: the

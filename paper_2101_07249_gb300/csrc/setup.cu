@@ -49,6 +49,42 @@ void launch_gaussian(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, 
     WC4D_LAUNCH(k_gaussian<<<ceil_div(nctr, 256), 256, 0, s>>>(seed, rows, total, ld, G));
 }
 
+// The same probes in FP32 arithmetic for the mixed path: the same Philox
+// counters and 53-bit uniforms, each rounded once to FP32 (the integer
+// (m + 1) converted with one rounding, then scaled exactly by 2^-53, so u
+// is the FP32 value nearest the FP64 uniform), then Box-Muller in FP32.
+// Values agree with the FP64 generator to FP32 rounding of the logarithm
+// and the sine/cosine, except where u1 is within a few ulp of 1 (the radius
+// -2 log u1 is then tiny in both).  No FP64 arithmetic: this part's FP64
+// rate is 1/64 of its FP32 rate.
+__device__ __forceinline__ float uniform53_f32(uint32_t a, uint32_t b)
+{
+    const uint64_t m = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+    return __ull2float_rn(m + 1) * 0x1p-53f;
+}
+
+__global__ void k_gaussian_f32(uint64_t seed, int64_t rows, int64_t total, int64_t ld, float *G)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * c >= total) return;
+    uint32_t x0 = (uint32_t)c, x1 = (uint32_t)((uint64_t)c >> 32), x2 = 0u, x3 = 0u;
+    philox4x32_10(x0, x1, x2, x3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const float u1 = uniform53_f32(x0, x1), u2 = uniform53_f32(x2, x3);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    int64_t e0 = 2 * c, e1 = 2 * c + 1;
+    G[(e0 / rows) * ld + (e0 % rows)] = r * cs;
+    if (e1 < total) G[(e1 / rows) * ld + (e1 % rows)] = r * sn;
+}
+
+void launch_gaussian_f32(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, int64_t ld, float *G)
+{
+    int64_t total = rows * cols;
+    int64_t nctr = (total + 1) / 2;
+    WC4D_LAUNCH(k_gaussian_f32<<<ceil_div(nctr, 256), 256, 0, s>>>(seed, rows, total, ld, G));
+}
+
 // ----------------------------------------------------------------------------
 // Tables: tab_full[j] = e^{2 pi i j / n} (j < n) for the set-up DFTs, and the
 // FFT twiddles tw[j] = e^{-2 pi i j / n} (j < n/2).

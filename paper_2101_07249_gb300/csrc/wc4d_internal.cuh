@@ -115,7 +115,8 @@ struct wc4d_ctx {
     bool tc_err_zeroed = false;
     bool gram_tc = true;        // FP32 Gram products on the tensor cores when the shape allows (wc4d_set_gram_path)
     bool gram_tc_used = false;  // ... and one ran since the error flag was last read
-    DevBuf oz_slices, oz_work;  // BF16 slices of the Gram operands; column maxima and exponents
+    DevBuf oz_slices, oz_work;
+    DevBuf chol_bar;            // grid-barrier counter of the cooperative Cholesky  // BF16 slices of the Gram operands; column maxima and exponents
     // tensor-core operands rounded to TF32 (nearest): the propagators, and
     // the probe block as the sweep produces it (nA x K, ld nA)
     DevBuf Mtf, MTtf, tc_round;
@@ -200,6 +201,7 @@ static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b)
 // ------------------------------------------------------------------ kernels (launchers)
 // set-up
 void launch_gaussian(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, int64_t ld, double *G);
+void launch_gaussian_f32(cudaStream_t s, uint64_t seed, int64_t rows, int64_t cols, int64_t ld, float *G);
 void launch_twiddles(cudaStream_t s, int n, double2 *tab_full, double2 *tw64, float2 *tw32);
 void launch_pass_twiddles(cudaStream_t s, int n, double2 *twp64, float2 *twp32);
 void launch_cov_sqrt(cudaStream_t s, int n, int logn, bool fft, int kind, double L, double var, const double *row,
@@ -247,6 +249,7 @@ template <typename T>
 int launch_atb(cudaStream_t s, int num_sms, int64_t rows, int ma, int mb, const T *A, int64_t lda, const T *B,
                int64_t ldb, double *part, size_t part_capacity, int *splits_out, double *C, int upper);
 void launch_chol_upper(cudaStream_t s, int m, const double *A, double *R, int *info);
+bool launch_chol_upper_coop(cudaStream_t s, int num_sms, int m, const double *A, double *R, int *info, unsigned *bar);
 void launch_shift_diag(cudaStream_t s, int m, double *A, double factor);   // A_ii += factor * trace(A)
 // Y (FP32, rows x m, ld) *= 2^-e when max |Y| is outside [2^-24, 2^24] (e kept
 // in work[1]); launch_unscale_R: R *= 2^e.  work: 2 device words.

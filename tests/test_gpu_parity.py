@@ -62,6 +62,25 @@ def test_gaussian_matches_oracle():
     assert np.abs(host(G) - ref).max() < 1e-13 * np.abs(ref).max()
 
 
+def test_gaussian_f32_matches_oracle_to_fp32_rounding():
+    """The mixed sketch's FP32 probes: the oracle's Philox stream and
+    Box-Muller in FP64, against the same counters in FP32 arithmetic.  The
+    uniforms are the FP32 roundings of the FP64 ones, so an entry differs by
+    a few FP32 ulp of the log, sqrt, sin and cos -- except where u1 is within
+    a few ulp of 1, where the radius sqrt(-2 log u1) is tiny in both and the
+    difference stays below its own size."""
+    cfg, S, _, _ = setup("ad_direct")
+    rows, cols = 100003, 5                          # ragged: an odd total uses half a counter
+    G = torch.zeros(cols, rows, dtype=torch.float32, device="cuda")
+    w.wc4d_gaussian_f32(S.ctx, 777, rows, cols, rows, G)
+    ref = oracle.gaussian(777, rows, cols)
+    got = host(G).astype(np.float64)
+    err = np.abs(got - ref)
+    assert np.all(err <= 1e-5 * np.maximum(np.abs(ref), 1.0) + 1e-3 * (np.abs(ref) < 1e-2))
+    assert np.median(err / np.maximum(np.abs(ref), 1e-30)) < 3e-7
+    assert abs(got.mean()) < 0.01 and abs(got.std() - 1.0) < 0.01
+
+
 def test_propagator_matches_stepping():
     cfg, S, _, _ = setup("ad_fft")
     M = torch.zeros(cfg.n, cfg.n, dtype=torch.float64, device="cuda")
