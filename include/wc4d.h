@@ -322,8 +322,9 @@ wc4d_status wc4d_apply_linvT(wc4d_ctx *ctx, void *W, int32_t K, int64_t ld, int3
  *     triangular, m x m, ld m); ENOTSPD when G is not numerically positive
  *     definite.
  *   wc4d_tall_times_small: Z = Y W for Y (rows x m, ldy; FP64, or FP32 with
- *     WC4D_MIXED) and W (m x k FP64, ld m; rounded to FP32 for FP32 data); Z
- *     (rows x k, ldz) in Y's precision; Z must not overlap Y; rows < 2^31. */
+ *     WC4D_MIXED) and W (m x k FP64, ld m); Z (rows x k, ldz) in Y's
+ *     precision (FP32 data: W rounded to FP32, the FP32 pipe); Z must not
+ *     overlap Y; rows < 2^31. */
 wc4d_status wc4d_gram(wc4d_ctx *ctx, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t rows, int32_t ma,
                       int32_t mb, double *C, int32_t precision);
 /* C = A^T B (m x m, FP64, column-major) for products known to be symmetric
@@ -428,17 +429,23 @@ wc4d_status wc4d_set_graphs(wc4d_ctx *ctx, int32_t enable);
    truncated) receives the failing CUDA call and its error, else "".
    -1 for a null context. */
 int32_t     wc4d_iteration_mode(const wc4d_ctx *ctx, char *note, int32_t note_len);
-/* Gram-type products of FP32 blocks in the mixed path -- the CholeskyQR
-   Gram Y^T Y (Alg. 3-5, orthonormalisation), the Rayleigh-Ritz matrix
-   Z^T (A Z) (Alg. 3 step 4, Alg. 4 step 4) and the Nystrom products --
-   computed to FP64-class accuracy.  tensor_cores = 1 (default): when the
+/* Dense FP32 contractions of the mixed path's sketch.  (1) Gram-type
+   products -- the CholeskyQR Gram Y^T Y (Alg. 3-5, orthonormalisation), the
+   Rayleigh-Ritz matrix Z^T (A Z) (Alg. 3 step 4, Alg. 4 step 4) and the
+   Nystrom products -- computed to FP64-class accuracy.  (2) The tall
+   product Y R^{-1} of CholeskyQR in 3xTF32: Y and R^{-1} each split into a
+   TF32 value and a TF32 remainder, three products summed in FP32 tensor
+   memory (about 2^-21 relative; the second CholeskyQR pass restores the
+   orthogonality), when m is a multiple of 32 up to 256 and there are at
+   least 128 rows.  tensor_cores = 1 (default), Gram products: when the
    block has a multiple of 128 columns and at least 512 rows, each FP32
    column is split (scaled by a power of two) into six 7-bit integer slices
    held exactly in BF16, the 21 slice products that matter are summed
    exactly by tcgen05 BF16 MMAs in FP32 tensor memory over 512-row chunks,
    and the chunks are combined in double-float and FP64 (relative accuracy
    about 2^-41 of the largest entries); 0: the FP32-pipe double-float
-   product (about 2^-44) for every shape.  EINVAL for a null context. */
+   product (about 2^-44) and the FP32-pipe tall product for every shape.
+   EINVAL for a null context. */
 wc4d_status wc4d_set_gram_path(wc4d_ctx *ctx, int32_t tensor_cores);
 /* Polls of the grid barriers of the persistent one-column sweeps (the FP64
    sweep, and the FP32 sweep when n is not a multiple of 2048) before a wait

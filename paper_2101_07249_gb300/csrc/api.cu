@@ -465,7 +465,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->tw64, &c->tw32, &c->twp64, &c->twp32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
-                      &c->tc_part, &c->tc_err, &c->oz_slices, &c->oz_work, &c->chol_bar, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
+                      &c->tc_part, &c->tc_err, &c->oz_slices, &c->oz_work, &c->chol_bar, &c->tall_ys, &c->tall_ws, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
                       &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf,
                       &c->lz_F, &c->lz_ab, &c->lz_h, &c->jq32};
     for (DevBuf *b : bufs) free_buf(*b);
@@ -801,7 +801,7 @@ static int gram_sym(wc4d_ctx *c, int64_t rows, int m, const T *A, int64_t lda, c
                     launch_oz_gram(c, rows, m, A, lda, B, ldb, P<uint16_t>(c->oz_slices), P<int>(c->oz_work),
                                    P<double>(c->part), c->part.bytes / 8, G, P<int>(c->tc_err))) {
                     if (S) *S = 1;
-                    c->gram_tc_used = true;
+                    c->tc_err_pending = true;
                     return 0;
                 }
                 cudaGetLastError();
@@ -810,6 +810,42 @@ static int gram_sym(wc4d_ctx *c, int64_t rows, int m, const T *A, int64_t lda, c
     }
     return launch_atb<T>(c->stream, c->num_sms, rows, m, m, A, lda, B, ldb, P<double>(c->part), c->part.bytes / 8, S,
                          G, 1);
+}
+
+bool tall_tc_supported(const wc4d_ctx *c, int64_t rows, int N, int Kd);
+int64_t tall_rows_pad(int64_t rows);
+bool launch_tall_tc(wc4d_ctx *c, int64_t rows, int N, int Kd, const float *Y, int64_t ldy, const double *W, int ldw,
+                    float *C, int64_t ldc, float *YS, float *WS, int *err);
+
+// C = Y W for a tall FP32 block Y (rows x Kd, ldy) and an FP64 factor W
+// (Kd x N, ldw) on the tensor cores in 3xTF32 when the shape allows it and
+// the context has not switched the tensor-core linear algebra off; false:
+// nothing launched, the caller takes the SIMT product.  Used for Y R^{-1}
+// of CholeskyQR only: its second pass restores the orthogonality the
+// ~2^-21 products lose, while the Ritz vectors of the LMP need FP32
+// accuracy.
+static bool tall_product_tc(wc4d_ctx *c, int64_t rows, int N, int Kd, const float *Y, int64_t ldy, const double *W,
+                            int ldw, float *C, int64_t ldc)
+{
+    if (!c->gram_tc || !tall_tc_supported(c, rows, N, Kd)) return false;
+    const size_t ys = (size_t)2 * tall_rows_pad(rows) * Kd, ws = (size_t)2 * N * Kd;
+    if (ensure(c, c->tall_ys, sizeof(float) * ys) != WC4D_OK || ensure(c, c->tall_ws, sizeof(float) * ws) != WC4D_OK ||
+        ensure(c, c->tc_err, sizeof(int)) != WC4D_OK)
+        return false;
+    if (!c->tc_err_zeroed) {
+        if (cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        c->tc_err_zeroed = true;
+    }
+    if (!launch_tall_tc(c, rows, N, Kd, Y, ldy, W, ldw, C, ldc, P<float>(c->tall_ys), P<float>(c->tall_ws),
+                        P<int>(c->tc_err))) {
+        cudaGetLastError();
+        return false;
+    }
+    c->tc_err_pending = true;
+    return true;
 }
 
 // Cholesky A = R^T R into R (info in counter word 0: 0, the failing pivot,
@@ -1239,8 +1275,8 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     }
     WC4D_TRY(sync(c, "cholqr info"));
     if (info < 0) return set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out");
-    if (c->gram_tc_used) {
-        c->gram_tc_used = false;
+    if (c->tc_err_pending) {
+        c->tc_err_pending = false;
         if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
     }
     // Numerically rank-deficient Y (the Gram is accurate to FP64 rounding --
@@ -1270,9 +1306,11 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     if constexpr (sizeof(T) == 8) {
         launch_gemm<double>(c->stream, (int)rows, m, m, Y, 1, ld, Rinv, m, tmp, rows, e);
     } else {
-        float *Rinv32 = reinterpret_cast<float *>(G);   // G is no longer needed
-        launch_convert_f64_f32(c->stream, (int64_t)mm, Rinv, Rinv32);
-        launch_gemm<float>(c->stream, (int)rows, m, m, Y, 1, ld, Rinv32, m, tmp, rows, e);
+        if (!tall_product_tc(c, rows, m, m, Y, ld, Rinv, m, tmp, rows)) {
+            float *Rinv32 = reinterpret_cast<float *>(G);   // G is no longer needed
+            launch_convert_f64_f32(c->stream, (int64_t)mm, Rinv, Rinv32);
+            launch_gemm<float>(c->stream, (int)rows, m, m, Y, 1, ld, Rinv32, m, tmp, rows, e);
+        }
     }
     WC4D_TRY(check_launch(c, "cholqr gemm"));
     WC4D_CUDA(c, cudaMemcpy2DAsync(Y, sizeof(T) * ld, tmp, sizeof(T) * rows, sizeof(T) * rows, m,
@@ -1541,8 +1579,8 @@ extern "C" wc4d_status wc4d_gram_sym(wc4d_ctx *c, const void *A, int64_t lda, co
     if (r != 0) return set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small");
     WC4D_TRY(check_launch(c, "gram_sym"));
     WC4D_TRY(sync(c, "gram_sym"));
-    if (c->gram_tc_used) {
-        c->gram_tc_used = false;
+    if (c->tc_err_pending) {
+        c->tc_err_pending = false;
         if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
     }
     return WC4D_OK;
@@ -1680,6 +1718,10 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
             if constexpr (sizeof(T) == 8) {
                 launch_gemm<double>(c->stream, (int)nA, k, m, Z, 1, nA, Wv, m, U, nA, e);
             } else {
+                // FP32 pipe: the LMP needs the Ritz vectors orthonormal to
+                // FP32 rounding (their loss of orthonormality is amplified by
+                // the largest Ritz values); the 3xTF32 product cost ~12 %
+                // more CG iterations on the n = 4096, N = 40 window
                 float *W32 = reinterpret_cast<float *>(Kmat);
                 launch_convert_f64_f32(c->stream, (int64_t)mm, Wv, W32);
                 launch_gemm<float>(c->stream, (int)nA, k, m, Z, 1, nA, W32, m, U, nA, e);
@@ -1837,8 +1879,8 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     c->theta_host.assign(k, 0.0);
     cudaMemcpyAsync(c->theta_host.data(), c->theta64.p, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream);
     WC4D_TRY(sync(c, "sketch"));
-    if (c->gram_tc_used) {
-        c->gram_tc_used = false;
+    if (c->tc_err_pending) {
+        c->tc_err_pending = false;
         if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
     }
     return WC4D_OK;

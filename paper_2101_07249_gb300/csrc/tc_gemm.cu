@@ -950,3 +950,214 @@ bool launch_oz_gram(wc4d_ctx *c, int64_t rows, int m, const float *A, int64_t ld
     WC4D_LAUNCH(k_oz_reduce<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>((int)S, m, part, C));
     return cudaPeekAtLastError() == cudaSuccess;
 }
+
+// ============================================================================
+// Tall products on the tensor cores: C = Y W for a tall FP32 block Y
+// (rows x Kd, column-major) and a small factor W (Kd x N, FP64) -- Y R^{-1}
+// of CholeskyQR (Alg. 3-5) -- in "3xTF32": both operands are split into a TF32 value and a
+// TF32 remainder (Y = Yh + Yl, W = Wh + Wl) and C = Yh Wh + Yh Wl + Yl Wh is
+// accumulated in FP32 tensor memory, which keeps about 21 of FP32's 24 bits
+// (the dropped Yl Wl is below 2^-22 of each product).
+//
+// k_tall_split_y writes Y transposed to row-major hi / lo halves (so that
+// the reduction index is contiguous, the K-major layout the MMA reads) and
+// k_tall_split_w the hi / lo rows of W^T.  One CTA of k_tc_tall3 computes a
+// 128-row block of C for all N columns: warp 0 lane 0 brings in, per 32-wide
+// step of the reduction, the hi and lo tiles of Y and of W by TMA (two-stage
+// ring), warp 1 lane 0 issues the three MMAs of each 8-wide slice into one
+// accumulator, and the four warps write C from tensor memory.  All waits
+// are bounded.
+// ============================================================================
+namespace {
+
+constexpr int TL_STAGES = 2;
+constexpr int TL_A = BM * BKF * 4;                     // 16 KB: one hi or lo tile of Y
+constexpr int TL_B = MAX_N * BKF * 4;                  // up to 32 KB: one hi or lo tile of W^T
+constexpr int TL_STAGE = 2 * TL_A + 2 * TL_B;          // 96 KB
+constexpr int TL_SMEM = 1024 + TL_STAGES * TL_STAGE + 256;
+
+// YS[r][k] = tf32(Y(r, k)), YS[rows_pad + r][k] = tf32(Y(r, k) - YS[r][k])
+// (zero for r >= rows); 32 x 32 tiles transposed through shared memory.
+__global__ void k_tall_split_y(int64_t rows, int64_t rows_pad, int Kd, const float *__restrict__ Y, int64_t ldy,
+                               float *YS)
+{
+    __shared__ float t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {   // column k0 + q, rows r0 + threadIdx.x
+        const int64_t r = r0 + threadIdx.x;
+        t[q][threadIdx.x] = (r < rows) ? Y[(int64_t)(k0 + q) * ldy + r] : 0.f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {   // row r0 + q, columns k0 + threadIdx.x
+        const float v = t[threadIdx.x][q];
+        const float hi = round_tf32(v);
+        const int64_t r = r0 + q;
+        YS[r * Kd + k0 + threadIdx.x] = hi;
+        YS[(rows_pad + r) * Kd + k0 + threadIdx.x] = round_tf32(v - hi);
+    }
+}
+
+// WS[j][k] = tf32(W(k, j)), WS[N + j][k] = tf32(W(k, j) - WS[j][k]) from the FP64 factor.
+__global__ void k_tall_split_w(int Kd, int N, const double *__restrict__ W, int ldw, float *WS)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Kd * N) return;
+    const int k = idx % Kd, j = idx / Kd;
+    const double w = W[(int64_t)j * ldw + k];
+    const float hi = round_tf32((float)w);
+    WS[(int64_t)j * Kd + k] = hi;
+    WS[(int64_t)(N + j) * Kd + k] = round_tf32((float)(w - (double)hi));
+}
+
+struct TallArgs {
+    int64_t rows;       // rows of C
+    int rows_pad;       // rows of each half of the Y map
+    int N, Kd;
+    float *C;
+    int64_t ldc;
+    int *err;
+};
+
+__global__ void __launch_bounds__(128, 1)
+k_tc_tall3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TallArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + TL_STAGES * TL_STAGE);
+    uint64_t *empty = full + TL_STAGES;
+    uint64_t *done = empty + TL_STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ int failed;
+    __shared__ int n_issued, n_consumed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    const int nk = a.Kd / BKF;
+    const uint32_t b_bytes = (uint32_t)a.N * BKF * 4;
+    const uint32_t ncols = 256;
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        n_issued = 0;
+        n_consumed = 0;
+        for (int s = 0; s < TL_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {   // producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % TL_STAGES, round = kb / TL_STAGES;
+            if (kb >= TL_STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) { failed = 1; break; }
+            unsigned char *st = base + s * TL_STAGE;
+            const int x = kb * BKF;
+            mbar_expect_tx(&full[s], 2 * TL_A + 2 * b_bytes);
+            tma_load_2d(st, &tmA, x, m0, &full[s]);                              // Y hi
+            tma_load_2d(st + TL_A, &tmA, x, a.rows_pad + m0, &full[s]);          // Y lo
+            tma_load_2d(st + 2 * TL_A, &tmB, x, 0, &full[s]);                    // W^T hi
+            tma_load_2d(st + 2 * TL_A + TL_B, &tmB, x, a.N, &full[s]);           // W^T lo
+            n_issued = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0) {   // MMA issuer
+        const uint32_t idesc = idesc_tf32(a.N);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % TL_STAGES, round = kb / TL_STAGES;
+            if (!mbar_wait(&full[s], round & 1)) { failed = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = smem_u32(base + s * TL_STAGE);
+            const uint64_t ah = smem_desc_sw128(st), al = smem_desc_sw128(st + TL_A);
+            const uint64_t bh = smem_desc_sw128(st + 2 * TL_A), bl = smem_desc_sw128(st + 2 * TL_A + TL_B);
+#pragma unroll
+            for (int kk = 0; kk < BKF / 8; ++kk) {   // 32 bytes per 8-wide slice: +2 in the address field
+                const uint64_t o = 2 * kk;
+                mma_tf32(tmem, al + o, bh + o, idesc, (kb | kk) ? 1u : 0u);   // small terms first
+                mma_tf32(tmem, ah + o, bl + o, idesc, 1u);
+                mma_tf32(tmem, ah + o, bh + o, idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+            n_consumed = kb + 1;
+        }
+        mma_commit(done);
+    }
+    __syncthreads();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0) ? 1 : 0) && !failed;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int64_t row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < a.N; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < a.rows) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < a.N) a.C[(int64_t)(c0 + j) * a.ldc + row] = __uint_as_float(r[j]);
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        for (int kb = n_consumed; kb < n_issued; ++kb) mbar_wait(&full[kb % TL_STAGES], (kb / TL_STAGES) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+}  // namespace
+
+// Shapes the tall tensor-core product takes: N a multiple of 16 up to 256,
+// Kd a multiple of 32, at least 128 rows, a compute capability 10.x device.
+bool tall_tc_supported(const wc4d_ctx *c, int64_t rows, int N, int Kd)
+{
+    if (N < 16 || N > MAX_N || N % 16 != 0 || Kd < BKF || Kd % BKF != 0 || rows < BM) return false;
+    if (rows > (int64_t)INT32_MAX / 2 - BM) return false;
+    if (!device_ok(c)) return false;
+    static const bool attr =
+        cudaFuncSetAttribute(k_tc_tall3, cudaFuncAttributeMaxDynamicSharedMemorySize, TL_SMEM) == cudaSuccess;
+    if (!attr) cudaGetLastError();
+    return attr;
+}
+
+int64_t tall_rows_pad(int64_t rows) { return (rows + BM - 1) / BM * BM; }
+
+// C (rows x N, ldc) = Y (rows x Kd, ldy) W (Kd x N, FP64, ldw) in 3xTF32.
+// YS: 2 tall_rows_pad(rows) Kd floats; WS: 2 N Kd floats.  false: nothing
+// launched (a tensor map could not be made).
+bool launch_tall_tc(wc4d_ctx *c, int64_t rows, int N, int Kd, const float *Y, int64_t ldy, const double *W, int ldw,
+                    float *C, int64_t ldc, float *YS, float *WS, int *err)
+{
+    const int64_t rp = tall_rows_pad(rows);
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, YS, (uint64_t)Kd, (uint64_t)(2 * rp), (uint64_t)Kd, BM)) return false;
+    if (!make_map(&mB, WS, (uint64_t)Kd, (uint64_t)(2 * N), (uint64_t)Kd, (uint32_t)N)) return false;
+    WC4D_LAUNCH(k_tall_split_y<<<dim3((unsigned)(rp / 32), (unsigned)(Kd / 32)), dim3(32, 8), 0, c->stream>>>(
+        rows, rp, Kd, Y, ldy, YS));
+    WC4D_LAUNCH(k_tall_split_w<<<(Kd * N + 255) / 256, 256, 0, c->stream>>>(Kd, N, W, ldw, WS));
+    TallArgs args{rows, (int)rp, N, Kd, C, ldc, err};
+    WC4D_LAUNCH(k_tc_tall3<<<(unsigned)(rp / BM), 128, TL_SMEM, c->stream>>>(mA, mB, args));
+    return cudaPeekAtLastError() == cudaSuccess;
+}

@@ -113,10 +113,11 @@ struct wc4d_ctx {
     // tensor-core sweeps: split partials and the error flag of bounded waits
     DevBuf tc_part, tc_err;
     bool tc_err_zeroed = false;
-    bool gram_tc = true;        // FP32 Gram products on the tensor cores when the shape allows (wc4d_set_gram_path)
-    bool gram_tc_used = false;  // ... and one ran since the error flag was last read
+    bool gram_tc = true;        // FP32 Gram and tall products on the tensor cores when the shape allows (wc4d_set_gram_path)
+    bool tc_err_pending = false;  // a tensor-core Gram or tall product ran since the error flag was last read
     DevBuf oz_slices, oz_work;
-    DevBuf chol_bar;            // grid-barrier counter of the cooperative Cholesky  // BF16 slices of the Gram operands; column maxima and exponents
+    DevBuf chol_bar;            // grid-barrier counter of the cooperative Cholesky
+    DevBuf tall_ys, tall_ws;    // TF32 hi / lo halves of the tall product's operands  // BF16 slices of the Gram operands; column maxima and exponents
     // tensor-core operands rounded to TF32 (nearest): the propagators, and
     // the probe block as the sweep produces it (nA x K, ld nA)
     DevBuf Mtf, MTtf, tc_round;
