@@ -465,7 +465,7 @@ extern "C" void wc4d_destroy(wc4d_ctx *c)
                       &c->tw64, &c->tw32, &c->twp64, &c->twp32, &c->cosn, &c->d, &c->rhs, &c->Dm12b, &c->work64, &c->work32,
                       &c->blkA, &c->blkB, &c->blkC, &c->blkD, &c->small0, &c->small1, &c->small2, &c->small3,
                       &c->part, &c->scal, &c->counter, &c->U64, &c->U32, &c->theta64, &c->c64, &c->c32,
-                      &c->tc_part, &c->tc_err, &c->oz_slices, &c->oz_work, &c->chol_bar, &c->tall_ys, &c->tall_ws, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
+                      &c->tc_part, &c->tc_err, &c->oz_slices, &c->oz_work, &c->chol_bar, &c->tall_ys, &c->tall_ws, &c->Mlo, &c->MTlo, &c->df_vec, &c->Urm64, &c->Urm32, &c->sweep_bar, &c->Mtf, &c->MTtf, &c->tc_round,
                       &c->lin, &c->ydev, &c->sk_k, &c->sk_w, &c->sk_r, &c->evd_r, &c->qcf, &c->learn_buf,
                       &c->lz_F, &c->lz_ab, &c->lz_h, &c->jq32};
     for (DevBuf *b : bufs) free_buf(*b);
@@ -622,6 +622,7 @@ extern "C" wc4d_status wc4d_set_propagator(wc4d_ctx *c, int32_t t, const double 
     else c->have_M = true;  // caller is responsible for setting every subwindow
     c->have_M32 = false;
     c->have_Mtf = false;
+    c->have_Mlo = false;
     return WC4D_OK;
 }
 
@@ -641,6 +642,7 @@ extern "C" wc4d_status wc4d_build_advdiff_propagator(wc4d_ctx *c, double kappa, 
     c->have_M = true;
     c->have_M32 = false;
     c->have_Mtf = false;
+    c->have_Mlo = false;
     return sync(c, "build_advdiff");
 }
 
@@ -654,6 +656,31 @@ static wc4d_status ensure_M32(wc4d_ctx *c)
     launch_convert_f64_f32(c->stream, (int64_t)cnt, P<double>(c->MT64), P<float>(c->MT32));
     WC4D_TRY(check_launch(c, "convert M"));
     c->have_M32 = true;
+    return WC4D_OK;
+}
+
+// FP32 remainders of the FP64 propagators (M - M32, M^T - MT32) for the
+// double-float sweeps of the mixed CG's true residual.
+__global__ void k_f32_remainder(int64_t cnt, const double *__restrict__ A, const float *__restrict__ Ah, float *Al)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        Al[i] = __double2float_rn(A[i] - (double)Ah[i]);
+}
+
+static wc4d_status ensure_Mlo(wc4d_ctx *c)
+{
+    if (c->have_Mlo) return WC4D_OK;
+    WC4D_TRY(ensure_M32(c));
+    const size_t cnt = (size_t)c->nM * c->prob.n * c->prob.n;
+    WC4D_TRY(ensure(c, c->Mlo, cnt * sizeof(float)));
+    WC4D_TRY(ensure(c, c->MTlo, cnt * sizeof(float)));
+    const int grid = 8 * c->num_sms;
+    WC4D_LAUNCH(k_f32_remainder<<<grid, 256, 0, c->stream>>>((int64_t)cnt, P<double>(c->M64), P<float>(c->M32),
+                                                             P<float>(c->Mlo)));
+    WC4D_LAUNCH(k_f32_remainder<<<grid, 256, 0, c->stream>>>((int64_t)cnt, P<double>(c->MT64), P<float>(c->MT32),
+                                                             P<float>(c->MTlo)));
+    WC4D_TRY(check_launch(c, "propagator remainders"));
+    c->have_Mlo = true;
     return WC4D_OK;
 }
 
@@ -911,6 +938,18 @@ static bool persistent_sweep(wc4d_ctx *c, T *W, int mode)
     if (cudaMemsetAsync(bar + 1, 0, (size_t)N * sizeof(unsigned), c->stream) != cudaSuccess) return false;
     const int n = c->prob.n;
     const int64_t mstride = (c->nM == 1) ? 0 : (int64_t)n * n;
+    if constexpr (sizeof(T) == 8) {
+        // the mixed CG's true residual: double-float on the FP32 pipe
+        if (c->sweep_df && ensure_Mlo(c) == WC4D_OK &&
+            ensure(c, c->df_vec, sizeof(float) * 2 * (size_t)c->nA) == WC4D_OK) {
+            const float *Mh = P<float>(mode == 0 ? c->M32 : c->MT32), *Ml = P<float>(mode == 0 ? c->Mlo : c->MTlo);
+            float *Wh = P<float>(c->df_vec), *Wl = Wh + c->nA;
+            if (launch_gemv_sweep_df(c->stream, c->num_sms, n, c->prob.N, Mh, Ml, mstride, (double *)W, Wh, Wl, mode,
+                                     1.0 / c->prob.sigma_o2, c->prob.obs_stride, c->prob.obs_t0,
+                                     c->prob.obs_tstride, bar + 1, reinterpret_cast<int *>(bar), c->wait_limit))
+                return true;
+        }
+    }
     const T *M0 = (mode == 0) ? Ops<T>::M(c, 0) : Ops<T>::MT(c, 0);
     return launch_gemv_sweep<T>(c->stream, c->num_sms, n, c->prob.N, M0, mstride, W, mode, 1.0 / c->prob.sigma_o2,
                                 c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride,
@@ -2085,12 +2124,23 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
 }
 
 // FP64 true relative residual |rhs - A x| / |rhs|; r64 receives rhs - A x.
-static wc4d_status true_residual(wc4d_ctx *c, const double *x, double *r64, double *rel, double *bnorm_out)
+static wc4d_status true_residual(wc4d_ctx *c, const double *x, double *r64, double *rel, double *bnorm_out,
+                                 bool df = false)
 {
     const int64_t nA = c->nA;
     WC4D_TRY(ensure(c, c->pcg64[6], sizeof(double) * nA));
     double *Ax = P<double>(c->pcg64[6]);
-    WC4D_TRY(hvp_impl<double>(c, x, Ax, 1, nA, false));
+    {
+        // df (the mixed CG): the one-column sweeps of this product in
+        // double-float (48-bit propagators, ~2^-44 sums), FP64 accuracy at
+        // the HBM rate; the FP64 path keeps FP64 arithmetic
+        struct DfScope {
+            wc4d_ctx *c;
+            DfScope(wc4d_ctx *ctx, bool on) : c(ctx) { c->sweep_df = on && c->prob.model == WC4D_MODEL_DENSE; }
+            ~DfScope() { c->sweep_df = false; }
+        } df_scope(c, df);
+        WC4D_TRY(hvp_impl<double>(c, x, Ax, 1, nA, false));
+    }
     launch_sub_f64(c->stream, nA, P<double>(c->rhs), Ax, r64);
     const int grid = std::min<int64_t>(2 * c->num_sms, std::max<int64_t>(1, (nA + 255) / 256));
     WC4D_TRY(ensure(c, c->small0, sizeof(double) * 2048));
@@ -2209,7 +2259,7 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
         launch_add_f32_to_f64(c->stream, nA, d, x);
         WC4D_CUDA(c, cudaMemsetAsync(d, 0, sizeof(float) * nA, c->stream));
         pending = false;
-        WC4D_TRY(true_residual(c, x, r64, &rel, nullptr));
+        WC4D_TRY(true_residual(c, x, r64, &rel, nullptr, true));
         rmax = rel;
         if (force == 0 && rel <= tol) { converged = true; ++it; break; }
         launch_convert_f64_f32(c->stream, nA, r64, r);
@@ -2223,7 +2273,7 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
     c->iter_mode = loop.exec ? 2 : graph.exec ? 1 : 0;
     if (pending) {   // iteration budget spent (or breakdown) between updates
         launch_add_f32_to_f64(c->stream, nA, d, x);
-        WC4D_TRY(true_residual(c, x, r64, &rel, nullptr));
+        WC4D_TRY(true_residual(c, x, r64, &rel, nullptr, true));
     }
     if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
     *iters_out = it;

@@ -1106,6 +1106,264 @@ template bool launch_gemv_sweep<double>(cudaStream_t, int, int, int, const doubl
 template bool launch_gemv_sweep<float>(cudaStream_t, int, int, int, const float *, int64_t, float *, int, double,
                                        int, int, int, unsigned *, int *, unsigned);
 
+// ----------------------------------------------------------------------------
+// Double-float form of the staged sweep, for the FP64 product of the mixed
+// CG's true residual.  Each FP64 propagator entry is held as its FP32
+// rounding Mh (the mixed path's FP32 copy) plus the FP32 rounding of the
+// remainder Ml = M - Mh (48 bits in all, 8 bytes per entry as in FP64), and
+// the vector as hi / lo floats; every term (Mh + Ml)(xh + xl) is summed as
+// Mh xh exactly (TwoProduct by FMA) plus Mh xl + Ml xh into a double-float
+// accumulator (TwoSum), so the FP32 pipe does the work of the FP64 pipe,
+// which runs at 1/64 of its rate on this GPU, and the sweep is bound by
+// HBM again.  Same work split, ring and grid barriers as the FP32 staged
+// sweep; a stage carries G rows of Mh and G rows of Ml.  The row finaliser
+// writes the FP64 result and its hi / lo split (Wh, Wl), which the next
+// subwindow reads; the first subwindow splits its FP64 input itself.
+// ----------------------------------------------------------------------------
+template <int J> struct SwShapeDf {
+    static constexpr int G = J == 1 ? 2 : 1;                              // rows per stage
+    static constexpr int NS = SW_RING / (2 * G * J * SW_THREADS * 16);    // stages in the ring
+};
+
+__device__ __forceinline__ void df_two_sum(float &s, float &c, float p)
+{
+    const float t = __fadd_rn(s, p), bp = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+    s = t;
+}
+
+// s + c += (a + al)(b + bl), dropping al bl
+__device__ __forceinline__ void df_term(float a, float al, float b, float bl, float &s, float &c)
+{
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);   // a b = p + e exactly
+    df_two_sum(s, c, p);
+    c = __fadd_rn(c, fmaf(a, bl, fmaf(al, b, e)));
+}
+
+__device__ __forceinline__ void df_split(double x, float &h, float &l)
+{
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+}
+
+template <int J>
+__global__ void __launch_bounds__(SW_THREADS + 32, 1)
+k_gemv_sweep_df(const float *__restrict__ Mh0, const float *__restrict__ Ml0, double *W, float *Wh, float *Wl,
+                SweepArgs a)
+{
+    constexpr int G = SwShapeDf<J>::G, NS = SwShapeDf<J>::NS;
+    extern __shared__ __align__(128) unsigned char sw_smem[];
+    __shared__ __align__(8) unsigned long long mbar[2 * NS];   // full[NS] | empty[NS]
+    __shared__ float part_s[SW_RMAX][SW_THREADS / 32], part_c[SW_RMAX][SW_THREADS / 32];
+    const float4 *ring = reinterpret_cast<const float4 *>(sw_smem);   // [NS][2][G][n / 4]: hi rows, then lo rows
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(sw_smem);
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+    const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rbeg = blockIdx.x * a.rows_per_cta;
+    const int R = max(0, min(n, rbeg + a.rows_per_cta) - rbeg);
+    const int S = (R + G - 1) / G;   // stages per subwindow
+    const int total = a.N * S;
+    const unsigned rowb = (unsigned)n * 4u;
+    if ((ring_s & 15u) != 0u || (reinterpret_cast<uintptr_t>(Mh0) & 15u) != 0u ||
+        (reinterpret_cast<uintptr_t>(Ml0) & 15u) != 0u || (reinterpret_cast<uintptr_t>(Wh) & 15u) != 0u ||
+        (reinterpret_cast<uintptr_t>(Wl) & 15u) != 0u || (reinterpret_cast<uintptr_t>(W) & 15u) != 0u ||
+        (rowb & 15u) != 0u) {
+        if (blockIdx.x == 0 && tid == 0) atomicExch(a.err, 2);
+        return;
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            sw_mb_init(mb + 8 * i, 1);
+            sw_mb_init(mb + 8 * (NS + i), SW_THREADS / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == SW_THREADS / 32) {   // producer warp: one thread issues
+        if (lane == 0) {
+            for (int k = 0; k < total; ++k) {
+                const int slot = k % NS;
+                if (k >= NS && !sw_mb_wait(mb + 8 * (NS + slot), ((k / NS) - 1) & 1)) {
+                    atomicExch(a.err, 3);
+                    break;
+                }
+                const int step = k / S, s0 = (k % S) * G;
+                const int rows = min(G, R - s0);
+                const int t = (a.mode == 0) ? step : a.N - 1 - step;
+                const int64_t off = (int64_t)t * a.mstride + (int64_t)(rbeg + s0) * n;
+                sw_mb_expect(mb + 8 * slot, 2u * rowb * (unsigned)rows);
+                for (int g = 0; g < rows; ++g) {
+                    sw_bulk_g2s(ring_s + (uint32_t)((slot * 2 + 0) * G + g) * rowb, Mh0 + off + (int64_t)g * n, rowb,
+                                mb + 8 * slot);
+                    sw_bulk_g2s(ring_s + (uint32_t)((slot * 2 + 1) * G + g) * rowb, Ml0 + off + (int64_t)g * n, rowb,
+                                mb + 8 * slot);
+                }
+            }
+        }
+        return;
+    }
+
+    const int nv = n / 4;
+    int k = 0;
+    bool bad = false, dead = false;
+    for (int step = 0; step < a.N; ++step) {
+        const int t = (a.mode == 0) ? step : a.N - 1 - step;
+        const int64_t xoff = (int64_t)((a.mode == 0) ? t : t + 1) * n;
+        const int64_t yoff = (int64_t)((a.mode == 0) ? t + 1 : t) * n;
+        float4 xh[J], xl[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int64_t e = xoff + 4 * (int64_t)(tid + SW_THREADS * j);
+            if (step == 0) {   // the input block: split here
+                const double2 u = __ldcg(reinterpret_cast<const double2 *>(W + e));
+                const double2 v = __ldcg(reinterpret_cast<const double2 *>(W + e + 2));
+                df_split(u.x, xh[j].x, xl[j].x);
+                df_split(u.y, xh[j].y, xl[j].y);
+                df_split(v.x, xh[j].z, xl[j].z);
+                df_split(v.y, xh[j].w, xl[j].w);
+            } else {           // written by the previous subwindow's finaliser
+                xh[j] = __ldcg(reinterpret_cast<const float4 *>(Wh + e));
+                xl[j] = __ldcg(reinterpret_cast<const float4 *>(Wl + e));
+            }
+        }
+        for (int s = 0; s < S; ++s, ++k) {
+            const int slot = k % NS;
+            // after a timed-out wait the thread stops waiting but follows the
+            // same path on the stale slot (every lane reaches every barrier)
+            if (!dead && !sw_mb_wait(mb + 8 * slot, (k / NS) & 1)) {
+                dead = true;
+                atomicExch(a.err, 4);
+            }
+            float vs[G], vc[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                float sum = 0.f, cor = 0.f;
+                if (s * G + g < R) {
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float4 mh = ring[((slot * 2 + 0) * G + g) * nv + tid + SW_THREADS * j];
+                        const float4 ml = ring[((slot * 2 + 1) * G + g) * nv + tid + SW_THREADS * j];
+                        df_term(mh.x, ml.x, xh[j].x, xl[j].x, sum, cor);
+                        df_term(mh.y, ml.y, xh[j].y, xl[j].y, sum, cor);
+                        df_term(mh.z, ml.z, xh[j].z, xl[j].z, sum, cor);
+                        df_term(mh.w, ml.w, xh[j].w, xl[j].w, sum, cor);
+                    }
+                }
+                vs[g] = sum;
+                vc[g] = cor;
+            }
+            __syncwarp();
+            if (lane == 0) sw_mb_arrive(mb + 8 * (NS + slot));   // the slot may be refilled
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, vs[g], o);
+                    const float c2 = __shfl_xor_sync(0xffffffffu, vc[g], o);
+                    vc[g] = __fadd_rn(vc[g], c2);
+                    df_two_sum(vs[g], vc[g], s2);
+                }
+                if (lane == 0 && s * G + g < R) {
+                    part_s[s * G + g][warp] = vs[g];
+                    part_c[s * G + g][warp] = vc[g];
+                }
+            }
+        }
+        sw_cbar();
+        if (tid < R) {
+            float sum = 0.f, cor = 0.f;
+#pragma unroll
+            for (int i = 0; i < SW_THREADS / 32; ++i) {
+                cor = __fadd_rn(cor, part_c[tid][i]);
+                df_two_sum(sum, cor, part_s[tid][i]);
+            }
+            const int row = rbeg + tid;
+            const double tot = (double)sum + (double)cor;
+            const double old = __ldcg(W + yoff + row);
+            double out;
+            if (a.mode == 0) {
+                out = old + tot;
+            } else {
+                const bool obs = (t >= a.t0 && (t - a.t0) % a.ts == 0 && row % a.obs_stride == 0);
+                out = tot + (obs ? a.obs_inv * old : 0.0);
+            }
+            W[yoff + row] = out;
+            float h, l;
+            df_split(out, h, l);
+            Wh[yoff + row] = h;
+            Wl[yoff + row] = l;
+        }
+        if (step + 1 < a.N) {
+            if (!bad) bad = !sw_step_barrier(a.bar, step, gridDim.x, a.err);
+            else sw_cbar();
+        }
+    }
+    if (dead) {   // copies may still be in flight into the ring: wait (bounded) for the last one of every slot
+        for (int kk = max(0, total - NS); kk < total; ++kk) sw_mb_wait(mb + 8 * (kk % NS), (kk / NS) & 1);
+    }
+}
+
+template <int J>
+static bool launch_sweep_df(cudaStream_t s, int num_sms, const float *Mh0, const float *Ml0, double *W, float *Wh,
+                            float *Wl, SweepArgs &args)
+{
+    const void *fn = (const void *)k_gemv_sweep_df<J>;
+    const int smem = SwShapeDf<J>::NS * 2 * SwShapeDf<J>::G * J * SW_THREADS * 16;
+    static const bool st = [fn, smem] {
+        int per_sm = 0;
+        const bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SW_THREADS + 32, smem) ==
+                            cudaSuccess &&
+                        per_sm >= 1;
+        cudaGetLastError();
+        return ok;
+    }();
+    if (!st) return false;
+    const int rpc = ceil_div(args.n, num_sms);
+    if (rpc > SW_RMAX) return false;
+    args.rows_per_cta = rpc;
+    args.pf = 0;
+    const int grid = ceil_div(args.n, rpc);
+    void *params[] = {(void *)&Mh0, (void *)&Ml0, (void *)&W, (void *)&Wh, (void *)&Wl, (void *)&args};
+    wc4d_note_launch();
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(SW_THREADS + 32), params, smem, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// The double-float persistent sweep over FP64 vectors W (ld n per time
+// block): n a multiple of 2048 (J = n / 2048 = 1, 2 or 4), Mh0 / Ml0 the
+// FP32 propagators and remainders, Wh / Wl FP32 scratch of W's size.
+// Returns false (nothing launched) when it does not apply.
+bool launch_gemv_sweep_df(cudaStream_t s, int num_sms, int n, int N, const float *Mh0, const float *Ml0,
+                          int64_t mstride, double *W, float *Wh, float *Wl, int mode, double obs_inv, int obs_stride,
+                          int t0, int ts, unsigned *bar, int *err, unsigned wait_limit)
+{
+    if (n % (SW_THREADS * 4) != 0) return false;
+    SweepArgs args;
+    args.n = n;
+    args.N = N;
+    args.pf = 0;
+    args.mstride = mstride;
+    args.mode = mode;
+    args.obs_inv = obs_inv;
+    args.obs_stride = obs_stride;
+    args.t0 = t0;
+    args.ts = ts > 0 ? ts : 1;
+    args.bar = bar;
+    args.err = err;
+    args.wait_limit = wait_limit;
+    const int slots = n / (SW_THREADS * 4);
+    if (slots == 1) return launch_sweep_df<1>(s, num_sms, Mh0, Ml0, W, Wh, Wl, args);
+    if (slots == 2) return launch_sweep_df<2>(s, num_sms, Mh0, Ml0, W, Wh, Wl, args);
+    if (slots == 4) return launch_sweep_df<4>(s, num_sms, Mh0, Ml0, W, Wh, Wl, args);
+    return false;
+}
+
 template <typename T>
 void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int64_t ldb, T *C, int64_t ldc,
                        const Epi &e)

@@ -117,7 +117,11 @@ struct wc4d_ctx {
     bool tc_err_pending = false;  // a tensor-core Gram or tall product ran since the error flag was last read
     DevBuf oz_slices, oz_work;
     DevBuf chol_bar;            // grid-barrier counter of the cooperative Cholesky
-    DevBuf tall_ys, tall_ws;    // TF32 hi / lo halves of the tall product's operands  // BF16 slices of the Gram operands; column maxima and exponents
+    DevBuf tall_ys, tall_ws;    // TF32 hi / lo halves of the tall product's operands
+    DevBuf Mlo, MTlo;           // FP32 remainders M - M32, M^T - MT32 (double-float true-residual sweeps)
+    bool have_Mlo = false;
+    bool sweep_df = false;      // one-column FP64 sweeps in double-float (set around the mixed CG's true residual)
+    DevBuf df_vec;              // hi / lo FP32 halves of the swept FP64 vector  // BF16 slices of the Gram operands; column maxima and exponents
     // tensor-core operands rounded to TF32 (nearest): the propagators, and
     // the probe block as the sweep produces it (nA x K, ld nA)
     DevBuf Mtf, MTtf, tc_round;
@@ -232,6 +236,9 @@ void launch_sweep_gemm(cudaStream_t s, int n, int K, const T *M, const T *B, int
 template <typename T>
 bool launch_gemv_sweep(cudaStream_t s, int num_sms, int n, int N, const T *M0, int64_t mstride, T *W, int mode,
                        double obs_inv, int obs_stride, int t0, int ts, unsigned *bar, int *err, unsigned wait_limit);
+bool launch_gemv_sweep_df(cudaStream_t s, int num_sms, int n, int N, const float *Mh0, const float *Ml0,
+                          int64_t mstride, double *W, float *Wh, float *Wl, int mode, double obs_inv, int obs_stride,
+                          int t0, int ts, unsigned *bar, int *err, unsigned wait_limit);
 template <typename T>
 void launch_obs_block(cudaStream_t s, int n, int K, T *W, int64_t ld, double scale, int stride);
 

@@ -44,7 +44,13 @@ def test_full_window_inner_loop_meets_tolerance_by_the_oracle(precision):
     r = b - oracle.hvp(p, x.cpu().numpy()[None, :])[0]
     # the two FP64 operators differ by ~1e-12 relative (propagator matrix
     # against stepping), i.e. by at most ~1e-8 of |b| in the residual
-    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05 * cfg.tol
+    rel_o = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel_o <= 1.05 * cfg.tol
+    # the reported residual is the library's FP64-class true residual (in
+    # the mixed path from the double-float sweeps): it agrees with the
+    # oracle's to the operators' ~1e-12 difference, far below the ~1e-7 of
+    # an FP32 product
+    assert abs(rel - rel_o) <= 1e-9, (rel, rel_o)
 
 
 def test_full_window_ritz_pairs_by_the_oracle():
