@@ -447,15 +447,26 @@ int32_t     wc4d_iteration_mode(const wc4d_ctx *ctx, char *note, int32_t note_le
    product (about 2^-44) and the FP32-pipe tall product for every shape.
    EINVAL for a null context. */
 wc4d_status wc4d_set_gram_path(wc4d_ctx *ctx, int32_t tensor_cores);
-/* Polls of the grid barriers of the persistent one-column sweeps (the FP64
-   sweep, and the FP32 sweep when n is not a multiple of 2048) before a wait
-   gives up: the kernel then records the failure and returns, and the call
-   that ran it (wc4d_pcg, wc4d_inner_loop) returns WC4D_ETIMEOUT with the
-   context still usable.  No asynchronous copy is in flight at these waits.
-   polls < 0 restores the default (2^22, seconds); 0 makes any barrier that
-   is not already complete at its first poll fail at once, which exercises
-   the timeout path.  EINVAL for a null context or polls >= 2^32. */
+/* Polls of a bounded device-side wait before it gives up, for the grid
+   barriers of the persistent one-column sweeps (the FP64 sweep, and the FP32
+   sweep when n is not a multiple of 2048) and for the waits of the FP32
+   Lorenz-96 sweeps on their staged stage-state copies.  A kernel whose wait
+   gives up records the failure and returns (a Lorenz-96 sweep first waits,
+   bounded, for its copies still in flight), and the call that ran it
+   (wc4d_hvp, wc4d_pcg, wc4d_inner_loop, wc4d_sketch) returns WC4D_ETIMEOUT
+   with the context still usable.  polls < 0 restores the default (2^22,
+   seconds); 0 makes a grid barrier that is not already complete at its first
+   poll, and every staged-copy wait, fail at once, which exercises the timeout
+   path.  EINVAL for a null context or polls >= 2^32. */
 wc4d_status wc4d_set_wait_limit(wc4d_ctx *ctx, int64_t polls);
+/* Synchronise the context's stream and report a device-side failure of the
+   work queued on it that no call has reported yet: WC4D_ETIMEOUT when a
+   bounded wait of a product queued by wc4d_hvp (a persistent sweep's grid
+   barrier, a staged-copy wait of an FP32 Lorenz-96 sweep, a tensor-core
+   kernel's wait) gave up; WC4D_ECUDA for a CUDA error; else WC4D_OK.  The
+   solves and sketches report these failures themselves.  EINVAL for a null
+   context. */
+wc4d_status wc4d_sync(wc4d_ctx *ctx);
 /* Mixed-precision CG (reliable updates): the FP32 recurrence residual must
    fall by the factor delta (0 < delta <= 1, default 1e-3) since the last
    update, or claim convergence, before the FP64 true residual replaces it.

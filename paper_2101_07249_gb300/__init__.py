@@ -85,6 +85,7 @@ _SIGS = {
     "wc4d_orthonormalize": (C.c_int, [_V, _V, C.c_int64, C.c_int32, C.c_int64, _D, C.c_int32]),
     "wc4d_symeig": (C.c_int, [_V, C.c_int32, _V, _D, _V]),
     "wc4d_set_wait_limit": (C.c_int, [_V, C.c_int64]),
+    "wc4d_sync": (C.c_int, [_V]),
     "wc4d_gram": (C.c_int, [_V, _V, C.c_int64, _V, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _V, C.c_int32]),
     "wc4d_chol_inverse": (C.c_int, [_V, C.c_int32, _V, _V]),
     "wc4d_tall_times_small": (C.c_int, [_V, _V, C.c_int64, C.c_int64, C.c_int32, _V, C.c_int32, _V, C.c_int64,
@@ -454,8 +455,16 @@ def wc4d_symeig(ctx, m, S, V):
 
 
 def wc4d_set_wait_limit(ctx, polls):
-    """Polls of the persistent sweeps' grid barriers before a timeout (< 0: default)."""
+    """Polls of a bounded device-side wait (grid barriers of the persistent
+    sweeps, staged-copy waits of the FP32 Lorenz-96 sweeps) before it gives
+    up (< 0: default; 0: fail at once)."""
     _check(ctx, load().wc4d_set_wait_limit(ctx, int(polls)))
+
+
+def wc4d_sync(ctx):
+    """Synchronise the context's stream; raises WC4DError (ETIMEOUT) if a
+    bounded wait of queued work gave up."""
+    _check(ctx, load().wc4d_sync(ctx))
 
 
 def wc4d_gram(ctx, A, lda, B, ldb, rows, ma, mb, C_out, precision=FP64):

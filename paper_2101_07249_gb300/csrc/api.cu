@@ -967,6 +967,44 @@ static int sweep_error(wc4d_ctx *c)
     return h;
 }
 
+// Error word of the kernels whose waits on asynchronous copies are bounded
+// (the tensor-core kernels, the FP32 Lorenz-96 sweeps): allocated and zeroed
+// once per context (the first iteration of a solve runs eagerly, so this
+// never happens inside a graph capture); null if that fails, and the kernels
+// then record nothing.
+static int *wait_err_word(wc4d_ctx *c)
+{
+    if (ensure(c, c->tc_err, sizeof(int)) != WC4D_OK) return nullptr;
+    if (!c->tc_err_zeroed) {
+        if (cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        c->tc_err_zeroed = true;
+    }
+    return P<int>(c->tc_err);
+}
+
+// WC4D_ETIMEOUT if a kernel with bounded copy waits ran since the error word
+// was last read and one of its waits gave up (reading synchronises).
+static wc4d_status pending_wait_error(wc4d_ctx *c)
+{
+    if (!c->tc_err_pending) return WC4D_OK;
+    c->tc_err_pending = false;
+    if (tc_read_error(c))
+        return set_err(c, WC4D_ETIMEOUT, "a bounded wait on an asynchronous copy timed out (FP32 Lorenz-96 sweep or "
+                                         "tensor-core kernel)");
+    return WC4D_OK;
+}
+
+extern "C" wc4d_status wc4d_sync(wc4d_ctx *c)
+{
+    if (!c) return WC4D_EINVAL;
+    WC4D_TRY(sync(c, "wc4d_sync"));
+    if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
+    return pending_wait_error(c);
+}
+
 // W (nA x K, ld) <- L^{-1} W in place: W_{t+1} += M_t W_t.
 template <typename T>
 static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allow_tc)
@@ -974,7 +1012,10 @@ static wc4d_status forward_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool allo
     const int n = c->prob.n, N = c->prob.N;
     if (c->prob.model == WC4D_MODEL_L96) {
         ProfScope ps(c, PROF_L96_TLM);
-        launch_l96_tlm_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld);
+        int *err = sizeof(T) == 4 ? wait_err_word(c) : nullptr;
+        launch_l96_tlm_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld, err,
+                                c->wait_limit);
+        if (err) c->tc_err_pending = true;
         return check_launch(c, "l96 tlm sweep");
     }
     if constexpr (sizeof(T) == 4) {
@@ -1001,8 +1042,11 @@ static wc4d_status adjoint_obs_sweep(wc4d_ctx *c, int K, T *W, int64_t ld, bool 
     const int n = c->prob.n, N = c->prob.N;
     if (c->prob.model == WC4D_MODEL_L96) {
         ProfScope ps(c, PROF_L96_ADJ);
+        int *err = sizeof(T) == 4 ? wait_err_word(c) : nullptr;
         launch_l96_adj_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld, 1,
-                                1.0 / c->prob.sigma_o2, c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride);
+                                1.0 / c->prob.sigma_o2, c->prob.obs_stride, c->prob.obs_t0, c->prob.obs_tstride, err,
+                                c->wait_limit);
+        if (err) c->tc_err_pending = true;
         return check_launch(c, "l96 adjoint sweep");
     }
     if constexpr (sizeof(T) == 4) {
@@ -1068,8 +1112,10 @@ static wc4d_status plain_adjoint_sweep(wc4d_ctx *c, int K, T *W, int64_t ld)
 {
     const int n = c->prob.n, N = c->prob.N;
     if (c->prob.model == WC4D_MODEL_L96) {
+        int *err = sizeof(T) == 4 ? wait_err_word(c) : nullptr;
         launch_l96_adj_sweep<T>(c->stream, n, N, c->prob.steps, c->prob.dt, Ops<T>::stages(c), K, W, ld, 0, 0.0, 1,
-                                0, 1);
+                                0, 1, err, c->wait_limit);
+        if (err) c->tc_err_pending = true;
         return check_launch(c, "l96 adjoint sweep");
     }
     Epi e{0, 1.0, 1.0, 0.0, 1};
@@ -1314,10 +1360,7 @@ static wc4d_status cholqr_pass(wc4d_ctx *c, T *Y, int64_t rows, int m, int64_t l
     }
     WC4D_TRY(sync(c, "cholqr info"));
     if (info < 0) return set_err(c, WC4D_ETIMEOUT, "Cholesky: a grid barrier timed out");
-    if (c->tc_err_pending) {
-        c->tc_err_pending = false;
-        if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
-    }
+    WC4D_TRY(pending_wait_error(c));
     // Numerically rank-deficient Y (the Gram is accurate to FP64 rounding --
     // to ~1e-12 relative on the tensor-core path -- so this happens when its
     // condition exceeds ~1e16 (~1e12), e.g. sketches of a
@@ -1618,10 +1661,7 @@ extern "C" wc4d_status wc4d_gram_sym(wc4d_ctx *c, const void *A, int64_t lda, co
     if (r != 0) return set_err(c, WC4D_EINVAL, "internal: Gram partial buffer too small");
     WC4D_TRY(check_launch(c, "gram_sym"));
     WC4D_TRY(sync(c, "gram_sym"));
-    if (c->tc_err_pending) {
-        c->tc_err_pending = false;
-        if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
-    }
+    WC4D_TRY(pending_wait_error(c));
     return WC4D_OK;
 }
 
@@ -1918,10 +1958,7 @@ static wc4d_status sketch_impl(wc4d_ctx *c, int method, int k, int l, int q, uin
     c->theta_host.assign(k, 0.0);
     cudaMemcpyAsync(c->theta_host.data(), c->theta64.p, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream);
     WC4D_TRY(sync(c, "sketch"));
-    if (c->tc_err_pending) {
-        c->tc_err_pending = false;
-        if (tc_read_error(c)) return set_err(c, WC4D_ETIMEOUT, "tensor-core Gram: a bounded wait timed out");
-    }
+    WC4D_TRY(pending_wait_error(c));
     return WC4D_OK;
 }
 
@@ -2117,6 +2154,7 @@ static wc4d_status pcg_core(wc4d_ctx *c, const T *b, T *x, double tol, int maxit
     WC4D_TRY(sync(c, "pcg end"));
     out.done = hflags[0] != 0;
     if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
+    WC4D_TRY(pending_wait_error(c));
     out.breakdown = hflags[1];
     out.iters = hflags[2];
     out.relres_rec = hs[4];
@@ -2276,6 +2314,7 @@ static wc4d_status pcg_reliable(wc4d_ctx *c, double *x, double tol, int maxit, i
         WC4D_TRY(true_residual(c, x, r64, &rel, nullptr, true));
     }
     if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
+    WC4D_TRY(pending_wait_error(c));
     *iters_out = it;
     *rel_out = rel;
     *breakdown_out = breakdown;
@@ -2363,6 +2402,7 @@ extern "C" wc4d_status wc4d_lanczos_cg(wc4d_ctx *c, double *x, double tol, int32
     WC4D_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
     WC4D_TRY(sync(c, "lanczos cg end"));
     if (const int e = sweep_error(c)) return set_err(c, WC4D_ETIMEOUT, "persistent sweep failed (code %d)", e);
+    WC4D_TRY(pending_wait_error(c));
     c->lz_J = hflags[2];
     if (iters_out) *iters_out = hflags[2];
     if (relres_out) *relres_out = hs[4];

@@ -10,6 +10,7 @@
 #include <cooperative_groups.h>
 
 #include "wc4d_internal.cuh"
+#include "bulk.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -288,392 +289,526 @@ k_l96_adj_cl(int n, int N, int steps, T h, const T *__restrict__ stages, T *W, i
 }
 
 // ---------------------------------------------------------------------------
-// Register-blocked FP32 sweeps (n = P nt, nt a multiple of 32 and <= 1024; P
-// = 8 points per thread): thread tau owns
-// the contiguous run of points P tau .. P tau + P - 1 of C probe columns.
-// The running stage input u and the RK4 accumulator live in registers; the
-// step's base state (d for the tangent-linear sweep, lambda for the adjoint)
-// is thread-private and kept in shared memory as float4 quads laid out
-// [c][p/4][tau] (consecutive lanes, consecutive 16-byte words: one
-// conflict-free 128-bit access per quad).  The stage state x of the
-// trajectory is staged in shared memory, double-buffered: each thread copies
-// its slice of the next stage's x with cp.async while the current stage
-// computes, so the L2 latency is off the critical path, and x serves all C
-// columns.  The stencils' halos of u and x come from the neighbouring lanes by
-// warp shuffles and, at warp boundaries, from a small double-buffered edge
-// table (u) or the staged x; one __syncthreads per RK4 stage orders it all.
+// Register-blocked FP32 sweeps (n = 8 nt, nt a multiple of 32 and at most
+// 1024): thread tau owns points 8 tau .. 8 tau + 7 of C probe columns (C = 2
+// for blocks, where each staged stage state then serves both columns; 1 for
+// few columns, where the CTAs are the parallelism).
+//  * The running stage input u and the RK4 accumulator live in registers.
+//    The step's base state (d for the tangent-linear sweep, lambda for the
+//    adjoint) is thread-private in shared memory, point-major and
+//    column-minor: quad s of thread tau holds entries 4s .. 4s + 3 of its
+//    flattened (point, column) run, at float4 slot s nt + tau (one
+//    conflict-free 128-bit access per quad).
+//  * The trajectory's stage states, shared by all probe columns, stream
+//    through a ring of RB_NB shared-memory buffers: after a stage's barrier
+//    one thread issues a single bulk asynchronous copy of the stage state
+//    RB_NB - 1 stages ahead into the buffer the previous stage read,
+//    completing on that buffer's mbarrier.  (Copying the state with one
+//    16-byte cp.async per thread instead loaded the memory pipeline so much
+//    that the sweep ran 1.4x slower.)
+//  * The stencils' halos of u come from the neighbours' edge values,
+//    published to shared memory (double-buffered by stage parity) before the
+//    stage's barrier; the halos of x are read from the neighbours' points of
+//    the staged state.
+//  * One __syncthreads per RK4 stage.  The tangent-linear stage 0 takes d
+//    from u itself (they are equal there); the adjoint's per-step start
+//    a = h/6 lambda is folded into its stage 0.
+//  * Every wait on a copy is bounded (the context's wait limit).  If one
+//    gives up, the stage's barrier tells every thread, the sweep stops,
+//    thread 0 waits (bounded) for the copies still in flight, sets the error
+//    word and the CTA returns.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
-                 "l"(gmem_src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+constexpr int RB_P = 8;    // points per thread
+constexpr int RB_NB = 3;   // staged stage states: prefetch distance 2
 
-// Stage this thread's P points of the stage state x into xb.
-template <int P>
-__device__ __forceinline__ void stage_x_async(float *xb, const float *__restrict__ x, int j0)
-{
-#pragma unroll
-    for (int q = 0; q < P / 4; ++q) cp_async16(xb + j0 + 4 * q, x + j0 + 4 * q);
-    cp_async_commit();
-}
-
-// x at points j0 - 2 .. j0 + P + 1 from the staged vector xs (v[q] = x[j0 - 2 + q]).
-template <int P>
-__device__ __forceinline__ void read_xwin(float (&v)[P + 4], const float *xs, int j0, int n, int lane)
-{
-#pragma unroll
-    for (int q = 0; q < P / 4; ++q) {
-        const float4 a = *reinterpret_cast<const float4 *>(xs + j0 + 4 * q);
-        v[2 + 4 * q] = a.x; v[3 + 4 * q] = a.y; v[4 + 4 * q] = a.z; v[5 + 4 * q] = a.w;
-    }
-    const float l0 = __shfl_up_sync(0xffffffffu, v[P], 1), l1 = __shfl_up_sync(0xffffffffu, v[P + 1], 1);
-    const float r0 = __shfl_down_sync(0xffffffffu, v[2], 1), r1 = __shfl_down_sync(0xffffffffu, v[3], 1);
-    v[0] = (lane == 0) ? xs[wrap(j0 - 2, n)] : l0;
-    v[1] = (lane == 0) ? xs[wrap(j0 - 1, n)] : l1;
-    v[P + 2] = (lane == 31) ? xs[wrap(j0 + P, n)] : r0;
-    v[P + 3] = (lane == 31) ? xs[wrap(j0 + P + 1, n)] : r1;
-}
-
-__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
-
-// Shared memory of the register-blocked sweeps: [C][P/4][nt] float4 base
-// state, two staged stage states of n floats, [2][C][nw][3] warp edges.
-template <int C, int P>
+// Shared memory (floats): base [C n], ring [RB_NB][n], edges A [2][nt][2C]
+// and B [2][nt][C]; then RB_NB mbarriers.
+template <int C>
 static size_t rb_smem(int n)
 {
-    return sizeof(float) * ((size_t)C * n + 2 * (size_t)n + (size_t)2 * C * (n / P / 32) * 3);
+    const int nt = n / RB_P;
+    return sizeof(float) * ((size_t)C * n + (size_t)RB_NB * n + (size_t)6 * nt * C) + 8 * RB_NB;
 }
 
-// Per-CTA state of the register-blocked sweeps, shared by the stage bodies.
+// Per-CTA layout (constant through the sweep; kept apart from the ring
+// bookkeeping so that it stays in registers with its pointer known to be
+// shared memory).
 struct RbCta {
-    int n, nt, tid, lane, wid, nw, j0;
-    float4 *base;   // [C][P/4][nt] thread-private base state (d or lambda)
-    float *xbuf;    // [2][n] staged stage states
-    float *edge;    // [2][C][nw][3] warp edges of the stage input
+    float *sm;      // dynamic shared memory
+    int n, nt, tau;
+    int tm1, tp1;   // neighbouring threads (periodic)
+    int ring0;      // offset (floats) of ring buffer 0
+    int ea0, eb0;   // offsets (floats) of edges A and B
+    uint32_t mb0;   // shared address of the ring's first mbarrier
+    unsigned limit; // polls of a ring wait before it gives up
 };
 
-template <int C, int P>
-__device__ __forceinline__ void load_base(const RbCta &r, int c, float (&d)[P])
+// Parity of the next completion of each ring buffer.  It changes the same
+// way in every thread (after each stage's wait, whatever the wait's outcome),
+// so it stays warp-uniform.
+struct RbRing {
+    unsigned ph = 0;
+};
+
+template <int C>
+__device__ __forceinline__ RbCta rb_setup(float *sm, int n, unsigned limit)
 {
-#pragma unroll
-    for (int q = 0; q < P / 4; ++q) {
-        const float4 v = r.base[(size_t)(c * (P / 4) + q) * r.nt + r.tid];
-        d[4 * q] = v.x; d[4 * q + 1] = v.y; d[4 * q + 2] = v.z; d[4 * q + 3] = v.w;
+    RbCta L;
+    L.sm = sm;
+    L.n = n;
+    L.nt = blockDim.x;
+    L.tau = threadIdx.x;
+    L.tm1 = L.tau == 0 ? L.nt - 1 : L.tau - 1;
+    L.tp1 = L.tau == L.nt - 1 ? 0 : L.tau + 1;
+    L.ring0 = C * n;
+    L.ea0 = (C + RB_NB) * n;
+    L.eb0 = L.ea0 + 4 * L.nt * C;
+    L.mb0 = (uint32_t)__cvta_generic_to_shared(sm + L.eb0 + 2 * L.nt * C);
+    L.limit = limit;
+    return L;
+}
+
+// Thread 0: start the copy of the stage state at src (none if null) into
+// ring buffer b.  The buffer was last read before the barrier the caller has
+// passed; the proxy fence orders those generic-proxy reads before the
+// asynchronous write.
+__device__ __forceinline__ void rb_fetch(const RbCta &L, RbRing &R, int b, const float *__restrict__ src)
+{
+    if (src && L.tau == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        sw_mb_expect(L.mb0 + 8 * b, (unsigned)L.n * 4u);
+        sw_bulk_g2s((uint32_t)__cvta_generic_to_shared(L.sm + L.ring0 + b * L.n), src, (unsigned)L.n * 4u, L.mb0 + 8 * b);
     }
 }
 
-template <int C, int P>
-__device__ __forceinline__ void store_base(const RbCta &r, int c, const float (&d)[P])
+// Wait (at most L.limit further polls; none with a limit of 0, which makes
+// every wait give up at once) for the copy into ring buffer b, then advance
+// the buffer's parity.
+__device__ __forceinline__ bool rb_wait(const RbCta &L, RbRing &R, int b)
 {
-#pragma unroll
-    for (int q = 0; q < P / 4; ++q)
-        r.base[(size_t)(c * (P / 4) + q) * r.nt + r.tid] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
-}
-
-// Halo exchange of the stage input u at the start of a stage (buffer `par`):
-// TLM needs u at j0 - 2, j0 - 1 (left) and j0 + P (right); the adjoint at
-// j0 - 1 (left) and j0 + P, j0 + P + 1 (right).  Lanes get them from their
-// neighbours by shuffles; warp edges go through the edge table, read after
-// the stage's __syncthreads (done by the caller between the two halves).
-template <int C, int P, bool ADJ>
-__device__ __forceinline__ void halo_publish(const RbCta &r, const float (&u)[C][P], int par, float (&HL)[C][2],
-                                             float (&HR)[C][2])
-{
-    float *eb = r.edge + (size_t)par * C * r.nw * 3;
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        if (!ADJ) {
-            HL[c][0] = shfl_up1(u[c][P - 2]);      // u_{j0-2}
-            HL[c][1] = shfl_up1(u[c][P - 1]);      // u_{j0-1}
-            HR[c][0] = shfl_dn1(u[c][0]);          // u_{j0+P}
-            if (r.lane == 31) { eb[(c * r.nw + r.wid) * 3 + 0] = u[c][P - 2]; eb[(c * r.nw + r.wid) * 3 + 1] = u[c][P - 1]; }
-            if (r.lane == 0) eb[(c * r.nw + r.wid) * 3 + 2] = u[c][0];
-        } else {
-            HL[c][1] = shfl_up1(u[c][P - 1]);      // a_{j0-1}
-            HR[c][0] = shfl_dn1(u[c][0]);          // a_{j0+P}
-            HR[c][1] = shfl_dn1(u[c][1]);          // a_{j0+P+1}
-            if (r.lane == 31) eb[(c * r.nw + r.wid) * 3 + 0] = u[c][P - 1];
-            if (r.lane == 0) { eb[(c * r.nw + r.wid) * 3 + 1] = u[c][0]; eb[(c * r.nw + r.wid) * 3 + 2] = u[c][1]; }
-        }
+    const uint32_t a = L.mb0 + 8 * b;
+    const unsigned par = (R.ph >> b) & 1u;
+    R.ph ^= 1u << b;
+    if (L.limit == 0) return false;
+    for (unsigned it = 0;; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(par)
+                     : "memory");
+        if (done) return true;
+        if (it >= L.limit) return false;
     }
 }
 
-template <int C, bool ADJ>
-__device__ __forceinline__ void halo_collect(const RbCta &r, int par, float (&HL)[C][2], float (&HR)[C][2])
+// x_{8 tau - 2 + q}, q = 0 .. 11, from ring buffer b.
+__device__ __forceinline__ void rb_read_x(const RbCta &L, int b, float (&X)[RB_P + 4])
 {
-    const float *eb = r.edge + (size_t)par * C * r.nw * 3;
-    const int wp = (r.wid == 0) ? r.nw - 1 : r.wid - 1, wn = (r.wid == r.nw - 1) ? 0 : r.wid + 1;
+    const float *xs = L.sm + L.ring0 + b * L.n;
+    const float2 lh = *reinterpret_cast<const float2 *>(xs + RB_P * L.tm1 + RB_P - 2);
+    const float4 a = *reinterpret_cast<const float4 *>(xs + RB_P * L.tau);
+    const float4 c = *reinterpret_cast<const float4 *>(xs + RB_P * L.tau + 4);
+    const float2 rh = *reinterpret_cast<const float2 *>(xs + RB_P * L.tp1);
+    X[0] = lh.x; X[1] = lh.y;
+    X[2] = a.x; X[3] = a.y; X[4] = a.z; X[5] = a.w;
+    X[6] = c.x; X[7] = c.y; X[8] = c.z; X[9] = c.w;
+    X[10] = rh.x; X[11] = rh.y;
+}
+
+// Base-state quad s of this thread.
+__device__ __forceinline__ float4 &rb_base(const RbCta &L, int s)
+{
+    return reinterpret_cast<float4 *>(L.sm)[s * L.nt + L.tau];
+}
+
+template <int C>
+__device__ __forceinline__ void rb_store_base(const RbCta &L, const float (&v)[RB_P][C])
+{
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        if (!ADJ) {
-            if (r.lane == 0) { HL[c][0] = eb[(c * r.nw + wp) * 3 + 0]; HL[c][1] = eb[(c * r.nw + wp) * 3 + 1]; }
-            if (r.lane == 31) HR[c][0] = eb[(c * r.nw + wn) * 3 + 2];
-        } else {
-            if (r.lane == 0) HL[c][1] = eb[(c * r.nw + wp) * 3 + 0];
-            if (r.lane == 31) { HR[c][0] = eb[(c * r.nw + wn) * 3 + 1]; HR[c][1] = eb[(c * r.nw + wn) * 3 + 2]; }
-        }
+    for (int s = 0; s < RB_P * C / 4; ++s) {
+        const int f = 4 * s;
+        rb_base(L, s) = make_float4(v[f / C][f % C], v[(f + 1) / C][(f + 1) % C], v[(f + 2) / C][(f + 2) % C],
+                                    v[(f + 3) / C][(f + 3) % C]);
     }
 }
 
-// One RK4 stage I (0..3) of the tangent-linear step: k = J(s_I) u,
-// acc (+)= w_I k, next input u = d + c_I k (I < 3) or d = d + h/6 (acc + k).
-template <int C, int P, int I>
-__device__ __forceinline__ void tlm_stage(const RbCta &r, float (&u)[C][P], float (&acc)[C][P],
-                                          const float *__restrict__ stages, int g, int G, int &sidx, float h)
+// Publish two points' values (points p0, p0 + 1, all columns) to edge A and
+// one point's (p1) to edge B, in edge buffer e.
+template <int C>
+__device__ __forceinline__ void rb_publish(const RbCta &L, int e, const float (&u)[RB_P][C], int p0, int p1)
 {
-    cp_async_wait_all();
-    float HL[C][2], HR[C][2];
-    halo_publish<C, P, false>(r, u, sidx & 1, HL, HR);
-    __syncthreads();
-    {   // stage the next stage state into the other buffer
-        const int gn = (I < 3) ? g : g + 1, in = (I < 3) ? I + 1 : 0;
-        if (gn < G) stage_x_async<P>(r.xbuf + (size_t)((sidx + 1) & 1) * r.n, stages + (int64_t)(4 * gn + in) * r.n, r.j0);
+    float *ea = L.sm + L.ea0 + (e * L.nt + L.tau) * 2 * C;
+    float *eb = L.sm + L.eb0 + (e * L.nt + L.tau) * C;
+    if constexpr (C == 2) {
+        *reinterpret_cast<float4 *>(ea) = make_float4(u[p0][0], u[p0][1], u[p0 + 1][0], u[p0 + 1][1]);
+        *reinterpret_cast<float2 *>(eb) = make_float2(u[p1][0], u[p1][1]);
+    } else {
+        *reinterpret_cast<float2 *>(ea) = make_float2(u[p0][0], u[p0 + 1][0]);
+        eb[0] = u[p1][0];
     }
-    halo_collect<C, false>(r, sidx & 1, HL, HR);
-    float xv[P + 4];
-    read_xwin<P>(xv, r.xbuf + (size_t)(sidx & 1) * r.n, r.j0, r.n, r.lane);
+}
+
+template <int C>
+__device__ __forceinline__ void rb_edge_a(const RbCta &L, int e, int who, float (&e0)[C], float (&e1)[C])
+{
+    const float *ea = L.sm + L.ea0 + (e * L.nt + who) * 2 * C;
+    if constexpr (C == 2) {
+        const float4 v = *reinterpret_cast<const float4 *>(ea);
+        e0[0] = v.x; e0[1] = v.y; e1[0] = v.z; e1[1] = v.w;
+    } else {
+        const float2 v = *reinterpret_cast<const float2 *>(ea);
+        e0[0] = v.x; e1[0] = v.y;
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void rb_edge_b(const RbCta &L, int e, int who, float (&v)[C])
+{
+    const float *eb = L.sm + L.eb0 + (e * L.nt + who) * C;
+    if constexpr (C == 2) {
+        const float2 q = *reinterpret_cast<const float2 *>(eb);
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        v[0] = eb[0];
+    }
+}
+
+// Start of an RK4 stage: wait for this stage's state in ring buffer xb,
+// publish the edges of u, pass the stage's barrier (false: a wait gave up
+// somewhere in the CTA), then start the copy of `next` (null: none) into the
+// buffer the previous stage read.
+template <int C>
+__device__ __forceinline__ bool rb_stage_begin(const RbCta &L, RbRing &R, int xb, int e, const float (&u)[RB_P][C],
+                                               int p0, int p1, const float *__restrict__ next)
+{
+    const bool ok = rb_wait(L, R, xb);
+    rb_publish<C>(L, e, u, p0, p1);
+    if (__syncthreads_or(!ok)) return false;
+    rb_fetch(L, R, xb == 0 ? RB_NB - 1 : xb - 1, next);
+    return true;
+}
+
+// One tangent-linear RK4 stage I on ring buffer xb (advanced on return):
+// k = J(s_I) u, acc (+)= w_I k, next input u = d + c_I k (I < 3) or
+// d = d + h/6 (acc + k).
+template <int C, int I>
+__device__ __forceinline__ bool rb_tlm_stage(const RbCta &L, RbRing &R, int &xb, const float *__restrict__ next,
+                                             float (&u)[RB_P][C], float (&acc)[RB_P][C], float h)
+{
+    constexpr int P = RB_P, e = I & 1;
+    if (!rb_stage_begin<C>(L, R, xb, e, u, P - 2, 0, next)) return false;
+    // Points run from the last down, so only the old u_{j+1} has to be
+    // carried (u_{j-1}, u_{j-2} are still the stage input when j is reached).
+    float lm2[C], lm1[C], up1[C];
+    rb_edge_b<C>(L, e, L.tp1, up1);                        // u_{8 tau + 8}
+    rb_edge_a<C>(L, e, L.tm1, lm2, lm1);                   // u_{8 tau - 2}, u_{8 tau - 1}
+    float X[P + 4];
+    rb_read_x(L, xb, X);
     const float cf = (I == 2) ? h : 0.5f * h;
+    float dq[4];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        float d[P];
-        load_base<C, P>(r, c, d);
-        float um2 = HL[c][0], um1 = HL[c][1];
+    for (int p = P - 1; p >= 0; --p) {
+        if (I > 0 && ((p + 1) * C) % 4 == 0) {
+            const float4 q = rb_base(L, ((p + 1) * C - 4) / 4);
+            dq[0] = q.x; dq[1] = q.y; dq[2] = q.z; dq[3] = q.w;
+        }
+        const float xa = X[p + 1], xd = X[p + 3] - X[p];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const float up1 = (p + 1 < P) ? u[c][p + 1] : HR[c][0];
-            const float cur = u[c][p];
+        for (int c = 0; c < C; ++c) {
+            const float um2 = (p >= 2) ? u[p - 2][c] : (p == 1 ? lm1[c] : lm2[c]);
+            const float um1 = (p >= 1) ? u[p - 1][c] : lm1[c];
+            const float cur = u[p][c];
             // (J u)_j = (u_{j+1} - u_{j-2}) x_{j-1} + (x_{j+1} - x_{j-2}) u_{j-1} - u_j
-            const float kk = fmaf(up1 - um2, xv[p + 1], fmaf(xv[p + 3] - xv[p], um1, -cur));
-            um2 = um1;
-            um1 = cur;
+            const float kk = fmaf(up1[c] - um2, xa, fmaf(xd, um1, -cur));
+            up1[c] = cur;
             if (I == 0) {
-                acc[c][p] = kk;
-                u[c][p] = fmaf(cf, kk, d[p]);
+                acc[p][c] = kk;
+                u[p][c] = fmaf(cf, kk, cur);                // d = u at stage 0
             } else if (I < 3) {
-                acc[c][p] = fmaf(2.f, kk, acc[c][p]);
-                u[c][p] = fmaf(cf, kk, d[p]);
+                acc[p][c] = fmaf(2.f, kk, acc[p][c]);
+                u[p][c] = fmaf(cf, kk, dq[(p * C + c) % 4]);
             } else {
-                u[c][p] = fmaf(h * (1.f / 6.f), acc[c][p] + kk, d[p]);
+                u[p][c] = fmaf(h * (1.f / 6.f), acc[p][c] + kk, dq[(p * C + c) % 4]);
             }
         }
-        if (I == 3) store_base<C, P>(r, c, u[c]);
     }
-    ++sidx;
+    if (I == 3) rb_store_base<C>(L, u);
+    xb = (xb == RB_NB - 1) ? 0 : xb + 1;
+    return true;
 }
 
-// One RK4 stage I (3..0) of the adjoint step (stage state s_I): g = J(s_I)^T a;
+// One adjoint RK4 stage I (3 .. 0) on ring buffer xb: g = J(s_I)^T a;
 // I = 3: acc = lam + g, a = h/3 lam + h g; I = 2: acc += g, a = h/3 lam + h/2 g;
-// I = 1: acc += g, a = h/6 lam + h/2 g; I = 0: lam = acc + g.
-template <int C, int P, int I>
-__device__ __forceinline__ void adj_stage(const RbCta &r, float (&u)[C][P], float (&acc)[C][P],
-                                          const float *__restrict__ stages, int g, int &sidx, float h)
+// I = 1: acc += g, a = h/6 lam + h/2 g; I = 0: lam = acc + g, a = h/6 lam
+// (the next step's first input).
+template <int C, int I>
+__device__ __forceinline__ bool rb_adj_stage(const RbCta &L, RbRing &R, int &xb, const float *__restrict__ next,
+                                             float (&u)[RB_P][C], float (&acc)[RB_P][C], float h)
 {
-    cp_async_wait_all();
-    float HL[C][2], HR[C][2];
-    halo_publish<C, P, true>(r, u, sidx & 1, HL, HR);
-    __syncthreads();
-    {   // stage the next stage state (backwards) into the other buffer
-        const int gn = (I > 0) ? g : g - 1, in = (I > 0) ? I - 1 : 3;
-        if (gn >= 0) stage_x_async<P>(r.xbuf + (size_t)((sidx + 1) & 1) * r.n, stages + (int64_t)(4 * gn + in) * r.n, r.j0);
-    }
-    halo_collect<C, true>(r, sidx & 1, HL, HR);
-    float xv[P + 4];
-    read_xwin<P>(xv, r.xbuf + (size_t)(sidx & 1) * r.n, r.j0, r.n, r.lane);
+    constexpr int P = RB_P, e = I & 1;
+    if (!rb_stage_begin<C>(L, R, xb, e, u, 0, P - 1, next)) return false;
+    float am1[C], apa[C], apb[C];
+    rb_edge_b<C>(L, e, L.tm1, am1);                        // a_{8 tau - 1}
+    rb_edge_a<C>(L, e, L.tp1, apa, apb);                   // a_{8 tau + 8}, a_{8 tau + 9}
+    float X[P + 4];
+    rb_read_x(L, xb, X);
+    float dq[4], lq[4];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        float lam[P];
-        load_base<C, P>(r, c, lam);
-        float am1 = HL[c][1];
+    for (int p = 0; p < P; ++p) {
+        if (I > 0 && (p * C) % 4 == 0) {
+            const float4 q = rb_base(L, p * C / 4);
+            dq[0] = q.x; dq[1] = q.y; dq[2] = q.z; dq[3] = q.w;
+        }
+        const float xm2 = X[p], xp1 = X[p + 3], xd = X[p + 4] - X[p + 1];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const float ap1 = (p + 1 < P) ? u[c][p + 1] : HR[c][0];
-            const float ap2 = (p + 2 < P) ? u[c][p + 2] : ((p + 2 == P) ? HR[c][0] : HR[c][1]);
-            const float cur = u[c][p];
+        for (int c = 0; c < C; ++c) {
+            const float ap1 = (p + 1 < P) ? u[p + 1][c] : apa[c];
+            const float ap2 = (p + 2 < P) ? u[p + 2][c] : ((p + 2 == P) ? apa[c] : apb[c]);
+            const float cur = u[p][c];
             // (J^T a)_i = x_{i-2} a_{i-1} - x_{i+1} a_{i+2} + (x_{i+2} - x_{i-1}) a_{i+1} - a_i
-            const float gg = fmaf(xv[p], am1, fmaf(-xv[p + 3], ap2, fmaf(xv[p + 4] - xv[p + 1], ap1, -cur)));
-            am1 = cur;
+            const float gg = fmaf(xm2, am1[c], fmaf(-xp1, ap2, fmaf(xd, ap1, -cur)));
+            am1[c] = cur;
             if (I == 3) {
-                acc[c][p] = lam[p] + gg;
-                u[c][p] = fmaf(h * (1.f / 3.f), lam[p], h * gg);
+                const float lam = dq[(p * C + c) % 4];
+                acc[p][c] = lam + gg;
+                u[p][c] = fmaf(h * (1.f / 3.f), lam, h * gg);
             } else if (I == 2) {
-                acc[c][p] += gg;
-                u[c][p] = fmaf(h * (1.f / 3.f), lam[p], 0.5f * h * gg);
+                acc[p][c] += gg;
+                u[p][c] = fmaf(h * (1.f / 3.f), dq[(p * C + c) % 4], 0.5f * h * gg);
             } else if (I == 1) {
-                acc[c][p] += gg;
-                u[c][p] = fmaf(h * (1.f / 6.f), lam[p], 0.5f * h * gg);
+                acc[p][c] += gg;
+                u[p][c] = fmaf(h * (1.f / 6.f), dq[(p * C + c) % 4], 0.5f * h * gg);
             } else {
-                lam[p] = acc[c][p] + gg;
+                const float lam = acc[p][c] + gg;
+                lq[(p * C + c) % 4] = lam;
+                u[p][c] = (h * (1.f / 6.f)) * lam;
             }
         }
-        if (I == 0) store_base<C, P>(r, c, lam);
+        if (I == 0 && ((p + 1) * C) % 4 == 0) rb_base(L, ((p + 1) * C - 4) / 4) = make_float4(lq[0], lq[1], lq[2], lq[3]);
     }
-    ++sidx;
+    xb = (xb == RB_NB - 1) ? 0 : xb + 1;
+    return true;
+}
+
+// Set up the ring: thread 0 initialises its mbarriers and starts the copies
+// of the first RB_NB - 1 stage states (stage indices first, first + dir, ...).
+template <int C>
+__device__ __forceinline__ void rb_ring_start(const RbCta &L, RbRing &R, const float *__restrict__ stages, int S,
+                                              int first, int dir)
+{
+    if (L.tau == 0) {
+        for (int b = 0; b < RB_NB; ++b) sw_mb_init(L.mb0 + 8 * b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    for (int d = 0; d < RB_NB - 1; ++d) {
+        const int si = first + dir * d;
+        rb_fetch(L, R, d, (si >= 0 && si < S) ? stages + (int64_t)si * L.n : nullptr);
+    }
+}
+
+// After the wait on ring buffer xb gave up somewhere in the CTA (before the
+// stage's copy was started): thread 0 waits (bounded) for the copies that
+// may still be in flight -- the one into xb and the one into the next buffer,
+// started one stage earlier unless this was the sweep's last stage -- and
+// records the failure.
+__device__ __forceinline__ void rb_abort(const RbCta &L, const RbRing &R, int xb, bool last, int *err)
+{
+    if (L.tau != 0) return;
+    const int nb = xb == RB_NB - 1 ? 0 : xb + 1;
+    sw_mb_wait(L.mb0 + 8 * xb, ((R.ph >> xb) & 1u) ^ 1u);
+    if (!last) sw_mb_wait(L.mb0 + 8 * nb, (R.ph >> nb) & 1u);
+    if (err) atomicExch(err, 1);
 }
 
 // Forward sweep L^{-1} (w_{t+1} += M_t w_t) for columns blockIdx.x*C .. +C-1 (< K).
-template <int C, int P>
-__global__ void __launch_bounds__(P == 16 ? 512 : 1024, 1)
-k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K)
+template <int C>
+__global__ void __launch_bounds__(1024, 1)
+k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K,
+             int *err, unsigned limit)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    RbCta r;
-    r.n = n; r.nt = blockDim.x; r.tid = threadIdx.x; r.lane = r.tid & 31; r.wid = r.tid >> 5; r.nw = r.nt >> 5;
-    r.j0 = r.tid * P;
-    r.base = reinterpret_cast<float4 *>(sm);
-    r.xbuf = reinterpret_cast<float *>(sm) + (size_t)C * n;
-    r.edge = r.xbuf + 2 * (size_t)n;
-    const int G = N * steps;
-    stage_x_async<P>(r.xbuf, stages, r.j0);                  // stage (g = 0, I = 0)
-    float u[C][P], acc[C][P];
+    constexpr int P = RB_P, D = RB_NB - 1;
+    extern __shared__ __align__(16) float rsm[];
+    const RbCta L = rb_setup<C>(rsm, n, limit);
+    RbRing R;
+    const int j0 = L.tau * P;
+    const int S = 4 * N * steps;                           // stage states, used in order 0 .. S - 1
+    rb_ring_start<C>(L, R, stages, S, 0, 1);
+    float u[P][C], acc[P][C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = blockIdx.x * C + c;
-        const float *w = W + (int64_t)min(col, K - 1) * ld;
+        const float *w = W + (int64_t)min(col, K - 1) * ld + j0;
 #pragma unroll
-        for (int p = 0; p < P; ++p) u[c][p] = (col < K) ? w[r.j0 + p] : 0.f;
-        store_base<C, P>(r, c, u[c]);
+        for (int p = 0; p < P; ++p) u[p][c] = (col < K) ? w[p] : 0.f;
     }
-    int sidx = 0;
-    for (int t = 0; t < N; ++t) {
+    rb_store_base<C>(L, u);
+    int q = 0, xb = 0;                                     // stages begun; ring buffer of the next
+    bool good = true;
+    for (int t = 0; t < N && good; ++t) {
         for (int k = 0; k < steps; ++k) {
-            const int g = t * steps + k;
-            tlm_stage<C, P, 0>(r, u, acc, stages, g, G, sidx, h);
-            tlm_stage<C, P, 1>(r, u, acc, stages, g, G, sidx, h);
-            tlm_stage<C, P, 2>(r, u, acc, stages, g, G, sidx, h);
-            tlm_stage<C, P, 3>(r, u, acc, stages, g, G, sidx, h);
+            const int s = q;                                // stage state 4 (t steps + k)
+            const float *x = stages + (int64_t)s * n;
+            if (!(good = rb_tlm_stage<C, 0>(L, R, xb, s + D < S ? x + D * n : nullptr, u, acc, h))) break;
+            ++q;
+            if (!(good = rb_tlm_stage<C, 1>(L, R, xb, s + 1 + D < S ? x + (1 + D) * n : nullptr, u, acc, h))) break;
+            ++q;
+            if (!(good = rb_tlm_stage<C, 2>(L, R, xb, s + 2 + D < S ? x + (2 + D) * n : nullptr, u, acc, h))) break;
+            ++q;
+            if (!(good = rb_tlm_stage<C, 3>(L, R, xb, s + 3 + D < S ? x + (3 + D) * n : nullptr, u, acc, h))) break;
+            ++q;
         }
+        if (!good) break;
         // subwindow boundary: w_{t+1} += d, d = w_{t+1}
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int col = blockIdx.x * C + c;
             if (col >= K) continue;
-            float *wn = W + (int64_t)col * ld + (int64_t)(t + 1) * n;
+            float *wn = W + (int64_t)col * ld + (int64_t)(t + 1) * n + j0;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float v = u[c][p] + wn[r.j0 + p];
-                wn[r.j0 + p] = v;
-                u[c][p] = v;
+                const float v = u[p][c] + wn[p];
+                wn[p] = v;
+                u[p][c] = v;
             }
-            store_base<C, P>(r, c, u[c]);
         }
+        rb_store_base<C>(L, u);
     }
-    cp_async_wait_all();
+    if (!good) rb_abort(L, R, xb, q == S - 1, err);   // q: the stage whose wait gave up
 }
 
 // Adjoint sweep L^{-T} for columns blockIdx.x*C .. +C-1 (< K); obs_mode as
 // k_l96_adj.
-template <int C, int P>
-__global__ void __launch_bounds__(P == 16 ? 512 : 1024, 1)
+template <int C>
+__global__ void __launch_bounds__(1024, 1)
 k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K,
-             int obs_mode, float obs_scale, int obs_stride, int t0, int ts)
+             int obs_mode, float obs_scale, int obs_stride, int t0, int ts, int *err, unsigned limit)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    RbCta r;
-    r.n = n; r.nt = blockDim.x; r.tid = threadIdx.x; r.lane = r.tid & 31; r.wid = r.tid >> 5; r.nw = r.nt >> 5;
-    r.j0 = r.tid * P;
-    r.base = reinterpret_cast<float4 *>(sm);
-    r.xbuf = reinterpret_cast<float *>(sm) + (size_t)C * n;
-    r.edge = r.xbuf + 2 * (size_t)n;
-    const int G = N * steps;
-    stage_x_async<P>(r.xbuf, stages + (int64_t)(4 * (G - 1) + 3) * n, r.j0);   // stage (g = G - 1, I = 3)
+    constexpr int P = RB_P, D = RB_NB - 1;
+    extern __shared__ __align__(16) float rsm[];
+    const RbCta L = rb_setup<C>(rsm, n, limit);
+    RbRing R;
+    const int j0 = L.tau * P;
+    const int S = 4 * N * steps;                           // stage states, used in order S - 1 .. 0
+    rb_ring_start<C>(L, R, stages, S, S - 1, -1);
     auto obs_at = [&](int t) { return t >= t0 && (t - t0) % ts == 0; };
-    float u[C][P], acc[C][P];
+    float u[P][C], acc[P][C];
     {
         const bool ob = obs_at(N);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int col = blockIdx.x * C + c;
-            float *wN = W + (int64_t)min(col, K - 1) * ld + (int64_t)N * n;
+            float *wN = W + (int64_t)min(col, K - 1) * ld + (int64_t)N * n + j0;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float v = (col < K) ? wN[r.j0 + p] : 0.f;
-                if (obs_mode == 1) v = (ob && (r.j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
-                if (col < K) wN[r.j0 + p] = v;
-                u[c][p] = v;
+                float v = (col < K) ? wN[p] : 0.f;
+                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
+                if (col < K) wN[p] = v;
+                u[p][c] = v;
             }
-            store_base<C, P>(r, c, u[c]);
         }
+        rb_store_base<C>(L, u);
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int c = 0; c < C; ++c) u[p][c] = (h * (1.f / 6.f)) * u[p][c];
     }
-    int sidx = 0;
-    for (int t = N - 1; t >= 0; --t) {
+    int q = 0, xb = 0;                                     // stages begun; ring buffer of the next
+    bool good = true;
+    for (int t = N - 1; t >= 0 && good; --t) {
         for (int k = steps - 1; k >= 0; --k) {
-            const int g = t * steps + k;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                float lam[P];
-                load_base<C, P>(r, c, lam);
-#pragma unroll
-                for (int p = 0; p < P; ++p) u[c][p] = (h * (1.f / 6.f)) * lam[p];
-            }
-            adj_stage<C, P, 3>(r, u, acc, stages, g, sidx, h);
-            adj_stage<C, P, 2>(r, u, acc, stages, g, sidx, h);
-            adj_stage<C, P, 1>(r, u, acc, stages, g, sidx, h);
-            adj_stage<C, P, 0>(r, u, acc, stages, g, sidx, h);
+            const int s = S - 1 - q;                        // stage state 4 (t steps + k) + 3
+            const float *x = stages + (int64_t)s * n;
+            if (!(good = rb_adj_stage<C, 3>(L, R, xb, s - D >= 0 ? x - D * n : nullptr, u, acc, h))) break;
+            ++q;
+            if (!(good = rb_adj_stage<C, 2>(L, R, xb, s - 1 - D >= 0 ? x - (1 + D) * n : nullptr, u, acc, h))) break;
+            ++q;
+            if (!(good = rb_adj_stage<C, 1>(L, R, xb, s - 2 - D >= 0 ? x - (2 + D) * n : nullptr, u, acc, h))) break;
+            ++q;
+            if (!(good = rb_adj_stage<C, 0>(L, R, xb, s - 3 - D >= 0 ? x - (3 + D) * n : nullptr, u, acc, h))) break;
+            ++q;
         }
-        // subwindow boundary: lam = obs(w_t) + lam, w_t = lam
+        if (!good) break;
+        // subwindow boundary: lam = obs(w_t) + lam, w_t = lam, a = h/6 lam
         const bool ob = obs_at(t);
+        float lam[P][C];
+#pragma unroll
+        for (int q = 0; q < P * C / 4; ++q) {
+            const float4 v = rb_base(L, q);
+            const int f = 4 * q;
+            lam[f / C][f % C] = v.x; lam[(f + 1) / C][(f + 1) % C] = v.y;
+            lam[(f + 2) / C][(f + 2) % C] = v.z; lam[(f + 3) / C][(f + 3) % C] = v.w;
+        }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int col = blockIdx.x * C + c;
             if (col >= K) continue;
-            float lam[P];
-            load_base<C, P>(r, c, lam);
-            float *wt = W + (int64_t)col * ld + (int64_t)t * n;
+            float *wt = W + (int64_t)col * ld + (int64_t)t * n + j0;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float v = wt[r.j0 + p];
-                if (obs_mode == 1) v = (ob && (r.j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
-                lam[p] += v;
-                wt[r.j0 + p] = lam[p];
+                float v = wt[p];
+                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
+                lam[p][c] += v;
+                wt[p] = lam[p][c];
             }
-            store_base<C, P>(r, c, lam);
         }
+        rb_store_base<C>(L, lam);
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int c = 0; c < C; ++c) u[p][c] = (h * (1.f / 6.f)) * lam[p][c];
     }
-    cp_async_wait_all();
+    if (!good) rb_abort(L, R, xb, q == S - 1, err);   // q: the stage whose wait gave up
 }
 
-// Register-blocked form: FP32, n = 8 nt with nt a multiple of 32 and at most
-// 1024 (0: not applicable).  Sixteen points per thread on half the threads
-// measured slower at n = 8192 (6.1 against 5.6 ms for a 256-column product).
-template <typename T> static int rb_points(int n)
+// Register-blocked form: FP32 and n = 8 nt with nt a multiple of 32 and at
+// most 1024.
+template <typename T> static bool rb_applies(int n)
 {
-    if (sizeof(T) != 4) return 0;
-    if (n % 256 == 0 && n / 8 <= 1024) return 8;
-    return 0;
+    return sizeof(T) == 4 && n % 256 == 0 && n / RB_P <= 1024;
 }
-// Columns per CTA: two for blocks (the staged stage states then serve both),
-// one for few columns, where the CTAs are the parallelism.
+// Columns per CTA: two for blocks, one for few columns.
 static int rb_cols(int K) { return K >= 64 ? 2 : 1; }
 
 static bool use_cluster(int n, int K) { return K <= 32 && n % L96_CL == 0 && n / L96_CL >= 2 && n / L96_CL <= 1024; }
 
-template <int C, int P>
+template <int C>
 static void launch_tlm_rb(cudaStream_t s, int n, int N, int steps, double dt, const float *stages, int K, float *W,
-                          int64_t ld)
+                          int64_t ld, int *err, unsigned limit)
 {
     static const bool attr = [] {
-        return cudaFuncSetAttribute(k_l96_tlm_rb<C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)rb_smem<C, P>(WC4D_FFT_MAX_N)) == cudaSuccess;
+        return cudaFuncSetAttribute(k_l96_tlm_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
     }();   // once, thread-safe
     (void)attr;
-    WC4D_LAUNCH(k_l96_tlm_rb<C, P><<<ceil_div(K, C), n / P, rb_smem<C, P>(n), s>>>(n, N, steps, (float)dt, stages, W,
-                                                                                  ld, K));
+    WC4D_LAUNCH(k_l96_tlm_rb<C><<<ceil_div(K, C), n / RB_P, rb_smem<C>(n), s>>>(n, N, steps, (float)dt, stages, W, ld,
+                                                                                K, err, limit));
+}
+
+template <int C>
+static void launch_adj_rb(cudaStream_t s, int n, int N, int steps, double dt, const float *stages, int K, float *W,
+                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride,
+                          int *err, unsigned limit)
+{
+    static const bool attr = [] {
+        return cudaFuncSetAttribute(k_l96_adj_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
+    }();   // once, thread-safe
+    (void)attr;
+    WC4D_LAUNCH(k_l96_adj_rb<C><<<ceil_div(K, C), n / RB_P, rb_smem<C>(n), s>>>(
+        n, N, steps, (float)dt, stages, W, ld, K, obs_mode, (float)obs_scale, obs_stride, obs_t0,
+        obs_tstride > 0 ? obs_tstride : 1, err, limit));
 }
 
 template <typename T>
 void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
-                          int64_t ld)
+                          int64_t ld, int *err, unsigned wait_limit)
 {
     if constexpr (sizeof(T) == 4) {
-        const int P = rb_points<T>(n);
-        if (P == 8) {
-            if (rb_cols(K) == 2) launch_tlm_rb<2, 8>(s, n, N, steps, dt, stages, K, W, ld);
-            else launch_tlm_rb<1, 8>(s, n, N, steps, dt, stages, K, W, ld);
+        if (rb_applies<T>(n)) {
+            if (rb_cols(K) == 2) launch_tlm_rb<2>(s, n, N, steps, dt, stages, K, W, ld, err, wait_limit);
+            else launch_tlm_rb<1>(s, n, N, steps, dt, stages, K, W, ld, err, wait_limit);
             return;
         }
     }
@@ -690,34 +825,21 @@ void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
     WC4D_LAUNCH(k_l96_tlm<T><<<K, L96_THREADS, 3 * (size_t)n * sizeof(T), s>>>(n, N, steps, (T)dt, stages, W, ld));
 }
 
-template <int C, int P>
-static void launch_adj_rb(cudaStream_t s, int n, int N, int steps, double dt, const float *stages, int K, float *W,
-                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
-{
-    static const bool attr = [] {
-        return cudaFuncSetAttribute(k_l96_adj_rb<C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)rb_smem<C, P>(WC4D_FFT_MAX_N)) == cudaSuccess;
-    }();   // once, thread-safe
-    (void)attr;
-    WC4D_LAUNCH(k_l96_adj_rb<C, P><<<ceil_div(K, C), n / P, rb_smem<C, P>(n), s>>>(
-        n, N, steps, (float)dt, stages, W, ld, K, obs_mode, (float)obs_scale, obs_stride, obs_t0,
-        obs_tstride > 0 ? obs_tstride : 1));
-}
-
 template <typename T>
 void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
-                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride)
+                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride,
+                          int *err, unsigned wait_limit)
 {
     if constexpr (sizeof(T) == 4) {
-        const int P = rb_points<T>(n);
-#define WC4D_ADJ_RB(CC, PP)                                                                                      \
-    launch_adj_rb<CC, PP>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0, obs_tstride)
-        if (P == 8) {
-            if (rb_cols(K) == 2) WC4D_ADJ_RB(2, 8);
-            else WC4D_ADJ_RB(1, 8);
+        if (rb_applies<T>(n)) {
+            if (rb_cols(K) == 2)
+                launch_adj_rb<2>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0,
+                                 obs_tstride, err, wait_limit);
+            else
+                launch_adj_rb<1>(s, n, N, steps, dt, stages, K, W, ld, obs_mode, obs_scale, obs_stride, obs_t0,
+                                 obs_tstride, err, wait_limit);
             return;
         }
-#undef WC4D_ADJ_RB
     }
     static const bool attr = [] {
         return cudaFuncSetAttribute(k_l96_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -736,12 +858,13 @@ void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, co
 }
 
 template void launch_l96_tlm_sweep<double>(cudaStream_t, int, int, int, double, const double *, int, double *,
-                                           int64_t);
-template void launch_l96_tlm_sweep<float>(cudaStream_t, int, int, int, double, const float *, int, float *, int64_t);
+                                           int64_t, int *, unsigned);
+template void launch_l96_tlm_sweep<float>(cudaStream_t, int, int, int, double, const float *, int, float *, int64_t,
+                                          int *, unsigned);
 template void launch_l96_adj_sweep<double>(cudaStream_t, int, int, int, double, const double *, int, double *,
-                                           int64_t, int, double, int, int, int);
+                                           int64_t, int, double, int, int, int, int *, unsigned);
 template void launch_l96_adj_sweep<float>(cudaStream_t, int, int, int, double, const float *, int, float *, int64_t,
-                                          int, double, int, int, int);
+                                          int, double, int, int, int, int *, unsigned);
 
 // Nonlinear RK4 run in FP64 on one CTA: traj[g+1] = RK4(traj[g]) for
 // g < nsteps, storing the stage states of every step; with eta (forcing,
@@ -791,9 +914,9 @@ __global__ void __launch_bounds__(1024) k_l96_run(int n, int nsteps, double F, d
                     }
                 }
             } else {
-#pragma unroll
                 const bool forced = eta && (g + 1) % steps == 0;
                 const double *eg = forced ? eta + (int64_t)((g + 1) / steps) * n : nullptr;
+#pragma unroll
                 for (int r = 0; r < R; ++r) {
                     int j = tid + r * nt;
                     if (j < n) {

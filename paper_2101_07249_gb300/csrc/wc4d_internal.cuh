@@ -114,7 +114,8 @@ struct wc4d_ctx {
     DevBuf tc_part, tc_err;
     bool tc_err_zeroed = false;
     bool gram_tc = true;        // FP32 Gram and tall products on the tensor cores when the shape allows (wc4d_set_gram_path)
-    bool tc_err_pending = false;  // a tensor-core Gram or tall product ran since the error flag was last read
+    bool tc_err_pending = false;  // a kernel with bounded copy waits (tensor-core Gram or tall product, FP32
+                                  // Lorenz-96 sweep) ran since tc_err was last read
     DevBuf oz_slices, oz_work;
     DevBuf chol_bar;            // grid-barrier counter of the cooperative Cholesky
     DevBuf tall_ys, tall_ws;    // TF32 hi / lo halves of the tall product's operands
@@ -354,13 +355,17 @@ void launch_axpby(cudaStream_t s, int64_t n, double alpha, const T *x, double be
 void launch_sub_f64(cudaStream_t s, int64_t n, const double *a, const double *b, double *out);
 void launch_add_f32_to_f64(cudaStream_t s, int64_t n, const float *a, double *b);
 
-// Lorenz-96 sweeps (one CTA per probe column, state kept on chip)
+// Lorenz-96 sweeps (state kept on chip).  The FP32 register-blocked form
+// bounds its waits on the staged stage states by wait_limit polls and sets
+// *err (when err is not null) if one gives up; the other forms have no waits
+// and ignore both.
 template <typename T>
 void launch_l96_tlm_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
-                          int64_t ld);
+                          int64_t ld, int *err, unsigned wait_limit);
 template <typename T>
 void launch_l96_adj_sweep(cudaStream_t s, int n, int N, int steps, double dt, const T *stages, int K, T *W,
-                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride);
+                          int64_t ld, int obs_mode, double obs_scale, int obs_stride, int obs_t0, int obs_tstride,
+                          int *err, unsigned wait_limit);
 void launch_l96_run(cudaStream_t s, int n, int nsteps, double F, double dt, double *traj, double *stages,
                     const double *eta, int steps);
 void launch_l96_stages(cudaStream_t s, int n, int nsteps, double F, double dt, const double *traj, double *stages);

@@ -1,10 +1,11 @@
 """The Lorenz-96 window at its own grid size (n = 8192, the benchmark's
 nonlinear window, here with N = 2 subwindows of 8 RK4 steps) against the
 FP64 oracle's tangent-linear / adjoint Hessian product along the same
-trajectory: one column (the PCG matvec, one 8-CTA cluster per column with
-halos in distributed shared memory), a ragged block and the 256-column
-sketch block (one CTA per column), in FP64 (1e-12) and in the mixed
-precision (FP32 sweeps along the FP32 trajectory, 2e-5)."""
+trajectory: one column (the PCG matvec: in FP64 one 8-CTA cluster per column
+with halos in distributed shared memory, in FP32 the register-blocked sweep
+with one column per CTA), a ragged block and the 256-column sketch block (two
+columns per CTA in FP32), in FP64 (1e-12) and in the mixed precision (FP32
+sweeps along the FP32 trajectory, 2e-5)."""
 import numpy as np
 import pytest
 
@@ -65,10 +66,11 @@ def test_l96_n8192_rhs_and_sweeps_match_oracle():
 
 @pytest.mark.parametrize("n,N,K", [(256, 3, 1), (256, 3, 70), (768, 2, 65), (2048, 2, 3), (2048, 2, 96)])
 def test_l96_register_blocked_sizes_match_oracle(n, N, K):
-    """Grid sizes where the register-blocked sweeps run with 8 points per
-    thread (n = 256: one warp, every halo wraps within it; n = 768: three
-    warps) or 16 (n = 2048, 8192), one or two columns per CTA (K >= 64,
-    FP32) and a partly filled last CTA."""
+    """Grid sizes where the FP32 register-blocked sweeps run (8 points per
+    thread; n = 256: one warp, every halo wraps within it; n = 768: three
+    warps; n = 2048: eight), one or two columns per CTA (K >= 64) and a
+    partly filled last CTA; the FP64 products run the cluster (K <= 32) and
+    one-CTA-per-column sweeps on the same grids."""
     cfg = inputs.L96.replace(name=f"l96_n{n}_N{N}", n=n, N=N, steps=4)
     tw = inputs.twin(cfg, spinup=5.0)
     S = w.Solver(cfg, tw)
