@@ -622,11 +622,46 @@ __device__ __forceinline__ void rb_abort(const RbCta &L, const RbRing &R, int xb
     if (err) atomicExch(err, 1);
 }
 
+// A thread's eight points of one column of W: two 16-byte accesses when W
+// and its leading dimension allow (vec), else eight 4-byte ones.
+__device__ __forceinline__ void rb_load8(const float *w, bool vec, float (&v)[RB_P])
+{
+    if (vec) {
+        const float4 a = *reinterpret_cast<const float4 *>(w), b = *reinterpret_cast<const float4 *>(w + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) v[p] = w[p];
+    }
+}
+__device__ __forceinline__ void rb_store8(float *w, bool vec, const float (&v)[RB_P])
+{
+    if (vec) {
+        *reinterpret_cast<float4 *>(w) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(w + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) w[p] = v[p];
+    }
+}
+// Bit p set when grid point j0 + p is observed (every obs_stride-th point).
+__device__ __forceinline__ unsigned rb_obs_mask(int j0, int obs_stride)
+{
+    unsigned m = 0;
+    int r = j0 % obs_stride;
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        if (r == 0) m |= 1u << p;
+        r = (r + 1 == obs_stride) ? 0 : r + 1;
+    }
+    return m;
+}
+
 // Forward sweep L^{-1} (w_{t+1} += M_t w_t) for columns blockIdx.x*C .. +C-1 (< K).
 template <int C>
 __global__ void __launch_bounds__(1024, 1)
 k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K,
-             int *err, unsigned limit)
+             int vec, int *err, unsigned limit)
 {
     constexpr int P = RB_P, D = RB_NB - 1;
     extern __shared__ __align__(16) float rsm[];
@@ -639,9 +674,10 @@ k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = blockIdx.x * C + c;
-        const float *w = W + (int64_t)min(col, K - 1) * ld + j0;
+        float v[P];
+        rb_load8(W + (int64_t)min(col, K - 1) * ld + j0, vec, v);
 #pragma unroll
-        for (int p = 0; p < P; ++p) u[p][c] = (col < K) ? w[p] : 0.f;
+        for (int p = 0; p < P; ++p) u[p][c] = (col < K) ? v[p] : 0.f;
     }
     rb_store_base<C>(L, u);
     int q = 0, xb = 0;                                     // stages begun; ring buffer of the next
@@ -666,12 +702,14 @@ k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
             const int col = blockIdx.x * C + c;
             if (col >= K) continue;
             float *wn = W + (int64_t)col * ld + (int64_t)(t + 1) * n + j0;
+            float v[P];
+            rb_load8(wn, vec, v);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float v = u[p][c] + wn[p];
-                wn[p] = v;
-                u[p][c] = v;
+                v[p] = u[p][c] + v[p];
+                u[p][c] = v[p];
             }
+            rb_store8(wn, vec, v);
         }
         rb_store_base<C>(L, u);
     }
@@ -683,7 +721,7 @@ k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
 template <int C>
 __global__ void __launch_bounds__(1024, 1)
 k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages, float *W, int64_t ld, int K,
-             int obs_mode, float obs_scale, int obs_stride, int t0, int ts, int *err, unsigned limit)
+             int obs_mode, float obs_scale, int obs_stride, int t0, int ts, int vec, int *err, unsigned limit)
 {
     constexpr int P = RB_P, D = RB_NB - 1;
     extern __shared__ __align__(16) float rsm[];
@@ -696,17 +734,20 @@ k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
     float u[P][C], acc[P][C];
     {
         const bool ob = obs_at(N);
+        const unsigned om = obs_mode == 1 ? rb_obs_mask(j0, obs_stride) : 0u;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int col = blockIdx.x * C + c;
             float *wN = W + (int64_t)min(col, K - 1) * ld + (int64_t)N * n + j0;
+            float v[P];
+            rb_load8(wN, vec, v);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float v = (col < K) ? wN[p] : 0.f;
-                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
-                if (col < K) wN[p] = v;
-                u[p][c] = v;
+                if (col >= K) v[p] = 0.f;
+                if (obs_mode == 1) v[p] = (ob && ((om >> p) & 1u)) ? obs_scale * v[p] : 0.f;
+                u[p][c] = v[p];
             }
+            if (col < K) rb_store8(wN, vec, v);
         }
         rb_store_base<C>(L, u);
 #pragma unroll
@@ -732,6 +773,7 @@ k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
         if (!good) break;
         // subwindow boundary: lam = obs(w_t) + lam, w_t = lam, a = h/6 lam
         const bool ob = obs_at(t);
+        const unsigned om = obs_mode == 1 ? rb_obs_mask(j0, obs_stride) : 0u;
         float lam[P][C];
 #pragma unroll
         for (int q = 0; q < P * C / 4; ++q) {
@@ -745,13 +787,15 @@ k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
             const int col = blockIdx.x * C + c;
             if (col >= K) continue;
             float *wt = W + (int64_t)col * ld + (int64_t)t * n + j0;
+            float v[P];
+            rb_load8(wt, vec, v);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float v = wt[p];
-                if (obs_mode == 1) v = (ob && (j0 + p) % obs_stride == 0) ? obs_scale * v : 0.f;
-                lam[p][c] += v;
-                wt[p] = lam[p][c];
+                if (obs_mode == 1) v[p] = (ob && ((om >> p) & 1u)) ? obs_scale * v[p] : 0.f;
+                lam[p][c] += v[p];
+                v[p] = lam[p][c];
             }
+            rb_store8(wt, vec, v);
         }
         rb_store_base<C>(L, lam);
 #pragma unroll
@@ -782,8 +826,9 @@ static void launch_tlm_rb(cudaStream_t s, int n, int N, int steps, double dt, co
                                     (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
     }();   // once, thread-safe
     (void)attr;
+    const int vec = (reinterpret_cast<uintptr_t>(W) % 16 == 0 && ld % 4 == 0) ? 1 : 0;
     WC4D_LAUNCH(k_l96_tlm_rb<C><<<ceil_div(K, C), n / RB_P, rb_smem<C>(n), s>>>(n, N, steps, (float)dt, stages, W, ld,
-                                                                                K, err, limit));
+                                                                                K, vec, err, limit));
 }
 
 template <int C>
@@ -796,9 +841,10 @@ static void launch_adj_rb(cudaStream_t s, int n, int N, int steps, double dt, co
                                     (int)rb_smem<C>(WC4D_FFT_MAX_N)) == cudaSuccess;
     }();   // once, thread-safe
     (void)attr;
+    const int vec = (reinterpret_cast<uintptr_t>(W) % 16 == 0 && ld % 4 == 0) ? 1 : 0;
     WC4D_LAUNCH(k_l96_adj_rb<C><<<ceil_div(K, C), n / RB_P, rb_smem<C>(n), s>>>(
         n, N, steps, (float)dt, stages, W, ld, K, obs_mode, (float)obs_scale, obs_stride, obs_t0,
-        obs_tstride > 0 ? obs_tstride : 1, err, limit));
+        obs_tstride > 0 ? obs_tstride : 1, vec, err, limit));
 }
 
 template <typename T>

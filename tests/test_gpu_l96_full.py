@@ -84,3 +84,29 @@ def test_l96_register_blocked_sizes_match_oracle(n, N, K):
     w.wc4d_hvp(S.ctx, torch.as_tensor(X, dtype=torch.float32, device="cuda"), Y32, K, cfg.nA, w.MIXED)
     assert colrel(Y32.double().cpu().numpy(), ref) < 2e-5
     S.close()
+
+
+def test_l96_fp32_sweeps_with_any_leading_dimension():
+    """At subwindow boundaries the FP32 register-blocked sweeps read and write
+    a thread's eight points of W with two 16-byte accesses when W and its
+    leading dimension allow (ld = nA here), else with eight 4-byte ones
+    (ld = nA + 1): both forms give the same L^{-1} and L^{-T}, bit for bit,
+    and match the oracle's to FP32 accuracy, for one column and a block of
+    two columns per CTA."""
+    cfg = inputs.L96.replace(name="l96_n256_N3", n=256, N=3, steps=4)
+    tw = inputs.twin(cfg, spinup=5.0)
+    S = w.Solver(cfg, tw)
+    p = oracle_problem(cfg, xb=tw.xb)
+    nA = cfg.nA
+    for K in (1, 66):
+        X = inputs.block(1300 + K, nA, K)
+        for apply, ref in ((w.wc4d_apply_linv, oracle.Linv(p, X)), (w.wc4d_apply_linvT, oracle.LinvT(p, X))):
+            out = []
+            for ld in (nA, nA + 1):
+                Wb = torch.zeros(K, ld, dtype=torch.float32, device="cuda")
+                Wb[:, :nA] = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+                apply(S.ctx, Wb, K, ld, w.MIXED)
+                out.append(Wb[:, :nA].cpu())
+            assert torch.equal(out[0], out[1])
+            assert colrel(out[0].double().numpy(), ref) < 2e-5
+    S.close()
