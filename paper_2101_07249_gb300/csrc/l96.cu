@@ -372,7 +372,7 @@ __device__ __forceinline__ RbCta rb_setup(float *sm, int n, unsigned limit)
 // ring buffer b.  The buffer was last read before the barrier the caller has
 // passed; the proxy fence orders those generic-proxy reads before the
 // asynchronous write.
-__device__ __forceinline__ void rb_fetch(const RbCta &L, RbRing &R, int b, const float *__restrict__ src)
+__device__ __forceinline__ void rb_fetch(const RbCta &L, int b, const float *__restrict__ src)
 {
     if (src && L.tau == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -485,7 +485,7 @@ __device__ __forceinline__ bool rb_stage_begin(const RbCta &L, RbRing &R, int xb
     const bool ok = rb_wait(L, R, xb);
     rb_publish<C>(L, e, u, p0, p1);
     if (__syncthreads_or(!ok)) return false;
-    rb_fetch(L, R, xb == 0 ? RB_NB - 1 : xb - 1, next);
+    rb_fetch(L, xb == 0 ? RB_NB - 1 : xb - 1, next);
     return true;
 }
 
@@ -593,9 +593,8 @@ __device__ __forceinline__ bool rb_adj_stage(const RbCta &L, RbRing &R, int &xb,
 
 // Set up the ring: thread 0 initialises its mbarriers and starts the copies
 // of the first RB_NB - 1 stage states (stage indices first, first + dir, ...).
-template <int C>
-__device__ __forceinline__ void rb_ring_start(const RbCta &L, RbRing &R, const float *__restrict__ stages, int S,
-                                              int first, int dir)
+__device__ __forceinline__ void rb_ring_start(const RbCta &L, const float *__restrict__ stages, int S, int first,
+                                              int dir)
 {
     if (L.tau == 0) {
         for (int b = 0; b < RB_NB; ++b) sw_mb_init(L.mb0 + 8 * b, 1);
@@ -604,7 +603,7 @@ __device__ __forceinline__ void rb_ring_start(const RbCta &L, RbRing &R, const f
     __syncthreads();
     for (int d = 0; d < RB_NB - 1; ++d) {
         const int si = first + dir * d;
-        rb_fetch(L, R, d, (si >= 0 && si < S) ? stages + (int64_t)si * L.n : nullptr);
+        rb_fetch(L, d, (si >= 0 && si < S) ? stages + (int64_t)si * L.n : nullptr);
     }
 }
 
@@ -669,7 +668,7 @@ k_l96_tlm_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
     RbRing R;
     const int j0 = L.tau * P;
     const int S = 4 * N * steps;                           // stage states, used in order 0 .. S - 1
-    rb_ring_start<C>(L, R, stages, S, 0, 1);
+    rb_ring_start(L, stages, S, 0, 1);
     float u[P][C], acc[P][C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -729,7 +728,7 @@ k_l96_adj_rb(int n, int N, int steps, float h, const float *__restrict__ stages,
     RbRing R;
     const int j0 = L.tau * P;
     const int S = 4 * N * steps;                           // stage states, used in order S - 1 .. 0
-    rb_ring_start<C>(L, R, stages, S, S - 1, -1);
+    rb_ring_start(L, stages, S, S - 1, -1);
     auto obs_at = [&](int t) { return t >= t0 && (t - t0) % ts == 0; };
     float u[P][C], acc[P][C];
     {
