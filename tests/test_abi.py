@@ -62,3 +62,12 @@ def test_create_rejects_bad_problems_without_touching_the_gpu(lib):
     p.sigma_o2, p.n = 0.01, 16384                             # n too large for the on-chip FFT
     assert lib.wc4d_create(C.byref(ctx), C.byref(p), None) == w.EINVAL
     assert lib.wc4d_hvp(None, None, None, 1, 1, 0) == w.EINVAL
+
+
+def test_wait_controls_reject_a_null_context_without_touching_the_gpu(lib):
+    """wc4d_set_wait_limit and wc4d_sync check their arguments before any
+    CUDA call: a null context is EINVAL, whatever the limit."""
+    import paper_2101_07249_gb300 as w
+    assert lib.wc4d_sync(None) == w.EINVAL
+    assert lib.wc4d_set_wait_limit(None, 0) == w.EINVAL
+    assert lib.wc4d_set_wait_limit(None, -1) == w.EINVAL
