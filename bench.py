@@ -342,7 +342,9 @@ def lorenz96_window(w, inputs, rank, stream, outer_loops=3, maxit=100, sm_mhz=20
 
 def profile_l96_hvp(inputs, K=256, blocks=2):
     """A short program for ncu captures of the Lorenz-96 stencil sweeps: the
-    n = 8192 window cut to N = 2 subwindows, two K-column FP32 Hessian blocks."""
+    n = 8192 window cut to N = 2 subwindows, two K-column FP32 Hessian blocks
+    (K = 256: the sketch's block, two columns per CTA; K = 1: the PCG
+    matvec, one CTA)."""
     import torch
     import paper_2101_07249_gb300 as w
     w.load()
@@ -491,6 +493,9 @@ def main():
                     help="large: n=4096 N=40 (the benchmark); medium: N=8 (profiling captures); tiny: n=100 N=5; "
                          "l96_hvp: two K=256 FP32 Hessian blocks on a 2-subwindow Lorenz-96 window "
                          "(profiling captures of the stencil sweeps, with --profile-run)")
+    ap.add_argument("--l96-k", type=int, default=256,
+                    help="with --workload l96_hvp: columns of each Hessian block (256: the sketch's block; 1: the "
+                         "PCG matvec)")
     ap.add_argument("--profile-run", action="store_true",
                     help="only --warmup inner loops and one more, then exit (a short program for ncu captures)")
     ap.add_argument("--eager", action="store_true",
@@ -502,7 +507,7 @@ def main():
     if args.workload == "l96_hvp":
         if not args.profile_run:
             ap.error("--workload l96_hvp is a profiling case: give --profile-run")
-        profile_l96_hvp(inputs)
+        profile_l96_hvp(inputs, K=args.l96_k)
         return
     cfg = {"large": inputs.LARGE, "medium": inputs.MEDIUM, "tiny": inputs.TINY}[args.workload]
     if args.impl == "reference":

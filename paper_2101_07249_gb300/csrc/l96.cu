@@ -402,18 +402,38 @@ __device__ __forceinline__ bool rb_wait(const RbCta &L, RbRing &R, int b)
     }
 }
 
-// x_{8 tau - 2 + q}, q = 0 .. 11, from ring buffer b.
+// x_{8 tau - 2 + q}, q = 0 .. 11, from ring buffer b.  ROT: the four
+// 16-byte units 2 tau - 1 .. 2 tau + 2 (left neighbour's upper half, own two
+// halves, right neighbour's lower half) as four 128-bit loads, lanes with bit
+// 2 set taking them rotated by one, so that the eight lanes of a
+// quarter-warp hit 32 distinct banks in every load (16 wavefronts a warp,
+// against 32 for the two own loads at a 32-byte stride and the two 64-bit
+// halo loads); the selects that undo the rotation cost registers, so the
+// two-column sweeps keep the plain form.
+template <bool ROT>
 __device__ __forceinline__ void rb_read_x(const RbCta &L, int b, float (&X)[RB_P + 4])
 {
     const float *xs = L.sm + L.ring0 + b * L.n;
-    const float2 lh = *reinterpret_cast<const float2 *>(xs + RB_P * L.tm1 + RB_P - 2);
-    const float4 a = *reinterpret_cast<const float4 *>(xs + RB_P * L.tau);
-    const float4 c = *reinterpret_cast<const float4 *>(xs + RB_P * L.tau + 4);
-    const float2 rh = *reinterpret_cast<const float2 *>(xs + RB_P * L.tp1);
-    X[0] = lh.x; X[1] = lh.y;
-    X[2] = a.x; X[3] = a.y; X[4] = a.z; X[5] = a.w;
-    X[6] = c.x; X[7] = c.y; X[8] = c.z; X[9] = c.w;
-    X[10] = rh.x; X[11] = rh.y;
+    if constexpr (ROT) {
+        const float4 *u4 = reinterpret_cast<const float4 *>(xs);
+        const bool r = (L.tau >> 2) & 1;
+        const int um = 2 * L.tm1 + 1, u0 = 2 * L.tau, u1 = u0 + 1, u2 = 2 * L.tp1;
+        const float4 v0 = u4[r ? u0 : um], v1 = u4[r ? u1 : u0], v2 = u4[r ? u2 : u1], v3 = u4[r ? um : u2];
+        const float4 lh = r ? v3 : v0, a = r ? v0 : v1, c = r ? v1 : v2, rh = r ? v2 : v3;
+        X[0] = lh.z; X[1] = lh.w;
+        X[2] = a.x; X[3] = a.y; X[4] = a.z; X[5] = a.w;
+        X[6] = c.x; X[7] = c.y; X[8] = c.z; X[9] = c.w;
+        X[10] = rh.x; X[11] = rh.y;
+    } else {
+        const float2 lh = *reinterpret_cast<const float2 *>(xs + RB_P * L.tm1 + RB_P - 2);
+        const float4 a = *reinterpret_cast<const float4 *>(xs + RB_P * L.tau);
+        const float4 c = *reinterpret_cast<const float4 *>(xs + RB_P * L.tau + 4);
+        const float2 rh = *reinterpret_cast<const float2 *>(xs + RB_P * L.tp1);
+        X[0] = lh.x; X[1] = lh.y;
+        X[2] = a.x; X[3] = a.y; X[4] = a.z; X[5] = a.w;
+        X[6] = c.x; X[7] = c.y; X[8] = c.z; X[9] = c.w;
+        X[10] = rh.x; X[11] = rh.y;
+    }
 }
 
 // Base-state quad s of this thread.
@@ -504,7 +524,7 @@ __device__ __forceinline__ bool rb_tlm_stage(const RbCta &L, RbRing &R, int &xb,
     rb_edge_b<C>(L, e, L.tp1, up1);                        // u_{8 tau + 8}
     rb_edge_a<C>(L, e, L.tm1, lm2, lm1);                   // u_{8 tau - 2}, u_{8 tau - 1}
     float X[P + 4];
-    rb_read_x(L, xb, X);
+    rb_read_x<C == 1>(L, xb, X);
     const float cf = (I == 2) ? h : 0.5f * h;
     float dq[4];
 #pragma unroll
@@ -552,7 +572,7 @@ __device__ __forceinline__ bool rb_adj_stage(const RbCta &L, RbRing &R, int &xb,
     rb_edge_b<C>(L, e, L.tm1, am1);                        // a_{8 tau - 1}
     rb_edge_a<C>(L, e, L.tp1, apa, apb);                   // a_{8 tau + 8}, a_{8 tau + 9}
     float X[P + 4];
-    rb_read_x(L, xb, X);
+    rb_read_x<C == 1>(L, xb, X);
     float dq[4], lq[4];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
